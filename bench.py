@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark: smoothed time-steps per second of the parallel MAP smoother.
+
+Workload (one "step" = one complete MAP solve, elements -> filter scan -> RTS
+pass -> x* written): the 2-D Wiener-velocity model (nx = 4, ny = 2, q = 1,
+r = 0.1), dt = 1e-3, T = 2^20 intervals, FP32, seeded synthetic observations
+resident in HBM.  The L2 cache (129 MB) is flushed by writing a 256 MiB buffer
+before every timed step; each step is timed with CUDA events on the solve's
+stream.  With --gpus N > 1 (torchrun) every rank solves its own independent
+problem (replicas; the path has no cross-GPU exchange) and the value is the
+total over ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (sequential Kalman filter + RTS
+smoother in plain C, one core) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("smoothed time-steps/sec at nx=4,T=2^20 (parallel vs sequential, same GB300) "
+          "and % HBM roofline")
+UNIT = "time-steps/s"
+T_FULL = 2 ** 20
+DT = 1e-3
+WORKLOAD = "wiener-velocity 2-D (nx=4, ny=2, q=1, r=0.1), dt=1e-3, T=2^20, RTS smoother"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM, SMS, MAX_SM_MHZ = 128, 152, 2070.0
+
+
+def model_and_data(seed, T=T_FULL):
+    from paper_2512_13319_gb300 import synth
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    _, y = synth.simulate(model, T, DT, seed=seed, substeps=1)
+    return model, y
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work per step (multiply-adds; FLOP = 2 MAC) of each phase, for
+# state dimension n, measurement dimension m, K steps per thread, B threads per tile
+# ----------------------------------------------------------------------------
+def work_model(n, m, K, B, wbytes):
+    combine = 8 * n ** 3 + 5 * n ** 2
+    apply_alpha = 4.5 * n ** 3 + 4.5 * n ** 2
+    apply_plain = 4.5 * n ** 3 + 2.5 * n ** 2
+    compose = n ** 3 + n ** 2
+    aff_apply = n ** 2
+    L = B * K
+    tree = (B - 1) / L
+    ne = n * n + 2 * n + n * (n + 1)       # element components
+    na = n * n + n                          # closed-loop map components
+    mac = {
+        "filter_reduce": (K - 1) / K * combine + tree * combine,
+        "filter_down": tree * (combine + apply_plain + compose) + apply_alpha + compose,
+        "rts_down": tree * (compose + aff_apply) + aff_apply,
+    }
+    byt = {   # minimal HBM bytes per step of each kernel
+        "filter_reduce": wbytes * (m + ne / K),
+        "filter_down": wbytes * (m + ne / K + na + na / K),
+        "rts_down": wbytes * (na + na / K + n),
+    }
+    return {k: 2 * v for k, v in mac.items()}, byt
+
+
+def solve_bytes(n, m, wbytes):
+    """Minimal bytes of one solve per step: y in, x out (the rest is intermediate)."""
+    return wbytes * (m + n)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid):
+        self.proc = None
+        self.lines = []
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if device_uuid:
+                cmd += ["-i", device_uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self, t0, t1):
+        rows = []
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(p[0].split(".")[0], "%Y/%m/%d %H:%M:%S")) + \
+                    float("0." + p[0].split(".")[1]) if "." in p[0] else 0.0
+                rows.append((ts, float(p[1]), float(p[2]), p))
+            except Exception:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "nvidia-smi gave no samples"}
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15]
+        note = "samples inside the timed region"
+        if not inside:
+            inside = rows
+            note = "timed region shorter than the sampling period: samples of warm-up + timed region"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[3][5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "note": note}
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def time_oracle(model, y, budget_s, min_runs=1):
+    import oracle
+    runs, t_tot = 0, 0.0
+    while runs < min_runs or t_tot < budget_s:
+        t = time.perf_counter()
+        oracle.smooth_lti(model, y, DT)
+        t_tot += time.perf_counter() - t
+        runs += 1
+    return t_tot / runs, runs
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    # per-step sample sized so that warm-up + timed steps take about a minute
+    model, y_full = model_and_data(1001)
+    probe_T = 2 ** 14
+    t_probe, _ = time_oracle(model, y_full[:probe_T], 0.2)
+    per_step = t_probe / probe_T
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    Ts = int(min(T_FULL, max(1024, budget / per_step)))
+    y = y_full[:Ts]
+    for _ in range(args.warmup):
+        oracle.smooth_lti(model, y, DT)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.smooth_lti(model, y, DT)
+    dt_run = (time.perf_counter() - t0) / args.steps
+    value = Ts / dt_run
+    sample = f"first {Ts} of the 2^20 intervals per step (FP64 KF + RTS, plain C, 1 thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_run * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": Ts, "nx": 4, "ny": 2, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_13319_gb300 import MapSmoother
+    from paper_2512_13319_gb300 import build as _b
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _b.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prec = args.precision
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    wbytes = 4 if prec == "fp32" else 8
+    model, y_np = model_and_data(1001 + rank)
+    T = T_FULL
+    y = torch.tensor(y_np, dtype=dtype, device=dev)
+    x = torch.empty((T + 1, 4), dtype=dtype, device=dev)
+    sm = MapSmoother(model, T, DT, precision=prec)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(3, args.warmup)):
+        sm.solve(y, x_out=x)
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)                  # let the sampler start before the timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        sm.solve(y, x_out=x)
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    ms = max_over_ranks(ms)
+    value = world * T / (ms * 1e-3)
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    # end to end through the host-buffer C-ABI call (H2D of y, D2H of x inside)
+    y_host = torch.tensor(y_np, dtype=dtype).pin_memory()
+    x_host = torch.empty((T + 1, 4), dtype=dtype).pin_memory()
+    for _ in range(3):
+        sm.solve_host(y_host, x_host)
+    ke = max(3, min(args.steps, 50))
+    barrier()
+    t = time.perf_counter()
+    for _ in range(ke):
+        sm.solve_host(y_host, x_host)
+    e2e_s = max_over_ranks((time.perf_counter() - t) / ke)
+    e2e = {"value": world * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_host.numel() * wbytes),
+           "d2h_bytes_per_step": int(x_host.numel() * wbytes), "ms_per_step": e2e_s * 1e3}
+
+    # per-phase device times (profiled solves, L2 flushed before each)
+    sm.profile(True)
+    phases = {}
+    for _ in range(10):
+        flush.zero_()
+        sm.solve(y, x_out=x)
+        for k, v in sm.phase_times().items():
+            phases.setdefault(k, []).append(v)
+    sm.profile(False)
+    phase_ms = {k: statistics.median(v) for k, v in phases.items()}
+    flops, byt = work_model(4, 2, 8, sm_B(sm), wbytes)
+    dom = max(("filter_reduce", "filter_down", "rts_down"), key=lambda k: phase_ms.get(k, 0.0))
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved_tf = flops[dom] * T / (phase_ms[dom] * 1e-3) / 1e12
+    alu_peak = fp32_peak if prec == "fp32" else fp32_peak / 64.0
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak, "traffic": None, "kernel": dom,
+                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts "
+                                "and max clock)" if prec == "fp32" else "FP32 figure / 64"),
+                "flop_per_step": flops[dom]}
+    per_phase = {k: {"ms": phase_ms[k],
+                     "tflops": (flops[k] * T / (phase_ms[k] * 1e-3) / 1e12) if k in flops else None,
+                     "gbs_min_bytes": (byt[k] * T / (phase_ms[k] * 1e-3) / 1e9) if k in byt else None}
+                 for k in phase_ms}
+    hbm = {"solve_min_bytes_per_step": solve_bytes(4, 2, wbytes),
+           "achieved_gbs": solve_bytes(4, 2, wbytes) * T / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+           "note": "y in + x out over the whole solve; intermediates excluded"}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
+    fb, sing = sm.stats()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": T, "nx": 4, "ny": 2, "precision": prec,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
+        "phases": per_phase, "hbm": hbm, "fp64_recomputes": fb, "singular_pivots": sing,
+    }
+    sm.close()
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        # FP64 path on the same workload
+        sm64 = MapSmoother(model, T, DT, precision="fp64")
+        y64 = y.double()
+        x64 = torch.empty((T + 1, 4), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            sm64.solve(y64, x_out=x64)
+        evs = []
+        for _ in range(5):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sm64.solve(y64, x_out=x64)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        ms64 = statistics.median(a.elapsed_time(b) for a, b in evs)
+        result["fp64"] = {"value": T / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+        sm64.close()
+        # sequential GPU baseline (one thread, KF + RTS), if built
+        seq = sequential_gpu(model, y, dtype, dev, flush, stream)
+        if seq:
+            result["sequential_gpu"] = seq
+            result["speedup_vs_sequential_gpu"] = value / seq["value"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_run, runs = time_oracle(model, y_np, 10.0)
+        result["cpu_baseline"] = {"value": T / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"the full T=2^20 workload, {runs} runs (FP64 KF + RTS, plain C)"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def sm_B(sm):
+    return 128 if sm.dtype.itemsize == 4 else 64
+
+
+def sequential_gpu(model, y, dtype, dev, flush, stream):
+    try:
+        from paper_2512_13319_gb300 import sequential
+    except Exception:
+        return None
+    return sequential.time_sequential(model, y, DT, dtype, dev, flush, stream)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

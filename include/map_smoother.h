@@ -1,0 +1,177 @@
+/*
+ * map_smoother.h - C ABI of the GB300 parallel-in-time MAP trajectory smoother.
+ *
+ * Problem (Section 2.1, Eq. 1-2): estimate the trajectory x(t) of
+ *     dx/dt = f(x, t) + L w(t),     y(t) = h(x, t) + nu(t),
+ * with white noises of spectral densities W and R and prior x(t0) ~ N(m0, P0),
+ * by minimising the Onsager-Machlup functional on the grid t_k = t0 + k dt,
+ * k = 0..T.  The observations are samples y_k = h(x_k) + N(0, R/dt) for
+ * k = 1..T (no measurement at t0).  Each interval [t_k, t_{k+1}] becomes one
+ * conditional value-function element (A, b, C, eta, J) (Section 4.1-4.2,
+ * Eq. 35-37; one explicit Euler step, or the exact exponential solution for
+ * linear time-invariant drift); the filter is the reversed-time all-suffix
+ * scan of Eq. (32) with the combine of Eq. (36); the smoother is either the
+ * RTS-type composition of closed-loop maps (Section 4.3, Eq. 40-42) or the
+ * two-filter combination (Section 4.3, Eq. 43 in information form); nonlinear
+ * models are iterated on their linearisation (Section 4.4).
+ *
+ * Conventions
+ *  - Host arrays in map_problem_desc are FP64, row-major, owned by the caller
+ *    and read only during map_smoother_create.
+ *  - Device arrays passed to solve/grad are owned by the caller, contiguous,
+ *    row-major, in the handle's precision (float for MAP_FP32, double for
+ *    MAP_FP64), resident on the device that was current at create time, and
+ *    16-byte aligned.
+ *  - y has T rows of ny values: row k-1 holds y_k, k = 1..T.
+ *  - x_out has T+1 rows of nx values: row k holds x*_k, k = 0..T.
+ *  - The handle owns its device workspace; destroy frees it.
+ *  - Calls enqueue work on the given CUDA stream (cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and return without waiting, except
+ *    where a host output is requested (noted per call).
+ *  - No exception crosses the ABI.  Every failure returns a negative status;
+ *    map_smoother_last_error() describes the last one.
+ */
+#ifndef MAP_SMOOTHER_H
+#define MAP_SMOOTHER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct map_smoother map_smoother;   /* opaque handle */
+
+typedef enum {
+    MAP_OK = 0,
+    MAP_ERR_INVALID_ARG = -1,   /* null pointer, bad enum, misaligned pointer */
+    MAP_ERR_SHAPE = -2,         /* unsupported nx/ny combination, T < 1 */
+    MAP_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    MAP_ERR_SINGULAR = -4,      /* a matrix that must be invertible was not */
+    MAP_ERR_TIMEOUT = -5,       /* reserved: no call of this library waits on the device */
+    MAP_ERR_UNSUPPORTED = -6    /* valid request this build does not implement */
+} map_status;
+
+typedef enum {
+    MAP_MODEL_LINEAR = 0,       /* f = F x + c, h = H x + r (Eq. 14), time invariant */
+    MAP_MODEL_COORD_TURN = 1,   /* Section 5.2, Eq. 46: nx = 5, ny = 2, range-bearing */
+    MAP_MODEL_CUBIC = 2         /* f = F x + c - gamma x^3 (elementwise), h = H x + r */
+} map_model;
+
+typedef enum { MAP_FP64 = 0, MAP_FP32 = 1 } map_precision;
+
+typedef enum {
+    MAP_EULER = 0,              /* one explicit Euler step of Eq. 37 per interval */
+    MAP_EXPM = 1,               /* exact A, b, C of Eq. 37 (linear models only) */
+    MAP_AUTO = 2                /* MAP_EXPM when |F|_inf dt > 0.05, else MAP_EULER */
+} map_discretisation;
+
+typedef enum { MAP_RTS = 0, MAP_TWO_FILTER = 1 } map_smoother_kind;
+
+typedef struct {
+    int model;                  /* map_model */
+    int nx, ny;                 /* state and measurement dimensions */
+    int nw;                     /* columns of L (dimension of w) */
+    int64_t T;                  /* number of intervals, >= 1 */
+    double t0, dt;              /* grid t_k = t0 + k dt (t0 is unused by autonomous models) */
+    const double *F, *c;        /* nx*nx, nx: linear / cubic drift (NULL c = 0) */
+    const double *L, *W;        /* nx*nw, nw*nw: dispersion and spectral density, Q = L W L^T */
+    const double *H, *r;        /* ny*nx, ny: linear measurement (NULL r = 0) */
+    const double *R;            /* ny*ny: measurement spectral density (diagonal for nonlinear models) */
+    const double *m0, *P0;      /* nx, nx*nx: Gaussian prior of x(t0) */
+    double gamma;               /* cubic drift coefficient (MAP_MODEL_CUBIC) */
+    int precision;              /* map_precision */
+    int discretisation;         /* map_discretisation */
+    int smoother;               /* map_smoother_kind */
+    int gn_iters;               /* nonlinear models: number of linearisation iterations, >= 1 */
+    double cond_max;            /* FP32: recompute a combine in FP64 when the infinity-norm
+                                   condition estimate of (I + C J) exceeds this (0 = 1e6) */
+    int tile_threads;           /* threads per tile CTA, power of two in [32, 256] (0 = tuned) */
+} map_problem_desc;
+
+/*
+ * Validate the problem, discretise it on the device (Euler: Eq. 37 one step;
+ * EXPM: Van Loan block exponentials in FP64) and allocate the workspace for T.
+ * Synchronises the current device.  Returns MAP_ERR_SHAPE for (nx, ny) pairs
+ * without compiled kernels (see map_smoother_supported).
+ */
+map_status map_smoother_create(map_smoother** out, const map_problem_desc* desc);
+
+/*
+ * MAP trajectory for observations y (device, T x ny).
+ *   x_out     device, (T+1) x nx.  For nonlinear models it must hold, on entry,
+ *             the trajectory of the first linearisation (x̄ of Section 4.4);
+ *             on exit it holds the estimate after desc.gn_iters iterations.
+ *   filt_out  device or NULL: (T+1) x (nx + nx(nx+1)/2) filter value functions
+ *             V(x) = 1/2 x^T S_k x - v_k^T x, row k = [v_k, packed upper S_k]
+ *             (S = P^-1 and v = P^-1 m of the Kalman-Bucy filter, Section 2.5);
+ *             for nonlinear models those of the last iteration.
+ *   cost_out  host or NULL: the discrete Onsager-Machlup cost of x_out (needs an
+ *             invertible Q; synchronises the stream).
+ * Asynchronous on `stream` unless cost_out is given.
+ */
+map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void* filt_out,
+                              double* cost_out, void* stream);
+
+/*
+ * End-to-end variant with HOST buffers: copies y_host (T x ny) to the device,
+ * solves, copies the estimate back to x_host ((T+1) x nx) and synchronises
+ * the stream.  For nonlinear models x_host also carries the first
+ * linearisation trajectory in.  Pinned host memory gives the fastest copies.
+ */
+map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_host,
+                                   void* stream);
+
+/*
+ * Gradient of a loss of the MAP trajectory of the last solve with respect to
+ * theta = (F (nx*nx, row-major), log q, log r), where Q = q L W L^T and
+ * R = r R_desc scale with q = r = 1 at the values given to create.
+ *   dL_dx     device (T+1) x nx, or NULL for L = the MAP cost itself.
+ *   dL_dtheta host, nx*nx + 2 values (synchronises the stream).
+ * Linear models, Euler discretisation and invertible Q only (else
+ * MAP_ERR_UNSUPPORTED).
+ */
+map_status map_smoother_grad(map_smoother* h, const void* y, const void* dL_dx,
+                             double* dL_dtheta, void* stream);
+
+/*
+ * Counters of the device-side precision policy since create or the last
+ * reset: [0] combines recomputed in FP64, [1] singular pivots met.
+ * Synchronises the stream.
+ */
+map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int reset, void* stream);
+
+/*
+ * Per-phase device timing.  With profiling on, every solve records CUDA events
+ * on its stream between its kernel launches; map_smoother_phase_times then
+ * returns the durations (ms) of the phases of the last solve, in launch order:
+ *   0 filter_reduce  per-thread folds and tile totals of the elements
+ *   1 filter_tiles   scan of the tile totals (one CTA)
+ *   2 filter_down    per-step filter values, closed-loop maps, their folds
+ *   3 affine_tiles   backward scan of the tile maps (one CTA)
+ *   4 rts_down       per-step smoothed states
+ * (for nonlinear models: those of the last iteration).  phase_times
+ * synchronises the stream of the last solve; *n_out receives the count.
+ */
+map_status map_smoother_profile(map_smoother* h, int enable);
+map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int* n_out);
+
+/* Free the handle and its workspace (NULL is ignored). */
+void map_smoother_destroy(map_smoother* h);
+
+/* Description of the last failure on this handle (or of the last failed create
+ * when h is NULL).  The string lives until the next call on the handle. */
+const char* map_smoother_last_error(const map_smoother* h);
+
+/* 1 when kernels for (model, nx, ny, precision) are compiled in, else 0. */
+int map_smoother_supported(int model, int nx, int ny, int precision);
+
+/* Library version string. */
+const char* map_smoother_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAP_SMOOTHER_H */

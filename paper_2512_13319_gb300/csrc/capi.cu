@@ -1,0 +1,354 @@
+// C ABI of the parallel MAP smoother: argument checks, model set-up, workspace
+// ownership and dispatch to the compiled (model, N, M, precision) instances.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+namespace mapk {
+
+template <int N, int M, typename S> const Ops* linear_ops();
+template <typename S> const Ops* coord_turn_ops();
+template <int N, int M, typename S> const Ops* cubic_ops();
+
+#define MAP_LINEAR_SHAPES(X) X(2, 1) X(3, 1) X(4, 2) X(5, 2) X(6, 3)
+#define MAP_CUBIC_SHAPES(X) X(2, 2)
+
+const Ops* find_ops(int model, int N, int M, int prec)
+{
+#define CASE_LIN(n, m)                                                        \
+    if (N == n && M == m) return prec == MAP_FP32 ? linear_ops<n, m, float>() \
+                                                  : linear_ops<n, m, double>();
+#define CASE_CUB(n, m)                                                        \
+    if (N == n && M == m) return prec == MAP_FP32 ? cubic_ops<n, m, float>()  \
+                                                  : cubic_ops<n, m, double>();
+    if (model == MAP_MODEL_LINEAR) { MAP_LINEAR_SHAPES(CASE_LIN) }
+    if (model == MAP_MODEL_COORD_TURN && N == 5 && M == 2)
+        return prec == MAP_FP32 ? coord_turn_ops<float>() : coord_turn_ops<double>();
+    if (model == MAP_MODEL_CUBIC) { MAP_CUBIC_SHAPES(CASE_CUB) }
+    return nullptr;
+#undef CASE_LIN
+#undef CASE_CUB
+}
+
+size_t elem_bytes(int prec) { return prec == MAP_FP32 ? 4 : 8; }
+
+map_status fail(map_smoother& h, map_status s, const std::string& msg)
+{
+    h.err = msg;
+    return s;
+}
+
+map_status cuda_fail(map_smoother& h, cudaError_t e, const char* where)
+{
+    h.err = std::string(where) + ": " + cudaGetErrorString(e);
+    return MAP_ERR_CUDA;
+}
+
+}  // namespace mapk
+
+using namespace mapk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+std::vector<double> copy_or(const double* p, size_t n, double fill = 0.0)
+{
+    std::vector<double> v(n, fill);
+    if (p) std::memcpy(v.data(), p, n * sizeof(double));
+    return v;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<size_t>(p) & 15) == 0; }
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+void free_handle(map_smoother* h)
+{
+    if (!h) return;
+    if (h->ws) cudaFree(h->ws);
+    if (h->d_stats) cudaFree(h->d_stats);
+    if (h->d_y) cudaFree(h->d_y);
+    if (h->d_x) cudaFree(h->d_x);
+    if (h->d_xtmp) cudaFree(h->d_xtmp);
+    if (h->d_cost) cudaFree(h->d_cost);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+map_status create_impl(map_smoother* h, const map_problem_desc* d)
+{
+    if (!d) return fail(*h, MAP_ERR_INVALID_ARG, "desc is NULL");
+    const int n = d->nx, m = d->ny, nw = d->nw;
+    if (n < 1 || n > MAXN || m < 1 || m > MAXM || nw < 1 || nw > MAXN)
+        return fail(*h, MAP_ERR_SHAPE, "nx, ny, nw must be in [1, 8]");
+    if (d->T < 1) return fail(*h, MAP_ERR_SHAPE, "T must be >= 1");
+    if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(*h, MAP_ERR_INVALID_ARG, "dt must be positive");
+    if (d->precision != MAP_FP32 && d->precision != MAP_FP64)
+        return fail(*h, MAP_ERR_INVALID_ARG, "unknown precision");
+    if (d->discretisation < MAP_EULER || d->discretisation > MAP_AUTO)
+        return fail(*h, MAP_ERR_INVALID_ARG, "unknown discretisation");
+    if (d->smoother != MAP_RTS && d->smoother != MAP_TWO_FILTER)
+        return fail(*h, MAP_ERR_INVALID_ARG, "unknown smoother");
+    if (!d->L || !d->W || !d->R || !d->m0 || !d->P0)
+        return fail(*h, MAP_ERR_INVALID_ARG, "L, W, R, m0 and P0 are required");
+    const bool linear_like = d->model == MAP_MODEL_LINEAR || d->model == MAP_MODEL_CUBIC;
+    if (linear_like && (!d->F || !d->H))
+        return fail(*h, MAP_ERR_INVALID_ARG, "F and H are required for linear and cubic models");
+    if (d->model == MAP_MODEL_COORD_TURN && (n != 5 || m != 2))
+        return fail(*h, MAP_ERR_SHAPE, "the coordinated-turn model has nx = 5, ny = 2");
+    if (d->model < MAP_MODEL_LINEAR || d->model > MAP_MODEL_CUBIC)
+        return fail(*h, MAP_ERR_INVALID_ARG, "unknown model");
+    if (d->model != MAP_MODEL_LINEAR && d->gn_iters < 1)
+        return fail(*h, MAP_ERR_INVALID_ARG, "gn_iters must be >= 1 for nonlinear models");
+    if (d->smoother == MAP_TWO_FILTER)
+        return fail(*h, MAP_ERR_UNSUPPORTED, "two-filter smoother is not built in this version");
+
+    h->model = d->model; h->N = n; h->M = m; h->NW = nw;
+    h->prec = d->precision; h->smoother = d->smoother;
+    h->gn_iters = d->model == MAP_MODEL_LINEAR ? 1 : d->gn_iters;
+    h->T = (long)d->T; h->dt = d->dt; h->gamma = d->gamma;
+    h->cond_max = d->cond_max > 0 ? d->cond_max : 1e6;
+    h->F = copy_or(d->F, (size_t)n * n);
+    h->c = copy_or(d->c, n);
+    h->L = copy_or(d->L, (size_t)n * nw);
+    h->W = copy_or(d->W, (size_t)nw * nw);
+    h->H = copy_or(d->H, (size_t)m * n);
+    h->r = copy_or(d->r, m);
+    h->R = copy_or(d->R, (size_t)m * m);
+    h->m0 = copy_or(d->m0, n);
+    h->P0 = copy_or(d->P0, (size_t)n * n);
+
+    const Ops* ops = find_ops(h->model, n, m, h->prec);
+    if (!ops) return fail(*h, MAP_ERR_SHAPE, "no compiled kernels for this (model, nx, ny, precision)");
+
+    int disc = d->discretisation;
+    if (disc == MAP_AUTO) {
+        double nF = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += std::fabs(h->F[i * n + j]);
+            nF = std::max(nF, s);
+        }
+        disc = (h->model == MAP_MODEL_LINEAR && nF * h->dt > 0.05) ? MAP_EXPM : MAP_EULER;
+    }
+    if (disc == MAP_EXPM && h->model != MAP_MODEL_LINEAR)
+        return fail(*h, MAP_ERR_UNSUPPORTED, "exact discretisation needs a linear drift");
+    h->disc = disc;
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return cuda_fail(*h, e, "cudaGetDevice");
+
+    // model set-up on the device (FP64)
+    {
+        DevBuf in, out;
+        const size_t nin = (size_t)n * n + n + (size_t)n * nw + (size_t)nw * nw + (size_t)m * n + m +
+                           (size_t)m * m + n + (size_t)n * n;
+        std::vector<double> host;
+        host.reserve(nin);
+        auto push = [&](const std::vector<double>& v) { host.insert(host.end(), v.begin(), v.end()); };
+        push(h->F); push(h->c); push(h->L); push(h->W); push(h->H); push(h->r); push(h->R); push(h->m0);
+        push(h->P0);
+        if ((e = cudaMalloc(&in.p, nin * sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+        if ((e = cudaMalloc(&out.p, sizeof(SetupOut))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+        if ((e = cudaMemcpy(in.p, host.data(), nin * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMemcpy");
+        const double* b = static_cast<const double*>(in.p);
+        SetupIn si{};
+        si.nx = n; si.ny = m; si.nw = nw; si.mode = disc; si.dt = h->dt;
+        size_t o = 0;
+        si.F = b + o; o += (size_t)n * n;
+        si.c = b + o; o += n;
+        si.L = b + o; o += (size_t)n * nw;
+        si.W = b + o; o += (size_t)nw * nw;
+        si.H = b + o; o += (size_t)m * n;
+        si.r = b + o; o += m;
+        si.R = b + o; o += (size_t)m * m;
+        si.m0 = b + o; o += n;
+        si.P0 = b + o;
+        if ((e = launch_setup(si, static_cast<SetupOut*>(out.p), 0)) != cudaSuccess)
+            return cuda_fail(*h, e, "set-up kernel launch");
+        if ((e = cudaMemcpy(&h->consts, out.p, sizeof(SetupOut), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(*h, e, "set-up kernel");
+    }
+    if (h->consts.flags & SETUP_SINGULAR_R) return fail(*h, MAP_ERR_SINGULAR, "R is singular");
+    if (h->consts.flags & SETUP_SINGULAR_P0) return fail(*h, MAP_ERR_SINGULAR, "P0 is singular");
+    if (h->consts.flags & SETUP_SINGULAR_A) return fail(*h, MAP_ERR_SINGULAR, "the interval map A is singular");
+
+    // launch geometry: shared memory of the tile CTA must fit
+    const size_t es = elem_bytes(h->prec);
+    const size_t ncomp = (size_t)n * n + 2 * n + (size_t)n * (n + 1) + n + (size_t)n * (n + 1) / 2;
+    int B = d->tile_threads > 0 ? d->tile_threads : (h->prec == MAP_FP32 ? 128 : 64);
+    if (B < 32 || B > 256 || (B & (B - 1)))
+        return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be a power of two in [32, 256]");
+    while (B > 32 && ncomp * 2 * B * es > 200 * 1024) B /= 2;
+    h->B = B;
+    h->K = 8;
+    const long L = (long)h->B * h->K;
+    h->nt = (int)((h->T + L - 1) / L);
+    h->Tpad = (long)h->nt * L;
+
+    h->ws_bytes = ops->workspace_bytes(*h);
+    if ((e = cudaMalloc(&h->ws, h->ws_bytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc workspace");
+    if ((e = cudaMalloc(&h->d_stats, 2 * sizeof(unsigned long long))) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMalloc");
+    if ((e = cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMemset");
+    if ((e = cudaMalloc(&h->d_cost, sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+    if (h->model != MAP_MODEL_LINEAR) {
+        if ((e = cudaMalloc(&h->d_xtmp, (size_t)(h->T + 1) * n * es)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(*h, e, "create");
+    return MAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+map_status map_smoother_create(map_smoother** out, const map_problem_desc* desc)
+{
+    if (!out) {
+        g_create_error = "out is NULL";
+        return MAP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    map_smoother* h = new (std::nothrow) map_smoother();
+    if (!h) {
+        g_create_error = "out of host memory";
+        return MAP_ERR_INVALID_ARG;
+    }
+    const map_status s = create_impl(h, desc);
+    if (s != MAP_OK) {
+        g_create_error = h->err;
+        free_handle(h);
+        return s;
+    }
+    *out = h;
+    return MAP_OK;
+}
+
+map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void* filt_out,
+                              double* cost_out, void* stream)
+{
+    if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
+    if (!y || !x_out) return fail(*h, MAP_ERR_INVALID_ARG, "y and x_out are required");
+    if (!aligned16(y) || !aligned16(x_out) || (filt_out && !aligned16(filt_out)))
+        return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
+    map_status s = ops->solve(*h, y, x_out, filt_out, st);
+    if (s != MAP_OK) return s;
+    if (cost_out) {
+        if (h->consts.flags & SETUP_SINGULAR_C)
+            return fail(*h, MAP_ERR_UNSUPPORTED, "the MAP cost needs an invertible process noise");
+        if (!ops->cost) return fail(*h, MAP_ERR_UNSUPPORTED, "no cost kernel for this model");
+        s = ops->cost(*h, y, x_out, h->d_cost, st);
+        if (s != MAP_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(cost_out, h->d_cost, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(*h, e, "cost read-back");
+    }
+    return MAP_OK;
+}
+
+map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_host, void* stream)
+{
+    if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
+    if (!y_host || !x_host) return fail(*h, MAP_ERR_INVALID_ARG, "y_host and x_host are required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = elem_bytes(h->prec);
+    const size_t ybytes = (size_t)h->T * h->M * es, xbytes = (size_t)(h->T + 1) * h->N * es;
+    cudaError_t e;
+    if (!h->d_y) {
+        if ((e = cudaMalloc(&h->d_y, ybytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+        if ((e = cudaMalloc(&h->d_x, xbytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+    }
+    if ((e = cudaMemcpyAsync(h->d_y, y_host, ybytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMemcpyAsync H2D");
+    if (h->model != MAP_MODEL_LINEAR &&
+        (e = cudaMemcpyAsync(h->d_x, x_host, xbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMemcpyAsync H2D");
+    map_status s = map_smoother_solve(h, h->d_y, h->d_x, nullptr, nullptr, stream);
+    if (s != MAP_OK) return s;
+    if ((e = cudaMemcpyAsync(x_host, h->d_x, xbytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMemcpyAsync D2H");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(*h, e, "cudaStreamSynchronize");
+    return MAP_OK;
+}
+
+map_status map_smoother_grad(map_smoother* h, const void* y, const void* dL_dx, double* dL_dtheta,
+                             void* stream)
+{
+    (void)y; (void)dL_dx; (void)dL_dtheta; (void)stream;
+    if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
+    return fail(*h, MAP_ERR_UNSUPPORTED, "gradient is not built in this version");
+}
+
+map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int reset, void* stream)
+{
+    if (!h || !out) return MAP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(out, h->d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(*h, e, "stats");
+    return MAP_OK;
+}
+
+map_status map_smoother_profile(map_smoother* h, int enable)
+{
+    if (!h) return MAP_ERR_INVALID_ARG;
+    if (enable && !h->ev[0]) {
+        for (cudaEvent_t& e : h->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(*h, r, "cudaEventCreate");
+        }
+    }
+    h->profile = enable != 0;
+    h->nev = 0;
+    return MAP_OK;
+}
+
+map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int* n_out)
+{
+    if (!h || !ms_out || !n_out) return MAP_ERR_INVALID_ARG;
+    *n_out = 0;
+    if (h->nev < 2) return fail(*h, MAP_ERR_INVALID_ARG, "no profiled solve recorded");
+    cudaError_t e = cudaEventSynchronize(h->ev[h->nev - 1]);
+    if (e != cudaSuccess) return cuda_fail(*h, e, "cudaEventSynchronize");
+    int n = 0;
+    for (int i = 0; i + 1 < h->nev && n < cap; ++i, ++n) {
+        e = cudaEventElapsedTime(ms_out + n, h->ev[i], h->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(*h, e, "cudaEventElapsedTime");
+    }
+    *n_out = n;
+    return MAP_OK;
+}
+
+void map_smoother_destroy(map_smoother* h) { free_handle(h); }
+
+const char* map_smoother_last_error(const map_smoother* h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int map_smoother_supported(int model, int nx, int ny, int precision)
+{
+    if (precision != MAP_FP32 && precision != MAP_FP64) return 0;
+    return find_ops(model, nx, ny, precision) != nullptr;
+}
+
+const char* map_smoother_version(void) { return "0.1.0"; }
+
+}  // extern "C"

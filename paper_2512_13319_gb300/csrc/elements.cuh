@@ -1,0 +1,304 @@
+// Conditional value-function elements and their associative combination.
+//
+// An element is the parameter tuple (A, b, C, eta, J) of the linear-affine
+// conditional value function of Eq. (35),
+//   V(phi; z) = 1/2 phi^T J phi - phi^T eta + 1/2 |z - A phi - b|^2_{C^-1},
+// where phi is the state at the start of the reversed-time interval and z the
+// state at its end.  C and J are symmetric and stored packed.
+//
+// combine(ei, ej) is the rule of Section 4.1 (Eq. 36) for ei on [s, gamma]
+// followed by ej on [gamma, t].  apply(e, P) is the same rule when the right
+// operand is a value function of one variable, V(z) = 1/2 z^T P z - v^T z
+// (A = C = b = 0 for it), i.e. the combination with a suffix that already
+// contains the terminal element a_T of Eq. (31); it also returns the
+// closed-loop affine map (Section 3.5, Eq. 40-41) of the interval,
+//   z*(phi) = E phi + g,  E = (I + C P)^-1 A,  g = (I + C P)^-1 (b + C v),
+// which the RTS pass composes.
+//
+// Precision policy: the (I + C J) inverse runs in the element precision S
+// with diagonal pivots.  When a pivot is small against its column
+// (tau = 1/2) or the infinity-norm condition estimate |M| |M^-1| exceeds the
+// threshold, the whole operation is recomputed in FP64 with row pivoting, and
+// a device counter records it.
+#pragma once
+#include "smallmat.cuh"
+
+namespace mapk {
+
+using ms::Sym;
+
+template <int N, typename S>
+struct Elem {
+    static constexpr int NS = Sym<N>::SZ;
+    static constexpr int NCOMP = N * N + 2 * N + 2 * NS;
+    S A[N * N];
+    S b[N];
+    S C[NS];
+    S eta[N];
+    S J[NS];
+};
+
+// value function of one variable: 1/2 x^T P x - v^T x
+template <int N, typename S>
+struct Red {
+    static constexpr int NS = Sym<N>::SZ;
+    static constexpr int NCOMP = N + NS;
+    S v[N];
+    S P[NS];
+};
+
+// affine map x -> F x + c
+template <int N, typename S>
+struct Aff {
+    static constexpr int NCOMP = N * N + N;
+    S F[N * N];
+    S c[N];
+};
+
+struct CombineCtx {
+    double cond_max;                 // FP64 recompute when |M| |M^-1| exceeds this
+    unsigned long long* stats;       // [0] FP64 recomputations, [1] singular pivots
+};
+
+template <int N, typename S>
+__device__ __forceinline__ void set_identity(Elem<N, S>& e)
+{
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) e.A[i] = (i % (N + 1) == 0) ? S(1) : S(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) { e.b[i] = S(0); e.eta[i] = S(0); }
+#pragma unroll
+    for (int i = 0; i < Elem<N, S>::NS; ++i) { e.C[i] = S(0); e.J[i] = S(0); }
+}
+
+template <int N, typename S>
+__device__ __forceinline__ void set_identity(Aff<N, S>& a)
+{
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) a.F[i] = (i % (N + 1) == 0) ? S(1) : S(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) a.c[i] = S(0);
+}
+
+// flat component access (the order is the SoA component order in memory)
+template <int N, typename S>
+__device__ __forceinline__ S& comp(Elem<N, S>& e, int i)
+{
+    constexpr int NS = Sym<N>::SZ;
+    return i < N * N ? e.A[i]
+         : i < N * N + N ? e.b[i - N * N]
+         : i < N * N + N + NS ? e.C[i - N * N - N]
+         : i < N * N + 2 * N + NS ? e.eta[i - N * N - N - NS]
+         : e.J[i - N * N - 2 * N - NS];
+}
+template <int N, typename S>
+__device__ __forceinline__ S& comp(Red<N, S>& r, int i) { return i < N ? r.v[i] : r.P[i - N]; }
+template <int N, typename S>
+__device__ __forceinline__ S& comp(Aff<N, S>& a, int i) { return i < N * N ? a.F[i] : a.c[i - N * N]; }
+
+// SoA load/store: component i of item `idx` lives at base[i * stride + idx]
+template <class T, typename S>
+__device__ __forceinline__ void soa_load(const S* __restrict__ base, long stride, long idx, T& x)
+{
+#pragma unroll
+    for (int i = 0; i < T::NCOMP; ++i) comp(x, i) = base[i * stride + idx];
+}
+template <class T, typename S>
+__device__ __forceinline__ void soa_store(S* __restrict__ base, long stride, long idx, T& x)
+{
+#pragma unroll
+    for (int i = 0; i < T::NCOMP; ++i) base[i * stride + idx] = comp(x, i);
+}
+
+template <int N, typename Sd, typename Ss>
+__device__ __forceinline__ void convert(const Elem<N, Ss>& s, Elem<N, Sd>& d)
+{
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) d.A[i] = Sd(s.A[i]);
+#pragma unroll
+    for (int i = 0; i < N; ++i) { d.b[i] = Sd(s.b[i]); d.eta[i] = Sd(s.eta[i]); }
+#pragma unroll
+    for (int i = 0; i < Sym<N>::SZ; ++i) { d.C[i] = Sd(s.C[i]); d.J[i] = Sd(s.J[i]); }
+}
+
+// ---------------------------------------------------------------------------
+// (I + C_i J_j) and its inverse; returns false when the fast path is not safe
+// ---------------------------------------------------------------------------
+template <int N, typename S>
+__device__ __forceinline__ bool inverse_I_plus(const S* Cp, const S* Jp, S* Mi, double cond_max,
+                                               bool pivot)
+{
+    S M[N * N];
+    ms::sym_sym<N, S>(Cp, Jp, M);
+#pragma unroll
+    for (int i = 0; i < N; ++i) M[i * N + i] += S(1);
+    if (pivot) return ms::inv_row_pivot<N, S>(M, Mi);
+    const S nM = ms::norm_inf<N, S>(M);
+    const bool ok = ms::inv_diag_pivot<N, S>(M, Mi, S(0.5));
+    const S nMi = ms::norm_inf<N, S>(Mi);
+    return ok && (double(nM) * double(nMi) <= cond_max);
+}
+
+// core of e_i (x) e_j given Mi = (I + C_i J_j)^-1
+template <int N, typename S>
+__device__ __forceinline__ void combine_core(const Elem<N, S>& ei, const Elem<N, S>& ej,
+                                             const S* Mi, Elem<N, S>& out)
+{
+    S T1[N * N], T2[N * N], T3[N * N], u[N], w[N];
+    ms::mm<N, S>(ej.A, Mi, T1);                       // A_j M^-1
+    Elem<N, S> r;
+    ms::mm<N, S>(T1, ei.A, r.A);                      // A_ij
+    ms::sym_v<N, S>(ei.C, ej.eta, u);                 // C_i eta_j
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] += ei.b[i];
+    ms::mv<N, S>(T1, u, w);
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.b[i] = w[i] + ej.b[i];   // b_ij
+    ms::m_sym<N, S>(T1, ei.C, T2);                    // A_j M^-1 C_i
+    ms::sym_abt_add<N, S>(T2, ej.A, ej.C, r.C);       // C_ij
+    ms::mm<N, S>(Mi, ei.A, T3);                       // M^-1 A_i  (= (A_i^T M^-T)^T)
+    ms::sym_v<N, S>(ej.J, ei.b, u);                   // J_j b_i
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = ej.eta[i] - u[i];
+    ms::mtv_add<N, S>(T3, u, ei.eta, r.eta);          // eta_ij
+    ms::sym_m<N, S>(ej.J, ei.A, T2);                  // J_j A_i
+    ms::sym_atb_add<N, S>(T3, T2, ei.J, r.J);         // J_ij
+    out = r;
+}
+
+template <int N, typename S>
+__device__ __noinline__ void combine_fp64(const Elem<N, S>& ei, const Elem<N, S>& ej,
+                                          Elem<N, S>& out, const CombineCtx& ctx)
+{
+    Elem<N, double> di, dj, dr;
+    convert(ei, di);
+    convert(ej, dj);
+    double Mi[N * N];
+    if (!inverse_I_plus<N, double>(di.C, dj.J, Mi, 0.0, true) && ctx.stats)
+        atomicAdd(ctx.stats + 1, 1ull);
+    combine_core<N, double>(di, dj, Mi, dr);
+    convert(dr, out);
+    if (ctx.stats) atomicAdd(ctx.stats, 1ull);
+}
+
+// out = ei (x) ej  (out may alias either operand)
+template <int N, typename S>
+__device__ __forceinline__ void combine(const Elem<N, S>& ei, const Elem<N, S>& ej,
+                                        Elem<N, S>& out, const CombineCtx& ctx)
+{
+    S Mi[N * N];
+    if (inverse_I_plus<N, S>(ei.C, ej.J, Mi, ctx.cond_max, false)) {
+        combine_core<N, S>(ei, ej, Mi, out);
+    } else {
+        combine_fp64<N, S>(ei, ej, out, ctx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// e (x) [P, v]: value-function update and the interval's closed-loop map
+// ---------------------------------------------------------------------------
+template <int N, typename S, bool ALPHA>
+__device__ __forceinline__ void apply_core(const Elem<N, S>& e, Red<N, S>& p, const S* Mi,
+                                           S* E, S* g)
+{
+    S Em[N * N], T4[N * N], u[N], w[N];
+    ms::mm<N, S>(Mi, e.A, Em);                        // E = M^-1 A
+    if (ALPHA) {
+        ms::sym_v<N, S>(e.C, p.v, u);
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[i] += e.b[i];
+        ms::mv<N, S>(Mi, u, g);                       // g = M^-1 (b + C v)
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) E[i] = Em[i];
+    }
+    ms::sym_m<N, S>(p.P, e.A, T4);                    // P A
+    ms::sym_v<N, S>(p.P, e.b, u);                     // P b
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] = p.v[i] - u[i];
+    Red<N, S> r;
+    ms::sym_atb_add<N, S>(Em, T4, e.J, r.P);          // A^T M^-T P A + J
+    ms::mtv_add<N, S>(Em, w, e.eta, r.v);             // A^T M^-T (v - P b) + eta
+    p = r;
+}
+
+template <int N, typename S, bool ALPHA>
+__device__ __noinline__ void apply_fp64(const Elem<N, S>& e, Red<N, S>& p, S* E, S* g,
+                                        const CombineCtx& ctx)
+{
+    Elem<N, double> de;
+    convert(e, de);
+    Red<N, double> dp;
+#pragma unroll
+    for (int i = 0; i < N; ++i) dp.v[i] = double(p.v[i]);
+#pragma unroll
+    for (int i = 0; i < Sym<N>::SZ; ++i) dp.P[i] = double(p.P[i]);
+    double Mi[N * N], dE[N * N], dg[N];
+    if (!inverse_I_plus<N, double>(de.C, dp.P, Mi, 0.0, true) && ctx.stats)
+        atomicAdd(ctx.stats + 1, 1ull);
+    apply_core<N, double, ALPHA>(de, dp, Mi, dE, dg);
+#pragma unroll
+    for (int i = 0; i < N; ++i) p.v[i] = S(dp.v[i]);
+#pragma unroll
+    for (int i = 0; i < Sym<N>::SZ; ++i) p.P[i] = S(dp.P[i]);
+    if (ALPHA) {
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) E[i] = S(dE[i]);
+#pragma unroll
+        for (int i = 0; i < N; ++i) g[i] = S(dg[i]);
+    }
+    if (ctx.stats) atomicAdd(ctx.stats, 1ull);
+}
+
+template <int N, typename S, bool ALPHA>
+__device__ __forceinline__ void apply(const Elem<N, S>& e, Red<N, S>& p, S* E, S* g,
+                                      const CombineCtx& ctx)
+{
+    S Mi[N * N];
+    if (inverse_I_plus<N, S>(e.C, p.P, Mi, ctx.cond_max, false)) {
+        apply_core<N, S, ALPHA>(e, p, Mi, E, g);
+    } else {
+        apply_fp64<N, S, ALPHA>(e, p, E, g, ctx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// affine maps (Eq. 40-41): (F1, c1) o (F2, c2) = (F1 F2, F1 c2 + c1)
+// ---------------------------------------------------------------------------
+template <int N, typename S>
+__device__ __forceinline__ void compose(const Aff<N, S>& a1, const Aff<N, S>& a2, Aff<N, S>& out)
+{
+    Aff<N, S> r;
+    ms::mm<N, S>(a1.F, a2.F, r.F);
+    ms::mv<N, S>(a1.F, a2.c, r.c);
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.c[i] += a1.c[i];
+    out = r;
+}
+
+template <int N, typename S>
+__device__ __forceinline__ void affine_apply(const Aff<N, S>& a, const S* x, S* y)
+{
+    ms::mv<N, S>(a.F, x, y);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] += a.c[i];
+}
+
+// x = P^-1 v (the minimiser of a one-variable value function, Eq. 18 initial condition)
+template <int N, typename S>
+__device__ __forceinline__ bool red_argmin(const Red<N, S>& p, S* x)
+{
+    double M[N * N], Mi[N * N], v[N], xd[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        v[i] = double(p.v[i]);
+#pragma unroll
+        for (int j = 0; j < N; ++j) M[i * N + j] = double(p.P[Sym<N>::at(i, j)]);
+    }
+    const bool ok = ms::inv_row_pivot<N, double>(M, Mi);
+    ms::mv<N, double>(Mi, v, xd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = S(xd[i]);
+    return ok;
+}
+
+}  // namespace mapk

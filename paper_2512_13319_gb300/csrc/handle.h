@@ -1,0 +1,55 @@
+// Host-side handle of the C ABI and the per-instantiation entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/map_smoother.h"
+#include "setup.h"
+
+struct map_smoother {
+    // problem
+    int model = 0, N = 0, M = 0, NW = 0, prec = 0, disc = 0, smoother = 0, gn_iters = 1;
+    long T = 0;
+    double dt = 0, gamma = 0, cond_max = 1e6;
+    int device = 0;
+    std::vector<double> F, c, L, W, H, r, R, m0, P0;
+    mapk::SetupOut consts{};           // FP64 model constants computed on the device
+    // launch geometry
+    int B = 128;                       // threads per tile CTA
+    int K = 8;                         // steps per thread
+    int nt = 0;                        // tiles
+    long Tpad = 0;                     // nt * B * K
+    // device memory owned by the handle
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned long long* d_stats = nullptr;
+    void* d_y = nullptr;               // staging for the host-buffer entry point
+    void* d_x = nullptr;
+    void* d_xtmp = nullptr;            // Gauss-Newton ping-pong trajectory
+    double* d_cost = nullptr;
+    // per-phase timing (map_smoother_profile)
+    bool profile = false;
+    cudaEvent_t ev[8] = {};
+    int nev = 0;
+    std::string err;
+};
+
+namespace mapk {
+
+size_t elem_bytes(int prec);
+
+// Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.
+struct Ops {
+    size_t (*workspace_bytes)(const map_smoother& h);
+    map_status (*solve)(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st);
+    map_status (*cost)(map_smoother& h, const void* y, const void* x, double* d_cost, cudaStream_t st);
+};
+
+const Ops* find_ops(int model, int N, int M, int prec);
+
+map_status fail(map_smoother& h, map_status s, const std::string& msg);
+map_status cuda_fail(map_smoother& h, cudaError_t e, const char* where);
+
+}  // namespace mapk

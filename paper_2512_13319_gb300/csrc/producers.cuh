@@ -1,0 +1,247 @@
+// Element producers: build the interval element (A, b, C, eta, J) of step k in
+// registers from per-step inputs, so elements are never stored.
+//
+// Orientation (time reversal, Section 2.2): element k spans [t_k, t_{k+1}];
+// its start state phi is x_{k+1} and its end state z is x_k.  One explicit
+// Euler step of Eq. (37) from the boundary values A = I, b = C = eta = J = 0
+// gives, with the reversed drift F~ = -F, c~ = -c,
+//   A = I - dt F,  b = -dt c,  C = dt Q,
+//   J = dt H^T R^-1 H,  eta = dt H^T R^-1 (y_{k+1} - r),
+// the measurement term being that of the start state x_{k+1}.  Steps k >= T
+// (padding of the last tile) produce the identity element (I, 0, 0, 0, 0),
+// which is neutral on both sides of the combine.
+#pragma once
+#include "elements.cuh"
+
+namespace mapk {
+
+// Load `CNT` consecutive scalars starting at src into dst; entries at or past
+// `avail` are zero.  Uses 16-byte vector loads when the run is complete and
+// aligned.
+template <int CNT, typename S>
+__device__ __forceinline__ void load_run(const S* __restrict__ src, long avail, S* dst)
+{
+    constexpr int V = 16 / sizeof(S);
+    if (CNT % V == 0 && avail >= CNT && (reinterpret_cast<size_t>(src) & 15) == 0) {
+#pragma unroll
+        for (int i = 0; i < CNT; i += V) {
+            if (sizeof(S) == 4) {
+                float4 q = __ldg(reinterpret_cast<const float4*>(src + i));
+                dst[i] = S(q.x); dst[i + 1] = S(q.y); dst[i + 2] = S(q.z); dst[i + 3] = S(q.w);
+            } else {
+                double2 q = __ldg(reinterpret_cast<const double2*>(src + i));
+                dst[i] = S(q.x); dst[i + 1] = S(q.y);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) dst[i] = i < avail ? __ldg(src + i) : S(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// linear time-invariant model: everything but eta is the same for every step
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+struct LtiParams {
+    static constexpr int NS = Sym<N>::SZ;
+    S A[N * N];
+    S b[N];
+    S C[NS];
+    S J[NS];
+    S G[N * M];      // dt H^T R^-1
+    S Gr[N];         // dt H^T R^-1 r
+};
+
+template <int N, int M, typename S>
+struct LtiProducer {
+    static constexpr int W = M;      // scalars read per step
+    const S* y;                      // (T, M), row k holds y_{k+1}
+    long T;
+    LtiParams<N, M, S> p;
+
+    template <int K>
+    __device__ __forceinline__ void load(long k0, S (&buf)[K * W]) const
+    {
+        const long avail = (T - k0) * W;
+        load_run<K * W, S>(y + k0 * W, avail, buf);
+    }
+
+    __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
+    {
+        if (k >= T) { set_identity(e); return; }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) e.A[i] = p.A[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) e.b[i] = p.b[i];
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) { e.C[i] = p.C[i]; e.J[i] = p.J[i]; }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = -p.Gr[i];
+#pragma unroll
+            for (int j = 0; j < M; ++j) s = fma(p.G[i * M + j], row[j], s);
+            e.eta[i] = s;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// nonlinear models, linearised at a trajectory xbar (Section 4.4):
+//   A = I - dt F(xbar_{k+1}),  b = -dt (f(xbar_{k+1}) - F xbar_{k+1}),  C = dt Q,
+//   J = dt Hb^T R^-1 Hb,  eta = dt Hb^T R^-1 (y - h(xbar) + Hb xbar) - dt/2 grad div f(xbar)
+// with Hb = dh/dx(xbar_{k+1}).  R is diagonal (Rinv holds its inverse).
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+struct NlParams {
+    static constexpr int NS = Sym<N>::SZ;
+    S dt;
+    S C[NS];          // dt Q
+    S Rinv[M];        // diagonal of R^-1
+    S F[N * N];       // linear part of the cubic drift
+    S c[N];
+    S H[M * N];       // linear measurement of the cubic model
+    S r[M];
+    S gamma;
+};
+
+template <typename S>
+__device__ __forceinline__ S wrap_angle(S a)
+{
+    const S pi = S(3.14159265358979323846);
+    const S twopi = S(6.28318530717958647692);
+    a = a - twopi * floor((a + pi) / twopi);
+    return a;
+}
+
+// coordinated turn (Section 5.2, Eq. 46), N = 5, M = 2
+template <typename S>
+struct CtModel {
+    static constexpr int N = 5, M = 2;
+    __device__ __forceinline__ static void drift(const NlParams<5, 2, S>&, const S* x, S* f, S* Fj, S* gdiv)
+    {
+#pragma unroll
+        for (int i = 0; i < 25; ++i) Fj[i] = S(0);
+        f[0] = x[2]; f[1] = x[3]; f[2] = -x[4] * x[3]; f[3] = x[4] * x[2]; f[4] = S(0);
+        Fj[0 * 5 + 2] = S(1);
+        Fj[1 * 5 + 3] = S(1);
+        Fj[2 * 5 + 3] = -x[4]; Fj[2 * 5 + 4] = -x[3];
+        Fj[3 * 5 + 2] = x[4];  Fj[3 * 5 + 4] = x[2];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) gdiv[i] = S(0);   // div f = 0 for this drift
+    }
+    // residual y - h(x) (bearing wrapped to (-pi, pi]) and Jacobian of h
+    __device__ __forceinline__ static void measure(const NlParams<5, 2, S>&, const S* x, const S* y, S* res, S* Hj)
+    {
+        const S r2 = x[0] * x[0] + x[1] * x[1];
+        const S rho = sqrt(r2);
+        res[0] = y[0] - rho;
+        res[1] = wrap_angle<S>(y[1] - atan2(x[1], x[0]));
+#pragma unroll
+        for (int i = 0; i < 10; ++i) Hj[i] = S(0);
+        Hj[0] = x[0] / rho; Hj[1] = x[1] / rho;
+        Hj[5] = -x[1] / r2; Hj[6] = x[0] / r2;
+    }
+};
+
+// cubic drift f = F x + c - gamma x^3 with linear measurement (state-dependent divergence)
+template <int NN, int MM, typename S>
+struct CubicModel {
+    static constexpr int N = NN, M = MM;
+    __device__ __forceinline__ static void drift(const NlParams<NN, MM, S>& p, const S* x, S* f, S* Fj, S* gdiv)
+    {
+#pragma unroll
+        for (int i = 0; i < NN; ++i) {
+            S s = p.c[i];
+#pragma unroll
+            for (int j = 0; j < NN; ++j) { s = fma(p.F[i * NN + j], x[j], s); Fj[i * NN + j] = p.F[i * NN + j]; }
+            f[i] = s - p.gamma * x[i] * x[i] * x[i];
+            Fj[i * NN + i] -= S(3) * p.gamma * x[i] * x[i];
+            gdiv[i] = S(-6) * p.gamma * x[i];
+        }
+    }
+    __device__ __forceinline__ static void measure(const NlParams<NN, MM, S>& p, const S* x, const S* y, S* res, S* Hj)
+    {
+#pragma unroll
+        for (int i = 0; i < MM; ++i) {
+            S s = p.r[i];
+#pragma unroll
+            for (int j = 0; j < NN; ++j) { s = fma(p.H[i * NN + j], x[j], s); Hj[i * NN + j] = p.H[i * NN + j]; }
+            res[i] = y[i] - s;
+        }
+    }
+};
+
+template <class Model, typename S>
+struct NlProducer {
+    static constexpr int N = Model::N, M = Model::M;
+    static constexpr int W = M + N;   // y_{k+1} then xbar_{k+1}
+    const S* y;                       // (T, M)
+    const S* xbar;                    // (T+1, N)
+    long T;
+    NlParams<N, M, S> p;
+
+    template <int K>
+    __device__ __forceinline__ void load(long k0, S (&buf)[K * W]) const
+    {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const long k = k0 + i;
+            const bool in = k < T;
+#pragma unroll
+            for (int j = 0; j < M; ++j) buf[i * W + j] = in ? __ldg(y + k * M + j) : S(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) buf[i * W + M + j] = in ? __ldg(xbar + (k + 1) * N + j) : S(0);
+        }
+    }
+
+    __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
+    {
+        if (k >= T) { set_identity(e); return; }
+        const S* yk = row;
+        const S* x1 = row + M;
+        S f[N], Fj[N * N], gd[N], res[M], Hj[M * N];
+        Model::drift(p, x1, f, Fj, gd);
+        Model::measure(p, x1, yk, res, Hj);
+        const S dt = p.dt;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = f[i];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                e.A[i * N + j] = (i == j ? S(1) : S(0)) - dt * Fj[i * N + j];
+                s = fma(-Fj[i * N + j], x1[j], s);
+            }
+            e.b[i] = -dt * s;
+        }
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) e.C[i] = p.C[i];
+        // measurement information and the linearised divergence term
+        S u[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            S s = res[i];
+#pragma unroll
+            for (int j = 0; j < N; ++j) s = fma(Hj[i * N + j], x1[j], s);
+            u[i] = s * p.Rinv[i] * dt;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = S(-0.5) * dt * gd[i];
+#pragma unroll
+            for (int j = 0; j < M; ++j) s = fma(Hj[j * N + i], u[j], s);
+            e.eta[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = i; j < N; ++j) {
+                S s = S(0);
+#pragma unroll
+                for (int l = 0; l < M; ++l) s = fma(Hj[l * N + i] * p.Rinv[l], Hj[l * N + j], s);
+                e.J[Sym<N>::at(i, j)] = dt * s;
+            }
+    }
+};
+
+}  // namespace mapk

@@ -1,0 +1,39 @@
+// Shared host/device declarations of the model set-up kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mapk {
+
+constexpr int MAXN = 8;
+constexpr int MAXM = 8;
+
+enum SetupFlags { SETUP_SINGULAR_R = 1, SETUP_SINGULAR_P0 = 2, SETUP_SINGULAR_A = 4, SETUP_SINGULAR_Q = 8,
+                  SETUP_SINGULAR_C = 16 };
+
+// device pointers to FP64 row-major inputs
+struct SetupIn {
+    int nx, ny, nw, mode;
+    double dt;
+    const double *F, *c, *L, *W, *H, *r, *R, *m0, *P0;
+};
+
+// FP64 outputs (full matrices, row-major, leading dimension = actual size)
+struct SetupOut {
+    double Q[MAXN * MAXN], Qinv[MAXN * MAXN];
+    double A[MAXN * MAXN], b[MAXN], C[MAXN * MAXN], Cinv[MAXN * MAXN];
+    double Rinv[MAXM * MAXM], G[MAXN * MAXM], Gr[MAXN], J[MAXN * MAXN];
+    double S0[MAXN * MAXN], v0[MAXN];
+    double Phi[MAXN * MAXN], beta[MAXN], Sigma[MAXN * MAXN];
+    int flags;
+};
+
+cudaError_t launch_setup(const SetupIn& in, SetupOut* d_out, cudaStream_t st);
+
+// FP64 constants of the discrete cost of a linear model
+template <int N, int M>
+struct LinCostParams {
+    double A[N * N], b[N], Cinv[N * N], H[M * N], r[M], Rinv[M * M], S0[N * N], m0[N];
+    double dt, trF;
+};
+
+}  // namespace mapk

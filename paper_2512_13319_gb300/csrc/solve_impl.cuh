@@ -1,0 +1,323 @@
+// Launch sequences of the solver, templated on the state dimension N, the
+// measurement dimension M and the precision S.  Included only by the
+// inst_*.cu translation units, which instantiate the combinations compiled
+// into the library.
+#pragma once
+#include <algorithm>
+#include <mutex>
+
+#include "handle.h"
+#include "scan.cuh"
+
+namespace mapk {
+
+constexpr int KSTEP = 8;   // steps per thread
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+template <int N, typename S>
+struct Layout {
+    size_t thr_agg, tile_agg, tile_pref, fin, Eg, thr_aff, tile_aff, tile_xend, total;
+    static Layout make(long nthr, long nt, long Tpad)
+    {
+        using E = Elem<N, S>;
+        using R = Red<N, S>;
+        using A = Aff<N, S>;
+        Layout l{};
+        size_t o = 0;
+        l.thr_agg = o;   o = align_up(o + sizeof(S) * E::NCOMP * nthr);
+        l.tile_agg = o;  o = align_up(o + sizeof(S) * E::NCOMP * nt);
+        l.tile_pref = o; o = align_up(o + sizeof(S) * R::NCOMP * nt);
+        l.fin = o;       o = align_up(o + sizeof(S) * R::NCOMP);
+        l.Eg = o;        o = align_up(o + sizeof(S) * A::NCOMP * Tpad);
+        l.thr_aff = o;   o = align_up(o + sizeof(S) * A::NCOMP * nthr);
+        l.tile_aff = o;  o = align_up(o + sizeof(S) * A::NCOMP * nt);
+        l.tile_xend = o; o = align_up(o + sizeof(S) * N * nt);
+        l.total = o;
+        return l;
+    }
+};
+
+// largest power-of-two CTA size <= 256 whose shared memory fits
+inline int pick_tile_scan_threads(size_t bytes_per_thread, int nt)
+{
+    int bt = 32;
+    while (bt < 256 && bt < nt) bt *= 2;
+    while (bt > 32 && bytes_per_thread * bt > 200 * 1024) bt /= 2;
+    return bt;
+}
+
+template <typename Kern>
+inline cudaError_t allow_smem(Kern k, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+template <int N, typename S>
+Red<N, S> prior_of(const map_smoother& h)
+{
+    Red<N, S> p;
+    for (int i = 0; i < N; ++i) p.v[i] = S(h.consts.v0[i]);
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) p.P[Sym<N>::at(i, j)] = S(h.consts.S0[i * N + j]);
+    return p;
+}
+
+template <int N, int M, typename S>
+LtiParams<N, M, S> lti_params(const map_smoother& h)
+{
+    const SetupOut& c = h.consts;
+    LtiParams<N, M, S> p;
+    for (int i = 0; i < N * N; ++i) p.A[i] = S(c.A[i]);
+    for (int i = 0; i < N; ++i) { p.b[i] = S(c.b[i]); p.Gr[i] = S(c.Gr[i]); }
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) {
+            p.C[Sym<N>::at(i, j)] = S(c.C[i * N + j]);
+            p.J[Sym<N>::at(i, j)] = S(c.J[i * N + j]);
+        }
+    for (int i = 0; i < N * M; ++i) p.G[i] = S(c.G[i]);
+    return p;
+}
+
+template <int N, typename S>
+size_t rts_workspace(const map_smoother& h)
+{
+    return Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad).total;
+}
+
+// Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
+template <int N, typename S, class Prod>
+map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st)
+{
+    using E = Elem<N, S>;
+    using R = Red<N, S>;
+    using A = Aff<N, S>;
+    constexpr int K = KSTEP;
+    const int B = h.B, nt = h.nt;
+    const long nthr = (long)nt * B;
+    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
+    S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
+    S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
+    S* tile_pref = reinterpret_cast<S*>(h.ws + L.tile_pref);
+    S* fin = reinterpret_cast<S*>(h.ws + L.fin);
+    S* Eg = reinterpret_cast<S*>(h.ws + L.Eg);
+    S* thr_aff = reinterpret_cast<S*>(h.ws + L.thr_aff);
+    S* tile_aff = reinterpret_cast<S*>(h.ws + L.tile_aff);
+    S* tile_xend = reinterpret_cast<S*>(h.ws + L.tile_xend);
+    const CombineCtx ctx{h.cond_max, h.d_stats};
+    const long T = h.T;
+    S* xT = x_out + T * N;
+
+    const size_t sh_reduce = sizeof(S) * E::NCOMP * 2 * B;
+    const size_t sh_down = sizeof(S) * std::max<size_t>(E::NCOMP + R::NCOMP, A::NCOMP) * 2 * B;
+    const size_t sh_rts = sizeof(S) * (A::NCOMP + N) * 2 * B;
+    const int bt_f = pick_tile_scan_threads(sizeof(S) * (E::NCOMP + R::NCOMP) * 2, nt);
+    const int bt_a = pick_tile_scan_threads(sizeof(S) * (A::NCOMP + N) * 2, nt);
+    const size_t sh_tf = sizeof(S) * (E::NCOMP + R::NCOMP) * 2 * bt_f;
+    const size_t sh_ta = sizeof(S) * (A::NCOMP + N) * 2 * bt_a;
+
+    static std::once_flag once;
+    cudaError_t e0 = cudaSuccess;
+    std::call_once(once, [&] {
+        const size_t big = 200 * 1024;
+        e0 = allow_smem(k_filter_reduce<N, S, Prod, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_affine_tiles<N, S>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S, K>, big);
+    });
+    if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
+
+    h.nev = 0;
+    auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
+    mark();
+    k_filter_reduce<N, S, Prod, K><<<nt, B, sh_reduce, st>>>(prod, thr_agg, tile_agg, ctx);
+    mark();
+    k_filter_tiles<N, S><<<1, bt_f, sh_tf, st>>>(tile_agg, nt, prior_of<N, S>(h), tile_pref, fin, xT,
+                                                  filt_out ? filt_out + T * R::NCOMP : nullptr, ctx);
+    mark();
+    k_filter_down<N, S, Prod, K><<<nt, B, sh_down, st>>>(prod, thr_agg, tile_pref, Eg, thr_aff,
+                                                         tile_aff, filt_out, ctx);
+    mark();
+    k_affine_tiles<N, S><<<1, bt_a, sh_ta, st>>>(tile_aff, nt, xT, tile_xend);
+    mark();
+    k_rts_down<N, S, K><<<nt, B, sh_rts, st>>>(Eg, thr_aff, tile_xend, T, x_out);
+    mark();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    return MAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// linear models
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st)
+{
+    LtiProducer<N, M, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.T = h.T;
+    prod.p = lti_params<N, M, S>(h);
+    return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
+}
+
+// Discrete Onsager-Machlup cost of a trajectory of a linear model:
+//   1/2 |x0 - m0|^2_{P0^-1} + sum_k 1/2 |x_k - A x_{k+1} - b|^2_{C^-1}
+//   + sum_k 1/2 dt |y_{k+1} - H x_{k+1} - r|^2_{R^-1} + 1/2 dt T tr F
+// (C^-1 = Q^-1 / dt for the Euler element).  FP64 accumulation.
+template <int N, int M, typename S>
+__global__ void k_cost_linear(const S* __restrict__ y, const S* __restrict__ x, long T,
+                              LinCostParams<N, M> p, double* out)
+{
+    double acc = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < T; k += (long)gridDim.x * blockDim.x) {
+        double xk[N], x1[N], rr[N], e[M];
+#pragma unroll
+        for (int i = 0; i < N; ++i) { xk[i] = double(x[k * N + i]); x1[i] = double(x[(k + 1) * N + i]); }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = xk[i] - p.b[i];
+#pragma unroll
+            for (int j = 0; j < N; ++j) s -= p.A[i * N + j] * x1[j];
+            rr[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) s += p.Cinv[i * N + j] * rr[j];
+            acc += 0.5 * rr[i] * s;
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            double s = double(y[k * M + i]) - p.r[i];
+#pragma unroll
+            for (int j = 0; j < N; ++j) s -= p.H[i * N + j] * x1[j];
+            e[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < M; ++j) s += p.Rinv[i * M + j] * e[j];
+            acc += 0.5 * p.dt * e[i] * s;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double e0[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) e0[i] = double(x[i]) - p.m0[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) s += p.S0[i * N + j] * e0[j];
+            acc += 0.5 * e0[i] * s;
+        }
+        acc += 0.5 * p.dt * double(T) * p.trF;
+    }
+    // warp + block reduction, one atomic per block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+
+template <int N, int M, typename S>
+map_status cost_linear(map_smoother& h, const void* y, const void* x, double* d_cost, cudaStream_t st)
+{
+    LinCostParams<N, M> p;
+    const SetupOut& c = h.consts;
+    for (int i = 0; i < N * N; ++i) { p.A[i] = c.A[i]; p.S0[i] = c.S0[i]; p.Cinv[i] = c.Cinv[i]; }
+    for (int i = 0; i < N; ++i) { p.b[i] = c.b[i]; p.m0[i] = h.m0[i]; }
+    for (int i = 0; i < M * N; ++i) p.H[i] = h.H[i];
+    for (int i = 0; i < M; ++i) p.r[i] = h.r[i];
+    for (int i = 0; i < M * M; ++i) p.Rinv[i] = c.Rinv[i];
+    p.dt = h.dt;
+    p.trF = 0.0;
+    for (int i = 0; i < N; ++i) p.trF += h.F[i * N + i];
+    cudaError_t e = cudaMemsetAsync(d_cost, 0, sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    const int blocks = (int)std::min<long>(1024, (h.T + 255) / 256);
+    k_cost_linear<N, M, S><<<std::max(blocks, 1), 256, 0, st>>>(static_cast<const S*>(y),
+                                                                static_cast<const S*>(x), h.T, p, d_cost);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "cost kernel launch");
+    return MAP_OK;
+}
+
+template <int N, int M, typename S>
+const Ops* linear_ops()
+{
+    static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>};
+    return &ops;
+}
+
+// ---------------------------------------------------------------------------
+// nonlinear models: iterated linearisation (Section 4.4), each iteration one
+// filter scan + RTS pass on the elements linearised at the previous estimate
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+NlParams<N, M, S> nl_params(const map_smoother& h)
+{
+    NlParams<N, M, S> p;
+    p.dt = S(h.dt);
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) p.C[Sym<N>::at(i, j)] = S(h.dt * h.consts.Q[i * N + j]);
+    for (int i = 0; i < M; ++i) p.Rinv[i] = S(1.0 / h.R[i * M + i]);
+    for (int i = 0; i < N * N; ++i) p.F[i] = S(h.F[i]);
+    for (int i = 0; i < N; ++i) p.c[i] = S(h.c[i]);
+    for (int i = 0; i < M * N; ++i) p.H[i] = S(h.H[i]);
+    for (int i = 0; i < M; ++i) p.r[i] = S(h.r[i]);
+    p.gamma = S(h.gamma);
+    return p;
+}
+
+template <class Model, typename S>
+map_status solve_nonlinear(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st)
+{
+    constexpr int N = Model::N, M = Model::M;
+    NlProducer<Model, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.T = h.T;
+    prod.p = nl_params<N, M, S>(h);
+    S* cur = static_cast<S*>(x_out);
+    S* nxt = static_cast<S*>(h.d_xtmp);
+    for (int it = 0; it < h.gn_iters; ++it) {
+        prod.xbar = cur;
+        const bool last = it + 1 == h.gn_iters;
+        map_status s = run_rts<N, S>(h, prod, nxt, last ? static_cast<S*>(filt_out) : nullptr, st);
+        if (s != MAP_OK) return s;
+        std::swap(cur, nxt);
+    }
+    if (cur != x_out) {
+        cudaError_t e = cudaMemcpyAsync(x_out, cur, sizeof(S) * (size_t)(h.T + 1) * N,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+    }
+    return MAP_OK;
+}
+
+template <typename S>
+const Ops* coord_turn_ops()
+{
+    static const Ops ops{&rts_workspace<5, S>, &solve_nonlinear<CtModel<S>, S>, nullptr};
+    return &ops;
+}
+
+template <int N, int M, typename S>
+const Ops* cubic_ops()
+{
+    static const Ops ops{&rts_workspace<N, S>, &solve_nonlinear<CubicModel<N, M, S>, S>, nullptr};
+    return &ops;
+}
+
+}  // namespace mapk

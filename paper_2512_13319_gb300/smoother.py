@@ -1,0 +1,95 @@
+"""PyTorch-facing wrapper of the C ABI: device memory and streams come from torch.
+
+Argument marshalling only; the solve runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _binding as B
+
+_PREC = {"fp32": B.MAP_FP32, "fp64": B.MAP_FP64}
+_DISC = {"euler": B.MAP_EULER, "expm": B.MAP_EXPM, "auto": B.MAP_AUTO}
+_SMOOTHER = {"rts": B.MAP_RTS, "two_filter": B.MAP_TWO_FILTER}
+
+
+class MapSmoother:
+    """One problem (model, T, dt, precision) with its device workspace.
+
+    ``solve(y)`` takes observations ``y`` (T, ny) on the current CUDA device and
+    returns the MAP trajectory (T+1, nx) in the handle's precision.
+    """
+
+    def __init__(self, model, T, dt, precision="fp32", discretisation="euler", smoother="rts",
+                 gn_iters=1, cond_max=0.0, tile_threads=0):
+        self.model, self.T, self.dt = model, int(T), float(dt)
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.nx, self.ny = model.nx, model.ny
+        desc, keep = B.make_desc(model, T, dt, _PREC[precision], _DISC[discretisation],
+                                 _SMOOTHER[smoother], gn_iters, cond_max, tile_threads)
+        self._h = B.map_smoother_create(desc)
+        del keep
+
+    def _stream(self, stream):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes_stream(s)
+
+    def _check_dev(self, t, shape, name):
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"{name} must be a contiguous {self.dtype} CUDA tensor of shape {shape}")
+
+    def solve(self, y, x_out=None, x_init=None, filt=False, cost=False, stream=None):
+        """MAP trajectory for device observations ``y``.
+
+        For nonlinear models ``x_init`` (T+1, nx) is the first linearisation
+        trajectory.  Returns ``x`` or a tuple ``(x, filt, cost)`` when extras are asked.
+        """
+        self._check_dev(y, (self.T, self.ny), "y")
+        if x_out is None:
+            x_out = torch.empty((self.T + 1, self.nx), dtype=self.dtype, device=y.device)
+        self._check_dev(x_out, (self.T + 1, self.nx), "x_out")
+        if x_init is not None:
+            x_out.copy_(x_init)
+        f = None
+        if filt:
+            f = torch.empty((self.T + 1, self.nx + self.nx * (self.nx + 1) // 2), dtype=self.dtype,
+                            device=y.device)
+        c = B.map_smoother_solve(self._h, y.data_ptr(), x_out.data_ptr(),
+                                 f.data_ptr() if f is not None else None, cost, self._stream(stream))
+        if filt or cost:
+            return x_out, f, c
+        return x_out
+
+    def solve_host(self, y_host, x_host=None, stream=None):
+        """End-to-end solve from host memory (pinned CPU tensors) into host memory."""
+        if x_host is None:
+            x_host = torch.empty((self.T + 1, self.nx), dtype=self.dtype).pin_memory()
+        B.map_smoother_solve_host(self._h, y_host.data_ptr(), x_host.data_ptr(), self._stream(stream))
+        return x_host
+
+    def profile(self, enable=True):
+        """Record per-phase CUDA events in every solve (see phase_times)."""
+        B.map_smoother_profile(self._h, enable)
+
+    def phase_times(self):
+        """{phase name: ms} of the last profiled solve."""
+        return dict(zip(B.PHASES, B.map_smoother_phase_times(self._h)))
+
+    def stats(self, reset=False, stream=None):
+        """(combines recomputed in FP64, singular pivots) since create or the last reset."""
+        return B.map_smoother_stats(self._h, reset, self._stream(stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.map_smoother_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctypes_stream(s):
+    return s.cuda_stream if hasattr(s, "cuda_stream") else s

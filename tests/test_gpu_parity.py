@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative trajectory error |X - X_ref|_F / |X_ref|_F over all
+(T+1) * nx entries): 1e-9 for FP64, 1e-4 for FP32.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_13319_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 1e-4}
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_13319_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_solve(model, y, dt, prec, x_init=None, **kw):
+    from paper_2512_13319_gb300 import MapSmoother
+    sm = MapSmoother(model, y.shape[0], dt, precision=prec, **kw)
+    yt = torch.tensor(y, dtype=DT[prec], device="cuda")
+    xi = None if x_init is None else torch.tensor(x_init, dtype=DT[prec], device="cuda")
+    x = sm.solve(yt, x_init=xi).cpu().numpy()
+    stats = sm.stats()
+    sm.close()
+    return x, stats
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_wiener_velocity_T1000(prec):
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    _, y = synth.simulate(model, 1000, 0.01, seed=synth.seed_for(0))
+    x, _ = gpu_solve(model, y, 0.01, prec)
+    assert rel(x, oracle.smooth_lti(model, y, 0.01)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [1, 2, 3, 7, 8, 9, 63, 64, 65, 511, 512, 513, 1023, 1024, 1025, 4097])
+def test_ragged_horizons(prec, T):
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    _, y = synth.simulate(model, T, 0.01, seed=T)
+    x, _ = gpu_solve(model, y, 0.01, prec)
+    assert rel(x, oracle.smooth_lti(model, y, 0.01)) <= TOL[prec]
+
+
+SHAPES = [
+    ("wv1", lambda: synth.wiener_velocity(1, q=2.0, r=0.05)),
+    ("ou3", lambda: synth.ou_model(3, 1, seed=7)),
+    ("ou4", lambda: synth.ou_model(4, 2, seed=8)),
+    ("ou5", lambda: synth.ou_model(5, 2, seed=9)),
+    ("wv3", lambda: synth.wiener_velocity(3, q=1.0, r=0.1)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", [s[0] for s in SHAPES])
+def test_state_dimensions(prec, name):
+    model = dict(SHAPES)[name]()
+    T, dt = 3000, 0.01
+    _, y = synth.simulate(model, T, dt, seed=3)
+    x, _ = gpu_solve(model, y, dt, prec)
+    assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_exact_discretisation(prec):
+    model = synth.ou_model(4, 2, seed=12)
+    T, dt = 2000, 0.05
+    _, y = synth.simulate(model, T, dt, seed=4)
+    x, _ = gpu_solve(model, y, dt, prec, discretisation="expm")
+    assert rel(x, oracle.smooth_lti(model, y, dt, mode=oracle.EXPM)) <= TOL[prec]
+    x2, _ = gpu_solve(model, y, dt, prec, discretisation="auto")   # |F| dt > 0.05 -> exact
+    assert np.array_equal(x, x2)
+
+
+def test_affine_drift_and_measurement_offset():
+    model = synth.ou_model(4, 2, seed=13)
+    model.c = np.array([0.5, -1.0, 0.25, 2.0])
+    model.r = np.array([0.3, -0.7])
+    model.m0 = np.array([1.0, 2.0, -1.0, 0.5])
+    T, dt = 1500, 0.01
+    _, y = synth.simulate(model, T, dt, seed=5)
+    for prec in ("fp64", "fp32"):
+        x, _ = gpu_solve(model, y, dt, prec)
+        assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
+
+
+def test_filter_output_is_the_information_filter():
+    from paper_2512_13319_gb300 import MapSmoother
+    model = synth.ou_model(4, 2, seed=14)
+    T, dt = 700, 0.01
+    _, y = synth.simulate(model, T, dt, seed=6)
+    _, mf, Pf = oracle.smooth_lti(model, y, dt, return_filter=True)
+    sm = MapSmoother(model, T, dt, precision="fp64")
+    x, f, _ = sm.solve(torch.tensor(y, device="cuda"), filt=True)
+    f = f.cpu().numpy()
+    n = 4
+    iu = np.triu_indices(n)
+    S = np.zeros((T + 1, n, n))
+    S[:, iu[0], iu[1]] = f[:, n:]
+    S[:, iu[1], iu[0]] = f[:, n:]
+    v = f[:, :n]
+    assert rel(np.linalg.inv(S), Pf) < 1e-9
+    assert rel(np.einsum("kij,kj->ki", np.linalg.inv(S), v), mf) < 1e-9
+
+
+def test_map_cost_output():
+    from paper_2512_13319_gb300 import MapSmoother
+    model = synth.ou_model(4, 2, seed=15)
+    T, dt = 900, 0.01
+    _, y = synth.simulate(model, T, dt, seed=7)
+    sm = MapSmoother(model, T, dt, precision="fp64")
+    x, _, cost = sm.solve(torch.tensor(y, device="cuda"), cost=True)
+    ref = oracle.cost(model, y, x.cpu().numpy(), dt)
+    assert abs(cost - ref) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_many_tiles(prec):
+    """nt > tile-scan CTA size: several tiles per thread in the tile scans."""
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    T, dt = 300_001, 1e-3
+    _, y = synth.simulate(model, T, dt, seed=11, substeps=1)
+    x, _ = gpu_solve(model, y, dt, prec)
+    assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_T_2_20(prec):
+    """The benchmark workload: nx = 4, T = 2^20, dt = 1e-3 (every output compared)."""
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    T, dt = 2 ** 20, 1e-3
+    _, y = synth.simulate(model, T, dt, seed=synth.seed_for(1), substeps=1)
+    x, _ = gpu_solve(model, y, dt, prec)
+    ref = oracle.smooth_lti(model, y, dt)
+    assert rel(x, ref) <= TOL[prec]
+    # per-step infinity-norm error relative to the trajectory's scale
+    assert np.abs(x - ref).max() / np.abs(ref).max() <= 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coordinated_turn_gauss_newton(prec):
+    model = synth.coordinated_turn()
+    T, dt, iters = 4000, 1e-3, 10
+    _, y = synth.simulate(model, T, dt, seed=synth.seed_for(2))
+    x0 = np.tile(model.m0, (T + 1, 1))
+    x, _ = gpu_solve(model, y, dt, prec, x_init=x0, gn_iters=iters)
+    ref = oracle.gauss_newton(model, y, dt, x0, iters)
+    assert rel(x, ref) <= TOL[prec]
+
+
+def test_cubic_drift_gauss_newton_with_divergence_term():
+    model = synth.cubic_model(2, gamma=1.5, q=0.5, r=0.05)
+    model.m0 = np.array([1.0, -0.5])
+    T, dt, iters = 3000, 0.01, 8
+    _, y = synth.simulate(model, T, dt, seed=3)
+    x0 = np.tile(model.m0, (T + 1, 1))
+    for prec in ("fp64", "fp32"):
+        x, _ = gpu_solve(model, y, dt, prec, x_init=x0, gn_iters=iters)
+        assert rel(x, oracle.gauss_newton(model, y, dt, x0, iters)) <= TOL[prec]
+
+
+def test_host_buffer_entry_point_matches_device_entry_point():
+    from paper_2512_13319_gb300 import MapSmoother
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    T, dt = 5000, 0.01
+    _, y = synth.simulate(model, T, dt, seed=9)
+    sm = MapSmoother(model, T, dt, precision="fp32")
+    x_dev = sm.solve(torch.tensor(y, dtype=torch.float32, device="cuda")).cpu()
+    y_host = torch.tensor(y, dtype=torch.float32).pin_memory()
+    x_host = sm.solve_host(y_host)
+    assert torch.equal(x_dev, x_host)
+
+
+def test_precision_policy_counter_and_fallback():
+    """A huge condition threshold keeps every combine in FP32; a tiny one
+    recomputes every combine in FP64, which must still agree with the oracle."""
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    T, dt = 5000, 0.01
+    _, y = synth.simulate(model, T, dt, seed=10)
+    ref = oracle.smooth_lti(model, y, dt)
+    x1, st1 = gpu_solve(model, y, dt, "fp32", cond_max=1e30)
+    x2, st2 = gpu_solve(model, y, dt, "fp32", cond_max=1.0 + 1e-12)
+    assert rel(x1, ref) <= 1e-4 and rel(x2, ref) <= 1e-4
+    assert st2[0] > st1[0] and st2[0] >= T
+    assert st1[1] == 0 and st2[1] == 0
+
+
+def test_invalid_arguments_raise():
+    from paper_2512_13319_gb300 import MapSmoother
+    from paper_2512_13319_gb300 import _binding as B
+    model = synth.wiener_velocity(2)
+    sm = MapSmoother(model, 10, 0.01)
+    with pytest.raises(ValueError):
+        sm.solve(torch.zeros((9, 2), device="cuda"))
+    with pytest.raises(B.MapError) as ei:
+        B.map_smoother_solve(sm._h, None, None)
+    assert ei.value.status == B.MAP_ERR_INVALID_ARG
+    sm.close()
