@@ -347,7 +347,7 @@ def ours(args):
 
 
 def sm_B(sm):
-    return 128 if sm.dtype.itemsize == 4 else 64
+    return 128
 
 
 def sequential_gpu(model, y, dtype, dev, flush, stream):

@@ -115,6 +115,16 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
                               double* cost_out, void* stream);
 
 /*
+ * Sequential baseline on the GPU: the same elements, information-filter
+ * recursion (Eq. 17 in discrete form, one element per step) and closed-loop
+ * maps as map_smoother_solve, evaluated by a single GPU thread in time order
+ * with no associative scan (the paper's sequential counterpart).  Same
+ * arguments and results as map_smoother_solve without the optional outputs;
+ * nonlinear models iterate desc.gn_iters times.  Asynchronous on `stream`.
+ */
+map_status map_smoother_solve_sequential(map_smoother* h, const void* y, void* x_out, void* stream);
+
+/*
  * End-to-end variant with HOST buffers: copies y_host (T x ny) to the device,
  * solves, copies the estimate back to x_host ((T+1) x nx) and synchronises
  * the stream.  For nonlinear models x_host also carries the first

@@ -43,6 +43,7 @@ _VP, _I, _CH = ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p
 EXPORTS = {
     "map_smoother_create": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(map_problem_desc)]),
     "map_smoother_solve": (_I, [_VP, _VP, _VP, _VP, _D, _VP]),
+    "map_smoother_solve_sequential": (_I, [_VP, _VP, _VP, _VP]),
     "map_smoother_solve_host": (_I, [_VP, _VP, _VP, _VP]),
     "map_smoother_grad": (_I, [_VP, _VP, _VP, _D, _VP]),
     "map_smoother_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_ulonglong), _I, _VP]),
@@ -115,6 +116,10 @@ def map_smoother_solve(h, y_ptr, x_ptr, filt_ptr=None, want_cost=False, stream=N
     _check(load().map_smoother_solve(h, y_ptr, x_ptr, filt_ptr,
                                      ctypes.pointer(cost) if want_cost else None, stream), h)
     return cost.value if want_cost else None
+
+
+def map_smoother_solve_sequential(h, y_ptr, x_ptr, stream=None):
+    _check(load().map_smoother_solve_sequential(h, y_ptr, x_ptr, stream), h)
 
 
 def map_smoother_solve_host(h, y_host_ptr, x_host_ptr, stream=None):

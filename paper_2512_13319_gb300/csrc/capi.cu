@@ -184,13 +184,16 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     if (h->consts.flags & SETUP_SINGULAR_P0) return fail(*h, MAP_ERR_SINGULAR, "P0 is singular");
     if (h->consts.flags & SETUP_SINGULAR_A) return fail(*h, MAP_ERR_SINGULAR, "the interval map A is singular");
 
-    // launch geometry: shared memory of the tile CTA must fit
+    // launch geometry: the tile CTA's tree (2B nodes with full, row-padded
+    // matrices, plus one scratch area per sub-warp group) must fit in shared memory
     const size_t es = elem_bytes(h->prec);
-    const size_t ncomp = (size_t)n * n + 2 * n + (size_t)n * (n + 1) + n + (size_t)n * (n + 1) / 2;
-    int B = d->tile_threads > 0 ? d->tile_threads : (h->prec == MAP_FP32 ? 128 : 64);
+    const size_t V = 16 / es, P = (n + V - 1) / V * V;
+    const size_t NE = 3 * n * P + 2 * P, NSCR = 3 * n * P + P, NL = n <= 2 ? 2 : n <= 4 ? 4 : 8;
+    auto tree_bytes = [&](int b) { return es * (2 * (size_t)b * NE + (size_t)b / NL * NSCR); };
+    int B = d->tile_threads > 0 ? d->tile_threads : 128;
     if (B < 32 || B > 256 || (B & (B - 1)))
         return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be a power of two in [32, 256]");
-    while (B > 32 && ncomp * 2 * B * es > 200 * 1024) B /= 2;
+    while (B > 32 && tree_bytes(B) > (d->tile_threads > 0 ? 200 : 100) * 1024) B /= 2;
     h->B = B;
     h->K = 8;
     const long L = (long)h->B * h->K;
@@ -260,6 +263,16 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
         if (e != cudaSuccess) return cuda_fail(*h, e, "cost read-back");
     }
     return MAP_OK;
+}
+
+map_status map_smoother_solve_sequential(map_smoother* h, const void* y, void* x_out, void* stream)
+{
+    if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
+    if (!y || !x_out) return fail(*h, MAP_ERR_INVALID_ARG, "y and x_out are required");
+    if (!aligned16(y) || !aligned16(x_out))
+        return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+    const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
+    return ops->solve_sequential(*h, y, x_out, static_cast<cudaStream_t>(stream));
 }
 
 map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_host, void* stream)

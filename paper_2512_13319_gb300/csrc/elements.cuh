@@ -18,8 +18,9 @@
 // Precision policy: the (I + C J) inverse runs in the element precision S
 // with diagonal pivots.  When a pivot is small against its column
 // (tau = 1/2) or the infinity-norm condition estimate |M| |M^-1| exceeds the
-// threshold, the whole operation is recomputed in FP64 with row pivoting, and
-// a device counter records it.
+// threshold, (I + C J) is formed and inverted again in FP64 with row
+// pivoting, and a device counter records it; the products around the inverse
+// stay in S.
 #pragma once
 #include "smallmat.cuh"
 
@@ -56,8 +57,8 @@ struct Aff {
 };
 
 struct CombineCtx {
-    double cond_max;                 // FP64 recompute when |M| |M^-1| exceeds this
-    unsigned long long* stats;       // [0] FP64 recomputations, [1] singular pivots
+    float cond_max;                  // FP64 inverse when |M| |M^-1| exceeds this
+    unsigned long long* stats;       // [0] FP64 inverses, [1] singular pivots
 };
 
 template <int N, typename S>
@@ -122,21 +123,52 @@ __device__ __forceinline__ void convert(const Elem<N, Ss>& s, Elem<N, Sd>& d)
 }
 
 // ---------------------------------------------------------------------------
-// (I + C_i J_j) and its inverse; returns false when the fast path is not safe
+// (I + C P) and its inverse.  Fast path: diagonal pivots in precision S, with
+// the pivot test and the infinity-norm condition estimate.  Slow path (rare):
+// (I + C P) formed and inverted in FP64 with row pivoting; only the inverse is
+// returned, the rest of the operation stays in S.  The slow path copies its
+// inputs into a local buffer inside the branch, so the operands of the fast
+// path stay in registers.
 // ---------------------------------------------------------------------------
 template <int N, typename S>
-__device__ __forceinline__ bool inverse_I_plus(const S* Cp, const S* Jp, S* Mi, double cond_max,
-                                               bool pivot)
+__device__ __noinline__ void inverse_I_plus_fp64(const S* buf, S* out, unsigned long long* stats)
 {
+    constexpr int NS = Sym<N>::SZ;
+    double Cd[NS], Pd[NS], M[N * N], Mi[N * N];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) { Cd[i] = double(buf[i]); Pd[i] = double(buf[NS + i]); }
+    ms::sym_sym<N, double>(Cd, Pd, M);
+#pragma unroll
+    for (int i = 0; i < N; ++i) M[i * N + i] += 1.0;
+    const bool ok = ms::inv_row_pivot<N, double>(M, Mi);
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) out[i] = S(Mi[i]);
+    if (stats) {
+        atomicAdd(stats, 1ull);
+        if (!ok) atomicAdd(stats + 1, 1ull);
+    }
+}
+
+template <int N, typename S>
+__device__ __forceinline__ void inverse_I_plus(const S* Cp, const S* Pp, S* Mi, float cond_max,
+                                               unsigned long long* stats)
+{
+    constexpr int NS = Sym<N>::SZ;
     S M[N * N];
-    ms::sym_sym<N, S>(Cp, Jp, M);
+    ms::sym_sym<N, S>(Cp, Pp, M);
 #pragma unroll
     for (int i = 0; i < N; ++i) M[i * N + i] += S(1);
-    if (pivot) return ms::inv_row_pivot<N, S>(M, Mi);
     const S nM = ms::norm_inf<N, S>(M);
     const bool ok = ms::inv_diag_pivot<N, S>(M, Mi, S(0.5));
     const S nMi = ms::norm_inf<N, S>(Mi);
-    return ok && (double(nM) * double(nMi) <= cond_max);
+    if (!(ok && float(nM) * float(nMi) <= cond_max)) {
+        S buf[2 * NS], out[N * N];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) { buf[i] = Cp[i]; buf[NS + i] = Pp[i]; }
+        inverse_I_plus_fp64<N, S>(buf, out, stats);
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) Mi[i] = out[i];
+    }
 }
 
 // core of e_i (x) e_j given Mi = (I + C_i J_j)^-1
@@ -145,8 +177,15 @@ __device__ __forceinline__ void combine_core(const Elem<N, S>& ei, const Elem<N,
                                              const S* Mi, Elem<N, S>& out)
 {
     S T1[N * N], T2[N * N], T3[N * N], u[N], w[N];
-    ms::mm<N, S>(ej.A, Mi, T1);                       // A_j M^-1
     Elem<N, S> r;
+    ms::mm<N, S>(Mi, ei.A, T3);                       // M^-1 A_i  (= (A_i^T M^-T)^T)
+    ms::sym_v<N, S>(ej.J, ei.b, u);                   // J_j b_i
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = ej.eta[i] - u[i];
+    ms::mtv_add<N, S>(T3, u, ei.eta, r.eta);          // eta_ij
+    ms::sym_m<N, S>(ej.J, ei.A, T2);                  // J_j A_i
+    ms::sym_atb_add<N, S>(T3, T2, ei.J, r.J);         // J_ij
+    ms::mm<N, S>(ej.A, Mi, T1);                       // A_j M^-1
     ms::mm<N, S>(T1, ei.A, r.A);                      // A_ij
     ms::sym_v<N, S>(ei.C, ej.eta, u);                 // C_i eta_j
 #pragma unroll
@@ -156,29 +195,7 @@ __device__ __forceinline__ void combine_core(const Elem<N, S>& ei, const Elem<N,
     for (int i = 0; i < N; ++i) r.b[i] = w[i] + ej.b[i];   // b_ij
     ms::m_sym<N, S>(T1, ei.C, T2);                    // A_j M^-1 C_i
     ms::sym_abt_add<N, S>(T2, ej.A, ej.C, r.C);       // C_ij
-    ms::mm<N, S>(Mi, ei.A, T3);                       // M^-1 A_i  (= (A_i^T M^-T)^T)
-    ms::sym_v<N, S>(ej.J, ei.b, u);                   // J_j b_i
-#pragma unroll
-    for (int i = 0; i < N; ++i) u[i] = ej.eta[i] - u[i];
-    ms::mtv_add<N, S>(T3, u, ei.eta, r.eta);          // eta_ij
-    ms::sym_m<N, S>(ej.J, ei.A, T2);                  // J_j A_i
-    ms::sym_atb_add<N, S>(T3, T2, ei.J, r.J);         // J_ij
     out = r;
-}
-
-template <int N, typename S>
-__device__ __noinline__ void combine_fp64(const Elem<N, S>& ei, const Elem<N, S>& ej,
-                                          Elem<N, S>& out, const CombineCtx& ctx)
-{
-    Elem<N, double> di, dj, dr;
-    convert(ei, di);
-    convert(ej, dj);
-    double Mi[N * N];
-    if (!inverse_I_plus<N, double>(di.C, dj.J, Mi, 0.0, true) && ctx.stats)
-        atomicAdd(ctx.stats + 1, 1ull);
-    combine_core<N, double>(di, dj, Mi, dr);
-    convert(dr, out);
-    if (ctx.stats) atomicAdd(ctx.stats, 1ull);
 }
 
 // out = ei (x) ej  (out may alias either operand)
@@ -187,20 +204,19 @@ __device__ __forceinline__ void combine(const Elem<N, S>& ei, const Elem<N, S>& 
                                         Elem<N, S>& out, const CombineCtx& ctx)
 {
     S Mi[N * N];
-    if (inverse_I_plus<N, S>(ei.C, ej.J, Mi, ctx.cond_max, false)) {
-        combine_core<N, S>(ei, ej, Mi, out);
-    } else {
-        combine_fp64<N, S>(ei, ej, out, ctx);
-    }
+    inverse_I_plus<N, S>(ei.C, ej.J, Mi, ctx.cond_max, ctx.stats);
+    combine_core<N, S>(ei, ej, Mi, out);
 }
 
 // ---------------------------------------------------------------------------
 // e (x) [P, v]: value-function update and the interval's closed-loop map
 // ---------------------------------------------------------------------------
 template <int N, typename S, bool ALPHA>
-__device__ __forceinline__ void apply_core(const Elem<N, S>& e, Red<N, S>& p, const S* Mi,
-                                           S* E, S* g)
+__device__ __forceinline__ void apply(const Elem<N, S>& e, Red<N, S>& p, S* E, S* g,
+                                      const CombineCtx& ctx)
 {
+    S Mi[N * N];
+    inverse_I_plus<N, S>(e.C, p.P, Mi, ctx.cond_max, ctx.stats);
     S Em[N * N], T4[N * N], u[N], w[N];
     ms::mm<N, S>(Mi, e.A, Em);                        // E = M^-1 A
     if (ALPHA) {
@@ -219,46 +235,6 @@ __device__ __forceinline__ void apply_core(const Elem<N, S>& e, Red<N, S>& p, co
     ms::sym_atb_add<N, S>(Em, T4, e.J, r.P);          // A^T M^-T P A + J
     ms::mtv_add<N, S>(Em, w, e.eta, r.v);             // A^T M^-T (v - P b) + eta
     p = r;
-}
-
-template <int N, typename S, bool ALPHA>
-__device__ __noinline__ void apply_fp64(const Elem<N, S>& e, Red<N, S>& p, S* E, S* g,
-                                        const CombineCtx& ctx)
-{
-    Elem<N, double> de;
-    convert(e, de);
-    Red<N, double> dp;
-#pragma unroll
-    for (int i = 0; i < N; ++i) dp.v[i] = double(p.v[i]);
-#pragma unroll
-    for (int i = 0; i < Sym<N>::SZ; ++i) dp.P[i] = double(p.P[i]);
-    double Mi[N * N], dE[N * N], dg[N];
-    if (!inverse_I_plus<N, double>(de.C, dp.P, Mi, 0.0, true) && ctx.stats)
-        atomicAdd(ctx.stats + 1, 1ull);
-    apply_core<N, double, ALPHA>(de, dp, Mi, dE, dg);
-#pragma unroll
-    for (int i = 0; i < N; ++i) p.v[i] = S(dp.v[i]);
-#pragma unroll
-    for (int i = 0; i < Sym<N>::SZ; ++i) p.P[i] = S(dp.P[i]);
-    if (ALPHA) {
-#pragma unroll
-        for (int i = 0; i < N * N; ++i) E[i] = S(dE[i]);
-#pragma unroll
-        for (int i = 0; i < N; ++i) g[i] = S(dg[i]);
-    }
-    if (ctx.stats) atomicAdd(ctx.stats, 1ull);
-}
-
-template <int N, typename S, bool ALPHA>
-__device__ __forceinline__ void apply(const Elem<N, S>& e, Red<N, S>& p, S* E, S* g,
-                                      const CombineCtx& ctx)
-{
-    S Mi[N * N];
-    if (inverse_I_plus<N, S>(e.C, p.P, Mi, ctx.cond_max, false)) {
-        apply_core<N, S, ALPHA>(e, p, Mi, E, g);
-    } else {
-        apply_fp64<N, S, ALPHA>(e, p, E, g, ctx);
-    }
 }
 
 // ---------------------------------------------------------------------------

@@ -45,6 +45,7 @@ struct Ops {
     size_t (*workspace_bytes)(const map_smoother& h);
     map_status (*solve)(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st);
     map_status (*cost)(map_smoother& h, const void* y, const void* x, double* d_cost, cudaStream_t st);
+    map_status (*solve_sequential)(map_smoother& h, const void* y, void* x_out, cudaStream_t st);
 };
 
 const Ops* find_ops(int model, int N, int M, int prec);

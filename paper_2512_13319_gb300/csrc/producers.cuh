@@ -67,6 +67,13 @@ struct LtiProducer {
         load_run<K * W, S>(y + k0 * W, avail, buf);
     }
 
+    // inputs of one step (zeros past T)
+    __device__ __forceinline__ void load1(long k, S* row) const
+    {
+#pragma unroll
+        for (int j = 0; j < W; ++j) row[j] = k < T ? __ldg(y + k * W + j) : S(0);
+    }
+
     __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
     {
         if (k >= T) { set_identity(e); return; }
@@ -193,6 +200,15 @@ struct NlProducer {
 #pragma unroll
             for (int j = 0; j < N; ++j) buf[i * W + M + j] = in ? __ldg(xbar + (k + 1) * N + j) : S(0);
         }
+    }
+
+    __device__ __forceinline__ void load1(long k, S* row) const
+    {
+        const bool in = k < T;
+#pragma unroll
+        for (int j = 0; j < M; ++j) row[j] = in ? __ldg(y + k * M + j) : S(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) row[M + j] = in ? __ldg(xbar + (k + 1) * N + j) : S(0);
     }
 
     __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const

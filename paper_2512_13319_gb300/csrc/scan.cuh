@@ -20,6 +20,7 @@
 // suffix), starting from x_T = S_T^-1 v_T (Eq. 18 initial condition).
 #pragma once
 #include "producers.cuh"
+#include "coop.cuh"
 
 namespace mapk {
 
@@ -88,138 +89,232 @@ __device__ __forceinline__ void aos_load(const S* __restrict__ base, long idx, T
     for (int i = 0; i < Tp::NCOMP; ++i) comp(x, i) = tmp[i];
 }
 
-// ---------------------------------------------------------------------------
-// block-level trees in shared memory (component-major: sh[c * 2B + node])
-// ---------------------------------------------------------------------------
-
-// up-sweep over B filter partials; level 0 must be stored by the caller
-template <int N, typename S>
-__device__ void elem_tree_up(S* sh, int B, int t, const CombineCtx& ctx)
+// warp-interleaved layouts: per-thread items with the 32 lanes of a warp
+// adjacent for every component, so that every access is one 128-byte line
+__device__ __forceinline__ long wi_idx(long gthr, int c, int NC)
 {
-    const int LB = ilog2(B);
-    const int st = 2 * B;
+    return ((gthr >> 5) * NC + c) * 32 + (gthr & 31);
+}
+__device__ __forceinline__ long wis_idx(long gthr, int i, int c, int K, int NC)
+{
+    return (((gthr >> 5) * K + i) * NC + c) * 32 + (gthr & 31);
+}
+template <class Tp, typename S>
+__device__ __forceinline__ void wi_store(S* __restrict__ base, long gthr, Tp& x)
+{
+#pragma unroll
+    for (int c = 0; c < Tp::NCOMP; ++c) base[wi_idx(gthr, c, Tp::NCOMP)] = comp(x, c);
+}
+template <class Tp, typename S>
+__device__ __forceinline__ void wi_load(const S* __restrict__ base, long gthr, Tp& x)
+{
+#pragma unroll
+    for (int c = 0; c < Tp::NCOMP; ++c) comp(x, c) = base[wi_idx(gthr, c, Tp::NCOMP)];
+}
+
+// ---------------------------------------------------------------------------
+// block-level trees over B = blockDim.x leaves, nodes in shared memory (slot
+// i of the tree at nodes + i * NE), evaluated by sub-warp groups (coop.cuh)
+// ---------------------------------------------------------------------------
+// slot j of level d in a tree whose node slots are NODE scalars apart
+template <int NODE, typename S>
+__device__ __forceinline__ S* slotn(S* nodes, int B, int d, int j)
+{
+    return nodes + (long)(lvl_off(B, d) + j) * NODE;
+}
+// element trees: slots of CoopLayout::NE scalars
+template <int N, typename S>
+__device__ __forceinline__ S* slot(S* nodes, int B, int d, int j)
+{
+    return slotn<CoopLayout<N, S>::NE>(nodes, B, d, j);
+}
+// affine trees: slots of CoopLayout::NA scalars
+template <int N, typename S>
+__device__ __forceinline__ S* aslot(S* nodes, int B, int d, int j)
+{
+    return slotn<CoopLayout<N, S>::NA>(nodes, B, d, j);
+}
+
+// up-sweep: node(d+1, j) = node(d, 2j+1) (x) node(d, 2j); leaves stored by the caller
+template <int N, typename S>
+__device__ void coop_elem_up(S* nodes, S* scr_all, const CombineCtx& ctx)
+{
+    using L = CoopLayout<N, S>;
+    const int B = blockDim.x, LB = ilog2(B);
+    const int ng = B / L::NL, g = threadIdx.x / L::NL;
+    S* scr = scr_all + g * L::NSCR;
     for (int d = 0; d < LB; ++d) {
         __syncthreads();
-        if (t < (B >> (d + 1))) {
-            Elem<N, S> l, r;
-            soa_load(sh, st, lvl_off(B, d) + 2 * t, l);
-            soa_load(sh, st, lvl_off(B, d) + 2 * t + 1, r);
-            combine<N, S>(r, l, r, ctx);               // later partial on the left
-            soa_store(sh, st, lvl_off(B, d + 1) + t, r);
+        const int cnt = B >> (d + 1);
+        for (int base = 0; base < cnt; base += ng) {
+            const int j = base + g;
+            const bool act = j < cnt;
+            if (__any_sync(0xffffffffu, act)) {
+                const int jj = act ? j : base;
+                coop_combine<N, S>(slot<N, S>(nodes, B, d, 2 * jj + 1), slot<N, S>(nodes, B, d, 2 * jj),
+                                   slot<N, S>(nodes, B, d + 1, jj), scr, act, ctx);
+            }
         }
     }
     __syncthreads();
 }
 
-// down-sweep: exclusive prefixes (one-variable value functions) of all leaves
-// given the prefix `pin` of the whole block (held by thread 0)
+// down-sweep: exclusive prefixes (value nodes, written over the element nodes)
+// of all leaves from the prefix `pin` of the block (given by thread 0)
 template <int N, typename S>
-__device__ void elem_tree_down(const S* sh, S* pr, int B, int t, const Red<N, S>& pin,
-                               const CombineCtx& ctx, Red<N, S>& out)
+__device__ void coop_elem_down(S* nodes, S* scr_all, const Red<N, S>& pin, const CombineCtx& ctx,
+                               Red<N, S>& out)
 {
-    const int LB = ilog2(B);
-    const int st = 2 * B;
-    if (t == 0) {
-        Red<N, S> p = pin;
-        soa_store(pr, st, lvl_off(B, LB), p);
+    using L = CoopLayout<N, S>;
+    const int B = blockDim.x, LB = ilog2(B);
+    const int NL = L::NL, ng = B / NL, g = threadIdx.x / NL, r = threadIdx.x & (NL - 1);
+    S* scr = scr_all + g * L::NSCR;
+    if (threadIdx.x == 0) node_store(pin, slot<N, S>(nodes, B, LB, 0));
+    for (int d = LB - 1; d >= 0; --d) {
+        __syncthreads();
+        const int cnt = B >> (d + 1);
+        for (int base = 0; base < cnt; base += ng) {
+            const int j = base + g;
+            const bool act = j < cnt;
+            if (__any_sync(0xffffffffu, act)) {
+                const int jj = act ? j : base;
+                S* par = slot<N, S>(nodes, B, d + 1, jj);
+                S* lft = slot<N, S>(nodes, B, d, 2 * jj);
+                S* rgt = slot<N, S>(nodes, B, d, 2 * jj + 1);
+                coop_apply<N, S>(lft, par, rgt, scr, act, ctx);
+                __syncwarp();
+                if (act)
+                    for (int i = r; i < L::NR; i += NL) lft[i] = par[i];
+            }
+        }
+    }
+    __syncthreads();
+    node_load(slot<N, S>(nodes, B, 0, threadIdx.x), out);
+}
+
+// affine up-sweep: node(d+1, j) = node(d, 2j) o node(d, 2j+1); a leaf maps the
+// state at the END of its steps to the state at their START
+template <int N, typename S>
+__device__ void coop_aff_up(S* nodes)
+{
+    using L = CoopLayout<N, S>;
+    const int B = blockDim.x, LB = ilog2(B);
+    const int ng = B / L::NL, g = threadIdx.x / L::NL;
+    for (int d = 0; d < LB; ++d) {
+        __syncthreads();
+        const int cnt = B >> (d + 1);
+        for (int base = 0; base < cnt; base += ng) {
+            const int j = base + g;
+            const bool act = j < cnt;
+            if (__any_sync(0xffffffffu, act)) {
+                const int jj = act ? j : base;
+                coop_compose<N, S>(aslot<N, S>(nodes, B, d, 2 * jj), aslot<N, S>(nodes, B, d, 2 * jj + 1),
+                                   aslot<N, S>(nodes, B, d + 1, jj), act);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// suffix down-sweep: the state at the END of every leaf (written over the
+// nodes) from the state `xend` at the end of the block (given by thread 0)
+template <int N, typename S>
+__device__ void coop_aff_down(S* nodes, const S* xend, S* out)
+{
+    using L = CoopLayout<N, S>;
+    const int B = blockDim.x, LB = ilog2(B);
+    const int NL = L::NL, ng = B / NL, g = threadIdx.x / NL, r = threadIdx.x & (NL - 1);
+    const int rr = r < N ? r : N - 1;
+    if (threadIdx.x == 0) {
+        S* root = aslot<N, S>(nodes, B, LB, 0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) root[i] = xend[i];
     }
     for (int d = LB - 1; d >= 0; --d) {
         __syncthreads();
-        if (t < (B >> (d + 1))) {
-            Red<N, S> p;
-            Elem<N, S> l;
-            soa_load(pr, st, lvl_off(B, d + 1) + t, p);
-            soa_store(pr, st, lvl_off(B, d) + 2 * t, p);
-            soa_load(sh, st, lvl_off(B, d) + 2 * t, l);
-            apply<N, S, false>(l, p, nullptr, nullptr, ctx);
-            soa_store(pr, st, lvl_off(B, d) + 2 * t + 1, p);
+        const int cnt = B >> (d + 1);
+        for (int base = 0; base < cnt; base += ng) {
+            const int j = base + g;
+            const bool act = j < cnt;
+            if (__any_sync(0xffffffffu, act)) {
+                const int jj = act ? j : base;
+                S* par = aslot<N, S>(nodes, B, d + 1, jj);
+                S* lft = aslot<N, S>(nodes, B, d, 2 * jj);
+                S* rgt = aslot<N, S>(nodes, B, d, 2 * jj + 1);
+                S f[N], x[N];
+                row_load<N, S>(rgt + L::oF, rr, f);
+                vec_load<N, S>(par, x);
+                S y = rgt[L::oc + rr];
+#pragma unroll
+                for (int q = 0; q < N; ++q) y = fma(f[q], x[q], y);
+                __syncwarp();
+                if (act && r < N) {
+                    lft[rr] = y;
+                    rgt[rr] = x[rr];
+                }
+            }
         }
     }
     __syncthreads();
-    soa_load(pr, st, t, out);
+    const S* leaf = aslot<N, S>(nodes, B, 0, threadIdx.x);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = leaf[i];
 }
 
-// affine maps: node(d+1, t) = node(d, 2t) o node(d, 2t+1)  (a leaf maps the
-// state at the END of its steps to the state at their START)
+// shared memory of the element trees: 2B node slots + one scratch area per group
 template <int N, typename S>
-__device__ void aff_tree_up(S* sh, int B, int t)
+__host__ __device__ constexpr size_t tree_smem(int B)
 {
-    const int LB = ilog2(B);
-    const int st = 2 * B;
-    for (int d = 0; d < LB; ++d) {
-        __syncthreads();
-        if (t < (B >> (d + 1))) {
-            Aff<N, S> l, r;
-            soa_load(sh, st, lvl_off(B, d) + 2 * t, l);
-            soa_load(sh, st, lvl_off(B, d) + 2 * t + 1, r);
-            compose<N, S>(l, r, l);
-            soa_store(sh, st, lvl_off(B, d + 1) + t, l);
-        }
-    }
-    __syncthreads();
+    return sizeof(S) * ((size_t)2 * B * CoopLayout<N, S>::NE +
+                        (size_t)(B / CoopLayout<N, S>::NL) * CoopLayout<N, S>::NSCR);
+}
+// shared memory of the affine trees: 2B node slots
+template <int N, typename S>
+__host__ __device__ constexpr size_t aff_tree_smem(int B)
+{
+    return sizeof(S) * (size_t)2 * B * CoopLayout<N, S>::NA;
 }
 
-// suffix down-sweep: the state at the END of every leaf, given the state at
-// the end of the block (held by thread 0)
 template <int N, typename S>
-__device__ void aff_tree_down(const S* sh, S* xs, int B, int t, const S* xend, S* out)
+__device__ __forceinline__ S* scratch_of(S* nodes)
 {
-    const int LB = ilog2(B);
-    const int st = 2 * B;
-    if (t == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) xs[i * st + lvl_off(B, LB)] = xend[i];
-    }
-    for (int d = LB - 1; d >= 0; --d) {
-        __syncthreads();
-        if (t < (B >> (d + 1))) {
-            S x[N], y[N];
-#pragma unroll
-            for (int i = 0; i < N; ++i) x[i] = xs[i * st + lvl_off(B, d + 1) + t];
-#pragma unroll
-            for (int i = 0; i < N; ++i) xs[i * st + lvl_off(B, d) + 2 * t + 1] = x[i];
-            Aff<N, S> r;
-            soa_load(sh, st, lvl_off(B, d) + 2 * t + 1, r);
-            affine_apply<N, S>(r, x, y);
-#pragma unroll
-            for (int i = 0; i < N; ++i) xs[i * st + lvl_off(B, d) + 2 * t] = y[i];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < N; ++i) out[i] = xs[i * st + t];
+    return nodes + (long)2 * blockDim.x * CoopLayout<N, S>::NE;
 }
 
 // ---------------------------------------------------------------------------
 // phase 1: per-thread fold and per-tile total of the filter elements
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod, int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 3)
 k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
                 S* __restrict__ tile_agg, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* sh = reinterpret_cast<S*>(smem_raw);
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
     const long gthr = (long)blockIdx.x * B + t;
     const long k0 = gthr * K;
 
-    S rows[K * Prod::W];
-    prod.template load<K>(k0, rows);
     Elem<N, S> G;
-    prod.make(k0, rows, G);
-#pragma unroll
+    {
+        S row[Prod::W];
+        prod.load1(k0, row);
+        prod.make(k0, row, G);
+    }
+#pragma unroll 1
     for (int i = 1; i < K; ++i) {
+        S row[Prod::W];
+        prod.load1(k0 + i, row);
         Elem<N, S> e;
-        prod.make(k0 + i, rows + i * Prod::W, e);
+        prod.make(k0 + i, row, e);
         combine<N, S>(e, G, G, ctx);
     }
-    aos_store(thr_agg, gthr, G);
-    soa_store(sh, 2 * B, t, G);
-    elem_tree_up<N, S>(sh, B, t, ctx);
+    wi_store(thr_agg, gthr, G);
+    node_store(G, slot<N, S>(nodes, B, 0, t));
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
     if (t == 0) {
         Elem<N, S> root;
-        soa_load(sh, 2 * B, lvl_off(B, ilog2(B)), root);
+        node_load(slot<N, S>(nodes, B, ilog2(B), 0), root);
         aos_store(tile_agg, (long)blockIdx.x, root);
     }
 }
@@ -234,9 +329,8 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior,
                S* __restrict__ filtT_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
-    S* sh = reinterpret_cast<S*>(smem_raw);
-    S* pr = sh + Elem<N, S>::NCOMP * 2 * B;
     const int per = (nt + B - 1) / B;
     const int first = t * per, last = min(nt, first + per);
 
@@ -247,10 +341,10 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior,
         aos_load(tile_agg, i, g);
         combine<N, S>(g, H, H, ctx);
     }
-    soa_store(sh, 2 * B, t, H);
-    elem_tree_up<N, S>(sh, B, t, ctx);
+    node_store(H, slot<N, S>(nodes, B, 0, t));
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
     Red<N, S> P;
-    elem_tree_down<N, S>(sh, pr, B, t, prior, ctx, P);
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), prior, ctx, P);
     for (int i = first; i < last; ++i) {
         aos_store(tile_pref, i, P);
         Elem<N, S> g;
@@ -276,34 +370,32 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior,
 // per-tile compositions
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod, int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 3)
 k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
               const S* __restrict__ tile_pref, S* __restrict__ Eg, S* __restrict__ thr_aff,
               S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
-    S* sh = reinterpret_cast<S*>(smem_raw);
-    S* pr = sh + Elem<N, S>::NCOMP * 2 * B;
     const long gthr = (long)blockIdx.x * B + t;
     const long k0 = gthr * K;
     const long T = prod.T;
+    constexpr int NA = Aff<N, S>::NCOMP;
 
-    S rows[K * Prod::W];
-    prod.template load<K>(k0, rows);
     {
         Elem<N, S> G;
-        aos_load(thr_agg, gthr, G);
-        soa_store(sh, 2 * B, t, G);
+        wi_load(thr_agg, gthr, G);
+        node_store(G, slot<N, S>(nodes, B, 0, t));
     }
-    elem_tree_up<N, S>(sh, B, t, ctx);
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
     Red<N, S> pin, X;
     if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
-    elem_tree_down<N, S>(sh, pr, B, t, pin, ctx, X);
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;
         if (k < T) {
@@ -312,11 +404,14 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
                 for (int c = 0; c < Red<N, S>::NCOMP; ++c)
                     filt_out[k * Red<N, S>::NCOMP + c] = comp(X, c);
             }
+            S row[Prod::W];
+            prod.load1(k, row);
             Elem<N, S> e;
-            prod.make(k, rows + i * Prod::W, e);
+            prod.make(k, row, e);
             Aff<N, S> a;
             apply<N, S, true>(e, X, a.F, a.c, ctx);
-            aos_store(Eg, k, a);
+#pragma unroll
+            for (int c = 0; c < NA; ++c) Eg[wis_idx(gthr, i, c, K, NA)] = comp(a, c);
             // x_{k0} = Phi x_{k+1} + beta:  beta += Phi g,  Phi = Phi E
             S tmp[N];
             ms::mv<N, S>(comp_t.F, a.c, tmp);
@@ -328,13 +423,13 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
             for (int j = 0; j < N * N; ++j) comp_t.F[j] = F2[j];
         }
     }
-    aos_store(thr_aff, gthr, comp_t);
-    __syncthreads();                       // trees above are done with shared memory
-    soa_store(sh, 2 * B, t, comp_t);
-    aff_tree_up<N, S>(sh, B, t);
+    wi_store(thr_aff, gthr, comp_t);
+    __syncthreads();                       // the filter trees are done with shared memory
+    node_store(comp_t, aslot<N, S>(nodes, B, 0, t));
+    coop_aff_up<N, S>(nodes);
     if (t == 0) {
         Aff<N, S> root;
-        soa_load(sh, 2 * B, lvl_off(B, ilog2(B)), root);
+        node_load(aslot<N, S>(nodes, B, ilog2(B), 0), root);
         aos_store(tile_aff, (long)blockIdx.x, root);
     }
 }
@@ -348,9 +443,8 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
                S* __restrict__ tile_xend)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
-    S* sh = reinterpret_cast<S*>(smem_raw);
-    S* xs = sh + Aff<N, S>::NCOMP * 2 * B;
     const int per = (nt + B - 1) / B;
     const int first = t * per, last = min(nt, first + per);
 
@@ -361,12 +455,12 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
         aos_load(tile_aff, i, a);
         compose<N, S>(a, H, H);
     }
-    soa_store(sh, 2 * B, t, H);
-    aff_tree_up<N, S>(sh, B, t);
+    node_store(H, aslot<N, S>(nodes, B, 0, t));
+    coop_aff_up<N, S>(nodes);
     S xe[N], x[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) xe[i] = xT[i];
-    aff_tree_down<N, S>(sh, xs, B, t, xe, x);
+    coop_aff_down<N, S>(nodes, xe, x);
     for (int i = last - 1; i >= first; --i) {
 #pragma unroll
         for (int j = 0; j < N; ++j) tile_xend[(long)i * N + j] = x[j];
@@ -383,39 +477,91 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
 // phase 5: per-step smoothed states x_k = E_k x_{k+1} + g_k
 // ---------------------------------------------------------------------------
 template <int N, typename S, int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_rts_down(const S* __restrict__ Eg, const S* __restrict__ thr_aff,
            const S* __restrict__ tile_xend, long T, S* __restrict__ x_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
-    S* sh = reinterpret_cast<S*>(smem_raw);
-    S* xs = sh + Aff<N, S>::NCOMP * 2 * B;
     const long gthr = (long)blockIdx.x * B + t;
     const long k0 = gthr * K;
+    constexpr int NA = Aff<N, S>::NCOMP;
     {
         Aff<N, S> a;
-        aos_load(thr_aff, gthr, a);
-        soa_store(sh, 2 * B, t, a);
+        wi_load(thr_aff, gthr, a);
+        node_store(a, aslot<N, S>(nodes, B, 0, t));
     }
-    aff_tree_up<N, S>(sh, B, t);
+    coop_aff_up<N, S>(nodes);
     S xe[N], x[N];
     if (t == 0) {
 #pragma unroll
         for (int i = 0; i < N; ++i) xe[i] = tile_xend[(long)blockIdx.x * N + i];
     }
-    aff_tree_down<N, S>(sh, xs, B, t, xe, x);
+    coop_aff_down<N, S>(nodes, xe, x);
+    S xs[K][N];
 #pragma unroll
     for (int i = K - 1; i >= 0; --i) {
         const long k = k0 + i;
         if (k < T) {
             Aff<N, S> a;
-            aos_load(Eg, k, a);
+#pragma unroll
+            for (int c = 0; c < NA; ++c) comp(a, c) = Eg[wis_idx(gthr, i, c, K, NA)];
             S y[N];
             affine_apply<N, S>(a, x, y);
 #pragma unroll
-            for (int j = 0; j < N; ++j) { x[j] = y[j]; x_out[k * N + j] = y[j]; }
+            for (int j = 0; j < N; ++j) x[j] = y[j];
         }
+#pragma unroll
+        for (int j = 0; j < N; ++j) xs[i][j] = x[j];
+    }
+    // stage the tile's states in shared memory and write them out coalesced
+    __syncthreads();
+    S* st = nodes;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) st[(t * K + i) * N + j] = xs[i][j];
+    __syncthreads();
+    const long base = (long)blockIdx.x * B * K * N;
+    const long lim = T * N;
+    for (int idx = t; idx < B * K * N; idx += B)
+        if (base + idx < lim) x_out[base + idx] = st[idx];
+}
+
+// ---------------------------------------------------------------------------
+// sequential baseline: the same elements and recursions evaluated by one
+// thread in time order (information filter of Eq. 17 in discrete form, then
+// the closed-loop maps backwards), no scan
+// ---------------------------------------------------------------------------
+template <int N, typename S, class Prod>
+__global__ void __launch_bounds__(32)
+k_sequential(const __grid_constant__ Prod prod, Red<N, S> prior, S* __restrict__ Eg,
+             S* __restrict__ x_out, CombineCtx ctx)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long T = prod.T;
+    Red<N, S> X = prior;
+    for (long k = 0; k < T; ++k) {
+        S row[Prod::W];
+        prod.load1(k, row);
+        Elem<N, S> e;
+        prod.make(k, row, e);
+        Aff<N, S> a;
+        apply<N, S, true>(e, X, a.F, a.c, ctx);
+        aos_store(Eg, k, a);
+    }
+    S x[N];
+    if (!red_argmin<N, S>(X, x) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+#pragma unroll
+    for (int j = 0; j < N; ++j) x_out[T * N + j] = x[j];
+    for (long k = T - 1; k >= 0; --k) {
+        Aff<N, S> a;
+        aos_load(Eg, k, a);
+        S y[N];
+        affine_apply<N, S>(a, x, y);
+#pragma unroll
+        for (int j = 0; j < N; ++j) { x[j] = y[j]; x_out[k * N + j] = y[j]; }
     }
 }
 

@@ -90,9 +90,7 @@ size_t rts_workspace(const map_smoother& h)
 template <int N, typename S, class Prod>
 map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st)
 {
-    using E = Elem<N, S>;
     using R = Red<N, S>;
-    using A = Aff<N, S>;
     constexpr int K = KSTEP;
     const int B = h.B, nt = h.nt;
     const long nthr = (long)nt * B;
@@ -109,13 +107,13 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const long T = h.T;
     S* xT = x_out + T * N;
 
-    const size_t sh_reduce = sizeof(S) * E::NCOMP * 2 * B;
-    const size_t sh_down = sizeof(S) * std::max<size_t>(E::NCOMP + R::NCOMP, A::NCOMP) * 2 * B;
-    const size_t sh_rts = sizeof(S) * (A::NCOMP + N) * 2 * B;
-    const int bt_f = pick_tile_scan_threads(sizeof(S) * (E::NCOMP + R::NCOMP) * 2, nt);
-    const int bt_a = pick_tile_scan_threads(sizeof(S) * (A::NCOMP + N) * 2, nt);
-    const size_t sh_tf = sizeof(S) * (E::NCOMP + R::NCOMP) * 2 * bt_f;
-    const size_t sh_ta = sizeof(S) * (A::NCOMP + N) * 2 * bt_a;
+    const size_t sh_reduce = tree_smem<N, S>(B);
+    const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B));
+    const size_t sh_rts = std::max(aff_tree_smem<N, S>(B), sizeof(S) * B * K * N);
+    const int bt_f = pick_tile_scan_threads(tree_smem<N, S>(256) / 256, nt);
+    const int bt_a = pick_tile_scan_threads(aff_tree_smem<N, S>(256) / 256, nt);
+    const size_t sh_tf = tree_smem<N, S>(bt_f);
+    const size_t sh_ta = aff_tree_smem<N, S>(bt_a);
 
     static std::once_flag once;
     cudaError_t e0 = cudaSuccess;
@@ -149,6 +147,19 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     return MAP_OK;
 }
 
+// Sequential baseline on the same elements: one thread, time order.
+template <int N, typename S, class Prod>
+map_status run_sequential(map_smoother& h, const Prod& prod, S* x_out, cudaStream_t st)
+{
+    const Layout<N, S> L = Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad);
+    S* Eg = reinterpret_cast<S*>(h.ws + L.Eg);
+    const CombineCtx ctx{h.cond_max, h.d_stats};
+    k_sequential<N, S, Prod><<<1, 32, 0, st>>>(prod, prior_of<N, S>(h), Eg, x_out, ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    return MAP_OK;
+}
+
 // ---------------------------------------------------------------------------
 // linear models
 // ---------------------------------------------------------------------------
@@ -160,6 +171,16 @@ map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_
     prod.T = h.T;
     prod.p = lti_params<N, M, S>(h);
     return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
+}
+
+template <int N, int M, typename S>
+map_status solve_linear_sequential(map_smoother& h, const void* y, void* x_out, cudaStream_t st)
+{
+    LtiProducer<N, M, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.T = h.T;
+    prod.p = lti_params<N, M, S>(h);
+    return run_sequential<N, S>(h, prod, static_cast<S*>(x_out), st);
 }
 
 // Discrete Onsager-Machlup cost of a trajectory of a linear model:
@@ -257,7 +278,8 @@ map_status cost_linear(map_smoother& h, const void* y, const void* x, double* d_
 template <int N, int M, typename S>
 const Ops* linear_ops()
 {
-    static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>};
+    static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
+                         &solve_linear_sequential<N, M, S>};
     return &ops;
 }
 
@@ -306,17 +328,43 @@ map_status solve_nonlinear(map_smoother& h, const void* y, void* x_out, void* fi
     return MAP_OK;
 }
 
+template <class Model, typename S>
+map_status solve_nonlinear_sequential(map_smoother& h, const void* y, void* x_out, cudaStream_t st)
+{
+    constexpr int N = Model::N, M = Model::M;
+    NlProducer<Model, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.T = h.T;
+    prod.p = nl_params<N, M, S>(h);
+    S* cur = static_cast<S*>(x_out);
+    S* nxt = static_cast<S*>(h.d_xtmp);
+    for (int it = 0; it < h.gn_iters; ++it) {
+        prod.xbar = cur;
+        map_status s = run_sequential<N, S>(h, prod, nxt, st);
+        if (s != MAP_OK) return s;
+        std::swap(cur, nxt);
+    }
+    if (cur != x_out) {
+        cudaError_t e = cudaMemcpyAsync(x_out, cur, sizeof(S) * (size_t)(h.T + 1) * N,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+    }
+    return MAP_OK;
+}
+
 template <typename S>
 const Ops* coord_turn_ops()
 {
-    static const Ops ops{&rts_workspace<5, S>, &solve_nonlinear<CtModel<S>, S>, nullptr};
+    static const Ops ops{&rts_workspace<5, S>, &solve_nonlinear<CtModel<S>, S>, nullptr,
+                         &solve_nonlinear_sequential<CtModel<S>, S>};
     return &ops;
 }
 
 template <int N, int M, typename S>
 const Ops* cubic_ops()
 {
-    static const Ops ops{&rts_workspace<N, S>, &solve_nonlinear<CubicModel<N, M, S>, S>, nullptr};
+    static const Ops ops{&rts_workspace<N, S>, &solve_nonlinear<CubicModel<N, M, S>, S>, nullptr,
+                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>};
     return &ops;
 }
 

@@ -60,6 +60,16 @@ class MapSmoother:
             return x_out, f, c
         return x_out
 
+    def solve_sequential(self, y, x_out=None, x_init=None, stream=None):
+        """Single-thread sequential baseline on the GPU (same elements, no scan)."""
+        self._check_dev(y, (self.T, self.ny), "y")
+        if x_out is None:
+            x_out = torch.empty((self.T + 1, self.nx), dtype=self.dtype, device=y.device)
+        if x_init is not None:
+            x_out.copy_(x_init)
+        B.map_smoother_solve_sequential(self._h, y.data_ptr(), x_out.data_ptr(), self._stream(stream))
+        return x_out
+
     def solve_host(self, y_host, x_host=None, stream=None):
         """End-to-end solve from host memory (pinned CPU tensors) into host memory."""
         if x_host is None:
