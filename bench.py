@@ -275,7 +275,7 @@ def ours(args):
             phases.setdefault(k, []).append(v)
     sm.profile(False)
     phase_ms = {k: statistics.median(v) for k, v in phases.items()}
-    flops, byt = work_model(4, 2, 8, sm_B(sm), wbytes)
+    flops, byt = work_model(4, 2, 16, sm_B(sm), wbytes)
     dom = max(("filter_reduce", "filter_down", "rts_down"), key=lambda k: phase_ms.get(k, 0.0))
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}

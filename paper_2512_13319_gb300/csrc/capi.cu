@@ -195,7 +195,7 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
         return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be a power of two in [32, 256]");
     while (B > 32 && tree_bytes(B) > (d->tile_threads > 0 ? 200 : 100) * 1024) B /= 2;
     h->B = B;
-    h->K = 8;
+    h->K = 16;
     const long L = (long)h->B * h->K;
     h->nt = (int)((h->T + L - 1) / L);
     h->Tpad = (long)h->nt * L;

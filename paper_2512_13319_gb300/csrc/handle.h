@@ -18,7 +18,7 @@ struct map_smoother {
     mapk::SetupOut consts{};           // FP64 model constants computed on the device
     // launch geometry
     int B = 128;                       // threads per tile CTA
-    int K = 8;                         // steps per thread
+    int K = 16;                        // steps per thread
     int nt = 0;                        // tiles
     long Tpad = 0;                     // nt * B * K
     // device memory owned by the handle

@@ -24,6 +24,16 @@
 
 namespace mapk {
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while its predecessor on the stream still runs;
+// pdl_wait() blocks until the predecessor grid has completed and its writes
+// are visible, pdl_trigger() lets the successor grid launch.  Each kernel
+// triggers only after its own pdl_wait(), so a kernel never starts before the
+// kernel two launches back has completed.  Both are no-ops without the
+// launch attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Level d of a tree over B leaves has B >> d nodes stored from lvl_off(B, d);
 // all 2B - 1 nodes fit in 2B slots.
 __device__ __forceinline__ int lvl_off(int B, int d) { return 2 * B - ((2 * B) >> d); }
@@ -294,6 +304,8 @@ k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
     const int B = blockDim.x, t = threadIdx.x;
     const long gthr = (long)blockIdx.x * B + t;
     const long k0 = gthr * K;
+    pdl_wait();
+    pdl_trigger();
 
     Elem<N, S> G;
     {
@@ -320,7 +332,11 @@ k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
 }
 
 // ---------------------------------------------------------------------------
-// phase 2: one CTA scans the tile totals from the prior (Eq. 31 a_T)
+// phase 2: one CTA scans the tile totals from the prior (Eq. 31 a_T).  Each
+// thread folds `per` consecutive tile totals, the per-thread totals are
+// scanned with Kogge-Stone (log2(B) levels, every thread active; inclusive
+// prefixes with the later partial on the left), and each thread then walks
+// its tiles from its exclusive prefix with the one-variable combine.
 // ---------------------------------------------------------------------------
 template <int N, typename S>
 __global__ void __launch_bounds__(256)
@@ -329,22 +345,39 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior,
                S* __restrict__ filtT_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* nodes = reinterpret_cast<S*>(smem_raw);
+    S* sh = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
     const int per = (nt + B - 1) / B;
     const int first = t * per, last = min(nt, first + per);
+    pdl_wait();
+    pdl_trigger();
 
-    Elem<N, S> H;
-    set_identity(H);
+    Elem<N, S> F;
+    set_identity(F);
     for (int i = first; i < last; ++i) {
         Elem<N, S> g;
         aos_load(tile_agg, i, g);
-        combine<N, S>(g, H, H, ctx);
+        combine<N, S>(g, F, F, ctx);
     }
-    node_store(H, slot<N, S>(nodes, B, 0, t));
-    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    Red<N, S> P;
-    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), prior, ctx, P);
+    for (int o = 1; o < B; o <<= 1) {
+        __syncthreads();
+        soa_store(sh, B, t, F);
+        __syncthreads();
+        if (t >= o) {
+            Elem<N, S> e;
+            soa_load(sh, B, t - o, e);
+            combine<N, S>(F, e, F, ctx);
+        }
+    }
+    __syncthreads();
+    soa_store(sh, B, t, F);
+    __syncthreads();
+    Red<N, S> P = prior;
+    if (t > 0) {
+        Elem<N, S> e;
+        soa_load(sh, B, t - 1, e);
+        apply<N, S, false>(e, P, nullptr, nullptr, ctx);
+    }
     for (int i = first; i < last; ++i) {
         aos_store(tile_pref, i, P);
         Elem<N, S> g;
@@ -389,6 +422,8 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
         node_store(G, slot<N, S>(nodes, B, 0, t));
     }
     coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    pdl_wait();                            // tile prefixes of the previous kernel
+    pdl_trigger();
     Red<N, S> pin, X;
     if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
     coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
@@ -435,7 +470,9 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
 }
 
 // ---------------------------------------------------------------------------
-// phase 4: one CTA scans the tile maps backwards from x_T
+// phase 4: one CTA scans the tile maps backwards from x_T: per-thread
+// composites of `per` tiles, Kogge-Stone suffix composition over threads,
+// then each thread walks its tiles backwards from the state at its end.
 // ---------------------------------------------------------------------------
 template <int N, typename S>
 __global__ void __launch_bounds__(256)
@@ -443,10 +480,12 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
                S* __restrict__ tile_xend)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* nodes = reinterpret_cast<S*>(smem_raw);
+    S* sh = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
     const int per = (nt + B - 1) / B;
     const int first = t * per, last = min(nt, first + per);
+    pdl_wait();
+    pdl_trigger();
 
     Aff<N, S> H;
     set_identity(H);
@@ -455,12 +494,30 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
         aos_load(tile_aff, i, a);
         compose<N, S>(a, H, H);
     }
-    node_store(H, aslot<N, S>(nodes, B, 0, t));
-    coop_aff_up<N, S>(nodes);
-    S xe[N], x[N];
+    for (int o = 1; o < B; o <<= 1) {               // H_t o H_{t+1} o ... (suffix)
+        __syncthreads();
+        soa_store(sh, B, t, H);
+        __syncthreads();
+        if (t + o < B) {
+            Aff<N, S> a;
+            soa_load(sh, B, t + o, a);
+            compose<N, S>(H, a, H);
+        }
+    }
+    __syncthreads();
+    soa_store(sh, B, t, H);
+    __syncthreads();
+    S x[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) xe[i] = xT[i];
-    coop_aff_down<N, S>(nodes, xe, x);
+    for (int i = 0; i < N; ++i) x[i] = xT[i];
+    if (t + 1 < B) {                                // state at the end of this thread's tiles
+        Aff<N, S> a;
+        soa_load(sh, B, t + 1, a);
+        S y[N];
+        affine_apply<N, S>(a, x, y);
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = y[i];
+    }
     for (int i = last - 1; i >= first; --i) {
 #pragma unroll
         for (int j = 0; j < N; ++j) tile_xend[(long)i * N + j] = x[j];
@@ -493,6 +550,7 @@ k_rts_down(const S* __restrict__ Eg, const S* __restrict__ thr_aff,
         node_store(a, aslot<N, S>(nodes, B, 0, t));
     }
     coop_aff_up<N, S>(nodes);
+    pdl_wait();                            // tile end states of the previous kernel
     S xe[N], x[N];
     if (t == 0) {
 #pragma unroll

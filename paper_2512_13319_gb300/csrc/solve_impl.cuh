@@ -11,7 +11,7 @@
 
 namespace mapk {
 
-constexpr int KSTEP = 8;   // steps per thread
+constexpr int KSTEP = 16;  // steps per thread
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
@@ -45,6 +45,24 @@ inline int pick_tile_scan_threads(size_t bytes_per_thread, int nt)
     while (bt < 256 && bt < nt) bt *= 2;
     while (bt > 32 && bytes_per_thread * bt > 200 * 1024) bt /= 2;
     return bt;
+}
+
+// Launch with optional programmatic stream serialisation (see pdl_wait in scan.cuh).
+template <typename... KArgs, typename... Args>
+inline void launch(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, bool pdl,
+                   Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 template <typename Kern>
@@ -110,10 +128,10 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const size_t sh_reduce = tree_smem<N, S>(B);
     const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B));
     const size_t sh_rts = std::max(aff_tree_smem<N, S>(B), sizeof(S) * B * K * N);
-    const int bt_f = pick_tile_scan_threads(tree_smem<N, S>(256) / 256, nt);
-    const int bt_a = pick_tile_scan_threads(aff_tree_smem<N, S>(256) / 256, nt);
-    const size_t sh_tf = tree_smem<N, S>(bt_f);
-    const size_t sh_ta = aff_tree_smem<N, S>(bt_a);
+    const int bt_f = pick_tile_scan_threads(sizeof(S) * Elem<N, S>::NCOMP, nt);
+    const int bt_a = pick_tile_scan_threads(sizeof(S) * Aff<N, S>::NCOMP, nt);
+    const size_t sh_tf = sizeof(S) * Elem<N, S>::NCOMP * bt_f;
+    const size_t sh_ta = sizeof(S) * Aff<N, S>::NCOMP * bt_a;
 
     static std::once_flag once;
     cudaError_t e0 = cudaSuccess;
@@ -127,20 +145,24 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
+    // kernels 2-5 overlap their prologues with their predecessor (PDL), except
+    // when per-phase events are recorded between them
     h.nev = 0;
+    const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
-    k_filter_reduce<N, S, Prod, K><<<nt, B, sh_reduce, st>>>(prod, thr_agg, tile_agg, ctx);
+    launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_reduce, st, false, prod, thr_agg, tile_agg, ctx);
     mark();
-    k_filter_tiles<N, S><<<1, bt_f, sh_tf, st>>>(tile_agg, nt, prior_of<N, S>(h), tile_pref, fin, xT,
-                                                  filt_out ? filt_out + T * R::NCOMP : nullptr, ctx);
+    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
+           tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
     mark();
-    k_filter_down<N, S, Prod, K><<<nt, B, sh_down, st>>>(prod, thr_agg, tile_pref, Eg, thr_aff,
-                                                         tile_aff, filt_out, ctx);
+    launch(k_filter_down<N, S, Prod, K>, nt, B, sh_down, st, pdl, prod, (const S*)thr_agg,
+           (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx);
     mark();
-    k_affine_tiles<N, S><<<1, bt_a, sh_ta, st>>>(tile_aff, nt, xT, tile_xend);
+    launch(k_affine_tiles<N, S>, 1, bt_a, sh_ta, st, pdl, (const S*)tile_aff, nt, (const S*)xT, tile_xend);
     mark();
-    k_rts_down<N, S, K><<<nt, B, sh_rts, st>>>(Eg, thr_aff, tile_xend, T, x_out);
+    launch(k_rts_down<N, S, K>, nt, B, sh_rts, st, pdl, (const S*)Eg, (const S*)thr_aff,
+           (const S*)tile_xend, T, x_out);
     mark();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
