@@ -167,6 +167,33 @@ map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int re
 map_status map_smoother_profile(map_smoother* h, int enable);
 map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int* n_out);
 
+/*
+ * Allocation-free solve (no counterpart in the paper; a deployment entry point).
+ * For callers that cannot call cudaMalloc at all, e.g. code running where the
+ * device-memory budget is fixed up front (a real-time tracking loop, an
+ * embedded service that pre-reserves all device memory, a plug-in whose host
+ * owns the allocator).  Same result as map_smoother_create + map_smoother_solve
+ * for a linear model with the RTS smoother, without a handle: the model
+ * set-up and the scan workspace use file-scope __device__ arrays of this
+ * library (64 MiB of scratch plus a few KB), which every GPU on which this call
+ * has run holds until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.
+ *   desc   problem description as for map_smoother_create (MAP_MODEL_LINEAR,
+ *          smoother MAP_RTS); T limited by the 64 MiB scratch (about 6e5
+ *          intervals at nx = 4 in FP32), beyond which MAP_ERR_SHAPE is returned
+ *          with a message naming the bytes needed.
+ *   y, x_out  device arrays as for map_smoother_solve.
+ * The model set-up synchronises `stream`; the solve kernels are then enqueued
+ * on it asynchronously.  The first call on a device (with that device current)
+ * looks up the device addresses of the arrays; make it before any stream
+ * capture.  All calls share the arrays and they keep the last call's contents
+ * (the precision-policy counters are cleared by each call); calls that overlap
+ * on the GPU race and must be serialised by the caller.  Failures are described
+ * by map_smoother_last_error(NULL).
+ */
+map_status map_smoother_solve_noalloc(const map_problem_desc* desc, const void* y, void* x_out,
+                                      void* stream);
+
 /* Free the handle and its workspace (NULL is ignored). */
 void map_smoother_destroy(map_smoother* h);
 

@@ -45,6 +45,7 @@ EXPORTS = {
     "map_smoother_solve": (_I, [_VP, _VP, _VP, _VP, _D, _VP]),
     "map_smoother_solve_sequential": (_I, [_VP, _VP, _VP, _VP]),
     "map_smoother_solve_host": (_I, [_VP, _VP, _VP, _VP]),
+    "map_smoother_solve_noalloc": (_I, [ctypes.POINTER(map_problem_desc), _VP, _VP, _VP]),
     "map_smoother_grad": (_I, [_VP, _VP, _VP, _D, _VP]),
     "map_smoother_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_ulonglong), _I, _VP]),
     "map_smoother_profile": (_I, [_VP, _I]),

@@ -217,6 +217,8 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
 
 }  // namespace
 
+void mapk::set_handle_free_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 map_status map_smoother_create(map_smoother** out, const map_problem_desc* desc)

@@ -51,6 +51,8 @@ struct Ops {
 const Ops* find_ops(int model, int N, int M, int prec);
 
 map_status fail(map_smoother& h, map_status s, const std::string& msg);
+// message returned by map_smoother_last_error(NULL) on this thread
+void set_handle_free_error(const std::string& msg);
 map_status cuda_fail(map_smoother& h, cudaError_t e, const char* where);
 
 }  // namespace mapk
