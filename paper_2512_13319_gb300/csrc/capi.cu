@@ -110,8 +110,8 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
         return fail(*h, MAP_ERR_INVALID_ARG, "unknown model");
     if (d->model != MAP_MODEL_LINEAR && d->gn_iters < 1)
         return fail(*h, MAP_ERR_INVALID_ARG, "gn_iters must be >= 1 for nonlinear models");
-    if (d->smoother == MAP_TWO_FILTER)
-        return fail(*h, MAP_ERR_UNSUPPORTED, "two-filter smoother is not built in this version");
+    if (d->smoother == MAP_TWO_FILTER && d->model != MAP_MODEL_LINEAR)
+        return fail(*h, MAP_ERR_UNSUPPORTED, "the two-filter smoother is built for linear models");
 
     h->model = d->model; h->N = n; h->M = m; h->NW = nw;
     h->prec = d->precision; h->smoother = d->smoother;

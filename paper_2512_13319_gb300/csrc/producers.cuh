@@ -74,6 +74,13 @@ struct LtiProducer {
         for (int j = 0; j < W; ++j) row[j] = k < T ? __ldg(y + k * W + j) : S(0);
     }
 
+    // terminal value function of a reversed scan (not used for forward scans)
+    __device__ __forceinline__ void terminal(Red<N, S>& r) const
+    {
+#pragma unroll
+        for (int i = 0; i < Red<N, S>::NCOMP; ++i) comp(r, i) = S(0);
+    }
+
     __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
     {
         if (k >= T) { set_identity(e); return; }
@@ -89,6 +96,83 @@ struct LtiProducer {
 #pragma unroll
             for (int j = 0; j < M; ++j) s = fma(p.G[i * M + j], row[j], s);
             e.eta[i] = s;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Backward information filter of the two-filter smoother (Section 3.5 second
+// method, Section 4.3 Eq. 43): the same combine applied to the interval
+// elements written the other way round.  The flipped element of interval k
+// has start x_k and end x_{k+1}: the forward transition
+//   A' = Phi = A^-1,  b' = beta = -A^-1 b,  C' = Sigma = A^-1 C A^-T,
+// with x_k's own measurement (y_k, none for k = 0) as its (J', eta').  They are
+// scanned in reversed order j = Tpad - 1 - k (Tpad = padded horizon, so that
+// thread chunks coincide with those of the forward scan), starting from the
+// terminal value function of x_T, which carries y_T.  The prefix before
+// element j is then the information on x_{k+1} from y_{k+1}..y_T.
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+struct FlipParams {
+    static constexpr int NS = Sym<N>::SZ;
+    S A[N * N];      // Phi
+    S b[N];          // beta
+    S C[NS];         // Sigma
+    S J[NS];         // dt H^T R^-1 H
+    S G[N * M];      // dt H^T R^-1
+    S Gr[N];         // dt H^T R^-1 r
+};
+
+template <int N, int M, typename S>
+struct RevFlipProducer {
+    static constexpr int W = M;
+    const S* y;                      // (T, M), row k-1 holds y_k
+    long T;
+    long Tpad;
+    FlipParams<N, M, S> p;
+
+    __device__ __forceinline__ void load1(long j, S* row) const
+    {
+        const long k = Tpad - 1 - j;
+        const bool in = k >= 1 && k < T;
+#pragma unroll
+        for (int q = 0; q < W; ++q) row[q] = in ? __ldg(y + (k - 1) * W + q) : S(0);
+    }
+
+    // information of y_T on x_T
+    __device__ __forceinline__ void terminal(Red<N, S>& r) const
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = -p.Gr[i];
+#pragma unroll
+            for (int q = 0; q < M; ++q) s = fma(p.G[i * M + q], __ldg(y + (T - 1) * M + q), s);
+            r.v[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) r.P[i] = p.J[i];
+    }
+
+    // the flipped element of interval k = Tpad - 1 - j (identity past the horizon)
+    __device__ __forceinline__ void make(long j, const S* row, Elem<N, S>& e) const
+    {
+        const long k = Tpad - 1 - j;
+        if (k >= T) { set_identity(e); return; }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) e.A[i] = p.A[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) e.b[i] = p.b[i];
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) e.C[i] = p.C[i];
+        const bool meas = k >= 1;
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) e.J[i] = meas ? p.J[i] : S(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = -p.Gr[i];
+#pragma unroll
+            for (int q = 0; q < M; ++q) s = fma(p.G[i * M + q], row[q], s);
+            e.eta[i] = meas ? s : S(0);
         }
     }
 };
@@ -209,6 +293,12 @@ struct NlProducer {
         for (int j = 0; j < M; ++j) row[j] = in ? __ldg(y + k * M + j) : S(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) row[M + j] = in ? __ldg(xbar + (k + 1) * N + j) : S(0);
+    }
+
+    __device__ __forceinline__ void terminal(Red<N, S>& r) const
+    {
+#pragma unroll
+        for (int i = 0; i < Red<N, S>::NCOMP; ++i) comp(r, i) = S(0);
     }
 
     __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const

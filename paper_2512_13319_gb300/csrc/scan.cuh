@@ -297,7 +297,7 @@ __device__ __forceinline__ S* scratch_of(S* nodes)
 template <int N, typename S, class Prod, int K>
 __global__ void __launch_bounds__(128, 3)
 k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
-                S* __restrict__ tile_agg, CombineCtx ctx)
+                S* __restrict__ tile_agg, S* __restrict__ terminal_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -306,6 +306,11 @@ k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
     const long k0 = gthr * K;
     pdl_wait();
     pdl_trigger();
+    if (terminal_out && blockIdx.x == 0 && t == 0) {
+        Red<N, S> r;
+        prod.terminal(r);
+        aos_store(terminal_out, 0, r);
+    }
 
     Elem<N, S> G;
     {
@@ -340,7 +345,7 @@ k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
 // ---------------------------------------------------------------------------
 template <int N, typename S>
 __global__ void __launch_bounds__(256)
-k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior,
+k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S* __restrict__ prior_dev,
                S* __restrict__ tile_pref, S* __restrict__ final_out, S* __restrict__ xT_out,
                S* __restrict__ filtT_out, CombineCtx ctx)
 {
@@ -351,6 +356,7 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior,
     const int first = t * per, last = min(nt, first + per);
     pdl_wait();
     pdl_trigger();
+    if (prior_dev) aos_load(prior_dev, 0, prior);   // terminal value function of a reversed scan
 
     Elem<N, S> F;
     set_identity(F);
@@ -467,6 +473,180 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
         node_load(aslot<N, S>(nodes, B, ilog2(B), 0), root);
         aos_store(tile_aff, (long)blockIdx.x, root);
     }
+}
+
+// ---------------------------------------------------------------------------
+// phase 3 of the two-filter smoother, forward part: per-step filter value
+// functions (S_k, v_k), stored per thread and step (warp-interleaved)
+// ---------------------------------------------------------------------------
+template <int N, typename S, class Prod, int K>
+__global__ void __launch_bounds__(128, 3)
+k_filter_states(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
+                const S* __restrict__ tile_pref, S* __restrict__ filt_ws, S* __restrict__ filt_out,
+                CombineCtx ctx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
+    const int B = blockDim.x, t = threadIdx.x;
+    const long gthr = (long)blockIdx.x * B + t;
+    const long k0 = gthr * K;
+    const long T = prod.T;
+    constexpr int NR = Red<N, S>::NCOMP;
+    {
+        Elem<N, S> G;
+        wi_load(thr_agg, gthr, G);
+        node_store(G, slot<N, S>(nodes, B, 0, t));
+    }
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    pdl_wait();
+    pdl_trigger();
+    Red<N, S> pin, X;
+    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) {
+        const long k = k0 + i;
+        if (k < T) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) filt_ws[wis_idx(gthr, i, c, K, NR)] = comp(X, c);
+            if (filt_out) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) filt_out[k * NR + c] = comp(X, c);
+            }
+            S row[Prod::W];
+            prod.load1(k, row);
+            Elem<N, S> e;
+            prod.make(k, row, e);
+            apply<N, S, false>(e, X, nullptr, nullptr, ctx);
+        }
+    }
+}
+
+// x = (S + L)^-1 (v + z) for symmetric positive definite S + L (Cholesky; a
+// non-positive pivot falls back to Gauss-Jordan with row pivoting)
+template <int N, typename S>
+__device__ __forceinline__ void spd_combine_solve(const Red<N, S>& a, const Red<N, S>& b, S* x)
+{
+    S M[N * N], rhs[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        rhs[i] = a.v[i] + b.v[i];
+#pragma unroll
+        for (int j = 0; j < N; ++j) M[i * N + j] = a.P[Sym<N>::at(i, j)] + b.P[Sym<N>::at(i, j)];
+    }
+    S Lc[N * N];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        S d = M[j * N + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fma(-Lc[j * N + k], Lc[j * N + k], d);
+        ok = ok && d > S(0);
+        const S ljj = sqrt(d > S(0) ? d : S(1));
+        const S il = S(1) / ljj;
+        Lc[j * N + j] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            S s = M[i * N + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = fma(-Lc[i * N + k], Lc[j * N + k], s);
+            Lc[i * N + j] = s * il;
+        }
+    }
+    if (ok) {
+        S z[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = rhs[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s = fma(-Lc[i * N + k], z[k], s);
+            z[i] = s / Lc[i * N + i];
+        }
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            S s = z[i];
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) s = fma(-Lc[k * N + i], x[k], s);
+            x[i] = s / Lc[i * N + i];
+        }
+    } else {
+        S Mi[N * N];
+        ms::inv_row_pivot<N, S>(M, Mi);
+        ms::mv<N, S>(Mi, rhs, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 3 of the two-filter smoother, backward part: per-step backward
+// information (Lam_k, zeta_k) on x_k from y_{k+1}..y_T, combined with the
+// forward filter: x*_k = (S_k + Lam_k)^-1 (v_k + zeta_k)  (Eq. 43 in
+// information form).  Thread g' of this reversed scan covers the steps of
+// forward thread g = nthr - 1 - g'.
+// ---------------------------------------------------------------------------
+template <int N, typename S, class RProd, int K>
+__global__ void __launch_bounds__(128, 3)
+k_tf_down(const __grid_constant__ RProd prod, const S* __restrict__ thr_agg,
+          const S* __restrict__ tile_pref, const S* __restrict__ filt_ws, S* __restrict__ x_out,
+          CombineCtx ctx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
+    const int B = blockDim.x, t = threadIdx.x;
+    const long gthr = (long)blockIdx.x * B + t;
+    const long nthr = (long)gridDim.x * B;
+    const long j0 = gthr * K;
+    const long T = prod.T, Tpad = prod.Tpad;
+    const long gf = nthr - 1 - gthr;            // forward thread with the same steps
+    constexpr int NR = Red<N, S>::NCOMP;
+    {
+        Elem<N, S> G;
+        wi_load(thr_agg, gthr, G);
+        node_store(G, slot<N, S>(nodes, B, 0, t));
+    }
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    pdl_wait();
+    Red<N, S> pin, X;
+    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
+    // the block's steps are forward tile (gridDim.x - 1 - blockIdx.x); its states
+    // are staged in shared memory (the tree is no longer needed) and stored coalesced
+    __syncthreads();
+    S* st = nodes;
+    const int tf = B - 1 - t;
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) {
+        const long j = j0 + i;
+        const long k = Tpad - 1 - j;
+        S* xk = st + (tf * K + (K - 1 - i)) * N;
+        if (k < T) {
+            S row[RProd::W];
+            prod.load1(j, row);
+            Elem<N, S> e;
+            prod.make(j, row, e);
+            Red<N, S> Lam = X, F;
+            Elem<N, S> e0 = e;
+#pragma unroll
+            for (int q = 0; q < Sym<N>::SZ; ++q) e0.J[q] = S(0);
+#pragma unroll
+            for (int q = 0; q < N; ++q) e0.eta[q] = S(0);
+            apply<N, S, false>(e0, Lam, nullptr, nullptr, ctx);   // information from y_{k+1}..y_T
+#pragma unroll
+            for (int c = 0; c < NR; ++c) comp(F, c) = filt_ws[wis_idx(gf, K - 1 - i, c, K, NR)];
+            S x[N];
+            spd_combine_solve<N, S>(F, Lam, x);
+#pragma unroll
+            for (int q = 0; q < N; ++q) xk[q] = x[q];
+#pragma unroll
+            for (int q = 0; q < Sym<N>::SZ; ++q) X.P[q] = Lam.P[q] + e.J[q];
+#pragma unroll
+            for (int q = 0; q < N; ++q) X.v[q] = Lam.v[q] + e.eta[q];
+        }
+    }
+    __syncthreads();
+    const long base = (long)(gridDim.x - 1 - blockIdx.x) * B * K * N;
+    const long lim = T * N;
+    for (int idx = t; idx < B * K * N; idx += B)
+        if (base + idx < lim) x_out[base + idx] = st[idx];
 }
 
 // ---------------------------------------------------------------------------

@@ -17,7 +17,8 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 template <int N, typename S>
 struct Layout {
-    size_t thr_agg, tile_agg, tile_pref, fin, Eg, thr_aff, tile_aff, tile_xend, total;
+    size_t thr_agg, tile_agg, tile_pref, fin, Eg, thr_aff, tile_aff, tile_xend;
+    size_t filt_ws, term, fin2, xdummy, total;
     static Layout make(long nthr, long nt, long Tpad)
     {
         using E = Elem<N, S>;
@@ -33,6 +34,10 @@ struct Layout {
         l.thr_aff = o;   o = align_up(o + sizeof(S) * A::NCOMP * nthr);
         l.tile_aff = o;  o = align_up(o + sizeof(S) * A::NCOMP * nt);
         l.tile_xend = o; o = align_up(o + sizeof(S) * N * nt);
+        l.filt_ws = o;   o = align_up(o + sizeof(S) * R::NCOMP * Tpad);
+        l.term = o;      o = align_up(o + sizeof(S) * R::NCOMP);
+        l.fin2 = o;      o = align_up(o + sizeof(S) * R::NCOMP);
+        l.xdummy = o;    o = align_up(o + sizeof(S) * N);
         l.total = o;
         return l;
     }
@@ -121,7 +126,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     S* thr_aff = reinterpret_cast<S*>(h.ws + L.thr_aff);
     S* tile_aff = reinterpret_cast<S*>(h.ws + L.tile_aff);
     S* tile_xend = reinterpret_cast<S*>(h.ws + L.tile_xend);
-    const CombineCtx ctx{h.cond_max, h.d_stats};
+    const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     const long T = h.T;
     S* xT = x_out + T * N;
 
@@ -151,10 +156,11 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
-    launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_reduce, st, false, prod, thr_agg, tile_agg, ctx);
+    launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_reduce, st, false, prod, thr_agg, tile_agg,
+           (S*)nullptr, ctx);
     mark();
     launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
-           tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
+           (const S*)nullptr, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
     mark();
     launch(k_filter_down<N, S, Prod, K>, nt, B, sh_down, st, pdl, prod, (const S*)thr_agg,
            (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx);
@@ -169,13 +175,78 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     return MAP_OK;
 }
 
+// Two-filter smoother (linear models): forward filter scan storing (S_k, v_k),
+// backward information-filter scan of the flipped elements in reversed order,
+// and the per-step combination x*_k = (S_k + Lam_k)^-1 (v_k + zeta_k).
+template <int N, typename S, class Prod, class RProd>
+map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_out, S* filt_out,
+                  cudaStream_t st)
+{
+    using R = Red<N, S>;
+    constexpr int K = KSTEP;
+    const int B = h.B, nt = h.nt;
+    const long nthr = (long)nt * B;
+    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
+    S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
+    S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
+    S* tile_pref = reinterpret_cast<S*>(h.ws + L.tile_pref);
+    S* fin = reinterpret_cast<S*>(h.ws + L.fin);
+    S* filt_ws = reinterpret_cast<S*>(h.ws + L.filt_ws);
+    S* term = reinterpret_cast<S*>(h.ws + L.term);
+    S* fin2 = reinterpret_cast<S*>(h.ws + L.fin2);
+    S* xdummy = reinterpret_cast<S*>(h.ws + L.xdummy);
+    const CombineCtx ctx{(float)h.cond_max, h.d_stats};
+    const long T = h.T;
+    S* xT = x_out + T * N;
+    const size_t sh_tree = tree_smem<N, S>(B);
+    const int bt_f = pick_tile_scan_threads(sizeof(S) * Elem<N, S>::NCOMP, nt);
+    const size_t sh_tf = sizeof(S) * Elem<N, S>::NCOMP * bt_f;
+
+    static std::once_flag once;
+    cudaError_t e0 = cudaSuccess;
+    std::call_once(once, [&] {
+        const size_t big = 200 * 1024;
+        e0 = allow_smem(k_filter_reduce<N, S, Prod, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_reduce<N, S, RProd, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_states<N, S, Prod, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_tf_down<N, S, RProd, K>, big);
+    });
+    if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
+
+    h.nev = 0;
+    const bool pdl = !h.profile;
+    auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
+    mark();
+    launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_tree, st, false, fprod, thr_agg, tile_agg,
+           (S*)nullptr, ctx);
+    mark();
+    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
+           (const S*)nullptr, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
+    mark();
+    launch(k_filter_states<N, S, Prod, K>, nt, B, sh_tree, st, pdl, fprod, (const S*)thr_agg,
+           (const S*)tile_pref, filt_ws, filt_out, ctx);
+    mark();
+    launch(k_filter_reduce<N, S, RProd, K>, nt, B, sh_tree, st, pdl, rprod, thr_agg, tile_agg, term, ctx);
+    mark();
+    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
+           (const S*)term, tile_pref, fin2, xdummy, (S*)nullptr, ctx);
+    mark();
+    launch(k_tf_down<N, S, RProd, K>, nt, B, sh_tree, st, pdl, rprod, (const S*)thr_agg,
+           (const S*)tile_pref, (const S*)filt_ws, x_out, ctx);
+    mark();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    return MAP_OK;
+}
+
 // Sequential baseline on the same elements: one thread, time order.
 template <int N, typename S, class Prod>
 map_status run_sequential(map_smoother& h, const Prod& prod, S* x_out, cudaStream_t st)
 {
     const Layout<N, S> L = Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad);
     S* Eg = reinterpret_cast<S*>(h.ws + L.Eg);
-    const CombineCtx ctx{h.cond_max, h.d_stats};
+    const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     k_sequential<N, S, Prod><<<1, 32, 0, st>>>(prod, prior_of<N, S>(h), Eg, x_out, ctx);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
@@ -186,12 +257,36 @@ map_status run_sequential(map_smoother& h, const Prod& prod, S* x_out, cudaStrea
 // linear models
 // ---------------------------------------------------------------------------
 template <int N, int M, typename S>
+FlipParams<N, M, S> flip_params(const map_smoother& h)
+{
+    const SetupOut& c = h.consts;
+    FlipParams<N, M, S> p;
+    for (int i = 0; i < N * N; ++i) p.A[i] = S(c.Phi[i]);
+    for (int i = 0; i < N; ++i) { p.b[i] = S(c.beta[i]); p.Gr[i] = S(c.Gr[i]); }
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) {
+            p.C[Sym<N>::at(i, j)] = S(0.5 * (c.Sigma[i * N + j] + c.Sigma[j * N + i]));
+            p.J[Sym<N>::at(i, j)] = S(c.J[i * N + j]);
+        }
+    for (int i = 0; i < N * M; ++i) p.G[i] = S(c.G[i]);
+    return p;
+}
+
+template <int N, int M, typename S>
 map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st)
 {
     LtiProducer<N, M, S> prod;
     prod.y = static_cast<const S*>(y);
     prod.T = h.T;
     prod.p = lti_params<N, M, S>(h);
+    if (h.smoother == MAP_TWO_FILTER) {
+        RevFlipProducer<N, M, S> rprod;
+        rprod.y = static_cast<const S*>(y);
+        rprod.T = h.T;
+        rprod.Tpad = h.Tpad;
+        rprod.p = flip_params<N, M, S>(h);
+        return run_tf<N, S>(h, prod, rprod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
+    }
     return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
 }
 

@@ -210,3 +210,54 @@ def test_invalid_arguments_raise():
         B.map_smoother_solve(sm._h, None, None)
     assert ei.value.status == B.MAP_ERR_INVALID_ARG
     sm.close()
+
+
+# ---------------------------------------------------------------- two-filter
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_two_filter_T1000(prec):
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    _, y = synth.simulate(model, 1000, 0.01, seed=synth.seed_for(0))
+    x, _ = gpu_solve(model, y, 0.01, prec, smoother="two_filter")
+    assert rel(x, oracle.smooth_lti(model, y, 0.01, smoother=oracle.TWO_FILTER)) <= TOL[prec]
+    assert rel(x, oracle.smooth_lti(model, y, 0.01)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [1, 2, 3, 15, 16, 17, 2047, 2048, 2049, 5000])
+def test_two_filter_ragged_horizons(prec, T):
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    _, y = synth.simulate(model, T, 0.01, seed=100 + T)
+    x, _ = gpu_solve(model, y, 0.01, prec, smoother="two_filter")
+    assert rel(x, oracle.smooth_lti(model, y, 0.01)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", [s[0] for s in SHAPES])
+def test_two_filter_state_dimensions(prec, name):
+    model = dict(SHAPES)[name]()
+    T, dt = 3000, 0.01
+    _, y = synth.simulate(model, T, dt, seed=31)
+    x, _ = gpu_solve(model, y, dt, prec, smoother="two_filter")
+    assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
+
+
+def test_two_filter_affine_terms_and_exact_discretisation():
+    model = synth.ou_model(4, 2, seed=41)
+    model.c = np.array([0.5, -1.0, 0.25, 2.0])
+    model.r = np.array([0.3, -0.7])
+    T, dt = 4000, 0.05
+    _, y = synth.simulate(model, T, dt, seed=42)
+    for prec in ("fp64", "fp32"):
+        x, _ = gpu_solve(model, y, dt, prec, smoother="two_filter", discretisation="expm")
+        assert rel(x, oracle.smooth_lti(model, y, dt, mode=oracle.EXPM, smoother=oracle.TWO_FILTER)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_two_filter_full_size_matches_rts(prec):
+    model = synth.wiener_velocity(2, q=1.0, r=0.1)
+    T, dt = 2 ** 20, 1e-3
+    _, y = synth.simulate(model, T, dt, seed=synth.seed_for(1), substeps=1)
+    x_tf, _ = gpu_solve(model, y, dt, prec, smoother="two_filter")
+    ref = oracle.smooth_lti(model, y, dt)
+    assert rel(x_tf, ref) <= TOL[prec]
