@@ -134,16 +134,36 @@ map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_
                                    void* stream);
 
 /*
- * Gradient of a loss of the MAP trajectory of the last solve with respect to
+ * Gradient of a loss of the MAP trajectory with respect to
  * theta = (F (nx*nx, row-major), log q, log r), where Q = q L W L^T and
- * R = r R_desc scale with q = r = 1 at the values given to create.
- *   dL_dx     device (T+1) x nx, or NULL for L = the MAP cost itself.
+ * R = r R_desc; q = r = 1 at create and map_smoother_update changes them.
+ * The MAP trajectory x* = argmin M(x; theta) of the discrete cost solves
+ * K(theta) x* = g(theta) with K symmetric, so (implicit-function adjoint):
+ *   dL_dx != NULL: lambda = K^-1 dL/dx is the MAP trajectory of the same
+ *     problem with b = 0, the measurement information vectors replaced by
+ *     dL/dx_{k+1} and the prior term by dL/dx_0 (same scans as solve);
+ *     dL/dtheta = -d_theta [lambda^T grad_x M(x*, theta)] at fixed x*, lambda.
+ *   dL_dx == NULL: L = M(x*(theta), theta), the MAP cost itself (Eq. 2,
+ *     constants omitted; flags & MAP_GRAD_LOGDET adds the Gaussian
+ *     log-normalisers 1/2 sum log det(2 pi C_k) + 1/2 sum log det(2 pi R/dt));
+ *     dL/dtheta = d_theta M at x* (envelope theorem).
+ *   y, x      device arrays of the solve (x = its result), dL_dx device (T+1) x nx.
  *   dL_dtheta host, nx*nx + 2 values (synchronises the stream).
- * Linear models, Euler discretisation and invertible Q only (else
- * MAP_ERR_UNSUPPORTED).
+ * Linear models with Euler elements and invertible Q only (else
+ * MAP_ERR_UNSUPPORTED).  No per-step state of the forward solve is kept: the
+ * adjoint re-runs the blocked scan, whose per-tile prefixes (one per 2048
+ * steps) are its only stored checkpoints.
  */
-map_status map_smoother_grad(map_smoother* h, const void* y, const void* dL_dx,
-                             double* dL_dtheta, void* stream);
+#define MAP_GRAD_LOGDET 1
+map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, const void* dL_dx,
+                             int flags, double* dL_dtheta, void* stream);
+
+/*
+ * Set theta = (F, log q, log r) of the handle (F NULL keeps F) and redo the
+ * device set-up (discretisation); synchronises the device.  For training loops
+ * that differentiate through the solve.
+ */
+map_status map_smoother_update(map_smoother* h, const double* F, double log_q, double log_r);
 
 /*
  * Counters of the device-side precision policy since create or the last

@@ -46,7 +46,8 @@ EXPORTS = {
     "map_smoother_solve_sequential": (_I, [_VP, _VP, _VP, _VP]),
     "map_smoother_solve_host": (_I, [_VP, _VP, _VP, _VP]),
     "map_smoother_solve_noalloc": (_I, [ctypes.POINTER(map_problem_desc), _VP, _VP, _VP]),
-    "map_smoother_grad": (_I, [_VP, _VP, _VP, _D, _VP]),
+    "map_smoother_grad": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP]),
+    "map_smoother_update": (_I, [_VP, _D, ctypes.c_double, ctypes.c_double]),
     "map_smoother_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_ulonglong), _I, _VP]),
     "map_smoother_profile": (_I, [_VP, _I]),
     "map_smoother_phase_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(_I)]),
@@ -127,10 +128,18 @@ def map_smoother_solve_host(h, y_host_ptr, x_host_ptr, stream=None):
     _check(load().map_smoother_solve_host(h, y_host_ptr, x_host_ptr, stream), h)
 
 
-def map_smoother_grad(h, y_ptr, dldx_ptr, n_theta, stream=None):
+MAP_GRAD_LOGDET = 1
+
+
+def map_smoother_grad(h, y_ptr, x_ptr, dldx_ptr, n_theta, flags=0, stream=None):
     out = (ctypes.c_double * n_theta)()
-    _check(load().map_smoother_grad(h, y_ptr, dldx_ptr, out, stream), h)
+    _check(load().map_smoother_grad(h, y_ptr, x_ptr, dldx_ptr, int(flags), out, stream), h)
     return np.array(out[:], dtype=np.float64)
+
+
+def map_smoother_update(h, F=None, log_q=0.0, log_r=0.0):
+    Fp = None if F is None else np.ascontiguousarray(np.asarray(F, dtype=np.float64))
+    _check(load().map_smoother_update(h, _ptr(Fp), float(log_q), float(log_r)), h)
 
 
 def map_smoother_stats(h, reset=False, stream=None):

@@ -80,9 +80,50 @@ void free_handle(map_smoother* h)
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_xtmp) cudaFree(h->d_xtmp);
     if (h->d_cost) cudaFree(h->d_cost);
+    if (h->d_lam) cudaFree(h->d_lam);
+    if (h->d_grad) cudaFree(h->d_grad);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;
+}
+
+// Model set-up on the device (FP64) for the current parameters: the noise
+// scales of the gradient parameters multiply W and R.
+map_status run_setup(map_smoother* h)
+{
+    const int n = h->N, m = h->M, nw = h->NW;
+    DevBuf in, out;
+    std::vector<double> W = h->W, R = h->R;
+    for (double& w : W) w *= std::exp(h->logq);
+    for (double& r : R) r *= std::exp(h->logr);
+    std::vector<double> host;
+    auto push = [&](const std::vector<double>& v) { host.insert(host.end(), v.begin(), v.end()); };
+    push(h->F); push(h->c); push(h->L); push(W); push(h->H); push(h->r); push(R); push(h->m0);
+    push(h->P0);
+    const size_t nin = host.size();
+    cudaError_t e;
+    if ((e = cudaMalloc(&in.p, nin * sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+    if ((e = cudaMalloc(&out.p, sizeof(SetupOut))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
+    if ((e = cudaMemcpy(in.p, host.data(), nin * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMemcpy");
+    const double* b = static_cast<const double*>(in.p);
+    SetupIn si{};
+    si.nx = n; si.ny = m; si.nw = nw; si.mode = h->disc; si.dt = h->dt;
+    size_t o = 0;
+    si.F = b + o; o += (size_t)n * n;
+    si.c = b + o; o += n;
+    si.L = b + o; o += (size_t)n * nw;
+    si.W = b + o; o += (size_t)nw * nw;
+    si.H = b + o; o += (size_t)m * n;
+    si.r = b + o; o += m;
+    si.R = b + o; o += (size_t)m * m;
+    si.m0 = b + o; o += n;
+    si.P0 = b + o;
+    if ((e = launch_setup(si, static_cast<SetupOut*>(out.p), 0)) != cudaSuccess)
+        return cuda_fail(*h, e, "set-up kernel launch");
+    if ((e = cudaMemcpy(&h->consts, out.p, sizeof(SetupOut), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(*h, e, "set-up kernel");
+    return MAP_OK;
 }
 
 map_status create_impl(map_smoother* h, const map_problem_desc* d)
@@ -148,38 +189,7 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return cuda_fail(*h, e, "cudaGetDevice");
 
-    // model set-up on the device (FP64)
-    {
-        DevBuf in, out;
-        const size_t nin = (size_t)n * n + n + (size_t)n * nw + (size_t)nw * nw + (size_t)m * n + m +
-                           (size_t)m * m + n + (size_t)n * n;
-        std::vector<double> host;
-        host.reserve(nin);
-        auto push = [&](const std::vector<double>& v) { host.insert(host.end(), v.begin(), v.end()); };
-        push(h->F); push(h->c); push(h->L); push(h->W); push(h->H); push(h->r); push(h->R); push(h->m0);
-        push(h->P0);
-        if ((e = cudaMalloc(&in.p, nin * sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
-        if ((e = cudaMalloc(&out.p, sizeof(SetupOut))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
-        if ((e = cudaMemcpy(in.p, host.data(), nin * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
-            return cuda_fail(*h, e, "cudaMemcpy");
-        const double* b = static_cast<const double*>(in.p);
-        SetupIn si{};
-        si.nx = n; si.ny = m; si.nw = nw; si.mode = disc; si.dt = h->dt;
-        size_t o = 0;
-        si.F = b + o; o += (size_t)n * n;
-        si.c = b + o; o += n;
-        si.L = b + o; o += (size_t)n * nw;
-        si.W = b + o; o += (size_t)nw * nw;
-        si.H = b + o; o += (size_t)m * n;
-        si.r = b + o; o += m;
-        si.R = b + o; o += (size_t)m * m;
-        si.m0 = b + o; o += n;
-        si.P0 = b + o;
-        if ((e = launch_setup(si, static_cast<SetupOut*>(out.p), 0)) != cudaSuccess)
-            return cuda_fail(*h, e, "set-up kernel launch");
-        if ((e = cudaMemcpy(&h->consts, out.p, sizeof(SetupOut), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_fail(*h, e, "set-up kernel");
-    }
+    if (map_status st = run_setup(h); st != MAP_OK) return st;
     if (h->consts.flags & SETUP_SINGULAR_R) return fail(*h, MAP_ERR_SINGULAR, "R is singular");
     if (h->consts.flags & SETUP_SINGULAR_P0) return fail(*h, MAP_ERR_SINGULAR, "P0 is singular");
     if (h->consts.flags & SETUP_SINGULAR_A) return fail(*h, MAP_ERR_SINGULAR, "the interval map A is singular");
@@ -209,6 +219,11 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     if ((e = cudaMalloc(&h->d_cost, sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
     if (h->model != MAP_MODEL_LINEAR) {
         if ((e = cudaMalloc(&h->d_xtmp, (size_t)(h->T + 1) * n * es)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+    } else {
+        if ((e = cudaMalloc(&h->d_lam, (size_t)(h->T + 1) * n * es)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+        if ((e = cudaMalloc(&h->d_grad, sizeof(double) * (n * n + 2))) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(*h, e, "create");
@@ -302,12 +317,35 @@ map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_
     return MAP_OK;
 }
 
-map_status map_smoother_grad(map_smoother* h, const void* y, const void* dL_dx, double* dL_dtheta,
-                             void* stream)
+map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, const void* dL_dx, int flags,
+                             double* dL_dtheta, void* stream)
 {
-    (void)y; (void)dL_dx; (void)dL_dtheta; (void)stream;
     if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
-    return fail(*h, MAP_ERR_UNSUPPORTED, "gradient is not built in this version");
+    if (!y || !x || !dL_dtheta) return fail(*h, MAP_ERR_INVALID_ARG, "y, x and dL_dtheta are required");
+    if (!aligned16(y) || !aligned16(x) || (dL_dx && !aligned16(dL_dx)))
+        return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+    if (h->model != MAP_MODEL_LINEAR || h->disc != MAP_EULER)
+        return fail(*h, MAP_ERR_UNSUPPORTED, "gradients need a linear model with Euler elements");
+    if (h->consts.flags & (SETUP_SINGULAR_C | SETUP_SINGULAR_Q))
+        return fail(*h, MAP_ERR_UNSUPPORTED, "gradients need an invertible process noise Q");
+    const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
+    return ops->grad(*h, y, x, dL_dx, flags, dL_dtheta, static_cast<cudaStream_t>(stream));
+}
+
+map_status map_smoother_update(map_smoother* h, const double* F, double log_q, double log_r)
+{
+    if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
+    if (!std::isfinite(log_q) || !std::isfinite(log_r))
+        return fail(*h, MAP_ERR_INVALID_ARG, "log_q and log_r must be finite");
+    if (F) std::memcpy(h->F.data(), F, sizeof(double) * h->N * h->N);
+    h->logq = log_q;
+    h->logr = log_r;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(*h, e, "cudaDeviceSynchronize");
+    if (map_status st = run_setup(h); st != MAP_OK) return st;
+    if (h->consts.flags & SETUP_SINGULAR_R) return fail(*h, MAP_ERR_SINGULAR, "R is singular");
+    if (h->consts.flags & SETUP_SINGULAR_A) return fail(*h, MAP_ERR_SINGULAR, "the interval map A is singular");
+    return MAP_OK;
 }
 
 map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int reset, void* stream)

@@ -29,6 +29,9 @@ struct map_smoother {
     void* d_x = nullptr;
     void* d_xtmp = nullptr;            // Gauss-Newton ping-pong trajectory
     double* d_cost = nullptr;
+    void* d_lam = nullptr;             // adjoint trajectory (linear models)
+    double* d_grad = nullptr;          // gradient accumulators
+    double logq = 0.0, logr = 0.0;     // noise scales of the gradient parameters
     // per-phase timing (map_smoother_profile)
     bool profile = false;
     cudaEvent_t ev[8] = {};
@@ -46,6 +49,8 @@ struct Ops {
     map_status (*solve)(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st);
     map_status (*cost)(map_smoother& h, const void* y, const void* x, double* d_cost, cudaStream_t st);
     map_status (*solve_sequential)(map_smoother& h, const void* y, void* x_out, cudaStream_t st);
+    map_status (*grad)(map_smoother& h, const void* y, const void* x, const void* dLdx, int flags,
+                       double* dtheta, cudaStream_t st);
 };
 
 const Ops* find_ops(int model, int N, int M, int prec);

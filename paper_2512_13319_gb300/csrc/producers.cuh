@@ -101,6 +101,55 @@ struct LtiProducer {
 };
 
 // ---------------------------------------------------------------------------
+// Adjoint of the MAP solve.  x* solves K x = g with K the (symmetric)
+// Hessian of the discrete cost, so lambda = K^-1 d (d = dL/dx*) is the MAP
+// trajectory of the same problem with b = 0, the measurement information
+// vectors replaced by d_{k+1} (element k) and the prior term by d_0:
+// same A, C, J; eta_k = d_{k+1}; terminal value function (d_0, P0^-1).
+// ---------------------------------------------------------------------------
+template <int N, typename S>
+struct AdjParams {
+    static constexpr int NS = Sym<N>::SZ;
+    S A[N * N];
+    S C[NS];
+    S J[NS];
+    S S0[NS];
+};
+
+template <int N, typename S>
+struct AdjProducer {
+    static constexpr int W = N;
+    const S* d;                      // (T+1, N): dL/dx*
+    long T;
+    AdjParams<N, S> p;
+
+    __device__ __forceinline__ void load1(long k, S* row) const
+    {
+#pragma unroll
+        for (int j = 0; j < W; ++j) row[j] = k < T ? __ldg(d + (k + 1) * N + j) : S(0);
+    }
+
+    __device__ __forceinline__ void terminal(Red<N, S>& r) const
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.v[i] = __ldg(d + i);
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) r.P[i] = p.S0[i];
+    }
+
+    __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
+    {
+        if (k >= T) { set_identity(e); return; }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) e.A[i] = p.A[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) { e.b[i] = S(0); e.eta[i] = row[i]; }
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) { e.C[i] = p.C[i]; e.J[i] = p.J[i]; }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Backward information filter of the two-filter smoother (Section 3.5 second
 // method, Section 4.3 Eq. 43): the same combine applied to the interval
 // elements written the other way round.  The flipped element of interval k

@@ -111,7 +111,8 @@ size_t rts_workspace(const map_smoother& h)
 
 // Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
 template <int N, typename S, class Prod>
-map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st)
+map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st,
+                   bool dev_prior = false)
 {
     using R = Red<N, S>;
     constexpr int K = KSTEP;
@@ -156,11 +157,13 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
+    // dev_prior: the prior comes from the producer's terminal() (device data)
+    S* term = dev_prior ? reinterpret_cast<S*>(h.ws + L.term) : nullptr;
     launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_reduce, st, false, prod, thr_agg, tile_agg,
-           (S*)nullptr, ctx);
+           term, ctx);
     mark();
     launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
-           (const S*)nullptr, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
+           (const S*)term, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
     mark();
     launch(k_filter_down<N, S, Prod, K>, nt, B, sh_down, st, pdl, prod, (const S*)thr_agg,
            (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx);
@@ -392,11 +395,182 @@ map_status cost_linear(map_smoother& h, const void* y, const void* x, double* d_
     return MAP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// gradient of a loss of the MAP trajectory w.r.t. theta = (F, log q, log r)
+// (Euler elements: A = I - dt F, C = dt q Q0, R = r R0)
+//  - MAP cost (envelope): d/dF = sum dt (C^-1 r_k) x_{k+1}^T + 1/2 dt T I,
+//    d/dlogq = -1/2 sum r^T C^-1 r, d/dlogr = -1/2 sum dt e^T R^-1 e
+//  - other losses: -d_theta [lambda^T grad_x M] at fixed x*, lambda:
+//    d/dF = -sum dt ((C^-1 r) lambda_{k+1}^T + (C^-1 s) x_{k+1}^T),
+//    d/dlogq = sum s^T C^-1 r, d/dlogr = sum dt (H lambda_{k+1})^T R^-1 e
+// with r_k = x_k - A x_{k+1} - b, s_k = lambda_k - A lambda_{k+1},
+// e_k = H x_{k+1} + r - y_{k+1}.  Per-step terms in S, FP64 accumulation.
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(256)
+k_grad_contract(const S* __restrict__ y, const S* __restrict__ x, const S* __restrict__ lam, long T,
+                LinCostParams<N, M> p, double* __restrict__ out)
+{
+    constexpr int NG = N * N + 2;
+    double acc[NG];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) acc[i] = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < T; k += (long)gridDim.x * blockDim.x) {
+        S xk[N], x1[N], r[N], Cr[N], e[M], Re[M];
+#pragma unroll
+        for (int i = 0; i < N; ++i) { xk[i] = x[k * N + i]; x1[i] = x[(k + 1) * N + i]; }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = xk[i] - S(p.b[i]);
+#pragma unroll
+            for (int j = 0; j < N; ++j) s = fma(-S(p.A[i * N + j]), x1[j], s);
+            r[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = S(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) s = fma(S(p.Cinv[i * N + j]), r[j], s);
+            Cr[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            S s = S(p.r[i]) - y[k * M + i];
+#pragma unroll
+            for (int j = 0; j < N; ++j) s = fma(S(p.H[i * N + j]), x1[j], s);
+            e[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            S s = S(0);
+#pragma unroll
+            for (int j = 0; j < M; ++j) s = fma(S(p.Rinv[i * M + j]), e[j], s);
+            Re[i] = s;
+        }
+        if (lam) {
+            S lk[N], l1[N], sv[N], Cs[N], Hl[M];
+#pragma unroll
+            for (int i = 0; i < N; ++i) { lk[i] = lam[k * N + i]; l1[i] = lam[(k + 1) * N + i]; }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                S s = lk[i];
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fma(-S(p.A[i * N + j]), l1[j], s);
+                sv[i] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                S s = S(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fma(S(p.Cinv[i * N + j]), sv[j], s);
+                Cs[i] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                S s = S(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fma(S(p.H[i * N + j]), l1[j], s);
+                Hl[i] = s;
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int b = 0; b < N; ++b)
+                    acc[a * N + b] -= p.dt * double(Cr[a] * l1[b] + Cs[a] * x1[b]);
+            S q = S(0), w = S(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) q = fma(sv[i], Cr[i], q);
+#pragma unroll
+            for (int i = 0; i < M; ++i) w = fma(Hl[i], Re[i], w);
+            acc[N * N] += double(q);
+            acc[N * N + 1] += p.dt * double(w);
+        } else {
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int b = 0; b < N; ++b) acc[a * N + b] += p.dt * double(Cr[a] * x1[b]);
+            S q = S(0), w = S(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) q = fma(r[i], Cr[i], q);
+#pragma unroll
+            for (int i = 0; i < M; ++i) w = fma(e[i], Re[i], w);
+            acc[N * N] -= 0.5 * double(q);
+            acc[N * N + 1] -= 0.5 * p.dt * double(w);
+        }
+    }
+    __shared__ double part[NG][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NG) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += part[threadIdx.x][w];
+        atomicAdd(out + threadIdx.x, v);
+    }
+}
+
+template <int N, int M, typename S>
+map_status grad_linear(map_smoother& h, const void* y, const void* x, const void* dLdx, int flags,
+                       double* dtheta, cudaStream_t st)
+{
+    LinCostParams<N, M> p;
+    const SetupOut& c = h.consts;
+    for (int i = 0; i < N * N; ++i) { p.A[i] = c.A[i]; p.S0[i] = c.S0[i]; p.Cinv[i] = c.Cinv[i]; }
+    for (int i = 0; i < N; ++i) { p.b[i] = c.b[i]; p.m0[i] = h.m0[i]; }
+    for (int i = 0; i < M * N; ++i) p.H[i] = h.H[i];
+    for (int i = 0; i < M; ++i) p.r[i] = h.r[i];
+    for (int i = 0; i < M * M; ++i) p.Rinv[i] = c.Rinv[i];
+    p.dt = h.dt;
+    p.trF = 0.0;
+    S* lam = nullptr;
+    if (dLdx) {
+        AdjProducer<N, S> prod;
+        prod.d = static_cast<const S*>(dLdx);
+        prod.T = h.T;
+        for (int i = 0; i < N * N; ++i) prod.p.A[i] = S(c.A[i]);
+        for (int i = 0; i < N; ++i)
+            for (int j = i; j < N; ++j) {
+                prod.p.C[Sym<N>::at(i, j)] = S(c.C[i * N + j]);
+                prod.p.J[Sym<N>::at(i, j)] = S(c.J[i * N + j]);
+                prod.p.S0[Sym<N>::at(i, j)] = S(c.S0[i * N + j]);
+            }
+        lam = static_cast<S*>(h.d_lam);
+        map_status s = run_rts<N, S>(h, prod, lam, nullptr, st, true);
+        if (s != MAP_OK) return s;
+    }
+    constexpr int NG = N * N + 2;
+    cudaError_t e = cudaMemsetAsync(h.d_grad, 0, sizeof(double) * NG, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    const int blocks = (int)std::max<long>(1, std::min<long>(2048, (h.T + 255) / 256));
+    k_grad_contract<N, M, S><<<blocks, 256, 0, st>>>(static_cast<const S*>(y), static_cast<const S*>(x),
+                                                     lam, h.T, p, h.d_grad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "gradient kernel launch");
+    double g[NG];
+    if ((e = cudaMemcpyAsync(g, h.d_grad, sizeof(double) * NG, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(h, e, "gradient read-back");
+    if (!dLdx) {
+        for (int a = 0; a < N; ++a) g[a * N + a] += 0.5 * h.dt * double(h.T);   // divergence tr F
+        if (flags & 1) {                                                        // log-normalisers
+            g[N * N] += 0.5 * N * double(h.T);
+            g[N * N + 1] += 0.5 * M * double(h.T);
+        }
+    }
+    for (int i = 0; i < NG; ++i) dtheta[i] = g[i];
+    return MAP_OK;
+}
+
 template <int N, int M, typename S>
 const Ops* linear_ops()
 {
     static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
-                         &solve_linear_sequential<N, M, S>};
+                         &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>};
     return &ops;
 }
 
@@ -473,7 +647,7 @@ template <typename S>
 const Ops* coord_turn_ops()
 {
     static const Ops ops{&rts_workspace<5, S>, &solve_nonlinear<CtModel<S>, S>, nullptr,
-                         &solve_nonlinear_sequential<CtModel<S>, S>};
+                         &solve_nonlinear_sequential<CtModel<S>, S>, nullptr};
     return &ops;
 }
 
@@ -481,7 +655,7 @@ template <int N, int M, typename S>
 const Ops* cubic_ops()
 {
     static const Ops ops{&rts_workspace<N, S>, &solve_nonlinear<CubicModel<N, M, S>, S>, nullptr,
-                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>};
+                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>, nullptr};
     return &ops;
 }
 

@@ -77,6 +77,25 @@ class MapSmoother:
         B.map_smoother_solve_host(self._h, y_host.data_ptr(), x_host.data_ptr(), self._stream(stream))
         return x_host
 
+    def grad(self, y, x, dLdx=None, logdet=False, stream=None):
+        """dL/d(F, log q, log r) (numpy, nx*nx + 2) at the handle's parameters.
+
+        ``dLdx=None`` differentiates the MAP cost itself; otherwise the loss
+        whose gradient with respect to the trajectory ``x`` is ``dLdx``.
+        """
+        self._check_dev(y, (self.T, self.ny), "y")
+        self._check_dev(x, (self.T + 1, self.nx), "x")
+        if dLdx is not None:
+            self._check_dev(dLdx, (self.T + 1, self.nx), "dLdx")
+        return B.map_smoother_grad(self._h, y.data_ptr(), x.data_ptr(),
+                                   dLdx.data_ptr() if dLdx is not None else None,
+                                   self.nx * self.nx + 2, B.MAP_GRAD_LOGDET if logdet else 0,
+                                   self._stream(stream))
+
+    def update(self, F=None, log_q=0.0, log_r=0.0):
+        """Set theta = (F, log q, log r) (Q = e^log_q L W L^T, R = e^log_r R)."""
+        B.map_smoother_update(self._h, F, log_q, log_r)
+
     def profile(self, enable=True):
         """Record per-phase CUDA events in every solve (see phase_times)."""
         B.map_smoother_profile(self._h, enable)

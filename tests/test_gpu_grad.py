@@ -1,0 +1,146 @@
+"""Gradient of the MAP solve (hand-written adjoint in the CUDA library) against
+the FP64 oracle's implicit-function gradient and central finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_13319_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+GTOL = {"fp64": 1e-8, "fp32": 2e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_13319_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def problem(T, dt=1e-3, seed=51):
+    model = synth.ou_model(4, 2, seed=seed)
+    x_true, y = synth.simulate(model, T, dt, seed=seed + 1, substeps=1)
+    return model, x_true, y
+
+
+def scaled(model, logq, logr):
+    m = synth.Model(**{**model.__dict__})
+    m.W = model.W * math.exp(logq)
+    m.R = model.R * math.exp(logr)
+    return m
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("loss", ["map_cost", "trajectory"])
+def test_gradient_matches_oracle(prec, loss):
+    from paper_2512_13319_gb300 import MapSmoother
+    T, dt = 20_000, 1e-3
+    model, x_true, y = problem(T, dt)
+    logq, logr = 0.3, -0.2
+    sm = MapSmoother(model, T, dt, precision=prec)
+    sm.update(model.F, logq, logr)
+    yt = torch.tensor(y, dtype=DT[prec], device="cuda")
+    x = sm.solve(yt)
+    if loss == "map_cost":
+        g = sm.grad(yt, x)
+        ref, _ = oracle.grad_lti(model, y, dt, logq, logr)
+    else:
+        xt = torch.tensor(x_true, dtype=DT[prec], device="cuda")
+        g = sm.grad(yt, x, x - xt)
+        x_ref = oracle.smooth_lti(scaled(model, logq, logr), y, dt)
+        ref, _ = oracle.grad_lti(model, y, dt, logq, logr, dLdx=x_ref - x_true)
+    sm.close()
+    assert rel(g, ref) <= GTOL[prec]
+
+
+def test_log_normaliser_flag_matches_oracle():
+    from paper_2512_13319_gb300 import MapSmoother
+    T, dt = 3000, 1e-3
+    model, _, y = problem(T, dt, seed=61)
+    sm = MapSmoother(model, T, dt, precision="fp64")
+    yt = torch.tensor(y, device="cuda")
+    x = sm.solve(yt)
+    g = sm.grad(yt, x, logdet=True)
+    ref, _ = oracle.grad_lti(model, y, dt, 0.0, 0.0, logdet=True)
+    assert rel(g, ref) <= 1e-8
+
+
+def test_gradient_against_central_differences_on_the_gpu():
+    """FP64 GPU solves at theta +- h (h = 1e-6) against the adjoint gradient."""
+    from paper_2512_13319_gb300 import MapSmoother
+    T, dt = 2000, 1e-3
+    model, x_true, y = problem(T, dt, seed=71)
+    sm = MapSmoother(model, T, dt, precision="fp64")
+    yt = torch.tensor(y, device="cuda")
+    xt = torch.tensor(x_true, device="cuda")
+    F0, lq, lr = model.F.copy(), 0.1, -0.1
+
+    def L(F, q, r):
+        sm.update(F, q, r)
+        x = sm.solve(yt)
+        return 0.5 * float(((x - xt) ** 2).sum())
+
+    sm.update(F0, lq, lr)
+    x = sm.solve(yt)
+    g = sm.grad(yt, x, x - xt)
+    h = 1e-6
+    fd = np.zeros(18)
+    for a, b in [(0, 0), (1, 2), (3, 1), (2, 3)]:
+        Fp = F0.copy(); Fp[a, b] += h
+        Fm = F0.copy(); Fm[a, b] -= h
+        fd[a * 4 + b] = (L(Fp, lq, lr) - L(Fm, lq, lr)) / (2 * h)
+    fd[16] = (L(F0, lq + h, lr) - L(F0, lq - h, lr)) / (2 * h)
+    fd[17] = (L(F0, lq, lr + h) - L(F0, lq, lr - h)) / (2 * h)
+    idx = [0, 6, 13, 11, 16, 17]
+    assert rel(g[idx], fd[idx]) <= 1e-6
+    sm.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_gradient_workload_T_2_18(prec):
+    """OU nx=4 MAP-cost gradient at T = 2^18 against the FP64 oracle."""
+    from paper_2512_13319_gb300 import MapSmoother
+    T, dt = 2 ** 18, 1e-3
+    model, _, y = problem(T, dt, seed=1004)
+    sm = MapSmoother(model, T, dt, precision=prec)
+    yt = torch.tensor(y, dtype=DT[prec], device="cuda")
+    x = sm.solve(yt)
+    g = sm.grad(yt, x)
+    ref, _ = oracle.grad_lti(model, y, dt, 0.0, 0.0)
+    sm.close()
+    assert rel(g, ref) <= GTOL[prec]
+
+
+def test_autograd_function_matches_c_abi_gradient():
+    from paper_2512_13319_gb300 import MapSmoother
+    from paper_2512_13319_gb300.autograd import map_cost, map_solve
+    T, dt = 4000, 1e-3
+    model, x_true, y = problem(T, dt, seed=81)
+    sm = MapSmoother(model, T, dt, precision="fp64")
+    yt = torch.tensor(y, device="cuda")
+    xt = torch.tensor(x_true, device="cuda")
+    F = torch.tensor(model.F, requires_grad=True)
+    lq = torch.tensor(0.2, dtype=torch.float64, requires_grad=True)
+    lr = torch.tensor(-0.3, dtype=torch.float64, requires_grad=True)
+    x = map_solve(sm, yt, F, lq, lr)
+    loss = 0.5 * ((x - xt) ** 2).sum()
+    loss.backward()
+    ref, _ = oracle.grad_lti(model, y, dt, 0.2, -0.3, dLdx=x.detach().cpu().numpy() - x_true)
+    got = np.concatenate([F.grad.numpy().ravel(), [lq.grad.item(), lr.grad.item()]])
+    assert rel(got, ref) <= 1e-8
+    F.grad = None
+    c = map_cost(sm, yt, F, lq, lr)
+    c.backward()
+    ref_c, _ = oracle.grad_lti(model, y, dt, 0.2, -0.3)
+    assert rel(F.grad.numpy().ravel(), ref_c[:16]) <= 1e-8
+    sm.close()
