@@ -87,7 +87,7 @@ typedef struct {
     int gn_iters;               /* nonlinear models: number of linearisation iterations, >= 1 */
     double cond_max;            /* FP32: recompute a combine in FP64 when the infinity-norm
                                    condition estimate of (I + C J) exceeds this (0 = 1e6) */
-    int tile_threads;           /* threads per tile CTA, power of two in [32, 256] (0 = tuned) */
+    int tile_threads;           /* threads per tile CTA: 32, 64 or 128 (0 = 128, reduced to fit) */
 } map_problem_desc;
 
 /*
@@ -213,6 +213,37 @@ map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int
  */
 map_status map_smoother_solve_noalloc(const map_problem_desc* desc, const void* y, void* x_out,
                                       void* stream);
+
+/*
+ * Batches of independent trajectories (row a9 of the build: thousands of
+ * trajectories of uneven length and state dimension in one launch).
+ * models[m] describes a linear model (desc.T is ignored, smoother MAP_RTS);
+ * trajectory j has lengths[j] >= 1 intervals of model model_of[j].
+ * All trajectories of one model are solved as ONE scan: they are concatenated
+ * in input order with the model's prior element (Eq. 31 a_T) inserted before
+ * every trajectory but the first; on the left of the combine (Eq. 36) that
+ * element keeps only its own value function, so it restarts the filter, and
+ * its closed-loop map is the constant map to the argmin of the previous
+ * trajectory's final value function (Eq. 18).  Per model m:
+ *   y[m]  device, y_rows x ny: trajectory j's lengths[j] observation rows in
+ *         order, with one unused row between consecutive trajectories;
+ *   x[m]  device, x_rows x nx: trajectory j's lengths[j] + 1 states in order.
+ * map_batch_rows gives y_rows and x_rows (0 for models without trajectories).
+ * map_batch_solve: on the first call, (steps per thread, threads per tile) of
+ * every model are autotuned by timing the candidates on these arrays (eager
+ * launches, synchronising `stream`); the per-model pipelines are then captured
+ * into one CUDA graph with concurrent branches, and every call with the same
+ * arrays is one graph launch on `stream` (asynchronous).  New arrays re-capture.
+ */
+typedef struct map_batch map_batch;
+map_status map_batch_create(map_batch** out, const map_problem_desc* models, int nmodels,
+                            const int64_t* lengths, const int* model_of, int ntraj);
+map_status map_batch_rows(const map_batch* b, int model, int64_t* y_rows, int64_t* x_rows);
+map_status map_batch_solve(map_batch* b, const void* const* y, void* const* x, void* stream);
+/* the autotuned (steps per thread, threads per tile) of model m (0, 0 before the first solve) */
+map_status map_batch_tuning(const map_batch* b, int model, int* K, int* B);
+const char* map_batch_last_error(const map_batch* b);
+void map_batch_destroy(map_batch* b);
 
 /* Free the handle and its workspace (NULL is ignored). */
 void map_smoother_destroy(map_smoother* h);

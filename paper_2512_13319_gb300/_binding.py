@@ -55,6 +55,13 @@ EXPORTS = {
     "map_smoother_last_error": (_CH, [_VP]),
     "map_smoother_supported": (_I, [_I, _I, _I, _I]),
     "map_smoother_version": (_CH, []),
+    "map_batch_create": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(map_problem_desc), _I,
+                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I), _I]),
+    "map_batch_rows": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "map_batch_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    "map_batch_tuning": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "map_batch_last_error": (_CH, [_VP]),
+    "map_batch_destroy": (None, [_VP]),
 }
 
 _lib = None

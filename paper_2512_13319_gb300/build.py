@@ -35,7 +35,8 @@ def nvcc() -> str:
 
 def units():
     """(object name, source, extra defines) of every translation unit."""
-    out = [("capi", "capi.cu", []), ("discretise", "discretise.cu", []), ("noalloc", "noalloc.cu", [])]
+    out = [("capi", "capi.cu", []), ("discretise", "discretise.cu", []), ("noalloc", "noalloc.cu", []),
+           ("batch", "batch.cu", [])]
     for prec, typ in (("f32", "float"), ("f64", "double")):
         for n, m in LINEAR_SHAPES:
             out.append((f"lin_{n}_{m}_{prec}", "inst_linear.cu",

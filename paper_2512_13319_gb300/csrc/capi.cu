@@ -201,8 +201,8 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     const size_t NE = 3 * n * P + 2 * P, NSCR = 3 * n * P + P, NL = n <= 2 ? 2 : n <= 4 ? 4 : 8;
     auto tree_bytes = [&](int b) { return es * (2 * (size_t)b * NE + (size_t)b / NL * NSCR); };
     int B = d->tile_threads > 0 ? d->tile_threads : 128;
-    if (B < 32 || B > 256 || (B & (B - 1)))
-        return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be a power of two in [32, 256]");
+    if (B < 32 || B > 128 || (B & (B - 1)))
+        return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be 32, 64 or 128");
     while (B > 32 && tree_bytes(B) > (d->tile_threads > 0 ? 200 : 100) * 1024) B /= 2;
     h->B = B;
     h->K = 16;
@@ -233,6 +233,41 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
 }  // namespace
 
 void mapk::set_handle_free_error(const std::string& msg) { g_create_error = msg; }
+
+bool mapk::geometry_fits(const map_smoother& h, int B)
+{
+    const size_t es = elem_bytes(h.prec);
+    const size_t n = h.N, V = 16 / es, P = (n + V - 1) / V * V;
+    const size_t NE = 3 * n * P + 2 * P, NSCR = 3 * n * P + P, NL = n <= 2 ? 2 : n <= 4 ? 4 : 8;
+    return es * (2 * (size_t)B * NE + (size_t)B / NL * NSCR) <= 200 * 1024;
+}
+
+void mapk::set_geometry(map_smoother& h, int K, int B)
+{
+    h.K = K;
+    h.B = B;
+    const long L = (long)B * K;
+    h.nt = (int)((h.T + L - 1) / L);
+    h.Tpad = (long)h.nt * L;
+}
+
+map_status mapk::ensure_workspace(map_smoother& h, size_t bytes)
+{
+    if (bytes <= h.ws_bytes) return MAP_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && h.ws) e = cudaFree(h.ws);
+    h.ws = nullptr;
+    h.ws_bytes = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&h.ws, bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace");
+    h.ws_bytes = bytes;
+    return MAP_OK;
+}
+
+map_status mapk::create_handle(map_smoother** out, const map_problem_desc* desc)
+{
+    return map_smoother_create(out, desc);
+}
 
 extern "C" {
 

@@ -51,7 +51,15 @@ struct Ops {
     map_status (*solve_sequential)(map_smoother& h, const void* y, void* x_out, cudaStream_t st);
     map_status (*grad)(map_smoother& h, const void* y, const void* x, const void* dLdx, int flags,
                        double* dtheta, cudaStream_t st);
+    map_status (*solve_seg)(map_smoother& h, const void* y, const unsigned char* reset, void* x_out,
+                            cudaStream_t st);
 };
+
+// geometry (steps per thread K, threads per tile B) and its workspace bytes
+void set_geometry(map_smoother& h, int K, int B);
+bool geometry_fits(const map_smoother& h, int B);
+map_status ensure_workspace(map_smoother& h, size_t bytes);
+map_status create_handle(map_smoother** out, const map_problem_desc* desc);
 
 const Ops* find_ops(int model, int N, int M, int prec);
 

@@ -56,6 +56,8 @@ struct LtiParams {
 template <int N, int M, typename S>
 struct LtiProducer {
     static constexpr int W = M;      // scalars read per step
+    static constexpr bool RESETS = false;
+    __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                      // (T, M), row k holds y_{k+1}
     long T;
     LtiParams<N, M, S> p;
@@ -101,6 +103,68 @@ struct LtiProducer {
 };
 
 // ---------------------------------------------------------------------------
+// Many independent trajectories of one linear model in one scan.  Trajectory
+// j > 0 is preceded by the model's prior element a_T = (0, 0, 0, P0^-1 m0,
+// P0^-1) (Eq. 31): on the left of the combine (Eq. 36) an element with
+// A = C = 0 keeps only its own (J, eta), so every prefix that contains it
+// restarts at the prior, and its closed-loop map is the constant map to the
+// argmin of the previous trajectory's last value function (Eq. 18).  Element k
+// reads row k of y; rows at the inserted positions are unused.
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+struct SegLtiProducer {
+    static constexpr int W = M;
+    static constexpr bool RESETS = true;
+    const S* y;                      // (T, M) with an unused row at every reset
+    const unsigned char* reset;      // (T): 1 where a trajectory starts (except the first)
+    long T;
+    LtiParams<N, M, S> p;
+    S S0[Sym<N>::SZ];                // P0^-1
+    S v0[N];                         // P0^-1 m0
+
+    __device__ __forceinline__ bool is_reset(long k) const { return k < T && __ldg(reset + k) != 0; }
+
+    __device__ __forceinline__ void load1(long k, S* row) const
+    {
+#pragma unroll
+        for (int j = 0; j < W; ++j) row[j] = k < T ? __ldg(y + k * W + j) : S(0);
+    }
+
+    __device__ __forceinline__ void terminal(Red<N, S>& r) const
+    {
+#pragma unroll
+        for (int i = 0; i < Red<N, S>::NCOMP; ++i) comp(r, i) = S(0);
+    }
+
+    __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
+    {
+        if (k >= T) { set_identity(e); return; }
+        if (is_reset(k)) {
+#pragma unroll
+            for (int i = 0; i < N * N; ++i) e.A[i] = S(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) { e.b[i] = S(0); e.eta[i] = v0[i]; }
+#pragma unroll
+            for (int i = 0; i < Sym<N>::SZ; ++i) { e.C[i] = S(0); e.J[i] = S0[i]; }
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) e.A[i] = p.A[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) e.b[i] = p.b[i];
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) { e.C[i] = p.C[i]; e.J[i] = p.J[i]; }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = -p.Gr[i];
+#pragma unroll
+            for (int j = 0; j < M; ++j) s = fma(p.G[i * M + j], row[j], s);
+            e.eta[i] = s;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Adjoint of the MAP solve.  x* solves K x = g with K the (symmetric)
 // Hessian of the discrete cost, so lambda = K^-1 d (d = dL/dx*) is the MAP
 // trajectory of the same problem with b = 0, the measurement information
@@ -119,6 +183,8 @@ struct AdjParams {
 template <int N, typename S>
 struct AdjProducer {
     static constexpr int W = N;
+    static constexpr bool RESETS = false;
+    __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* d;                      // (T+1, N): dL/dx*
     long T;
     AdjParams<N, S> p;
@@ -175,6 +241,8 @@ struct FlipParams {
 template <int N, int M, typename S>
 struct RevFlipProducer {
     static constexpr int W = M;
+    static constexpr bool RESETS = false;
+    __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                      // (T, M), row k-1 holds y_k
     long T;
     long Tpad;
@@ -316,6 +384,8 @@ template <class Model, typename S>
 struct NlProducer {
     static constexpr int N = Model::N, M = Model::M;
     static constexpr int W = M + N;   // y_{k+1} then xbar_{k+1}
+    static constexpr bool RESETS = false;
+    __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                       // (T, M)
     const S* xbar;                    // (T+1, N)
     long T;

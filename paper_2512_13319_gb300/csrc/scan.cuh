@@ -450,7 +450,15 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
             Elem<N, S> e;
             prod.make(k, row, e);
             Aff<N, S> a;
-            apply<N, S, true>(e, X, a.F, a.c, ctx);
+            if (Prod::RESETS && prod.is_reset(k)) {
+                // trajectory start: the previous trajectory ends at the argmin of X
+#pragma unroll
+                for (int j = 0; j < N * N; ++j) a.F[j] = S(0);
+                if (!red_argmin<N, S>(X, a.c) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+                apply<N, S, false>(e, X, nullptr, nullptr, ctx);
+            } else {
+                apply<N, S, true>(e, X, a.F, a.c, ctx);
+            }
 #pragma unroll
             for (int c = 0; c < NA; ++c) Eg[wis_idx(gthr, i, c, K, NA)] = comp(a, c);
             // x_{k0} = Phi x_{k+1} + beta:  beta += Phi g,  Phi = Phi E

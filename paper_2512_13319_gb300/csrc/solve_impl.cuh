@@ -110,12 +110,11 @@ size_t rts_workspace(const map_smoother& h)
 }
 
 // Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
-template <int N, typename S, class Prod>
+template <int N, typename S, class Prod, int K = KSTEP>
 map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st,
                    bool dev_prior = false)
 {
     using R = Red<N, S>;
-    constexpr int K = KSTEP;
     const int B = h.B, nt = h.nt;
     const long nthr = (long)nt * B;
     const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
@@ -145,6 +144,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         const size_t big = 200 * 1024;
         e0 = allow_smem(k_filter_reduce<N, S, Prod, K>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S, K>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_affine_tiles<N, S>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S, K>, big);
@@ -301,6 +301,25 @@ map_status solve_linear_sequential(map_smoother& h, const void* y, void* x_out, 
     prod.T = h.T;
     prod.p = lti_params<N, M, S>(h);
     return run_sequential<N, S>(h, prod, static_cast<S*>(x_out), st);
+}
+
+// Many trajectories of one linear model concatenated with reset elements
+// (SegLtiProducer); K (steps per thread) is 8 or 16, chosen at run time.
+template <int N, int M, typename S>
+map_status solve_linear_seg(map_smoother& h, const void* y, const unsigned char* reset, void* x_out,
+                            cudaStream_t st)
+{
+    SegLtiProducer<N, M, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.reset = reset;
+    prod.T = h.T;
+    prod.p = lti_params<N, M, S>(h);
+    for (int i = 0; i < N; ++i) {
+        prod.v0[i] = S(h.consts.v0[i]);
+        for (int j = i; j < N; ++j) prod.S0[Sym<N>::at(i, j)] = S(h.consts.S0[i * N + j]);
+    }
+    if (h.K == 8) return run_rts<N, S, SegLtiProducer<N, M, S>, 8>(h, prod, static_cast<S*>(x_out), nullptr, st);
+    return run_rts<N, S, SegLtiProducer<N, M, S>, 16>(h, prod, static_cast<S*>(x_out), nullptr, st);
 }
 
 // Discrete Onsager-Machlup cost of a trajectory of a linear model:
@@ -570,7 +589,8 @@ template <int N, int M, typename S>
 const Ops* linear_ops()
 {
     static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
-                         &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>};
+                         &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
+                         &solve_linear_seg<N, M, S>};
     return &ops;
 }
 
@@ -647,7 +667,7 @@ template <typename S>
 const Ops* coord_turn_ops()
 {
     static const Ops ops{&rts_workspace<5, S>, &solve_nonlinear<CtModel<S>, S>, nullptr,
-                         &solve_nonlinear_sequential<CtModel<S>, S>, nullptr};
+                         &solve_nonlinear_sequential<CtModel<S>, S>, nullptr, nullptr};
     return &ops;
 }
 
@@ -655,7 +675,7 @@ template <int N, int M, typename S>
 const Ops* cubic_ops()
 {
     static const Ops ops{&rts_workspace<N, S>, &solve_nonlinear<CubicModel<N, M, S>, S>, nullptr,
-                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>, nullptr};
+                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>, nullptr, nullptr};
     return &ops;
 }
 

@@ -313,3 +313,24 @@ def batched_lengths_and_dims(num: int = 4096, lo: int = 256, hi: int = 65536,
     lengths = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=num))).astype(np.int64)
     nxs = rng.choice(np.asarray(dims), size=num)
     return lengths, nxs
+
+
+def batched_workload(num: int = 4096, lo: int = 256, hi: int = 65536, seed: int = 1003,
+                     dt: float = 0.01, q: float = 1.0, r: float = 0.1, lengths=None, dims=None):
+    """Ragged batch of Wiener-velocity trajectories in 1, 2 and 3 dimensions.
+
+    Returns (models [d=1, 2, 3], lengths, model_of, ys) with ys[j] of shape
+    (lengths[j], d_j).  Lengths are log-uniform in [lo, hi] unless given.
+    """
+    if lengths is None:
+        lengths, nxs = batched_lengths_and_dims(num, lo, hi, (2, 4, 6), seed)
+    else:
+        lengths = np.asarray(lengths, dtype=np.int64)
+        nxs = np.asarray(dims) * 2
+    models = [wiener_velocity(d, q=q, r=r) for d in (1, 2, 3)]
+    model_of = (nxs // 2 - 1).astype(np.int32)
+    ys = []
+    for j, (T, mi) in enumerate(zip(lengths, model_of)):
+        _, y = simulate(models[mi], int(T), dt, seed=seed * 100003 + j, substeps=1)
+        ys.append(y)
+    return models, lengths, model_of, ys
