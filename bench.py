@@ -328,11 +328,12 @@ def ours(args):
         ms64 = statistics.median(a.elapsed_time(b) for a, b in evs)
         result["fp64"] = {"value": T / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
         sm64.close()
-        # sequential GPU baseline (one thread, KF + RTS), if built
+        # sequential GPU baseline (one thread, same recursions), if built
         seq = sequential_gpu(model, y, dtype, dev, flush, stream)
         if seq:
             result["sequential_gpu"] = seq
             result["speedup_vs_sequential_gpu"] = value / seq["value"]
+        result["extras"] = extras(dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -348,6 +349,129 @@ def ours(args):
 
 def sm_B(sm):
     return 128
+
+
+def timed(fn, flush, stream, dev, reps=3):
+    """Median device time (ms) of fn() with the L2 flushed before each call."""
+    import torch
+    fn()
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def rel_err(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def extras(dev, flush, stream):
+    """The other workloads of the path, each with its error against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2512_13319_gb300 import MapSmoother, synth
+    out = {}
+
+    def guard(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:          # report, do not lose the main line
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+
+    def ou8():
+        model = synth.ou_model(8, 4, seed=1001)
+        _, y = synth.simulate(model, T_FULL, DT, seed=1011, substeps=1)
+        sm = MapSmoother(model, T_FULL, DT, precision="fp32")
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        x = torch.empty((T_FULL + 1, 8), dtype=torch.float32, device=dev)
+        ms = timed(lambda: sm.solve(yt, x_out=x), flush, stream, dev)
+        err = rel_err(x.cpu().numpy(), oracle.smooth_lti(model, y, DT))
+        sm.close()
+        return {"workload": "OU nx=8 ny=4, T=2^20, dt=1e-3, FP32, RTS", "ms": ms,
+                "value": T_FULL / (ms * 1e-3), "unit": UNIT, "rel_err_vs_oracle": err}
+
+    def two_filter():
+        model, y = model_and_data(1001)
+        sm = MapSmoother(model, T_FULL, DT, precision="fp32", smoother="two_filter")
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        x = torch.empty((T_FULL + 1, 4), dtype=torch.float32, device=dev)
+        ms = timed(lambda: sm.solve(yt, x_out=x), flush, stream, dev)
+        err = rel_err(x.cpu().numpy(), oracle.smooth_lti(model, y, DT))
+        sm.close()
+        return {"workload": "Wiener velocity nx=4, T=2^20, FP32, two-filter smoother", "ms": ms,
+                "value": T_FULL / (ms * 1e-3), "unit": UNIT, "rel_err_vs_oracle": err}
+
+    def coord_turn():
+        model = synth.coordinated_turn()
+        T, iters = 2 ** 16, 10
+        _, y = synth.simulate(model, T, DT, seed=1002)
+        x0 = np.tile(model.m0, (T + 1, 1))
+        sm = MapSmoother(model, T, DT, precision="fp32", gn_iters=iters)
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        xi = torch.tensor(x0, dtype=torch.float32, device=dev)
+        x = torch.empty_like(xi)
+        ms = timed(lambda: sm.solve(yt, x_out=x, x_init=xi), flush, stream, dev)
+        ref = oracle.gauss_newton(model, y, DT, x0, iters)
+        err = rel_err(x.cpu().numpy(), ref)
+        seq = torch.empty_like(xi)
+        ms_seq = timed(lambda: sm.solve_sequential(yt, x_out=seq, x_init=xi), flush, stream, dev, reps=1)
+        sm.close()
+        return {"workload": "coordinated turn nx=5 ny=2, T=2^16, dt=1e-3, 10 Gauss-Newton iterations, FP32",
+                "ms": ms, "value": T * iters / (ms * 1e-3), "unit": "time-steps x iterations/s",
+                "rel_err_vs_oracle": err, "sequential_gpu_ms": ms_seq,
+                "speedup_vs_sequential_gpu": ms_seq / ms}
+
+    def batched():
+        from paper_2512_13319_gb300.batch import MapBatch
+        models, lengths, model_of, ys = synth.batched_workload()
+        mb = MapBatch(models, lengths, model_of, [0.01] * len(models), precision="fp32")
+        yd = mb.pack_observations(ys)
+        xd = mb.empty_outputs()
+        mb.solve(yd, xd)                 # autotune + graph capture
+        ms = timed(lambda: mb.solve(yd, xd), flush, stream, dev)
+        xs = mb.unpack_states(xd)
+        rng = np.random.default_rng(0)
+        errs = [rel_err(xs[j], oracle.smooth_lti(models[model_of[j]], ys[j], 0.01))
+                for j in rng.choice(len(lengths), size=20, replace=False)]
+        tuning = {f"nx={mdl.nx}": mb.tuning(i) for i, mdl in enumerate(models)}
+        mb.close()
+        return {"workload": "4096 Wiener-velocity trajectories, nx in {2,4,6}, lengths log-uniform 256..65536, "
+                            "dt=0.01, FP32, one CUDA graph", "steps": int(lengths.sum()), "ms": ms,
+                "value": float(lengths.sum()) / (ms * 1e-3), "unit": UNIT,
+                "max_rel_err_vs_oracle_20_sampled": max(errs), "tuning_K_B": tuning}
+
+    def gradient():
+        T = 2 ** 18
+        model = synth.ou_model(4, 2, seed=51)
+        _, y = synth.simulate(model, T, DT, seed=1004, substeps=1)
+        sm = MapSmoother(model, T, DT, precision="fp32")
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        x = sm.solve(yt)
+        box = {}
+
+        def step():
+            sm.solve(yt, x_out=x)
+            box["g"] = sm.grad(yt, x)
+        ms = timed(step, flush, stream, dev)
+        ref, _ = oracle.grad_lti(model, y, DT)
+        sm.close()
+        return {"workload": "MAP-cost gradient w.r.t. (F 4x4, log q, log r), OU nx=4, T=2^18, FP32 "
+                            "(solve + adjoint solve + contraction)", "ms": ms,
+                "rel_err_vs_fp64_oracle_gradient": rel_err(box["g"], ref)}
+
+    for name, fn in (("ou_nx8", ou8), ("two_filter", two_filter), ("coordinated_turn", coord_turn),
+                     ("batched", batched), ("gradient", gradient)):
+        guard(name, fn)
+    return out
 
 
 def sequential_gpu(model, y, dtype, dev, flush, stream):

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 # (nx, ny) of the linear-model instances; keep in sync with MAP_LINEAR_SHAPES in capi.cu
-LINEAR_SHAPES = [(2, 1), (3, 1), (4, 2), (5, 2), (6, 3)]
+LINEAR_SHAPES = [(2, 1), (3, 1), (4, 2), (5, 2), (6, 3), (8, 4)]
 CUBIC_SHAPES = [(2, 2)]
 
 

@@ -155,9 +155,9 @@ map_status map_batch_create(map_batch** out, const map_problem_desc* models, int
             ++cnt;
         }
         if (cnt == 0) continue;
-        if (models[m].model != MAP_MODEL_LINEAR || models[m].smoother != MAP_RTS) {
+        if (models[m].model != MAP_MODEL_LINEAR || models[m].smoother != MAP_RTS || models[m].nx > 6) {
             destroy_batch(b);
-            return bfail(nullptr, MAP_ERR_UNSUPPORTED, "batches hold linear models with the RTS smoother");
+            return bfail(nullptr, MAP_ERR_UNSUPPORTED, "batches hold linear models with nx <= 6 and the RTS smoother");
         }
         map_batch::Group g;
         g.model = m;

@@ -15,7 +15,7 @@ template <int N, int M, typename S> const Ops* linear_ops();
 template <typename S> const Ops* coord_turn_ops();
 template <int N, int M, typename S> const Ops* cubic_ops();
 
-#define MAP_LINEAR_SHAPES(X) X(2, 1) X(3, 1) X(4, 2) X(5, 2) X(6, 3)
+#define MAP_LINEAR_SHAPES(X) X(2, 1) X(3, 1) X(4, 2) X(5, 2) X(6, 3) X(8, 4)
 #define MAP_CUBIC_SHAPES(X) X(2, 2)
 
 const Ops* find_ops(int model, int N, int M, int prec)
@@ -151,8 +151,8 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
         return fail(*h, MAP_ERR_INVALID_ARG, "unknown model");
     if (d->model != MAP_MODEL_LINEAR && d->gn_iters < 1)
         return fail(*h, MAP_ERR_INVALID_ARG, "gn_iters must be >= 1 for nonlinear models");
-    if (d->smoother == MAP_TWO_FILTER && d->model != MAP_MODEL_LINEAR)
-        return fail(*h, MAP_ERR_UNSUPPORTED, "the two-filter smoother is built for linear models");
+    if (d->smoother == MAP_TWO_FILTER && (d->model != MAP_MODEL_LINEAR || n > 6))
+        return fail(*h, MAP_ERR_UNSUPPORTED, "the two-filter smoother is built for linear models with nx <= 6");
 
     h->model = d->model; h->N = n; h->M = m; h->NW = nw;
     h->prec = d->precision; h->smoother = d->smoother;
@@ -364,6 +364,7 @@ map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, cons
     if (h->consts.flags & (SETUP_SINGULAR_C | SETUP_SINGULAR_Q))
         return fail(*h, MAP_ERR_UNSUPPORTED, "gradients need an invertible process noise Q");
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
+    if (!ops->grad) return fail(*h, MAP_ERR_UNSUPPORTED, "no gradient kernels for this state dimension");
     return ops->grad(*h, y, x, dL_dx, flags, dL_dtheta, static_cast<cudaStream_t>(stream));
 }
 

@@ -295,7 +295,7 @@ __device__ __forceinline__ S* scratch_of(S* nodes)
 // phase 1: per-thread fold and per-tile total of the filter elements
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod, int K>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
                 S* __restrict__ tile_agg, S* __restrict__ terminal_out, CombineCtx ctx)
 {
@@ -409,7 +409,7 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S*
 // per-tile compositions
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod, int K>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
               const S* __restrict__ tile_pref, S* __restrict__ Eg, S* __restrict__ thr_aff,
               S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx)
@@ -488,7 +488,7 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
 // functions (S_k, v_k), stored per thread and step (warp-interleaved)
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod, int K>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_states(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
                 const S* __restrict__ tile_pref, S* __restrict__ filt_ws, S* __restrict__ filt_out,
                 CombineCtx ctx)
@@ -592,7 +592,7 @@ __device__ __forceinline__ void spd_combine_solve(const Red<N, S>& a, const Red<
 // forward thread g = nthr - 1 - g'.
 // ---------------------------------------------------------------------------
 template <int N, typename S, class RProd, int K>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_tf_down(const __grid_constant__ RProd prod, const S* __restrict__ thr_agg,
           const S* __restrict__ tile_pref, const S* __restrict__ filt_ws, S* __restrict__ x_out,
           CombineCtx ctx)

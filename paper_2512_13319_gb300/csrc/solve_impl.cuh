@@ -47,7 +47,8 @@ struct Layout {
 inline int pick_tile_scan_threads(size_t bytes_per_thread, int nt)
 {
     int bt = 32;
-    while (bt < 256 && bt < nt) bt *= 2;
+    const int cap = bytes_per_thread > 400 ? 128 : 256;   // large 5-tuples: fewer, heavier threads
+    while (bt < cap && bt < nt) bt *= 2;
     while (bt > 32 && bytes_per_thread * bt > 200 * 1024) bt /= 2;
     return bt;
 }
@@ -282,7 +283,7 @@ map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_
     prod.y = static_cast<const S*>(y);
     prod.T = h.T;
     prod.p = lti_params<N, M, S>(h);
-    if (h.smoother == MAP_TWO_FILTER) {
+    if constexpr (N <= 6) if (h.smoother == MAP_TWO_FILTER) {
         RevFlipProducer<N, M, S> rprod;
         rprod.y = static_cast<const S*>(y);
         rprod.T = h.T;
@@ -585,13 +586,21 @@ map_status grad_linear(map_smoother& h, const void* y, const void* x, const void
     return MAP_OK;
 }
 
+// State dimensions up to 6 get every path; larger ones (whose 5-tuples do not
+// fit one thread's registers) the RTS solve, the cost and the sequential baseline.
 template <int N, int M, typename S>
 const Ops* linear_ops()
 {
-    static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
-                         &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
-                         &solve_linear_seg<N, M, S>};
-    return &ops;
+    if constexpr (N <= 6) {
+        static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
+                             &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
+                             &solve_linear_seg<N, M, S>};
+        return &ops;
+    } else {
+        static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
+                             &solve_linear_sequential<N, M, S>, nullptr, nullptr};
+        return &ops;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -261,3 +261,23 @@ def test_two_filter_full_size_matches_rts(prec):
     x_tf, _ = gpu_solve(model, y, dt, prec, smoother="two_filter")
     ref = oracle.smooth_lti(model, y, dt)
     assert rel(x_tf, ref) <= TOL[prec]
+
+
+# ---------------------------------------------------------------- nx = 8 OU
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [1, 17, 3000])
+def test_ou_nx8(prec, T):
+    model = synth.ou_model(8, 4, seed=1001)
+    _, y = synth.simulate(model, T, 1e-3, seed=T + 5, substeps=1)
+    x, _ = gpu_solve(model, y, 1e-3, prec)
+    assert rel(x, oracle.smooth_lti(model, y, 1e-3)) <= TOL[prec]
+
+
+def test_ou_nx8_full_size_fp32():
+    """The second model of the benchmark configuration: OU nx=8, ny=4, T=2^20."""
+    model = synth.ou_model(8, 4, seed=1001)
+    T, dt = 2 ** 20, 1e-3
+    _, y = synth.simulate(model, T, dt, seed=synth.seed_for(1) + 10, substeps=1)
+    x, _ = gpu_solve(model, y, dt, "fp32")
+    assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL["fp32"]
