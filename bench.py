@@ -275,7 +275,8 @@ def ours(args):
             phases.setdefault(k, []).append(v)
     sm.profile(False)
     phase_ms = {k: statistics.median(v) for k, v in phases.items()}
-    flops, byt = work_model(4, 2, 16, sm_B(sm), wbytes)
+    K_g, B_g, nt_g = sm.geometry()
+    flops, byt = work_model(4, 2, K_g, B_g, wbytes)
     dom = max(("filter_reduce", "filter_down", "rts_down"), key=lambda k: phase_ms.get(k, 0.0))
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
@@ -303,7 +304,8 @@ def ours(args):
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": T, "nx": 4, "ny": 2, "precision": prec,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "flushed before every timed step (256 MiB write)"},
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "steps_per_thread": K_g, "threads_per_tile": B_g, "tiles": nt_g},
         "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
         "phases": per_phase, "hbm": hbm, "fp64_recomputes": fb, "singular_pivots": sing,
     }
@@ -345,10 +347,6 @@ def ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
-
-
-def sm_B(sm):
-    return 128
 
 
 def timed(fn, flush, stream, dev, reps=3):

@@ -188,6 +188,15 @@ map_status map_smoother_profile(map_smoother* h, int enable);
 map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int* n_out);
 
 /*
+ * Launch geometry of the handle's scans (host-side read, no GPU work): steps
+ * per thread K, threads per tile CTA B and the number of tiles ceil(T / (B K)).
+ * K is chosen at create time so that the tiles fill whole waves of the CTAs
+ * that the GPU keeps resident (at least 8, at most 64 steps per thread).
+ * Returns MAP_ERR_INVALID_ARG for a NULL argument.
+ */
+map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* tiles);
+
+/*
  * Allocation-free solve (no counterpart in the paper; a deployment entry point).
  * For callers that cannot call cudaMalloc at all, e.g. code running where the
  * device-memory budget is fixed up front (a real-time tracking loop, an

@@ -51,6 +51,7 @@ EXPORTS = {
     "map_smoother_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_ulonglong), _I, _VP]),
     "map_smoother_profile": (_I, [_VP, _I]),
     "map_smoother_phase_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(_I)]),
+    "map_smoother_geometry": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "map_smoother_destroy": (None, [_VP]),
     "map_smoother_last_error": (_CH, [_VP]),
     "map_smoother_supported": (_I, [_I, _I, _I, _I]),
@@ -160,6 +161,13 @@ PHASES = ("filter_reduce", "filter_tiles", "filter_down", "affine_tiles", "rts_d
 
 def map_smoother_profile(h, enable=True):
     _check(load().map_smoother_profile(h, int(bool(enable))), h)
+
+
+def map_smoother_geometry(h):
+    """(K steps per thread, B threads per tile, tiles) of the handle."""
+    K, Bt, nt = _I(), _I(), _I()
+    _check(load().map_smoother_geometry(h, ctypes.byref(K), ctypes.byref(Bt), ctypes.byref(nt)), h)
+    return K.value, Bt.value, nt.value
 
 
 def map_smoother_phase_times(h):

@@ -6,7 +6,8 @@
 // The per-model pipelines are captured once into a CUDA graph whose branches
 // run concurrently; each later call with the same arrays is one graph launch.
 // The steps per thread K and threads per tile B of every model are chosen by
-// timing the candidates on the caller's first arrays (autotuning).
+// timing the candidates (K = 8, 16 and the wave-filling K of each B) on the
+// caller's first arrays (autotuning).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -84,9 +85,12 @@ map_status autotune(map_batch* b, map_batch::Group& g, const void* y, void* x)
     const Ops* ops = find_ops(g.h->model, g.h->N, g.h->M, g.h->prec);
     struct Cand { int K, B; };
     std::vector<Cand> cands;
-    for (int K : {8, 16})
-        for (int B : {32, 64, 128})     // the scan kernels are built for <= 128 threads
-            if (geometry_fits(*g.h, B)) cands.push_back({K, B});
+    for (int B : {32, 64, 128}) {       // the scan kernels are built for <= 128 threads
+        if (!geometry_fits(*g.h, B)) continue;
+        const int kb = balanced_steps_per_thread(*g.h, B);
+        for (int K : {8, 16, kb})
+            if (K != kb || (kb != 8 && kb != 16)) cands.push_back({K, B});
+    }
     size_t need = 0;
     for (const Cand& c : cands) {
         set_geometry(*g.h, c.K, c.B);

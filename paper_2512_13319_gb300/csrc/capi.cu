@@ -204,11 +204,7 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     if (B < 32 || B > 128 || (B & (B - 1)))
         return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be 32, 64 or 128");
     while (B > 32 && tree_bytes(B) > (d->tile_threads > 0 ? 200 : 100) * 1024) B /= 2;
-    h->B = B;
-    h->K = 16;
-    const long L = (long)h->B * h->K;
-    h->nt = (int)((h->T + L - 1) / L);
-    h->Tpad = (long)h->nt * L;
+    set_geometry(*h, balanced_steps_per_thread(*h, B), B);
 
     h->ws_bytes = ops->workspace_bytes(*h);
     if ((e = cudaMalloc(&h->ws, h->ws_bytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc workspace");
@@ -240,6 +236,31 @@ bool mapk::geometry_fits(const map_smoother& h, int B)
     const size_t n = h.N, V = 16 / es, P = (n + V - 1) / V * V;
     const size_t NE = 3 * n * P + 2 * P, NSCR = 3 * n * P + P, NL = n <= 2 ? 2 : n <= 4 ? 4 : 8;
     return es * (2 * (size_t)B * NE + (size_t)B / NL * NSCR) <= 200 * 1024;
+}
+
+int mapk::balanced_steps_per_thread(const map_smoother& h, int B)
+{
+    // A tile of B*K steps is one CTA and all tiles of a launch run at once
+    // when there are at most SMs x (resident CTAs per SM) of them.  K is the
+    // smallest value in [KMIN, kmax] for which the tiles fill a whole number
+    // of such waves: a partial last wave would run a few CTAs alone.
+    constexpr int KMIN = 8, KMAX = 64;
+    const Ops* ops = find_ops(h.model, h.N, h.M, h.prec);
+    int sms = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    const int per_sm = ops && ops->resident_blocks ? ops->resident_blocks(B) : 1;
+    const long wave = (long)sms * per_sm * B;
+    // the RTS pass stages B*K states next to its affine tree in shared memory
+    const size_t es = elem_bytes(h.prec);
+    const size_t n = h.N, V = 16 / es, P = (n + V - 1) / V * V, NA = n * P + P;
+    int kmax = KMAX;
+    while (kmax > KMIN && es * (2 * (size_t)B * NA + (size_t)B * ((kmax * n) | 1)) > 200 * 1024) --kmax;
+    const long waves = std::max(1L, (h.T + wave * kmax - 1) / (wave * kmax));
+    const long K = (h.T + waves * wave - 1) / (waves * wave);
+    return (int)std::min<long>(kmax, std::max<long>(KMIN, K));
 }
 
 void mapk::set_geometry(map_smoother& h, int K, int B)
@@ -392,6 +413,15 @@ map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int re
     if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(*h, e, "stats");
+    return MAP_OK;
+}
+
+map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* tiles)
+{
+    if (!h || !K || !B || !tiles) return MAP_ERR_INVALID_ARG;
+    *K = h->K;
+    *B = h->B;
+    *tiles = h->nt;
     return MAP_OK;
 }
 

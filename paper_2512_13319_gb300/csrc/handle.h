@@ -53,10 +53,13 @@ struct Ops {
                        double* dtheta, cudaStream_t st);
     map_status (*solve_seg)(map_smoother& h, const void* y, const unsigned char* reset, void* x_out,
                             cudaStream_t st);
+    int (*resident_blocks)(int B);     // CTAs of the filter kernels per SM at B threads
 };
 
 // geometry (steps per thread K, threads per tile B) and its workspace bytes
 void set_geometry(map_smoother& h, int K, int B);
+// K for B threads per tile such that the tiles fill whole waves of resident CTAs
+int balanced_steps_per_thread(const map_smoother& h, int B);
 bool geometry_fits(const map_smoother& h, int B);
 map_status ensure_workspace(map_smoother& h, size_t bytes);
 map_status create_handle(map_smoother** out, const map_problem_desc* desc);

@@ -294,9 +294,9 @@ __device__ __forceinline__ S* scratch_of(S* nodes)
 // ---------------------------------------------------------------------------
 // phase 1: per-thread fold and per-tile total of the filter elements
 // ---------------------------------------------------------------------------
-template <int N, typename S, class Prod, int K>
+template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
+k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 S* __restrict__ tile_agg, S* __restrict__ terminal_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -338,10 +338,10 @@ k_filter_reduce(const __grid_constant__ Prod prod, S* __restrict__ thr_agg,
 
 // ---------------------------------------------------------------------------
 // phase 2: one CTA scans the tile totals from the prior (Eq. 31 a_T).  Each
-// thread folds `per` consecutive tile totals, the per-thread totals are
-// scanned with Kogge-Stone (log2(B) levels, every thread active; inclusive
-// prefixes with the later partial on the left), and each thread then walks
-// its tiles from its exclusive prefix with the one-variable combine.
+// thread folds `per` consecutive tile totals; the per-thread totals are
+// scanned with the same sub-warp up/down sweep as the tile trees, which gives
+// every thread the value function before its first tile; each thread then
+// walks its tiles with the one-variable combine.
 // ---------------------------------------------------------------------------
 template <int N, typename S>
 __global__ void __launch_bounds__(256)
@@ -350,40 +350,29 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S*
                S* __restrict__ filtT_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* sh = reinterpret_cast<S*>(smem_raw);
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
     const int per = (nt + B - 1) / B;
-    const int first = t * per, last = min(nt, first + per);
+    const int first = min(nt, t * per), last = min(nt, first + per);
     pdl_wait();
     pdl_trigger();
-    if (prior_dev) aos_load(prior_dev, 0, prior);   // terminal value function of a reversed scan
+    if (prior_dev && t == 0) aos_load(prior_dev, 0, prior);   // terminal value function of a reversed scan
 
     Elem<N, S> F;
-    set_identity(F);
-    for (int i = first; i < last; ++i) {
-        Elem<N, S> g;
-        aos_load(tile_agg, i, g);
-        combine<N, S>(g, F, F, ctx);
-    }
-    for (int o = 1; o < B; o <<= 1) {
-        __syncthreads();
-        soa_store(sh, B, t, F);
-        __syncthreads();
-        if (t >= o) {
-            Elem<N, S> e;
-            soa_load(sh, B, t - o, e);
-            combine<N, S>(F, e, F, ctx);
+    if (first < last) {
+        aos_load(tile_agg, first, F);
+        for (int i = first + 1; i < last; ++i) {
+            Elem<N, S> g;
+            aos_load(tile_agg, i, g);
+            combine<N, S>(g, F, F, ctx);
         }
+    } else {
+        set_identity(F);
     }
-    __syncthreads();
-    soa_store(sh, B, t, F);
-    __syncthreads();
-    Red<N, S> P = prior;
-    if (t > 0) {
-        Elem<N, S> e;
-        soa_load(sh, B, t - 1, e);
-        apply<N, S, false>(e, P, nullptr, nullptr, ctx);
-    }
+    node_store(F, slot<N, S>(nodes, B, 0, t));
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    Red<N, S> P;
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), prior, ctx, P);
     for (int i = first; i < last; ++i) {
         aos_store(tile_pref, i, P);
         Elem<N, S> g;
@@ -408,9 +397,9 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S*
 // phase 3: per-step filter values, closed-loop maps and their per-thread /
 // per-tile compositions
 // ---------------------------------------------------------------------------
-template <int N, typename S, class Prod, int K>
+template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
+k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ thr_agg,
               const S* __restrict__ tile_pref, S* __restrict__ Eg, S* __restrict__ thr_aff,
               S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx)
 {
@@ -487,9 +476,9 @@ k_filter_down(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
 // phase 3 of the two-filter smoother, forward part: per-step filter value
 // functions (S_k, v_k), stored per thread and step (warp-interleaved)
 // ---------------------------------------------------------------------------
-template <int N, typename S, class Prod, int K>
+template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_filter_states(const __grid_constant__ Prod prod, const S* __restrict__ thr_agg,
+k_filter_states(const __grid_constant__ Prod prod, int K, const S* __restrict__ thr_agg,
                 const S* __restrict__ tile_pref, S* __restrict__ filt_ws, S* __restrict__ filt_out,
                 CombineCtx ctx)
 {
@@ -591,9 +580,9 @@ __device__ __forceinline__ void spd_combine_solve(const Red<N, S>& a, const Red<
 // information form).  Thread g' of this reversed scan covers the steps of
 // forward thread g = nthr - 1 - g'.
 // ---------------------------------------------------------------------------
-template <int N, typename S, class RProd, int K>
+template <int N, typename S, class RProd>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_tf_down(const __grid_constant__ RProd prod, const S* __restrict__ thr_agg,
+k_tf_down(const __grid_constant__ RProd prod, int K, const S* __restrict__ thr_agg,
           const S* __restrict__ tile_pref, const S* __restrict__ filt_ws, S* __restrict__ x_out,
           CombineCtx ctx)
 {
@@ -659,8 +648,9 @@ k_tf_down(const __grid_constant__ RProd prod, const S* __restrict__ thr_agg,
 
 // ---------------------------------------------------------------------------
 // phase 4: one CTA scans the tile maps backwards from x_T: per-thread
-// composites of `per` tiles, Kogge-Stone suffix composition over threads,
-// then each thread walks its tiles backwards from the state at its end.
+// composites of `per` tiles, the affine up/down sweep of the tile trees over
+// the threads (the state at the end of every thread's tiles), then each
+// thread walks its tiles backwards from that state.
 // ---------------------------------------------------------------------------
 template <int N, typename S>
 __global__ void __launch_bounds__(256)
@@ -668,10 +658,10 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
                S* __restrict__ tile_xend)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* sh = reinterpret_cast<S*>(smem_raw);
+    S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
     const int per = (nt + B - 1) / B;
-    const int first = t * per, last = min(nt, first + per);
+    const int first = min(nt, t * per), last = min(nt, first + per);
     pdl_wait();
     pdl_trigger();
 
@@ -682,30 +672,14 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
         aos_load(tile_aff, i, a);
         compose<N, S>(a, H, H);
     }
-    for (int o = 1; o < B; o <<= 1) {               // H_t o H_{t+1} o ... (suffix)
-        __syncthreads();
-        soa_store(sh, B, t, H);
-        __syncthreads();
-        if (t + o < B) {
-            Aff<N, S> a;
-            soa_load(sh, B, t + o, a);
-            compose<N, S>(H, a, H);
-        }
-    }
-    __syncthreads();
-    soa_store(sh, B, t, H);
-    __syncthreads();
-    S x[N];
+    node_store(H, aslot<N, S>(nodes, B, 0, t));
+    coop_aff_up<N, S>(nodes);
+    S xe[N], x[N];
+    if (t == 0) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) x[i] = xT[i];
-    if (t + 1 < B) {                                // state at the end of this thread's tiles
-        Aff<N, S> a;
-        soa_load(sh, B, t + 1, a);
-        S y[N];
-        affine_apply<N, S>(a, x, y);
-#pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = y[i];
+        for (int i = 0; i < N; ++i) xe[i] = xT[i];
     }
+    coop_aff_down<N, S>(nodes, xe, x);              // state at the end of this thread's tiles
     for (int i = last - 1; i >= first; --i) {
 #pragma unroll
         for (int j = 0; j < N; ++j) tile_xend[(long)i * N + j] = x[j];
@@ -721,9 +695,12 @@ k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
 // ---------------------------------------------------------------------------
 // phase 5: per-step smoothed states x_k = E_k x_{k+1} + g_k
 // ---------------------------------------------------------------------------
-template <int N, typename S, int K>
+// shared-memory stride of one thread's staged states (odd: no bank conflicts)
+__host__ __device__ __forceinline__ int rts_stage_stride(int K, int N) { return (K * N) | 1; }
+
+template <int N, typename S>
 __global__ void __launch_bounds__(128)
-k_rts_down(const S* __restrict__ Eg, const S* __restrict__ thr_aff,
+k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff,
            const S* __restrict__ tile_xend, long T, S* __restrict__ x_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -732,6 +709,7 @@ k_rts_down(const S* __restrict__ Eg, const S* __restrict__ thr_aff,
     const long gthr = (long)blockIdx.x * B + t;
     const long k0 = gthr * K;
     constexpr int NA = Aff<N, S>::NCOMP;
+    constexpr int U = 4;                   // steps whose maps are loaded ahead of use
     {
         Aff<N, S> a;
         wi_load(thr_aff, gthr, a);
@@ -745,34 +723,57 @@ k_rts_down(const S* __restrict__ Eg, const S* __restrict__ thr_aff,
         for (int i = 0; i < N; ++i) xe[i] = tile_xend[(long)blockIdx.x * N + i];
     }
     coop_aff_down<N, S>(nodes, xe, x);
-    S xs[K][N];
+    // the states are staged past the affine tree and written out coalesced
+    const int SP = rts_stage_stride(K, N);
+    S* st = nodes + 2 * B * CoopLayout<N, S>::NA;
+    S* mine = st + t * SP;
+#pragma unroll 1
+    for (int i0 = K - 1; i0 >= 0; i0 -= U) {
+        S buf[U][NA];
 #pragma unroll
-    for (int i = K - 1; i >= 0; --i) {
-        const long k = k0 + i;
-        if (k < T) {
-            Aff<N, S> a;
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 - u;
+            if (i >= 0 && k0 + i < T) {
 #pragma unroll
-            for (int c = 0; c < NA; ++c) comp(a, c) = Eg[wis_idx(gthr, i, c, K, NA)];
-            S y[N];
-            affine_apply<N, S>(a, x, y);
-#pragma unroll
-            for (int j = 0; j < N; ++j) x[j] = y[j];
+                for (int c = 0; c < NA; ++c) buf[u][c] = Eg[wis_idx(gthr, i, c, K, NA)];
+            }
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) xs[i][j] = x[j];
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 - u;
+            if (i >= 0) {
+                if (k0 + i < T) {
+                    S y[N];
+#pragma unroll
+                    for (int r = 0; r < N; ++r) {
+                        S acc = buf[u][N * N + r];
+#pragma unroll
+                        for (int q = 0; q < N; ++q) acc = fma(buf[u][r * N + q], x[q], acc);
+                        y[r] = acc;
+                    }
+#pragma unroll
+                    for (int j = 0; j < N; ++j) x[j] = y[j];
+                }
+#pragma unroll
+                for (int j = 0; j < N; ++j) mine[i * N + j] = x[j];
+            }
+        }
     }
-    // stage the tile's states in shared memory and write them out coalesced
     __syncthreads();
-    S* st = nodes;
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) st[(t * K + i) * N + j] = xs[i][j];
-    __syncthreads();
-    const long base = (long)blockIdx.x * B * K * N;
+    const int KN = K * N;
+    const long base = (long)blockIdx.x * B * KN;
     const long lim = T * N;
-    for (int idx = t; idx < B * K * N; idx += B)
-        if (base + idx < lim) x_out[base + idx] = st[idx];
+    for (int idx = t; idx < B * KN; idx += B) {
+        const int tt = idx / KN;
+        if (base + idx < lim) x_out[base + idx] = st[tt * SP + (idx - tt * KN)];
+    }
+}
+
+// shared memory of k_rts_down: the affine tree and the staged states
+template <int N, typename S>
+__host__ __device__ constexpr size_t rts_smem(int B, int K)
+{
+    return aff_tree_smem<N, S>(B) + sizeof(S) * (size_t)B * rts_stage_stride(K, N);
 }
 
 // ---------------------------------------------------------------------------

@@ -11,8 +11,6 @@
 
 namespace mapk {
 
-constexpr int KSTEP = 16;  // steps per thread
-
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 template <int N, typename S>
@@ -43,13 +41,14 @@ struct Layout {
     }
 };
 
-// largest power-of-two CTA size <= 256 whose shared memory fits
-inline int pick_tile_scan_threads(size_t bytes_per_thread, int nt)
+// CTA size of a single-CTA tile scan: the smallest power of two >= nt (at
+// least 32, at most 256) whose tree, of smem(bt) bytes, fits in shared memory
+template <class SmemOf>
+inline int pick_tile_scan_threads(int nt, SmemOf smem)
 {
     int bt = 32;
-    const int cap = bytes_per_thread > 400 ? 128 : 256;   // large 5-tuples: fewer, heavier threads
-    while (bt < cap && bt < nt) bt *= 2;
-    while (bt > 32 && bytes_per_thread * bt > 200 * 1024) bt /= 2;
+    while (bt < 256 && bt < nt) bt *= 2;
+    while (bt > 32 && smem(bt) > 200 * 1024) bt /= 2;
     return bt;
 }
 
@@ -110,8 +109,23 @@ size_t rts_workspace(const map_smoother& h)
     return Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad).total;
 }
 
+// CTAs of B threads of the filter kernels of `Prod` resident on one SM
+template <int N, typename S, class Prod>
+int rts_resident_blocks(int B)
+{
+    const size_t big = 200 * 1024;
+    if (allow_smem(k_filter_reduce<N, S, Prod>, big) != cudaSuccess ||
+        allow_smem(k_filter_down<N, S, Prod>, big) != cudaSuccess)
+        return 1;
+    int a = 1, b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_filter_reduce<N, S, Prod>, B, tree_smem<N, S>(B));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_filter_down<N, S, Prod>, B, std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B)));
+    return std::max(1, std::min(a, b));
+}
+
 // Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
-template <int N, typename S, class Prod, int K = KSTEP>
+template <int N, typename S, class Prod>
 map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st,
                    bool dev_prior = false)
 {
@@ -133,22 +147,22 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
 
     const size_t sh_reduce = tree_smem<N, S>(B);
     const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B));
-    const size_t sh_rts = std::max(aff_tree_smem<N, S>(B), sizeof(S) * B * K * N);
-    const int bt_f = pick_tile_scan_threads(sizeof(S) * Elem<N, S>::NCOMP, nt);
-    const int bt_a = pick_tile_scan_threads(sizeof(S) * Aff<N, S>::NCOMP, nt);
-    const size_t sh_tf = sizeof(S) * Elem<N, S>::NCOMP * bt_f;
-    const size_t sh_ta = sizeof(S) * Aff<N, S>::NCOMP * bt_a;
+    const int K = h.K;
+    const size_t sh_rts = rts_smem<N, S>(B, K);
+    const int bt_f = pick_tile_scan_threads(nt, [](int b) { return tree_smem<N, S>(b); });
+    const int bt_a = pick_tile_scan_threads(nt, [](int b) { return aff_tree_smem<N, S>(b); });
+    const size_t sh_tf = tree_smem<N, S>(bt_f);
+    const size_t sh_ta = aff_tree_smem<N, S>(bt_a);
 
     static std::once_flag once;
     cudaError_t e0 = cudaSuccess;
     std::call_once(once, [&] {
         const size_t big = 200 * 1024;
-        e0 = allow_smem(k_filter_reduce<N, S, Prod, K>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod, K>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S, K>, big);
+        e0 = allow_smem(k_filter_reduce<N, S, Prod>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_affine_tiles<N, S>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S, K>, big);
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
@@ -160,18 +174,18 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     mark();
     // dev_prior: the prior comes from the producer's terminal() (device data)
     S* term = dev_prior ? reinterpret_cast<S*>(h.ws + L.term) : nullptr;
-    launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_reduce, st, false, prod, thr_agg, tile_agg,
+    launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg,
            term, ctx);
     mark();
     launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
            (const S*)term, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
     mark();
-    launch(k_filter_down<N, S, Prod, K>, nt, B, sh_down, st, pdl, prod, (const S*)thr_agg,
+    launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl, prod, K, (const S*)thr_agg,
            (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx);
     mark();
     launch(k_affine_tiles<N, S>, 1, bt_a, sh_ta, st, pdl, (const S*)tile_aff, nt, (const S*)xT, tile_xend);
     mark();
-    launch(k_rts_down<N, S, K>, nt, B, sh_rts, st, pdl, (const S*)Eg, (const S*)thr_aff,
+    launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff,
            (const S*)tile_xend, T, x_out);
     mark();
     cudaError_t e = cudaGetLastError();
@@ -187,7 +201,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
                   cudaStream_t st)
 {
     using R = Red<N, S>;
-    constexpr int K = KSTEP;
+    const int K = h.K;
     const int B = h.B, nt = h.nt;
     const long nthr = (long)nt * B;
     const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
@@ -203,18 +217,19 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const long T = h.T;
     S* xT = x_out + T * N;
     const size_t sh_tree = tree_smem<N, S>(B);
-    const int bt_f = pick_tile_scan_threads(sizeof(S) * Elem<N, S>::NCOMP, nt);
-    const size_t sh_tf = sizeof(S) * Elem<N, S>::NCOMP * bt_f;
+    const size_t sh_tfd = std::max(sh_tree, sizeof(S) * (size_t)B * K * N);   // k_tf_down stages the states
+    const int bt_f = pick_tile_scan_threads(nt, [](int b) { return tree_smem<N, S>(b); });
+    const size_t sh_tf = tree_smem<N, S>(bt_f);
 
     static std::once_flag once;
     cudaError_t e0 = cudaSuccess;
     std::call_once(once, [&] {
         const size_t big = 200 * 1024;
-        e0 = allow_smem(k_filter_reduce<N, S, Prod, K>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_reduce<N, S, RProd, K>, big);
+        e0 = allow_smem(k_filter_reduce<N, S, Prod>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_reduce<N, S, RProd>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_states<N, S, Prod, K>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_tf_down<N, S, RProd, K>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_states<N, S, Prod>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_tf_down<N, S, RProd>, big);
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
@@ -222,21 +237,21 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
-    launch(k_filter_reduce<N, S, Prod, K>, nt, B, sh_tree, st, false, fprod, thr_agg, tile_agg,
+    launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg,
            (S*)nullptr, ctx);
     mark();
     launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
            (const S*)nullptr, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
     mark();
-    launch(k_filter_states<N, S, Prod, K>, nt, B, sh_tree, st, pdl, fprod, (const S*)thr_agg,
+    launch(k_filter_states<N, S, Prod>, nt, B, sh_tree, st, pdl, fprod, K, (const S*)thr_agg,
            (const S*)tile_pref, filt_ws, filt_out, ctx);
     mark();
-    launch(k_filter_reduce<N, S, RProd, K>, nt, B, sh_tree, st, pdl, rprod, thr_agg, tile_agg, term, ctx);
+    launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
     launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
            (const S*)term, tile_pref, fin2, xdummy, (S*)nullptr, ctx);
     mark();
-    launch(k_tf_down<N, S, RProd, K>, nt, B, sh_tree, st, pdl, rprod, (const S*)thr_agg,
+    launch(k_tf_down<N, S, RProd>, nt, B, sh_tfd, st, pdl, rprod, K, (const S*)thr_agg,
            (const S*)tile_pref, (const S*)filt_ws, x_out, ctx);
     mark();
     cudaError_t e = cudaGetLastError();
@@ -305,7 +320,7 @@ map_status solve_linear_sequential(map_smoother& h, const void* y, void* x_out, 
 }
 
 // Many trajectories of one linear model concatenated with reset elements
-// (SegLtiProducer); K (steps per thread) is 8 or 16, chosen at run time.
+// (SegLtiProducer).
 template <int N, int M, typename S>
 map_status solve_linear_seg(map_smoother& h, const void* y, const unsigned char* reset, void* x_out,
                             cudaStream_t st)
@@ -319,8 +334,7 @@ map_status solve_linear_seg(map_smoother& h, const void* y, const unsigned char*
         prod.v0[i] = S(h.consts.v0[i]);
         for (int j = i; j < N; ++j) prod.S0[Sym<N>::at(i, j)] = S(h.consts.S0[i * N + j]);
     }
-    if (h.K == 8) return run_rts<N, S, SegLtiProducer<N, M, S>, 8>(h, prod, static_cast<S*>(x_out), nullptr, st);
-    return run_rts<N, S, SegLtiProducer<N, M, S>, 16>(h, prod, static_cast<S*>(x_out), nullptr, st);
+    return run_rts<N, S>(h, prod, static_cast<S*>(x_out), nullptr, st);
 }
 
 // Discrete Onsager-Machlup cost of a trajectory of a linear model:
@@ -594,11 +608,12 @@ const Ops* linear_ops()
     if constexpr (N <= 6) {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
                              &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
-                             &solve_linear_seg<N, M, S>};
+                             &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>};
         return &ops;
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
-                             &solve_linear_sequential<N, M, S>, nullptr, nullptr};
+                             &solve_linear_sequential<N, M, S>, nullptr, nullptr,
+                             &rts_resident_blocks<N, S, LtiProducer<N, M, S>>};
         return &ops;
     }
 }
@@ -676,7 +691,8 @@ template <typename S>
 const Ops* coord_turn_ops()
 {
     static const Ops ops{&rts_workspace<5, S>, &solve_nonlinear<CtModel<S>, S>, nullptr,
-                         &solve_nonlinear_sequential<CtModel<S>, S>, nullptr, nullptr};
+                         &solve_nonlinear_sequential<CtModel<S>, S>, nullptr, nullptr,
+                         &rts_resident_blocks<5, S, NlProducer<CtModel<S>, S>>};
     return &ops;
 }
 
@@ -684,7 +700,8 @@ template <int N, int M, typename S>
 const Ops* cubic_ops()
 {
     static const Ops ops{&rts_workspace<N, S>, &solve_nonlinear<CubicModel<N, M, S>, S>, nullptr,
-                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>, nullptr, nullptr};
+                         &solve_nonlinear_sequential<CubicModel<N, M, S>, S>, nullptr, nullptr,
+                         &rts_resident_blocks<N, S, NlProducer<CubicModel<N, M, S>, S>>};
     return &ops;
 }
 

@@ -96,6 +96,10 @@ class MapSmoother:
         """Set theta = (F, log q, log r) (Q = e^log_q L W L^T, R = e^log_r R)."""
         B.map_smoother_update(self._h, F, log_q, log_r)
 
+    def geometry(self):
+        """(K steps per thread, B threads per tile, number of tiles)."""
+        return B.map_smoother_geometry(self._h)
+
     def profile(self, enable=True):
         """Record per-phase CUDA events in every solve (see phase_times)."""
         B.map_smoother_profile(self._h, enable)
