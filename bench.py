@@ -296,7 +296,7 @@ def ours(args):
            "achieved_gbs": solve_bytes(4, 2, wbytes) * T / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
            "note": "y in + x out over the whole solve; intermediates excluded"}
     hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
-    fb, sing = sm.stats()
+    fb, sing, timeouts = sm.stats()
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -307,7 +307,7 @@ def ours(args):
                    "l2": "flushed before every timed step (256 MiB write)",
                    "steps_per_thread": K_g, "threads_per_tile": B_g, "tiles": nt_g},
         "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
-        "phases": per_phase, "hbm": hbm, "fp64_recomputes": fb, "singular_pivots": sing,
+        "phases": per_phase, "hbm": hbm, "fp64_recomputes": fb, "singular_pivots": sing, "copy_wait_timeouts": timeouts,
     }
     sm.close()
 

@@ -166,11 +166,12 @@ map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, cons
 map_status map_smoother_update(map_smoother* h, const double* F, double log_q, double log_r);
 
 /*
- * Counters of the device-side precision policy since create or the last
- * reset: [0] combines recomputed in FP64, [1] singular pivots met.
- * Synchronises the stream.
+ * Device-side counters since create or the last reset: [0] combines
+ * recomputed in FP64 (precision policy), [1] singular pivots met, [2] bulk
+ * input copies whose bounded wait gave up (their tile was not computed and
+ * the solve's result is invalid; expected to stay 0).  Synchronises the stream.
  */
-map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int reset, void* stream);
+map_status map_smoother_stats(map_smoother* h, unsigned long long out[3], int reset, void* stream);
 
 /*
  * Per-phase device timing.  With profiling on, every solve records CUDA events

@@ -151,9 +151,9 @@ def map_smoother_update(h, F=None, log_q=0.0, log_r=0.0):
 
 
 def map_smoother_stats(h, reset=False, stream=None):
-    out = (ctypes.c_ulonglong * 2)()
+    out = (ctypes.c_ulonglong * 3)()
     _check(load().map_smoother_stats(h, out, int(bool(reset)), stream), h)
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 PHASES = ("filter_reduce", "filter_tiles", "filter_down", "affine_tiles", "rts_down")

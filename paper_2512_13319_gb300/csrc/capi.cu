@@ -82,6 +82,7 @@ void free_handle(map_smoother* h)
     if (h->d_cost) cudaFree(h->d_cost);
     if (h->d_lam) cudaFree(h->d_lam);
     if (h->d_grad) cudaFree(h->d_grad);
+    if (h->d_fold) cudaFree(h->d_fold);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;
@@ -92,6 +93,7 @@ void free_handle(map_smoother* h)
 map_status run_setup(map_smoother* h)
 {
     const int n = h->N, m = h->M, nw = h->NW;
+    h->fold_K = 0;                     // linear-fold constants follow the model
     DevBuf in, out;
     std::vector<double> W = h->W, R = h->R;
     for (double& w : W) w *= std::exp(h->logq);
@@ -208,9 +210,9 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
 
     h->ws_bytes = ops->workspace_bytes(*h);
     if ((e = cudaMalloc(&h->ws, h->ws_bytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc workspace");
-    if ((e = cudaMalloc(&h->d_stats, 2 * sizeof(unsigned long long))) != cudaSuccess)
+    if ((e = cudaMalloc(&h->d_stats, 3 * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMalloc");
-    if ((e = cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
+    if ((e = cudaMemset(h->d_stats, 0, 3 * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMemset");
     if ((e = cudaMalloc(&h->d_cost, sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
     if (h->model != MAP_MODEL_LINEAR) {
@@ -220,6 +222,8 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
         if ((e = cudaMalloc(&h->d_lam, (size_t)(h->T + 1) * n * es)) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
         if ((e = cudaMalloc(&h->d_grad, sizeof(double) * (n * n + 2))) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+        if ((e = cudaMalloc(&h->d_fold, fold_bytes(n, m, es))) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(*h, e, "create");
@@ -405,12 +409,12 @@ map_status map_smoother_update(map_smoother* h, const double* F, double log_q, d
     return MAP_OK;
 }
 
-map_status map_smoother_stats(map_smoother* h, unsigned long long out[2], int reset, void* stream)
+map_status map_smoother_stats(map_smoother* h, unsigned long long out[3], int reset, void* stream)
 {
     if (!h || !out) return MAP_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(out, h->d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemcpyAsync(out, h->d_stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->d_stats, 0, 3 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(*h, e, "stats");
     return MAP_OK;

@@ -42,12 +42,37 @@ struct CoopLayout {
     static constexpr int NSCR = 3 * N * P + P;
 };
 
+// One padded row (P scalars, 16-byte aligned: every node, scratch and level
+// block keeps rows at multiples of P from a 16-byte aligned base) with 16-byte
+// shared-memory loads; the first N scalars go to out.
+template <int N, typename S>
+__device__ __forceinline__ void padded_row_load(const S* __restrict__ row, S* out)
+{
+    constexpr int P = CoopLayout<N, S>::P;
+    if constexpr (sizeof(S) == 4) {
+#pragma unroll
+        for (int j = 0; j < P; j += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(row + j);
+            if (j < N) out[j] = v.x;
+            if (j + 1 < N) out[j + 1] = v.y;
+            if (j + 2 < N) out[j + 2] = v.z;
+            if (j + 3 < N) out[j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < P; j += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(row + j);
+            if (j < N) out[j] = v.x;
+            if (j + 1 < N) out[j + 1] = v.y;
+        }
+    }
+}
+
 template <int N, typename S>
 __device__ __forceinline__ void row_load(const S* __restrict__ m, int r, S* out)
 {
     constexpr int P = CoopLayout<N, S>::P;
-#pragma unroll
-    for (int q = 0; q < N; ++q) out[q] = m[r * P + q];
+    padded_row_load<N, S>(m + r * P, out);
 }
 
 template <int N, typename S>
@@ -55,9 +80,7 @@ __device__ __forceinline__ void mat_load(const S* __restrict__ m, S (*out)[N])
 {
     constexpr int P = CoopLayout<N, S>::P;
 #pragma unroll
-    for (int k = 0; k < N; ++k)
-#pragma unroll
-        for (int q = 0; q < N; ++q) out[k][q] = m[k * P + q];
+    for (int k = 0; k < N; ++k) padded_row_load<N, S>(m + k * P, out[k]);
 }
 
 template <int N, typename S>
@@ -202,7 +225,7 @@ __device__ __forceinline__ void coop_inverse(const S* __restrict__ Cm, const S* 
         const S below = group_max<NL, S>(rr > cc ? ms::sabs(x[cc]) : S(0));
         const S p = px[cc];
         ok = ok && (ms::sabs(p) > S(0.5) * below) && (p != S(0));
-        const S ip = S(1) / p;
+        const S ip = ms::pivot_rcp(p);
         if (rr == cc) {
 #pragma unroll
             for (int q = 0; q < N; ++q) { x[q] = px[q] * ip; y[q] = py[q] * ip; }
@@ -340,10 +363,12 @@ __device__ __forceinline__ void coop_combine(const S* __restrict__ Ln, const S* 
     }
 }
 
-// On (value node) = En (x) Pn  (En: element node, Pn: value node); On may be Pn
+// On (value node) = E (x) Pn for the element E whose A, C, J are those of
+// node En and whose b, eta are the vectors eb, eeta; On may be Pn
 template <int N, typename S>
-__device__ __forceinline__ void coop_apply(const S* __restrict__ En, const S* Pn, S* On,
-                                           S* __restrict__ scr, bool active, const CombineCtx& ctx)
+__device__ __forceinline__ void coop_apply_parts(const S* __restrict__ En, const S* __restrict__ eb,
+                                                 const S* __restrict__ eeta, const S* Pn, S* On,
+                                                 S* __restrict__ scr, bool active, const CombineCtx& ctx)
 {
     using L = CoopLayout<N, S>;
     constexpr int NL = L::NL, P = L::P;
@@ -355,7 +380,7 @@ __device__ __forceinline__ void coop_apply(const S* __restrict__ En, const S* Pn
     S AE[N][N], SP[N][N], bE[N], v[N];
     mat_load<N, S>(En + L::oA, AE);
     mat_load<N, S>(Pn + L::oS, SP);
-    vec_load<N, S>(En + L::ob, bE);
+    vec_load<N, S>(eb, bE);
     vec_load<N, S>(Pn + L::ov, v);
     S e[N], t4[N], w[N];
 #pragma unroll
@@ -388,7 +413,7 @@ __device__ __forceinline__ void coop_apply(const S* __restrict__ En, const S* Pn
     mat_load<N, S>(scr + L::sT3, Ef);
     mat_load<N, S>(scr + L::sT4, T4);
     S os[N];
-    S ov = En[L::oeta + rr];
+    S ov = eeta[rr];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         S s = En[L::oJ + rr * P + q];
@@ -403,6 +428,15 @@ __device__ __forceinline__ void coop_apply(const S* __restrict__ En, const S* Pn
         for (int q = 0; q < N; ++q) On[L::oS + rr * P + q] = os[q];
         On[L::ov + rr] = ov;
     }
+}
+
+// On (value node) = En (x) Pn  (En: element node, Pn: value node); On may be Pn
+template <int N, typename S>
+__device__ __forceinline__ void coop_apply(const S* __restrict__ En, const S* Pn, S* On,
+                                           S* __restrict__ scr, bool active, const CombineCtx& ctx)
+{
+    using L = CoopLayout<N, S>;
+    coop_apply_parts<N, S>(En, En + L::ob, En + L::oeta, Pn, On, scr, active, ctx);
 }
 
 // On = F1n o F2n (affine maps)

@@ -31,6 +31,8 @@ struct map_smoother {
     double* d_cost = nullptr;
     void* d_lam = nullptr;             // adjoint trajectory (linear models)
     double* d_grad = nullptr;          // gradient accumulators
+    void* d_fold = nullptr;            // linear-fold constants of K steps (linear models)
+    int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
     double logq = 0.0, logr = 0.0;     // noise scales of the gradient parameters
     // per-phase timing (map_smoother_profile)
     bool profile = false;
@@ -42,6 +44,18 @@ struct map_smoother {
 namespace mapk {
 
 size_t elem_bytes(int prec);
+
+// bytes of the linear-fold constants of an (n, m) linear model in scalars of
+// es bytes: up to 64 steps per thread and 8 tree levels (the layout of
+// FoldLayout in lti_fold.cuh)
+inline size_t fold_bytes(int n, int m, size_t es)
+{
+    const int ns = n * (n + 1) / 2, V = 16 / (int)es, P = (n + V - 1) / V * V;
+    const int oG = (n * n + 2 * ns + 2 * n + 3) / 4 * 4;
+    const int oL = (oG + 64 * 2 * n * m + 3) / 4 * 4;
+    const int LS = (3 * n * P + 4 * n * n + 3) / 4 * 4;
+    return es * (size_t)(oL + 8 * LS);
+}
 
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.
 struct Ops {

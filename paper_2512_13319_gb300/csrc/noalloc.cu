@@ -17,7 +17,7 @@
 // device.  Make that first call before any stream capture.
 //
 // Every call shares the arrays and they keep the contents of the last call:
-// the two counters of the precision policy are cleared at the start of each
+// the three device counters (precision policy, bounded waits) are cleared at the start of each
 // call; everything else is fully written before it is read.  Calls that
 // overlap on the GPU (two streams, two host threads) race on the arrays and
 // must be serialised by the caller.
@@ -38,7 +38,7 @@ constexpr int SETUP_IN_DOUBLES = 8 * 8 * 4 + 8 * 5 + 8 * 8 * 2;   // F, L, W, H,
 constexpr int MAX_DEVICES = 64;
 
 __device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
-__device__ __align__(256) unsigned long long g_stats[2];
+__device__ __align__(256) unsigned long long g_stats[3];
 __device__ __align__(256) double g_setup_in[SETUP_IN_DOUBLES];
 __device__ __align__(256) mapk::SetupOut g_setup_out;
 
@@ -194,17 +194,21 @@ extern "C" map_status map_smoother_solve_noalloc(const map_problem_desc* d, cons
     const long L = (long)h.B * h.K;
     h.nt = (int)((h.T + L - 1) / L);
     h.Tpad = (long)h.nt * L;
-    const size_t need = ops->workspace_bytes(h);
+    const size_t fold_off = (ops->workspace_bytes(h) + 255) / 256 * 256;
+    const size_t need = fold_off + fold_bytes(n, m, es);
     if (need > NOALLOC_SCRATCH_BYTES)
         return noalloc_fail(MAP_ERR_SHAPE,
                             "T too large for the allocation-free scratch: needs " + std::to_string(need) +
                                 " bytes, the __device__ array holds " + std::to_string(NOALLOC_SCRATCH_BYTES));
     h.ws = arr.scratch;
+    h.d_fold = arr.scratch + fold_off;     // recomputed by every call (fold_K = 0)
+    h.fold_K = 0;
     h.d_stats = arr.stats;
-    if ((e = cudaMemsetAsync(arr.stats, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(arr.stats, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess)
         return noalloc_fail(MAP_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const map_status s = ops->solve(h, y, x_out, nullptr, st);
     h.ws = nullptr;        // the stack handle owns nothing
+    h.d_fold = nullptr;
     h.d_stats = nullptr;
     if (s != MAP_OK) return noalloc_fail(s, h.err);
     return MAP_OK;

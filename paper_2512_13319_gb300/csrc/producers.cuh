@@ -57,6 +57,7 @@ template <int N, int M, typename S>
 struct LtiProducer {
     static constexpr int W = M;      // scalars read per step
     static constexpr bool RESETS = false;
+    static constexpr bool LINEAR_FOLD = true;   // see lti_fold.cuh
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                      // (T, M), row k holds y_{k+1}
     long T;
@@ -115,6 +116,7 @@ template <int N, int M, typename S>
 struct SegLtiProducer {
     static constexpr int W = M;
     static constexpr bool RESETS = true;
+    static constexpr bool LINEAR_FOLD = false;
     const S* y;                      // (T, M) with an unused row at every reset
     const unsigned char* reset;      // (T): 1 where a trajectory starts (except the first)
     long T;
@@ -184,6 +186,7 @@ template <int N, typename S>
 struct AdjProducer {
     static constexpr int W = N;
     static constexpr bool RESETS = false;
+    static constexpr bool LINEAR_FOLD = false;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* d;                      // (T+1, N): dL/dx*
     long T;
@@ -242,6 +245,7 @@ template <int N, int M, typename S>
 struct RevFlipProducer {
     static constexpr int W = M;
     static constexpr bool RESETS = false;
+    static constexpr bool LINEAR_FOLD = false;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                      // (T, M), row k-1 holds y_k
     long T;
@@ -385,6 +389,7 @@ struct NlProducer {
     static constexpr int N = Model::N, M = Model::M;
     static constexpr int W = M + N;   // y_{k+1} then xbar_{k+1}
     static constexpr bool RESETS = false;
+    static constexpr bool LINEAR_FOLD = false;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                       // (T, M)
     const S* xbar;                    // (T+1, N)

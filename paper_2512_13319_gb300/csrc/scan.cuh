@@ -21,6 +21,8 @@
 #pragma once
 #include "producers.cuh"
 #include "coop.cuh"
+#include "lti_fold.cuh"
+#include "bulk.cuh"
 
 namespace mapk {
 
@@ -294,6 +296,223 @@ __device__ __forceinline__ S* scratch_of(S* nodes)
 // ---------------------------------------------------------------------------
 // phase 1: per-thread fold and per-tile total of the filter elements
 // ---------------------------------------------------------------------------
+// a tile (CTA) whose B*K steps all lie before T: with a linear-fold constant
+// block its tree runs on the (b, eta) parts only (lti_fold.cuh)
+__device__ __forceinline__ bool lti_full_tile(long T, int K)
+{
+    return (long)(blockIdx.x + 1) * blockDim.x * K <= T;
+}
+
+// Exclusive prefix (value function before the thread's first step) of every
+// thread of a tile, from the per-thread aggregates thr_agg of the reduce
+// kernel and the tile prefix tile_pref of the tile scan: the tile's up-sweep,
+// the wait for the previous kernel (PDL), and the down-sweep.
+// With linear-fold constants (fold != nullptr, lti_fold.cuh) the reduce
+// kernel has covered the full tiles 0 .. gridDim.x - 2 with (b, eta) parts
+// only, and their trees run on those; the last tile's per-thread folds are
+// formed here (linear fold for threads whose K steps are all before T, the
+// step-by-step fold for the one that reaches T, the identity past it).
+// gam: shared memory for the Gamma_i (behind the element tree).
+template <int N, typename S, class Prod>
+__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int K, const S* __restrict__ thr_agg,
+                                                   const S* __restrict__ tile_pref, const S* __restrict__ fold,
+                                                   S* nodes, S* gam, const CombineCtx& ctx, bool trigger,
+                                                   Red<N, S>& X)
+{
+    const int B = blockDim.x, t = threadIdx.x;
+    const long gthr = (long)blockIdx.x * B + t;
+    Elem<N, S> G;
+    bool have_leaf = false;
+    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+        if (fold) {
+            using FL = FoldLayout<N, Prod::W, S>;
+            if (blockIdx.x + 1 < gridDim.x) {
+                using TS = LtiTreeSmem<N, Prod::W, S>;
+                const int LB = ilog2(B);
+                S* pre = nodes + TS::pre(B);
+                S* bq = nodes + TS::bq(B);
+                S* lv = nodes + TS::lv(B);
+                for (int q = t; q < (LB + 1) * FL::LS; q += B) lv[q] = fold[FL::oL + q];
+#pragma unroll
+                for (int c = 0; c < 2 * N; ++c) bq[t * 2 * N + c] = thr_agg[wi_idx(gthr, c, 2 * N)];
+                lti_tree_up<N, Prod::W, S>(bq, lv);
+                pdl_wait();                // tile prefixes of the previous kernel
+                if (trigger) pdl_trigger();
+                if (t == 0) {
+                    Red<N, S> pin;
+                    aos_load(tile_pref, (long)blockIdx.x, pin);
+                    node_store(pin, pre + (2 * B - 2) * CoopLayout<N, S>::NR);
+                }
+                lti_tree_down<N, Prod::W, S>(bq, lv, pre, scratch_of<N, S>(nodes), ctx, X);
+                return;
+            }
+            // last tile
+            for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
+            __syncthreads();
+            const long k0 = gthr * K;
+            const long r = prod.T - k0;
+            if (r >= K) {
+                lti_fold_elem<N, S>(prod, fold, gam, K, k0, G);
+            } else if (r <= 0) {
+                set_identity(G);
+            } else {
+                S row[Prod::W];
+                prod.load1(k0, row);
+                prod.make(k0, row, G);
+#pragma unroll 1
+                for (int i = 1; i < r; ++i) {
+                    prod.load1(k0 + i, row);
+                    Elem<N, S> e;
+                    prod.make(k0 + i, row, e);
+                    combine<N, S>(e, G, G, ctx);
+                }
+            }
+            have_leaf = true;
+        }
+    }
+    if (!have_leaf) wi_load(thr_agg, gthr, G);
+    node_store(G, slot<N, S>(nodes, B, 0, t));
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    pdl_wait();                            // tile prefixes of the previous kernel
+    if (trigger) pdl_trigger();
+    Red<N, S> pin;
+    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
+}
+
+// The thread of the last tile that holds step T-1 writes the value function
+// at x_T (after its steps), its minimiser x_T and, if asked, its filter value
+// (linear-fold mode, where the tile scan does not see the last tile).
+template <int N, typename S>
+__device__ __forceinline__ void write_final_if_last(long T, int K, const Red<N, S>& X, S* final_out,
+                                                    S* xT_out, S* filtT_out, const CombineCtx& ctx)
+{
+    const long k0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) * K;
+    if (!final_out || blockIdx.x + 1 != gridDim.x || k0 >= T || k0 + K < T) return;
+    Red<N, S> P = X;
+    aos_store(final_out, 0, P);
+    S x[N];
+    if (!red_argmin<N, S>(P, x) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+#pragma unroll
+    for (int i = 0; i < N; ++i) xT_out[i] = x[i];
+    if (filtT_out) {
+#pragma unroll
+        for (int i = 0; i < Red<N, S>::NCOMP; ++i) filtT_out[i] = comp(P, i);
+    }
+}
+
+// shared memory of k_filter_reduce_lti (offsets in scalars of S): the tile's
+// inputs staged by one bulk copy, the Gamma_i, the tree level constants, the
+// (b, eta) nodes, then the mbarrier of the copy
+template <int N, int M, typename S>
+struct LtiReduceSmem {
+    __host__ __device__ static constexpr int al(int x) { return (x + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int gam(int B, int K) { return al(B * K * M); }
+    __host__ __device__ static constexpr int lv(int B, int K) { return gam(B, K) + al(K * 2 * N * M); }
+    __host__ __device__ static constexpr int bq(int B, int K, int LB)
+    {
+        return lv(B, K) + (LB + 1) * FoldLayout<N, M, S>::LS;
+    }
+    __host__ __device__ static constexpr int bar(int B, int K, int LB) { return bq(B, K, LB) + al(2 * B * 2 * N); }
+    __host__ __device__ static constexpr size_t bytes(int B, int K, int LB)
+    {
+        return sizeof(S) * (size_t)bar(B, K, LB) + 16;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// phase 1, linear time-invariant model: per-thread folds and tile totals of
+// the full tiles 0 .. gridDim.x - 1 (every step before T), on the (b, eta)
+// parts only (lti_fold.cuh).  The tile's inputs arrive in shared memory by one
+// bulk copy; per thread K steps cost 2 N M multiply-adds and the tree 4 N^2
+// per node.  The per-thread (b, eta) go to thr_agg (2N components,
+// warp-interleaved), the tile totals to tile_agg.  A bulk copy that does not
+// complete within the poll limit is counted in ctx.stats[2] and the tile is
+// left unwritten.
+// ---------------------------------------------------------------------------
+template <int N, typename S, class Prod>
+__global__ void __launch_bounds__(128, 3)
+k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
+                    S* __restrict__ tile_agg, const S* __restrict__ fold, CombineCtx ctx)
+{
+    constexpr int M = Prod::W;
+    using FL = FoldLayout<N, M, S>;
+    using RS = LtiReduceSmem<N, M, S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S* sm = reinterpret_cast<S*>(smem_raw);
+    const int B = blockDim.x, t = threadIdx.x, LB = ilog2(B);
+    const long gthr = (long)blockIdx.x * B + t;
+    S* ys = sm;
+    S* gam = sm + RS::gam(B, K);
+    S* lv = sm + RS::lv(B, K);
+    S* bq = sm + RS::bq(B, K, LB);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + RS::bar(B, K, LB));
+    const unsigned bytes = (unsigned)(sizeof(S) * (size_t)B * K * M);
+    pdl_wait();
+    pdl_trigger();
+    if (t == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (t == 0) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(ys, prod.y + (long)blockIdx.x * B * K * M, bytes, bar);
+    }
+    for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
+    for (int q = t; q < (LB + 1) * FL::LS; q += B) lv[q] = fold[FL::oL + q];
+    bool ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
+    if (!__syncthreads_and(ok)) {
+        if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
+        mbar_wait_bounded(bar, 0, MBAR_POLLS);      // the copy may still be in flight
+        return;
+    }
+    // (b, eta) of this thread's K steps: offsets + sum_i Gamma_i y_{k0+i}
+    S v[2 * N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) { v[q] = __ldg(fold + FL::ob + q); v[N + q] = __ldg(fold + FL::oe + q); }
+    const S* yt = ys + t * K * M;
+#pragma unroll 2
+    for (int i = 0; i < K; ++i) {
+        S row[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) row[c] = yt[i * M + c];
+        const S* gi = gam + i * FL::GS;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                v[a] = fma(gi[a * M + c], row[c], v[a]);
+                v[N + a] = fma(gi[(N + a) * M + c], row[c], v[N + a]);
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * N; ++c) {
+        thr_agg[wi_idx(gthr, c, 2 * N)] = v[c];
+        bq[t * 2 * N + c] = v[c];
+    }
+    lti_tree_up<N, M, S>(bq, lv);
+    if (t == 0) {
+        using CL = CoopLayout<N, S>;
+        const S* cn = lv + LB * FL::LS;
+        const S* rq = bq + (2 * B - 2) * 2 * N;
+        Elem<N, S> root;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) root.A[i * N + j] = cn[CL::oA + i * CL::P + j];
+#pragma unroll
+            for (int j = i; j < N; ++j) {
+                root.C[Sym<N>::at(i, j)] = cn[CL::oC + i * CL::P + j];
+                root.J[Sym<N>::at(i, j)] = cn[CL::oJ + i * CL::P + j];
+            }
+            root.b[i] = rq[i];
+            root.eta[i] = rq[N + i];
+        }
+        aos_store(tile_agg, (long)blockIdx.x, root);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 1: per-thread fold and per-tile total of the filter elements
+// ---------------------------------------------------------------------------
 template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
@@ -349,6 +568,9 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S*
                S* __restrict__ tile_pref, S* __restrict__ final_out, S* __restrict__ xT_out,
                S* __restrict__ filtT_out, CombineCtx ctx)
 {
+    // nt tile totals -> prefixes tile_pref[0 .. nt] (tile_pref[nt]: after all
+    // of them); final_out (optional): the same value function with its
+    // minimiser and filter value
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
@@ -380,7 +602,9 @@ k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S*
         apply<N, S, false>(g, P, nullptr, nullptr, ctx);
     }
     if (t == B - 1) {
-        // P is now the value function at the end of the last tile, i.e. at x_T
+        // P is now the value function after the last total
+        aos_store(tile_pref, nt, P);
+        if (!final_out) return;
         aos_store(final_out, 0, P);
         S x[N];
         if (!red_argmin<N, S>(P, x) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
@@ -401,7 +625,9 @@ template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ thr_agg,
               const S* __restrict__ tile_pref, S* __restrict__ Eg, S* __restrict__ thr_aff,
-              S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx)
+              S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx,
+              const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
+              S* __restrict__ filtT_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -411,17 +637,9 @@ k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ th
     const long T = prod.T;
     constexpr int NA = Aff<N, S>::NCOMP;
 
-    {
-        Elem<N, S> G;
-        wi_load(thr_agg, gthr, G);
-        node_store(G, slot<N, S>(nodes, B, 0, t));
-    }
-    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    pdl_wait();                            // tile prefixes of the previous kernel
-    pdl_trigger();
-    Red<N, S> pin, X;
-    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
-    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
+    Red<N, S> X;
+    tile_thread_prefix<N, S>(prod, K, thr_agg, tile_pref, fold, nodes, nodes + tree_smem<N, S>(B) / sizeof(S),
+                             ctx, true, X);
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
@@ -461,6 +679,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ th
             for (int j = 0; j < N * N; ++j) comp_t.F[j] = F2[j];
         }
     }
+    write_final_if_last<N, S>(T, K, X, final_out, xT_out, filtT_out, ctx);
     wi_store(thr_aff, gthr, comp_t);
     __syncthreads();                       // the filter trees are done with shared memory
     node_store(comp_t, aslot<N, S>(nodes, B, 0, t));
@@ -480,7 +699,8 @@ template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_states(const __grid_constant__ Prod prod, int K, const S* __restrict__ thr_agg,
                 const S* __restrict__ tile_pref, S* __restrict__ filt_ws, S* __restrict__ filt_out,
-                CombineCtx ctx)
+                CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out,
+                S* __restrict__ xT_out, S* __restrict__ filtT_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -489,17 +709,9 @@ k_filter_states(const __grid_constant__ Prod prod, int K, const S* __restrict__ 
     const long k0 = gthr * K;
     const long T = prod.T;
     constexpr int NR = Red<N, S>::NCOMP;
-    {
-        Elem<N, S> G;
-        wi_load(thr_agg, gthr, G);
-        node_store(G, slot<N, S>(nodes, B, 0, t));
-    }
-    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    pdl_wait();
-    pdl_trigger();
-    Red<N, S> pin, X;
-    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
-    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
+    Red<N, S> X;
+    tile_thread_prefix<N, S>(prod, K, thr_agg, tile_pref, fold, nodes, nodes + tree_smem<N, S>(B) / sizeof(S),
+                             ctx, true, X);
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;
@@ -517,6 +729,7 @@ k_filter_states(const __grid_constant__ Prod prod, int K, const S* __restrict__ 
             apply<N, S, false>(e, X, nullptr, nullptr, ctx);
         }
     }
+    write_final_if_last<N, S>(T, K, X, final_out, xT_out, filtT_out, ctx);
 }
 
 // x = (S + L)^-1 (v + z) for symmetric positive definite S + L (Cholesky; a

@@ -28,6 +28,12 @@ struct Sym {
 template <typename S> MS_DEV S sabs(S x) { return fabs(x); }
 template <> MS_DEV float sabs<float>(float x) { return fabsf(x); }
 
+// reciprocal of a Gauss-Jordan pivot: the hardware approximation in FP32
+// (within 2 ulp; the pivot test and the condition estimate guard the
+// elimination), the correctly rounded quotient in FP64
+template <typename S> MS_DEV S pivot_rcp(S p) { return S(1) / p; }
+template <> MS_DEV float pivot_rcp<float>(float p) { return __fdividef(1.0f, p); }
+
 // c = a b  (N x N)
 template <int N, typename S>
 MS_DEV void mm(const S* a, const S* b, S* c)
@@ -192,7 +198,7 @@ MS_DEV bool inv_diag_pivot(S* X, S* Y, S tau)
             below = a > below ? a : below;
         }
         ok = ok && (sabs(p) > tau * below) && (p != S(0));
-        const S ip = S(1) / p;
+        const S ip = pivot_rcp(p);
 #pragma unroll
         for (int j = c + 1; j < N; ++j) X[c * N + j] *= ip;
 #pragma unroll

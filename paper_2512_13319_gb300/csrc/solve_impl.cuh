@@ -13,6 +13,13 @@ namespace mapk {
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
+inline int ilog2_host(int x)
+{
+    int l = 0;
+    while ((2 << l) <= x) ++l;
+    return l;
+}
+
 template <int N, typename S>
 struct Layout {
     size_t thr_agg, tile_agg, tile_pref, fin, Eg, thr_aff, tile_aff, tile_xend;
@@ -26,7 +33,7 @@ struct Layout {
         size_t o = 0;
         l.thr_agg = o;   o = align_up(o + sizeof(S) * E::NCOMP * nthr);
         l.tile_agg = o;  o = align_up(o + sizeof(S) * E::NCOMP * nt);
-        l.tile_pref = o; o = align_up(o + sizeof(S) * R::NCOMP * nt);
+        l.tile_pref = o; o = align_up(o + sizeof(S) * R::NCOMP * (nt + 1));
         l.fin = o;       o = align_up(o + sizeof(S) * R::NCOMP);
         l.Eg = o;        o = align_up(o + sizeof(S) * A::NCOMP * Tpad);
         l.thr_aff = o;   o = align_up(o + sizeof(S) * A::NCOMP * nthr);
@@ -127,7 +134,7 @@ int rts_resident_blocks(int B)
 // Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
 template <int N, typename S, class Prod>
 map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st,
-                   bool dev_prior = false)
+                   bool dev_prior = false, const S* fold = nullptr)
 {
     using R = Red<N, S>;
     const int B = h.B, nt = h.nt;
@@ -145,9 +152,15 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const long T = h.T;
     S* xT = x_out + T * N;
 
-    const size_t sh_reduce = tree_smem<N, S>(B);
-    const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B));
     const int K = h.K;
+    // linear-fold mode (fold != nullptr): the reduce kernel takes the full
+    // tiles 0..nt-2, the down-sweep's last CTA folds the last tile itself and
+    // writes the value function at x_T (see tile_thread_prefix)
+    const bool lti = fold != nullptr;
+    const int nagg = lti ? nt - 1 : nt;
+    const size_t sh_reduce = tree_smem<N, S>(B);
+    const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B)) +
+                           (lti ? sizeof(S) * (size_t)K * 2 * N * Prod::W : 0);
     const size_t sh_rts = rts_smem<N, S>(B, K);
     const int bt_f = pick_tile_scan_threads(nt, [](int b) { return tree_smem<N, S>(b); });
     const int bt_a = pick_tile_scan_threads(nt, [](int b) { return aff_tree_smem<N, S>(b); });
@@ -174,14 +187,31 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     mark();
     // dev_prior: the prior comes from the producer's terminal() (device data)
     S* term = dev_prior ? reinterpret_cast<S*>(h.ws + L.term) : nullptr;
-    launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg,
-           term, ctx);
+    S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
+    bool first = true;                     // no PDL edge to whatever ran before the solve
+    if (!lti) {
+        launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx);
+        first = false;
+    } else if (nagg > 0) {
+        if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+            const int LB = ilog2_host(B);
+            const size_t sh = LtiReduceSmem<N, Prod::W, S>::bytes(B, K, LB);
+            static std::once_flag once_lti;
+            cudaError_t e1 = cudaSuccess;
+            std::call_once(once_lti, [&] { e1 = allow_smem(k_filter_reduce_lti<N, S, Prod>, 200 * 1024); });
+            if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaFuncSetAttribute");
+            launch(k_filter_reduce_lti<N, S, Prod>, nagg, B, sh, st, false, prod, K, thr_agg, tile_agg, fold, ctx);
+            first = false;
+        }
+    }
     mark();
-    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
-           (const S*)term, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
+    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl && !first, (const S*)tile_agg, nagg,
+           prior_of<N, S>(h), (const S*)term, tile_pref, lti ? (S*)nullptr : fin, lti ? (S*)nullptr : xT,
+           lti ? (S*)nullptr : filtT, ctx);
     mark();
     launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl, prod, K, (const S*)thr_agg,
-           (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx);
+           (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx, fold, lti ? fin : (S*)nullptr,
+           lti ? xT : (S*)nullptr, lti ? filtT : (S*)nullptr);
     mark();
     launch(k_affine_tiles<N, S>, 1, bt_a, sh_ta, st, pdl, (const S*)tile_aff, nt, (const S*)xT, tile_xend);
     mark();
@@ -198,7 +228,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
 // and the per-step combination x*_k = (S_k + Lam_k)^-1 (v_k + zeta_k).
 template <int N, typename S, class Prod, class RProd>
 map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_out, S* filt_out,
-                  cudaStream_t st)
+                  cudaStream_t st, const S* fold = nullptr)
 {
     using R = Red<N, S>;
     const int K = h.K;
@@ -216,7 +246,9 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     const long T = h.T;
     S* xT = x_out + T * N;
+    const bool lti = fold != nullptr;          // forward scan in linear-fold mode (see run_rts)
     const size_t sh_tree = tree_smem<N, S>(B);
+    const size_t sh_states = sh_tree + (lti ? sizeof(S) * (size_t)K * 2 * N * Prod::W : 0);
     const size_t sh_tfd = std::max(sh_tree, sizeof(S) * (size_t)B * K * N);   // k_tf_down stages the states
     const int bt_f = pick_tile_scan_threads(nt, [](int b) { return tree_smem<N, S>(b); });
     const size_t sh_tf = tree_smem<N, S>(bt_f);
@@ -237,14 +269,32 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
-    launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg,
-           (S*)nullptr, ctx);
+    S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
+    const int nagg = lti ? nt - 1 : nt;
+    bool first = true;
+    if (!lti) {
+        launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg, (S*)nullptr,
+               ctx);
+        first = false;
+    } else if (nagg > 0) {
+        if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+            const size_t sh = LtiReduceSmem<N, Prod::W, S>::bytes(B, K, ilog2_host(B));
+            static std::once_flag once_lti;
+            cudaError_t e1 = cudaSuccess;
+            std::call_once(once_lti, [&] { e1 = allow_smem(k_filter_reduce_lti<N, S, Prod>, 200 * 1024); });
+            if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaFuncSetAttribute");
+            launch(k_filter_reduce_lti<N, S, Prod>, nagg, B, sh, st, false, fprod, K, thr_agg, tile_agg, fold, ctx);
+            first = false;
+        }
+    }
     mark();
-    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
-           (const S*)nullptr, tile_pref, fin, xT, filt_out ? filt_out + T * R::NCOMP : (S*)nullptr, ctx);
+    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl && !first, (const S*)tile_agg, nagg,
+           prior_of<N, S>(h), (const S*)nullptr, tile_pref, lti ? (S*)nullptr : fin, lti ? (S*)nullptr : xT,
+           lti ? (S*)nullptr : filtT, ctx);
     mark();
-    launch(k_filter_states<N, S, Prod>, nt, B, sh_tree, st, pdl, fprod, K, (const S*)thr_agg,
-           (const S*)tile_pref, filt_ws, filt_out, ctx);
+    launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl, fprod, K, (const S*)thr_agg,
+           (const S*)tile_pref, filt_ws, filt_out, ctx, fold, lti ? fin : (S*)nullptr, lti ? xT : (S*)nullptr,
+           lti ? filtT : (S*)nullptr);
     mark();
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
@@ -291,9 +341,38 @@ FlipParams<N, M, S> flip_params(const map_smoother& h)
     return p;
 }
 
+// constants of the linear per-thread fold (lti_fold.cuh) for the current K,
+// recomputed on `st` after a change of K or of the model; nullptr when K is
+// beyond the fold's range (the kernels then fold step by step)
+template <int N, int M, typename S>
+map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
+{
+    using FL = FoldLayout<N, M, S>;
+    *out = nullptr;
+    if constexpr (N > 6) return MAP_OK;        // the kernels take the linear fold for N <= 6
+    int LB = 0;
+    while ((2 << LB) <= h.B) ++LB;
+    if (!h.d_fold || h.K > FL::KMAX || LB > FL::LMAX || sizeof(S) * (size_t)FL::TOTAL > fold_bytes(N, M, sizeof(S)) ||
+        LtiTreeSmem<N, M, S>::end(h.B, LB) > 2 * h.B * CoopLayout<N, S>::NE ||
+        LtiReduceSmem<N, M, S>::bytes(h.B, h.K, LB) > 200 * 1024)
+        return MAP_OK;
+    if (h.fold_K != h.K || h.fold_B != h.B) {
+        k_lti_fold<N, M, S><<<1, FL::KMAX, 0, st>>>(lti_params<N, M, double>(h), h.K, LB,
+                                                    static_cast<S*>(h.d_fold));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
+        h.fold_K = h.K;
+        h.fold_B = h.B;
+    }
+    *out = static_cast<const S*>(h.d_fold);
+    return MAP_OK;
+}
+
 template <int N, int M, typename S>
 map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st)
 {
+    const S* fold = nullptr;
+    if (map_status s = lti_fold_consts<N, M, S>(h, st, &fold); s != MAP_OK) return s;
     LtiProducer<N, M, S> prod;
     prod.y = static_cast<const S*>(y);
     prod.T = h.T;
@@ -304,9 +383,9 @@ map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_
         rprod.T = h.T;
         rprod.Tpad = h.Tpad;
         rprod.p = flip_params<N, M, S>(h);
-        return run_tf<N, S>(h, prod, rprod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
+        return run_tf<N, S>(h, prod, rprod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, fold);
     }
-    return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
+    return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, false, fold);
 }
 
 template <int N, int M, typename S>

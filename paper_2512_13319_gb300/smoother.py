@@ -109,7 +109,8 @@ class MapSmoother:
         return dict(zip(B.PHASES, B.map_smoother_phase_times(self._h)))
 
     def stats(self, reset=False, stream=None):
-        """(combines recomputed in FP64, singular pivots) since create or the last reset."""
+        """(combines recomputed in FP64, singular pivots, bulk copies whose bounded
+        wait gave up) since create or the last reset."""
         return B.map_smoother_stats(self._h, reset, self._stream(stream))
 
     def close(self):
