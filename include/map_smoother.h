@@ -176,14 +176,17 @@ map_status map_smoother_stats(map_smoother* h, unsigned long long out[3], int re
 /*
  * Per-phase device timing.  With profiling on, every solve records CUDA events
  * on its stream between its kernel launches; map_smoother_phase_times then
- * returns the durations (ms) of the phases of the last solve, in launch order:
+ * returns the durations (ms) of the phases of the last solve, in launch order.
+ * For the RTS smoother:
  *   0 filter_reduce  per-thread folds and tile totals of the elements
- *   1 filter_tiles   scan of the tile totals (one CTA)
- *   2 filter_down    per-step filter values, closed-loop maps, their folds
- *   3 affine_tiles   backward scan of the tile maps (one CTA)
- *   4 rts_down       per-step smoothed states
- * (for nonlinear models: those of the last iteration).  phase_times
- * synchronises the stream of the last solve; *n_out receives the count.
+ *   1 filter_down    per-tile prefix from the totals before the tile, per-step
+ *                    filter values, closed-loop maps and their folds
+ *   2 rts_down       per-tile end state from the maps after the tile, per-step
+ *                    smoothed states
+ * (for nonlinear models: those of the last iteration); for the two-filter
+ * smoother: forward reduce, forward states, backward reduce, backward
+ * combination.  phase_times synchronises the stream of the last solve;
+ * *n_out receives the count.
  */
 map_status map_smoother_profile(map_smoother* h, int enable);
 map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int* n_out);

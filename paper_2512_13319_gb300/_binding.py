@@ -156,7 +156,8 @@ def map_smoother_stats(h, reset=False, stream=None):
     return int(out[0]), int(out[1]), int(out[2])
 
 
-PHASES = ("filter_reduce", "filter_tiles", "filter_down", "affine_tiles", "rts_down")
+PHASES = ("filter_reduce", "filter_down", "rts_down")
+PHASES_TWO_FILTER = ("forward_reduce", "forward_states", "backward_reduce", "backward_combine")
 
 
 def map_smoother_profile(h, enable=True):

@@ -52,7 +52,12 @@ struct FoldLayout {
     static constexpr int LN = 3 * N * CL::P;                // (A_d, C_d, J_d) node part
     static constexpr int oX = LN, oY = LN + N * N, oZ = LN + 2 * N * N, oW = LN + 3 * N * N;
     static constexpr int LS = (LN + 4 * N * N + 3) / 4 * 4;
-    static constexpr int TOTAL = oL + (LMAX + 1) * LS;
+    // folds of r = 1 .. KMAX-1 steps (a thread that reaches T): per r the
+    // constants A, C, J, b0, eta0 (HS scalars, packed as above) then Gamma_0..r-1
+    static constexpr int oP = oL + (LMAX + 1) * LS;
+    static constexpr int HS = (N * N + 2 * NS + 2 * N + 3) / 4 * 4;
+    __host__ __device__ static constexpr int poff(int r) { return oP + (r - 1) * HS + GS * (r - 1) * r / 2; }
+    static constexpr int TOTAL = oP + (KMAX - 1) * HS + GS * (KMAX - 1) * KMAX / 2;
 };
 
 // Plan-time helpers of k_lti_fold (FP64, plain loops: run once per model and
@@ -175,6 +180,30 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
     double gb[N * M], ge[N * M];                  // Gamma_j (b rows, eta rows)
 #pragma unroll 1
     for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = j == 0 ? Gm[q] : 0.0; }
+    // the r-step fold (r < K): constants by thread 0, Gamma_j by thread j < r
+    auto write_partial = [&](int r) {
+        S* pb = out + FL::poff(r);
+        if (j == 0) {
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) pb[FL::oA + q] = S(Ac[q]);
+#pragma unroll 1
+            for (int a = 0; a < N; ++a) {
+#pragma unroll 1
+                for (int c = a; c < N; ++c) {
+                    pb[FL::oC + Sym<N>::at(a, c)] = S(0.5 * (Cc[a * N + c] + Cc[c * N + a]));
+                    pb[FL::oJ + Sym<N>::at(a, c)] = S(0.5 * (Jc[a * N + c] + Jc[c * N + a]));
+                }
+                pb[FL::ob + a] = S(ob[a]);
+                pb[FL::oe + a] = S(oe[a]);
+            }
+        }
+        if (j < r) {
+            S* g = pb + FL::HS + j * FL::GS;
+#pragma unroll 1
+            for (int q = 0; q < N * M; ++q) { g[q] = S(gb[q]); g[N * M + q] = S(ge[q]); }
+        }
+    };
+    if (K > 1) write_partial(1);
 #pragma unroll 1
     for (int i = 1; i < K; ++i) {
         if (j == 0) {
@@ -228,6 +257,7 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
             for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = Gm[q]; }
         }
         __syncthreads();
+        if (i + 1 < K) write_partial(i + 1);
     }
     if (j < K) {
         S* g = out + FL::oG + j * FL::GS;
@@ -327,6 +357,37 @@ __device__ __forceinline__ void lti_linear_fold(const Prod& prod, const S* __res
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) { bq[q] = ab[q]; bq[N + q] = ae[q]; }
+}
+
+// The element of a thread whose first r < K steps are before T (the rest are
+// identity padding): the r-step fold from its constants, read from global
+// memory (one thread per solve takes this path)
+template <int N, typename S, class Prod>
+__device__ __forceinline__ void lti_partial_fold_elem(const Prod& prod, const S* __restrict__ fold, int r, long k0,
+                                                      Elem<N, S>& G)
+{
+    constexpr int M = Prod::W;
+    using FL = FoldLayout<N, M, S>;
+    const S* pb = fold + FL::poff(r);
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) G.A[q] = pb[FL::oA + q];
+#pragma unroll
+    for (int q = 0; q < Sym<N>::SZ; ++q) { G.C[q] = pb[FL::oC + q]; G.J[q] = pb[FL::oJ + q]; }
+#pragma unroll
+    for (int q = 0; q < N; ++q) { G.b[q] = pb[FL::ob + q]; G.eta[q] = pb[FL::oe + q]; }
+#pragma unroll 1
+    for (int i = 0; i < r; ++i) {
+        S row[M];
+        prod.load1(k0 + i, row);
+        const S* g = pb + FL::HS + i * FL::GS;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                G.b[a] = fma(g[a * M + c], row[c], G.b[a]);
+                G.eta[a] = fma(g[(N + a) * M + c], row[c], G.eta[a]);
+            }
+    }
 }
 
 // The full element of one thread's K full steps (constants + linear fold)

@@ -1,14 +1,16 @@
-// Blocked three-phase associative scans (reduce / scan of tile totals /
-// down-sweep) for the filter (Section 3.3-3.4, Eq. 32) and the RTS pass
-// (Section 3.5 and 4.3, Eq. 40-42).
+// Blocked associative scans (reduce, then down-sweep) for the filter
+// (Section 3.3-3.4, Eq. 32) and the RTS pass (Section 3.5 and 4.3, Eq. 40-42).
 //
 // Work decomposition.  A tile of L = B*K consecutive steps is one CTA of B
 // threads; thread t owns steps [k0, k0+K), k0 = (tile*B + t)*K, and builds
 // its elements in registers from the per-step inputs.  Within a CTA the
 // per-thread partials are scanned with a work-efficient up/down sweep
-// (Blelloch) through shared memory; across tiles a single CTA scans the tile
-// totals.  There are no inter-CTA waits anywhere: every dependency between
-// tiles is a kernel boundary.
+// (Blelloch) through shared memory.  Across tiles, every CTA of a down-sweep
+// reduces the totals of the tiles before it (for the filter) or after it (for
+// the RTS pass) itself: at most ceil(tile / B) totals per thread and one
+// sub-warp tree, all CTAs at once, instead of a scan of the totals by one CTA
+// between the kernels.  There are no inter-CTA waits anywhere: every
+// dependency between tiles is a kernel boundary.
 //
 // Orientation.  Elements are stored in original-time order.  The filter value
 // function of x_k, V(., tau_{T-k}) = e_{k-1} (x) ... (x) e_0 (x) a_T, is the
@@ -294,95 +296,169 @@ __device__ __forceinline__ S* scratch_of(S* nodes)
 }
 
 // ---------------------------------------------------------------------------
-// phase 1: per-thread fold and per-tile total of the filter elements
+// tile prefixes and suffixes, computed by each CTA of a down-sweep
 // ---------------------------------------------------------------------------
-// a tile (CTA) whose B*K steps all lie before T: with a linear-fold constant
-// block its tree runs on the (b, eta) parts only (lti_fold.cuh)
-__device__ __forceinline__ bool lti_full_tile(long T, int K)
+// Value function before tile `tile` (returned in thread 0): thread t folds a
+// contiguous run of at most ceil(tile / B) of the totals of tiles 0..tile-1,
+// the runs are reduced with the sub-warp tree (empty runs are the identity
+// element, neutral on both sides of the combine) and the total is applied to
+// the prior.  Uses the element-tree area of `nodes`; ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void tile_prefix_of(const S* __restrict__ tile_agg, int tile, const Red<N, S>& prior,
+                                               S* nodes, const CombineCtx& ctx, Red<N, S>& out)
 {
-    return (long)(blockIdx.x + 1) * blockDim.x * K <= T;
+    const int B = blockDim.x, t = threadIdx.x;
+    if (tile == 0) {
+        out = prior;
+        return;
+    }
+    const int per = (tile + B - 1) / B;
+    const int first = min(tile, t * per), last = min(tile, first + per);
+    Elem<N, S> F;
+    if (first < last) {
+        aos_load(tile_agg, first, F);
+        for (int i = first + 1; i < last; ++i) {
+            Elem<N, S> g;
+            aos_load(tile_agg, i, g);
+            combine<N, S>(g, F, F, ctx);
+        }
+    } else {
+        set_identity(F);
+    }
+    node_store(F, slot<N, S>(nodes, B, 0, t));
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    if (t == 0) {
+        Elem<N, S> root;
+        node_load(slot<N, S>(nodes, B, ilog2(B), 0), root);
+        Red<N, S> P = prior;
+        apply<N, S, false>(root, P, nullptr, nullptr, ctx);
+        out = P;
+    }
+    __syncthreads();
+}
+
+// State at the end of tile `tile`, written by thread 0 to the N scalars at
+// `xe` (shared memory outside the affine-tree area): the closed-loop maps of
+// tiles tile+1..nt-1 composed (thread runs, then the affine tree; a map takes
+// the state at the end of its steps to the state at their start) and applied
+// to x_T.  Uses the affine-tree area of `nodes`; ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void tile_suffix_state(const S* __restrict__ tile_aff, int tile, int nt,
+                                                  const S* __restrict__ xT, S* nodes, S* xe)
+{
+    const int B = blockDim.x, t = threadIdx.x;
+    const int cnt = nt - 1 - tile;
+    if (cnt == 0) {
+        if (t == 0)
+            for (int i = 0; i < N; ++i) xe[i] = xT[i];
+        __syncthreads();
+        return;
+    }
+    const int per = (cnt + B - 1) / B;
+    const int first = tile + 1 + min(cnt, t * per), last = min(nt, first + per);
+    Aff<N, S> H;
+    set_identity(H);
+    for (int i = last - 1; i >= first; --i) {      // H = a_first o ... o a_last
+        Aff<N, S> a;
+        aos_load(tile_aff, i, a);
+        compose<N, S>(a, H, H);
+    }
+    node_store(H, aslot<N, S>(nodes, B, 0, t));
+    coop_aff_up<N, S>(nodes);
+    if (t == 0) {
+        Aff<N, S> root;
+        node_load(aslot<N, S>(nodes, B, ilog2(B), 0), root);
+        S x[N], y[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = xT[i];
+        affine_apply<N, S>(root, x, y);
+#pragma unroll
+        for (int i = 0; i < N; ++i) xe[i] = y[i];
+    }
+    __syncthreads();
+}
+
+// prior of a scan: the model's (v0, S0), or the terminal value function that a
+// reversed scan's reduce kernel wrote to prior_dev
+template <int N, typename S>
+__device__ __forceinline__ Red<N, S> scan_prior(const Red<N, S>& prior, const S* __restrict__ prior_dev)
+{
+    Red<N, S> p = prior;
+    if (prior_dev) aos_load(prior_dev, 0, p);
+    return p;
 }
 
 // Exclusive prefix (value function before the thread's first step) of every
-// thread of a tile, from the per-thread aggregates thr_agg of the reduce
-// kernel and the tile prefix tile_pref of the tile scan: the tile's up-sweep,
-// the wait for the previous kernel (PDL), and the down-sweep.
+// thread of a tile from the tile's prefix `pin` (valid in thread 0): the
+// tile's up-sweep over the per-thread aggregates and the down-sweep.
 // With linear-fold constants (fold != nullptr, lti_fold.cuh) the reduce
-// kernel has covered the full tiles 0 .. gridDim.x - 2 with (b, eta) parts
-// only, and their trees run on those; the last tile's per-thread folds are
-// formed here (linear fold for threads whose K steps are all before T, the
-// step-by-step fold for the one that reaches T, the identity past it).
-// gam: shared memory for the Gamma_i (behind the element tree).
+// kernel has left (b, eta) aggregates (2N components) for the full tiles
+// 0..gridDim.x-2 and their trees run on those; the last tile's aggregates are
+// full elements (written by the down-sweep's last CTA before its wait).
 template <int N, typename S, class Prod>
-__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int K, const S* __restrict__ thr_agg,
-                                                   const S* __restrict__ tile_pref, const S* __restrict__ fold,
-                                                   S* nodes, S* gam, const CombineCtx& ctx, bool trigger,
-                                                   Red<N, S>& X)
+__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, const S* __restrict__ thr_agg,
+                                                   const Red<N, S>& pin, const S* __restrict__ fold, S* nodes,
+                                                   const CombineCtx& ctx, Red<N, S>& X)
 {
     const int B = blockDim.x, t = threadIdx.x;
     const long gthr = (long)blockIdx.x * B + t;
-    Elem<N, S> G;
-    bool have_leaf = false;
     if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        if (fold) {
+        if (fold && blockIdx.x + 1 < gridDim.x) {
             using FL = FoldLayout<N, Prod::W, S>;
-            if (blockIdx.x + 1 < gridDim.x) {
-                using TS = LtiTreeSmem<N, Prod::W, S>;
-                const int LB = ilog2(B);
-                S* pre = nodes + TS::pre(B);
-                S* bq = nodes + TS::bq(B);
-                S* lv = nodes + TS::lv(B);
-                for (int q = t; q < (LB + 1) * FL::LS; q += B) lv[q] = fold[FL::oL + q];
+            using TS = LtiTreeSmem<N, Prod::W, S>;
+            const int LB = ilog2(B);
+            S* pre = nodes + TS::pre(B);
+            S* bq = nodes + TS::bq(B);
+            S* lv = nodes + TS::lv(B);
+            for (int q = t; q < (LB + 1) * FL::LS; q += B) lv[q] = fold[FL::oL + q];
 #pragma unroll
-                for (int c = 0; c < 2 * N; ++c) bq[t * 2 * N + c] = thr_agg[wi_idx(gthr, c, 2 * N)];
-                lti_tree_up<N, Prod::W, S>(bq, lv);
-                pdl_wait();                // tile prefixes of the previous kernel
-                if (trigger) pdl_trigger();
-                if (t == 0) {
-                    Red<N, S> pin;
-                    aos_load(tile_pref, (long)blockIdx.x, pin);
-                    node_store(pin, pre + (2 * B - 2) * CoopLayout<N, S>::NR);
-                }
-                lti_tree_down<N, Prod::W, S>(bq, lv, pre, scratch_of<N, S>(nodes), ctx, X);
-                return;
-            }
-            // last tile
-            for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
-            __syncthreads();
-            const long k0 = gthr * K;
-            const long r = prod.T - k0;
-            if (r >= K) {
-                lti_fold_elem<N, S>(prod, fold, gam, K, k0, G);
-            } else if (r <= 0) {
-                set_identity(G);
-            } else {
-                S row[Prod::W];
-                prod.load1(k0, row);
-                prod.make(k0, row, G);
-#pragma unroll 1
-                for (int i = 1; i < r; ++i) {
-                    prod.load1(k0 + i, row);
-                    Elem<N, S> e;
-                    prod.make(k0 + i, row, e);
-                    combine<N, S>(e, G, G, ctx);
-                }
-            }
-            have_leaf = true;
+            for (int c = 0; c < 2 * N; ++c) bq[t * 2 * N + c] = thr_agg[wi_idx(gthr, c, 2 * N)];
+            if (t == 0) node_store(pin, pre + (2 * B - 2) * CoopLayout<N, S>::NR);
+            lti_tree_up<N, Prod::W, S>(bq, lv);
+            lti_tree_down<N, Prod::W, S>(bq, lv, pre, scratch_of<N, S>(nodes), ctx, X);
+            return;
         }
     }
-    if (!have_leaf) wi_load(thr_agg, gthr, G);
-    node_store(G, slot<N, S>(nodes, B, 0, t));
+    {
+        Elem<N, S> G;
+        wi_load(thr_agg, gthr, G);
+        node_store(G, slot<N, S>(nodes, B, 0, t));
+    }
     coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    pdl_wait();                            // tile prefixes of the previous kernel
-    if (trigger) pdl_trigger();
-    Red<N, S> pin;
-    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
     coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
 }
 
+// Linear-fold mode, last tile: the per-thread aggregates, written to thr_agg
+// as full elements (the reduce kernel does not cover this tile).  A thread
+// whose K steps are before T takes the K-step linear fold, the one that
+// reaches T the r-step fold, threads past T the identity.  gam: shared memory
+// for the Gamma_i of the K-step fold.
+template <int N, typename S, class Prod>
+__device__ __forceinline__ void lti_last_tile_leaves(const Prod& prod, int K, const S* __restrict__ fold, S* gam,
+                                                     S* __restrict__ thr_agg)
+{
+    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+        using FL = FoldLayout<N, Prod::W, S>;
+        const int B = blockDim.x, t = threadIdx.x;
+        const long gthr = (long)blockIdx.x * B + t;
+        for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
+        __syncthreads();
+        const long k0 = gthr * K;
+        const long r = prod.T - k0;
+        Elem<N, S> G;
+        if (r >= K)
+            lti_fold_elem<N, S>(prod, fold, gam, K, k0, G);
+        else if (r <= 0)
+            set_identity(G);
+        else
+            lti_partial_fold_elem<N, S>(prod, fold, (int)r, k0, G);
+        wi_store(thr_agg, gthr, G);
+        __syncthreads();
+    }
+}
+
 // The thread of the last tile that holds step T-1 writes the value function
-// at x_T (after its steps), its minimiser x_T and, if asked, its filter value
-// (linear-fold mode, where the tile scan does not see the last tile).
+// at x_T (after its steps), its minimiser x_T and, if asked, its filter value.
 template <int N, typename S>
 __device__ __forceinline__ void write_final_if_last(long T, int K, const Red<N, S>& X, S* final_out,
                                                     S* xT_out, S* filtT_out, const CombineCtx& ctx)
@@ -556,77 +632,15 @@ k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
 }
 
 // ---------------------------------------------------------------------------
-// phase 2: one CTA scans the tile totals from the prior (Eq. 31 a_T).  Each
-// thread folds `per` consecutive tile totals; the per-thread totals are
-// scanned with the same sub-warp up/down sweep as the tile trees, which gives
-// every thread the value function before its first tile; each thread then
-// walks its tiles with the one-variable combine.
-// ---------------------------------------------------------------------------
-template <int N, typename S>
-__global__ void __launch_bounds__(256)
-k_filter_tiles(const S* __restrict__ tile_agg, int nt, Red<N, S> prior, const S* __restrict__ prior_dev,
-               S* __restrict__ tile_pref, S* __restrict__ final_out, S* __restrict__ xT_out,
-               S* __restrict__ filtT_out, CombineCtx ctx)
-{
-    // nt tile totals -> prefixes tile_pref[0 .. nt] (tile_pref[nt]: after all
-    // of them); final_out (optional): the same value function with its
-    // minimiser and filter value
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* nodes = reinterpret_cast<S*>(smem_raw);
-    const int B = blockDim.x, t = threadIdx.x;
-    const int per = (nt + B - 1) / B;
-    const int first = min(nt, t * per), last = min(nt, first + per);
-    pdl_wait();
-    pdl_trigger();
-    if (prior_dev && t == 0) aos_load(prior_dev, 0, prior);   // terminal value function of a reversed scan
-
-    Elem<N, S> F;
-    if (first < last) {
-        aos_load(tile_agg, first, F);
-        for (int i = first + 1; i < last; ++i) {
-            Elem<N, S> g;
-            aos_load(tile_agg, i, g);
-            combine<N, S>(g, F, F, ctx);
-        }
-    } else {
-        set_identity(F);
-    }
-    node_store(F, slot<N, S>(nodes, B, 0, t));
-    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    Red<N, S> P;
-    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), prior, ctx, P);
-    for (int i = first; i < last; ++i) {
-        aos_store(tile_pref, i, P);
-        Elem<N, S> g;
-        aos_load(tile_agg, i, g);
-        apply<N, S, false>(g, P, nullptr, nullptr, ctx);
-    }
-    if (t == B - 1) {
-        // P is now the value function after the last total
-        aos_store(tile_pref, nt, P);
-        if (!final_out) return;
-        aos_store(final_out, 0, P);
-        S x[N];
-        if (!red_argmin<N, S>(P, x) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
-#pragma unroll
-        for (int i = 0; i < N; ++i) xT_out[i] = x[i];
-        if (filtT_out) {
-#pragma unroll
-            for (int i = 0; i < Red<N, S>::NCOMP; ++i) filtT_out[i] = comp(P, i);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// phase 3: per-step filter values, closed-loop maps and their per-thread /
-// per-tile compositions
+// phase 2: per-step filter values, closed-loop maps and their per-thread /
+// per-tile compositions; the last CTA writes the value function at x_T
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ thr_agg,
-              const S* __restrict__ tile_pref, S* __restrict__ Eg, S* __restrict__ thr_aff,
-              S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx,
-              const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
+k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
+              const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
+              S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
+              CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
               S* __restrict__ filtT_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -637,9 +651,13 @@ k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ th
     const long T = prod.T;
     constexpr int NA = Aff<N, S>::NCOMP;
 
-    Red<N, S> X;
-    tile_thread_prefix<N, S>(prod, K, thr_agg, tile_pref, fold, nodes, nodes + tree_smem<N, S>(B) / sizeof(S),
-                             ctx, true, X);
+    if (fold && blockIdx.x + 1 == gridDim.x)
+        lti_last_tile_leaves<N, S>(prod, K, fold, nodes + tree_smem<N, S>(B) / sizeof(S), thr_agg);
+    pdl_wait();                            // totals and aggregates of the reduce kernel
+    pdl_trigger();
+    Red<N, S> pin, X;
+    tile_prefix_of<N, S>(tile_agg, blockIdx.x, scan_prior(prior, prior_dev), nodes, ctx, pin);
+    tile_thread_prefix<N, S>(prod, thr_agg, pin, fold, nodes, ctx, X);
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
@@ -692,15 +710,15 @@ k_filter_down(const __grid_constant__ Prod prod, int K, const S* __restrict__ th
 }
 
 // ---------------------------------------------------------------------------
-// phase 3 of the two-filter smoother, forward part: per-step filter value
+// phase 2 of the two-filter smoother, forward part: per-step filter value
 // functions (S_k, v_k), stored per thread and step (warp-interleaved)
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_filter_states(const __grid_constant__ Prod prod, int K, const S* __restrict__ thr_agg,
-                const S* __restrict__ tile_pref, S* __restrict__ filt_ws, S* __restrict__ filt_out,
-                CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out,
-                S* __restrict__ xT_out, S* __restrict__ filtT_out)
+k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
+                const S* __restrict__ tile_agg, const Red<N, S> prior, S* __restrict__ filt_ws,
+                S* __restrict__ filt_out, CombineCtx ctx, const S* __restrict__ fold,
+                S* __restrict__ final_out, S* __restrict__ xT_out, S* __restrict__ filtT_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -709,9 +727,13 @@ k_filter_states(const __grid_constant__ Prod prod, int K, const S* __restrict__ 
     const long k0 = gthr * K;
     const long T = prod.T;
     constexpr int NR = Red<N, S>::NCOMP;
-    Red<N, S> X;
-    tile_thread_prefix<N, S>(prod, K, thr_agg, tile_pref, fold, nodes, nodes + tree_smem<N, S>(B) / sizeof(S),
-                             ctx, true, X);
+    if (fold && blockIdx.x + 1 == gridDim.x)
+        lti_last_tile_leaves<N, S>(prod, K, fold, nodes + tree_smem<N, S>(B) / sizeof(S), thr_agg);
+    pdl_wait();
+    pdl_trigger();
+    Red<N, S> pin, X;
+    tile_prefix_of<N, S>(tile_agg, blockIdx.x, prior, nodes, ctx, pin);
+    tile_thread_prefix<N, S>(prod, thr_agg, pin, fold, nodes, ctx, X);
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;
@@ -787,17 +809,18 @@ __device__ __forceinline__ void spd_combine_solve(const Red<N, S>& a, const Red<
 }
 
 // ---------------------------------------------------------------------------
-// phase 3 of the two-filter smoother, backward part: per-step backward
+// phase 2 of the two-filter smoother, backward part: per-step backward
 // information (Lam_k, zeta_k) on x_k from y_{k+1}..y_T, combined with the
 // forward filter: x*_k = (S_k + Lam_k)^-1 (v_k + zeta_k)  (Eq. 43 in
 // information form).  Thread g' of this reversed scan covers the steps of
-// forward thread g = nthr - 1 - g'.
+// forward thread g = nthr - 1 - g'; the scan's prior is the terminal value
+// function that its reduce kernel wrote to prior_dev.
 // ---------------------------------------------------------------------------
 template <int N, typename S, class RProd>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_tf_down(const __grid_constant__ RProd prod, int K, const S* __restrict__ thr_agg,
-          const S* __restrict__ tile_pref, const S* __restrict__ filt_ws, S* __restrict__ x_out,
-          CombineCtx ctx)
+          const S* __restrict__ tile_agg, const S* __restrict__ prior_dev, const S* __restrict__ filt_ws,
+          S* __restrict__ x_out, CombineCtx ctx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -808,15 +831,17 @@ k_tf_down(const __grid_constant__ RProd prod, int K, const S* __restrict__ thr_a
     const long T = prod.T, Tpad = prod.Tpad;
     const long gf = nthr - 1 - gthr;            // forward thread with the same steps
     constexpr int NR = Red<N, S>::NCOMP;
+    pdl_wait();
+    Red<N, S> pin, X, zero;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) comp(zero, c) = S(0);
+    tile_prefix_of<N, S>(tile_agg, blockIdx.x, scan_prior(zero, prior_dev), nodes, ctx, pin);
     {
         Elem<N, S> G;
         wi_load(thr_agg, gthr, G);
         node_store(G, slot<N, S>(nodes, B, 0, t));
     }
     coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    pdl_wait();
-    Red<N, S> pin, X;
-    if (t == 0) aos_load(tile_pref, (long)blockIdx.x, pin);
     coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
     // the block's steps are forward tile (gridDim.x - 1 - blockIdx.x); its states
     // are staged in shared memory (the tree is no longer needed) and stored coalesced
@@ -859,62 +884,16 @@ k_tf_down(const __grid_constant__ RProd prod, int K, const S* __restrict__ thr_a
         if (base + idx < lim) x_out[base + idx] = st[idx];
 }
 
-// ---------------------------------------------------------------------------
-// phase 4: one CTA scans the tile maps backwards from x_T: per-thread
-// composites of `per` tiles, the affine up/down sweep of the tile trees over
-// the threads (the state at the end of every thread's tiles), then each
-// thread walks its tiles backwards from that state.
-// ---------------------------------------------------------------------------
-template <int N, typename S>
-__global__ void __launch_bounds__(256)
-k_affine_tiles(const S* __restrict__ tile_aff, int nt, const S* __restrict__ xT,
-               S* __restrict__ tile_xend)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* nodes = reinterpret_cast<S*>(smem_raw);
-    const int B = blockDim.x, t = threadIdx.x;
-    const int per = (nt + B - 1) / B;
-    const int first = min(nt, t * per), last = min(nt, first + per);
-    pdl_wait();
-    pdl_trigger();
-
-    Aff<N, S> H;
-    set_identity(H);
-    for (int i = last - 1; i >= first; --i) {      // H = a_first o ... o a_last
-        Aff<N, S> a;
-        aos_load(tile_aff, i, a);
-        compose<N, S>(a, H, H);
-    }
-    node_store(H, aslot<N, S>(nodes, B, 0, t));
-    coop_aff_up<N, S>(nodes);
-    S xe[N], x[N];
-    if (t == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) xe[i] = xT[i];
-    }
-    coop_aff_down<N, S>(nodes, xe, x);              // state at the end of this thread's tiles
-    for (int i = last - 1; i >= first; --i) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) tile_xend[(long)i * N + j] = x[j];
-        Aff<N, S> a;
-        aos_load(tile_aff, i, a);
-        S y[N];
-        affine_apply<N, S>(a, x, y);
-#pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = y[j];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// phase 5: per-step smoothed states x_k = E_k x_{k+1} + g_k
-// ---------------------------------------------------------------------------
 // shared-memory stride of one thread's staged states (odd: no bank conflicts)
 __host__ __device__ __forceinline__ int rts_stage_stride(int K, int N) { return (K * N) | 1; }
 
+// ---------------------------------------------------------------------------
+// phase 3: per-step smoothed states x_k = E_k x_{k+1} + g_k
+// ---------------------------------------------------------------------------
 template <int N, typename S>
 __global__ void __launch_bounds__(128)
-k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff,
-           const S* __restrict__ tile_xend, long T, S* __restrict__ x_out)
+k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const S* __restrict__ tile_aff,
+           const S* __restrict__ xT, long T, S* __restrict__ x_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -923,18 +902,18 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff,
     const long k0 = gthr * K;
     constexpr int NA = Aff<N, S>::NCOMP;
     constexpr int U = 4;                   // steps whose maps are loaded ahead of use
+    pdl_wait();                            // maps and x_T of the previous kernel
+    S* xe_sh = nodes + 2 * B * CoopLayout<N, S>::NA;   // staging area, free until the state loop
+    tile_suffix_state<N, S>(tile_aff, blockIdx.x, gridDim.x, xT, nodes, xe_sh);
+    S xe[N], x[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) xe[i] = xe_sh[i];
     {
         Aff<N, S> a;
         wi_load(thr_aff, gthr, a);
         node_store(a, aslot<N, S>(nodes, B, 0, t));
     }
     coop_aff_up<N, S>(nodes);
-    pdl_wait();                            // tile end states of the previous kernel
-    S xe[N], x[N];
-    if (t == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) xe[i] = tile_xend[(long)blockIdx.x * N + i];
-    }
     coop_aff_down<N, S>(nodes, xe, x);
     // the states are staged past the affine tree and written out coalesced
     const int SP = rts_stage_stride(K, N);

@@ -22,8 +22,7 @@ inline int ilog2_host(int x)
 
 template <int N, typename S>
 struct Layout {
-    size_t thr_agg, tile_agg, tile_pref, fin, Eg, thr_aff, tile_aff, tile_xend;
-    size_t filt_ws, term, fin2, xdummy, total;
+    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, total;
     static Layout make(long nthr, long nt, long Tpad)
     {
         using E = Elem<N, S>;
@@ -33,31 +32,16 @@ struct Layout {
         size_t o = 0;
         l.thr_agg = o;   o = align_up(o + sizeof(S) * E::NCOMP * nthr);
         l.tile_agg = o;  o = align_up(o + sizeof(S) * E::NCOMP * nt);
-        l.tile_pref = o; o = align_up(o + sizeof(S) * R::NCOMP * (nt + 1));
         l.fin = o;       o = align_up(o + sizeof(S) * R::NCOMP);
         l.Eg = o;        o = align_up(o + sizeof(S) * A::NCOMP * Tpad);
         l.thr_aff = o;   o = align_up(o + sizeof(S) * A::NCOMP * nthr);
         l.tile_aff = o;  o = align_up(o + sizeof(S) * A::NCOMP * nt);
-        l.tile_xend = o; o = align_up(o + sizeof(S) * N * nt);
         l.filt_ws = o;   o = align_up(o + sizeof(S) * R::NCOMP * Tpad);
         l.term = o;      o = align_up(o + sizeof(S) * R::NCOMP);
-        l.fin2 = o;      o = align_up(o + sizeof(S) * R::NCOMP);
-        l.xdummy = o;    o = align_up(o + sizeof(S) * N);
         l.total = o;
         return l;
     }
 };
-
-// CTA size of a single-CTA tile scan: the smallest power of two >= nt (at
-// least 32, at most 256) whose tree, of smem(bt) bytes, fits in shared memory
-template <class SmemOf>
-inline int pick_tile_scan_threads(int nt, SmemOf smem)
-{
-    int bt = 32;
-    while (bt < 256 && bt < nt) bt *= 2;
-    while (bt > 32 && smem(bt) > 200 * 1024) bt /= 2;
-    return bt;
-}
 
 // Launch with optional programmatic stream serialisation (see pdl_wait in scan.cuh).
 template <typename... KArgs, typename... Args>
@@ -132,40 +116,36 @@ int rts_resident_blocks(int B)
 }
 
 // Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
+// Three kernels: reduce (per-thread and per-tile totals), filter down-sweep
+// (each CTA reduces the totals before its tile, then per-step values and
+// closed-loop maps; the last CTA writes x_T), RTS pass (each CTA composes the
+// maps after its tile, then the per-step states).  With linear-fold constants
+// (fold != nullptr) the reduce kernel covers the full tiles 0..nt-2 on (b, eta)
+// parts and the down-sweep's last CTA folds the last tile itself.
 template <int N, typename S, class Prod>
 map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st,
                    bool dev_prior = false, const S* fold = nullptr)
 {
     using R = Red<N, S>;
-    const int B = h.B, nt = h.nt;
+    const int B = h.B, nt = h.nt, K = h.K;
     const long nthr = (long)nt * B;
     const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
     S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
     S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
-    S* tile_pref = reinterpret_cast<S*>(h.ws + L.tile_pref);
     S* fin = reinterpret_cast<S*>(h.ws + L.fin);
     S* Eg = reinterpret_cast<S*>(h.ws + L.Eg);
     S* thr_aff = reinterpret_cast<S*>(h.ws + L.thr_aff);
     S* tile_aff = reinterpret_cast<S*>(h.ws + L.tile_aff);
-    S* tile_xend = reinterpret_cast<S*>(h.ws + L.tile_xend);
     const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     const long T = h.T;
     S* xT = x_out + T * N;
-
-    const int K = h.K;
-    // linear-fold mode (fold != nullptr): the reduce kernel takes the full
-    // tiles 0..nt-2, the down-sweep's last CTA folds the last tile itself and
-    // writes the value function at x_T (see tile_thread_prefix)
+    S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
     const bool lti = fold != nullptr;
-    const int nagg = lti ? nt - 1 : nt;
+
     const size_t sh_reduce = tree_smem<N, S>(B);
     const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B)) +
                            (lti ? sizeof(S) * (size_t)K * 2 * N * Prod::W : 0);
     const size_t sh_rts = rts_smem<N, S>(B, K);
-    const int bt_f = pick_tile_scan_threads(nt, [](int b) { return tree_smem<N, S>(b); });
-    const int bt_a = pick_tile_scan_threads(nt, [](int b) { return aff_tree_smem<N, S>(b); });
-    const size_t sh_tf = tree_smem<N, S>(bt_f);
-    const size_t sh_ta = aff_tree_smem<N, S>(bt_a);
 
     static std::once_flag once;
     cudaError_t e0 = cudaSuccess;
@@ -174,49 +154,39 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         e0 = allow_smem(k_filter_reduce<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_affine_tiles<N, S>, big);
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
-    // kernels 2-5 overlap their prologues with their predecessor (PDL), except
-    // when per-phase events are recorded between them
+    // the down-sweep and the RTS pass overlap their prologues with their
+    // predecessor (PDL), except when per-phase events are recorded between them
     h.nev = 0;
     const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
     // dev_prior: the prior comes from the producer's terminal() (device data)
     S* term = dev_prior ? reinterpret_cast<S*>(h.ws + L.term) : nullptr;
-    S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
     bool first = true;                     // no PDL edge to whatever ran before the solve
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx);
         first = false;
-    } else if (nagg > 0) {
+    } else if (nt > 1) {
         if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-            const int LB = ilog2_host(B);
-            const size_t sh = LtiReduceSmem<N, Prod::W, S>::bytes(B, K, LB);
+            const size_t sh = LtiReduceSmem<N, Prod::W, S>::bytes(B, K, ilog2_host(B));
             static std::once_flag once_lti;
             cudaError_t e1 = cudaSuccess;
             std::call_once(once_lti, [&] { e1 = allow_smem(k_filter_reduce_lti<N, S, Prod>, 200 * 1024); });
             if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaFuncSetAttribute");
-            launch(k_filter_reduce_lti<N, S, Prod>, nagg, B, sh, st, false, prod, K, thr_agg, tile_agg, fold, ctx);
+            launch(k_filter_reduce_lti<N, S, Prod>, nt - 1, B, sh, st, false, prod, K, thr_agg, tile_agg, fold,
+                   ctx);
             first = false;
         }
     }
     mark();
-    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl && !first, (const S*)tile_agg, nagg,
-           prior_of<N, S>(h), (const S*)term, tile_pref, lti ? (S*)nullptr : fin, lti ? (S*)nullptr : xT,
-           lti ? (S*)nullptr : filtT, ctx);
+    launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl && !first, prod, K, thr_agg, (const S*)tile_agg,
+           prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT);
     mark();
-    launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl, prod, K, (const S*)thr_agg,
-           (const S*)tile_pref, Eg, thr_aff, tile_aff, filt_out, ctx, fold, lti ? fin : (S*)nullptr,
-           lti ? xT : (S*)nullptr, lti ? filtT : (S*)nullptr);
-    mark();
-    launch(k_affine_tiles<N, S>, 1, bt_a, sh_ta, st, pdl, (const S*)tile_aff, nt, (const S*)xT, tile_xend);
-    mark();
-    launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff,
-           (const S*)tile_xend, T, x_out);
+    launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
+           (const S*)xT, T, x_out);
     mark();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
@@ -237,21 +207,17 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
     S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
     S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
-    S* tile_pref = reinterpret_cast<S*>(h.ws + L.tile_pref);
     S* fin = reinterpret_cast<S*>(h.ws + L.fin);
     S* filt_ws = reinterpret_cast<S*>(h.ws + L.filt_ws);
     S* term = reinterpret_cast<S*>(h.ws + L.term);
-    S* fin2 = reinterpret_cast<S*>(h.ws + L.fin2);
-    S* xdummy = reinterpret_cast<S*>(h.ws + L.xdummy);
     const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     const long T = h.T;
     S* xT = x_out + T * N;
+    S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
     const bool lti = fold != nullptr;          // forward scan in linear-fold mode (see run_rts)
     const size_t sh_tree = tree_smem<N, S>(B);
     const size_t sh_states = sh_tree + (lti ? sizeof(S) * (size_t)K * 2 * N * Prod::W : 0);
     const size_t sh_tfd = std::max(sh_tree, sizeof(S) * (size_t)B * K * N);   // k_tf_down stages the states
-    const int bt_f = pick_tile_scan_threads(nt, [](int b) { return tree_smem<N, S>(b); });
-    const size_t sh_tf = tree_smem<N, S>(bt_f);
 
     static std::once_flag once;
     cudaError_t e0 = cudaSuccess;
@@ -259,7 +225,6 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
         const size_t big = 200 * 1024;
         e0 = allow_smem(k_filter_reduce<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_reduce<N, S, RProd>, big);
-        if (e0 == cudaSuccess) e0 = allow_smem(k_filter_tiles<N, S>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_states<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_tf_down<N, S, RProd>, big);
     });
@@ -269,40 +234,31 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const bool pdl = !h.profile;
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
-    S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
-    const int nagg = lti ? nt - 1 : nt;
     bool first = true;
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg, (S*)nullptr,
                ctx);
         first = false;
-    } else if (nagg > 0) {
+    } else if (nt > 1) {
         if constexpr (Prod::LINEAR_FOLD && N <= 6) {
             const size_t sh = LtiReduceSmem<N, Prod::W, S>::bytes(B, K, ilog2_host(B));
             static std::once_flag once_lti;
             cudaError_t e1 = cudaSuccess;
             std::call_once(once_lti, [&] { e1 = allow_smem(k_filter_reduce_lti<N, S, Prod>, 200 * 1024); });
             if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaFuncSetAttribute");
-            launch(k_filter_reduce_lti<N, S, Prod>, nagg, B, sh, st, false, fprod, K, thr_agg, tile_agg, fold, ctx);
+            launch(k_filter_reduce_lti<N, S, Prod>, nt - 1, B, sh, st, false, fprod, K, thr_agg, tile_agg, fold,
+                   ctx);
             first = false;
         }
     }
     mark();
-    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl && !first, (const S*)tile_agg, nagg,
-           prior_of<N, S>(h), (const S*)nullptr, tile_pref, lti ? (S*)nullptr : fin, lti ? (S*)nullptr : xT,
-           lti ? (S*)nullptr : filtT, ctx);
-    mark();
-    launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl, fprod, K, (const S*)thr_agg,
-           (const S*)tile_pref, filt_ws, filt_out, ctx, fold, lti ? fin : (S*)nullptr, lti ? xT : (S*)nullptr,
-           lti ? filtT : (S*)nullptr);
+    launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl && !first, fprod, K, thr_agg,
+           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, fold, fin, xT, filtT);
     mark();
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
-    launch(k_filter_tiles<N, S>, 1, bt_f, sh_tf, st, pdl, (const S*)tile_agg, nt, prior_of<N, S>(h),
-           (const S*)term, tile_pref, fin2, xdummy, (S*)nullptr, ctx);
-    mark();
-    launch(k_tf_down<N, S, RProd>, nt, B, sh_tfd, st, pdl, rprod, K, (const S*)thr_agg,
-           (const S*)tile_pref, (const S*)filt_ws, x_out, ctx);
+    launch(k_tf_down<N, S, RProd>, nt, B, sh_tfd, st, pdl, rprod, K, (const S*)thr_agg, (const S*)tile_agg,
+           (const S*)term, (const S*)filt_ws, x_out, ctx);
     mark();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");

@@ -22,7 +22,7 @@ class MapSmoother:
 
     def __init__(self, model, T, dt, precision="fp32", discretisation="euler", smoother="rts",
                  gn_iters=1, cond_max=0.0, tile_threads=0):
-        self.model, self.T, self.dt = model, int(T), float(dt)
+        self.model, self.T, self.dt, self.smoother = model, int(T), float(dt), smoother
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.nx, self.ny = model.nx, model.ny
         desc, keep = B.make_desc(model, T, dt, _PREC[precision], _DISC[discretisation],
@@ -106,7 +106,8 @@ class MapSmoother:
 
     def phase_times(self):
         """{phase name: ms} of the last profiled solve."""
-        return dict(zip(B.PHASES, B.map_smoother_phase_times(self._h)))
+        names = B.PHASES_TWO_FILTER if self.smoother == "two_filter" else B.PHASES
+        return dict(zip(names, B.map_smoother_phase_times(self._h)))
 
     def stats(self, reset=False, stream=None):
         """(combines recomputed in FP64, singular pivots, bulk copies whose bounded

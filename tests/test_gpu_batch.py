@@ -44,7 +44,7 @@ def test_mixed_batch_matches_oracle_per_trajectory(prec):
         assert rel(xs[j], ref) <= TOL[prec], (j, lengths[j], dims[j])
     for m in range(3):
         K, B = mb.tuning(m)
-        assert K in (8, 16) and B in (32, 64, 128)
+        assert 8 <= K <= 64 and B in (32, 64, 128)
     # graph replay and re-capture on new arrays give the same states
     first = [x.clone() for x in xdev]
     mb.solve(ydev, xdev)
