@@ -226,7 +226,30 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
     __syncthreads();
     if (!binv(out->C, out->Cinv, n, s.pivw)) { if (threadIdx.x == 0) s.flag |= SETUP_SINGULAR_C; }
     __syncthreads();
-    if (threadIdx.x == 0) out->flags = s.flag;
+    // C = Gam Gam^T by outer-product Cholesky with diagonal pivoting: each
+    // column takes the largest remaining diagonal; stop when it falls below
+    // 1e-13 of the largest diagonal of C (the numerical rank)
+    if (threadIdx.x == 0) {
+        double* Rm = s.pivw;
+        double dmax = 0.0;
+        for (int e = 0; e < n * n; ++e) Rm[e] = out->C[e];
+        for (int i = 0; i < n; ++i) dmax = fmax(dmax, Rm[i * n + i]);
+        for (int e = 0; e < n * n; ++e) out->Gam[e] = 0.0;
+        int rk = 0;
+        for (; rk < n; ++rk) {
+            int p = 0;
+            for (int i = 1; i < n; ++i)
+                if (Rm[i * n + i] > Rm[p * n + p]) p = i;
+            const double d = Rm[p * n + p];
+            if (!(d > 1e-13 * dmax) || dmax <= 0.0) break;
+            const double sd = sqrt(d);
+            for (int i = 0; i < n; ++i) out->Gam[i * n + rk] = Rm[i * n + p] / sd;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) Rm[i * n + j] -= out->Gam[i * n + rk] * out->Gam[j * n + rk];
+        }
+        out->rank = rk;
+        out->flags = s.flag;
+    }
 }
 
 cudaError_t launch_setup(const SetupIn& in, SetupOut* d_out, cudaStream_t st)

@@ -238,6 +238,185 @@ __device__ __forceinline__ void apply(const Elem<N, S>& e, Red<N, S>& p, S* E, S
 }
 
 // ---------------------------------------------------------------------------
+// e (x) [P, v] when C = Gam Gam^T with Gam N x R (R < N): by the matrix
+// inversion lemma
+//   (I + C P)^-1 = I - Gam W Gam^T P,   W = (I_R + Gam^T P Gam)^-1,
+// so with U = P Gam the closed-loop map is E = A - Gam W (U^T A),
+// g = z - Gam W (U^T z) with z = b + Gam (Gam^T v), and (P (I + C P)^-1 =
+// (I + P C)^-1 P, push-through)
+//   P' = A^T (P E) + J,   v' = E^T (v - P b) + eta.
+// The R x R matrix D = I + Gam^T P Gam is symmetric positive definite for a
+// positive semidefinite P; it is inverted by Cholesky.  Returns false (and
+// leaves p unchanged) when a Cholesky pivot is not positive or the
+// infinity-norm condition estimate |D| |D^-1| exceeds cond_max (the same
+// threshold as the general update's); the caller then takes the general
+// update with its FP64 recomputation.
+// ---------------------------------------------------------------------------
+template <int N, int R, typename S, bool ALPHA>
+__device__ __forceinline__ bool apply_lowrank(const Elem<N, S>& e, const S* Gam, Red<N, S>& p, S* E, S* g,
+                                              float cond_max)
+{
+    S U[N * R];                                       // U = P Gam
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            S s = S(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) s = fma(p.P[Sym<N>::at(i, j)], Gam[j * R + k], s);
+            U[i * R + k] = s;
+        }
+    S L[R * R], Li[R * R], W[R * R];                  // I + Gam^T U = L L^T,  W = L^-T L^-1
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+#pragma unroll
+        for (int i = j; i < R; ++i) {
+            S s = (i == j) ? S(1) : S(0);
+#pragma unroll
+            for (int q = 0; q < N; ++q) s = fma(Gam[q * R + i], U[q * R + j], s);
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = fma(-L[i * R + k], L[j * R + k], s);
+            if (i == j) {
+                ok = ok && s > S(0);
+                L[j * R + j] = sqrt(s > S(0) ? s : S(1));
+                Li[j * R + j] = S(1) / L[j * R + j];
+            } else {
+                L[i * R + j] = s * Li[j * R + j];
+            }
+        }
+    }
+    if (!ok) return false;
+    S nD = S(0);                                      // |D|_inf, D = L L^T
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        S row = S(0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            S d = S(0);
+#pragma unroll
+            for (int k = 0; k <= (i < j ? i : j); ++k) d = fma(L[i * R + k], L[j * R + k], d);
+            row += ms::sabs(d);
+        }
+        nD = row > nD ? row : nD;
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i)                       // L^-1 (lower triangular)
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            S s = S(0);
+#pragma unroll
+            for (int k = j; k < i; ++k) s = fma(L[i * R + k], Li[k * R + j], s);
+            Li[i * R + j] = -s * Li[i * R + i];
+        }
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            S s = S(0);
+#pragma unroll
+            for (int k = i; k < R; ++k) s = fma(Li[k * R + i], Li[k * R + j], s);
+            W[i * R + j] = s;
+            W[j * R + i] = s;
+        }
+    S nW = S(0);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        S row = S(0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) row += ms::sabs(W[i * R + j]);
+        nW = row > nW ? row : nW;
+    }
+    if (!(float(nD) * float(nW) <= cond_max)) return false;
+    S V[R * N], Em[N * N];                            // V = W (U^T A),  E = A - Gam V
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            S s = S(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) s = fma(U[i * R + k], e.A[i * N + j], s);
+            Em[k * N + j] = s;                        // U^T A, temporarily
+        }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            S s = S(0);
+#pragma unroll
+            for (int l = 0; l < R; ++l) s = fma(W[k * R + l], Em[l * N + j], s);
+            V[k * N + j] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            S s = e.A[i * N + j];
+#pragma unroll
+            for (int k = 0; k < R; ++k) s = fma(-Gam[i * R + k], V[k * N + j], s);
+            Em[i * N + j] = s;
+        }
+    if (ALPHA) {
+        S t[R], z[N], t2[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            S s = S(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) s = fma(Gam[i * R + k], p.v[i], s);
+            t[k] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = e.b[i];
+#pragma unroll
+            for (int k = 0; k < R; ++k) s = fma(Gam[i * R + k], t[k], s);
+            z[i] = s;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            S s = S(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) s = fma(U[i * R + k], z[i], s);
+            t[k] = s;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            S s = S(0);
+#pragma unroll
+            for (int l = 0; l < R; ++l) s = fma(W[k * R + l], t[l], s);
+            t2[k] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S s = z[i];
+#pragma unroll
+            for (int k = 0; k < R; ++k) s = fma(-Gam[i * R + k], t2[k], s);
+            g[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) E[i] = Em[i];
+    }
+    S PE[N * N], w[N];                                // P E,  w = v - P b
+    ms::sym_m<N, S>(p.P, Em, PE);
+    ms::sym_v<N, S>(p.P, e.b, w);
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] = p.v[i] - w[i];
+    Red<N, S> r;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = i; j < N; ++j) {
+            S s = e.J[Sym<N>::at(i, j)];
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fma(e.A[k * N + i], PE[k * N + j], s);
+            r.P[Sym<N>::at(i, j)] = s;
+        }
+    ms::mtv_add<N, S>(Em, w, e.eta, r.v);             // E^T w + eta
+    p = r;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // affine maps (Eq. 40-41): (F1, c1) o (F2, c2) = (F1 F2, F1 c2 + c1)
 // ---------------------------------------------------------------------------
 template <int N, typename S>

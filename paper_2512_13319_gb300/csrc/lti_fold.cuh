@@ -360,32 +360,27 @@ __device__ __forceinline__ void lti_linear_fold(const Prod& prod, const S* __res
 }
 
 // The element of a thread whose first r < K steps are before T (the rest are
-// identity padding): the r-step fold from its constants, read from global
-// memory (one thread per solve takes this path)
-template <int N, typename S, class Prod>
-__device__ __forceinline__ void lti_partial_fold_elem(const Prod& prod, const S* __restrict__ fold, int r, long k0,
-                                                      Elem<N, S>& G)
+// identity padding): the r-step fold from its constants pb (FoldLayout::poff(r)
+// block, staged in shared memory) and its observations yq (r rows of M, staged)
+template <int N, int M, typename S>
+__device__ __forceinline__ void lti_partial_fold_elem(const S* pb, const S* yq, int r, Elem<N, S>& G)
 {
-    constexpr int M = Prod::W;
     using FL = FoldLayout<N, M, S>;
-    const S* pb = fold + FL::poff(r);
 #pragma unroll
     for (int q = 0; q < N * N; ++q) G.A[q] = pb[FL::oA + q];
 #pragma unroll
     for (int q = 0; q < Sym<N>::SZ; ++q) { G.C[q] = pb[FL::oC + q]; G.J[q] = pb[FL::oJ + q]; }
 #pragma unroll
     for (int q = 0; q < N; ++q) { G.b[q] = pb[FL::ob + q]; G.eta[q] = pb[FL::oe + q]; }
-#pragma unroll 1
+#pragma unroll 4
     for (int i = 0; i < r; ++i) {
-        S row[M];
-        prod.load1(k0 + i, row);
         const S* g = pb + FL::HS + i * FL::GS;
 #pragma unroll
         for (int a = 0; a < N; ++a)
 #pragma unroll
             for (int c = 0; c < M; ++c) {
-                G.b[a] = fma(g[a * M + c], row[c], G.b[a]);
-                G.eta[a] = fma(g[(N + a) * M + c], row[c], G.eta[a]);
+                G.b[a] = fma(g[a * M + c], yq[i * M + c], G.b[a]);
+                G.eta[a] = fma(g[(N + a) * M + c], yq[i * M + c], G.eta[a]);
             }
     }
 }

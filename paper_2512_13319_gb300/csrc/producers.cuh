@@ -45,12 +45,15 @@ __device__ __forceinline__ void load_run(const S* __restrict__ src, long avail, 
 template <int N, int M, typename S>
 struct LtiParams {
     static constexpr int NS = Sym<N>::SZ;
+    static constexpr int R = (N + 1) / 2;   // column count of the low-rank factor of C
     S A[N * N];
     S b[N];
     S C[NS];
     S J[NS];
     S G[N * M];      // dt H^T R^-1
     S Gr[N];         // dt H^T R^-1 r
+    S Gam[N * R];    // C = Gam Gam^T when lowrank (zero columns beyond the rank)
+    int lowrank;     // rank(C) <= R: the per-step value-function update uses Gam
 };
 
 template <int N, int M, typename S>
@@ -58,6 +61,7 @@ struct LtiProducer {
     static constexpr int W = M;      // scalars read per step
     static constexpr bool RESETS = false;
     static constexpr bool LINEAR_FOLD = true;   // see lti_fold.cuh
+    static constexpr bool LOWRANK = true;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                      // (T, M), row k holds y_{k+1}
     long T;
@@ -117,6 +121,7 @@ struct SegLtiProducer {
     static constexpr int W = M;
     static constexpr bool RESETS = true;
     static constexpr bool LINEAR_FOLD = false;
+    static constexpr bool LOWRANK = true;
     const S* y;                      // (T, M) with an unused row at every reset
     const unsigned char* reset;      // (T): 1 where a trajectory starts (except the first)
     long T;
@@ -187,6 +192,7 @@ struct AdjProducer {
     static constexpr int W = N;
     static constexpr bool RESETS = false;
     static constexpr bool LINEAR_FOLD = false;
+    static constexpr bool LOWRANK = false;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* d;                      // (T+1, N): dL/dx*
     long T;
@@ -246,6 +252,7 @@ struct RevFlipProducer {
     static constexpr int W = M;
     static constexpr bool RESETS = false;
     static constexpr bool LINEAR_FOLD = false;
+    static constexpr bool LOWRANK = false;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                      // (T, M), row k-1 holds y_k
     long T;
@@ -390,6 +397,7 @@ struct NlProducer {
     static constexpr int W = M + N;   // y_{k+1} then xbar_{k+1}
     static constexpr bool RESETS = false;
     static constexpr bool LINEAR_FOLD = false;
+    static constexpr bool LOWRANK = false;
     __device__ __forceinline__ bool is_reset(long) const { return false; }
     const S* y;                       // (T, M)
     const S* xbar;                    // (T+1, N)

@@ -388,22 +388,28 @@ __device__ __forceinline__ Red<N, S> scan_prior(const Red<N, S>& prior, const S*
     return p;
 }
 
+// Tile of a down-sweep CTA: block 0 takes the last tile, block b > 0 tile
+// b - 1.  The last tile's CTA (in linear-fold mode the one with the extra
+// work before its wait) is then dispatched first and overlaps that work with
+// the previous kernel.
+__device__ __forceinline__ int down_tile() { return blockIdx.x == 0 ? gridDim.x - 1 : blockIdx.x - 1; }
+
 // Exclusive prefix (value function before the thread's first step) of every
 // thread of a tile from the tile's prefix `pin` (valid in thread 0): the
 // tile's up-sweep over the per-thread aggregates and the down-sweep.
 // With linear-fold constants (fold != nullptr, lti_fold.cuh) the reduce
 // kernel has left (b, eta) aggregates (2N components) for the full tiles
-// 0..gridDim.x-2 and their trees run on those; the last tile's aggregates are
-// full elements (written by the down-sweep's last CTA before its wait).
+// 0..gridDim.x-2 and their trees run on those (the last tile takes
+// lti_last_tile_tree / lti_last_tile_prefix instead).
 template <int N, typename S, class Prod>
-__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, const S* __restrict__ thr_agg,
+__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, const S* __restrict__ thr_agg,
                                                    const Red<N, S>& pin, const S* __restrict__ fold, S* nodes,
                                                    const CombineCtx& ctx, Red<N, S>& X)
 {
     const int B = blockDim.x, t = threadIdx.x;
-    const long gthr = (long)blockIdx.x * B + t;
+    const long gthr = (long)tile * B + t;
     if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        if (fold && blockIdx.x + 1 < gridDim.x) {
+        if (fold && tile + 1 < (int)gridDim.x) {
             using FL = FoldLayout<N, Prod::W, S>;
             using TS = LtiTreeSmem<N, Prod::W, S>;
             const int LB = ilog2(B);
@@ -432,39 +438,86 @@ __device__ __forceinline__ void tile_thread_prefix(const Prod& prod, const S* __
 // as full elements (the reduce kernel does not cover this tile).  A thread
 // whose K steps are before T takes the K-step linear fold, the one that
 // reaches T the r-step fold, threads past T the identity.  gam: shared memory
-// for the Gamma_i of the K-step fold.
+// for the Gamma_i of the K-step fold, followed by room for the r-step fold's
+// constants and observations (lti_last_tile_smem scalars in all).
+template <int N, int M>
+__host__ __device__ constexpr int lti_last_tile_smem(int K)
+{
+    using FL = FoldLayout<N, M, float>;        // offsets in scalars do not depend on the type
+    return (K * FL::GS + 3) / 4 * 4 + (FL::HS + (FL::KMAX - 1) * FL::GS + 3) / 4 * 4 + FL::KMAX * M;
+}
+
 template <int N, typename S, class Prod>
-__device__ __forceinline__ void lti_last_tile_leaves(const Prod& prod, int K, const S* __restrict__ fold, S* gam,
-                                                     S* __restrict__ thr_agg)
+__device__ __forceinline__ void lti_last_tile_leaves(const Prod& prod, int tile, int K, const S* __restrict__ fold,
+                                                     S* gam, Elem<N, S>& G)
 {
     if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        using FL = FoldLayout<N, Prod::W, S>;
+        constexpr int M = Prod::W;
+        using FL = FoldLayout<N, M, S>;
         const int B = blockDim.x, t = threadIdx.x;
-        const long gthr = (long)blockIdx.x * B + t;
+        const long gthr = (long)tile * B + t;
+        const long t0 = (long)tile * B * K;                 // first step of the tile
+        const long tl = prod.T - t0;                        // steps of the tile before T
+        const int ts = (int)(tl / K), rs = (int)(tl - (long)ts * K);   // thread that reaches T, its steps
+        S* pbs = gam + (K * FL::GS + 3) / 4 * 4;                      // its fold constants
+        S* yqs = pbs + (FL::HS + rs * FL::GS + 3) / 4 * 4;           // its observations
         for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
+        if (rs > 0) {
+            const S* pb = fold + FL::poff(rs);
+            for (int q = t; q < FL::HS + rs * FL::GS; q += B) pbs[q] = pb[q];
+            for (int q = t; q < rs * M; q += B) yqs[q] = prod.y[(t0 + (long)ts * K) * M + q];
+        }
         __syncthreads();
         const long k0 = gthr * K;
-        const long r = prod.T - k0;
-        Elem<N, S> G;
-        if (r >= K)
+        if (t < ts)
             lti_fold_elem<N, S>(prod, fold, gam, K, k0, G);
-        else if (r <= 0)
-            set_identity(G);
+        else if (t == ts && rs > 0)
+            lti_partial_fold_elem<N, M, S>(pbs, yqs, rs, G);
         else
-            lti_partial_fold_elem<N, S>(prod, fold, (int)r, k0, G);
-        wi_store(thr_agg, gthr, G);
+            set_identity(G);
         __syncthreads();
     }
+}
+
+// Linear-fold mode, last tile, before the wait for the reduce kernel: the
+// tile's leaves and up-sweep (the general sub-warp tree, as the tile reaches
+// past T), parked in global memory (ltree, 2B nodes) while the shared memory
+// serves the tile-prefix reduction
+template <int N, typename S, class Prod>
+__device__ __forceinline__ void lti_last_tile_tree(const Prod& prod, int tile, int K, const S* __restrict__ fold,
+                                                   S* nodes, S* __restrict__ ltree, const CombineCtx& ctx)
+{
+    const int B = blockDim.x, t = threadIdx.x;
+    Elem<N, S> G;
+    set_identity(G);
+    lti_last_tile_leaves<N, S>(prod, tile, K, fold, nodes + tree_smem<N, S>(B) / sizeof(S), G);
+    node_store(G, slot<N, S>(nodes, B, 0, t));
+    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    const int cnt = 2 * B * CoopLayout<N, S>::NE;
+    for (int q = t; q < cnt; q += B) ltree[q] = nodes[q];
+    __syncthreads();
+}
+
+// the parked tree back into shared memory, then the down-sweep from pin
+template <int N, typename S>
+__device__ __forceinline__ void lti_last_tile_prefix(const S* __restrict__ ltree, const Red<N, S>& pin, S* nodes,
+                                                     const CombineCtx& ctx, Red<N, S>& X)
+{
+    const int B = blockDim.x, t = threadIdx.x;
+    const int cnt = 2 * B * CoopLayout<N, S>::NE;
+    for (int q = t; q < cnt; q += B) nodes[q] = ltree[q];
+    __syncthreads();                       // the whole tree is back before the root takes pin
+    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
 }
 
 // The thread of the last tile that holds step T-1 writes the value function
 // at x_T (after its steps), its minimiser x_T and, if asked, its filter value.
 template <int N, typename S>
-__device__ __forceinline__ void write_final_if_last(long T, int K, const Red<N, S>& X, S* final_out,
+__device__ __forceinline__ void write_final_if_last(long T, int tile, int K, const Red<N, S>& X, S* final_out,
                                                     S* xT_out, S* filtT_out, const CombineCtx& ctx)
 {
-    const long k0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) * K;
-    if (!final_out || blockIdx.x + 1 != gridDim.x || k0 >= T || k0 + K < T) return;
+    const long k0 = ((long)tile * blockDim.x + threadIdx.x) * K;
+    if (!final_out || tile + 1 != (int)gridDim.x || k0 >= T || k0 + K < T) return;
     Red<N, S> P = X;
     aos_store(final_out, 0, P);
     S x[N];
@@ -514,7 +567,7 @@ k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ th
     constexpr int M = Prod::W;
     using FL = FoldLayout<N, M, S>;
     using RS = LtiReduceSmem<N, M, S>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     S* sm = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x, LB = ilog2(B);
     const long gthr = (long)blockIdx.x * B + t;
@@ -641,23 +694,27 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
               const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
               S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
               CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
-              S* __restrict__ filtT_out)
+              S* __restrict__ filtT_out, S* __restrict__ ltree)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
-    const long gthr = (long)blockIdx.x * B + t;
+    const int tile = down_tile();
+    const long gthr = (long)tile * B + t;
     const long k0 = gthr * K;
     const long T = prod.T;
     constexpr int NA = Aff<N, S>::NCOMP;
 
-    if (fold && blockIdx.x + 1 == gridDim.x)
-        lti_last_tile_leaves<N, S>(prod, K, fold, nodes + tree_smem<N, S>(B) / sizeof(S), thr_agg);
+    const bool last_lti = fold && tile + 1 == (int)gridDim.x;
+    if (last_lti) lti_last_tile_tree<N, S>(prod, tile, K, fold, nodes, ltree, ctx);
     pdl_wait();                            // totals and aggregates of the reduce kernel
     pdl_trigger();
     Red<N, S> pin, X;
-    tile_prefix_of<N, S>(tile_agg, blockIdx.x, scan_prior(prior, prior_dev), nodes, ctx, pin);
-    tile_thread_prefix<N, S>(prod, thr_agg, pin, fold, nodes, ctx, X);
+    tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin);
+    if (last_lti)
+        lti_last_tile_prefix<N, S>(ltree, pin, nodes, ctx, X);
+    else
+        tile_thread_prefix<N, S>(prod, tile, thr_agg, pin, fold, nodes, ctx, X);
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
@@ -682,7 +739,12 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 if (!red_argmin<N, S>(X, a.c) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
                 apply<N, S, false>(e, X, nullptr, nullptr, ctx);
             } else {
-                apply<N, S, true>(e, X, a.F, a.c, ctx);
+                bool done = false;
+                if constexpr (Prod::LOWRANK) {
+                    if (prod.p.lowrank)
+                        done = apply_lowrank<N, (N + 1) / 2, S, true>(e, prod.p.Gam, X, a.F, a.c, ctx.cond_max);
+                }
+                if (!done) apply<N, S, true>(e, X, a.F, a.c, ctx);
             }
 #pragma unroll
             for (int c = 0; c < NA; ++c) Eg[wis_idx(gthr, i, c, K, NA)] = comp(a, c);
@@ -697,7 +759,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
             for (int j = 0; j < N * N; ++j) comp_t.F[j] = F2[j];
         }
     }
-    write_final_if_last<N, S>(T, K, X, final_out, xT_out, filtT_out, ctx);
+    write_final_if_last<N, S>(T, tile, K, X, final_out, xT_out, filtT_out, ctx);
     wi_store(thr_aff, gthr, comp_t);
     __syncthreads();                       // the filter trees are done with shared memory
     node_store(comp_t, aslot<N, S>(nodes, B, 0, t));
@@ -705,7 +767,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
     if (t == 0) {
         Aff<N, S> root;
         node_load(aslot<N, S>(nodes, B, ilog2(B), 0), root);
-        aos_store(tile_aff, (long)blockIdx.x, root);
+        aos_store(tile_aff, (long)tile, root);
     }
 }
 
@@ -718,22 +780,27 @@ __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 const S* __restrict__ tile_agg, const Red<N, S> prior, S* __restrict__ filt_ws,
                 S* __restrict__ filt_out, CombineCtx ctx, const S* __restrict__ fold,
-                S* __restrict__ final_out, S* __restrict__ xT_out, S* __restrict__ filtT_out)
+                S* __restrict__ final_out, S* __restrict__ xT_out, S* __restrict__ filtT_out,
+                S* __restrict__ ltree)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
-    const long gthr = (long)blockIdx.x * B + t;
+    const int tile = down_tile();
+    const long gthr = (long)tile * B + t;
     const long k0 = gthr * K;
     const long T = prod.T;
     constexpr int NR = Red<N, S>::NCOMP;
-    if (fold && blockIdx.x + 1 == gridDim.x)
-        lti_last_tile_leaves<N, S>(prod, K, fold, nodes + tree_smem<N, S>(B) / sizeof(S), thr_agg);
+    const bool last_lti = fold && tile + 1 == (int)gridDim.x;
+    if (last_lti) lti_last_tile_tree<N, S>(prod, tile, K, fold, nodes, ltree, ctx);
     pdl_wait();
     pdl_trigger();
     Red<N, S> pin, X;
-    tile_prefix_of<N, S>(tile_agg, blockIdx.x, prior, nodes, ctx, pin);
-    tile_thread_prefix<N, S>(prod, thr_agg, pin, fold, nodes, ctx, X);
+    tile_prefix_of<N, S>(tile_agg, tile, prior, nodes, ctx, pin);
+    if (last_lti)
+        lti_last_tile_prefix<N, S>(ltree, pin, nodes, ctx, X);
+    else
+        tile_thread_prefix<N, S>(prod, tile, thr_agg, pin, fold, nodes, ctx, X);
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;
@@ -748,10 +815,15 @@ k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
             prod.load1(k, row);
             Elem<N, S> e;
             prod.make(k, row, e);
-            apply<N, S, false>(e, X, nullptr, nullptr, ctx);
+            bool done = false;
+            if constexpr (Prod::LOWRANK) {
+                if (prod.p.lowrank)
+                    done = apply_lowrank<N, (N + 1) / 2, S, false>(e, prod.p.Gam, X, nullptr, nullptr, ctx.cond_max);
+            }
+            if (!done) apply<N, S, false>(e, X, nullptr, nullptr, ctx);
         }
     }
-    write_final_if_last<N, S>(T, K, X, final_out, xT_out, filtT_out, ctx);
+    write_final_if_last<N, S>(T, tile, K, X, final_out, xT_out, filtT_out, ctx);
 }
 
 // x = (S + L)^-1 (v + z) for symmetric positive definite S + L (Cholesky; a

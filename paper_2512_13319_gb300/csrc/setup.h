@@ -24,6 +24,8 @@ struct SetupOut {
     double Rinv[MAXM * MAXM], G[MAXN * MAXM], Gr[MAXN], J[MAXN * MAXN];
     double S0[MAXN * MAXN], v0[MAXN];
     double Phi[MAXN * MAXN], beta[MAXN], Sigma[MAXN * MAXN];
+    double Gam[MAXN * MAXN];           // C = Gam Gam^T, Gam n x rank (leading dimension n)
+    int rank;                          // numerical rank of C (pivoted Cholesky, relative 1e-13)
     int flags;
 };
 

@@ -22,9 +22,10 @@ inline int ilog2_host(int x)
 
 template <int N, typename S>
 struct Layout {
-    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, total;
+    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, ltree, total;
     static Layout make(long nthr, long nt, long Tpad)
     {
+        const long B = nt > 0 ? nthr / nt : 0;
         using E = Elem<N, S>;
         using R = Red<N, S>;
         using A = Aff<N, S>;
@@ -38,6 +39,7 @@ struct Layout {
         l.tile_aff = o;  o = align_up(o + sizeof(S) * A::NCOMP * nt);
         l.filt_ws = o;   o = align_up(o + sizeof(S) * R::NCOMP * Tpad);
         l.term = o;      o = align_up(o + sizeof(S) * R::NCOMP);
+        l.ltree = o;     o = align_up(o + sizeof(S) * 2 * B * CoopLayout<N, S>::NE);   // last tile's tree
         l.total = o;
         return l;
     }
@@ -91,6 +93,10 @@ LtiParams<N, M, S> lti_params(const map_smoother& h)
             p.J[Sym<N>::at(i, j)] = S(c.J[i * N + j]);
         }
     for (int i = 0; i < N * M; ++i) p.G[i] = S(c.G[i]);
+    constexpr int R = LtiParams<N, M, S>::R;
+    p.lowrank = c.rank <= R;
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < R; ++k) p.Gam[i * R + k] = (k < c.rank && p.lowrank) ? S(c.Gam[i * N + k]) : S(0);
     return p;
 }
 
@@ -144,7 +150,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
 
     const size_t sh_reduce = tree_smem<N, S>(B);
     const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B)) +
-                           (lti ? sizeof(S) * (size_t)K * 2 * N * Prod::W : 0);
+                           (lti ? sizeof(S) * (size_t)lti_last_tile_smem<N, Prod::W>(K) : 0);
     const size_t sh_rts = rts_smem<N, S>(B, K);
 
     static std::once_flag once;
@@ -183,7 +189,8 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     }
     mark();
     launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl && !first, prod, K, thr_agg, (const S*)tile_agg,
-           prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT);
+           prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT,
+           reinterpret_cast<S*>(h.ws + L.ltree));
     mark();
     launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
            (const S*)xT, T, x_out);
@@ -216,7 +223,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
     const bool lti = fold != nullptr;          // forward scan in linear-fold mode (see run_rts)
     const size_t sh_tree = tree_smem<N, S>(B);
-    const size_t sh_states = sh_tree + (lti ? sizeof(S) * (size_t)K * 2 * N * Prod::W : 0);
+    const size_t sh_states = sh_tree + (lti ? sizeof(S) * (size_t)lti_last_tile_smem<N, Prod::W>(K) : 0);
     const size_t sh_tfd = std::max(sh_tree, sizeof(S) * (size_t)B * K * N);   // k_tf_down stages the states
 
     static std::once_flag once;
@@ -253,7 +260,8 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     }
     mark();
     launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl && !first, fprod, K, thr_agg,
-           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, fold, fin, xT, filtT);
+           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, fold, fin, xT, filtT,
+           reinterpret_cast<S*>(h.ws + L.ltree));
     mark();
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
