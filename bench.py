@@ -45,30 +45,42 @@ def model_and_data(seed, T=T_FULL):
 
 
 # ----------------------------------------------------------------------------
-# algorithmic work per step (multiply-adds; FLOP = 2 MAC) of each phase, for
-# state dimension n, measurement dimension m, K steps per thread, B threads per tile
+# algorithmic work per step (multiply-adds; FLOP = 2 MAC) of each kernel of
+# one solve, for state dimension n, measurement dimension m, K steps per
+# thread, B threads per tile, nt tiles and process-noise rank r (r < n: the
+# per-step update goes through the matrix inversion lemma)
 # ----------------------------------------------------------------------------
-def work_model(n, m, K, B, wbytes):
-    combine = 8 * n ** 3 + 5 * n ** 2
-    apply_alpha = 4.5 * n ** 3 + 4.5 * n ** 2
+def work_model(n, m, K, B, nt, wbytes, r=None):
+    combine = 8 * n ** 3 + 5 * n ** 2           # general combine (Eq. 36), one (I + C J) inverse
+    apply_alpha = 4.5 * n ** 3 + 4.5 * n ** 2   # one-variable update + closed-loop map
     apply_plain = 4.5 * n ** 3 + 2.5 * n ** 2
+    if r is not None and r < n:
+        apply_alpha = (n * n * r + n * r * (r + 1) / 2 + r ** 3 + 2 * r * n * n + r * r * n
+                       + 4 * n * r + r * r + n ** 3 + n * n * (n + 1) / 2 + 2 * n * n)
     compose = n ** 3 + n ** 2
-    aff_apply = n ** 2
+    lin_node = 4 * n * n                        # (b, eta) tree node of a full tile
     L = B * K
     tree = (B - 1) / L
-    ne = n * n + 2 * n + n * (n + 1)       # element components
-    na = n * n + n                          # closed-loop map components
+    # each CTA's reduction of the tile totals before it: ceil(nt / B) combines per
+    # thread, a tree of B leaves and one one-variable update
+    prefix = (-(-nt // B) * combine + (B - 1) * combine + apply_plain) / L
+    na = n * n + n                              # closed-loop map components
     mac = {
-        "filter_reduce": (K - 1) / K * combine + tree * combine,
-        "filter_down": tree * (combine + apply_plain + compose) + apply_alpha + compose,
-        "rts_down": tree * (compose + aff_apply) + aff_apply,
+        "filter_reduce": 2 * n * m + tree * lin_node,
+        "filter_down": (n * m + apply_alpha + compose + prefix + tree * (lin_node + apply_plain + compose)),
+        "rts_down": n * n + tree * (compose + n * n) + (-(-nt // B) * compose + (B - 1) * compose) / L,
     }
-    byt = {   # minimal HBM bytes per step of each kernel
-        "filter_reduce": wbytes * (m + ne / K),
-        "filter_down": wbytes * (m + ne / K + na + na / K),
+    byt = {   # minimal DRAM bytes per step of each kernel
+        "filter_reduce": wbytes * (m + 2 * n / K),
+        "filter_down": wbytes * (m + 2 * n / K + na + na / K),
         "rts_down": wbytes * (na + na / K + n),
     }
     return {k: 2 * v for k, v in mac.items()}, byt
+
+
+# DRAM bytes (read + write) of one k_filter_down launch on the nx=4, T=2^20 FP32
+# workload, from one ncu capture of this kernel version (cold cache)
+K_FILTER_DOWN_DRAM_BYTES = 11.562496e6 + 42.679552e6
 
 
 def solve_bytes(n, m, wbytes):
@@ -135,14 +147,15 @@ class ClockSampler:
 # oracle timing (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------
 def time_oracle(model, y, budget_s, min_runs=1):
+    """Mean seconds per oracle solve over runs filling budget_s, the run count and the trajectory."""
     import oracle
-    runs, t_tot = 0, 0.0
+    runs, t_tot, x = 0, 0.0, None
     while runs < min_runs or t_tot < budget_s:
         t = time.perf_counter()
-        oracle.smooth_lti(model, y, DT)
+        x = oracle.smooth_lti(model, y, DT)
         t_tot += time.perf_counter() - t
         runs += 1
-    return t_tot / runs, runs
+    return t_tot / runs, runs, x
 
 
 def reference_arm(args):
@@ -154,7 +167,7 @@ def reference_arm(args):
     # per-step sample sized so that warm-up + timed steps take about a minute
     model, y_full = model_and_data(1001)
     probe_T = 2 ** 14
-    t_probe, _ = time_oracle(model, y_full[:probe_T], 0.2)
+    t_probe, _, _ = time_oracle(model, y_full[:probe_T], 0.2)
     per_step = t_probe / probe_T
     budget = 60.0 / max(1, args.steps + args.warmup)
     Ts = int(min(T_FULL, max(1024, budget / per_step)))
@@ -246,8 +259,9 @@ def ours(args):
     t_wall1 = time.time()
     time.sleep(0.25)
     sampler.stop()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-    ms = max_over_ranks(ms)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_mean = max_over_ranks(sum(step_ms) / args.steps)
+    ms = max_over_ranks(statistics.median(step_ms))      # median step time, max over ranks
     value = world * T / (ms * 1e-3)
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -276,7 +290,7 @@ def ours(args):
     sm.profile(False)
     phase_ms = {k: statistics.median(v) for k, v in phases.items()}
     K_g, B_g, nt_g = sm.geometry()
-    flops, byt = work_model(4, 2, K_g, B_g, wbytes)
+    flops, byt = work_model(4, 2, K_g, B_g, nt_g, wbytes, r=2)
     dom = max(("filter_reduce", "filter_down", "rts_down"), key=lambda k: phase_ms.get(k, 0.0))
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
@@ -284,7 +298,9 @@ def ours(args):
     achieved_tf = flops[dom] * T / (phase_ms[dom] * 1e-3) / 1e12
     alu_peak = fp32_peak if prec == "fp32" else fp32_peak / 64.0
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak, "traffic": None, "kernel": dom,
+                "frac": achieved_tf / alu_peak,
+                "traffic": K_FILTER_DOWN_DRAM_BYTES if (dom == "filter_down" and prec == "fp32") else None,
+                "kernel": dom,
                 "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts "
                                 "and max clock)" if prec == "fp32" else "FP32 figure / 64"),
                 "flop_per_step": flops[dom]}
@@ -297,6 +313,10 @@ def ours(args):
            "note": "y in + x out over the whole solve; intermediates excluded"}
     hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
     fb, sing, timeouts = sm.stats()
+    # kernels of one solve: reduce (linear fold: full tiles only, absent for one
+    # tile), group totals (more than 4B tiles), filter down-sweep, RTS pass
+    launches_per_solve = (1 if nt_g > 1 else 0) + (1 if nt_g - 1 > 4 * B_g else 0) + 2
+    x_last = x
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -306,7 +326,8 @@ def ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed before every timed step (256 MiB write)",
                    "steps_per_thread": K_g, "threads_per_tile": B_g, "tiles": nt_g},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
+        "ms_per_step_mean": ms_mean,
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_solve * args.steps, "roofline": roofline,
         "phases": per_phase, "hbm": hbm, "fp64_recomputes": fb, "singular_pivots": sing, "copy_wait_timeouts": timeouts,
     }
     sm.close()
@@ -339,9 +360,12 @@ def ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        t_run, runs = time_oracle(model, y_np, 10.0)
+        t_run, runs, x_ref = time_oracle(model, y_np, 10.0)
         result["cpu_baseline"] = {"value": T / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": f"the full T=2^20 workload, {runs} runs (FP64 KF + RTS, plain C)"}
+        # relative trajectory error of the timed solve's output against the oracle
+        x_gpu = x_last.double().cpu().numpy()
+        result["rel_err_vs_oracle"] = float(np.linalg.norm(x_gpu - x_ref) / np.linalg.norm(x_ref))
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -298,28 +298,25 @@ __device__ __forceinline__ S* scratch_of(S* nodes)
 // ---------------------------------------------------------------------------
 // tile prefixes and suffixes, computed by each CTA of a down-sweep
 // ---------------------------------------------------------------------------
-// Value function before tile `tile` (returned in thread 0): thread t folds a
-// contiguous run of at most ceil(tile / B) of the totals of tiles 0..tile-1,
-// the runs are reduced with the sub-warp tree (empty runs are the identity
-// element, neutral on both sides of the combine) and the total is applied to
-// the prior.  Uses the element-tree area of `nodes`; ends with a barrier.
+// Fold, in thread 0, of the totals first..last-1 (later on the left of the
+// combine): thread t folds a contiguous run of at most ceil(count / B), the runs
+// are reduced with the sub-warp tree (empty runs are the identity element,
+// neutral on both sides of the combine).  Uses the element-tree area of
+// `nodes`; ends with a barrier.
 template <int N, typename S>
-__device__ __forceinline__ void tile_prefix_of(const S* __restrict__ tile_agg, int tile, const Red<N, S>& prior,
-                                               S* nodes, const CombineCtx& ctx, Red<N, S>& out)
+__device__ __forceinline__ void fold_totals(const S* __restrict__ totals, int first_all, int last_all, S* nodes,
+                                            const CombineCtx& ctx, Elem<N, S>& out)
 {
     const int B = blockDim.x, t = threadIdx.x;
-    if (tile == 0) {
-        out = prior;
-        return;
-    }
-    const int per = (tile + B - 1) / B;
-    const int first = min(tile, t * per), last = min(tile, first + per);
+    const int cnt = last_all - first_all;
+    const int per = (cnt + B - 1) / B;
+    const int first = first_all + min(cnt, t * per), last = min(last_all, first + per);
     Elem<N, S> F;
     if (first < last) {
-        aos_load(tile_agg, first, F);
+        aos_load(totals, first, F);
         for (int i = first + 1; i < last; ++i) {
             Elem<N, S> g;
-            aos_load(tile_agg, i, g);
+            aos_load(totals, i, g);
             combine<N, S>(g, F, F, ctx);
         }
     } else {
@@ -327,14 +324,65 @@ __device__ __forceinline__ void tile_prefix_of(const S* __restrict__ tile_agg, i
     }
     node_store(F, slot<N, S>(nodes, B, 0, t));
     coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    if (t == 0) node_load(slot<N, S>(nodes, B, ilog2(B), 0), out);
+    __syncthreads();
+}
+
+// Tiles per group of the two-level prefix: groups of 4B tiles are reduced by
+// k_group_totals when a scan has more than one group.
+__host__ __device__ constexpr int prefix_group_tiles(int B) { return 4 * B; }
+
+// Value function before tile `tile` (returned in thread 0): the fold of the
+// totals of tiles 0..tile-1 applied to the prior.  With group totals
+// (group_agg != nullptr) the fold is that of the groups before the tile's group
+// followed by the tiles of its group before it, so that no thread folds more
+// than ceil(groups / B) or 4 totals.
+template <int N, typename S>
+__device__ __forceinline__ void tile_prefix_of(const S* __restrict__ tile_agg, int tile, const Red<N, S>& prior,
+                                               S* nodes, const CombineCtx& ctx, Red<N, S>& out,
+                                               const S* __restrict__ group_agg = nullptr)
+{
+    const int t = threadIdx.x;
+    if (tile == 0) {
+        out = prior;
+        return;
+    }
+    Elem<N, S> tot;
+    if (!group_agg) {
+        fold_totals<N, S>(tile_agg, 0, tile, nodes, ctx, tot);
+    } else {
+        const int G = prefix_group_tiles(blockDim.x), g = tile / G;
+        Elem<N, S> ga, tb;
+        if (g > 0) fold_totals<N, S>(group_agg, 0, g, nodes, ctx, ga);
+        fold_totals<N, S>(tile_agg, g * G, tile, nodes, ctx, tb);
+        if (t == 0) {
+            if (g > 0)
+                combine<N, S>(tb, ga, tot, ctx);
+            else
+                tot = tb;
+        }
+    }
     if (t == 0) {
-        Elem<N, S> root;
-        node_load(slot<N, S>(nodes, B, ilog2(B), 0), root);
         Red<N, S> P = prior;
-        apply<N, S, false>(root, P, nullptr, nullptr, ctx);
+        apply<N, S, false>(tot, P, nullptr, nullptr, ctx);
         out = P;
     }
-    __syncthreads();
+}
+
+// Totals of the groups of prefix_group_tiles(B) consecutive tiles (one CTA per
+// group), for the two-level tile prefix of scans with many tiles
+template <int N, typename S>
+__global__ void __launch_bounds__(128)
+k_group_totals(const S* __restrict__ tile_agg, int nt, S* __restrict__ group_agg, CombineCtx ctx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
+    pdl_wait();                            // tile totals of the reduce kernel
+    pdl_trigger();
+    const int G = prefix_group_tiles(blockDim.x), g = blockIdx.x;
+    Elem<N, S> tot;
+    fold_totals<N, S>(tile_agg, g * G, min(nt, (g + 1) * G), nodes, ctx, tot);
+    if (threadIdx.x == 0) aos_store(group_agg, (long)g, tot);
 }
 
 // State at the end of tile `tile`, written by thread 0 to the N scalars at
@@ -694,7 +742,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
               const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
               S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
               CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
-              S* __restrict__ filtT_out, S* __restrict__ ltree)
+              S* __restrict__ filtT_out, S* __restrict__ ltree, const S* __restrict__ group_agg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -710,7 +758,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
     pdl_wait();                            // totals and aggregates of the reduce kernel
     pdl_trigger();
     Red<N, S> pin, X;
-    tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin);
+    tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
     if (last_lti)
         lti_last_tile_prefix<N, S>(ltree, pin, nodes, ctx, X);
     else

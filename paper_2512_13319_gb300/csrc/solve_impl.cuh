@@ -22,8 +22,10 @@ inline int ilog2_host(int x)
 
 template <int N, typename S>
 struct Layout {
-    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, ltree, total;
-    static Layout make(long nthr, long nt, long Tpad)
+    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, ltree, group_agg, total;
+    // filt_ws (the forward filter values of the two-filter smoother) only when
+    // two_filter; Eg (the closed-loop maps) always (RTS pass, sequential baseline)
+    static Layout make(long nthr, long nt, long Tpad, bool two_filter)
     {
         const long B = nt > 0 ? nthr / nt : 0;
         using E = Elem<N, S>;
@@ -37,9 +39,11 @@ struct Layout {
         l.Eg = o;        o = align_up(o + sizeof(S) * A::NCOMP * Tpad);
         l.thr_aff = o;   o = align_up(o + sizeof(S) * A::NCOMP * nthr);
         l.tile_aff = o;  o = align_up(o + sizeof(S) * A::NCOMP * nt);
-        l.filt_ws = o;   o = align_up(o + sizeof(S) * R::NCOMP * Tpad);
+        l.filt_ws = o;   o = align_up(o + (two_filter ? sizeof(S) * R::NCOMP * Tpad : 0));
         l.term = o;      o = align_up(o + sizeof(S) * R::NCOMP);
         l.ltree = o;     o = align_up(o + sizeof(S) * 2 * B * CoopLayout<N, S>::NE);   // last tile's tree
+        const long ng = B > 0 ? (nt + prefix_group_tiles((int)B) - 1) / prefix_group_tiles((int)B) : 0;
+        l.group_agg = o; o = align_up(o + sizeof(S) * E::NCOMP * ng);
         l.total = o;
         return l;
     }
@@ -103,7 +107,7 @@ LtiParams<N, M, S> lti_params(const map_smoother& h)
 template <int N, typename S>
 size_t rts_workspace(const map_smoother& h)
 {
-    return Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad).total;
+    return Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad, h.smoother == MAP_TWO_FILTER).total;
 }
 
 // CTAs of B threads of the filter kernels of `Prod` resident on one SM
@@ -135,7 +139,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     using R = Red<N, S>;
     const int B = h.B, nt = h.nt, K = h.K;
     const long nthr = (long)nt * B;
-    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
+    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad, h.smoother == MAP_TWO_FILTER);
     S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
     S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
     S* fin = reinterpret_cast<S*>(h.ws + L.fin);
@@ -160,6 +164,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         e0 = allow_smem(k_filter_reduce<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_group_totals<N, S>, big);
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
@@ -187,10 +192,20 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
             first = false;
         }
     }
+    // scans with more than one group of tiles: group totals for the two-level
+    // tile prefix (the last tile's total is not needed and may be absent)
+    const int G = prefix_group_tiles(B);
+    const int ng = (lti ? nt - 1 : nt) > G ? (nt + G - 1) / G : 0;
+    S* group_agg = ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr;
+    if (ng) {
+        launch(k_group_totals<N, S>, ng, B, tree_smem<N, S>(B), st, pdl && !first, (const S*)tile_agg,
+               lti ? nt - 1 : nt, group_agg, ctx);
+        first = false;
+    }
     mark();
     launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl && !first, prod, K, thr_agg, (const S*)tile_agg,
            prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT,
-           reinterpret_cast<S*>(h.ws + L.ltree));
+           reinterpret_cast<S*>(h.ws + L.ltree), (const S*)group_agg);
     mark();
     launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
            (const S*)xT, T, x_out);
@@ -211,7 +226,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const int K = h.K;
     const int B = h.B, nt = h.nt;
     const long nthr = (long)nt * B;
-    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad);
+    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad, h.smoother == MAP_TWO_FILTER);
     S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
     S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
     S* fin = reinterpret_cast<S*>(h.ws + L.fin);
@@ -277,7 +292,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
 template <int N, typename S, class Prod>
 map_status run_sequential(map_smoother& h, const Prod& prod, S* x_out, cudaStream_t st)
 {
-    const Layout<N, S> L = Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad);
+    const Layout<N, S> L = Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad, h.smoother == MAP_TWO_FILTER);
     S* Eg = reinterpret_cast<S*>(h.ws + L.Eg);
     const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     k_sequential<N, S, Prod><<<1, 32, 0, st>>>(prod, prior_of<N, S>(h), Eg, x_out, ctx);
