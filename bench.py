@@ -79,8 +79,9 @@ def work_model(n, m, K, B, nt, wbytes, r=None):
 
 
 # DRAM bytes (read + write) of one k_filter_down launch on the nx=4, T=2^20 FP32
-# workload, from one ncu capture of this kernel version (cold cache)
-K_FILTER_DOWN_DRAM_BYTES = 11.562496e6 + 42.679552e6
+# workload, from one ncu capture of this kernel version (cold cache); None
+# until the current version has been captured
+K_FILTER_DOWN_DRAM_BYTES = None
 
 
 def solve_bytes(n, m, wbytes):

@@ -248,6 +248,32 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
                 for (int j = 0; j < n; ++j) Rm[i * n + j] -= out->Gam[i * n + rk] * out->Gam[j * n + rk];
         }
         out->rank = rk;
+        // pseudo-inverse of Gam: (Gam^T Gam)^-1 Gam^T by Gauss-Jordan on the rank x rank Gram matrix
+        double* Gm = s.pivw;                    // rk x rk, then its inverse beside it
+        double* Gi = s.pivw + MAXN * MAXN;
+        for (int a = 0; a < rk; ++a)
+            for (int c = 0; c < rk; ++c) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += out->Gam[i * n + a] * out->Gam[i * n + c];
+                Gm[a * rk + c] = acc;
+                Gi[a * rk + c] = a == c ? 1.0 : 0.0;
+            }
+        for (int col = 0; col < rk; ++col) {   // symmetric positive definite: no pivoting needed
+            const double ip = 1.0 / Gm[col * rk + col];
+            for (int c = 0; c < rk; ++c) { Gm[col * rk + c] *= ip; Gi[col * rk + c] *= ip; }
+            for (int r = 0; r < rk; ++r) {
+                if (r == col) continue;
+                const double f = Gm[r * rk + col];
+                for (int c = 0; c < rk; ++c) { Gm[r * rk + c] -= f * Gm[col * rk + c]; Gi[r * rk + c] -= f * Gi[col * rk + c]; }
+            }
+        }
+        for (int e = 0; e < n * n; ++e) out->Gpinv[e] = 0.0;
+        for (int a = 0; a < rk; ++a)
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int c = 0; c < rk; ++c) acc += Gi[a * rk + c] * out->Gam[i * n + c];
+                out->Gpinv[a * n + i] = acc;
+            }
         out->flags = s.flag;
     }
 }

@@ -254,7 +254,7 @@ __device__ __forceinline__ void apply(const Elem<N, S>& e, Red<N, S>& p, S* E, S
 // ---------------------------------------------------------------------------
 template <int N, int R, typename S, bool ALPHA>
 __device__ __forceinline__ bool apply_lowrank(const Elem<N, S>& e, const S* Gam, Red<N, S>& p, S* E, S* g,
-                                              float cond_max)
+                                              float cond_max, S* Vout = nullptr)
 {
     S U[N * R];                                       // U = P Gam
 #pragma unroll
@@ -347,6 +347,10 @@ __device__ __forceinline__ bool apply_lowrank(const Elem<N, S>& e, const S* Gam,
             for (int l = 0; l < R; ++l) s = fma(W[k * R + l], Em[l * N + j], s);
             V[k * N + j] = s;
         }
+    if (Vout) {                                       // E = A - Gam V: the compact form of the map
+#pragma unroll
+        for (int q = 0; q < R * N; ++q) Vout[q] = V[q];
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll

@@ -53,6 +53,7 @@ struct LtiParams {
     S G[N * M];      // dt H^T R^-1
     S Gr[N];         // dt H^T R^-1 r
     S Gam[N * R];    // C = Gam Gam^T when lowrank (zero columns beyond the rank)
+    S Gpinv[R * N];  // pseudo-inverse of Gam (zero rows beyond the rank)
     int lowrank;     // rank(C) <= R: the per-step value-function update uses Gam
 };
 

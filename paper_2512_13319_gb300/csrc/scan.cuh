@@ -766,6 +766,11 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
+    // compact closed-loop maps: (V, g) instead of (E, g) when E = A - Gam V
+    constexpr int NAC = ((N + 1) / 2) * N + N;
+    bool compact = false;
+    if constexpr (Prod::LOWRANK && !Prod::RESETS) compact = prod.p.lowrank != 0;
+    S Vc[((N + 1) / 2) * N];
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;
@@ -790,12 +795,39 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 bool done = false;
                 if constexpr (Prod::LOWRANK) {
                     if (prod.p.lowrank)
-                        done = apply_lowrank<N, (N + 1) / 2, S, true>(e, prod.p.Gam, X, a.F, a.c, ctx.cond_max);
+                        done = apply_lowrank<N, (N + 1) / 2, S, true>(e, prod.p.Gam, X, a.F, a.c, ctx.cond_max,
+                                                                      compact ? Vc : nullptr);
                 }
-                if (!done) apply<N, S, true>(e, X, a.F, a.c, ctx);
-            }
+                if (!done) {
+                    apply<N, S, true>(e, X, a.F, a.c, ctx);
+                    if constexpr (Prod::LOWRANK && !Prod::RESETS) {
+                        if (compact) {                 // V = Gam^+ (A - E), exact: A - E lies in range(Gam)
+                            constexpr int R = (N + 1) / 2;
 #pragma unroll
-            for (int c = 0; c < NA; ++c) Eg[wis_idx(gthr, i, c, K, NA)] = comp(a, c);
+                            for (int q = 0; q < R; ++q)
+#pragma unroll
+                                for (int j = 0; j < N; ++j) {
+                                    S sv = S(0);
+#pragma unroll
+                                    for (int l = 0; l < N; ++l)
+                                        sv = fma(prod.p.Gpinv[q * N + l], e.A[l * N + j] - a.F[l * N + j], sv);
+                                    Vc[q * N + j] = sv;
+                                }
+                        }
+                    }
+                }
+            }
+            if (compact) {
+                // compact map (V, g), E = A - Gam V (linear model with low-rank noise)
+                constexpr int R = (N + 1) / 2;
+#pragma unroll
+                for (int c = 0; c < R * N; ++c) Eg[wis_idx(gthr, i, c, K, NAC)] = Vc[c];
+#pragma unroll
+                for (int c = 0; c < N; ++c) Eg[wis_idx(gthr, i, R * N + c, K, NAC)] = a.c[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < NA; ++c) Eg[wis_idx(gthr, i, c, K, NA)] = comp(a, c);
+            }
             // x_{k0} = Phi x_{k+1} + beta:  beta += Phi g,  Phi = Phi E
             S tmp[N];
             ms::mv<N, S>(comp_t.F, a.c, tmp);
@@ -1010,10 +1042,20 @@ __host__ __device__ __forceinline__ int rts_stage_stride(int K, int N) { return 
 // ---------------------------------------------------------------------------
 // phase 3: per-step smoothed states x_k = E_k x_{k+1} + g_k
 // ---------------------------------------------------------------------------
+// form of the stored closed-loop maps: (E, g), or the compact (V, g) with
+// E = A - Gam V for linear models with low-rank process noise
+template <int N, typename S>
+struct EgForm {
+    static constexpr int R = (N + 1) / 2;
+    int compact;
+    S A[N * N];
+    S Gam[N * R];
+};
+
 template <int N, typename S>
 __global__ void __launch_bounds__(128)
 k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const S* __restrict__ tile_aff,
-           const S* __restrict__ xT, long T, S* __restrict__ x_out)
+           const S* __restrict__ xT, long T, S* __restrict__ x_out, const __grid_constant__ EgForm<N, S> form)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -1039,35 +1081,81 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const
     const int SP = rts_stage_stride(K, N);
     S* st = nodes + 2 * B * CoopLayout<N, S>::NA;
     S* mine = st + t * SP;
+    if (form.compact) {
+        // x_k = A x_{k+1} - Gam (V_k x_{k+1}) + g_k
+        constexpr int R = EgForm<N, S>::R, NAC = R * N + N;
 #pragma unroll 1
-    for (int i0 = K - 1; i0 >= 0; i0 -= U) {
-        S buf[U][NA];
+        for (int i0 = K - 1; i0 >= 0; i0 -= U) {
+            S buf[U][NAC];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = i0 - u;
-            if (i >= 0 && k0 + i < T) {
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 - u;
+                if (i >= 0 && k0 + i < T) {
 #pragma unroll
-                for (int c = 0; c < NA; ++c) buf[u][c] = Eg[wis_idx(gthr, i, c, K, NA)];
+                    for (int c = 0; c < NAC; ++c) buf[u][c] = Eg[wis_idx(gthr, i, c, K, NAC)];
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = i0 - u;
-            if (i >= 0) {
-                if (k0 + i < T) {
-                    S y[N];
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 - u;
+                if (i >= 0) {
+                    if (k0 + i < T) {
+                        S vx[R], y[N];
 #pragma unroll
-                    for (int r = 0; r < N; ++r) {
-                        S acc = buf[u][N * N + r];
+                        for (int q = 0; q < R; ++q) {
+                            S acc = S(0);
 #pragma unroll
-                        for (int q = 0; q < N; ++q) acc = fma(buf[u][r * N + q], x[q], acc);
-                        y[r] = acc;
+                            for (int j = 0; j < N; ++j) acc = fma(buf[u][q * N + j], x[j], acc);
+                            vx[q] = acc;
+                        }
+#pragma unroll
+                        for (int r = 0; r < N; ++r) {
+                            S acc = buf[u][R * N + r];
+#pragma unroll
+                            for (int q = 0; q < N; ++q) acc = fma(form.A[r * N + q], x[q], acc);
+#pragma unroll
+                            for (int q = 0; q < R; ++q) acc = fma(-form.Gam[r * R + q], vx[q], acc);
+                            y[r] = acc;
+                        }
+#pragma unroll
+                        for (int j = 0; j < N; ++j) x[j] = y[j];
                     }
 #pragma unroll
-                    for (int j = 0; j < N; ++j) x[j] = y[j];
+                    for (int j = 0; j < N; ++j) mine[i * N + j] = x[j];
                 }
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int i0 = K - 1; i0 >= 0; i0 -= U) {
+            S buf[U][NA];
 #pragma unroll
-                for (int j = 0; j < N; ++j) mine[i * N + j] = x[j];
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 - u;
+                if (i >= 0 && k0 + i < T) {
+#pragma unroll
+                    for (int c = 0; c < NA; ++c) buf[u][c] = Eg[wis_idx(gthr, i, c, K, NA)];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 - u;
+                if (i >= 0) {
+                    if (k0 + i < T) {
+                        S y[N];
+#pragma unroll
+                        for (int r = 0; r < N; ++r) {
+                            S acc = buf[u][N * N + r];
+#pragma unroll
+                            for (int q = 0; q < N; ++q) acc = fma(buf[u][r * N + q], x[q], acc);
+                            y[r] = acc;
+                        }
+#pragma unroll
+                        for (int j = 0; j < N; ++j) x[j] = y[j];
+                    }
+#pragma unroll
+                    for (int j = 0; j < N; ++j) mine[i * N + j] = x[j];
+                }
             }
         }
     }

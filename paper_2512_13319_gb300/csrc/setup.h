@@ -25,6 +25,7 @@ struct SetupOut {
     double S0[MAXN * MAXN], v0[MAXN];
     double Phi[MAXN * MAXN], beta[MAXN], Sigma[MAXN * MAXN];
     double Gam[MAXN * MAXN];           // C = Gam Gam^T, Gam n x rank (leading dimension n)
+    double Gpinv[MAXN * MAXN];         // (Gam^T Gam)^-1 Gam^T, rank x n (leading dimension n)
     int rank;                          // numerical rank of C (pivoted Cholesky, relative 1e-13)
     int flags;
 };

@@ -100,7 +100,11 @@ LtiParams<N, M, S> lti_params(const map_smoother& h)
     constexpr int R = LtiParams<N, M, S>::R;
     p.lowrank = c.rank <= R;
     for (int i = 0; i < N; ++i)
-        for (int k = 0; k < R; ++k) p.Gam[i * R + k] = (k < c.rank && p.lowrank) ? S(c.Gam[i * N + k]) : S(0);
+        for (int k = 0; k < R; ++k) {
+            const bool in = k < c.rank && p.lowrank;
+            p.Gam[i * R + k] = in ? S(c.Gam[i * N + k]) : S(0);
+            p.Gpinv[k * N + i] = in ? S(c.Gpinv[k * N + i]) : S(0);
+        }
     return p;
 }
 
@@ -207,8 +211,14 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
            prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT,
            reinterpret_cast<S*>(h.ws + L.ltree), (const S*)group_agg);
     mark();
+    EgForm<N, S> form{};                     // how k_filter_down stored the closed-loop maps
+    if constexpr (Prod::LOWRANK && !Prod::RESETS) {
+        form.compact = prod.p.lowrank;
+        for (int i = 0; i < N * N; ++i) form.A[i] = prod.p.A[i];
+        for (int i = 0; i < N * EgForm<N, S>::R; ++i) form.Gam[i] = prod.p.Gam[i];
+    }
     launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
-           (const S*)xT, T, x_out);
+           (const S*)xT, T, x_out, form);
     mark();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
