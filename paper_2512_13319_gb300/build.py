@@ -39,8 +39,9 @@ def units():
            ("batch", "batch.cu", [])]
     for prec, typ in (("f32", "float"), ("f64", "double")):
         for n, m in LINEAR_SHAPES:
-            out.append((f"lin_{n}_{m}_{prec}", "inst_linear.cu",
-                        [f"-DINST_N={n}", f"-DINST_M={m}", f"-DINST_S={typ}"]))
+            for part in ((0, 1) if n <= 6 else (0,)):
+                out.append((f"lin_{n}_{m}_{prec}_{part}", "inst_linear.cu",
+                            [f"-DINST_N={n}", f"-DINST_M={m}", f"-DINST_S={typ}", f"-DINST_PART={part}"]))
         out.append((f"ct_{prec}", "inst_nonlinear.cu", ["-DINST_CT=1", f"-DINST_S={typ}"]))
         for n, m in CUBIC_SHAPES:
             out.append((f"cubic_{n}_{m}_{prec}", "inst_nonlinear.cu",

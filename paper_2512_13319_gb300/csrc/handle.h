@@ -46,16 +46,16 @@ namespace mapk {
 size_t elem_bytes(int prec);
 
 // bytes of the linear-fold constants of an (n, m) linear model in scalars of
-// es bytes: up to 64 steps per thread, 8 tree levels and the folds of fewer
-// steps (the layout of FoldLayout in lti_fold.cuh)
+// es bytes: up to 64 steps per thread, 8 tree levels and the thread-prefix
+// tables of up to 128 threads per tile (the layout of FoldLayout in lti_fold.cuh)
 inline size_t fold_bytes(int n, int m, size_t es)
 {
     const int ns = n * (n + 1) / 2, V = 16 / (int)es, P = (n + V - 1) / V * V;
     const int oG = (n * n + 2 * ns + 2 * n + 3) / 4 * 4;
     const int oL = (oG + 64 * 2 * n * m + 3) / 4 * 4;
     const int LS = (3 * n * P + 4 * n * n + 3) / 4 * 4;
-    const int HS = (n * n + 2 * ns + 2 * n + 3) / 4 * 4;
-    return es * (size_t)(oL + 8 * LS + 63 * HS + 2 * n * m * 63 * 64 / 2);
+    const int PS = (n * n + 2 * ns + 3) / 4 * 4;
+    return es * (size_t)(oL + 8 * LS + 128 * PS + 128 * 4 * n * n);
 }
 
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.

@@ -1,5 +1,5 @@
-// Folds and tile trees of a linear time-invariant model as linear functions
-// of the observations.
+// Folds, tile trees and thread prefixes of a linear time-invariant model as
+// linear functions of the observations.
 //
 // For an LTI model every element of the filter scan has the same (A, b, C, J)
 // and eta_k = G y_k - Gr with G = dt H^T R^-1 (Section 4.2 elements).  In the
@@ -19,17 +19,28 @@
 //       eta <- Te (eta - J_acc b_e) + G y_i - Gr,
 //       A <- A_acc Mi A_e,  C <- A_acc Mi C_e A_acc^T + C_acc,  J <- A_e^T Mi^T J_acc A_e + J_e.
 //
-// (2) In the tree of a tile whose B*K steps are all before T, the two children
-//     of a level-d node are folds of 2^d full threads, with the same (A_d,
-//     C_d, J_d).  With Mi = (I + C_d J_d)^-1 the parent (later child i on the
-//     left, earlier child j on the right) is
+// (2) In the up-sweep of a tile whose threads hold full folds, the two children
+//     of a level-d node are folds of 2^d threads with the same (A_d, C_d, J_d).
+//     With Mi = (I + C_d J_d)^-1 the parent (later child i on the left, earlier
+//     child j on the right) is
 //       b   = X_d b_i + b_j + Y_d eta_j,       X_d = A_d Mi,  Y_d = A_d Mi C_d,
 //       eta = eta_i + Z_d eta_j - W_d b_i,     Z_d = A_d^T Mi^T,  W_d = Z_d J_d,
 //     and (A_d+1, C_d+1, J_d+1) is the combine of (A_d, C_d, J_d) with itself.
 //
-// The reduce and down-sweep kernels evaluate (1) and (2) with these constants
-// (2 N M multiply-adds per step and 4 N^2 per tree node instead of a combine);
-// tiles that reach past T keep the general per-step fold and tree.
+// (3) The exclusive prefix of thread s of such a tile, D_s = the fold of its
+//     threads 0..s-1, has the (A, C, J) of s thread folds (table "pre") and a
+//     (b, eta) that a down-sweep on (b, eta) alone computes: the right child
+//     that starts at thread p = (2j+1) 2^d receives U (x) D, U its left sibling
+//     (level-d constants) and D the prefix of its parent (p - 2^d threads):
+//       b   = X_p b_U + Y_p eta_D + b_D,  eta = eta_U + Z_p eta_D - W_p b_U,
+//     with Mi = (I + C_U J_D)^-1, X_p = A_D Mi, Y_p = X_p C_U, Z_p = (Mi A_U)^T
+//     and W_p = Z_p J_D (table "co").  A thread then needs one combine of D_s
+//     (the one-variable case of Eq. 36, which updates a value function) with the
+//     tile's prefix.
+//
+// All constants depend on the model, K and B only.  The reduce and down-sweep
+// kernels evaluate (1)-(3) with them: 2 N M multiply-adds per step and 4 N^2
+// per tree node instead of a combine.
 #pragma once
 #include "producers.cuh"
 #include "coop.cuh"
@@ -37,14 +48,16 @@
 namespace mapk {
 
 // Layout of the constants (scalars of type S).  K-fold constants with packed
-// symmetric C, J; the Gamma_i; then per tree level d = 0..LMAX the children's
+// symmetric C, J; the Gamma_i; per tree level d = 0..LMAX the children's
 // (A_d, C_d, J_d) as an element node of CoopLayout (full rows padded to P)
-// followed by X_d, Y_d, Z_d, W_d (N x N row-major).
+// followed by X_d, Y_d, Z_d, W_d (N x N row-major); the thread-prefix
+// constants pre_s = (A, C, J) of s thread folds (s = 0..BMAX-1, C and J
+// packed); the right-child coefficients co_p = (X, Y, Z, W)_p (p = 1..BMAX-1).
 template <int N, int M, typename S>
 struct FoldLayout {
     using CL = CoopLayout<N, S>;
     static constexpr int NS = Sym<N>::SZ;
-    static constexpr int KMAX = 64, LMAX = 7;              // K <= 64, B <= 128
+    static constexpr int KMAX = 64, LMAX = 7, BMAX = 128;   // K <= 64, B <= 128
     static constexpr int oA = 0, oC = N * N, oJ = oC + NS, ob = oJ + NS, oe = ob + N;
     static constexpr int oG = (oe + N + 3) / 4 * 4;         // Gamma_i at oG + i * GS
     static constexpr int GS = 2 * N * M;                    // rows 0..N-1: b, rows N..2N-1: eta
@@ -52,12 +65,11 @@ struct FoldLayout {
     static constexpr int LN = 3 * N * CL::P;                // (A_d, C_d, J_d) node part
     static constexpr int oX = LN, oY = LN + N * N, oZ = LN + 2 * N * N, oW = LN + 3 * N * N;
     static constexpr int LS = (LN + 4 * N * N + 3) / 4 * 4;
-    // folds of r = 1 .. KMAX-1 steps (a thread that reaches T): per r the
-    // constants A, C, J, b0, eta0 (HS scalars, packed as above) then Gamma_0..r-1
-    static constexpr int oP = oL + (LMAX + 1) * LS;
-    static constexpr int HS = (N * N + 2 * NS + 2 * N + 3) / 4 * 4;
-    __host__ __device__ static constexpr int poff(int r) { return oP + (r - 1) * HS + GS * (r - 1) * r / 2; }
-    static constexpr int TOTAL = oP + (KMAX - 1) * HS + GS * (KMAX - 1) * KMAX / 2;
+    static constexpr int PS = (N * N + 2 * NS + 3) / 4 * 4; // pre_s at oPre + s * PS: A, C, J
+    static constexpr int oPre = oL + (LMAX + 1) * LS;
+    static constexpr int CS = 4 * N * N;                    // co_p at oCo + p * CS: X, Y, Z, W
+    static constexpr int oCo = oPre + BMAX * PS;
+    static constexpr int TOTAL = oCo + BMAX * CS;
 };
 
 // Plan-time helpers of k_lti_fold (FP64, plain loops: run once per model and
@@ -140,9 +152,40 @@ __device__ inline void inv_I_plus(int n, const double* c, const double* j, doubl
     }
 }
 
+// coefficients of the (b, eta) part of U (x) D (U the later operand):
+// Mi = (I + C_U J_D)^-1, X = A_D Mi, Y = X C_U, Z = (Mi A_U)^T, W = Z J_D;
+// wk: 4 n^2 scratch
+__device__ inline void pair_coeffs(int n, const double* AU, const double* CU, const double* AD, const double* JD,
+                                   double* X, double* Y, double* Z, double* W, double* wk)
+{
+    double* Mi = wk;
+    double* T = wk + n * n;
+    inv_I_plus(n, CU, JD, Mi, wk + 2 * n * n);
+    mm(n, AD, Mi, X);
+    mm(n, X, CU, Y);
+    mm(n, Mi, AU, T);
+    tr(n, T, Z);
+    mm(n, Z, JD, W);
+}
+
+// (A, C, J) of U (x) D from the coefficients of pair_coeffs:
+// A = X A_U, C = Y A_D^T + C_D, J = W A_U + J_U; wk: n^2 scratch
+__device__ inline void pair_acj(int n, const double* AU, const double* JU, const double* AD, const double* CD,
+                                const double* X, const double* Y, const double* W, double* Ao, double* Co,
+                                double* Jo, double* wk)
+{
+    mm(n, X, AU, Ao);
+    tr(n, AD, wk);
+    mm(n, Y, wk, Co);
+    mm(n, W, AU, Jo);
+#pragma unroll 1
+    for (int q = 0; q < n * n; ++q) { Co[q] += CD[q]; Jo[q] += JU[q]; }
+}
+
 }  // namespace fold_detail
 
-// One CTA of KMAX threads; thread j carries Gamma_j.  FP64 throughout.
+// One CTA of KMAX threads; thread j carries Gamma_j.  FP64 throughout.  LB:
+// log2 of the threads per tile (B = 2^LB <= BMAX).
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(64)
 k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
@@ -152,10 +195,11 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
     namespace fd = fold_detail;
     constexpr int NN = N * N;
     // accumulated composite (Ac, Cc, Jc), per-step maps (Tb, Te), offsets,
-    // the element's constants and thread-0 scratch
+    // the element's constants, thread-0 scratch and the tree levels' (A, C, J)
     __shared__ double Ac[NN], Cc[NN], Jc[NN], Tb[NN], Te[NN], ob[N], oe[N];
     __shared__ double Ae[NN], Ce[NN], Je[NN], be[N], Gm[N * M], Gr[N];
-    __shared__ double Mi[NN], T1[NN], T2[NN], T3[NN], wk[2 * NN], u[N], w[N];
+    __shared__ double Mi[NN], T1[NN], T2[NN], T3[NN], wk[4 * NN], u[N], w[N];
+    __shared__ double LA[FL::LMAX + 1][NN], LC[FL::LMAX + 1][NN], LJ[FL::LMAX + 1][NN];
     const int j = threadIdx.x;
     if (j == 0) {
 #pragma unroll 1
@@ -180,30 +224,6 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
     double gb[N * M], ge[N * M];                  // Gamma_j (b rows, eta rows)
 #pragma unroll 1
     for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = j == 0 ? Gm[q] : 0.0; }
-    // the r-step fold (r < K): constants by thread 0, Gamma_j by thread j < r
-    auto write_partial = [&](int r) {
-        S* pb = out + FL::poff(r);
-        if (j == 0) {
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) pb[FL::oA + q] = S(Ac[q]);
-#pragma unroll 1
-            for (int a = 0; a < N; ++a) {
-#pragma unroll 1
-                for (int c = a; c < N; ++c) {
-                    pb[FL::oC + Sym<N>::at(a, c)] = S(0.5 * (Cc[a * N + c] + Cc[c * N + a]));
-                    pb[FL::oJ + Sym<N>::at(a, c)] = S(0.5 * (Jc[a * N + c] + Jc[c * N + a]));
-                }
-                pb[FL::ob + a] = S(ob[a]);
-                pb[FL::oe + a] = S(oe[a]);
-            }
-        }
-        if (j < r) {
-            S* g = pb + FL::HS + j * FL::GS;
-#pragma unroll 1
-            for (int q = 0; q < N * M; ++q) { g[q] = S(gb[q]); g[N * M + q] = S(ge[q]); }
-        }
-    };
-    if (K > 1) write_partial(1);
 #pragma unroll 1
     for (int i = 1; i < K; ++i) {
         if (j == 0) {
@@ -257,61 +277,102 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
             for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = Gm[q]; }
         }
         __syncthreads();
-        if (i + 1 < K) write_partial(i + 1);
     }
     if (j < K) {
         S* g = out + FL::oG + j * FL::GS;
 #pragma unroll 1
         for (int q = 0; q < N * M; ++q) { g[q] = S(gb[q]); g[N * M + q] = S(ge[q]); }
     }
-    if (j != 0) return;
+    if (j == 0) {
 #pragma unroll 1
-    for (int q = 0; q < NN; ++q) out[FL::oA + q] = S(Ac[q]);
+        for (int q = 0; q < NN; ++q) out[FL::oA + q] = S(Ac[q]);
 #pragma unroll 1
-    for (int a = 0; a < N; ++a) {
+        for (int a = 0; a < N; ++a) {
 #pragma unroll 1
-        for (int c = a; c < N; ++c) {
-            out[FL::oC + Sym<N>::at(a, c)] = S(0.5 * (Cc[a * N + c] + Cc[c * N + a]));
-            out[FL::oJ + Sym<N>::at(a, c)] = S(0.5 * (Jc[a * N + c] + Jc[c * N + a]));
-        }
-        out[FL::ob + a] = S(ob[a]);
-        out[FL::oe + a] = S(oe[a]);
-    }
-    // tree levels: level d holds the constants of its children
-#pragma unroll 1
-    for (int d = 0; d <= LB && d <= FL::LMAX; ++d) {
-        S* lv = out + FL::oL + d * FL::LS;
-#pragma unroll 1
-        for (int a = 0; a < N; ++a)
-#pragma unroll 1
-            for (int c = 0; c < CL::P; ++c) {
-                const bool in = c < N;
-                lv[CL::oA + a * CL::P + c] = in ? S(Ac[a * N + c]) : S(0);
-                lv[CL::oC + a * CL::P + c] = in ? S(0.5 * (Cc[a * N + c] + Cc[c * N + a])) : S(0);
-                lv[CL::oJ + a * CL::P + c] = in ? S(0.5 * (Jc[a * N + c] + Jc[c * N + a])) : S(0);
+            for (int c = a; c < N; ++c) {
+                out[FL::oC + Sym<N>::at(a, c)] = S(0.5 * (Cc[a * N + c] + Cc[c * N + a]));
+                out[FL::oJ + Sym<N>::at(a, c)] = S(0.5 * (Jc[a * N + c] + Jc[c * N + a]));
             }
-        if (d == LB) break;
-        // X = A Mi, Y = A Mi C, Z = (Mi A)^T, W = Z J with Mi = (I + C J)^-1
-        fd::inv_I_plus(N, Cc, Jc, Mi, wk);
-        fd::mm(N, Ac, Mi, T1);                    // X
-        fd::mm(N, T1, Cc, Tb);                    // Y
-        fd::mm(N, Mi, Ac, T2);
-        fd::tr(N, T2, Te);                        // Z
-        fd::mm(N, Te, Jc, T3);                    // W
+            out[FL::ob + a] = S(ob[a]);
+            out[FL::oe + a] = S(oe[a]);
+        }
+        // tree levels: level d holds the constants of its children
+#pragma unroll 1
+        for (int d = 0; d <= LB && d <= FL::LMAX; ++d) {
+            S* lv = out + FL::oL + d * FL::LS;
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) { LA[d][q] = Ac[q]; LC[d][q] = Cc[q]; LJ[d][q] = Jc[q]; }
+#pragma unroll 1
+            for (int a = 0; a < N; ++a)
+#pragma unroll 1
+                for (int c = 0; c < CL::P; ++c) {
+                    const bool in = c < N;
+                    lv[CL::oA + a * CL::P + c] = in ? S(Ac[a * N + c]) : S(0);
+                    lv[CL::oC + a * CL::P + c] = in ? S(0.5 * (Cc[a * N + c] + Cc[c * N + a])) : S(0);
+                    lv[CL::oJ + a * CL::P + c] = in ? S(0.5 * (Jc[a * N + c] + Jc[c * N + a])) : S(0);
+                }
+            if (d == LB) break;
+            fd::pair_coeffs(N, Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);   // X, Y, Z, W
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) {
+                lv[FL::oX + q] = S(T1[q]);
+                lv[FL::oY + q] = S(Tb[q]);
+                lv[FL::oZ + q] = S(Te[q]);
+                lv[FL::oW + q] = S(T3[q]);
+            }
+            fd::pair_acj(N, Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
+        }
+    }
+    __syncthreads();
+    // thread prefixes, p = j and j + KMAX: pre_p = the fold of p threads (pre_0
+    // the identity) and, for p > 0, co_p.  With 2^d the lowest set bit of p,
+    // pre_p = (level-d node) (x) pre_{p - 2^d}; unrolled over the set bits of p
+    // from the highest (earliest threads) down, pre_p is a product of at most
+    // LB level nodes.  (A sequential recurrence pre_{p+1} = fold (x) pre_p
+    // compounds its rounding errors from thread to thread and is unstable for
+    // models whose interval elements are ill-conditioned.)
+    const int B = 1 << LB;
+#pragma unroll 1
+    for (int p = j; p < B; p += FL::KMAX) {
+        double pA[NN], pC[NN], pJ[NN], X[NN], Y[NN], Z[NN], W[NN], nA[NN], nC[NN], nJ[NN], pw[4 * NN];
 #pragma unroll 1
         for (int q = 0; q < NN; ++q) {
-            lv[FL::oX + q] = S(T1[q]);
-            lv[FL::oY + q] = S(Tb[q]);
-            lv[FL::oZ + q] = S(Te[q]);
-            lv[FL::oW + q] = S(T3[q]);
+            pA[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+            pC[q] = 0.0;
+            pJ[q] = 0.0;
         }
-        // parent: A = X A, C = Y A^T + C, J = W A + J
-        fd::mm(N, T1, Ac, T2);
-        fd::tr(N, Ac, wk);
-        fd::mm(N, Tb, wk, Mi);
-        fd::mm(N, T3, Ac, wk + NN);
 #pragma unroll 1
-        for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] += Mi[q]; Jc[q] += wk[NN + q]; }
+        for (int d = LB - 1; d >= 0; --d) {
+            if (!((p >> d) & 1)) continue;
+            fd::pair_coeffs(N, LA[d], LC[d], pA, pJ, X, Y, Z, W, pw);
+            fd::pair_acj(N, LA[d], LJ[d], pA, pC, X, Y, W, nA, nC, nJ, pw);
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) { pA[q] = nA[q]; pC[q] = nC[q]; pJ[q] = nJ[q]; }
+        }
+        // co_p: the coefficients of the last (lowest-bit) product
+        if (p > 0) {
+            S* co = out + FL::oCo + p * FL::CS;
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) {
+                co[q] = S(X[q]);
+                co[NN + q] = S(Y[q]);
+                co[2 * NN + q] = S(Z[q]);
+                co[3 * NN + q] = S(W[q]);
+            }
+        }
+        S* pr = out + FL::oPre + p * FL::PS;
+#pragma unroll 1
+        for (int a = 0; a < N; ++a) {
+#pragma unroll 1
+            for (int c = 0; c < N; ++c) pr[a * N + c] = S(pA[a * N + c]);
+#pragma unroll 1
+            for (int c = a; c < N; ++c) {
+                pr[NN + Sym<N>::at(a, c)] = S(0.5 * (pC[a * N + c] + pC[c * N + a]));
+                pr[NN + FL::NS + Sym<N>::at(a, c)] = S(0.5 * (pJ[a * N + c] + pJ[c * N + a]));
+            }
+        }
     }
 }
 
@@ -359,48 +420,6 @@ __device__ __forceinline__ void lti_linear_fold(const Prod& prod, const S* __res
     for (int q = 0; q < N; ++q) { bq[q] = ab[q]; bq[N + q] = ae[q]; }
 }
 
-// The element of a thread whose first r < K steps are before T (the rest are
-// identity padding): the r-step fold from its constants pb (FoldLayout::poff(r)
-// block, staged in shared memory) and its observations yq (r rows of M, staged)
-template <int N, int M, typename S>
-__device__ __forceinline__ void lti_partial_fold_elem(const S* pb, const S* yq, int r, Elem<N, S>& G)
-{
-    using FL = FoldLayout<N, M, S>;
-#pragma unroll
-    for (int q = 0; q < N * N; ++q) G.A[q] = pb[FL::oA + q];
-#pragma unroll
-    for (int q = 0; q < Sym<N>::SZ; ++q) { G.C[q] = pb[FL::oC + q]; G.J[q] = pb[FL::oJ + q]; }
-#pragma unroll
-    for (int q = 0; q < N; ++q) { G.b[q] = pb[FL::ob + q]; G.eta[q] = pb[FL::oe + q]; }
-#pragma unroll 4
-    for (int i = 0; i < r; ++i) {
-        const S* g = pb + FL::HS + i * FL::GS;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int c = 0; c < M; ++c) {
-                G.b[a] = fma(g[a * M + c], yq[i * M + c], G.b[a]);
-                G.eta[a] = fma(g[(N + a) * M + c], yq[i * M + c], G.eta[a]);
-            }
-    }
-}
-
-// The full element of one thread's K full steps (constants + linear fold)
-template <int N, typename S, class Prod>
-__device__ __forceinline__ void lti_fold_elem(const Prod& prod, const S* __restrict__ fold, const S* gam,
-                                              int K, long k0, Elem<N, S>& G)
-{
-    using FL = FoldLayout<N, Prod::W, S>;
-#pragma unroll
-    for (int q = 0; q < N * N; ++q) G.A[q] = __ldg(fold + FL::oA + q);
-#pragma unroll
-    for (int q = 0; q < Sym<N>::SZ; ++q) { G.C[q] = __ldg(fold + FL::oC + q); G.J[q] = __ldg(fold + FL::oJ + q); }
-    S bq[2 * N];
-    lti_linear_fold<N, S>(prod, fold, gam, K, k0, bq);
-#pragma unroll
-    for (int q = 0; q < N; ++q) { G.b[q] = bq[q]; G.eta[q] = bq[N + q]; }
-}
-
 // Up-sweep of a full tile's tree on the (b, eta) parts: bq holds 2B nodes of
 // 2N scalars (tree levels as lvl_off), leaves stored by the caller; lv the
 // level constants (FoldLayout level blocks, in shared memory).
@@ -439,51 +458,80 @@ __device__ void lti_tree_up(S* bq, const S* lv)
     __syncthreads();
 }
 
-// Down-sweep of a full tile's tree: the value function before every leaf
-// (value nodes pre, 2B slots of CoopLayout::NR) from the prefix of the tile
-// (stored by the caller at the root slot), with the left children's elements
-// given by the level constants and the (b, eta) nodes of the up-sweep.
+// Down-sweep of the tile's tree on the (b, eta) parts, in place over the
+// up-sweep nodes bq (item (3) above): on return leaf t of bq holds the (b, eta)
+// of the fold of threads 0..t-1 (zero for t = 0).  A left child takes its
+// parent's prefix; the right child starting at thread p takes the left
+// sibling's up-sweep value combined with it through co_p (global memory).
+// Leaf t's prefix uses only the leaves before t.
 template <int N, int M, typename S>
-__device__ void lti_tree_down(const S* bq, const S* lv, S* pre, S* scr_all, const CombineCtx& ctx,
-                              Red<N, S>& out)
+__device__ void lti_tree_down_linear(S* bq, const S* __restrict__ co)
 {
     using FL = FoldLayout<N, M, S>;
-    using L = CoopLayout<N, S>;
-    const int B = blockDim.x, LB = 31 - __clz(B);
-    const int NL = L::NL, ng = B / NL, g = threadIdx.x / NL, r = threadIdx.x & (NL - 1);
-    S* scr = scr_all + g * L::NSCR;
-    auto lvl_off = [B](int d) { return 2 * B - ((2 * B) >> d); };
+    constexpr int NN = N * N;
+    const int B = blockDim.x, t = threadIdx.x;
+    const int LB = 31 - __clz(B);
+    if (t < 2 * N) bq[(2 * B - 2) * 2 * N + t] = S(0);            // root: empty prefix
     for (int d = LB - 1; d >= 0; --d) {
         __syncthreads();
         const int cnt = B >> (d + 1);
-        for (int base = 0; base < cnt; base += ng) {
-            const int j = base + g;
-            const bool act = j < cnt;
-            if (__any_sync(0xffffffffu, act)) {
-                const int jj = act ? j : base;
-                const S* par = pre + (lvl_off(d + 1) + jj) * L::NR;
-                S* lft = pre + (lvl_off(d) + 2 * jj) * L::NR;
-                S* rgt = lft + L::NR;
-                const S* lq = bq + (lvl_off(d) + 2 * jj) * 2 * N;         // left child's (b, eta)
-                coop_apply_parts<N, S>(lv + d * FL::LS, lq, lq + N, par, rgt, scr, act, ctx);
-                __syncwarp();
-                if (act)
-                    for (int i = r; i < L::NR; i += NL) lft[i] = par[i];
+        if (t < cnt) {
+            const S* par = bq + (2 * B - ((2 * B) >> (d + 1)) + t) * 2 * N;
+            S* lft = bq + (2 * B - ((2 * B) >> d) + 2 * t) * 2 * N;  // left child = U
+            S* rgt = lft + 2 * N;
+            const S* c = co + ((2 * t + 1) << d) * FL::CS;
+            S bD[N], eD[N], bU[N], eU[N];
+#pragma unroll
+            for (int q = 0; q < N; ++q) { bD[q] = par[q]; eD[q] = par[N + q]; bU[q] = lft[q]; eU[q] = lft[N + q]; }
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                S sb = bD[a], se = eU[a];
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    sb = fma(__ldg(c + a * N + k), bU[k], sb);
+                    sb = fma(__ldg(c + NN + a * N + k), eD[k], sb);
+                    se = fma(__ldg(c + 2 * NN + a * N + k), eD[k], se);
+                    se = fma(-__ldg(c + 3 * NN + a * N + k), bU[k], se);
+                }
+                rgt[a] = sb;
+                rgt[N + a] = se;
             }
+#pragma unroll
+            for (int q = 0; q < N; ++q) { lft[q] = bD[q]; lft[N + q] = eD[q]; }
         }
     }
     __syncthreads();
-    node_load(pre + (long)threadIdx.x * L::NR, out);
 }
 
-// LTI tile-tree shared memory inside the element-tree area: value nodes, the
-// (b, eta) nodes and the level constants (offsets in scalars)
+// Value function before the first step of thread t of the tile: its prefix
+// D_t (constants pre_t, (b, eta) from the down-sweep at dleaf) applied to the
+// tile's prefix pin (one-variable combine, Eq. 36); thread 0 takes pin itself.
+template <int N, int M, typename S>
+__device__ __forceinline__ void lti_thread_value(const S* __restrict__ fold, const S* dleaf, const Red<N, S>& pin,
+                                                 const CombineCtx& ctx, Red<N, S>& X)
+{
+    using FL = FoldLayout<N, M, S>;
+    X = pin;
+    if (threadIdx.x == 0) return;
+    const S* pr = fold + FL::oPre + threadIdx.x * FL::PS;
+    Elem<N, S> D;
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) D.A[q] = __ldg(pr + q);
+#pragma unroll
+    for (int q = 0; q < Sym<N>::SZ; ++q) { D.C[q] = __ldg(pr + N * N + q); D.J[q] = __ldg(pr + N * N + FL::NS + q); }
+#pragma unroll
+    for (int q = 0; q < N; ++q) { D.b[q] = dleaf[q]; D.eta[q] = dleaf[N + q]; }
+    apply<N, S, false>(D, X, nullptr, nullptr, ctx);
+}
+
+// LTI tile-tree shared memory inside the element-tree area (offsets in
+// scalars): the (b, eta) nodes, the level constants, the tile's prefix
 template <int N, int M, typename S>
 struct LtiTreeSmem {
-    __host__ __device__ static constexpr int pre(int) { return 0; }
-    __host__ __device__ static constexpr int bq(int B) { return 2 * B * CoopLayout<N, S>::NR; }
-    __host__ __device__ static constexpr int lv(int B) { return (bq(B) + 2 * B * 2 * N + 3) / 4 * 4; }
-    __host__ __device__ static constexpr int end(int B, int LB) { return lv(B) + (LB + 1) * FoldLayout<N, M, S>::LS; }
+    __host__ __device__ static constexpr int bq(int) { return 0; }
+    __host__ __device__ static constexpr int lv(int B) { return (2 * B * 2 * N + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int pin(int B, int LB) { return lv(B) + (LB + 1) * FoldLayout<N, M, S>::LS; }
+    __host__ __device__ static constexpr int end(int B, int LB) { return pin(B, LB) + CoopLayout<N, S>::NR; }
 };
 
 }  // namespace mapk

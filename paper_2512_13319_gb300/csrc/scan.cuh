@@ -445,31 +445,40 @@ __device__ __forceinline__ int down_tile() { return blockIdx.x == 0 ? gridDim.x 
 // Exclusive prefix (value function before the thread's first step) of every
 // thread of a tile from the tile's prefix `pin` (valid in thread 0): the
 // tile's up-sweep over the per-thread aggregates and the down-sweep.
-// With linear-fold constants (fold != nullptr, lti_fold.cuh) the reduce
-// kernel has left (b, eta) aggregates (2N components) for the full tiles
-// 0..gridDim.x-2 and their trees run on those (the last tile takes
-// lti_last_tile_tree / lti_last_tile_prefix instead).
+// With linear-fold constants (fold != nullptr, lti_fold.cuh) the tree runs on
+// (b, eta) parts only: the leaves are the per-thread (b, eta) aggregates (2N
+// components) that the reduce kernel left in thr_agg, or with use_leaf `leaf`
+// (the last tile, see lti_last_tile_leaf), and every thread ends with one
+// one-variable combine of its prefix with pin.
 template <int N, typename S, class Prod>
-__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, const S* __restrict__ thr_agg,
-                                                   const Red<N, S>& pin, const S* __restrict__ fold, S* nodes,
+__device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, int K, const S* __restrict__ thr_agg,
+                                                   const Red<N, S>& pin, const S* __restrict__ fold,
+                                                   bool use_leaf, const S (&leaf)[2 * N], S* nodes,
                                                    const CombineCtx& ctx, Red<N, S>& X)
 {
     const int B = blockDim.x, t = threadIdx.x;
     const long gthr = (long)tile * B + t;
     if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        if (fold && tile + 1 < (int)gridDim.x) {
-            using FL = FoldLayout<N, Prod::W, S>;
-            using TS = LtiTreeSmem<N, Prod::W, S>;
+        if (fold) {
+            constexpr int M = Prod::W;
+            using FL = FoldLayout<N, M, S>;
+            using TS = LtiTreeSmem<N, M, S>;
             const int LB = ilog2(B);
-            S* pre = nodes + TS::pre(B);
             S* bq = nodes + TS::bq(B);
             S* lv = nodes + TS::lv(B);
-            for (int q = t; q < (LB + 1) * FL::LS; q += B) lv[q] = fold[FL::oL + q];
+            S* ps = nodes + TS::pin(B, LB);
+            for (int q = t; q < LB * FL::LS; q += B) lv[q] = fold[FL::oL + q];
 #pragma unroll
-            for (int c = 0; c < 2 * N; ++c) bq[t * 2 * N + c] = thr_agg[wi_idx(gthr, c, 2 * N)];
-            if (t == 0) node_store(pin, pre + (2 * B - 2) * CoopLayout<N, S>::NR);
-            lti_tree_up<N, Prod::W, S>(bq, lv);
-            lti_tree_down<N, Prod::W, S>(bq, lv, pre, scratch_of<N, S>(nodes), ctx, X);
+            for (int c = 0; c < 2 * N; ++c) bq[t * 2 * N + c] = use_leaf ? leaf[c] : thr_agg[wi_idx(gthr, c, 2 * N)];
+            if (t == 0) node_store(pin, ps);
+            lti_tree_up<N, M, S>(bq, lv);
+            lti_tree_down_linear<N, M, S>(bq, fold + FL::oCo);
+            Red<N, S> P;
+            node_load(ps, P);
+            if (gthr * K < prod.T)
+                lti_thread_value<N, M, S>(fold, bq + t * 2 * N, P, ctx, X);
+            else
+                X = P;                          // no steps: the value is not used
             return;
         }
     }
@@ -482,80 +491,46 @@ __device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, c
     coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
 }
 
-// Linear-fold mode, last tile: the per-thread aggregates, written to thr_agg
-// as full elements (the reduce kernel does not cover this tile).  A thread
-// whose K steps are before T takes the K-step linear fold, the one that
-// reaches T the r-step fold, threads past T the identity.  gam: shared memory
-// for the Gamma_i of the K-step fold, followed by room for the r-step fold's
-// constants and observations (lti_last_tile_smem scalars in all).
-template <int N, int M>
-__host__ __device__ constexpr int lti_last_tile_smem(int K)
-{
-    using FL = FoldLayout<N, M, float>;        // offsets in scalars do not depend on the type
-    return (K * FL::GS + 3) / 4 * 4 + (FL::HS + (FL::KMAX - 1) * FL::GS + 3) / 4 * 4 + FL::KMAX * M;
-}
-
+// Shared memory (bytes) that the linear-fold mode of the down-sweep kernels
+// needs: the staged Gamma_i of lti_last_tile_leaf and the LtiTreeSmem area
+// (0 for producers without the linear fold)
 template <int N, typename S, class Prod>
-__device__ __forceinline__ void lti_last_tile_leaves(const Prod& prod, int tile, int K, const S* __restrict__ fold,
-                                                     S* gam, Elem<N, S>& G)
+__host__ __device__ constexpr size_t lti_down_smem(int B, int K)
 {
     if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        constexpr int M = Prod::W;
-        using FL = FoldLayout<N, M, S>;
-        const int B = blockDim.x, t = threadIdx.x;
-        const long gthr = (long)tile * B + t;
-        const long t0 = (long)tile * B * K;                 // first step of the tile
-        const long tl = prod.T - t0;                        // steps of the tile before T
-        const int ts = (int)(tl / K), rs = (int)(tl - (long)ts * K);   // thread that reaches T, its steps
-        S* pbs = gam + (K * FL::GS + 3) / 4 * 4;                      // its fold constants
-        S* yqs = pbs + (FL::HS + rs * FL::GS + 3) / 4 * 4;           // its observations
-        for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
-        if (rs > 0) {
-            const S* pb = fold + FL::poff(rs);
-            for (int q = t; q < FL::HS + rs * FL::GS; q += B) pbs[q] = pb[q];
-            for (int q = t; q < rs * M; q += B) yqs[q] = prod.y[(t0 + (long)ts * K) * M + q];
-        }
-        __syncthreads();
-        const long k0 = gthr * K;
-        if (t < ts)
-            lti_fold_elem<N, S>(prod, fold, gam, K, k0, G);
-        else if (t == ts && rs > 0)
-            lti_partial_fold_elem<N, M, S>(pbs, yqs, rs, G);
-        else
-            set_identity(G);
-        __syncthreads();
+        int LB = 0;
+        while ((2 << LB) <= B) ++LB;
+        const int g = K * FoldLayout<N, Prod::W, S>::GS, tr = LtiTreeSmem<N, Prod::W, S>::end(B, LB);
+        return sizeof(S) * (size_t)(g > tr ? g : tr);
+    } else {
+        return 0;
     }
 }
 
-// Linear-fold mode, last tile, before the wait for the reduce kernel: the
-// tile's leaves and up-sweep (the general sub-warp tree, as the tile reaches
-// past T), parked in global memory (ltree, 2B nodes) while the shared memory
-// serves the tile-prefix reduction
+// Linear-fold mode, last tile (which the reduce kernel does not cover), before
+// the wait for the reduce kernel: the thread's leaf (b, eta) in registers.  A
+// thread whose K steps are all before T takes the K-step linear fold; the
+// others take zero, which only the prefixes of threads after them see (the
+// thread that reaches T and those past it fold or skip their steps one by
+// one).  Stages the Gamma_i in `nodes` (K * 2 N M scalars); ends with a barrier.
 template <int N, typename S, class Prod>
-__device__ __forceinline__ void lti_last_tile_tree(const Prod& prod, int tile, int K, const S* __restrict__ fold,
-                                                   S* nodes, S* __restrict__ ltree, const CombineCtx& ctx)
+__device__ __forceinline__ void lti_last_tile_leaf(const Prod& prod, int tile, int K, const S* __restrict__ fold,
+                                                   S* nodes, S (&leaf)[2 * N])
 {
-    const int B = blockDim.x, t = threadIdx.x;
-    Elem<N, S> G;
-    set_identity(G);
-    lti_last_tile_leaves<N, S>(prod, tile, K, fold, nodes + tree_smem<N, S>(B) / sizeof(S), G);
-    node_store(G, slot<N, S>(nodes, B, 0, t));
-    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
-    const int cnt = 2 * B * CoopLayout<N, S>::NE;
-    for (int q = t; q < cnt; q += B) ltree[q] = nodes[q];
-    __syncthreads();
-}
-
-// the parked tree back into shared memory, then the down-sweep from pin
-template <int N, typename S>
-__device__ __forceinline__ void lti_last_tile_prefix(const S* __restrict__ ltree, const Red<N, S>& pin, S* nodes,
-                                                     const CombineCtx& ctx, Red<N, S>& X)
-{
-    const int B = blockDim.x, t = threadIdx.x;
-    const int cnt = 2 * B * CoopLayout<N, S>::NE;
-    for (int q = t; q < cnt; q += B) nodes[q] = ltree[q];
-    __syncthreads();                       // the whole tree is back before the root takes pin
-    coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
+    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+        using FL = FoldLayout<N, Prod::W, S>;
+        const int B = blockDim.x, t = threadIdx.x;
+        const long k0 = ((long)tile * B + t) * K;
+        for (int q = t; q < K * FL::GS; q += B) nodes[q] = fold[FL::oG + q];
+        __syncthreads();
+        if (k0 + K <= prod.T) {
+            lti_linear_fold<N, S>(prod, fold, nodes, K, k0, leaf);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2 * N; ++c) leaf[c] = S(0);
+        }
+        __syncthreads();
+    }
 }
 
 // The thread of the last tile that holds step T-1 writes the value function
@@ -742,7 +717,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
               const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
               S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
               CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
-              S* __restrict__ filtT_out, S* __restrict__ ltree, const S* __restrict__ group_agg)
+              S* __restrict__ filtT_out, const S* __restrict__ group_agg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -754,15 +729,13 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
     constexpr int NA = Aff<N, S>::NCOMP;
 
     const bool last_lti = fold && tile + 1 == (int)gridDim.x;
-    if (last_lti) lti_last_tile_tree<N, S>(prod, tile, K, fold, nodes, ltree, ctx);
+    S leaf[2 * N] = {};
+    if (last_lti) lti_last_tile_leaf<N, S>(prod, tile, K, fold, nodes, leaf);
     pdl_wait();                            // totals and aggregates of the reduce kernel
     pdl_trigger();
     Red<N, S> pin, X;
     tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
-    if (last_lti)
-        lti_last_tile_prefix<N, S>(ltree, pin, nodes, ctx, X);
-    else
-        tile_thread_prefix<N, S>(prod, tile, thr_agg, pin, fold, nodes, ctx, X);
+    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, fold, last_lti, leaf, nodes, ctx, X);
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
@@ -860,8 +833,7 @@ __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 const S* __restrict__ tile_agg, const Red<N, S> prior, S* __restrict__ filt_ws,
                 S* __restrict__ filt_out, CombineCtx ctx, const S* __restrict__ fold,
-                S* __restrict__ final_out, S* __restrict__ xT_out, S* __restrict__ filtT_out,
-                S* __restrict__ ltree)
+                S* __restrict__ final_out, S* __restrict__ xT_out, S* __restrict__ filtT_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -872,15 +844,13 @@ k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
     const long T = prod.T;
     constexpr int NR = Red<N, S>::NCOMP;
     const bool last_lti = fold && tile + 1 == (int)gridDim.x;
-    if (last_lti) lti_last_tile_tree<N, S>(prod, tile, K, fold, nodes, ltree, ctx);
+    S leaf[2 * N] = {};
+    if (last_lti) lti_last_tile_leaf<N, S>(prod, tile, K, fold, nodes, leaf);
     pdl_wait();
     pdl_trigger();
     Red<N, S> pin, X;
     tile_prefix_of<N, S>(tile_agg, tile, prior, nodes, ctx, pin);
-    if (last_lti)
-        lti_last_tile_prefix<N, S>(ltree, pin, nodes, ctx, X);
-    else
-        tile_thread_prefix<N, S>(prod, tile, thr_agg, pin, fold, nodes, ctx, X);
+    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, fold, last_lti, leaf, nodes, ctx, X);
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;

@@ -22,7 +22,7 @@ inline int ilog2_host(int x)
 
 template <int N, typename S>
 struct Layout {
-    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, ltree, group_agg, total;
+    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, group_agg, total;
     // filt_ws (the forward filter values of the two-filter smoother) only when
     // two_filter; Eg (the closed-loop maps) always (RTS pass, sequential baseline)
     static Layout make(long nthr, long nt, long Tpad, bool two_filter)
@@ -41,7 +41,6 @@ struct Layout {
         l.tile_aff = o;  o = align_up(o + sizeof(S) * A::NCOMP * nt);
         l.filt_ws = o;   o = align_up(o + (two_filter ? sizeof(S) * R::NCOMP * Tpad : 0));
         l.term = o;      o = align_up(o + sizeof(S) * R::NCOMP);
-        l.ltree = o;     o = align_up(o + sizeof(S) * 2 * B * CoopLayout<N, S>::NE);   // last tile's tree
         const long ng = B > 0 ? (nt + prefix_group_tiles((int)B) - 1) / prefix_group_tiles((int)B) : 0;
         l.group_agg = o; o = align_up(o + sizeof(S) * E::NCOMP * ng);
         l.total = o;
@@ -157,8 +156,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const bool lti = fold != nullptr;
 
     const size_t sh_reduce = tree_smem<N, S>(B);
-    const size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B)) +
-                           (lti ? sizeof(S) * (size_t)lti_last_tile_smem<N, Prod::W>(K) : 0);
+    const size_t sh_down = std::max({tree_smem<N, S>(B), aff_tree_smem<N, S>(B), lti_down_smem<N, S, Prod>(B, K)});
     const size_t sh_rts = rts_smem<N, S>(B, K);
 
     static std::once_flag once;
@@ -209,7 +207,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     mark();
     launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl && !first, prod, K, thr_agg, (const S*)tile_agg,
            prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT,
-           reinterpret_cast<S*>(h.ws + L.ltree), (const S*)group_agg);
+           (const S*)group_agg);
     mark();
     EgForm<N, S> form{};                     // how k_filter_down stored the closed-loop maps
     if constexpr (Prod::LOWRANK && !Prod::RESETS) {
@@ -248,7 +246,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
     const bool lti = fold != nullptr;          // forward scan in linear-fold mode (see run_rts)
     const size_t sh_tree = tree_smem<N, S>(B);
-    const size_t sh_states = sh_tree + (lti ? sizeof(S) * (size_t)lti_last_tile_smem<N, Prod::W>(K) : 0);
+    const size_t sh_states = std::max(sh_tree, lti ? lti_down_smem<N, S, Prod>(B, K) : 0);
     const size_t sh_tfd = std::max(sh_tree, sizeof(S) * (size_t)B * K * N);   // k_tf_down stages the states
 
     static std::once_flag once;
@@ -285,8 +283,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     }
     mark();
     launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl && !first, fprod, K, thr_agg,
-           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, fold, fin, xT, filtT,
-           reinterpret_cast<S*>(h.ws + L.ltree));
+           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, fold, fin, xT, filtT);
     mark();
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
@@ -357,23 +354,34 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
     return MAP_OK;
 }
 
+// Two-filter smoother of a linear model (its own function so that the build
+// can compile it in a separate translation unit, see inst_linear.cu)
+template <int N, int M, typename S>
+map_status solve_linear_tf(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st,
+                           const S* fold)
+{
+    LtiProducer<N, M, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.T = h.T;
+    prod.p = lti_params<N, M, S>(h);
+    RevFlipProducer<N, M, S> rprod;
+    rprod.y = static_cast<const S*>(y);
+    rprod.T = h.T;
+    rprod.Tpad = h.Tpad;
+    rprod.p = flip_params<N, M, S>(h);
+    return run_tf<N, S>(h, prod, rprod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, fold);
+}
+
 template <int N, int M, typename S>
 map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st)
 {
     const S* fold = nullptr;
     if (map_status s = lti_fold_consts<N, M, S>(h, st, &fold); s != MAP_OK) return s;
+    if constexpr (N <= 6) if (h.smoother == MAP_TWO_FILTER) return solve_linear_tf<N, M, S>(h, y, x_out, filt_out, st, fold);
     LtiProducer<N, M, S> prod;
     prod.y = static_cast<const S*>(y);
     prod.T = h.T;
     prod.p = lti_params<N, M, S>(h);
-    if constexpr (N <= 6) if (h.smoother == MAP_TWO_FILTER) {
-        RevFlipProducer<N, M, S> rprod;
-        rprod.y = static_cast<const S*>(y);
-        rprod.T = h.T;
-        rprod.Tpad = h.Tpad;
-        rprod.p = flip_params<N, M, S>(h);
-        return run_tf<N, S>(h, prod, rprod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, fold);
-    }
     return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, false, fold);
 }
 

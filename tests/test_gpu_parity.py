@@ -65,13 +65,16 @@ SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("tile_threads", [0, 128])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", [s[0] for s in SHAPES])
-def test_state_dimensions(prec, name):
+def test_state_dimensions(prec, name, tile_threads):
+    # tile_threads=128: the largest tiles, whose thread prefixes span the most
+    # steps (OU models have ill-conditioned long-interval elements)
     model = dict(SHAPES)[name]()
     T, dt = 3000, 0.01
     _, y = synth.simulate(model, T, dt, seed=3)
-    x, _ = gpu_solve(model, y, dt, prec)
+    x, _ = gpu_solve(model, y, dt, prec, tile_threads=tile_threads)
     assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
 
 
