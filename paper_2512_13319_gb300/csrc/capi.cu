@@ -223,7 +223,7 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
             return cuda_fail(*h, e, "cudaMalloc");
         if ((e = cudaMalloc(&h->d_grad, sizeof(double) * (n * n + 2))) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
-        if ((e = cudaMalloc(&h->d_fold, fold_bytes(n, m, es))) != cudaSuccess)
+        if ((e = cudaMalloc(&h->d_fold, fold_bytes(n, m, es, h->nt))) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(*h, e, "create");

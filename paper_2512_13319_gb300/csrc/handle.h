@@ -47,15 +47,18 @@ size_t elem_bytes(int prec);
 
 // bytes of the linear-fold constants of an (n, m) linear model in scalars of
 // es bytes: up to 64 steps per thread, 8 tree levels and the thread-prefix
-// tables of up to 128 threads per tile (the layout of FoldLayout in lti_fold.cuh)
-inline size_t fold_bytes(int n, int m, size_t es)
+// tables of up to 128 threads per tile, then the tile tables of nt tiles (the
+// layouts of FoldLayout and TileTables in lti_fold.cuh)
+inline size_t fold_bytes(int n, int m, size_t es, long nt)
 {
+    auto al = [](size_t x) { return (x + 15) / 16 * 16; };
     const int ns = n * (n + 1) / 2, V = 16 / (int)es, P = (n + V - 1) / V * V;
     const int oG = (n * n + 2 * ns + 2 * n + 3) / 4 * 4;
     const int oL = (oG + 64 * 2 * n * m + 3) / 4 * 4;
     const int LS = (3 * n * P + 4 * n * n + 3) / 4 * 4;
     const int PS = (n * n + 2 * ns + 3) / 4 * 4;
-    return es * (size_t)(oL + 8 * LS + 128 * PS + 128 * 4 * n * n);
+    const size_t consts = es * (size_t)(oL + 8 * LS + 128 * PS + 128 * 4 * n * n);
+    return al(consts) + sizeof(double) * 24 * 3 * n * n + al(es * nt * ns) + es * nt * n * n;
 }
 
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.

@@ -38,9 +38,22 @@
 //     (the one-variable case of Eq. 36, which updates a value function) with the
 //     tile's prefix.
 //
-// All constants depend on the model, K and B only.  The reduce and down-sweep
-// kernels evaluate (1)-(3) with them: 2 N M multiply-adds per step and 4 N^2
-// per tree node instead of a combine.
+// (4) The tiles 0..nt-2 of a scan are full, so their totals share the
+//     (A_T, C_T, J_T) of B thread folds.  The value function before tile j,
+//     (P_j, v_j), then has a data-independent P_j, from the prior's P_0 by the
+//     P part of the one-variable combine (Eq. 36),
+//       P_{j+1} = A_T^T P_j E_j + J_T,  E_j = (I + C_T P_j)^-1 A_T,
+//     and v_{j+1} = E_j^T v_j + w_j with w_j = eta_j - E_j^T P_j b_j, (b_j,
+//     eta_j) the tile's total.  P_j is computed for all j in parallel: the
+//     elements of 2^e full tiles are obtained by doubling, and P_j applies those
+//     of the set bits of j to P_0 (chunks of equally many full tiles are the
+//     same element, so their order does not matter).  The kernels then fold the
+//     affine maps v -> E_j^T v + w_j of the tiles before theirs instead of
+//     combining tile totals.
+//
+// All constants depend on the model, K, B and the number of tiles only.  The
+// reduce and down-sweep kernels evaluate (1)-(4) with them: 2 N M
+// multiply-adds per step and 4 N^2 per tree node instead of a combine.
 #pragma once
 #include "producers.cuh"
 #include "coop.cuh"
@@ -70,6 +83,34 @@ struct FoldLayout {
     static constexpr int CS = 4 * N * N;                    // co_p at oCo + p * CS: X, Y, Z, W
     static constexpr int oCo = oPre + BMAX * PS;
     static constexpr int TOTAL = oCo + BMAX * CS;
+};
+
+// Per-tile tables of item (4), in the fold buffer after FoldLayout::TOTAL
+// (offsets in bytes): the FP64 (A, C, J) of 2^e full tiles (e < ELMAX, full
+// N x N matrices), then P_j (packed, scalars of S) and F_j = E_j^T (N x N
+// row-major) for j < nt.
+template <int N, int M, typename S>
+struct TileTables {
+    static constexpr int ELMAX = 24;                        // up to 2^24 tiles
+    static constexpr int NN = N * N, NS = Sym<N>::SZ;
+    __host__ __device__ static constexpr size_t al(size_t x) { return (x + 15) / 16 * 16; }
+    __host__ __device__ static constexpr size_t tl_off() { return al(sizeof(S) * FoldLayout<N, M, S>::TOTAL); }
+    __host__ __device__ static constexpr size_t p_off() { return tl_off() + sizeof(double) * ELMAX * 3 * NN; }
+    __host__ __device__ static constexpr size_t f_off(long nt) { return p_off() + al(sizeof(S) * nt * NS); }
+    __host__ __device__ static constexpr size_t bytes(long nt) { return f_off(nt) + sizeof(S) * nt * NN; }
+};
+
+// Tile-level inputs of the linear-fold kernels: the fold constants, the tile
+// tables P_j and F_j, the per-solve w_j (N scalars per tile, written by the
+// reduce kernel) and, for scans with more than one group of tiles, the
+// composed maps of the groups (Aff records)
+template <typename S>
+struct LtiTiles {
+    const S* fold;
+    const S* P;
+    const S* F;
+    S* w;
+    S* gmaps;
 };
 
 // Plan-time helpers of k_lti_fold (FP64, plain loops: run once per model and
@@ -182,13 +223,38 @@ __device__ inline void pair_acj(int n, const double* AU, const double* JU, const
     for (int q = 0; q < n * n; ++q) { Co[q] += CD[q]; Jo[q] += JU[q]; }
 }
 
+// P <- A^T P (I + C P)^-1 A + J, symmetrised (full matrices); w: 4 n^2 scratch
+__device__ inline void riccati(int n, const double* A, const double* C, const double* J, double* P, double* w)
+{
+    double* Mi = w;
+    double* T1 = w + n * n;
+    double* T2 = w + 2 * n * n;
+    inv_I_plus(n, C, P, Mi, w + 3 * n * n);
+    mm(n, Mi, A, T1);                  // (I + C P)^-1 A
+    mm(n, P, T1, T2);                  // P (I + C P)^-1 A
+#pragma unroll 1
+    for (int i = 0; i < n; ++i)
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            double s = J[i * n + j];
+#pragma unroll 1
+            for (int k = 0; k < n; ++k) s += A[k * n + i] * T2[k * n + j];
+            Mi[i * n + j] = s;
+        }
+#pragma unroll 1
+    for (int i = 0; i < n; ++i)
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) P[i * n + j] = 0.5 * (Mi[i * n + j] + Mi[j * n + i]);
+}
+
 }  // namespace fold_detail
 
 // One CTA of KMAX threads; thread j carries Gamma_j.  FP64 throughout.  LB:
-// log2 of the threads per tile (B = 2^LB <= BMAX).
+// log2 of the threads per tile (B = 2^LB <= BMAX); ne: the tile levels of
+// item (4) to write (2^ne above every tile index).
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(64)
-k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
+k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict__ out)
 {
     using FL = FoldLayout<N, M, S>;
     using CL = CoopLayout<N, S>;
@@ -256,7 +322,7 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
         }
         __syncthreads();
         if (j < i) {                              // earlier observations: old eta parts on the right
-            double nb[N * M], ne[N * M];
+            double nb[N * M], nq[N * M];
 #pragma unroll 1
             for (int a = 0; a < N; ++a)
 #pragma unroll 1
@@ -268,10 +334,10 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
                         se += Te[a * N + k] * ge[k * M + c];
                     }
                     nb[a * M + c] = sb;
-                    ne[a * M + c] = se;
+                    nq[a * M + c] = se;
                 }
 #pragma unroll 1
-            for (int q = 0; q < N * M; ++q) { gb[q] = nb[q]; ge[q] = ne[q]; }
+            for (int q = 0; q < N * M; ++q) { gb[q] = nb[q]; ge[q] = nq[q]; }
         } else if (j == i) {
 #pragma unroll 1
             for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = Gm[q]; }
@@ -320,6 +386,22 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
                 lv[FL::oZ + q] = S(Te[q]);
                 lv[FL::oW + q] = S(T3[q]);
             }
+            fd::pair_acj(N, Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
+        }
+        // tile levels (item (4)): (Ac, Cc, Jc) now hold the full tile
+        double* tl = reinterpret_cast<double*>(reinterpret_cast<char*>(out) + TileTables<N, M, S>::tl_off());
+#pragma unroll 1
+        for (int e = 0; e < ne; ++e) {
+#pragma unroll 1
+            for (int q = 0; q < NN; ++q) {
+                tl[e * 3 * NN + q] = Ac[q];
+                tl[e * 3 * NN + NN + q] = Cc[q];
+                tl[e * 3 * NN + 2 * NN + q] = Jc[q];
+            }
+            if (e + 1 == ne) break;
+            fd::pair_coeffs(N, Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);
             fd::pair_acj(N, Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
@@ -373,6 +455,39 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, S* __restrict__ out)
                 pr[NN + FL::NS + Sym<N>::at(a, c)] = S(0.5 * (pJ[a * N + c] + pJ[c * N + a]));
             }
         }
+    }
+}
+
+// Tile tables of item (4): thread j computes P_j and F_j = E_j^T from the
+// tile levels (written by k_lti_fold) and the prior's P_0.  FP64 throughout.
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(64)
+k_lti_tiles(const Red<N, double> prior, int nt, int ne, S* __restrict__ out)
+{
+    using TT = TileTables<N, M, S>;
+    namespace fd = fold_detail;
+    constexpr int NN = N * N;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nt) return;
+    const double* tl = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::tl_off());
+    double P[NN], E[NN], w[5 * NN];
+#pragma unroll 1
+    for (int a = 0; a < N; ++a)
+#pragma unroll 1
+        for (int c = 0; c < N; ++c) P[a * N + c] = prior.P[Sym<N>::at(a, c)];
+#pragma unroll 1
+    for (int e = ne - 1; e >= 0; --e)
+        if ((j >> e) & 1) fd::riccati(N, tl + e * 3 * NN, tl + e * 3 * NN + NN, tl + e * 3 * NN + 2 * NN, P, w);
+    fd::inv_I_plus(N, tl + NN, P, w, w + NN);            // (I + C_T P_j)^-1
+    fd::mm(N, w, tl, E);                                   // E_j
+    S* tp = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::p_off()) + (long)j * Sym<N>::SZ;
+    S* tf = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::f_off(nt)) + (long)j * NN;
+#pragma unroll 1
+    for (int a = 0; a < N; ++a) {
+#pragma unroll 1
+        for (int c = a; c < N; ++c) tp[Sym<N>::at(a, c)] = S(P[a * N + c]);
+#pragma unroll 1
+        for (int c = 0; c < N; ++c) tf[a * N + c] = S(E[c * N + a]);
     }
 }
 

@@ -195,7 +195,7 @@ extern "C" map_status map_smoother_solve_noalloc(const map_problem_desc* d, cons
     h.nt = (int)((h.T + L - 1) / L);
     h.Tpad = (long)h.nt * L;
     const size_t fold_off = (ops->workspace_bytes(h) + 255) / 256 * 256;
-    const size_t need = fold_off + fold_bytes(n, m, es);
+    const size_t need = fold_off + fold_bytes(n, m, es, h.nt);
     if (need > NOALLOC_SCRATCH_BYTES)
         return noalloc_fail(MAP_ERR_SHAPE,
                             "T too large for the allocation-free scratch: needs " + std::to_string(need) +

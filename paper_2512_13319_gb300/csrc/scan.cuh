@@ -385,6 +385,86 @@ k_group_totals(const S* __restrict__ tile_agg, int nt, S* __restrict__ group_agg
     if (threadIdx.x == 0) aos_store(group_agg, (long)g, tot);
 }
 
+// Linear-fold mode (lti_fold.cuh, item (4)): fold, in thread 0, of the affine
+// tile maps m_i(v) = F_i v + w_i for i = first_all..last_all-1, the later map
+// outermost.  Map i has F_i at F + i * fs and w_i at w + i * ws.  Thread t
+// composes the t-th run of at most ceil(count / B) maps counted from the end;
+// the runs are composed with the sub-warp affine tree (leaf 0 outermost).
+// Uses the affine-tree area of `nodes`; ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void fold_tile_maps(const S* __restrict__ F, int fs, const S* __restrict__ w, int ws,
+                                               int first_all, int last_all, S* nodes, Aff<N, S>& out)
+{
+    const int B = blockDim.x, t = threadIdx.x;
+    const int cnt = last_all - first_all, per = (cnt + B - 1) / B;
+    const int hi = last_all - min(cnt, t * per), lo = max(first_all, hi - per);
+    Aff<N, S> H;
+    set_identity(H);
+    for (int i = lo; i < hi; ++i) {          // H = m_i o H
+        Aff<N, S> m;
+#pragma unroll
+        for (int q = 0; q < N * N; ++q) m.F[q] = __ldg(F + (long)i * fs + q);
+#pragma unroll
+        for (int q = 0; q < N; ++q) m.c[q] = w[(long)i * ws + q];
+        compose<N, S>(m, H, H);
+    }
+    node_store(H, aslot<N, S>(nodes, B, 0, t));
+    coop_aff_up<N, S>(nodes);
+    if (t == 0) node_load(aslot<N, S>(nodes, B, ilog2(B), 0), out);
+    __syncthreads();
+}
+
+// Linear-fold mode: value function before tile `tile` (returned in thread 0):
+// P_tile from the tile tables, v_tile = (m_{tile-1} o ... o m_0)(v_0).  With
+// group maps the fold is that of the groups before the tile's group followed
+// by the maps of its group before it.
+template <int N, typename S>
+__device__ __forceinline__ void lti_tile_prefix(const LtiTiles<S>& lt, int tile, const Red<N, S>& prior, S* nodes,
+                                                Red<N, S>& out)
+{
+    constexpr int NN = N * N, NA = Aff<N, S>::NCOMP;
+    if (tile == 0) {
+        out = prior;
+        return;
+    }
+    Aff<N, S> H;
+    if (!lt.gmaps) {
+        fold_tile_maps<N, S>(lt.F, NN, lt.w, N, 0, tile, nodes, H);
+    } else {
+        const int G = prefix_group_tiles(blockDim.x), g = tile / G;
+        Aff<N, S> hg, ht;
+        if (g > 0) fold_tile_maps<N, S>(lt.gmaps, NA, lt.gmaps + NN, NA, 0, g, nodes, hg);
+        fold_tile_maps<N, S>(lt.F, NN, lt.w, N, g * G, tile, nodes, ht);
+        if (threadIdx.x == 0) {
+            if (g > 0)
+                compose<N, S>(ht, hg, H);
+            else
+                H = ht;
+        }
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < Sym<N>::SZ; ++q) out.P[q] = lt.P[(long)tile * Sym<N>::SZ + q];
+        affine_apply<N, S>(H, prior.v, out.v);
+    }
+}
+
+// Linear-fold mode: composed maps of the groups of prefix_group_tiles(B) full
+// tiles (one CTA per group), for scans with many tiles
+template <int N, typename S>
+__global__ void __launch_bounds__(128)
+k_lti_group_maps(const LtiTiles<S> lt, int nfull)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
+    pdl_wait();                            // w_j of the reduce kernel
+    pdl_trigger();
+    const int G = prefix_group_tiles(blockDim.x), g = blockIdx.x;
+    Aff<N, S> H;
+    fold_tile_maps<N, S>(lt.F, N * N, lt.w, N, g * G, min(nfull, (g + 1) * G), nodes, H);
+    if (threadIdx.x == 0) aos_store(lt.gmaps, (long)g, H);
+}
+
 // State at the end of tile `tile`, written by thread 0 to the N scalars at
 // `xe` (shared memory outside the affine-tree area): the closed-loop maps of
 // tiles tile+1..nt-1 composed (thread runs, then the affine tree; a map takes
@@ -578,15 +658,17 @@ struct LtiReduceSmem {
 // parts only (lti_fold.cuh).  The tile's inputs arrive in shared memory by one
 // bulk copy; per thread K steps cost 2 N M multiply-adds and the tree 4 N^2
 // per node.  The per-thread (b, eta) go to thr_agg (2N components,
-// warp-interleaved), the tile totals to tile_agg.  A bulk copy that does not
+// warp-interleaved); the tile's total enters only through its affine tile map,
+// whose w_j goes to lt.w (item (4) of lti_fold.cuh).  A bulk copy that does not
 // complete within the poll limit is counted in ctx.stats[2] and the tile is
 // left unwritten.
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, 3)
-k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
-                    S* __restrict__ tile_agg, const S* __restrict__ fold, CombineCtx ctx)
+k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg, const LtiTiles<S> lt,
+                    CombineCtx ctx)
 {
+    const S* __restrict__ fold = lt.fold;
     constexpr int M = Prod::W;
     using FL = FoldLayout<N, M, S>;
     using RS = LtiReduceSmem<N, M, S>;
@@ -642,23 +724,24 @@ k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ th
     }
     lti_tree_up<N, M, S>(bq, lv);
     if (t == 0) {
-        using CL = CoopLayout<N, S>;
-        const S* cn = lv + LB * FL::LS;
+        // w_j = eta_j - F_j P_j b_j (item (4) of lti_fold.cuh), F_j = E_j^T
         const S* rq = bq + (2 * B - 2) * 2 * N;
-        Elem<N, S> root;
+        const long j = blockIdx.x;
+        S Pb[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
+        for (int a = 0; a < N; ++a) {
+            S acc = S(0);
 #pragma unroll
-            for (int j = 0; j < N; ++j) root.A[i * N + j] = cn[CL::oA + i * CL::P + j];
-#pragma unroll
-            for (int j = i; j < N; ++j) {
-                root.C[Sym<N>::at(i, j)] = cn[CL::oC + i * CL::P + j];
-                root.J[Sym<N>::at(i, j)] = cn[CL::oJ + i * CL::P + j];
-            }
-            root.b[i] = rq[i];
-            root.eta[i] = rq[N + i];
+            for (int c = 0; c < N; ++c) acc = fma(lt.P[j * Sym<N>::SZ + Sym<N>::at(a, c)], rq[c], acc);
+            Pb[a] = acc;
         }
-        aos_store(tile_agg, (long)blockIdx.x, root);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            S acc = rq[N + a];
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc = fma(-lt.F[j * N * N + a * N + c], Pb[c], acc);
+            lt.w[j * N + a] = acc;
+        }
     }
 }
 
@@ -716,9 +799,10 @@ __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
               const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
               S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
-              CombineCtx ctx, const S* __restrict__ fold, S* __restrict__ final_out, S* __restrict__ xT_out,
+              CombineCtx ctx, const LtiTiles<S> lt, S* __restrict__ final_out, S* __restrict__ xT_out,
               S* __restrict__ filtT_out, const S* __restrict__ group_agg)
 {
+    const S* __restrict__ fold = lt.fold;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
@@ -734,7 +818,10 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
     pdl_wait();                            // totals and aggregates of the reduce kernel
     pdl_trigger();
     Red<N, S> pin, X;
-    tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
+    if (fold)
+        lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
+    else
+        tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
     tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, fold, last_lti, leaf, nodes, ctx, X);
 
     Aff<N, S> comp_t;
@@ -832,9 +919,10 @@ template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 const S* __restrict__ tile_agg, const Red<N, S> prior, S* __restrict__ filt_ws,
-                S* __restrict__ filt_out, CombineCtx ctx, const S* __restrict__ fold,
+                S* __restrict__ filt_out, CombineCtx ctx, const LtiTiles<S> lt,
                 S* __restrict__ final_out, S* __restrict__ xT_out, S* __restrict__ filtT_out)
 {
+    const S* __restrict__ fold = lt.fold;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
     const int B = blockDim.x, t = threadIdx.x;
@@ -849,7 +937,10 @@ k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
     pdl_wait();
     pdl_trigger();
     Red<N, S> pin, X;
-    tile_prefix_of<N, S>(tile_agg, tile, prior, nodes, ctx, pin);
+    if (fold)
+        lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
+    else
+        tile_prefix_of<N, S>(tile_agg, tile, prior, nodes, ctx, pin);
     tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, fold, last_lti, leaf, nodes, ctx, X);
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {

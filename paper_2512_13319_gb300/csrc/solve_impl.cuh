@@ -131,6 +131,28 @@ int rts_resident_blocks(int B)
 // Filter scan + RTS pass for the elements of `prod`; writes x_out (T+1, N).
 // Three kernels: reduce (per-thread and per-tile totals), filter down-sweep
 // (each CTA reduces the totals before its tile, then per-step values and
+
+// Tile-level pointers of the linear-fold mode (lti_fold.cuh): the tables in
+// the fold buffer, w_j in the tile-total area (unused by that mode otherwise)
+// and the group maps in the group-total area
+template <int N, typename S, class Prod>
+LtiTiles<S> lti_tiles_of(const map_smoother& h, const S* fold, S* w, S* gmaps)
+{
+    LtiTiles<S> lt{};
+    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+        if (fold) {
+            using TT = TileTables<N, Prod::W, S>;
+            const char* base = reinterpret_cast<const char*>(fold);
+            lt.fold = fold;
+            lt.P = reinterpret_cast<const S*>(base + TT::p_off());
+            lt.F = reinterpret_cast<const S*>(base + TT::f_off(h.nt));
+            lt.w = w;
+            lt.gmaps = gmaps;
+        }
+    }
+    return lt;
+}
+
 // closed-loop maps; the last CTA writes x_T), RTS pass (each CTA composes the
 // maps after its tile, then the per-step states).  With linear-fold constants
 // (fold != nullptr) the reduce kernel covers the full tiles 0..nt-2 on (b, eta)
@@ -167,6 +189,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_down<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_rts_down<N, S>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_group_totals<N, S>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_lti_group_maps<N, S>, big);
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
@@ -179,6 +202,10 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     // dev_prior: the prior comes from the producer's terminal() (device data)
     S* term = dev_prior ? reinterpret_cast<S*>(h.ws + L.term) : nullptr;
     bool first = true;                     // no PDL edge to whatever ran before the solve
+    const int G = prefix_group_tiles(B);
+    const int ng = (lti ? nt - 1 : nt) > G ? (nt + G - 1) / G : 0;
+    S* group_agg = ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr;
+    const LtiTiles<S> lt = lti_tiles_of<N, S, Prod>(h, fold, tile_agg, group_agg);
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx);
         first = false;
@@ -189,24 +216,24 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
             cudaError_t e1 = cudaSuccess;
             std::call_once(once_lti, [&] { e1 = allow_smem(k_filter_reduce_lti<N, S, Prod>, 200 * 1024); });
             if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaFuncSetAttribute");
-            launch(k_filter_reduce_lti<N, S, Prod>, nt - 1, B, sh, st, false, prod, K, thr_agg, tile_agg, fold,
-                   ctx);
+            launch(k_filter_reduce_lti<N, S, Prod>, nt - 1, B, sh, st, false, prod, K, thr_agg, lt, ctx);
             first = false;
         }
     }
-    // scans with more than one group of tiles: group totals for the two-level
-    // tile prefix (the last tile's total is not needed and may be absent)
-    const int G = prefix_group_tiles(B);
-    const int ng = (lti ? nt - 1 : nt) > G ? (nt + G - 1) / G : 0;
-    S* group_agg = ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr;
+    // scans with more than one group of tiles: group totals (group maps in
+    // linear-fold mode) for the two-level tile prefix (the last tile's total
+    // is not needed and may be absent)
     if (ng) {
-        launch(k_group_totals<N, S>, ng, B, tree_smem<N, S>(B), st, pdl && !first, (const S*)tile_agg,
-               lti ? nt - 1 : nt, group_agg, ctx);
+        if (lti)
+            launch(k_lti_group_maps<N, S>, ng, B, aff_tree_smem<N, S>(B), st, pdl && !first, lt, nt - 1);
+        else
+            launch(k_group_totals<N, S>, ng, B, tree_smem<N, S>(B), st, pdl && !first, (const S*)tile_agg, nt,
+                   group_agg, ctx);
         first = false;
     }
     mark();
     launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl && !first, prod, K, thr_agg, (const S*)tile_agg,
-           prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, fold, fin, xT, filtT,
+           prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, lt, fin, xT, filtT,
            (const S*)group_agg);
     mark();
     EgForm<N, S> form{};                     // how k_filter_down stored the closed-loop maps
@@ -257,6 +284,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_reduce<N, S, RProd>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_filter_states<N, S, Prod>, big);
         if (e0 == cudaSuccess) e0 = allow_smem(k_tf_down<N, S, RProd>, big);
+        if (e0 == cudaSuccess) e0 = allow_smem(k_lti_group_maps<N, S>, big);
     });
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "cudaFuncSetAttribute");
 
@@ -265,6 +293,11 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     auto mark = [&] { if (h.profile) cudaEventRecord(h.ev[h.nev++], st); };
     mark();
     bool first = true;
+    // linear-fold mode: tile maps, and group maps when the forward scan has
+    // more than one group of tiles (the general forward scan folds all totals)
+    const int ng = lti && nt - 1 > prefix_group_tiles(B) ? (nt + prefix_group_tiles(B) - 1) / prefix_group_tiles(B) : 0;
+    const LtiTiles<S> lt =
+        lti_tiles_of<N, S, Prod>(h, fold, tile_agg, ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr);
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg, (S*)nullptr,
                ctx);
@@ -276,14 +309,17 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
             cudaError_t e1 = cudaSuccess;
             std::call_once(once_lti, [&] { e1 = allow_smem(k_filter_reduce_lti<N, S, Prod>, 200 * 1024); });
             if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaFuncSetAttribute");
-            launch(k_filter_reduce_lti<N, S, Prod>, nt - 1, B, sh, st, false, fprod, K, thr_agg, tile_agg, fold,
-                   ctx);
+            launch(k_filter_reduce_lti<N, S, Prod>, nt - 1, B, sh, st, false, fprod, K, thr_agg, lt, ctx);
             first = false;
         }
     }
+    if (ng) {
+        launch(k_lti_group_maps<N, S>, ng, B, aff_tree_smem<N, S>(B), st, pdl && !first, lt, nt - 1);
+        first = false;
+    }
     mark();
     launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl && !first, fprod, K, thr_agg,
-           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, fold, fin, xT, filtT);
+           (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, lt, fin, xT, filtT);
     mark();
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
@@ -327,9 +363,10 @@ FlipParams<N, M, S> flip_params(const map_smoother& h)
     return p;
 }
 
-// constants of the linear per-thread fold (lti_fold.cuh) for the current K,
-// recomputed on `st` after a change of K or of the model; nullptr when K is
-// beyond the fold's range (the kernels then fold step by step)
+// constants of the linear per-thread fold and the tile tables (lti_fold.cuh)
+// for the current geometry, recomputed on `st` after a change of K, B or of
+// the model; nullptr when the geometry is beyond their range (the kernels then
+// fold step by step and combine tile totals)
 template <int N, int M, typename S>
 map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
 {
@@ -338,13 +375,19 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
     if constexpr (N > 6) return MAP_OK;        // the kernels take the linear fold for N <= 6
     int LB = 0;
     while ((2 << LB) <= h.B) ++LB;
-    if (!h.d_fold || h.K > FL::KMAX || LB > FL::LMAX || sizeof(S) * (size_t)FL::TOTAL > fold_bytes(N, M, sizeof(S)) ||
+    using TT = TileTables<N, M, S>;
+    int ne = 1;                                // tile levels: 2^ne > nt - 1, the largest tile index
+    while (ne < 31 && (1L << ne) <= (long)h.nt - 1) ++ne;
+    if (!h.d_fold || h.K > FL::KMAX || LB > FL::LMAX || ne > TT::ELMAX ||
+        TT::bytes(h.nt) > fold_bytes(N, M, sizeof(S), h.nt) ||
         LtiTreeSmem<N, M, S>::end(h.B, LB) > 2 * h.B * CoopLayout<N, S>::NE ||
         LtiReduceSmem<N, M, S>::bytes(h.B, h.K, LB) > 200 * 1024)
         return MAP_OK;
     if (h.fold_K != h.K || h.fold_B != h.B) {
-        k_lti_fold<N, M, S><<<1, FL::KMAX, 0, st>>>(lti_params<N, M, double>(h), h.K, LB,
+        k_lti_fold<N, M, S><<<1, FL::KMAX, 0, st>>>(lti_params<N, M, double>(h), h.K, LB, ne,
                                                     static_cast<S*>(h.d_fold));
+        k_lti_tiles<N, M, S><<<(h.nt + 63) / 64, 64, 0, st>>>(prior_of<N, double>(h), h.nt, ne,
+                                                             static_cast<S*>(h.d_fold));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
         h.fold_K = h.K;

@@ -141,6 +141,22 @@ def test_many_tiles(prec):
     assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
 
 
+@pytest.mark.parametrize("smoother", ["rts", "two_filter"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tile_groups(prec, smoother):
+    """More than 4B tiles: the two-level tile prefix (group maps / group totals)."""
+    from paper_2512_13319_gb300 import MapSmoother
+    model = synth.ou_model(4, 2, seed=21)
+    T, dt = 600_001, 1e-3
+    _, y = synth.simulate(model, T, dt, seed=12, substeps=1)
+    sm = MapSmoother(model, T, dt, precision=prec, smoother=smoother, tile_threads=32)
+    K, B, nt = sm.geometry()
+    assert nt - 1 > 4 * B
+    x = sm.solve(torch.tensor(y, dtype=DT[prec], device="cuda")).cpu().numpy()
+    sm.close()
+    assert rel(x, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_full_size_T_2_20(prec):
     """The benchmark workload: nx = 4, T = 2^20, dt = 1e-3 (every output compared)."""
