@@ -55,6 +55,7 @@
 // reduce and down-sweep kernels evaluate (1)-(4) with them: 2 N M
 // multiply-adds per step and 4 N^2 per tree node instead of a combine.
 #pragma once
+#include <type_traits>
 #include "producers.cuh"
 #include "coop.cuh"
 
@@ -111,7 +112,19 @@ struct LtiTiles {
     const S* F;
     S* w;
     S* gmaps;
+    int co_smem;                    // the co table is staged in shared memory (LtiDownSmem)
 };
+
+// The co table is stored by tree level: level d holds the B / 2^(d+1) right
+// children p = (2i+1) 2^d of a tile of B threads, component-major (component
+// q of entry i at q * B / 2^(d+1) + i, the components X, Y, Z, W row-major),
+// so that the threads of a down-sweep level read consecutive words.  Offset of
+// level d in scalars; the table holds 4 N^2 (B - 1) scalars.
+template <int N>
+__host__ __device__ constexpr int lti_co_level(int B, int d)
+{
+    return 4 * N * N * (B - (B >> d));
+}
 
 // Plan-time helpers of k_lti_fold (FP64, plain loops: run once per model and
 // geometry, so they are kept small rather than unrolled)
@@ -433,15 +446,17 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) { pA[q] = nA[q]; pC[q] = nC[q]; pJ[q] = nJ[q]; }
         }
-        // co_p: the coefficients of the last (lowest-bit) product
+        // co_p: the coefficients of the last (lowest-bit) product, p = (2i+1) 2^d
+        // stored as entry i of level d (lti_co_level)
         if (p > 0) {
-            S* co = out + FL::oCo + p * FL::CS;
+            const int d = __ffs(p) - 1, i = p >> (d + 1), cnt = B >> (d + 1);
+            S* co = out + FL::oCo + lti_co_level<N>(B, d) + i;
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) {
-                co[q] = S(X[q]);
-                co[NN + q] = S(Y[q]);
-                co[2 * NN + q] = S(Z[q]);
-                co[3 * NN + q] = S(W[q]);
+                co[q * cnt] = S(X[q]);
+                co[(NN + q) * cnt] = S(Y[q]);
+                co[(2 * NN + q) * cnt] = S(Z[q]);
+                co[(3 * NN + q) * cnt] = S(W[q]);
             }
         }
         S* pr = out + FL::oPre + p * FL::PS;
@@ -535,9 +550,13 @@ __device__ __forceinline__ void lti_linear_fold(const Prod& prod, const S* __res
     for (int q = 0; q < N; ++q) { bq[q] = ab[q]; bq[N + q] = ae[q]; }
 }
 
-// Up-sweep of a full tile's tree on the (b, eta) parts: bq holds 2B nodes of
-// 2N scalars (tree levels as lvl_off), leaves stored by the caller; lv the
-// level constants (FoldLayout level blocks, in shared memory).
+// (b, eta) nodes of a tile's tree: level d (B / 2^d nodes) starts at scalar
+// 2N (2B - 2B / 2^d), component-major (component c of node j at c B / 2^d + j).
+__host__ __device__ constexpr int lti_node_level(int N2, int B, int d) { return N2 * (2 * B - ((2 * B) >> d)); }
+
+// Up-sweep of a full tile's tree on the (b, eta) parts: bq holds the nodes
+// (lti_node_level; leaves stored by the caller); lv the level constants
+// (FoldLayout level blocks, in shared memory).
 template <int N, int M, typename S>
 __device__ void lti_tree_up(S* bq, const S* lv)
 {
@@ -546,15 +565,19 @@ __device__ void lti_tree_up(S* bq, const S* lv)
     const int LB = 31 - __clz(B);
     for (int d = 0; d < LB; ++d) {
         __syncthreads();
-        const int cnt = B >> (d + 1);
+        const int cnt = B >> (d + 1), nd = 2 * cnt;
         if (t < cnt) {
             const S* L = lv + d * FL::LS;
-            const S* ci = bq + (2 * B - ((2 * B) >> d) + 2 * t + 1) * 2 * N;    // later child
-            const S* cj = ci - 2 * N;                                           // earlier child
-            S* par = bq + (2 * B - ((2 * B) >> (d + 1)) + t) * 2 * N;
-            S bi[N], ei[N], bj[N], ej[N];
+            const S* ch = bq + lti_node_level(2 * N, B, d);
+            S* par = bq + lti_node_level(2 * N, B, d + 1);
+            S bi[N], ei[N], bj[N], ej[N];       // later child 2t+1, earlier child 2t
 #pragma unroll
-            for (int q = 0; q < N; ++q) { bi[q] = ci[q]; ei[q] = ci[N + q]; bj[q] = cj[q]; ej[q] = cj[N + q]; }
+            for (int q = 0; q < N; ++q) {
+                bi[q] = ch[q * nd + 2 * t + 1];
+                ei[q] = ch[(N + q) * nd + 2 * t + 1];
+                bj[q] = ch[q * nd + 2 * t];
+                ej[q] = ch[(N + q) * nd + 2 * t];
+            }
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 S sb = bj[a], se = ei[a];
@@ -565,8 +588,8 @@ __device__ void lti_tree_up(S* bq, const S* lv)
                     se = fma(L[FL::oZ + a * N + k], ej[k], se);
                     se = fma(-L[FL::oW + a * N + k], bi[k], se);
                 }
-                par[a] = sb;
-                par[N + a] = se;
+                par[a * cnt + t] = sb;
+                par[(N + a) * cnt + t] = se;
             }
         }
     }
@@ -577,42 +600,49 @@ __device__ void lti_tree_up(S* bq, const S* lv)
 // up-sweep nodes bq (item (3) above): on return leaf t of bq holds the (b, eta)
 // of the fold of threads 0..t-1 (zero for t = 0).  A left child takes its
 // parent's prefix; the right child starting at thread p takes the left
-// sibling's up-sweep value combined with it through co_p (global memory).
-// Leaf t's prefix uses only the leaves before t.
+// sibling's up-sweep value combined with it through co_p (co: the table in
+// shared or global memory, lti_co_level layout).  Leaf t's prefix uses only
+// the leaves before t.
 template <int N, int M, typename S>
-__device__ void lti_tree_down_linear(S* bq, const S* __restrict__ co)
+__device__ void lti_tree_down_linear(S* bq, const S* co)
 {
-    using FL = FoldLayout<N, M, S>;
     constexpr int NN = N * N;
     const int B = blockDim.x, t = threadIdx.x;
     const int LB = 31 - __clz(B);
-    if (t < 2 * N) bq[(2 * B - 2) * 2 * N + t] = S(0);            // root: empty prefix
+    if (t < 2 * N) bq[lti_node_level(2 * N, B, LB) + t] = S(0);   // root: empty prefix
     for (int d = LB - 1; d >= 0; --d) {
         __syncthreads();
-        const int cnt = B >> (d + 1);
+        const int cnt = B >> (d + 1), nd = 2 * cnt;
         if (t < cnt) {
-            const S* par = bq + (2 * B - ((2 * B) >> (d + 1)) + t) * 2 * N;
-            S* lft = bq + (2 * B - ((2 * B) >> d) + 2 * t) * 2 * N;  // left child = U
-            S* rgt = lft + 2 * N;
-            const S* c = co + ((2 * t + 1) << d) * FL::CS;
+            const S* par = bq + lti_node_level(2 * N, B, d + 1);
+            S* lvl = bq + lti_node_level(2 * N, B, d);
+            const S* c = co + lti_co_level<N>(B, d) + t;
             S bD[N], eD[N], bU[N], eU[N];
 #pragma unroll
-            for (int q = 0; q < N; ++q) { bD[q] = par[q]; eD[q] = par[N + q]; bU[q] = lft[q]; eU[q] = lft[N + q]; }
+            for (int q = 0; q < N; ++q) {
+                bD[q] = par[q * cnt + t];
+                eD[q] = par[(N + q) * cnt + t];
+                bU[q] = lvl[q * nd + 2 * t];
+                eU[q] = lvl[(N + q) * nd + 2 * t];
+            }
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 S sb = bD[a], se = eU[a];
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
-                    sb = fma(__ldg(c + a * N + k), bU[k], sb);
-                    sb = fma(__ldg(c + NN + a * N + k), eD[k], sb);
-                    se = fma(__ldg(c + 2 * NN + a * N + k), eD[k], se);
-                    se = fma(-__ldg(c + 3 * NN + a * N + k), bU[k], se);
+                    sb = fma(c[(a * N + k) * cnt], bU[k], sb);
+                    sb = fma(c[(NN + a * N + k) * cnt], eD[k], sb);
+                    se = fma(c[(2 * NN + a * N + k) * cnt], eD[k], se);
+                    se = fma(-c[(3 * NN + a * N + k) * cnt], bU[k], se);
                 }
-                rgt[a] = sb;
-                rgt[N + a] = se;
+                lvl[a * nd + 2 * t + 1] = sb;
+                lvl[(N + a) * nd + 2 * t + 1] = se;
             }
 #pragma unroll
-            for (int q = 0; q < N; ++q) { lft[q] = bD[q]; lft[N + q] = eD[q]; }
+            for (int q = 0; q < N; ++q) {
+                lvl[q * nd + 2 * t] = bD[q];
+                lvl[(N + q) * nd + 2 * t] = eD[q];
+            }
         }
     }
     __syncthreads();
@@ -622,8 +652,8 @@ __device__ void lti_tree_down_linear(S* bq, const S* __restrict__ co)
 // D_t (constants pre_t, (b, eta) from the down-sweep at dleaf) applied to the
 // tile's prefix pin (one-variable combine, Eq. 36); thread 0 takes pin itself.
 template <int N, int M, typename S>
-__device__ __forceinline__ void lti_thread_value(const S* __restrict__ fold, const S* dleaf, const Red<N, S>& pin,
-                                                 const CombineCtx& ctx, Red<N, S>& X)
+__device__ __forceinline__ void lti_thread_value(const S* __restrict__ fold, const S (&dleaf)[2 * N],
+                                                 const Red<N, S>& pin, const CombineCtx& ctx, Red<N, S>& X)
 {
     using FL = FoldLayout<N, M, S>;
     X = pin;
@@ -639,14 +669,49 @@ __device__ __forceinline__ void lti_thread_value(const S* __restrict__ fold, con
     apply<N, S, false>(D, X, nullptr, nullptr, ctx);
 }
 
-// LTI tile-tree shared memory inside the element-tree area (offsets in
-// scalars): the (b, eta) nodes, the level constants, the tile's prefix
+// Shared memory of the linear-fold down-sweep kernels (offsets in scalars of
+// S).  A work area at 0, reused in turn by the tile-prefix affine tree, the
+// (b, eta) tree with the tile's prefix value node after it, the last tile's
+// staged Gamma_i, and the tile's own affine tree; then the tree level
+// constants (levels 0..LB-1) and, with co_smem, the co table (entries
+// 0..B-1), both staged before the wait for the preceding kernel.
 template <int N, int M, typename S>
-struct LtiTreeSmem {
+struct LtiDownSmem {
+    using FL = FoldLayout<N, M, S>;
+    __host__ __device__ static constexpr int al(int x) { return (x + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int mx(int a, int b) { return a > b ? a : b; }
+    __host__ __device__ static constexpr int lb(int B) { return B >= 128 ? 7 : B >= 64 ? 6 : B >= 32 ? 5 : B >= 16 ? 4 : 3; }
     __host__ __device__ static constexpr int bq(int) { return 0; }
-    __host__ __device__ static constexpr int lv(int B) { return (2 * B * 2 * N + 3) / 4 * 4; }
-    __host__ __device__ static constexpr int pin(int B, int LB) { return lv(B) + (LB + 1) * FoldLayout<N, M, S>::LS; }
-    __host__ __device__ static constexpr int end(int B, int LB) { return pin(B, LB) + CoopLayout<N, S>::NR; }
+    __host__ __device__ static constexpr int pin(int B) { return 2 * B * 2 * N; }
+    __host__ __device__ static constexpr int lv(int B, int K)
+    {
+        return al(mx(mx(pin(B) + CoopLayout<N, S>::NR, K * FL::GS), 2 * B * CoopLayout<N, S>::NA));
+    }
+    __host__ __device__ static constexpr int co(int B, int K) { return lv(B, K) + al(lb(B) * FL::LS); }
+    __host__ __device__ static constexpr size_t bytes(int B, int K, bool co_smem)
+    {
+        return sizeof(S) * (size_t)(co(B, K) + (co_smem ? B * FL::CS : 0));
+    }
 };
+
+// Stage the level constants and (co_smem) the co table into shared memory;
+// copies of 16-byte words (both tables start at multiples of 4 scalars)
+template <int N, int M, typename S>
+__device__ __forceinline__ void lti_stage_tables(const LtiTiles<S>& lt, int K, S* sm)
+{
+    using FL = FoldLayout<N, M, S>;
+    using DS = LtiDownSmem<N, M, S>;
+    using V = typename std::conditional<sizeof(S) == 4, float4, double2>::type;
+    constexpr int W = 16 / sizeof(S);
+    const int B = blockDim.x, t = threadIdx.x, LB = 31 - __clz(B);
+    const V* src = reinterpret_cast<const V*>(lt.fold + FL::oL);
+    V* dst = reinterpret_cast<V*>(sm + DS::lv(B, K));
+    for (int q = t; q < (LB * FL::LS) / W; q += B) dst[q] = src[q];
+    if (lt.co_smem) {
+        src = reinterpret_cast<const V*>(lt.fold + FL::oCo);
+        dst = reinterpret_cast<V*>(sm + DS::co(B, K));
+        for (int q = t; q < ((B - 1) * FL::CS) / W; q += B) dst[q] = src[q];
+    }
+}
 
 }  // namespace mapk

@@ -525,38 +525,39 @@ __device__ __forceinline__ int down_tile() { return blockIdx.x == 0 ? gridDim.x 
 // Exclusive prefix (value function before the thread's first step) of every
 // thread of a tile from the tile's prefix `pin` (valid in thread 0): the
 // tile's up-sweep over the per-thread aggregates and the down-sweep.
-// With linear-fold constants (fold != nullptr, lti_fold.cuh) the tree runs on
+// With linear-fold constants (lt.fold != nullptr, lti_fold.cuh; the level
+// constants and co table staged by lti_stage_tables) the tree runs on
 // (b, eta) parts only: the leaves are the per-thread (b, eta) aggregates (2N
 // components) that the reduce kernel left in thr_agg, or with use_leaf `leaf`
 // (the last tile, see lti_last_tile_leaf), and every thread ends with one
 // one-variable combine of its prefix with pin.
 template <int N, typename S, class Prod>
 __device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, int K, const S* __restrict__ thr_agg,
-                                                   const Red<N, S>& pin, const S* __restrict__ fold,
+                                                   const Red<N, S>& pin, const LtiTiles<S>& lt,
                                                    bool use_leaf, const S (&leaf)[2 * N], S* nodes,
                                                    const CombineCtx& ctx, Red<N, S>& X)
 {
     const int B = blockDim.x, t = threadIdx.x;
     const long gthr = (long)tile * B + t;
     if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        if (fold) {
+        if (lt.fold) {
             constexpr int M = Prod::W;
             using FL = FoldLayout<N, M, S>;
-            using TS = LtiTreeSmem<N, M, S>;
-            const int LB = ilog2(B);
-            S* bq = nodes + TS::bq(B);
-            S* lv = nodes + TS::lv(B);
-            S* ps = nodes + TS::pin(B, LB);
-            for (int q = t; q < LB * FL::LS; q += B) lv[q] = fold[FL::oL + q];
+            using DS = LtiDownSmem<N, M, S>;
+            S* bq = nodes + DS::bq(B);
+            S* ps = nodes + DS::pin(B);
 #pragma unroll
-            for (int c = 0; c < 2 * N; ++c) bq[t * 2 * N + c] = use_leaf ? leaf[c] : thr_agg[wi_idx(gthr, c, 2 * N)];
+            for (int c = 0; c < 2 * N; ++c) bq[c * B + t] = use_leaf ? leaf[c] : thr_agg[wi_idx(gthr, c, 2 * N)];
             if (t == 0) node_store(pin, ps);
-            lti_tree_up<N, M, S>(bq, lv);
-            lti_tree_down_linear<N, M, S>(bq, fold + FL::oCo);
+            lti_tree_up<N, M, S>(bq, nodes + DS::lv(B, K));
+            lti_tree_down_linear<N, M, S>(bq, lt.co_smem ? nodes + DS::co(B, K) : lt.fold + FL::oCo);
             Red<N, S> P;
             node_load(ps, P);
+            S dl[2 * N];
+#pragma unroll
+            for (int c = 0; c < 2 * N; ++c) dl[c] = bq[c * B + t];
             if (gthr * K < prod.T)
-                lti_thread_value<N, M, S>(fold, bq + t * 2 * N, P, ctx, X);
+                lti_thread_value<N, M, S>(lt.fold, dl, P, ctx, X);
             else
                 X = P;                          // no steps: the value is not used
             return;
@@ -569,22 +570,6 @@ __device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, i
     }
     coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
     coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
-}
-
-// Shared memory (bytes) that the linear-fold mode of the down-sweep kernels
-// needs: the staged Gamma_i of lti_last_tile_leaf and the LtiTreeSmem area
-// (0 for producers without the linear fold)
-template <int N, typename S, class Prod>
-__host__ __device__ constexpr size_t lti_down_smem(int B, int K)
-{
-    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        int LB = 0;
-        while ((2 << LB) <= B) ++LB;
-        const int g = K * FoldLayout<N, Prod::W, S>::GS, tr = LtiTreeSmem<N, Prod::W, S>::end(B, LB);
-        return sizeof(S) * (size_t)(g > tr ? g : tr);
-    } else {
-        return 0;
-    }
 }
 
 // Linear-fold mode, last tile (which the reduce kernel does not cover), before
@@ -720,7 +705,7 @@ k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ th
 #pragma unroll
     for (int c = 0; c < 2 * N; ++c) {
         thr_agg[wi_idx(gthr, c, 2 * N)] = v[c];
-        bq[t * 2 * N + c] = v[c];
+        bq[c * B + t] = v[c];
     }
     lti_tree_up<N, M, S>(bq, lv);
     if (t == 0) {
@@ -814,6 +799,8 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
 
     const bool last_lti = fold && tile + 1 == (int)gridDim.x;
     S leaf[2 * N] = {};
+    if constexpr (Prod::LINEAR_FOLD && N <= 6)
+        if (fold) lti_stage_tables<N, Prod::W, S>(lt, K, nodes);
     if (last_lti) lti_last_tile_leaf<N, S>(prod, tile, K, fold, nodes, leaf);
     pdl_wait();                            // totals and aggregates of the reduce kernel
     pdl_trigger();
@@ -822,7 +809,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
         lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
     else
         tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
-    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, fold, last_lti, leaf, nodes, ctx, X);
+    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, lt, last_lti, leaf, nodes, ctx, X);
 
     Aff<N, S> comp_t;
     set_identity(comp_t);
@@ -933,6 +920,8 @@ k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
     constexpr int NR = Red<N, S>::NCOMP;
     const bool last_lti = fold && tile + 1 == (int)gridDim.x;
     S leaf[2 * N] = {};
+    if constexpr (Prod::LINEAR_FOLD && N <= 6)
+        if (fold) lti_stage_tables<N, Prod::W, S>(lt, K, nodes);
     if (last_lti) lti_last_tile_leaf<N, S>(prod, tile, K, fold, nodes, leaf);
     pdl_wait();
     pdl_trigger();
@@ -941,7 +930,7 @@ k_filter_states(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
         lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
     else
         tile_prefix_of<N, S>(tile_agg, tile, prior, nodes, ctx, pin);
-    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, fold, last_lti, leaf, nodes, ctx, X);
+    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, lt, last_lti, leaf, nodes, ctx, X);
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;

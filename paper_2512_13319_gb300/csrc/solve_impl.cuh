@@ -148,6 +148,8 @@ LtiTiles<S> lti_tiles_of(const map_smoother& h, const S* fold, S* w, S* gmaps)
             lt.F = reinterpret_cast<const S*>(base + TT::f_off(h.nt));
             lt.w = w;
             lt.gmaps = gmaps;
+            // the co table goes to shared memory when three CTAs per SM still fit
+            lt.co_smem = LtiDownSmem<N, Prod::W, S>::bytes(h.B, h.K, true) <= 72 * 1024;
         }
     }
     return lt;
@@ -178,7 +180,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const bool lti = fold != nullptr;
 
     const size_t sh_reduce = tree_smem<N, S>(B);
-    const size_t sh_down = std::max({tree_smem<N, S>(B), aff_tree_smem<N, S>(B), lti_down_smem<N, S, Prod>(B, K)});
+    size_t sh_down = std::max(tree_smem<N, S>(B), aff_tree_smem<N, S>(B));
     const size_t sh_rts = rts_smem<N, S>(B, K);
 
     static std::once_flag once;
@@ -206,6 +208,8 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const int ng = (lti ? nt - 1 : nt) > G ? (nt + G - 1) / G : 0;
     S* group_agg = ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr;
     const LtiTiles<S> lt = lti_tiles_of<N, S, Prod>(h, fold, tile_agg, group_agg);
+    if constexpr (Prod::LINEAR_FOLD && N <= 6)
+        if (lti) sh_down = LtiDownSmem<N, Prod::W, S>::bytes(B, K, lt.co_smem);
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx);
         first = false;
@@ -273,7 +277,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     S* filtT = filt_out ? filt_out + T * R::NCOMP : (S*)nullptr;
     const bool lti = fold != nullptr;          // forward scan in linear-fold mode (see run_rts)
     const size_t sh_tree = tree_smem<N, S>(B);
-    const size_t sh_states = std::max(sh_tree, lti ? lti_down_smem<N, S, Prod>(B, K) : 0);
+    size_t sh_states = sh_tree;
     const size_t sh_tfd = std::max(sh_tree, sizeof(S) * (size_t)B * K * N);   // k_tf_down stages the states
 
     static std::once_flag once;
@@ -298,6 +302,8 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     const int ng = lti && nt - 1 > prefix_group_tiles(B) ? (nt + prefix_group_tiles(B) - 1) / prefix_group_tiles(B) : 0;
     const LtiTiles<S> lt =
         lti_tiles_of<N, S, Prod>(h, fold, tile_agg, ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr);
+    if constexpr (Prod::LINEAR_FOLD && N <= 6)
+        if (lti) sh_states = LtiDownSmem<N, Prod::W, S>::bytes(B, K, lt.co_smem);
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg, (S*)nullptr,
                ctx);
@@ -380,7 +386,7 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
     while (ne < 31 && (1L << ne) <= (long)h.nt - 1) ++ne;
     if (!h.d_fold || h.K > FL::KMAX || LB > FL::LMAX || ne > TT::ELMAX ||
         TT::bytes(h.nt) > fold_bytes(N, M, sizeof(S), h.nt) ||
-        LtiTreeSmem<N, M, S>::end(h.B, LB) > 2 * h.B * CoopLayout<N, S>::NE ||
+        LtiDownSmem<N, M, S>::bytes(h.B, h.K, false) > 200 * 1024 ||
         LtiReduceSmem<N, M, S>::bytes(h.B, h.K, LB) > 200 * 1024)
         return MAP_OK;
     if (h.fold_K != h.K || h.fold_B != h.B) {
