@@ -206,6 +206,96 @@ __device__ void coop_elem_down(S* nodes, S* scr_all, const Red<N, S>& pin, const
     node_load(slot<N, S>(nodes, B, 0, threadIdx.x), out);
 }
 
+// ---------------------------------------------------------------------------
+// ordered compositions of one affine map per thread (leaf t = thread t, leaf 0
+// outermost) with warp shuffles: no shared-memory tree levels and only one or
+// two block barriers
+// ---------------------------------------------------------------------------
+// Within a warp (Kogge-Stone): lane l ends with H_l o H_{l+1} o ... o H_31.
+template <int N, typename S>
+__device__ __forceinline__ void warp_aff_suffix(Aff<N, S>& H)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        Aff<N, S> G;
+#pragma unroll
+        for (int q = 0; q < N * N; ++q) G.F[q] = __shfl_down_sync(0xffffffffu, H.F[q], d);
+#pragma unroll
+        for (int q = 0; q < N; ++q) G.c[q] = __shfl_down_sync(0xffffffffu, H.c[q], d);
+        if (lane + d < 32) compose<N, S>(H, G, H);
+    }
+}
+
+// H_0 o H_1 o ... o H_{B-1}, returned in thread 0 (H is overwritten in the
+// other threads).  red: B / 32 Aff records of shared memory.  Ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void block_aff_reduce(Aff<N, S>& H, S* red)
+{
+    constexpr int NA = Aff<N, S>::NCOMP;
+    const int t = threadIdx.x, nw = blockDim.x >> 5;
+    warp_aff_suffix<N, S>(H);
+    if ((t & 31) == 0)
+        for (int c = 0; c < NA; ++c) red[(t >> 5) * NA + c] = comp(H, c);
+    __syncthreads();
+    if (t == 0) {
+        for (int w = 1; w < nw; ++w) {
+            Aff<N, S> g;
+            for (int c = 0; c < NA; ++c) comp(g, c) = red[w * NA + c];
+            compose<N, S>(H, g, H);
+        }
+    }
+    __syncthreads();
+}
+
+// The state at the END of every thread's steps, x_t = (H_{t+1} o ... o H_{B-1})(xe),
+// from the state xe at the end of the block (read by thread 0 from xe_in).
+// red: B / 32 Aff records followed by B / 32 states of shared memory.
+// Ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void block_aff_end_states(const Aff<N, S>& H, const S* xe_in, S* red, S* x)
+{
+    constexpr int NA = Aff<N, S>::NCOMP;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    S* ys = red + nw * NA;
+    Aff<N, S> Sf = H;
+    warp_aff_suffix<N, S>(Sf);             // lane l: H_l o ... o H_31 of its warp
+    if (lane == 0)
+        for (int c = 0; c < NA; ++c) red[w * NA + c] = comp(Sf, c);
+    __syncthreads();
+    if (t == 0) {                          // y_w: the state at the end of warp w
+        S y[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) y[i] = xe_in[i];
+        for (int ww = nw - 1; ww >= 0; --ww) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) ys[ww * N + i] = y[i];
+            if (ww == 0) break;
+            Aff<N, S> g;
+            for (int c = 0; c < NA; ++c) comp(g, c) = red[ww * NA + c];
+            S z[N];
+            affine_apply<N, S>(g, y, z);
+#pragma unroll
+            for (int i = 0; i < N; ++i) y[i] = z[i];
+        }
+    }
+    __syncthreads();
+    Aff<N, S> nx;                          // H_{l+1} o ... o H_31
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) nx.F[q] = __shfl_down_sync(0xffffffffu, Sf.F[q], 1);
+#pragma unroll
+    for (int q = 0; q < N; ++q) nx.c[q] = __shfl_down_sync(0xffffffffu, Sf.c[q], 1);
+    S y[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = ys[w * N + i];
+    if (lane < 31)
+        affine_apply<N, S>(nx, y, x);
+    else
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = y[i];
+    __syncthreads();
+}
+
 // affine up-sweep: node(d+1, j) = node(d, 2j) o node(d, 2j+1); a leaf maps the
 // state at the END of its steps to the state at their START
 template <int N, typename S>
@@ -389,8 +479,8 @@ k_group_totals(const S* __restrict__ tile_agg, int nt, S* __restrict__ group_agg
 // tile maps m_i(v) = F_i v + w_i for i = first_all..last_all-1, the later map
 // outermost.  Map i has F_i at F + i * fs and w_i at w + i * ws.  Thread t
 // composes the t-th run of at most ceil(count / B) maps counted from the end;
-// the runs are composed with the sub-warp affine tree (leaf 0 outermost).
-// Uses the affine-tree area of `nodes`; ends with a barrier.
+// the runs are composed in thread order (block_aff_reduce, leaf 0 outermost).
+// Uses the start of `nodes`; ends with a barrier.
 template <int N, typename S>
 __device__ __forceinline__ void fold_tile_maps(const S* __restrict__ F, int fs, const S* __restrict__ w, int ws,
                                                int first_all, int last_all, S* nodes, Aff<N, S>& out)
@@ -408,10 +498,8 @@ __device__ __forceinline__ void fold_tile_maps(const S* __restrict__ F, int fs, 
         for (int q = 0; q < N; ++q) m.c[q] = w[(long)i * ws + q];
         compose<N, S>(m, H, H);
     }
-    node_store(H, aslot<N, S>(nodes, B, 0, t));
-    coop_aff_up<N, S>(nodes);
-    if (t == 0) node_load(aslot<N, S>(nodes, B, ilog2(B), 0), out);
-    __syncthreads();
+    block_aff_reduce<N, S>(H, nodes);
+    if (t == 0) out = H;
 }
 
 // Linear-fold mode: value function before tile `tile` (returned in thread 0):
@@ -469,7 +557,7 @@ k_lti_group_maps(const LtiTiles<S> lt, int nfull)
 // `xe` (shared memory outside the affine-tree area): the closed-loop maps of
 // tiles tile+1..nt-1 composed (thread runs, then the affine tree; a map takes
 // the state at the end of its steps to the state at their start) and applied
-// to x_T.  Uses the affine-tree area of `nodes`; ends with a barrier.
+// to x_T.  Uses the start of `nodes` (block_aff_reduce); ends with a barrier.
 template <int N, typename S>
 __device__ __forceinline__ void tile_suffix_state(const S* __restrict__ tile_aff, int tile, int nt,
                                                   const S* __restrict__ xT, S* nodes, S* xe)
@@ -491,15 +579,12 @@ __device__ __forceinline__ void tile_suffix_state(const S* __restrict__ tile_aff
         aos_load(tile_aff, i, a);
         compose<N, S>(a, H, H);
     }
-    node_store(H, aslot<N, S>(nodes, B, 0, t));
-    coop_aff_up<N, S>(nodes);
+    block_aff_reduce<N, S>(H, nodes);
     if (t == 0) {
-        Aff<N, S> root;
-        node_load(aslot<N, S>(nodes, B, ilog2(B), 0), root);
         S x[N], y[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) x[i] = xT[i];
-        affine_apply<N, S>(root, x, y);
+        affine_apply<N, S>(H, x, y);
 #pragma unroll
         for (int i = 0; i < N; ++i) xe[i] = y[i];
     }
@@ -889,13 +974,8 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
     write_final_if_last<N, S>(T, tile, K, X, final_out, xT_out, filtT_out, ctx);
     wi_store(thr_aff, gthr, comp_t);
     __syncthreads();                       // the filter trees are done with shared memory
-    node_store(comp_t, aslot<N, S>(nodes, B, 0, t));
-    coop_aff_up<N, S>(nodes);
-    if (t == 0) {
-        Aff<N, S> root;
-        node_load(aslot<N, S>(nodes, B, ilog2(B), 0), root);
-        aos_store(tile_aff, (long)tile, root);
-    }
+    block_aff_reduce<N, S>(comp_t, nodes);
+    if (t == 0) aos_store(tile_aff, (long)tile, comp_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1117,16 +1197,12 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const
     pdl_wait();                            // maps and x_T of the previous kernel
     S* xe_sh = nodes + 2 * B * CoopLayout<N, S>::NA;   // staging area, free until the state loop
     tile_suffix_state<N, S>(tile_aff, blockIdx.x, gridDim.x, xT, nodes, xe_sh);
-    S xe[N], x[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) xe[i] = xe_sh[i];
+    S x[N];
     {
         Aff<N, S> a;
         wi_load(thr_aff, gthr, a);
-        node_store(a, aslot<N, S>(nodes, B, 0, t));
+        block_aff_end_states<N, S>(a, xe_sh, nodes, x);
     }
-    coop_aff_up<N, S>(nodes);
-    coop_aff_down<N, S>(nodes, xe, x);
     // the states are staged past the affine tree and written out coalesced
     const int SP = rts_stage_stride(K, N);
     S* st = nodes + 2 * B * CoopLayout<N, S>::NA;
@@ -1210,12 +1286,18 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const
         }
     }
     __syncthreads();
+    // each warp stores whole rows (one thread's K states, contiguous in x_out)
     const int KN = K * N;
     const long base = (long)blockIdx.x * B * KN;
-    const long lim = T * N;
-    for (int idx = t; idx < B * KN; idx += B) {
-        const int tt = idx / KN;
-        if (base + idx < lim) x_out[base + idx] = st[tt * SP + (idx - tt * KN)];
+    const long lim = T * N;                // x_T itself comes from the filter kernel
+    const int lane = t & 31, nw = B >> 5;
+    for (int tt = t >> 5; tt < B; tt += nw) {
+        const S* src = st + tt * SP;
+        S* dst = x_out + base + (long)tt * KN;
+        const long rem = lim - (base + (long)tt * KN);
+#pragma unroll 4
+        for (int r = lane; r < KN; r += 32)
+            if (r < rem) dst[r] = src[r];
     }
 }
 
