@@ -1,7 +1,8 @@
-// Bulk global -> shared copies on the tensor memory accelerator (TMA):
-// cp.async.bulk completing on an mbarrier in shared memory, with a bounded
-// wait.  Used to stage a tile's contiguous per-step inputs with one
-// instruction instead of per-thread strided loads.
+// Bulk copies on the tensor memory accelerator (TMA): global -> shared
+// completing on an mbarrier in shared memory, with a bounded wait (a tile's
+// contiguous per-step inputs staged with one instruction instead of per-thread
+// strided loads), and shared -> global in bulk groups (a tile's outputs written
+// with one instruction).
 //
 // Requirements (checked by the callers): source and destination 16-byte
 // aligned, size a multiple of 16 bytes and below 2^20 (the transaction count
@@ -63,5 +64,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 }
 
 constexpr int MBAR_POLLS = 1 << 22;
+
+// Bulk shared -> global copy (bulk-group completion).  The generic-proxy
+// writes of the source must be made visible to the async proxy first
+// (fence_proxy_async_smem by the issuing thread after a block barrier).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, const void* src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// commit the issued bulk copies as one group and wait until all of them have
+// completed (source read and destination written)
+__device__ __forceinline__ void bulk_commit_and_wait()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 
 }  // namespace mapk

@@ -1166,8 +1166,26 @@ k_tf_down(const __grid_constant__ RProd prod, int K, const S* __restrict__ thr_a
         if (base + idx < lim) x_out[base + idx] = st[idx];
 }
 
-// shared-memory stride of one thread's staged states (odd: no bank conflicts)
-__host__ __device__ __forceinline__ int rts_stage_stride(int K, int N) { return (K * N) | 1; }
+// shared-memory stride of one thread's staged states: its K states
+// contiguous, so that the staged block is the tile's output block
+__host__ __device__ __forceinline__ int rts_stage_stride(int K, int N) { return K * N; }
+
+// x (N scalars) into shared memory, as 16-byte words when the row allows
+template <int N, typename S>
+__device__ __forceinline__ void stage_state(S* dst, const S* x)
+{
+    if constexpr (sizeof(S) == 4 && N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N; q += 4)
+            *reinterpret_cast<float4*>(dst + q) = make_float4(x[q], x[q + 1], x[q + 2], x[q + 3]);
+    } else if constexpr (sizeof(S) == 8 && N % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < N; q += 2) *reinterpret_cast<double2*>(dst + q) = make_double2(x[q], x[q + 1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) dst[q] = x[q];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // phase 3: per-step smoothed states x_k = E_k x_{k+1} + g_k
@@ -1246,8 +1264,7 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const
 #pragma unroll
                         for (int j = 0; j < N; ++j) x[j] = y[j];
                     }
-#pragma unroll
-                    for (int j = 0; j < N; ++j) mine[i * N + j] = x[j];
+                    stage_state<N, S>(mine + i * N, x);
                 }
             }
         }
@@ -1279,26 +1296,28 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const
 #pragma unroll
                         for (int j = 0; j < N; ++j) x[j] = y[j];
                     }
-#pragma unroll
-                    for (int j = 0; j < N; ++j) mine[i * N + j] = x[j];
+                    stage_state<N, S>(mine + i * N, x);
                 }
             }
         }
     }
     __syncthreads();
-    // each warp stores whole rows (one thread's K states, contiguous in x_out)
+    // the staged block is the tile's block of x_out (x_T itself comes from the
+    // filter kernel): one bulk copy of its 16-byte part, the rest by plain stores
     const int KN = K * N;
     const long base = (long)blockIdx.x * B * KN;
-    const long lim = T * N;                // x_T itself comes from the filter kernel
-    const int lane = t & 31, nw = B >> 5;
-    for (int tt = t >> 5; tt < B; tt += nw) {
-        const S* src = st + tt * SP;
-        S* dst = x_out + base + (long)tt * KN;
-        const long rem = lim - (base + (long)tt * KN);
-#pragma unroll 4
-        for (int r = lane; r < KN; r += 32)
-            if (r < rem) dst[r] = src[r];
+    const long cnt = min((long)B * KN, T * N - base);
+    long done = 0;
+    if ((reinterpret_cast<uintptr_t>(x_out + base) & 15) == 0) {
+        done = cnt * (long)sizeof(S) / 16 * 16 / (long)sizeof(S);
+        if (t == 0 && done > 0) {
+            fence_proxy_async_smem();
+            bulk_copy_s2g(x_out + base, st, (unsigned)(done * sizeof(S)));
+            bulk_commit_and_wait();
+        }
     }
+    for (long idx = done + t; idx < cnt; idx += B) x_out[base + idx] = st[idx];
+    __syncthreads();                       // the bulk copy has read the staged block
 }
 
 // shared memory of k_rts_down: the affine tree and the staged states
