@@ -257,15 +257,7 @@ __device__ __forceinline__ bool apply_lowrank(const Elem<N, S>& e, const S* Gam,
                                               float cond_max, S* Vout = nullptr)
 {
     S U[N * R];                                       // U = P Gam
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            S s = S(0);
-#pragma unroll
-            for (int j = 0; j < N; ++j) s = fma(p.P[Sym<N>::at(i, j)], Gam[j * R + k], s);
-            U[i * R + k] = s;
-        }
+    ms::sym_mr<N, R, S>(p.P, Gam, U);
     S L[R * R], Li[R * R], W[R * R];                  // I + Gam^T U = L L^T,  W = L^-T L^-1
     bool ok = true;
 #pragma unroll
@@ -329,37 +321,13 @@ __device__ __forceinline__ bool apply_lowrank(const Elem<N, S>& e, const S* Gam,
     }
     if (!(float(nD) * float(nW) <= cond_max)) return false;
     S V[R * N], Em[N * N];                            // V = W (U^T A),  E = A - Gam V
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            S s = S(0);
-#pragma unroll
-            for (int i = 0; i < N; ++i) s = fma(U[i * R + k], e.A[i * N + j], s);
-            Em[k * N + j] = s;                        // U^T A, temporarily
-        }
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            S s = S(0);
-#pragma unroll
-            for (int l = 0; l < R; ++l) s = fma(W[k * R + l], Em[l * N + j], s);
-            V[k * N + j] = s;
-        }
+    ms::mtm<R, N, N, S>(U, e.A, Em);                  // U^T A, temporarily
+    ms::mm_sub<R, R, N, S>(nullptr, W, Em, V);
     if (Vout) {                                       // E = A - Gam V: the compact form of the map
 #pragma unroll
         for (int q = 0; q < R * N; ++q) Vout[q] = V[q];
     }
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            S s = e.A[i * N + j];
-#pragma unroll
-            for (int k = 0; k < R; ++k) s = fma(-Gam[i * R + k], V[k * N + j], s);
-            Em[i * N + j] = s;
-        }
+    ms::mm_sub<N, R, N, S>(e.A, Gam, V, Em);
     if (ALPHA) {
         S t[R], z[N], t2[R];
 #pragma unroll
@@ -406,15 +374,7 @@ __device__ __forceinline__ bool apply_lowrank(const Elem<N, S>& e, const S* Gam,
 #pragma unroll
     for (int i = 0; i < N; ++i) w[i] = p.v[i] - w[i];
     Red<N, S> r;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = i; j < N; ++j) {
-            S s = e.J[Sym<N>::at(i, j)];
-#pragma unroll
-            for (int k = 0; k < N; ++k) s = fma(e.A[k * N + i], PE[k * N + j], s);
-            r.P[Sym<N>::at(i, j)] = s;
-        }
+    ms::sym_atb_add<N, S>(e.A, PE, e.J, r.P);         // A^T (P E) + J
     ms::mtv_add<N, S>(Em, w, e.eta, r.v);             // E^T w + eta
     p = r;
     return true;

@@ -10,6 +10,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+#include <type_traits>
 
 #define MS_DEV __device__ __forceinline__
 
@@ -34,10 +35,30 @@ template <> MS_DEV float sabs<float>(float x) { return fabsf(x); }
 template <typename S> MS_DEV S pivot_rcp(S p) { return S(1) / p; }
 template <> MS_DEV float pivot_rcp<float>(float p) { return __fdividef(1.0f, p); }
 
+// FP32 with an even N: two adjacent output columns per paired multiply-add
+// (one f32x2 instruction; the same operations and rounding as two FMAs)
+template <int N, typename S>
+constexpr bool use_ffma2 = std::is_same<S, float>::value && N % 2 == 0;
+
 // c = a b  (N x N)
 template <int N, typename S>
 MS_DEV void mm(const S* a, const S* b, S* c)
 {
+    if constexpr (use_ffma2<N, S>) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; j += 2) {
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    s = __ffma2_rn(make_float2(a[i * N + k], a[i * N + k]), make_float2(b[k * N + j], b[k * N + j + 1]),
+                                   s);
+                c[i * N + j] = s.x;
+                c[i * N + j + 1] = s.y;
+            }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -68,6 +89,22 @@ MS_DEV void m_sym(const S* a, const S* sp, S* c)
 template <int N, typename S>
 MS_DEV void sym_m(const S* sp, const S* a, S* c)
 {
+    if constexpr (use_ffma2<N, S>) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; j += 2) {
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float p = sp[Sym<N>::at(i, k)];
+                    s = __ffma2_rn(make_float2(p, p), make_float2(a[k * N + j], a[k * N + j + 1]), s);
+                }
+                c[i * N + j] = s.x;
+                c[i * N + j + 1] = s.y;
+            }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -113,6 +150,22 @@ MS_DEV void sym_abt_add(const S* a, const S* b, const S* add, S* out)
 template <int N, typename S>
 MS_DEV void sym_atb_add(const S* a, const S* b, const S* add, S* out)
 {
+    if constexpr (use_ffma2<N, S>) {
+        // the column pairs (j, j+1) that meet the upper triangle of row i
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = i & ~1; j < N; j += 2) {
+                float2 s = make_float2(j >= i ? add[Sym<N>::at(i, j)] : 0.f, add[Sym<N>::at(i, j + 1)]);
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    s = __ffma2_rn(make_float2(a[k * N + i], a[k * N + i]), make_float2(b[k * N + j], b[k * N + j + 1]),
+                                   s);
+                if (j >= i) out[Sym<N>::at(i, j)] = s.x;
+                out[Sym<N>::at(i, j + 1)] = s.y;
+            }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -141,12 +194,117 @@ MS_DEV void mv(const S* a, const S* x, S* y)
 template <int N, typename S>
 MS_DEV void mtv_add(const S* a, const S* x, const S* add, S* y)
 {
+    if constexpr (use_ffma2<N, S>) {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            float2 s = make_float2(add[i], add[i + 1]);
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                s = __ffma2_rn(make_float2(a[k * N + i], a[k * N + i + 1]), make_float2(x[k], x[k]), s);
+            y[i] = s.x;
+            y[i + 1] = s.y;
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         S s = add[i];
 #pragma unroll
         for (int k = 0; k < N; ++k) s = fma(a[k * N + i], x[k], s);
         y[i] = s;
+    }
+}
+
+// Rectangular products for the low-rank update (row-major operands; FP32
+// pairs two adjacent output columns per instruction when C is even).
+// c (N x C) = S b, S packed symmetric N x N, b N x C
+template <int N, int C, typename S>
+MS_DEV void sym_mr(const S* sp, const S* b, S* c)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if constexpr (std::is_same<S, float>::value && C % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < C; j += 2) {
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float p = sp[Sym<N>::at(i, k)];
+                    s = __ffma2_rn(make_float2(p, p), make_float2(b[k * C + j], b[k * C + j + 1]), s);
+                }
+                c[i * C + j] = s.x;
+                c[i * C + j + 1] = s.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                S s = S(0);
+#pragma unroll
+                for (int k = 0; k < N; ++k) s = fma(sp[Sym<N>::at(i, k)], b[k * C + j], s);
+                c[i * C + j] = s;
+            }
+        }
+    }
+}
+
+// c (R x C) = a^T b, a K x R, b K x C
+template <int R, int K, int C, typename S>
+MS_DEV void mtm(const S* a, const S* b, S* c)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if constexpr (std::is_same<S, float>::value && C % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < C; j += 2) {
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    s = __ffma2_rn(make_float2(a[k * R + r], a[k * R + r]), make_float2(b[k * C + j], b[k * C + j + 1]),
+                                   s);
+                c[r * C + j] = s.x;
+                c[r * C + j + 1] = s.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                S s = S(0);
+#pragma unroll
+                for (int k = 0; k < K; ++k) s = fma(a[k * R + r], b[k * C + j], s);
+                c[r * C + j] = s;
+            }
+        }
+    }
+}
+
+// c (R x C) = base - a b, a R x K, b K x C (base may be null: c = a b)
+template <int R, int K, int C, typename S>
+MS_DEV void mm_sub(const S* base, const S* a, const S* b, S* c)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if constexpr (std::is_same<S, float>::value && C % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < C; j += 2) {
+                float2 s = base ? make_float2(base[r * C + j], base[r * C + j + 1]) : make_float2(0.f, 0.f);
+                const float sg = base ? -1.f : 1.f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float v = sg * a[r * K + k];
+                    s = __ffma2_rn(make_float2(v, v), make_float2(b[k * C + j], b[k * C + j + 1]), s);
+                }
+                c[r * C + j] = s.x;
+                c[r * C + j + 1] = s.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                S s = base ? base[r * C + j] : S(0);
+                const S sg = base ? S(-1) : S(1);
+#pragma unroll
+                for (int k = 0; k < K; ++k) s = fma(sg * a[r * K + k], b[k * C + j], s);
+                c[r * C + j] = s;
+            }
+        }
     }
 }
 
