@@ -51,29 +51,36 @@ def model_and_data(seed, T=T_FULL):
 # per-step update goes through the matrix inversion lemma)
 # ----------------------------------------------------------------------------
 def work_model(n, m, K, B, nt, wbytes, r=None):
-    combine = 8 * n ** 3 + 5 * n ** 2           # general combine (Eq. 36), one (I + C J) inverse
-    apply_alpha = 4.5 * n ** 3 + 4.5 * n ** 2   # one-variable update + closed-loop map
-    apply_plain = 4.5 * n ** 3 + 2.5 * n ** 2
-    if r is not None and r < n:
-        apply_alpha = (n * n * r + n * r * (r + 1) / 2 + r ** 3 + 2 * r * n * n + r * r * n
-                       + 4 * n * r + r * r + n ** 3 + n * n * (n + 1) / 2 + 2 * n * n)
-    compose = n ** 3 + n ** 2
-    lin_node = 4 * n * n                        # (b, eta) tree node of a full tile
+    """Multiply-adds (returned as FLOP = 2 MAC) and minimal DRAM bytes per time
+    step of each kernel of the linear-fold (LTI) solve, counted from the kernels:
+    per-step work, plus the per-tile work (tile prefix, thread-prefix trees,
+    tile map) spread over the B*K steps of a tile.  Redundant work of the
+    shuffle reductions is not counted."""
+    compose = n ** 3 + n ** 2                   # affine map composition
+    apply_plain = 4.5 * n ** 3 + 2.5 * n ** 2   # one-variable combine (value function update)
+    apply_alpha = 4.5 * n ** 3 + 4.5 * n ** 2   # ... plus the closed-loop map
+    if r is not None and r < n:                 # matrix-inversion-lemma update of rank r
+        apply_alpha = (n * n * r + n * r * (r + 1) / 2 + r ** 3 + r * n * n + r * r * n + n * n * r
+                       + (2 * n * r + r * r + n * r + n * r)   # closed-loop offset g
+                       + n ** 3 + n * n + n * n * (n + 1) / 2 + n * n)
+    lin_node = 4 * n * n                        # (b, eta) tree node
     L = B * K
-    tree = (B - 1) / L
-    # each CTA's reduction of the tile totals before it: ceil(nt / B) combines per
-    # thread, a tree of B leaves and one one-variable update
-    prefix = (-(-nt // B) * combine + (B - 1) * combine + apply_plain) / L
-    na = n * n + n                              # closed-loop map components
+    mean_prefix_maps = (nt - 1) / 2.0           # tile maps a CTA folds, on average
+    per_tile_down = (mean_prefix_maps * compose + n * n          # tile prefix
+                     + 2 * (B - 1) * lin_node + B * apply_plain   # thread-prefix up/down sweeps, one combine each
+                     + (B - 1) * compose)                         # tile map
+    per_tile_rts = mean_prefix_maps * compose + (B - 1) * compose + B * n * n
+    na = (r * n + n) if (r is not None and r < n) else (n * n + n)   # stored closed-loop map
+    per_step_rts = (r * n + n * n + n * r) if (r is not None and r < n) else n * n
     mac = {
-        "filter_reduce": 2 * n * m + tree * lin_node,
-        "filter_down": (n * m + apply_alpha + compose + prefix + tree * (lin_node + apply_plain + compose)),
-        "rts_down": n * n + tree * (compose + n * n) + (-(-nt // B) * compose + (B - 1) * compose) / L,
+        "filter_reduce": 2 * n * m + ((B - 1) * lin_node + 2 * n * n) / L,
+        "filter_down": n * m + apply_alpha + compose + per_tile_down / L,
+        "rts_down": per_step_rts + per_tile_rts / L,
     }
     byt = {   # minimal DRAM bytes per step of each kernel
         "filter_reduce": wbytes * (m + 2 * n / K),
-        "filter_down": wbytes * (m + 2 * n / K + na + na / K),
-        "rts_down": wbytes * (na + na / K + n),
+        "filter_down": wbytes * (m + 2 * n / K + na + (n * n + n) / K),
+        "rts_down": wbytes * (na + (n * n + n) / K + n),
     }
     return {k: 2 * v for k, v in mac.items()}, byt
 
@@ -81,7 +88,7 @@ def work_model(n, m, K, B, nt, wbytes, r=None):
 # DRAM bytes (read + write) of one k_filter_down launch on the nx=4, T=2^20 FP32
 # workload, from one ncu capture of this kernel version (cold cache); None
 # until the current version has been captured
-K_FILTER_DOWN_DRAM_BYTES = None
+K_FILTER_DOWN_DRAM_BYTES = 10482944 + 3812864
 
 
 def solve_bytes(n, m, wbytes):

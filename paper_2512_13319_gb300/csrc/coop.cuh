@@ -439,35 +439,4 @@ __device__ __forceinline__ void coop_apply(const S* __restrict__ En, const S* Pn
     coop_apply_parts<N, S>(En, En + L::ob, En + L::oeta, Pn, On, scr, active, ctx);
 }
 
-// On = F1n o F2n (affine maps)
-template <int N, typename S>
-__device__ __forceinline__ void coop_compose(const S* __restrict__ F1n, const S* __restrict__ F2n,
-                                             S* __restrict__ On, bool active)
-{
-    using L = CoopLayout<N, S>;
-    constexpr int NL = L::NL, P = L::P;
-    const int r = threadIdx.x & (NL - 1);
-    const int rr = r < N ? r : N - 1;
-    S f1[N], F2[N][N], c2[N];
-    row_load<N, S>(F1n + L::oF, rr, f1);
-    mat_load<N, S>(F2n + L::oF, F2);
-    vec_load<N, S>(F2n + L::oc, c2);
-    S o[N];
-    S oc = F1n[L::oc + rr];
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        S s = S(0);
-#pragma unroll
-        for (int k = 0; k < N; ++k) s = fma(f1[k], F2[k][q], s);
-        o[q] = s;
-        oc = fma(f1[q], c2[q], oc);
-    }
-    __syncwarp();
-    if (active && r < N) {
-#pragma unroll
-        for (int q = 0; q < N; ++q) On[L::oF + rr * P + q] = o[q];
-        On[L::oc + rr] = oc;
-    }
-}
-
 }  // namespace mapk

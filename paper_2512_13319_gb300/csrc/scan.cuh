@@ -142,12 +142,6 @@ __device__ __forceinline__ S* slot(S* nodes, int B, int d, int j)
 {
     return slotn<CoopLayout<N, S>::NE>(nodes, B, d, j);
 }
-// affine trees: slots of CoopLayout::NA scalars
-template <int N, typename S>
-__device__ __forceinline__ S* aslot(S* nodes, int B, int d, int j)
-{
-    return slotn<CoopLayout<N, S>::NA>(nodes, B, d, j);
-}
 
 // up-sweep: node(d+1, j) = node(d, 2j+1) (x) node(d, 2j); leaves stored by the caller
 template <int N, typename S>
@@ -296,74 +290,6 @@ __device__ __forceinline__ void block_aff_end_states(const Aff<N, S>& H, const S
     __syncthreads();
 }
 
-// affine up-sweep: node(d+1, j) = node(d, 2j) o node(d, 2j+1); a leaf maps the
-// state at the END of its steps to the state at their START
-template <int N, typename S>
-__device__ void coop_aff_up(S* nodes)
-{
-    using L = CoopLayout<N, S>;
-    const int B = blockDim.x, LB = ilog2(B);
-    const int ng = B / L::NL, g = threadIdx.x / L::NL;
-    for (int d = 0; d < LB; ++d) {
-        __syncthreads();
-        const int cnt = B >> (d + 1);
-        for (int base = 0; base < cnt; base += ng) {
-            const int j = base + g;
-            const bool act = j < cnt;
-            if (__any_sync(0xffffffffu, act)) {
-                const int jj = act ? j : base;
-                coop_compose<N, S>(aslot<N, S>(nodes, B, d, 2 * jj), aslot<N, S>(nodes, B, d, 2 * jj + 1),
-                                   aslot<N, S>(nodes, B, d + 1, jj), act);
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// suffix down-sweep: the state at the END of every leaf (written over the
-// nodes) from the state `xend` at the end of the block (given by thread 0)
-template <int N, typename S>
-__device__ void coop_aff_down(S* nodes, const S* xend, S* out)
-{
-    using L = CoopLayout<N, S>;
-    const int B = blockDim.x, LB = ilog2(B);
-    const int NL = L::NL, ng = B / NL, g = threadIdx.x / NL, r = threadIdx.x & (NL - 1);
-    const int rr = r < N ? r : N - 1;
-    if (threadIdx.x == 0) {
-        S* root = aslot<N, S>(nodes, B, LB, 0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) root[i] = xend[i];
-    }
-    for (int d = LB - 1; d >= 0; --d) {
-        __syncthreads();
-        const int cnt = B >> (d + 1);
-        for (int base = 0; base < cnt; base += ng) {
-            const int j = base + g;
-            const bool act = j < cnt;
-            if (__any_sync(0xffffffffu, act)) {
-                const int jj = act ? j : base;
-                S* par = aslot<N, S>(nodes, B, d + 1, jj);
-                S* lft = aslot<N, S>(nodes, B, d, 2 * jj);
-                S* rgt = aslot<N, S>(nodes, B, d, 2 * jj + 1);
-                S f[N], x[N];
-                row_load<N, S>(rgt + L::oF, rr, f);
-                vec_load<N, S>(par, x);
-                S y = rgt[L::oc + rr];
-#pragma unroll
-                for (int q = 0; q < N; ++q) y = fma(f[q], x[q], y);
-                __syncwarp();
-                if (act && r < N) {
-                    lft[rr] = y;
-                    rgt[rr] = x[rr];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    const S* leaf = aslot<N, S>(nodes, B, 0, threadIdx.x);
-#pragma unroll
-    for (int i = 0; i < N; ++i) out[i] = leaf[i];
-}
 
 // shared memory of the element trees: 2B node slots + one scratch area per group
 template <int N, typename S>
