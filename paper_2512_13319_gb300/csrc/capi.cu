@@ -210,9 +210,10 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
 
     h->ws_bytes = ops->workspace_bytes(*h);
     if ((e = cudaMalloc(&h->ws, h->ws_bytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc workspace");
-    if ((e = cudaMalloc(&h->d_stats, 3 * sizeof(unsigned long long))) != cudaSuccess)
+    // three event counters, then the grid barrier state of the single-launch solve
+    if ((e = cudaMalloc(&h->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMalloc");
-    if ((e = cudaMemset(h->d_stats, 0, 3 * sizeof(unsigned long long))) != cudaSuccess)
+    if ((e = cudaMemset(h->d_stats, 0, 4 * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMemset");
     if ((e = cudaMalloc(&h->d_cost, sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
     if (h->model != MAP_MODEL_LINEAR) {

@@ -22,6 +22,7 @@
 // pivoting, and a device counter records it; the products around the inverse
 // stay in S.
 #pragma once
+#include <type_traits>
 #include "smallmat.cuh"
 
 namespace mapk {
@@ -402,19 +403,141 @@ __device__ __forceinline__ void affine_apply(const Aff<N, S>& a, const S* x, S* 
     for (int i = 0; i < N; ++i) y[i] += a.c[i];
 }
 
+// FP32 Cholesky factor of a packed symmetric matrix (L lower, il = 1 / diag);
+// false when a pivot is not positive
+template <int N>
+__device__ __forceinline__ bool chol_f32(const float* P, float* L, float* il)
+{
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        float d = P[Sym<N>::at(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fmaf(-L[j * N + k], L[j * N + k], d);
+        pd = pd && d > 0.f;
+        il[j] = rsqrtf(d > 0.f ? d : 1.f);
+        L[j * N + j] = 1.f / il[j];
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            float s = P[Sym<N>::at(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = fmaf(-L[i * N + k], L[j * N + k], s);
+            L[i * N + j] = s * il[j];
+        }
+    }
+    return pd;
+}
+
+// x = (L L^T)^-1 r
+template <int N>
+__device__ __forceinline__ void chol_solve_f32(const float* L, const float* il, const float* r, float* x)
+{
+    float z[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float s = r[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s = fmaf(-L[i * N + k], z[k], s);
+        z[i] = s * il[i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        float s = z[i];
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) s = fmaf(-L[k * N + i], x[k], s);
+        x[i] = s * il[i];
+    }
+}
+
 // x = P^-1 v (the minimiser of a one-variable value function, Eq. 18 initial condition)
 template <int N, typename S>
 __device__ __forceinline__ bool red_argmin(const Red<N, S>& p, S* x)
 {
-    double M[N * N], Mi[N * N], v[N], xd[N];
+    if constexpr (std::is_same<S, float>::value) {
+        // FP32 Cholesky with iterative refinement on FP64 residuals v - P x: the
+        // FP64 solution to within a few FP32 ulps once a correction falls below
+        // 2^-22 of x (at most three rounds); otherwise the FP64 solve below
+        float L[N * N], il[N], xf[N];
+        if (chol_f32<N>(p.P, L, il)) {
+            chol_solve_f32<N>(L, il, p.v, xf);
+            bool conv = false;
+#pragma unroll 1
+            for (int it = 0; it < 3 && !conv; ++it) {
+                float r[N], dx[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    double s = double(p.v[i]);
+#pragma unroll
+                    for (int k = 0; k < N; ++k) s = fma(-double(p.P[Sym<N>::at(i, k)]), double(xf[k]), s);
+                    r[i] = float(s);
+                }
+                chol_solve_f32<N>(L, il, r, dx);
+                float nd = 0.f, nx = 0.f;
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    xf[i] += dx[i];
+                    nd = fmaxf(nd, fabsf(dx[i]));
+                    nx = fmaxf(nx, fabsf(xf[i]));
+                }
+                conv = nd <= 0x1p-22f * nx;
+            }
+            if (conv) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) x[i] = xf[i];
+                return true;
+            }
+        }
+    }
+    double M[N * N], v[N], xd[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         v[i] = double(p.v[i]);
 #pragma unroll
         for (int j = 0; j < N; ++j) M[i * N + j] = double(p.P[Sym<N>::at(i, j)]);
     }
-    const bool ok = ms::inv_row_pivot<N, double>(M, Mi);
-    ms::mv<N, double>(Mi, v, xd);
+    // P is symmetric positive definite for an observable model with P0 > 0:
+    // Cholesky (fixed indexing, one reciprocal per column); a non-positive
+    // pivot falls back to Gauss-Jordan with row pivoting
+    double L[N * N], il[N];
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        double d = M[j * N + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fma(-L[j * N + k], L[j * N + k], d);
+        pd = pd && d > 0.0;
+        const double ljj = sqrt(d > 0.0 ? d : 1.0);
+        il[j] = 1.0 / ljj;
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            double s = M[i * N + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = fma(-L[i * N + k], L[j * N + k], s);
+            L[i * N + j] = s * il[j];
+        }
+    }
+    bool ok = true;
+    if (pd) {
+        double z[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = v[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s = fma(-L[i * N + k], z[k], s);
+            z[i] = s * il[i];
+        }
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            double s = z[i];
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) s = fma(-L[k * N + i], xd[k], s);
+            xd[i] = s * il[i];
+        }
+    } else {
+        double Mi[N * N];
+        ok = ms::inv_row_pivot<N, double>(M, Mi);
+        ms::mv<N, double>(Mi, v, xd);
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) x[i] = S(xd[i]);
     return ok;

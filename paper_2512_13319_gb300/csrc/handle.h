@@ -33,6 +33,7 @@ struct map_smoother {
     double* d_grad = nullptr;          // gradient accumulators
     void* d_fold = nullptr;            // linear-fold constants of K steps (linear models)
     int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
+    int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
     double logq = 0.0, logr = 0.0;     // noise scales of the gradient parameters
     // per-phase timing (map_smoother_profile)
     bool profile = false;
@@ -47,8 +48,9 @@ size_t elem_bytes(int prec);
 
 // bytes of the linear-fold constants of an (n, m) linear model in scalars of
 // es bytes: up to 64 steps per thread, 8 tree levels and the thread-prefix
-// tables of up to 128 threads per tile, then the tile tables of nt tiles (the
-// layouts of FoldLayout and TileTables in lti_fold.cuh)
+// tables of up to 128 threads per tile, then the tile tables of nt tiles and,
+// for at most 513 tiles, their products (the layouts of FoldLayout and
+// TileTables in lti_fold.cuh)
 inline size_t fold_bytes(int n, int m, size_t es, long nt)
 {
     auto al = [](size_t x) { return (x + 15) / 16 * 16; };
@@ -58,7 +60,10 @@ inline size_t fold_bytes(int n, int m, size_t es, long nt)
     const int LS = (3 * n * P + 4 * n * n + 3) / 4 * 4;
     const int PS = (n * n + 2 * ns + 3) / 4 * 4;
     const size_t consts = es * (size_t)(oL + 8 * LS + 128 * PS + 128 * 4 * n * n);
-    return al(consts) + sizeof(double) * 24 * 3 * n * n + al(es * nt * ns) + es * nt * n * n;
+    const size_t tiles = al(consts) + sizeof(double) * 24 * 3 * n * n + al(es * nt * ns);
+    const size_t e64 = al(tiles + es * nt * n * n);
+    const size_t pi = al(e64 + sizeof(double) * nt * n * n);
+    return pi + (nt <= 4 * 128 + 1 ? es * (size_t)(nt * (nt + 1) / 2) * n * n : 0);
 }
 
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.

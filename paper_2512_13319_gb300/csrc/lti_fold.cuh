@@ -51,6 +51,17 @@
 //     affine maps v -> E_j^T v + w_j of the tiles before theirs instead of
 //     combining tile totals.
 //
+// (5) Unrolling the tile recursions: with Pi(a, b) = E_a E_{a+1} ... E_{b-1}
+//     (data-independent, a table for scans of at most PI_TILES tiles),
+//       v_j = Pi(0, j)^T v_0 + sum_{i<j} Pi(i+1, j)^T w_i,
+//     and on the RTS side the state at the end of tile j < nt - 1 is
+//       x_end(j) = Pi(j+1, nt-1) x_L + sum_{i=j+1}^{nt-2} Pi(j+1, i) beta_i,
+//     x_L the state at the start of the last tile and beta_i the offset of
+//     full tile i's map (whose linear part is E_i: the composition of a tile's
+//     closed-loop maps is the closed-loop map of its combined element).  Both
+//     are sums of independent terms: a CTA's threads take one term each and
+//     add them up, without a chain of compositions.
+//
 // All constants depend on the model, K, B and the number of tiles only.  The
 // reduce and down-sweep kernels evaluate (1)-(4) with them: 2 N M
 // multiply-adds per step and 4 N^2 per tree node instead of a combine.
@@ -89,7 +100,8 @@ struct FoldLayout {
 // Per-tile tables of item (4), in the fold buffer after FoldLayout::TOTAL
 // (offsets in bytes): the FP64 (A, C, J) of 2^e full tiles (e < ELMAX, full
 // N x N matrices), then P_j (packed, scalars of S) and F_j = E_j^T (N x N
-// row-major) for j < nt.
+// row-major) for j < nt, E_j in FP64, and for scans of at most PI_TILES tiles
+// the products Pi(a, b) of consecutive tiles' closed-loop maps (item (5)).
 template <int N, int M, typename S>
 struct TileTables {
     static constexpr int ELMAX = 24;                        // up to 2^24 tiles
@@ -98,7 +110,16 @@ struct TileTables {
     __host__ __device__ static constexpr size_t tl_off() { return al(sizeof(S) * FoldLayout<N, M, S>::TOTAL); }
     __host__ __device__ static constexpr size_t p_off() { return tl_off() + sizeof(double) * ELMAX * 3 * NN; }
     __host__ __device__ static constexpr size_t f_off(long nt) { return p_off() + al(sizeof(S) * nt * NS); }
-    __host__ __device__ static constexpr size_t bytes(long nt) { return f_off(nt) + sizeof(S) * nt * NN; }
+    // E_j in FP64, then (scans of at most PI_TILES tiles) the products
+    // Pi(a, b) = E_a E_{a+1} ... E_{b-1}, 0 <= a <= b < nt, row a holding b = a..nt-1
+    static constexpr long PI_TILES = 4 * 128 + 1;
+    __host__ __device__ static constexpr size_t e_off(long nt) { return al(f_off(nt) + sizeof(S) * nt * NN); }
+    __host__ __device__ static constexpr size_t pi_off(long nt) { return al(e_off(nt) + sizeof(double) * nt * NN); }
+    __host__ __device__ static constexpr long pi_index(long nt, long a, long b) { return a * nt - a * (a - 1) / 2 + (b - a); }
+    __host__ __device__ static constexpr size_t bytes(long nt)
+    {
+        return pi_off(nt) + (nt <= PI_TILES ? sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN : 0);
+    }
 };
 
 // Tile-level inputs of the linear-fold kernels: the fold constants, the tile
@@ -113,6 +134,7 @@ struct LtiTiles {
     S* w;
     S* gmaps;
     int co_smem;                    // the co table is staged in shared memory (LtiDownSmem)
+    const S* pi;                    // tile-map products (item (5)), or nullptr beyond PI_TILES
 };
 
 // The co table is stored by tree level: level d holds the B / 2^(d+1) right
@@ -497,12 +519,44 @@ k_lti_tiles(const Red<N, double> prior, int nt, int ne, S* __restrict__ out)
     fd::mm(N, w, tl, E);                                   // E_j
     S* tp = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::p_off()) + (long)j * Sym<N>::SZ;
     S* tf = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::f_off(nt)) + (long)j * NN;
+    double* te = reinterpret_cast<double*>(reinterpret_cast<char*>(out) + TT::e_off(nt)) + (long)j * NN;
+#pragma unroll 1
+    for (int q = 0; q < NN; ++q) te[q] = E[q];
 #pragma unroll 1
     for (int a = 0; a < N; ++a) {
 #pragma unroll 1
         for (int c = a; c < N; ++c) tp[Sym<N>::at(a, c)] = S(P[a * N + c]);
 #pragma unroll 1
         for (int c = 0; c < N; ++c) tf[a * N + c] = S(E[c * N + a]);
+    }
+}
+
+// Products of consecutive full tiles' closed-loop maps (item (5)): thread a
+// writes Pi(a, b) = E_a ... E_{b-1} for b = a..nt-1 (Pi(a, a) = I), FP64
+// products rounded to S.  Runs after k_lti_tiles, for nt <= PI_TILES.
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(64)
+k_lti_products(int nt, S* __restrict__ out)
+{
+    using TT = TileTables<N, M, S>;
+    namespace fd = fold_detail;
+    constexpr int NN = N * N;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nt) return;
+    const double* E = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::e_off(nt));
+    S* pi = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::pi_off(nt));
+    double P[NN], Q[NN];
+#pragma unroll 1
+    for (int q = 0; q < NN; ++q) P[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+#pragma unroll 1
+    for (int b = a; b < nt; ++b) {
+        S* o = pi + TT::pi_index(nt, a, b) * NN;
+#pragma unroll 1
+        for (int q = 0; q < NN; ++q) o[q] = S(P[q]);
+        if (b + 1 == nt) break;
+        fd::mm(N, P, E + (long)b * NN, Q);         // Pi(a, b + 1) = Pi(a, b) E_b
+#pragma unroll 1
+        for (int q = 0; q < NN; ++q) P[q] = Q[q];
     }
 }
 

@@ -38,7 +38,7 @@ constexpr int SETUP_IN_DOUBLES = 8 * 8 * 4 + 8 * 5 + 8 * 8 * 2;   // F, L, W, H,
 constexpr int MAX_DEVICES = 64;
 
 __device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
-__device__ __align__(256) unsigned long long g_stats[3];
+__device__ __align__(256) unsigned long long g_stats[4];   // 3 counters + grid barrier state
 __device__ __align__(256) double g_setup_in[SETUP_IN_DOUBLES];
 __device__ __align__(256) mapk::SetupOut g_setup_out;
 

@@ -408,7 +408,7 @@ k_group_totals(const S* __restrict__ tile_agg, int nt, S* __restrict__ group_agg
 // the runs are composed in thread order (block_aff_reduce, leaf 0 outermost).
 // Uses the start of `nodes`; ends with a barrier.
 template <int N, typename S>
-__device__ __forceinline__ void fold_tile_maps(const S* __restrict__ F, int fs, const S* __restrict__ w, int ws,
+__device__ __forceinline__ void fold_tile_maps(const S* __restrict__ F, int fs, const S* w, int ws,
                                                int first_all, int last_all, S* nodes, Aff<N, S>& out)
 {
     const int B = blockDim.x, t = threadIdx.x;
@@ -421,7 +421,7 @@ __device__ __forceinline__ void fold_tile_maps(const S* __restrict__ F, int fs, 
 #pragma unroll
         for (int q = 0; q < N * N; ++q) m.F[q] = __ldg(F + (long)i * fs + q);
 #pragma unroll
-        for (int q = 0; q < N; ++q) m.c[q] = w[(long)i * ws + q];
+        for (int q = 0; q < N; ++q) m.c[q] = w[(long)i * ws + q];   // written by other CTAs: no __ldg
         compose<N, S>(m, H, H);
     }
     block_aff_reduce<N, S>(H, nodes);
@@ -463,6 +463,170 @@ __device__ __forceinline__ void lti_tile_prefix(const LtiTiles<S>& lt, int tile,
     }
 }
 
+// Linear-fold mode: state at the end of tile `tile` (written by thread 0 to
+// xe), the tile maps a_i of the tiles after it composed (earlier map
+// outermost) and applied to x_T.  A full tile's map has F = E_i = F_i^T of the
+// tile tables (the composition of a tile's closed-loop maps is the closed-loop
+// map of its combined element, item (4) of lti_fold.cuh) and its offset in
+// tile_aff; the last (partial) tile's map is read whole from tile_aff.
+// Uses the start of `nodes`; ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void lti_tile_suffix_state(const LtiTiles<S>& lt, const S* tile_aff, int tile, int nt,
+                                                      const S* xT, S* nodes, S* xe)
+{
+    constexpr int NN = N * N, NA = Aff<N, S>::NCOMP;
+    const int B = blockDim.x, t = threadIdx.x;
+    const int cnt = nt - 1 - tile;
+    Aff<N, S> H;
+    set_identity(H);
+    if (cnt > 0) {
+        const int per = (cnt + B - 1) / B;
+        const int first = tile + 1 + min(cnt, t * per), last = min(nt, first + per);
+        for (int i = last - 1; i >= first; --i) {          // H = a_first o ... o a_last
+            Aff<N, S> a;
+            if (i == nt - 1) {
+#pragma unroll
+                for (int c = 0; c < NA; ++c) comp(a, c) = tile_aff[(long)i * NA + c];
+            } else {
+#pragma unroll
+                for (int r = 0; r < N; ++r)
+#pragma unroll
+                    for (int c = 0; c < N; ++c) a.F[r * N + c] = __ldg(lt.F + (long)i * NN + c * N + r);
+#pragma unroll
+                for (int c = 0; c < N; ++c) a.c[c] = tile_aff[(long)i * NA + NN + c];
+            }
+            compose<N, S>(a, H, H);
+        }
+    }
+    block_aff_reduce<N, S>(H, nodes);
+    if (t == 0) {
+        S x[N], y[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = xT[i];
+        affine_apply<N, S>(H, x, y);
+#pragma unroll
+        for (int i = 0; i < N; ++i) xe[i] = y[i];
+    }
+    __syncthreads();
+}
+
+// Sum over the CTA of one N-vector per thread, returned in thread 0.  red:
+// B / 32 * N scalars of shared memory; ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void block_vec_sum(S* v, S* red)
+{
+    const int t = threadIdx.x, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_down_sync(0xffffffffu, v[i], d);
+    if ((t & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[(t >> 5) * N + i] = v[i];
+    __syncthreads();
+    if (t == 0)
+        for (int w = 1; w < nw; ++w)
+#pragma unroll
+            for (int i = 0; i < N; ++i) v[i] += red[w * N + i];
+    __syncthreads();
+}
+
+// Linear-fold mode with the product table (item (5) of lti_fold.cuh): value
+// function before tile `tile` (returned in thread 0), v_tile as a sum of
+// independent terms.  red: B / 32 * N scalars of shared memory.
+template <int N, typename S>
+__device__ __forceinline__ void lti_tile_prefix_sum(const LtiTiles<S>& lt, int tile, int nt, const Red<N, S>& prior,
+                                                    S* red, Red<N, S>& out)
+{
+    using TT = TileTables<N, 1, S>;                     // pi_index does not depend on M
+    constexpr int NN = N * N;
+    const int t = threadIdx.x;
+    if (tile == 0) {
+        out = prior;
+        return;
+    }
+    S v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = S(0);
+    // terms i = t - 1 + u B (i = -1: Pi(0, tile)^T v_0, else Pi(i+1, tile)^T w_i); at
+    // most 5 per thread (tile <= 4B + 1), their loads issued together
+    constexpr int UMAX = 5;
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u) {
+        const int i = t - 1 + u * (int)blockDim.x;
+        if (i < tile) {
+            const S* P = lt.pi + TT::pi_index(nt, i + 1, tile) * NN;
+            S w[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) w[c] = i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
+#pragma unroll
+            for (int r = 0; r < N; ++r)
+#pragma unroll
+                for (int c = 0; c < N; ++c) v[r] = fma(__ldg(P + c * N + r), w[c], v[r]);
+        }
+    }
+    block_vec_sum<N, S>(v, red);
+    if (t == 0) {
+#pragma unroll
+        for (int q = 0; q < Sym<N>::SZ; ++q) out.P[q] = lt.P[(long)tile * Sym<N>::SZ + q];
+#pragma unroll
+        for (int i = 0; i < N; ++i) out.v[i] = v[i];
+    }
+}
+
+// Linear-fold mode with the product table: state at the end of tile `tile`
+// (thread 0 writes it to xe), x_T for the last tile, else
+// Pi(tile+1, nt-1) x_L + sum_{i=tile+1}^{nt-2} Pi(tile+1, i) beta_i with
+// x_L = (last tile's map)(x_T) and beta_i the offset of tile i's map in
+// tile_aff.  red: B / 32 * N scalars; ends with a barrier.
+template <int N, typename S>
+__device__ __forceinline__ void lti_tile_suffix_sum(const LtiTiles<S>& lt, const S* tile_aff, int tile, int nt,
+                                                    const S* xT, S* red, S* xe)
+{
+    using TT = TileTables<N, 1, S>;
+    constexpr int NN = N * N, NA = Aff<N, S>::NCOMP;
+    const int t = threadIdx.x;
+    if (tile + 1 == nt) {
+        if (t == 0)
+#pragma unroll
+            for (int i = 0; i < N; ++i) xe[i] = xT[i];
+        __syncthreads();
+        return;
+    }
+    S v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = S(0);
+    constexpr int UMAX = 5;                             // nt <= 4B + 1: at most 5 terms per thread
+#pragma unroll
+    for (int uu = 0; uu < UMAX; ++uu) {                 // term i: Pi(tile+1, i) beta_i; i = nt-1: x_L
+        const int i = tile + 1 + t + uu * (int)blockDim.x;
+        if (i >= nt) continue;
+        const S* P = lt.pi + TT::pi_index(nt, tile + 1, i) * NN;
+        S u[N];
+        if (i + 1 == nt) {
+            Aff<N, S> a;
+#pragma unroll
+            for (int c = 0; c < NA; ++c) comp(a, c) = tile_aff[(long)i * NA + c];
+            S x[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) x[c] = xT[c];
+            affine_apply<N, S>(a, x, u);
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) u[c] = tile_aff[(long)i * NA + NN + c];
+        }
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[r] = fma(__ldg(P + r * N + c), u[c], v[r]);
+    }
+    block_vec_sum<N, S>(v, red);
+    if (t == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) xe[i] = v[i];
+    __syncthreads();
+}
+
 // Linear-fold mode: composed maps of the groups of prefix_group_tiles(B) full
 // tiles (one CTA per group), for scans with many tiles
 template <int N, typename S>
@@ -501,7 +665,7 @@ __device__ __forceinline__ void tile_suffix_state(const S* __restrict__ tile_aff
     Aff<N, S> H;
     set_identity(H);
     for (int i = last - 1; i >= first; --i) {      // H = a_first o ... o a_last
-        Aff<N, S> a;
+        Aff<N, S> a;                               // written by other CTAs: no __ldg
         aos_load(tile_aff, i, a);
         compose<N, S>(a, H, H);
     }
@@ -786,43 +950,19 @@ k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
     }
 }
 
-// ---------------------------------------------------------------------------
-// phase 2: per-step filter values, closed-loop maps and their per-thread /
-// per-tile compositions; the last CTA writes the value function at x_T
-// ---------------------------------------------------------------------------
-template <int N, typename S, class Prod>
-__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
-              const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
-              S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
-              CombineCtx ctx, const LtiTiles<S> lt, S* __restrict__ final_out, S* __restrict__ xT_out,
-              S* __restrict__ filtT_out, const S* __restrict__ group_agg)
+// The per-step part of the filter down-sweep for one thread: from the value
+// function X before step k0, for each of its K steps (those before T) the
+// filter value (filt_out), the one-variable combine with the step's element,
+// the closed-loop map stored to Eg (compact (V, g) with low-rank noise) and the
+// thread's composite map comp_t (x_{k0} = Phi x_{k0+K} + beta).  row_of(i, k,
+// row) supplies the step's producer inputs.
+template <int N, typename S, class Prod, class RowFn>
+__device__ __forceinline__ void filter_steps(const Prod& prod, int K, long k0, long gthr, Red<N, S>& X,
+                                             S* __restrict__ Eg, S* __restrict__ filt_out, const CombineCtx& ctx,
+                                             Aff<N, S>& comp_t, RowFn row_of)
 {
-    const S* __restrict__ fold = lt.fold;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* nodes = reinterpret_cast<S*>(smem_raw);
-    const int B = blockDim.x, t = threadIdx.x;
-    const int tile = down_tile();
-    const long gthr = (long)tile * B + t;
-    const long k0 = gthr * K;
     const long T = prod.T;
     constexpr int NA = Aff<N, S>::NCOMP;
-
-    const bool last_lti = fold && tile + 1 == (int)gridDim.x;
-    S leaf[2 * N] = {};
-    if constexpr (Prod::LINEAR_FOLD && N <= 6)
-        if (fold) lti_stage_tables<N, Prod::W, S>(lt, K, nodes);
-    if (last_lti) lti_last_tile_leaf<N, S>(prod, tile, K, fold, nodes, leaf);
-    pdl_wait();                            // totals and aggregates of the reduce kernel
-    pdl_trigger();
-    Red<N, S> pin, X;
-    if (fold)
-        lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
-    else
-        tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
-    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, lt, last_lti, leaf, nodes, ctx, X);
-
-    Aff<N, S> comp_t;
     set_identity(comp_t);
     // compact closed-loop maps: (V, g) instead of (E, g) when E = A - Gam V
     constexpr int NAC = ((N + 1) / 2) * N + N;
@@ -839,7 +979,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                     filt_out[k * Red<N, S>::NCOMP + c] = comp(X, c);
             }
             S row[Prod::W];
-            prod.load1(k, row);
+            row_of(i, k, row);
             Elem<N, S> e;
             prod.make(k, row, e);
             Aff<N, S> a;
@@ -897,6 +1037,46 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
             for (int j = 0; j < N * N; ++j) comp_t.F[j] = F2[j];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// phase 2: per-step filter values, closed-loop maps and their per-thread /
+// per-tile compositions; the last CTA writes the value function at x_T
+// ---------------------------------------------------------------------------
+template <int N, typename S, class Prod>
+__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
+k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
+              const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
+              S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
+              CombineCtx ctx, const LtiTiles<S> lt, S* __restrict__ final_out, S* __restrict__ xT_out,
+              S* __restrict__ filtT_out, const S* __restrict__ group_agg)
+{
+    const S* __restrict__ fold = lt.fold;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
+    const int B = blockDim.x, t = threadIdx.x;
+    const int tile = down_tile();
+    const long gthr = (long)tile * B + t;
+    const long k0 = gthr * K;
+    const long T = prod.T;
+
+    const bool last_lti = fold && tile + 1 == (int)gridDim.x;
+    S leaf[2 * N] = {};
+    if constexpr (Prod::LINEAR_FOLD && N <= 6)
+        if (fold) lti_stage_tables<N, Prod::W, S>(lt, K, nodes);
+    if (last_lti) lti_last_tile_leaf<N, S>(prod, tile, K, fold, nodes, leaf);
+    pdl_wait();                            // totals and aggregates of the reduce kernel
+    pdl_trigger();
+    Red<N, S> pin, X;
+    if (fold)
+        lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
+    else
+        tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
+    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, lt, last_lti, leaf, nodes, ctx, X);
+
+    Aff<N, S> comp_t;
+    filter_steps<N, S>(prod, K, k0, gthr, X, Eg, filt_out, ctx, comp_t,
+                       [&](int, long k, S* row) { prod.load1(k, row); });
     write_final_if_last<N, S>(T, tile, K, X, final_out, xT_out, filtT_out, ctx);
     wi_store(thr_aff, gthr, comp_t);
     __syncthreads();                       // the filter trees are done with shared memory
@@ -1126,31 +1306,15 @@ struct EgForm {
     S Gam[N * R];
 };
 
+// The per-step part of the RTS pass for one thread: from the state x at the
+// end of its steps, x_k = E_k x_{k+1} + g_k for its steps before T, backwards,
+// each state staged at mine[i N] (the maps are loaded four steps ahead).
 template <int N, typename S>
-__global__ void __launch_bounds__(128)
-k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const S* __restrict__ tile_aff,
-           const S* __restrict__ xT, long T, S* __restrict__ x_out, const __grid_constant__ EgForm<N, S> form)
+__device__ __forceinline__ void rts_steps(const S* __restrict__ Eg, int K, long k0, long gthr, long T,
+                                          const EgForm<N, S>& form, S* x, S* mine)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* nodes = reinterpret_cast<S*>(smem_raw);
-    const int B = blockDim.x, t = threadIdx.x;
-    const long gthr = (long)blockIdx.x * B + t;
-    const long k0 = gthr * K;
     constexpr int NA = Aff<N, S>::NCOMP;
     constexpr int U = 4;                   // steps whose maps are loaded ahead of use
-    pdl_wait();                            // maps and x_T of the previous kernel
-    S* xe_sh = nodes + 2 * B * CoopLayout<N, S>::NA;   // staging area, free until the state loop
-    tile_suffix_state<N, S>(tile_aff, blockIdx.x, gridDim.x, xT, nodes, xe_sh);
-    S x[N];
-    {
-        Aff<N, S> a;
-        wi_load(thr_aff, gthr, a);
-        block_aff_end_states<N, S>(a, xe_sh, nodes, x);
-    }
-    // the states are staged past the affine tree and written out coalesced
-    const int SP = rts_stage_stride(K, N);
-    S* st = nodes + 2 * B * CoopLayout<N, S>::NA;
-    S* mine = st + t * SP;
     if (form.compact) {
         // x_k = A x_{k+1} - Gam (V_k x_{k+1}) + g_k
         constexpr int R = EgForm<N, S>::R, NAC = R * N + N;
@@ -1227,6 +1391,32 @@ k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const
             }
         }
     }
+}
+
+template <int N, typename S>
+__global__ void __launch_bounds__(128)
+k_rts_down(const S* __restrict__ Eg, int K, const S* __restrict__ thr_aff, const S* __restrict__ tile_aff,
+           const S* __restrict__ xT, long T, S* __restrict__ x_out, const __grid_constant__ EgForm<N, S> form)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* nodes = reinterpret_cast<S*>(smem_raw);
+    const int B = blockDim.x, t = threadIdx.x;
+    const long gthr = (long)blockIdx.x * B + t;
+    const long k0 = gthr * K;
+    pdl_wait();                            // maps and x_T of the previous kernel
+    S* xe_sh = nodes + 2 * B * CoopLayout<N, S>::NA;   // staging area, free until the state loop
+    tile_suffix_state<N, S>(tile_aff, blockIdx.x, gridDim.x, xT, nodes, xe_sh);
+    S x[N];
+    {
+        Aff<N, S> a;
+        wi_load(thr_aff, gthr, a);
+        block_aff_end_states<N, S>(a, xe_sh, nodes, x);
+    }
+    // the states are staged past the affine tree and written out coalesced
+    const int SP = rts_stage_stride(K, N);
+    S* st = nodes + 2 * B * CoopLayout<N, S>::NA;
+    S* mine = st + t * SP;
+    rts_steps<N, S>(Eg, K, k0, gthr, T, form, x, mine);
     __syncthreads();
     // the staged block is the tile's block of x_out (x_T itself comes from the
     // filter kernel): one bulk copy of its 16-byte part, the rest by plain stores
@@ -1251,6 +1441,244 @@ template <int N, typename S>
 __host__ __device__ constexpr size_t rts_smem(int B, int K)
 {
     return aff_tree_smem<N, S>(B) + sizeof(S) * (size_t)B * rts_stage_stride(K, N);
+}
+
+// ---------------------------------------------------------------------------
+// single-launch solve of a linear time-invariant model (RTS smoother): the
+// reduce, filter down-sweep and RTS phases of the three-kernel path in one
+// cooperative launch of one CTA per tile, separated by two grid barriers
+// ---------------------------------------------------------------------------
+// Grid barrier state in global memory: arrivals and generation (both start at
+// zero; the last arrival resets the count before it advances the generation).
+struct GridSync {
+    unsigned int* count;
+    unsigned int* gen;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned int* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr int GRID_SPINS = 1 << 24;         // bounded wait (about a second with the back-off)
+
+// All CTAs of the (co-resident) grid reach this point; the global writes of
+// each CTA before it are visible to all after it.  A wait that runs out counts
+// in stats[2] and lets the CTA continue.
+__device__ __forceinline__ void grid_sync(const GridSync& gs, unsigned long long* stats)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = ld_acquire_u32(gs.gen);
+        __threadfence();
+        if (atomicAdd(gs.count, 1u) == gridDim.x - 1) {
+            atomicExch(gs.count, 0u);
+            __threadfence();
+            atomicAdd(gs.gen, 1u);
+        } else {
+            int n = 0;
+            while (ld_acquire_u32(gs.gen) == g) {
+                if (++n > GRID_SPINS) {
+                    if (stats) atomicAdd(stats + 2, 1ull);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// shared memory of k_lti_solve (offsets in scalars): the (b, eta) nodes and
+// the tile's prefix, the composition area of the shuffle reductions, the
+// tile's observations (bulk copy), the Gamma_i, the bulk copy's mbarrier, the
+// level constants and the co table; the RTS phase stages the states from 0.
+template <int N, int M, typename S>
+struct FusedSmem {
+    using FL = FoldLayout<N, M, S>;
+    __host__ __device__ static constexpr int al(int x) { return (x + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int lb(int B) { return B >= 128 ? 7 : B >= 64 ? 6 : B >= 32 ? 5 : 4; }
+    __host__ __device__ static constexpr int bq(int) { return 0; }
+    __host__ __device__ static constexpr int pin(int B) { return 2 * B * 2 * N; }
+    __host__ __device__ static constexpr int red(int B) { return al(pin(B) + CoopLayout<N, S>::NR); }
+    __host__ __device__ static constexpr int ys(int B) { return al(red(B) + (B / 32) * (Aff<N, S>::NCOMP + N) + N); }
+    __host__ __device__ static constexpr int gam(int B, int K) { return al(ys(B) + B * K * M); }
+    __host__ __device__ static constexpr int bar(int B, int K) { return al(gam(B, K) + K * FL::GS); }
+    __host__ __device__ static constexpr int lv(int B, int K) { return bar(B, K) + 4; }
+    __host__ __device__ static constexpr int co(int B, int K) { return lv(B, K) + al(lb(B) * FL::LS); }
+    __host__ __device__ static constexpr int end(int B, int K) { return co(B, K) + B * FL::CS; }
+    __host__ __device__ static constexpr int stage(int B) { return al((B / 32) * (Aff<N, S>::NCOMP + N) + N); }
+    __host__ __device__ static constexpr size_t bytes(int B, int K)
+    {
+        const int e = end(B, K), r = stage(B) + B * K * N;
+        return sizeof(S) * (size_t)(e > r ? e : r);
+    }
+};
+
+template <int N, typename S, class Prod>
+__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
+k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, const Red<N, S> prior,
+            S* __restrict__ Eg, S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx,
+            S* __restrict__ final_out, S* __restrict__ x_out, S* __restrict__ filtT_out,
+            const __grid_constant__ EgForm<N, S> form, const GridSync gs)
+{
+    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
+        constexpr int M = Prod::W;
+        using FL = FoldLayout<N, M, S>;
+        using FS = FusedSmem<N, M, S>;
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        S* sm = reinterpret_cast<S*>(smem_raw);
+        const int B = blockDim.x, t = threadIdx.x;
+        const int tile = blockIdx.x;
+        const long gthr = (long)tile * B + t;
+        const long k0 = gthr * K;
+        const long T = prod.T;
+        const bool last = tile + 1 == (int)gridDim.x;
+        const S* fold = lt.fold;
+        S* bq = sm + FS::bq(B);
+        S* ps = sm + FS::pin(B);
+        S* red = sm + FS::red(B);
+        S* ys = sm + FS::ys(B);
+        S* gam = sm + FS::gam(B, K);
+        S* lv = sm + FS::lv(B, K);
+        S* co = sm + FS::co(B, K);
+        unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + FS::bar(B, K));
+
+        // ---- phase 1: the tile's observations, per-thread folds, up-sweep, w_j
+        const unsigned ybytes = (unsigned)(sizeof(S) * (size_t)B * K * M);
+        if (!last) {
+            if (t == 0) mbar_init(bar, 1);
+            __syncthreads();
+            if (t == 0) {
+                mbar_arrive_expect_tx(bar, ybytes);
+                bulk_copy_g2s(ys, prod.y + (long)tile * B * K * M, ybytes, bar);
+            }
+        }
+        {   // level constants and co (lti_stage_tables layout, here at FS offsets), Gamma_i
+            using V = typename std::conditional<sizeof(S) == 4, float4, double2>::type;
+            constexpr int W = 16 / sizeof(S);
+            const int LB = ilog2(B);
+            const V* src = reinterpret_cast<const V*>(fold + FL::oL);
+            V* dst = reinterpret_cast<V*>(lv);
+            for (int q = t; q < (LB * FL::LS) / W; q += B) dst[q] = src[q];
+            src = reinterpret_cast<const V*>(fold + FL::oCo);
+            dst = reinterpret_cast<V*>(co);
+            for (int q = t; q < ((B - 1) * FL::CS) / W; q += B) dst[q] = src[q];
+            for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
+        }
+        if (last) {                                // the last tile's observations up to T, zeros after
+            const long base = (long)tile * B * K * M, have = T * M - base;
+            for (long q = t; q < (long)B * K * M; q += B) ys[q] = q < have ? prod.y[base + q] : S(0);
+        }
+        bool ok = true;
+        if (!last) ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
+        if (!__syncthreads_and(ok)) {
+            if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
+            mbar_wait_bounded(bar, 0, MBAR_POLLS);  // the copy may still be in flight
+        }
+        S leaf[2 * N];
+        if (!last || k0 + K <= T) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) { leaf[q] = __ldg(fold + FL::ob + q); leaf[N + q] = __ldg(fold + FL::oe + q); }
+            const S* yt = ys + t * K * M;
+#pragma unroll 2
+            for (int i = 0; i < K; ++i) {
+                const S* gi = gam + i * FL::GS;
+#pragma unroll
+                for (int a = 0; a < N; ++a)
+#pragma unroll
+                    for (int c = 0; c < M; ++c) {
+                        leaf[a] = fma(gi[a * M + c], yt[i * M + c], leaf[a]);
+                        leaf[N + a] = fma(gi[(N + a) * M + c], yt[i * M + c], leaf[N + a]);
+                    }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2 * N; ++c) leaf[c] = S(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 2 * N; ++c) bq[c * B + t] = leaf[c];
+        lti_tree_up<N, M, S>(bq, lv);              // starts and ends with a barrier
+        if (!last && t == 0) {
+            const S* rq = bq + lti_node_level(2 * N, B, ilog2(B));
+            const long j = tile;
+            S Pb[N];
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                S acc = S(0);
+#pragma unroll
+                for (int c = 0; c < N; ++c) acc = fma(lt.P[j * Sym<N>::SZ + Sym<N>::at(a, c)], rq[c], acc);
+                Pb[a] = acc;
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                S acc = rq[N + a];
+#pragma unroll
+                for (int c = 0; c < N; ++c) acc = fma(-lt.F[j * N * N + a * N + c], Pb[c], acc);
+                lt.w[j * N + a] = acc;
+            }
+        }
+        grid_sync(gs, ctx.stats);
+
+        // ---- phase 2: tile prefix, thread prefixes, per-step filter, tile map
+        Red<N, S> pin, X;
+        lti_tile_prefix_sum<N, S>(lt, tile, gridDim.x, prior, red, pin);
+        if (t == 0) node_store(pin, ps);
+        lti_tree_down_linear<N, M, S>(bq, co);     // starts and ends with a barrier
+        {
+            Red<N, S> P;
+            node_load(ps, P);
+            S dl[2 * N];
+#pragma unroll
+            for (int c = 0; c < 2 * N; ++c) dl[c] = bq[c * B + t];
+            if (k0 < T)
+                lti_thread_value<N, M, S>(fold, dl, P, ctx, X);
+            else
+                X = P;
+        }
+        Aff<N, S> comp_t;
+        const S* yt = ys + t * K * M;
+        filter_steps<N, S>(prod, K, k0, gthr, X, Eg, filt_out, ctx, comp_t, [&](int i, long, S* row) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) row[c] = yt[i * M + c];
+        });
+        S* xT = x_out + T * N;
+        write_final_if_last<N, S>(T, tile, K, X, final_out, xT, filtT_out, ctx);
+        {
+            Aff<N, S> H = comp_t;
+            __syncthreads();                       // the trees are done with shared memory
+            block_aff_reduce<N, S>(H, red);
+            if (t == 0) aos_store(tile_aff, (long)tile, H);
+        }
+        grid_sync(gs, ctx.stats);
+
+        // ---- phase 3: tile suffix, thread end states, per-step states, bulk store
+        S* st = sm + FS::stage(B);
+        S* xe_sh = red + (B / 32) * (Aff<N, S>::NCOMP + N);
+        lti_tile_suffix_sum<N, S>(lt, tile_aff, tile, gridDim.x, xT, red, xe_sh);
+        S x[N];
+        block_aff_end_states<N, S>(comp_t, xe_sh, red, x);
+        S* mine = st + t * rts_stage_stride(K, N);
+        rts_steps<N, S>(Eg, K, k0, gthr, T, form, x, mine);
+        __syncthreads();
+        const int KN = K * N;
+        const long base = (long)tile * B * KN;
+        const long cnt = min((long)B * KN, T * N - base);
+        long done = 0;
+        if ((reinterpret_cast<uintptr_t>(x_out + base) & 15) == 0) {
+            done = cnt * (long)sizeof(S) / 16 * 16 / (long)sizeof(S);
+            if (t == 0 && done > 0) {
+                fence_proxy_async_smem();
+                bulk_copy_s2g(x_out + base, st, (unsigned)(done * sizeof(S)));
+                bulk_commit_and_wait();
+            }
+        }
+        for (long idx = done + t; idx < cnt; idx += B) x_out[base + idx] = st[idx];
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -57,17 +57,17 @@ MS_DEV void mm(const S* a, const S* b, S* c)
                 c[i * N + j] = s.x;
                 c[i * N + j + 1] = s.y;
             }
-        return;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                S s = a[i * N] * b[j];
+#pragma unroll
+                for (int k = 1; k < N; ++k) s = fma(a[i * N + k], b[k * N + j], s);
+                c[i * N + j] = s;
+            }
     }
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            S s = a[i * N] * b[j];
-#pragma unroll
-            for (int k = 1; k < N; ++k) s = fma(a[i * N + k], b[k * N + j], s);
-            c[i * N + j] = s;
-        }
 }
 
 // c = a S  (S packed symmetric)
@@ -103,17 +103,17 @@ MS_DEV void sym_m(const S* sp, const S* a, S* c)
                 c[i * N + j] = s.x;
                 c[i * N + j + 1] = s.y;
             }
-        return;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                S s = sp[Sym<N>::at(i, 0)] * a[j];
+#pragma unroll
+                for (int k = 1; k < N; ++k) s = fma(sp[Sym<N>::at(i, k)], a[k * N + j], s);
+                c[i * N + j] = s;
+            }
     }
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            S s = sp[Sym<N>::at(i, 0)] * a[j];
-#pragma unroll
-            for (int k = 1; k < N; ++k) s = fma(sp[Sym<N>::at(i, k)], a[k * N + j], s);
-            c[i * N + j] = s;
-        }
 }
 
 // c = S1 S2 (both packed symmetric), general result
@@ -164,17 +164,17 @@ MS_DEV void sym_atb_add(const S* a, const S* b, const S* add, S* out)
                 if (j >= i) out[Sym<N>::at(i, j)] = s.x;
                 out[Sym<N>::at(i, j + 1)] = s.y;
             }
-        return;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = i; j < N; ++j) {
+                S s = add[Sym<N>::at(i, j)];
+#pragma unroll
+                for (int k = 0; k < N; ++k) s = fma(a[k * N + i], b[k * N + j], s);
+                out[Sym<N>::at(i, j)] = s;
+            }
     }
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = i; j < N; ++j) {
-            S s = add[Sym<N>::at(i, j)];
-#pragma unroll
-            for (int k = 0; k < N; ++k) s = fma(a[k * N + i], b[k * N + j], s);
-            out[Sym<N>::at(i, j)] = s;
-        }
 }
 
 // y = a x
@@ -204,14 +204,14 @@ MS_DEV void mtv_add(const S* a, const S* x, const S* add, S* y)
             y[i] = s.x;
             y[i + 1] = s.y;
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        S s = add[i];
+        for (int i = 0; i < N; ++i) {
+            S s = add[i];
 #pragma unroll
-        for (int k = 0; k < N; ++k) s = fma(a[k * N + i], x[k], s);
-        y[i] = s;
+            for (int k = 0; k < N; ++k) s = fma(a[k * N + i], x[k], s);
+            y[i] = s;
+        }
     }
 }
 

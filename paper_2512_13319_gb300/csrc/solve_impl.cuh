@@ -148,6 +148,7 @@ LtiTiles<S> lti_tiles_of(const map_smoother& h, const S* fold, S* w, S* gmaps)
             lt.F = reinterpret_cast<const S*>(base + TT::f_off(h.nt));
             lt.w = w;
             lt.gmaps = gmaps;
+            lt.pi = h.nt <= TT::PI_TILES ? reinterpret_cast<const S*>(base + TT::pi_off(h.nt)) : nullptr;
             // the co table goes to shared memory when three CTAs per SM still fit
             lt.co_smem = LtiDownSmem<N, Prod::W, S>::bytes(h.B, h.K, true) <= 72 * 1024;
         }
@@ -158,7 +159,9 @@ LtiTiles<S> lti_tiles_of(const map_smoother& h, const S* fold, S* w, S* gmaps)
 // closed-loop maps; the last CTA writes x_T), RTS pass (each CTA composes the
 // maps after its tile, then the per-step states).  With linear-fold constants
 // (fold != nullptr) the reduce kernel covers the full tiles 0..nt-2 on (b, eta)
-// parts and the down-sweep's last CTA folds the last tile itself.
+// parts and the down-sweep's last CTA folds the last tile itself; when all
+// tiles fit on the GPU at once the three phases run as one cooperative launch
+// (k_lti_solve).
 template <int N, typename S, class Prod>
 map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cudaStream_t st,
                    bool dev_prior = false, const S* fold = nullptr)
@@ -208,8 +211,49 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     const int ng = (lti ? nt - 1 : nt) > G ? (nt + G - 1) / G : 0;
     S* group_agg = ng ? reinterpret_cast<S*>(h.ws + L.group_agg) : nullptr;
     const LtiTiles<S> lt = lti_tiles_of<N, S, Prod>(h, fold, tile_agg, group_agg);
-    if constexpr (Prod::LINEAR_FOLD && N <= 6)
+    EgForm<N, S> form{};                     // how the filter stores the closed-loop maps
+    if constexpr (Prod::LOWRANK && !Prod::RESETS) {
+        form.compact = prod.p.lowrank;
+        for (int i = 0; i < N * N; ++i) form.A[i] = prod.p.A[i];
+        for (int i = 0; i < N * EgForm<N, S>::R; ++i) form.Gam[i] = prod.p.Gam[i];
+    }
+    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
         if (lti) sh_down = LtiDownSmem<N, Prod::W, S>::bytes(B, K, lt.co_smem);
+        // single cooperative launch when every tile's CTA can be resident at once
+        // (one group of tiles, 16-byte aligned observations, no per-phase events)
+        if (lti && lt.pi && !dev_prior && !h.profile && nt > 1 && nt - 1 <= G &&
+            (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0) {
+            const size_t sh = FusedSmem<N, Prod::W, S>::bytes(B, K);
+            if (h.fused < 0) {
+                int nb = 0, sms = 0;
+                h.fused = allow_smem(k_lti_solve<N, S, Prod>, sh) == cudaSuccess &&
+                          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lti_solve<N, S, Prod>, B, sh) ==
+                              cudaSuccess &&
+                          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device) == cudaSuccess &&
+                          (long)nb * sms >= nt;
+                cudaGetLastError();
+            }
+            if (h.fused == 1) {
+                unsigned int* gw = reinterpret_cast<unsigned int*>(h.d_stats + 3);
+                const GridSync gs{gw, gw + 1};
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(nt);
+                cfg.blockDim = dim3(B);
+                cfg.dynamicSmemBytes = sh;
+                cfg.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                cudaLaunchKernelEx(&cfg, k_lti_solve<N, S, Prod>, prod, K, lt, prior_of<N, S>(h), Eg, tile_aff,
+                                   filt_out, ctx, fin, x_out, filtT, form, gs);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+                return MAP_OK;
+            }
+        }
+    }
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx);
         first = false;
@@ -240,12 +284,6 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
            prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, lt, fin, xT, filtT,
            (const S*)group_agg);
     mark();
-    EgForm<N, S> form{};                     // how k_filter_down stored the closed-loop maps
-    if constexpr (Prod::LOWRANK && !Prod::RESETS) {
-        form.compact = prod.p.lowrank;
-        for (int i = 0; i < N * N; ++i) form.A[i] = prod.p.A[i];
-        for (int i = 0; i < N * EgForm<N, S>::R; ++i) form.Gam[i] = prod.p.Gam[i];
-    }
     launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
            (const S*)xT, T, x_out, form);
     mark();
@@ -394,6 +432,8 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
                                                     static_cast<S*>(h.d_fold));
         k_lti_tiles<N, M, S><<<(h.nt + 63) / 64, 64, 0, st>>>(prior_of<N, double>(h), h.nt, ne,
                                                              static_cast<S*>(h.d_fold));
+        if (h.nt <= TT::PI_TILES)
+            k_lti_products<N, M, S><<<(h.nt + 63) / 64, 64, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
         h.fold_K = h.K;
