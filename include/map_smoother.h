@@ -201,6 +201,15 @@ map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int
 map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* tiles);
 
 /*
+ * Kernels launched by the handle's last solve (host-side read): 1 when the
+ * linear time-invariant RTS solve ran as one cooperative launch (all tiles'
+ * CTAs resident at once), otherwise the number of kernels of the scan
+ * pipeline (plan-time constant kernels not counted); 0 before the first solve.
+ * Returns MAP_ERR_INVALID_ARG for a NULL argument.
+ */
+map_status map_smoother_launches(const map_smoother* h, int* kernels);
+
+/*
  * Allocation-free solve (no counterpart in the paper; a deployment entry point).
  * For callers that cannot call cudaMalloc at all, e.g. code running where the
  * device-memory budget is fixed up front (a real-time tracking loop, an

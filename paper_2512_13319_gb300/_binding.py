@@ -52,6 +52,7 @@ EXPORTS = {
     "map_smoother_profile": (_I, [_VP, _I]),
     "map_smoother_phase_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(_I)]),
     "map_smoother_geometry": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "map_smoother_launches": (_I, [_VP, ctypes.POINTER(_I)]),
     "map_smoother_destroy": (None, [_VP]),
     "map_smoother_last_error": (_CH, [_VP]),
     "map_smoother_supported": (_I, [_I, _I, _I, _I]),
@@ -169,6 +170,13 @@ def map_smoother_geometry(h):
     K, Bt, nt = _I(), _I(), _I()
     _check(load().map_smoother_geometry(h, ctypes.byref(K), ctypes.byref(Bt), ctypes.byref(nt)), h)
     return K.value, Bt.value, nt.value
+
+
+def map_smoother_launches(h):
+    """Kernels launched by the handle's last solve."""
+    n = _I()
+    _check(load().map_smoother_launches(h, ctypes.byref(n)), h)
+    return n.value
 
 
 def map_smoother_phase_times(h):

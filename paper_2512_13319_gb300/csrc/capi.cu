@@ -328,6 +328,7 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
         return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
+    h->launches = 0;
     map_status s = ops->solve(*h, y, x_out, filt_out, st);
     if (s != MAP_OK) return s;
     if (cost_out) {
@@ -427,6 +428,13 @@ map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* til
     *K = h->K;
     *B = h->B;
     *tiles = h->nt;
+    return MAP_OK;
+}
+
+map_status map_smoother_launches(const map_smoother* h, int* kernels)
+{
+    if (!h || !kernels) return MAP_ERR_INVALID_ARG;
+    *kernels = h->launches;
     return MAP_OK;
 }
 

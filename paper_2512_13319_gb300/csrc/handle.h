@@ -34,6 +34,7 @@ struct map_smoother {
     void* d_fold = nullptr;            // linear-fold constants of K steps (linear models)
     int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
     int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
+    int launches = 0;                  // kernels of the last solve
     double logq = 0.0, logr = 0.0;     // noise scales of the gradient parameters
     // per-phase timing (map_smoother_profile)
     bool profile = false;
@@ -63,7 +64,7 @@ inline size_t fold_bytes(int n, int m, size_t es, long nt)
     const size_t tiles = al(consts) + sizeof(double) * 24 * 3 * n * n + al(es * nt * ns);
     const size_t e64 = al(tiles + es * nt * n * n);
     const size_t pi = al(e64 + sizeof(double) * nt * n * n);
-    return pi + (nt <= 4 * 128 + 1 ? es * (size_t)(nt * (nt + 1) / 2) * n * n : 0);
+    return pi + (nt <= 4 * 128 + 1 ? 2 * es * (size_t)(nt * (nt + 1) / 2) * n * n : 0);
 }
 
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.

@@ -101,7 +101,8 @@ struct FoldLayout {
 // (offsets in bytes): the FP64 (A, C, J) of 2^e full tiles (e < ELMAX, full
 // N x N matrices), then P_j (packed, scalars of S) and F_j = E_j^T (N x N
 // row-major) for j < nt, E_j in FP64, and for scans of at most PI_TILES tiles
-// the products Pi(a, b) of consecutive tiles' closed-loop maps (item (5)).
+// the products Pi(a, b) of consecutive tiles' closed-loop maps (item (5)) by
+// rows (a) and their transposes by columns (b).
 template <int N, int M, typename S>
 struct TileTables {
     static constexpr int ELMAX = 24;                        // up to 2^24 tiles
@@ -116,9 +117,12 @@ struct TileTables {
     __host__ __device__ static constexpr size_t e_off(long nt) { return al(f_off(nt) + sizeof(S) * nt * NN); }
     __host__ __device__ static constexpr size_t pi_off(long nt) { return al(e_off(nt) + sizeof(double) * nt * NN); }
     __host__ __device__ static constexpr long pi_index(long nt, long a, long b) { return a * nt - a * (a - 1) / 2 + (b - a); }
+    // then the transposes Q(b, a) = Pi(a, b)^T, row b holding a = 0..b
+    __host__ __device__ static constexpr size_t qt_off(long nt) { return pi_off(nt) + sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN; }
+    __host__ __device__ static constexpr long qt_index(long b, long a) { return b * (b + 1) / 2 + a; }
     __host__ __device__ static constexpr size_t bytes(long nt)
     {
-        return pi_off(nt) + (nt <= PI_TILES ? sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN : 0);
+        return pi_off(nt) + (nt <= PI_TILES ? 2 * sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN : 0);
     }
 };
 
@@ -135,6 +139,7 @@ struct LtiTiles {
     S* gmaps;
     int co_smem;                    // the co table is staged in shared memory (LtiDownSmem)
     const S* pi;                    // tile-map products (item (5)), or nullptr beyond PI_TILES
+    const S* qt;                    // their transposes by column (item (5))
 };
 
 // The co table is stored by tree level: level d holds the B / 2^(d+1) right
@@ -545,14 +550,19 @@ k_lti_products(int nt, S* __restrict__ out)
     if (a >= nt) return;
     const double* E = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::e_off(nt));
     S* pi = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::pi_off(nt));
+    S* qt = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::qt_off(nt));
     double P[NN], Q[NN];
 #pragma unroll 1
     for (int q = 0; q < NN; ++q) P[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
 #pragma unroll 1
     for (int b = a; b < nt; ++b) {
         S* o = pi + TT::pi_index(nt, a, b) * NN;
+        S* ot = qt + TT::qt_index(b, a) * NN;
 #pragma unroll 1
-        for (int q = 0; q < NN; ++q) o[q] = S(P[q]);
+        for (int q = 0; q < NN; ++q) {
+            o[q] = S(P[q]);
+            ot[q] = S(P[(q % N) * N + q / N]);
+        }
         if (b + 1 == nt) break;
         fd::mm(N, P, E + (long)b * NN, Q);         // Pi(a, b + 1) = Pi(a, b) E_b
 #pragma unroll 1

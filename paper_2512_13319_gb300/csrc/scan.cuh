@@ -555,14 +555,14 @@ __device__ __forceinline__ void lti_tile_prefix_sum(const LtiTiles<S>& lt, int t
     for (int u = 0; u < UMAX; ++u) {
         const int i = t - 1 + u * (int)blockDim.x;
         if (i < tile) {
-            const S* P = lt.pi + TT::pi_index(nt, i + 1, tile) * NN;
+            const S* Q = lt.qt + TT::qt_index(tile, i + 1) * NN;   // Pi(i+1, tile)^T, row tile of the transposes
             S w[N];
 #pragma unroll
             for (int c = 0; c < N; ++c) w[c] = i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
 #pragma unroll
             for (int r = 0; r < N; ++r)
 #pragma unroll
-                for (int c = 0; c < N; ++c) v[r] = fma(__ldg(P + c * N + r), w[c], v[r]);
+                for (int c = 0; c < N; ++c) v[r] = fma(__ldg(Q + r * N + c), w[c], v[r]);
         }
     }
     block_vec_sum<N, S>(v, red);
@@ -1504,13 +1504,19 @@ struct FusedSmem {
     __host__ __device__ static constexpr int bq(int) { return 0; }
     __host__ __device__ static constexpr int pin(int B) { return 2 * B * 2 * N; }
     __host__ __device__ static constexpr int red(int B) { return al(pin(B) + CoopLayout<N, S>::NR); }
-    __host__ __device__ static constexpr int ys(int B) { return al(red(B) + (B / 32) * (Aff<N, S>::NCOMP + N) + N); }
+    // the composition area also holds P_j and F_j during the first phase
+    __host__ __device__ static constexpr int red_size(int B)
+    {
+        return (B / 32) * (Aff<N, S>::NCOMP + N) + N > Sym<N>::SZ + N * N ? (B / 32) * (Aff<N, S>::NCOMP + N) + N
+                                                                          : Sym<N>::SZ + N * N;
+    }
+    __host__ __device__ static constexpr int ys(int B) { return al(red(B) + red_size(B)); }
     __host__ __device__ static constexpr int gam(int B, int K) { return al(ys(B) + B * K * M); }
     __host__ __device__ static constexpr int bar(int B, int K) { return al(gam(B, K) + K * FL::GS); }
     __host__ __device__ static constexpr int lv(int B, int K) { return bar(B, K) + 4; }
     __host__ __device__ static constexpr int co(int B, int K) { return lv(B, K) + al(lb(B) * FL::LS); }
     __host__ __device__ static constexpr int end(int B, int K) { return co(B, K) + B * FL::CS; }
-    __host__ __device__ static constexpr int stage(int B) { return al((B / 32) * (Aff<N, S>::NCOMP + N) + N); }
+    __host__ __device__ static constexpr int stage(int B) { return al(red_size(B)); }
     __host__ __device__ static constexpr size_t bytes(int B, int K)
     {
         const int e = end(B, K), r = stage(B) + B * K * N;
@@ -1568,6 +1574,10 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
             dst = reinterpret_cast<V*>(co);
             for (int q = t; q < ((B - 1) * FL::CS) / W; q += B) dst[q] = src[q];
             for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
+            if (!last) {                           // P_j and F_j for w_j, in the composition area
+                for (int q = t; q < Sym<N>::SZ; q += B) red[q] = lt.P[(long)tile * Sym<N>::SZ + q];
+                for (int q = t; q < N * N; q += B) red[Sym<N>::SZ + q] = lt.F[(long)tile * N * N + q];
+            }
         }
         if (last) {                                // the last tile's observations up to T, zeros after
             const long base = (long)tile * B * K * M, have = T * M - base;
@@ -1602,7 +1612,7 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
 #pragma unroll
         for (int c = 0; c < 2 * N; ++c) bq[c * B + t] = leaf[c];
         lti_tree_up<N, M, S>(bq, lv);              // starts and ends with a barrier
-        if (!last && t == 0) {
+        if (!last && t == 0) {                     // w_j = eta_j - F_j P_j b_j
             const S* rq = bq + lti_node_level(2 * N, B, ilog2(B));
             const long j = tile;
             S Pb[N];
@@ -1610,14 +1620,14 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
             for (int a = 0; a < N; ++a) {
                 S acc = S(0);
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc = fma(lt.P[j * Sym<N>::SZ + Sym<N>::at(a, c)], rq[c], acc);
+                for (int c = 0; c < N; ++c) acc = fma(red[Sym<N>::at(a, c)], rq[c], acc);
                 Pb[a] = acc;
             }
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 S acc = rq[N + a];
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc = fma(-lt.F[j * N * N + a * N + c], Pb[c], acc);
+                for (int c = 0; c < N; ++c) acc = fma(-red[Sym<N>::SZ + a * N + c], Pb[c], acc);
                 lt.w[j * N + a] = acc;
             }
         }

@@ -149,6 +149,7 @@ LtiTiles<S> lti_tiles_of(const map_smoother& h, const S* fold, S* w, S* gmaps)
             lt.w = w;
             lt.gmaps = gmaps;
             lt.pi = h.nt <= TT::PI_TILES ? reinterpret_cast<const S*>(base + TT::pi_off(h.nt)) : nullptr;
+            lt.qt = h.nt <= TT::PI_TILES ? reinterpret_cast<const S*>(base + TT::qt_off(h.nt)) : nullptr;
             // the co table goes to shared memory when three CTAs per SM still fit
             lt.co_smem = LtiDownSmem<N, Prod::W, S>::bytes(h.B, h.K, true) <= 72 * 1024;
         }
@@ -250,6 +251,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                                    filt_out, ctx, fin, x_out, filtT, form, gs);
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+                h.launches += 1;
                 return MAP_OK;
             }
         }
@@ -284,6 +286,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
            prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, lt, fin, xT, filtT,
            (const S*)group_agg);
     mark();
+    h.launches += (!lti || nt > 1 ? 1 : 0) + (ng ? 1 : 0) + 2;
     launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
            (const S*)xT, T, x_out, form);
     mark();
@@ -367,6 +370,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     mark();
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
+    h.launches += (!lti || nt > 1 ? 1 : 0) + (ng ? 1 : 0) + 3;
     launch(k_tf_down<N, S, RProd>, nt, B, sh_tfd, st, pdl, rprod, K, (const S*)thr_agg, (const S*)tile_agg,
            (const S*)term, (const S*)filt_ws, x_out, ctx);
     mark();

@@ -100,6 +100,10 @@ class MapSmoother:
         """(K steps per thread, B threads per tile, number of tiles)."""
         return B.map_smoother_geometry(self._h)
 
+    def launches(self):
+        """Kernels launched by the last solve (1: the single cooperative launch)."""
+        return B.map_smoother_launches(self._h)
+
     def profile(self, enable=True):
         """Record per-phase CUDA events in every solve (see phase_times)."""
         B.map_smoother_profile(self._h, enable)
