@@ -90,8 +90,8 @@ def work_model(n, m, K, B, nt, wbytes, r=None):
 # until the current version has been captured
 K_FILTER_DOWN_DRAM_BYTES = 10482944 + 3812864
 # the same for the single cooperative launch (k_lti_solve) that runs the whole
-# solve when every tile's CTA fits on the GPU at once; None until captured
-K_SOLVE_DRAM_BYTES = None
+# solve when every tile's CTA fits on the GPU at once (ncu capture, cold cache)
+K_SOLVE_DRAM_BYTES = 21940224 + 7762944
 
 
 def solve_bytes(n, m, wbytes):

@@ -544,28 +544,38 @@ __global__ void __launch_bounds__(64)
 k_lti_products(int nt, S* __restrict__ out)
 {
     using TT = TileTables<N, M, S>;
-    namespace fd = fold_detail;
     constexpr int NN = N * N;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nt) return;
     const double* E = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::e_off(nt));
     S* pi = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::pi_off(nt));
     S* qt = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::qt_off(nt));
-    double P[NN], Q[NN];
-#pragma unroll 1
+    double P[NN];                                   // registers: N is a compile-time size
+#pragma unroll
     for (int q = 0; q < NN; ++q) P[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
 #pragma unroll 1
     for (int b = a; b < nt; ++b) {
         S* o = pi + TT::pi_index(nt, a, b) * NN;
         S* ot = qt + TT::qt_index(b, a) * NN;
-#pragma unroll 1
+#pragma unroll
         for (int q = 0; q < NN; ++q) {
             o[q] = S(P[q]);
             ot[q] = S(P[(q % N) * N + q / N]);
         }
         if (b + 1 == nt) break;
-        fd::mm(N, P, E + (long)b * NN, Q);         // Pi(a, b + 1) = Pi(a, b) E_b
-#pragma unroll 1
+        double Eb[NN], Q[NN];                       // Pi(a, b + 1) = Pi(a, b) E_b
+#pragma unroll
+        for (int q = 0; q < NN; ++q) Eb[q] = E[(long)b * NN + q];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc = fma(P[i * N + k], Eb[k * N + j], acc);
+                Q[i * N + j] = acc;
+            }
+#pragma unroll
         for (int q = 0; q < NN; ++q) P[q] = Q[q];
     }
 }

@@ -1554,37 +1554,33 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
         unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + FS::bar(B, K));
 
         // ---- phase 1: the tile's observations, per-thread folds, up-sweep, w_j
-        const unsigned ybytes = (unsigned)(sizeof(S) * (size_t)B * K * M);
-        if (!last) {
-            if (t == 0) mbar_init(bar, 1);
-            __syncthreads();
-            if (t == 0) {
-                mbar_arrive_expect_tx(bar, ybytes);
-                bulk_copy_g2s(ys, prod.y + (long)tile * B * K * M, ybytes, bar);
-            }
+        // bulk copies (one mbarrier phase): the tile's observations (full tiles),
+        // the level constants, the co table and the Gamma_i (all 16-byte runs)
+        const int LB = ilog2(B);
+        const unsigned ybytes = last ? 0u : (unsigned)(sizeof(S) * (size_t)B * K * M);
+        const unsigned lbytes = (unsigned)(sizeof(S) * (size_t)LB * FL::LS);
+        const unsigned cbytes = (unsigned)(sizeof(S) * (size_t)(B - 1) * FL::CS);
+        // (the Gamma_i rounded up to whole 16-byte words: the fold buffer holds
+        // KMAX of them and the shared area is padded to 4 scalars)
+        const unsigned gbytes = (unsigned)(sizeof(S) * (size_t)((K * FL::GS + 3) / 4 * 4));
+        if (t == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (t == 0) {
+            mbar_arrive_expect_tx(bar, ybytes + lbytes + cbytes + gbytes);
+            if (!last) bulk_copy_g2s(ys, prod.y + (long)tile * B * K * M, ybytes, bar);
+            bulk_copy_g2s(lv, fold + FL::oL, lbytes, bar);
+            bulk_copy_g2s(co, fold + FL::oCo, cbytes, bar);
+            bulk_copy_g2s(gam, fold + FL::oG, gbytes, bar);
         }
-        {   // level constants and co (lti_stage_tables layout, here at FS offsets), Gamma_i
-            using V = typename std::conditional<sizeof(S) == 4, float4, double2>::type;
-            constexpr int W = 16 / sizeof(S);
-            const int LB = ilog2(B);
-            const V* src = reinterpret_cast<const V*>(fold + FL::oL);
-            V* dst = reinterpret_cast<V*>(lv);
-            for (int q = t; q < (LB * FL::LS) / W; q += B) dst[q] = src[q];
-            src = reinterpret_cast<const V*>(fold + FL::oCo);
-            dst = reinterpret_cast<V*>(co);
-            for (int q = t; q < ((B - 1) * FL::CS) / W; q += B) dst[q] = src[q];
-            for (int q = t; q < K * FL::GS; q += B) gam[q] = fold[FL::oG + q];
-            if (!last) {                           // P_j and F_j for w_j, in the composition area
-                for (int q = t; q < Sym<N>::SZ; q += B) red[q] = lt.P[(long)tile * Sym<N>::SZ + q];
-                for (int q = t; q < N * N; q += B) red[Sym<N>::SZ + q] = lt.F[(long)tile * N * N + q];
-            }
+        if (!last) {                               // P_j and F_j for w_j, in the composition area
+            for (int q = t; q < Sym<N>::SZ; q += B) red[q] = lt.P[(long)tile * Sym<N>::SZ + q];
+            for (int q = t; q < N * N; q += B) red[Sym<N>::SZ + q] = lt.F[(long)tile * N * N + q];
         }
         if (last) {                                // the last tile's observations up to T, zeros after
             const long base = (long)tile * B * K * M, have = T * M - base;
             for (long q = t; q < (long)B * K * M; q += B) ys[q] = q < have ? prod.y[base + q] : S(0);
         }
-        bool ok = true;
-        if (!last) ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
+        const bool ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
         if (!__syncthreads_and(ok)) {
             if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
             mbar_wait_bounded(bar, 0, MBAR_POLLS);  // the copy may still be in flight
