@@ -969,6 +969,12 @@ __device__ __forceinline__ void filter_steps(const Prod& prod, int K, long k0, l
     bool compact = false;
     if constexpr (Prod::LOWRANK && !Prod::RESETS) compact = prod.p.lowrank != 0;
     S Vc[((N + 1) / 2) * N];
+    // the factor Gam of the process noise in registers for the whole loop
+    S gam[((N + 1) / 2) * N];
+    if constexpr (Prod::LOWRANK) {
+#pragma unroll
+        for (int q = 0; q < ((N + 1) / 2) * N; ++q) gam[q] = prod.p.Gam[q];
+    }
 #pragma unroll 1
     for (int i = 0; i < K; ++i) {
         const long k = k0 + i;
@@ -993,7 +999,7 @@ __device__ __forceinline__ void filter_steps(const Prod& prod, int K, long k0, l
                 bool done = false;
                 if constexpr (Prod::LOWRANK) {
                     if (prod.p.lowrank)
-                        done = apply_lowrank<N, (N + 1) / 2, S, true>(e, prod.p.Gam, X, a.F, a.c, ctx.cond_max,
+                        done = apply_lowrank<N, (N + 1) / 2, S, true>(e, gam, X, a.F, a.c, ctx.cond_max,
                                                                       compact ? Vc : nullptr);
                 }
                 if (!done) {
@@ -1316,6 +1322,14 @@ __device__ __forceinline__ void rts_steps(const S* __restrict__ Eg, int K, long 
     constexpr int NA = Aff<N, S>::NCOMP;
     constexpr int U = 4;                   // steps whose maps are loaded ahead of use
     if (form.compact) {
+        // A and Gam in registers for the whole loop (form is kernel-parameter
+        // memory reached through a reference)
+        constexpr int RR = EgForm<N, S>::R;
+        S fA[N * N], fG[N * RR];
+#pragma unroll
+        for (int q = 0; q < N * N; ++q) fA[q] = form.A[q];
+#pragma unroll
+        for (int q = 0; q < N * RR; ++q) fG[q] = form.Gam[q];
         // x_k = A x_{k+1} - Gam (V_k x_{k+1}) + g_k
         constexpr int R = EgForm<N, S>::R, NAC = R * N + N;
 #pragma unroll 1
@@ -1346,9 +1360,9 @@ __device__ __forceinline__ void rts_steps(const S* __restrict__ Eg, int K, long 
                         for (int r = 0; r < N; ++r) {
                             S acc = buf[u][R * N + r];
 #pragma unroll
-                            for (int q = 0; q < N; ++q) acc = fma(form.A[r * N + q], x[q], acc);
+                            for (int q = 0; q < N; ++q) acc = fma(fA[r * N + q], x[q], acc);
 #pragma unroll
-                            for (int q = 0; q < R; ++q) acc = fma(-form.Gam[r * R + q], vx[q], acc);
+                            for (int q = 0; q < R; ++q) acc = fma(-fG[r * R + q], vx[q], acc);
                             y[r] = acc;
                         }
 #pragma unroll

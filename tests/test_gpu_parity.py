@@ -158,6 +158,28 @@ def test_tile_groups(prec, smoother):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_launch_matches_three_kernel_pipeline(prec):
+    """The cooperative single-launch solve and the three-kernel pipeline (run
+    when per-phase events are recorded) give the same trajectory."""
+    from paper_2512_13319_gb300 import MapSmoother
+    model = synth.ou_model(4, 2, seed=31)
+    T, dt = 200_000, 1e-3
+    _, y = synth.simulate(model, T, dt, seed=13, substeps=1)
+    sm = MapSmoother(model, T, dt, precision=prec)
+    yt = torch.tensor(y, dtype=DT[prec], device="cuda")
+    x1 = sm.solve(yt).cpu().numpy()
+    n1 = sm.launches()
+    sm.profile(True)
+    x3 = sm.solve(yt).cpu().numpy()
+    n3 = sm.launches()
+    sm.close()
+    # FP32 at nx = 4: every tile's CTA fits at once (one launch); FP64 may not
+    assert n3 >= 3 and (n1 == 1 if prec == "fp32" else n1 >= 1)
+    assert rel(x1, x3) <= TOL[prec]
+    assert rel(x1, oracle.smooth_lti(model, y, dt)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_full_size_T_2_20(prec):
     """The benchmark workload: nx = 4, T = 2^20, dt = 1e-3 (every output compared)."""
     model = synth.wiener_velocity(2, q=1.0, r=0.1)
