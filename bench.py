@@ -513,8 +513,27 @@ def extras(dev, flush, stream):
                             "(solve + adjoint solve + contraction)", "ms": ms,
                 "rel_err_vs_fp64_oracle_gradient": rel_err(box["g"], ref)}
 
+    def parameter_update():
+        # a learning step changes theta: set-up and plan-time constants again
+        # (discretisation, folds, tile tables, products), then one solve
+        T = 2 ** 18
+        model = synth.ou_model(4, 2, seed=51)
+        _, y = synth.simulate(model, T, DT, seed=1004, substeps=1)
+        sm = MapSmoother(model, T, DT, precision="fp32")
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        x = sm.solve(yt)
+
+        def step():
+            sm.update(F=model.F, log_q=0.0, log_r=0.0)
+            sm.solve(yt, x_out=x)
+        ms = timed(step, flush, stream, dev)
+        solve_ms = timed(lambda: sm.solve(yt, x_out=x), flush, stream, dev)
+        sm.close()
+        return {"workload": "parameter update + solve, OU nx=4, T=2^18, FP32", "ms": ms,
+                "solve_only_ms": solve_ms}
+
     for name, fn in (("ou_nx8", ou8), ("two_filter", two_filter), ("coordinated_turn", coord_turn),
-                     ("batched", batched), ("gradient", gradient)):
+                     ("batched", batched), ("gradient", gradient), ("parameter_update", parameter_update)):
         guard(name, fn)
     return out
 

@@ -153,64 +153,68 @@ __host__ __device__ constexpr int lti_co_level(int B, int d)
     return 4 * N * N * (B - (B >> d));
 }
 
-// Plan-time helpers of k_lti_fold (FP64, plain loops: run once per model and
-// geometry, so they are kept small rather than unrolled)
+// Plan-time helpers of the constant kernels (FP64; n is the state dimension,
+// a compile-time size, and the loops unroll)
 namespace fold_detail {
 
 // c = a b (n x n, row-major)
-__device__ inline void mm(int n, const double* a, const double* b, double* c)
+template <int n>
+__device__ inline void mm(const double* a, const double* b, double* c)
 {
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < n; ++i)
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < n; ++j) {
             double s = 0.0;
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < n; ++k) s += a[i * n + k] * b[k * n + j];
             c[i * n + j] = s;
         }
 }
 
 // c = a^T (n x n)
-__device__ inline void tr(int n, const double* a, double* c)
+template <int n>
+__device__ inline void tr(const double* a, double* c)
 {
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < n; ++i)
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < n; ++j) c[i * n + j] = a[j * n + i];
 }
 
 // y = a x
-__device__ inline void mv(int n, const double* a, const double* x, double* y)
+template <int n>
+__device__ inline void mv(const double* a, const double* x, double* y)
 {
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < n; ++k) s += a[i * n + k] * x[k];
         y[i] = s;
     }
 }
 
 // out = (I + c j)^-1 by Gauss-Jordan elimination with row pivoting; w: 2 n^2 scratch
-__device__ inline void inv_I_plus(int n, const double* c, const double* j, double* out, double* w)
+template <int n>
+__device__ inline void inv_I_plus(const double* c, const double* j, double* out, double* w)
 {
     double* X = w;
-    mm(n, c, j, X);
-#pragma unroll 1
+    mm<n>(c, j, X);
+#pragma unroll
     for (int i = 0; i < n; ++i) {
         X[i * n + i] += 1.0;
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < n; ++k) out[i * n + k] = i == k ? 1.0 : 0.0;
     }
-#pragma unroll 1
+#pragma unroll
     for (int col = 0; col < n; ++col) {
         int piv = col;
-#pragma unroll 1
+#pragma unroll
         for (int r = col + 1; r < n; ++r)
             if (fabs(X[r * n + col]) > fabs(X[piv * n + col])) piv = r;
         if (piv != col) {
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < n; ++k) {
                 double t = X[col * n + k]; X[col * n + k] = X[piv * n + k]; X[piv * n + k] = t;
                 t = out[col * n + k]; out[col * n + k] = out[piv * n + k]; out[piv * n + k] = t;
@@ -218,13 +222,13 @@ __device__ inline void inv_I_plus(int n, const double* c, const double* j, doubl
         }
         const double p = X[col * n + col];
         const double ip = p != 0.0 ? 1.0 / p : 0.0;
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < n; ++k) { X[col * n + k] *= ip; out[col * n + k] *= ip; }
-#pragma unroll 1
+#pragma unroll
         for (int r = 0; r < n; ++r) {
             if (r == col) continue;
             const double f = X[r * n + col];
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < n; ++k) {
                 X[r * n + k] -= f * X[col * n + k];
                 out[r * n + k] -= f * out[col * n + k];
@@ -236,54 +240,57 @@ __device__ inline void inv_I_plus(int n, const double* c, const double* j, doubl
 // coefficients of the (b, eta) part of U (x) D (U the later operand):
 // Mi = (I + C_U J_D)^-1, X = A_D Mi, Y = X C_U, Z = (Mi A_U)^T, W = Z J_D;
 // wk: 4 n^2 scratch
-__device__ inline void pair_coeffs(int n, const double* AU, const double* CU, const double* AD, const double* JD,
+template <int n>
+__device__ inline void pair_coeffs(const double* AU, const double* CU, const double* AD, const double* JD,
                                    double* X, double* Y, double* Z, double* W, double* wk)
 {
     double* Mi = wk;
     double* T = wk + n * n;
-    inv_I_plus(n, CU, JD, Mi, wk + 2 * n * n);
-    mm(n, AD, Mi, X);
-    mm(n, X, CU, Y);
-    mm(n, Mi, AU, T);
-    tr(n, T, Z);
-    mm(n, Z, JD, W);
+    inv_I_plus<n>(CU, JD, Mi, wk + 2 * n * n);
+    mm<n>(AD, Mi, X);
+    mm<n>(X, CU, Y);
+    mm<n>(Mi, AU, T);
+    tr<n>(T, Z);
+    mm<n>(Z, JD, W);
 }
 
 // (A, C, J) of U (x) D from the coefficients of pair_coeffs:
 // A = X A_U, C = Y A_D^T + C_D, J = W A_U + J_U; wk: n^2 scratch
-__device__ inline void pair_acj(int n, const double* AU, const double* JU, const double* AD, const double* CD,
+template <int n>
+__device__ inline void pair_acj(const double* AU, const double* JU, const double* AD, const double* CD,
                                 const double* X, const double* Y, const double* W, double* Ao, double* Co,
                                 double* Jo, double* wk)
 {
-    mm(n, X, AU, Ao);
-    tr(n, AD, wk);
-    mm(n, Y, wk, Co);
-    mm(n, W, AU, Jo);
-#pragma unroll 1
+    mm<n>(X, AU, Ao);
+    tr<n>(AD, wk);
+    mm<n>(Y, wk, Co);
+    mm<n>(W, AU, Jo);
+#pragma unroll
     for (int q = 0; q < n * n; ++q) { Co[q] += CD[q]; Jo[q] += JU[q]; }
 }
 
 // P <- A^T P (I + C P)^-1 A + J, symmetrised (full matrices); w: 4 n^2 scratch
-__device__ inline void riccati(int n, const double* A, const double* C, const double* J, double* P, double* w)
+template <int n>
+__device__ inline void riccati(const double* A, const double* C, const double* J, double* P, double* w)
 {
     double* Mi = w;
     double* T1 = w + n * n;
     double* T2 = w + 2 * n * n;
-    inv_I_plus(n, C, P, Mi, w + 3 * n * n);
-    mm(n, Mi, A, T1);                  // (I + C P)^-1 A
-    mm(n, P, T1, T2);                  // P (I + C P)^-1 A
-#pragma unroll 1
+    inv_I_plus<n>(C, P, Mi, w + 3 * n * n);
+    mm<n>(Mi, A, T1);                  // (I + C P)^-1 A
+    mm<n>(P, T1, T2);                  // P (I + C P)^-1 A
+#pragma unroll
     for (int i = 0; i < n; ++i)
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < n; ++j) {
             double s = J[i * n + j];
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < n; ++k) s += A[k * n + i] * T2[k * n + j];
             Mi[i * n + j] = s;
         }
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < n; ++i)
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < n; ++j) P[i * n + j] = 0.5 * (Mi[i * n + j] + Mi[j * n + i]);
 }
 
@@ -333,30 +340,30 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
 #pragma unroll 1
     for (int i = 1; i < K; ++i) {
         if (j == 0) {
-            fd::inv_I_plus(N, Ce, Jc, Mi, wk);    // (I + C_e J_acc)^-1
-            fd::mm(N, Ac, Mi, T1);                // A_acc Mi
-            fd::mm(N, T1, Ce, Tb);                // Tb = A_acc Mi C_e
-            fd::mm(N, Mi, Ae, T2);
-            fd::tr(N, T2, Te);                    // Te = (Mi A_e)^T
+            fd::inv_I_plus<N>(Ce, Jc, Mi, wk);    // (I + C_e J_acc)^-1
+            fd::mm<N>(Ac, Mi, T1);                // A_acc Mi
+            fd::mm<N>(T1, Ce, Tb);                // Tb = A_acc Mi C_e
+            fd::mm<N>(Mi, Ae, T2);
+            fd::tr<N>(T2, Te);                    // Te = (Mi A_e)^T
             // offsets: b <- b + Tb eta + A_acc Mi b_e;  eta <- Te (eta - J_acc b_e) - Gr
-            fd::mv(N, Jc, be, u);
+            fd::mv<N>(Jc, be, u);
 #pragma unroll 1
             for (int a = 0; a < N; ++a) u[a] = oe[a] - u[a];
-            fd::mv(N, Te, u, w);
-            fd::mv(N, Tb, oe, u);
+            fd::mv<N>(Te, u, w);
+            fd::mv<N>(Tb, oe, u);
 #pragma unroll 1
             for (int a = 0; a < N; ++a) { ob[a] += u[a]; oe[a] = w[a] - Gr[a]; }
-            fd::mv(N, T1, be, u);
+            fd::mv<N>(T1, be, u);
 #pragma unroll 1
             for (int a = 0; a < N; ++a) ob[a] += u[a];
             // composite: A = A_acc Mi A_e, C = Tb A_acc^T + C_acc, J = Te J_acc A_e + J_e
-            fd::mm(N, T1, Ae, T2);
-            fd::tr(N, Ac, T3);
-            fd::mm(N, Tb, T3, T1);
+            fd::mm<N>(T1, Ae, T2);
+            fd::tr<N>(Ac, T3);
+            fd::mm<N>(Tb, T3, T1);
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] += T1[q]; }
-            fd::mm(N, Jc, Ae, T2);
-            fd::mm(N, Te, T2, T3);
+            fd::mm<N>(Jc, Ae, T2);
+            fd::mm<N>(Te, T2, T3);
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) Jc[q] = T3[q] + Je[q];
         }
@@ -418,7 +425,7 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
                     lv[CL::oJ + a * CL::P + c] = in ? S(0.5 * (Jc[a * N + c] + Jc[c * N + a])) : S(0);
                 }
             if (d == LB) break;
-            fd::pair_coeffs(N, Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);   // X, Y, Z, W
+            fd::pair_coeffs<N>(Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);   // X, Y, Z, W
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) {
                 lv[FL::oX + q] = S(T1[q]);
@@ -426,7 +433,7 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
                 lv[FL::oZ + q] = S(Te[q]);
                 lv[FL::oW + q] = S(T3[q]);
             }
-            fd::pair_acj(N, Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
+            fd::pair_acj<N>(Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
         }
@@ -441,8 +448,8 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
                 tl[e * 3 * NN + 2 * NN + q] = Jc[q];
             }
             if (e + 1 == ne) break;
-            fd::pair_coeffs(N, Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);
-            fd::pair_acj(N, Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
+            fd::pair_coeffs<N>(Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);
+            fd::pair_acj<N>(Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
         }
@@ -468,8 +475,8 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
 #pragma unroll 1
         for (int d = LB - 1; d >= 0; --d) {
             if (!((p >> d) & 1)) continue;
-            fd::pair_coeffs(N, LA[d], LC[d], pA, pJ, X, Y, Z, W, pw);
-            fd::pair_acj(N, LA[d], LJ[d], pA, pC, X, Y, W, nA, nC, nJ, pw);
+            fd::pair_coeffs<N>(LA[d], LC[d], pA, pJ, X, Y, Z, W, pw);
+            fd::pair_acj<N>(LA[d], LJ[d], pA, pC, X, Y, W, nA, nC, nJ, pw);
 #pragma unroll 1
             for (int q = 0; q < NN; ++q) { pA[q] = nA[q]; pC[q] = nC[q]; pJ[q] = nJ[q]; }
         }
@@ -519,9 +526,9 @@ k_lti_tiles(const Red<N, double> prior, int nt, int ne, S* __restrict__ out)
         for (int c = 0; c < N; ++c) P[a * N + c] = prior.P[Sym<N>::at(a, c)];
 #pragma unroll 1
     for (int e = ne - 1; e >= 0; --e)
-        if ((j >> e) & 1) fd::riccati(N, tl + e * 3 * NN, tl + e * 3 * NN + NN, tl + e * 3 * NN + 2 * NN, P, w);
-    fd::inv_I_plus(N, tl + NN, P, w, w + NN);            // (I + C_T P_j)^-1
-    fd::mm(N, w, tl, E);                                   // E_j
+        if ((j >> e) & 1) fd::riccati<N>(tl + e * 3 * NN, tl + e * 3 * NN + NN, tl + e * 3 * NN + 2 * NN, P, w);
+    fd::inv_I_plus<N>(tl + NN, P, w, w + NN);            // (I + C_T P_j)^-1
+    fd::mm<N>(w, tl, E);                                   // E_j
     S* tp = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::p_off()) + (long)j * Sym<N>::SZ;
     S* tf = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::f_off(nt)) + (long)j * NN;
     double* te = reinterpret_cast<double*>(reinterpret_cast<char*>(out) + TT::e_off(nt)) + (long)j * NN;
