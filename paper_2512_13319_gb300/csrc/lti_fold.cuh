@@ -548,7 +548,7 @@ k_lti_tiles(const Red<N, double> prior, int nt, int ne, S* __restrict__ out)
 // products rounded to S.  Runs after k_lti_tiles, for nt <= PI_TILES.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(64)
-k_lti_products(int nt, S* __restrict__ out)
+k_lti_products(int nt, S* __restrict__ out)   // any block size
 {
     using TT = TileTables<N, M, S>;
     constexpr int NN = N * N;

@@ -437,7 +437,8 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
         k_lti_tiles<N, M, S><<<(h.nt + 63) / 64, 64, 0, st>>>(prior_of<N, double>(h), h.nt, ne,
                                                              static_cast<S*>(h.d_fold));
         if (h.nt <= TT::PI_TILES)
-            k_lti_products<N, M, S><<<(h.nt + 63) / 64, 64, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
+            // serial FP64 chains, one per tile: spread over many SMs' FP64 units
+            k_lti_products<N, M, S><<<(h.nt + 3) / 4, 4, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
         h.fold_K = h.K;
