@@ -549,22 +549,25 @@ __device__ __forceinline__ void lti_tile_prefix_sum(const LtiTiles<S>& lt, int t
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = S(0);
     // terms i = t - 1 + u B (i = -1: Pi(0, tile)^T v_0, else Pi(i+1, tile)^T w_i); at
-    // most 5 per thread (tile <= 4B + 1), their loads issued together
+    // most 5 per thread (tile <= 4B + 1): all their operands are loaded first
+    // (16-byte loads of the table rows), then multiplied
     constexpr int UMAX = 5;
+    S Qm[UMAX][NN], wv[UMAX][N];
 #pragma unroll
     for (int u = 0; u < UMAX; ++u) {
         const int i = t - 1 + u * (int)blockDim.x;
-        if (i < tile) {
-            const S* Q = lt.qt + TT::qt_index(tile, i + 1) * NN;   // Pi(i+1, tile)^T, row tile of the transposes
-            S w[N];
+        const bool on = i < tile;
+        const S* Q = lt.qt + TT::qt_index(tile, on ? i + 1 : 0) * NN;   // Pi(i+1, tile)^T
+        load_run_aligned<NN, S>(Q, Qm[u]);
 #pragma unroll
-            for (int c = 0; c < N; ++c) w[c] = i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
-#pragma unroll
-            for (int r = 0; r < N; ++r)
-#pragma unroll
-                for (int c = 0; c < N; ++c) v[r] = fma(__ldg(Q + r * N + c), w[c], v[r]);
-        }
+        for (int c = 0; c < N; ++c) wv[u][c] = !on ? S(0) : i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
     }
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u)
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[r] = fma(Qm[u][r * N + c], wv[u][c], v[r]);
     block_vec_sum<N, S>(v, red);
     if (t == 0) {
 #pragma unroll
@@ -596,30 +599,34 @@ __device__ __forceinline__ void lti_tile_suffix_sum(const LtiTiles<S>& lt, const
     S v[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = S(0);
-    constexpr int UMAX = 5;                             // nt <= 4B + 1: at most 5 terms per thread
+    // terms i = tile + 1 + t + u B (at most 5 per thread: nt <= 4B + 1): all
+    // operands loaded first, then multiplied; i = nt - 1 is x_L
+    constexpr int UMAX = 5;
+    S Pm[UMAX][NN], uv[UMAX][N];
 #pragma unroll
-    for (int uu = 0; uu < UMAX; ++uu) {                 // term i: Pi(tile+1, i) beta_i; i = nt-1: x_L
+    for (int uu = 0; uu < UMAX; ++uu) {
         const int i = tile + 1 + t + uu * (int)blockDim.x;
-        if (i >= nt) continue;
-        const S* P = lt.pi + TT::pi_index(nt, tile + 1, i) * NN;
-        S u[N];
-        if (i + 1 == nt) {
+        const bool on = i < nt;
+        load_run_aligned<NN, S>(lt.pi + TT::pi_index(nt, tile + 1, on ? i : tile + 1) * NN, Pm[uu]);
+        if (on && i + 1 == nt) {
             Aff<N, S> a;
 #pragma unroll
             for (int c = 0; c < NA; ++c) comp(a, c) = tile_aff[(long)i * NA + c];
             S x[N];
 #pragma unroll
             for (int c = 0; c < N; ++c) x[c] = xT[c];
-            affine_apply<N, S>(a, x, u);
+            affine_apply<N, S>(a, x, uv[uu]);
         } else {
 #pragma unroll
-            for (int c = 0; c < N; ++c) u[c] = tile_aff[(long)i * NA + NN + c];
+            for (int c = 0; c < N; ++c) uv[uu][c] = on ? tile_aff[(long)i * NA + NN + c] : S(0);
         }
+    }
+#pragma unroll
+    for (int uu = 0; uu < UMAX; ++uu)
 #pragma unroll
         for (int r = 0; r < N; ++r)
 #pragma unroll
-            for (int c = 0; c < N; ++c) v[r] = fma(__ldg(P + r * N + c), u[c], v[r]);
-    }
+            for (int c = 0; c < N; ++c) v[r] = fma(Pm[uu][r * N + c], uv[uu][c], v[r]);
     block_vec_sum<N, S>(v, red);
     if (t == 0)
 #pragma unroll
