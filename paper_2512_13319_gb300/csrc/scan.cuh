@@ -463,53 +463,6 @@ __device__ __forceinline__ void lti_tile_prefix(const LtiTiles<S>& lt, int tile,
     }
 }
 
-// Linear-fold mode: state at the end of tile `tile` (written by thread 0 to
-// xe), the tile maps a_i of the tiles after it composed (earlier map
-// outermost) and applied to x_T.  A full tile's map has F = E_i = F_i^T of the
-// tile tables (the composition of a tile's closed-loop maps is the closed-loop
-// map of its combined element, item (4) of lti_fold.cuh) and its offset in
-// tile_aff; the last (partial) tile's map is read whole from tile_aff.
-// Uses the start of `nodes`; ends with a barrier.
-template <int N, typename S>
-__device__ __forceinline__ void lti_tile_suffix_state(const LtiTiles<S>& lt, const S* tile_aff, int tile, int nt,
-                                                      const S* xT, S* nodes, S* xe)
-{
-    constexpr int NN = N * N, NA = Aff<N, S>::NCOMP;
-    const int B = blockDim.x, t = threadIdx.x;
-    const int cnt = nt - 1 - tile;
-    Aff<N, S> H;
-    set_identity(H);
-    if (cnt > 0) {
-        const int per = (cnt + B - 1) / B;
-        const int first = tile + 1 + min(cnt, t * per), last = min(nt, first + per);
-        for (int i = last - 1; i >= first; --i) {          // H = a_first o ... o a_last
-            Aff<N, S> a;
-            if (i == nt - 1) {
-#pragma unroll
-                for (int c = 0; c < NA; ++c) comp(a, c) = tile_aff[(long)i * NA + c];
-            } else {
-#pragma unroll
-                for (int r = 0; r < N; ++r)
-#pragma unroll
-                    for (int c = 0; c < N; ++c) a.F[r * N + c] = __ldg(lt.F + (long)i * NN + c * N + r);
-#pragma unroll
-                for (int c = 0; c < N; ++c) a.c[c] = tile_aff[(long)i * NA + NN + c];
-            }
-            compose<N, S>(a, H, H);
-        }
-    }
-    block_aff_reduce<N, S>(H, nodes);
-    if (t == 0) {
-        S x[N], y[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = xT[i];
-        affine_apply<N, S>(H, x, y);
-#pragma unroll
-        for (int i = 0; i < N; ++i) xe[i] = y[i];
-    }
-    __syncthreads();
-}
-
 // Sum over the CTA of one N-vector per thread, returned in thread 0.  red:
 // B / 32 * N scalars of shared memory; ends with a barrier.
 template <int N, typename S>
@@ -1584,14 +1537,20 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
         // (the Gamma_i rounded up to whole 16-byte words: the fold buffer holds
         // KMAX of them and the shared area is padded to 4 scalars)
         const unsigned gbytes = (unsigned)(sizeof(S) * (size_t)((K * FL::GS + 3) / 4 * 4));
-        if (t == 0) mbar_init(bar, 1);
+        // the co table (needed only in phase 2) completes on a second mbarrier
+        unsigned long long* bar_co = bar + 1;
+        if (t == 0) {
+            mbar_init(bar, 1);
+            mbar_init(bar_co, 1);
+        }
         __syncthreads();
         if (t == 0) {
-            mbar_arrive_expect_tx(bar, ybytes + lbytes + cbytes + gbytes);
+            mbar_arrive_expect_tx(bar, ybytes + lbytes + gbytes);
             if (!last) bulk_copy_g2s(ys, prod.y + (long)tile * B * K * M, ybytes, bar);
             bulk_copy_g2s(lv, fold + FL::oL, lbytes, bar);
-            bulk_copy_g2s(co, fold + FL::oCo, cbytes, bar);
             bulk_copy_g2s(gam, fold + FL::oG, gbytes, bar);
+            mbar_arrive_expect_tx(bar_co, cbytes);
+            bulk_copy_g2s(co, fold + FL::oCo, cbytes, bar_co);
         }
         if (!last) {                               // P_j and F_j for w_j, in the composition area
             for (int q = t; q < Sym<N>::SZ; q += B) red[q] = lt.P[(long)tile * Sym<N>::SZ + q];
@@ -1654,6 +1613,8 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
         Red<N, S> pin, X;
         lti_tile_prefix_sum<N, S>(lt, tile, gridDim.x, prior, red, pin);
         if (t == 0) node_store(pin, ps);
+        if (!mbar_wait_bounded(bar_co, 0, MBAR_POLLS) && ctx.stats && t == 0)
+            atomicAdd(ctx.stats + 2, 1ull);        // the co table
         lti_tree_down_linear<N, M, S>(bq, co);     // starts and ends with a barrier
         {
             Red<N, S> P;
