@@ -91,7 +91,7 @@ def work_model(n, m, K, B, nt, wbytes, r=None):
 K_FILTER_DOWN_DRAM_BYTES = 10482944 + 3812864
 # the same for the single cooperative launch (k_lti_solve) that runs the whole
 # solve when every tile's CTA fits on the GPU at once (ncu capture, cold cache)
-K_SOLVE_DRAM_BYTES = 21931776 + 7794944
+K_SOLVE_DRAM_BYTES = 21929472 + 8958208
 
 
 def solve_bytes(n, m, wbytes):

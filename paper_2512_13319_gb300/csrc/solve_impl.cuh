@@ -247,12 +247,16 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                 at[0].val.cooperative = 1;
                 cfg.attrs = at;
                 cfg.numAttrs = 1;
-                cudaLaunchKernelEx(&cfg, k_lti_solve<N, S, Prod>, prod, K, lt, prior_of<N, S>(h), Eg, tile_aff,
-                                   filt_out, ctx, fin, x_out, filtT, form, gs);
-                cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
-                h.launches += 1;
-                return MAP_OK;
+                cudaError_t e = cudaLaunchKernelEx(&cfg, k_lti_solve<N, S, Prod>, prod, K, lt, prior_of<N, S>(h),
+                                                   Eg, tile_aff, filt_out, ctx, fin, x_out, filtT, form, gs);
+                if (e == cudaSuccess) {
+                    h.launches += 1;
+                    return MAP_OK;
+                }
+                // the grid cannot be resident at once after all (e.g. another
+                // context holds part of the GPU): the three-kernel pipeline instead
+                cudaGetLastError();
+                h.fused = 0;
             }
         }
     }
