@@ -544,8 +544,8 @@ k_lti_tiles(const Red<N, double> prior, int nt, int ne, S* __restrict__ out)
 }
 
 // Products of consecutive full tiles' closed-loop maps (item (5)): thread a
-// writes Pi(a, b) = E_a ... E_{b-1} for b = a..nt-1 (Pi(a, a) = I), FP64
-// products rounded to S.  Runs after k_lti_tiles, for nt <= PI_TILES.
+// writes Pi(a, b) = E_a ... E_{b-1} for b = a..nt-1 (Pi(a, a) = I), in the
+// solve's precision.  Runs after k_lti_tiles, for nt <= PI_TILES.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(64)
 k_lti_products(int nt, S* __restrict__ out)   // any block size
@@ -557,9 +557,15 @@ k_lti_products(int nt, S* __restrict__ out)   // any block size
     const double* E = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::e_off(nt));
     S* pi = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::pi_off(nt));
     S* qt = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::qt_off(nt));
-    double P[NN];                                   // registers: N is a compile-time size
+    // products in the solve's precision (the FP64 E_j rounded): the terms that
+    // matter are short products, the long ones have decayed; registers, N is a
+    // compile-time size
+    S P[NN], En[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) P[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    for (int q = 0; q < NN; ++q) {
+        P[q] = q % (N + 1) == 0 ? S(1) : S(0);
+        En[q] = S(E[(long)a * NN + q]);             // E_b, loaded one step ahead
+    }
 #pragma unroll 1
     for (int b = a; b < nt; ++b) {
         S* o = pi + TT::pi_index(nt, a, b) * NN;
@@ -570,14 +576,17 @@ k_lti_products(int nt, S* __restrict__ out)   // any block size
             ot[q] = S(P[(q % N) * N + q / N]);
         }
         if (b + 1 == nt) break;
-        double Eb[NN], Q[NN];                       // Pi(a, b + 1) = Pi(a, b) E_b
+        S Eb[NN], Q[NN];                            // Pi(a, b + 1) = Pi(a, b) E_b
 #pragma unroll
-        for (int q = 0; q < NN; ++q) Eb[q] = E[(long)b * NN + q];
+        for (int q = 0; q < NN; ++q) {
+            Eb[q] = En[q];
+            if (b + 2 < nt) En[q] = S(E[(long)(b + 1) * NN + q]);
+        }
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                double acc = 0.0;
+                S acc = S(0);
 #pragma unroll
                 for (int k = 0; k < N; ++k) acc = fma(P[i * N + k], Eb[k * N + j], acc);
                 Q[i * N + j] = acc;
