@@ -66,11 +66,6 @@ std::vector<double> copy_or(const double* p, size_t n, double fill = 0.0)
 
 bool aligned16(const void* p) { return (reinterpret_cast<size_t>(p) & 15) == 0; }
 
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-};
-
 void free_handle(map_smoother* h)
 {
     if (!h) return;
@@ -83,6 +78,7 @@ void free_handle(map_smoother* h)
     if (h->d_lam) cudaFree(h->d_lam);
     if (h->d_grad) cudaFree(h->d_grad);
     if (h->d_fold) cudaFree(h->d_fold);
+    if (h->d_setup) cudaFree(h->d_setup);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;
@@ -94,7 +90,6 @@ map_status run_setup(map_smoother* h)
 {
     const int n = h->N, m = h->M, nw = h->NW;
     h->fold_K = 0;                     // linear-fold constants follow the model
-    DevBuf in, out;
     std::vector<double> W = h->W, R = h->R;
     for (double& w : W) w *= std::exp(h->logq);
     for (double& r : R) r *= std::exp(h->logr);
@@ -104,11 +99,16 @@ map_status run_setup(map_smoother* h)
     push(h->P0);
     const size_t nin = host.size();
     cudaError_t e;
-    if ((e = cudaMalloc(&in.p, nin * sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
-    if ((e = cudaMalloc(&out.p, sizeof(SetupOut))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
-    if ((e = cudaMemcpy(in.p, host.data(), nin * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if (nin > (size_t)SETUP_IN_CAP) return fail(*h, MAP_ERR_SHAPE, "model too large for the set-up buffer");
+    // one buffer for the handle's lifetime (inputs, then SetupOut), so that a
+    // parameter update allocates nothing
+    if (!h->d_setup &&
+        (e = cudaMalloc(&h->d_setup, SETUP_IN_CAP * sizeof(double) + sizeof(SetupOut))) != cudaSuccess)
+        return cuda_fail(*h, e, "cudaMalloc");
+    SetupOut* d_out = reinterpret_cast<SetupOut*>(h->d_setup + SETUP_IN_CAP);
+    if ((e = cudaMemcpy(h->d_setup, host.data(), nin * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMemcpy");
-    const double* b = static_cast<const double*>(in.p);
+    const double* b = h->d_setup;
     SetupIn si{};
     si.nx = n; si.ny = m; si.nw = nw; si.mode = h->disc; si.dt = h->dt;
     size_t o = 0;
@@ -121,9 +121,9 @@ map_status run_setup(map_smoother* h)
     si.R = b + o; o += (size_t)m * m;
     si.m0 = b + o; o += n;
     si.P0 = b + o;
-    if ((e = launch_setup(si, static_cast<SetupOut*>(out.p), 0)) != cudaSuccess)
+    if ((e = launch_setup(si, d_out, 0)) != cudaSuccess)
         return cuda_fail(*h, e, "set-up kernel launch");
-    if ((e = cudaMemcpy(&h->consts, out.p, sizeof(SetupOut), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpy(&h->consts, d_out, sizeof(SetupOut), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(*h, e, "set-up kernel");
     return MAP_OK;
 }

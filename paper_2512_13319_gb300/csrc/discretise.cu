@@ -26,7 +26,8 @@ namespace mapk {
 struct SetupShared {
     double Z[MAXD * MAXD], E[MAXD * MAXD], T1[MAXD * MAXD], T2[MAXD * MAXD];
     double X[8 * 8], Y[8 * 8];
-    double pivw[2 * MAXD * MAXD];
+    double inw[6][2 * MAXN * MAXN];        // per-warp scratch of the stage-3 warps
+    double Gam[MAXN * MAXN];
     int flag;
 };
 
@@ -42,37 +43,145 @@ __device__ void bmm(const double* a, const double* b, double* c, int n, int k, i
     __syncthreads();
 }
 
-// inverse by Gauss-Jordan with partial pivoting, thread 0; returns false if singular
-__device__ bool binv(const double* a, double* x, int n, double* w)
+// |x| ordering of finite FP64 values through their bit patterns (no FP64 op)
+__device__ inline unsigned long long absbits(double x)
 {
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const int m = 2 * n;
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < m; ++j) w[i * m + j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
-        for (int c = 0; c < n && ok; ++c) {
-            int p = c;
-            for (int r = c + 1; r < n; ++r)
-                if (fabs(w[r * m + c]) > fabs(w[p * m + c])) p = r;
-            if (w[p * m + c] == 0.0) { ok = 0; break; }
-            if (p != c)
-                for (int j = 0; j < m; ++j) { double t = w[c * m + j]; w[c * m + j] = w[p * m + j]; w[p * m + j] = t; }
-            const double d = 1.0 / w[c * m + c];
-            for (int j = 0; j < m; ++j) w[c * m + j] *= d;
-            for (int r = 0; r < n; ++r) {
-                if (r == c) continue;
-                const double f = w[r * m + c];
-                for (int j = 0; j < m; ++j) w[r * m + j] -= f * w[c * m + j];
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+// x = a^-1 (n x n, n <= MAXN) by Gauss-Jordan elimination with partial
+// pivoting on [a | I], by the calling warp: lane l updates entries l, l + 32,
+// ... of the augmented matrix, reading all of them before any is written.
+// Returns false (the same on every lane) at a zero pivot, x then unwritten.
+// w: 2 n^2 scratch.  (The FP64 pipe takes a warp instruction at about the
+// same cost however many lanes are active, so the lanes share the work.)
+__device__ bool winv(const double* a, double* x, int n, double* w)
+{
+    const int l = threadIdx.x & 31, m = 2 * n, E = n * m;
+    for (int e = l; e < E; e += 32) {
+        const int i = e / m, j = e - i * m;
+        w[e] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    constexpr int R = (2 * MAXN * MAXN + 31) / 32;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        unsigned long long best = absbits(w[c * m + c]);
+        for (int r = c + 1; r < n; ++r) {
+            const unsigned long long v = absbits(w[r * m + c]);
+            if (v > best) { best = v; p = r; }
+        }
+        const double piv = w[p * m + c];
+        if (piv == 0.0) return false;
+        const double d = 1.0 / piv;
+        // rows c and p swapped, row c scaled, column c eliminated elsewhere
+        double nv[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = l + 32 * t;
+            if (e < E) {
+                const int r = e / m, j = e - r * m;
+                const double pk = w[p * m + j] * d;
+                const int sr = r == p ? c : r;
+                nv[t] = r == c ? pk : fma(-w[sr * m + c], pk, w[sr * m + j]);
             }
         }
-        if (ok)
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) x[i * n + j] = w[i * m + n + j];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = l + 32 * t;
+            if (e < E) w[e] = nv[t];
+        }
+        __syncwarp();
     }
-    __syncthreads();
-    return ok != 0;
+    for (int e = l; e < n * n; e += 32) x[e] = w[(e / n) * m + n + e % n];
+    __syncwarp();
+    return true;
 }
+
+// C = Gam Gam^T by outer-product Cholesky with diagonal pivoting, by the
+// calling warp: each column takes the largest remaining diagonal; stop when it
+// falls below 1e-13 of the largest diagonal of C (the numerical rank).  Then
+// the pseudo-inverse of Gam, (Gam^T Gam)^-1 Gam^T, by Gauss-Jordan on the
+// rank x rank Gram matrix (positive definite: no pivoting).  w: 2 MAXN^2
+// scratch, Gam: MAXN^2 (shared).
+__device__ void wgam(const double* C, int n, double* w, double* Gam, SetupOut* out)
+{
+    const int l = threadIdx.x & 31;
+    double* Rm = w;
+    for (int e = l; e < n * n; e += 32) { Rm[e] = C[e]; Gam[e] = 0.0; }
+    __syncwarp();
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) dmax = fmax(dmax, Rm[i * n + i]);
+    int rk = 0;
+    for (; rk < n; ++rk) {
+        int p = 0;                             // signed bit order: positive values in FP order
+        long long best = __double_as_longlong(Rm[0]);
+        for (int i = 1; i < n; ++i) {
+            const long long v = __double_as_longlong(Rm[i * n + i]);
+            if (v > best) { best = v; p = i; }
+        }
+        const double d = Rm[p * n + p];
+        if (!(d > 1e-13 * dmax) || dmax <= 0.0) break;
+        const double sd = sqrt(d);
+        if (l < n) Gam[l * n + rk] = Rm[l * n + p] / sd;
+        __syncwarp();
+        for (int e = l; e < n * n; e += 32) {
+            const int i = e / n, j = e - i * n;
+            Rm[e] = fma(-Gam[i * n + rk], Gam[j * n + rk], Rm[e]);
+        }
+        __syncwarp();
+    }
+    for (int e = l; e < n * n; e += 32) out->Gam[e] = Gam[e];
+    // Gram matrix beside the identity: [Gm | Gi], rk x 2 rk
+    const int m = 2 * rk, E = rk * m;
+    double* A = w;
+    for (int e = l; e < E; e += 32) {
+        const int a = e / m, c = e - a * m;
+        double acc = 0.0;
+        if (c < rk)
+            for (int i = 0; i < n; ++i) acc = fma(Gam[i * n + a], Gam[i * n + c], acc);
+        else
+            acc = c - rk == a ? 1.0 : 0.0;
+        A[e] = acc;
+    }
+    __syncwarp();
+    constexpr int R = (2 * MAXN * MAXN + 31) / 32;
+    for (int col = 0; col < rk; ++col) {
+        const double ip = 1.0 / A[col * m + col];
+        double nv[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = l + 32 * t;
+            if (e < E) {
+                const int r = e / m, c = e - r * m;
+                const double pk = A[col * m + c] * ip;
+                nv[t] = r == col ? pk : fma(-A[r * m + col], pk, A[e]);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = l + 32 * t;
+            if (e < E) A[e] = nv[t];
+        }
+        __syncwarp();
+    }
+    for (int e = l; e < n * n; e += 32) {
+        const int a = e / n, i = e - a * n;
+        double acc = 0.0;
+        if (a < rk)
+            for (int c = 0; c < rk; ++c) acc = fma(A[a * m + rk + c], Gam[i * n + c], acc);
+        out->Gpinv[e] = acc;
+    }
+    if (l == 0) out->rank = rk;
+    __syncwarp();
+}
+
+// 1/k for the Taylor terms, each rounded once at compile time
+__constant__ double kRecip[25] = {0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8,
+                                  1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16,
+                                  1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24};
 
 // E = exp(Z) for Z of order d (in shared memory), all threads
 __device__ void bexpm(SetupShared& s, int d)
@@ -97,11 +206,12 @@ __device__ void bexpm(SetupShared& s, int d)
         s.T1[e] = s.E[e];
     }
     __syncthreads();
-    // Horner-free accumulation: term_k = term_{k-1} Z / k
+    // Horner-free accumulation: term_k = term_{k-1} Z (1/k)
+#pragma unroll 1
     for (int k = 1; k <= 24; ++k) {
         bmm(s.T1, s.Z, s.T2, d, d, d);
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
-            s.T1[e] = s.T2[e] / k;
+            s.T1[e] = s.T2[e] * kRecip[k];
             s.E[e] += s.T1[e];
         }
         __syncthreads();
@@ -170,21 +280,47 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
         }
         __syncthreads();
     }
-    // measurement
-    if (!binv(in.R, out->Rinv, m, s.pivw)) { if (threadIdx.x == 0) s.flag |= SETUP_SINGULAR_R; }
+    // inverses and the factor of C, one warp each, side by side
+    {
+        const int wid = threadIdx.x >> 5;
+        int bad = 0;
+        if (wid == 0) bad = winv(in.R, out->Rinv, m, s.inw[0]) ? 0 : SETUP_SINGULAR_R;
+        else if (wid == 1) bad = winv(in.P0, out->S0, n, s.inw[1]) ? 0 : SETUP_SINGULAR_P0;
+        else if (wid == 2) bad = winv(out->A, out->Phi, n, s.inw[2]) ? 0 : SETUP_SINGULAR_A;
+        else if (wid == 3) bad = winv(out->Q, out->Qinv, n, s.inw[3]) ? 0 : SETUP_SINGULAR_Q;
+        else if (wid == 4) bad = winv(out->C, out->Cinv, n, s.inw[4]) ? 0 : SETUP_SINGULAR_C;
+        else if (wid == 5) wgam(out->C, n, s.inw[5], s.Gam, out);
+        if (bad && (threadIdx.x & 31) == 0) atomicOr(&s.flag, bad);
+    }
     __syncthreads();
+    // measurement: G = dt H^T R^-1, J = G H (symmetrised), Gr = G r
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
         double acc = 0.0;
         for (int l = 0; l < m; ++l) acc = fma(in.H[l * n + i], out->Rinv[l * m + j], acc);
         out->G[e] = dt * acc;
     }
-    __syncthreads();
+    // prior: v0 = S0 m0
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < n; ++l) acc = fma(out->S0[i * n + l], in.m0[l], acc);
+        out->v0[i] = acc;
+    }
+    // forward transition: beta = -Phi b, Sigma = Phi C Phi^T
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < n; ++l) acc = fma(out->Phi[i * n + l], out->b[l], acc);
+        out->beta[i] = -acc;
+    }
+    bmm(out->Phi, out->C, s.T1, n, n, n);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
         double acc = 0.0;
         for (int l = 0; l < m; ++l) acc = fma(out->G[i * m + l], in.H[l * n + j], acc);
         s.Y[e] = acc;
+        acc = 0.0;
+        for (int l = 0; l < n; ++l) acc = fma(s.T1[i * n + l], out->Phi[j * n + l], acc);
+        out->Sigma[e] = acc;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double acc = 0.0;
@@ -196,86 +332,7 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
         const int i = e / n, j = e % n;
         out->J[e] = 0.5 * (s.Y[i * n + j] + s.Y[j * n + i]);
     }
-    // prior
-    if (!binv(in.P0, out->S0, n, s.pivw)) { if (threadIdx.x == 0) s.flag |= SETUP_SINGULAR_P0; }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double acc = 0.0;
-        for (int l = 0; l < n; ++l) acc = fma(out->S0[i * n + l], in.m0[l], acc);
-        out->v0[i] = acc;
-    }
-    __syncthreads();
-    // forward transition
-    if (!binv(out->A, out->Phi, n, s.pivw)) { if (threadIdx.x == 0) s.flag |= SETUP_SINGULAR_A; }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double acc = 0.0;
-        for (int l = 0; l < n; ++l) acc = fma(out->Phi[i * n + l], out->b[l], acc);
-        out->beta[i] = -acc;
-    }
-    bmm(out->Phi, out->C, s.T1, n, n, n);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        double acc = 0.0;
-        for (int l = 0; l < n; ++l) acc = fma(s.T1[i * n + l], out->Phi[j * n + l], acc);
-        out->Sigma[e] = acc;
-    }
-    __syncthreads();
-    // Q^-1 and C^-1 when they exist (cost and gradient)
-    if (!binv(out->Q, out->Qinv, n, s.pivw)) { if (threadIdx.x == 0) s.flag |= SETUP_SINGULAR_Q; }
-    __syncthreads();
-    if (!binv(out->C, out->Cinv, n, s.pivw)) { if (threadIdx.x == 0) s.flag |= SETUP_SINGULAR_C; }
-    __syncthreads();
-    // C = Gam Gam^T by outer-product Cholesky with diagonal pivoting: each
-    // column takes the largest remaining diagonal; stop when it falls below
-    // 1e-13 of the largest diagonal of C (the numerical rank)
-    if (threadIdx.x == 0) {
-        double* Rm = s.pivw;
-        double dmax = 0.0;
-        for (int e = 0; e < n * n; ++e) Rm[e] = out->C[e];
-        for (int i = 0; i < n; ++i) dmax = fmax(dmax, Rm[i * n + i]);
-        for (int e = 0; e < n * n; ++e) out->Gam[e] = 0.0;
-        int rk = 0;
-        for (; rk < n; ++rk) {
-            int p = 0;
-            for (int i = 1; i < n; ++i)
-                if (Rm[i * n + i] > Rm[p * n + p]) p = i;
-            const double d = Rm[p * n + p];
-            if (!(d > 1e-13 * dmax) || dmax <= 0.0) break;
-            const double sd = sqrt(d);
-            for (int i = 0; i < n; ++i) out->Gam[i * n + rk] = Rm[i * n + p] / sd;
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) Rm[i * n + j] -= out->Gam[i * n + rk] * out->Gam[j * n + rk];
-        }
-        out->rank = rk;
-        // pseudo-inverse of Gam: (Gam^T Gam)^-1 Gam^T by Gauss-Jordan on the rank x rank Gram matrix
-        double* Gm = s.pivw;                    // rk x rk, then its inverse beside it
-        double* Gi = s.pivw + MAXN * MAXN;
-        for (int a = 0; a < rk; ++a)
-            for (int c = 0; c < rk; ++c) {
-                double acc = 0.0;
-                for (int i = 0; i < n; ++i) acc += out->Gam[i * n + a] * out->Gam[i * n + c];
-                Gm[a * rk + c] = acc;
-                Gi[a * rk + c] = a == c ? 1.0 : 0.0;
-            }
-        for (int col = 0; col < rk; ++col) {   // symmetric positive definite: no pivoting needed
-            const double ip = 1.0 / Gm[col * rk + col];
-            for (int c = 0; c < rk; ++c) { Gm[col * rk + c] *= ip; Gi[col * rk + c] *= ip; }
-            for (int r = 0; r < rk; ++r) {
-                if (r == col) continue;
-                const double f = Gm[r * rk + col];
-                for (int c = 0; c < rk; ++c) { Gm[r * rk + c] -= f * Gm[col * rk + c]; Gi[r * rk + c] -= f * Gi[col * rk + c]; }
-            }
-        }
-        for (int e = 0; e < n * n; ++e) out->Gpinv[e] = 0.0;
-        for (int a = 0; a < rk; ++a)
-            for (int i = 0; i < n; ++i) {
-                double acc = 0.0;
-                for (int c = 0; c < rk; ++c) acc += Gi[a * rk + c] * out->Gam[i * n + c];
-                out->Gpinv[a * n + i] = acc;
-            }
-        out->flags = s.flag;
-    }
+    if (threadIdx.x == 0) out->flags = s.flag;
 }
 
 cudaError_t launch_setup(const SetupIn& in, SetupOut* d_out, cudaStream_t st)

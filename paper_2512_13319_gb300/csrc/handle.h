@@ -32,6 +32,7 @@ struct map_smoother {
     void* d_lam = nullptr;             // adjoint trajectory (linear models)
     double* d_grad = nullptr;          // gradient accumulators
     void* d_fold = nullptr;            // linear-fold constants of K steps (linear models)
+    double* d_setup = nullptr;         // set-up kernel inputs (SETUP_IN_CAP doubles), then its SetupOut
     int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
     int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
     int launches = 0;                  // kernels of the last solve
@@ -61,10 +62,9 @@ inline size_t fold_bytes(int n, int m, size_t es, long nt)
     const int LS = (3 * n * P + 4 * n * n + 3) / 4 * 4;
     const int PS = (n * n + 2 * ns + 3) / 4 * 4;
     const size_t consts = es * (size_t)(oL + 8 * LS + 128 * PS + 128 * 4 * n * n);
-    const size_t tiles = al(consts) + sizeof(double) * 24 * 3 * n * n + al(es * nt * ns);
-    const size_t e64 = al(tiles + es * nt * n * n);
-    const size_t pi = al(e64 + sizeof(double) * nt * n * n);
-    return pi + (nt <= 4 * 128 + 1 ? 2 * es * (size_t)(nt * (nt + 1) / 2) * n * n : 0);
+    const size_t tiles = al(consts) + sizeof(double) * (24 + 8) * 3 * n * n + al(es * nt * ns);
+    const size_t pi = al(tiles + es * nt * n * n);
+    return pi + (nt <= 4 * 128 + 1 ? al(2 * es * (size_t)(nt * (nt + 1) / 2) * n * n) + es * (size_t)nt * n * n : 0);
 }
 
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.

@@ -99,8 +99,8 @@ struct FoldLayout {
 
 // Per-tile tables of item (4), in the fold buffer after FoldLayout::TOTAL
 // (offsets in bytes): the FP64 (A, C, J) of 2^e full tiles (e < ELMAX, full
-// N x N matrices), then P_j (packed, scalars of S) and F_j = E_j^T (N x N
-// row-major) for j < nt, E_j in FP64, and for scans of at most PI_TILES tiles
+// N x N matrices) and of the tree levels' children (LMAX + 1), then P_j (packed, scalars of S) and F_j = E_j^T (N x N
+// row-major) for j < nt, and for scans of at most PI_TILES tiles
 // the products Pi(a, b) of consecutive tiles' closed-loop maps (item (5)) by
 // rows (a) and their transposes by columns (b).
 template <int N, int M, typename S>
@@ -109,20 +109,29 @@ struct TileTables {
     static constexpr int NN = N * N, NS = Sym<N>::SZ;
     __host__ __device__ static constexpr size_t al(size_t x) { return (x + 15) / 16 * 16; }
     __host__ __device__ static constexpr size_t tl_off() { return al(sizeof(S) * FoldLayout<N, M, S>::TOTAL); }
-    __host__ __device__ static constexpr size_t p_off() { return tl_off() + sizeof(double) * ELMAX * 3 * NN; }
+    // tile levels e < ELMAX, then the tree levels d <= LMAX at ELMAX + d
+    __host__ __device__ static constexpr size_t p_off()
+    {
+        return tl_off() + sizeof(double) * (ELMAX + FoldLayout<N, M, S>::LMAX + 1) * 3 * NN;
+    }
     __host__ __device__ static constexpr size_t f_off(long nt) { return p_off() + al(sizeof(S) * nt * NS); }
-    // E_j in FP64, then (scans of at most PI_TILES tiles) the products
+    // then (scans of at most PI_TILES tiles) the products
     // Pi(a, b) = E_a E_{a+1} ... E_{b-1}, 0 <= a <= b < nt, row a holding b = a..nt-1
     static constexpr long PI_TILES = 4 * 128 + 1;
-    __host__ __device__ static constexpr size_t e_off(long nt) { return al(f_off(nt) + sizeof(S) * nt * NN); }
-    __host__ __device__ static constexpr size_t pi_off(long nt) { return al(e_off(nt) + sizeof(double) * nt * NN); }
+    __host__ __device__ static constexpr size_t pi_off(long nt) { return al(f_off(nt) + sizeof(S) * nt * NN); }
     __host__ __device__ static constexpr long pi_index(long nt, long a, long b) { return a * nt - a * (a - 1) / 2 + (b - a); }
     // then the transposes Q(b, a) = Pi(a, b)^T, row b holding a = 0..b
     __host__ __device__ static constexpr size_t qt_off(long nt) { return pi_off(nt) + sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN; }
     __host__ __device__ static constexpr long qt_index(long b, long a) { return b * (b + 1) / 2 + a; }
+    // then the segment products G(c) = Pi(c, c + PI_SEG) (k_lti_segments)
+    static constexpr int PI_SEG = 16;
+    __host__ __device__ static constexpr size_t g_off(long nt)
+    {
+        return pi_off(nt) + al(2 * sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN);
+    }
     __host__ __device__ static constexpr size_t bytes(long nt)
     {
-        return pi_off(nt) + (nt <= PI_TILES ? 2 * sizeof(S) * (size_t)(nt * (nt + 1) / 2) * NN : 0);
+        return nt <= PI_TILES ? g_off(nt) + sizeof(S) * (size_t)nt * NN : pi_off(nt);
     }
 };
 
@@ -153,120 +162,179 @@ __host__ __device__ constexpr int lti_co_level(int B, int d)
     return 4 * N * N * (B - (B >> d));
 }
 
-// Plan-time helpers of the constant kernels (FP64; n is the state dimension,
-// a compile-time size, and the loops unroll)
-namespace fold_detail {
+// Plan-time helpers of the constant kernels, in FP64 and warp-cooperative: a
+// whole warp calls each one with the same arguments, lane l computes entries
+// l, l + 32, ... of the result, and a __syncwarp() at the end makes the result
+// visible to every lane.  Matrices are n x n row-major (n a compile-time size);
+// outputs are in shared memory and never alias an input.  The FP64 pipe of an
+// SM sub-partition takes a warp instruction at about the same cost however
+// many of its lanes are active, so a chain of small-matrix products spread over
+// the lanes issues about n times fewer FP64 instructions than the same chain in
+// one thread.
+namespace fold_warp {
 
-// c = a b (n x n, row-major)
+__device__ inline int lane() { return threadIdx.x & 31; }
+
+// |x| ordering of finite FP64 values through their bit patterns (no FP64 op)
+__device__ inline unsigned long long absbits(double x)
+{
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+// c = a b
 template <int n>
 __device__ inline void mm(const double* a, const double* b, double* c)
 {
-#pragma unroll
-    for (int i = 0; i < n; ++i)
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < n; ++k) s += a[i * n + k] * b[k * n + j];
-            c[i * n + j] = s;
-        }
-}
-
-// c = a^T (n x n)
-template <int n>
-__device__ inline void tr(const double* a, double* c)
-{
-#pragma unroll
-    for (int i = 0; i < n; ++i)
-#pragma unroll
-        for (int j = 0; j < n; ++j) c[i * n + j] = a[j * n + i];
-}
-
-// y = a x
-template <int n>
-__device__ inline void mv(const double* a, const double* x, double* y)
-{
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;
         double s = 0.0;
 #pragma unroll
-        for (int k = 0; k < n; ++k) s += a[i * n + k] * x[k];
-        y[i] = s;
+        for (int k = 0; k < n; ++k) s = fma(a[i * n + k], b[k * n + j], s);
+        c[q] = s;
     }
+    __syncwarp();
 }
 
-// out = (I + c j)^-1 by Gauss-Jordan elimination with row pivoting; w: 2 n^2 scratch
+// c = a b + d
 template <int n>
-__device__ inline void inv_I_plus(const double* c, const double* j, double* out, double* w)
+__device__ inline void mm_add(const double* a, const double* b, const double* d, double* c)
 {
-    double* X = w;
-    mm<n>(c, j, X);
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;
+        double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < n; ++i) {
-        X[i * n + i] += 1.0;
-#pragma unroll
-        for (int k = 0; k < n; ++k) out[i * n + k] = i == k ? 1.0 : 0.0;
+        for (int k = 0; k < n; ++k) s = fma(a[i * n + k], b[k * n + j], s);
+        c[q] = s + d[q];
     }
+    __syncwarp();
+}
+
+// c = (a b)^T
+template <int n>
+__device__ inline void mm_t(const double* a, const double* b, double* c)
+{
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;         // c[i][j] = (a b)[j][i]
+        double s = 0.0;
 #pragma unroll
+        for (int k = 0; k < n; ++k) s = fma(a[j * n + k], b[k * n + i], s);
+        c[q] = s;
+    }
+    __syncwarp();
+}
+
+// c = a b^T
+template <int n>
+__device__ inline void mm_bt(const double* a, const double* b, double* c)
+{
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) s = fma(a[i * n + k], b[j * n + k], s);
+        c[q] = s;
+    }
+    __syncwarp();
+}
+
+// dst = src (n x n)
+template <int n>
+__device__ inline void copy(const double* src, double* dst)
+{
+    for (int q = lane(); q < n * n; q += 32) dst[q] = src[q];
+    __syncwarp();
+}
+
+// out = (I + c j)^-1 by Gauss-Jordan elimination with row pivoting on the
+// augmented [I + c j | I]; X: n^2 scratch
+template <int n>
+__device__ inline void inv_I_plus(const double* c, const double* j, double* out, double* X)
+{
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, k = q - i * n;
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < n; ++t) s = fma(c[i * n + t], j[t * n + k], s);
+        if (i == k) s += 1.0;
+        X[q] = s;
+        out[q] = i == k ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    constexpr int E = 2 * n * n, R = (E + 31) / 32;
+#pragma unroll 1
     for (int col = 0; col < n; ++col) {
-        int piv = col;
+        int piv = col;                              // first row of largest magnitude
+        unsigned long long best = absbits(X[col * n + col]);
 #pragma unroll
-        for (int r = col + 1; r < n; ++r)
-            if (fabs(X[r * n + col]) > fabs(X[piv * n + col])) piv = r;
-        if (piv != col) {
-#pragma unroll
-            for (int k = 0; k < n; ++k) {
-                double t = X[col * n + k]; X[col * n + k] = X[piv * n + k]; X[piv * n + k] = t;
-                t = out[col * n + k]; out[col * n + k] = out[piv * n + k]; out[piv * n + k] = t;
-            }
+        for (int r = col + 1; r < n; ++r) {
+            const unsigned long long v = absbits(X[r * n + col]);
+            if (v > best) { best = v; piv = r; }
         }
-        const double p = X[col * n + col];
+        const double p = X[piv * n + col];
         const double ip = p != 0.0 ? 1.0 / p : 0.0;
+        // rows col and piv swapped, row col scaled by ip, column col
+        // eliminated from the other rows: all reads first, then all writes
+        double nv[R];
 #pragma unroll
-        for (int k = 0; k < n; ++k) { X[col * n + k] *= ip; out[col * n + k] *= ip; }
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-            if (r == col) continue;
-            const double f = X[r * n + col];
-#pragma unroll
-            for (int k = 0; k < n; ++k) {
-                X[r * n + k] -= f * X[col * n + k];
-                out[r * n + k] -= f * out[col * n + k];
+        for (int t = 0; t < R; ++t) {
+            const int e = lane() + 32 * t;
+            if (e < E) {
+                const int r = e / (2 * n), k = e - r * 2 * n;
+                const double* A = k < n ? X : out;
+                const int kk = k < n ? k : k - n;
+                const double pk = A[piv * n + kk] * ip;
+                const int sr = r == piv ? col : r;
+                nv[t] = r == col ? pk : fma(-X[sr * n + col], pk, A[sr * n + kk]);
             }
         }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = lane() + 32 * t;
+            if (e < E) {
+                const int r = e / (2 * n), k = e - r * 2 * n;
+                (k < n ? X : out)[r * n + (k < n ? k : k - n)] = nv[t];
+            }
+        }
+        __syncwarp();
     }
 }
 
 // coefficients of the (b, eta) part of U (x) D (U the later operand):
 // Mi = (I + C_U J_D)^-1, X = A_D Mi, Y = X C_U, Z = (Mi A_U)^T, W = Z J_D;
-// wk: 4 n^2 scratch
+// wk: 2 n^2 scratch
 template <int n>
 __device__ inline void pair_coeffs(const double* AU, const double* CU, const double* AD, const double* JD,
                                    double* X, double* Y, double* Z, double* W, double* wk)
 {
     double* Mi = wk;
-    double* T = wk + n * n;
-    inv_I_plus<n>(CU, JD, Mi, wk + 2 * n * n);
+    inv_I_plus<n>(CU, JD, Mi, wk + n * n);
     mm<n>(AD, Mi, X);
     mm<n>(X, CU, Y);
-    mm<n>(Mi, AU, T);
-    tr<n>(T, Z);
+    mm_t<n>(Mi, AU, Z);
     mm<n>(Z, JD, W);
 }
 
 // (A, C, J) of U (x) D from the coefficients of pair_coeffs:
-// A = X A_U, C = Y A_D^T + C_D, J = W A_U + J_U; wk: n^2 scratch
+// A = X A_U, C = Y A_D^T + C_D, J = W A_U + J_U
 template <int n>
 __device__ inline void pair_acj(const double* AU, const double* JU, const double* AD, const double* CD,
                                 const double* X, const double* Y, const double* W, double* Ao, double* Co,
-                                double* Jo, double* wk)
+                                double* Jo)
 {
     mm<n>(X, AU, Ao);
-    tr<n>(AD, wk);
-    mm<n>(Y, wk, Co);
-    mm<n>(W, AU, Jo);
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;
+        double s = 0.0, u = 0.0;
 #pragma unroll
-    for (int q = 0; q < n * n; ++q) { Co[q] += CD[q]; Jo[q] += JU[q]; }
+        for (int k = 0; k < n; ++k) {
+            s = fma(Y[i * n + k], AD[j * n + k], s);
+            u = fma(W[i * n + k], AU[k * n + j], u);
+        }
+        Co[q] = s + CD[q];
+        Jo[q] = u + JU[q];
+    }
+    __syncwarp();
 }
 
 // P <- A^T P (I + C P)^-1 A + J, symmetrised (full matrices); w: 4 n^2 scratch
@@ -279,320 +347,413 @@ __device__ inline void riccati(const double* A, const double* C, const double* J
     inv_I_plus<n>(C, P, Mi, w + 3 * n * n);
     mm<n>(Mi, A, T1);                  // (I + C P)^-1 A
     mm<n>(P, T1, T2);                  // P (I + C P)^-1 A
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;
+        double s = J[q];
 #pragma unroll
-    for (int i = 0; i < n; ++i)
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-            double s = J[i * n + j];
-#pragma unroll
-            for (int k = 0; k < n; ++k) s += A[k * n + i] * T2[k * n + j];
-            Mi[i * n + j] = s;
-        }
-#pragma unroll
-    for (int i = 0; i < n; ++i)
-#pragma unroll
-        for (int j = 0; j < n; ++j) P[i * n + j] = 0.5 * (Mi[i * n + j] + Mi[j * n + i]);
+        for (int k = 0; k < n; ++k) s = fma(A[k * n + i], T2[k * n + j], s);
+        Mi[q] = s;
+    }
+    __syncwarp();
+    for (int q = lane(); q < n * n; q += 32) {
+        const int i = q / n, j = q - i * n;
+        P[q] = 0.5 * (Mi[i * n + j] + Mi[j * n + i]);
+    }
+    __syncwarp();
 }
 
-}  // namespace fold_detail
+}  // namespace fold_warp
 
-// One CTA of KMAX threads; thread j carries Gamma_j.  FP64 throughout.  LB:
-// log2 of the threads per tile (B = 2^LB <= BMAX); ne: the tile levels of
-// item (4) to write (2^ne above every tile index).
+// One warp, lane-parallel FP64 (fold_warp).  The K-step fold: its (A, C, J)
+// and the per-step maps (Tb_i, Te_i) of item (1) forward; the Gamma_j then
+// backward, Gamma_j = R_j (0; G) with R_j = U_{K-1} ... U_{j+1} and U_i the map
+// (b, eta) -> (b + Tb_i eta, Te_i eta) of step i.  Then the tree levels of
+// item (2) (also kept in FP64 for k_lti_tables) and the tile levels of item
+// (4).  LB: log2 of the threads per tile (B = 2^LB <= BMAX); ne: the tile
+// levels to write (2^ne above every tile index).
 template <int N, int M, typename S>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(32)
 k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict__ out)
 {
     using FL = FoldLayout<N, M, S>;
     using CL = CoopLayout<N, S>;
-    namespace fd = fold_detail;
+    using TT = TileTables<N, M, S>;
+    namespace fw = fold_warp;
     constexpr int NN = N * N;
-    // accumulated composite (Ac, Cc, Jc), per-step maps (Tb, Te), offsets,
-    // the element's constants, thread-0 scratch and the tree levels' (A, C, J)
-    __shared__ double Ac[NN], Cc[NN], Jc[NN], Tb[NN], Te[NN], ob[N], oe[N];
-    __shared__ double Ae[NN], Ce[NN], Je[NN], be[N], Gm[N * M], Gr[N];
-    __shared__ double Mi[NN], T1[NN], T2[NN], T3[NN], wk[4 * NN], u[N], w[N];
-    __shared__ double LA[FL::LMAX + 1][NN], LC[FL::LMAX + 1][NN], LJ[FL::LMAX + 1][NN];
-    const int j = threadIdx.x;
-    if (j == 0) {
-#pragma unroll 1
-        for (int a = 0; a < N; ++a) {
-#pragma unroll 1
-            for (int c = 0; c < N; ++c) {
-                Ae[a * N + c] = p.A[a * N + c];
-                Ce[a * N + c] = p.C[Sym<N>::at(a, c)];
-                Je[a * N + c] = p.J[Sym<N>::at(a, c)];
-            }
-            be[a] = p.b[a];
-            Gr[a] = p.Gr[a];
-        }
-#pragma unroll 1
-        for (int q = 0; q < N * M; ++q) Gm[q] = p.G[q];
-#pragma unroll 1
-        for (int q = 0; q < NN; ++q) { Ac[q] = Ae[q]; Cc[q] = Ce[q]; Jc[q] = Je[q]; }
-#pragma unroll 1
-        for (int a = 0; a < N; ++a) { ob[a] = be[a]; oe[a] = -Gr[a]; }
+    __shared__ double Ac[NN], Cc[NN], Jc[NN], Ae[NN], Ce[NN], Je[NN], Mi[NN], T1[NN], T2[NN], wk[2 * NN];
+    __shared__ double X[NN], Y[NN], Z[NN], W[NN], Rb[2][NN], Re[2][NN];
+    __shared__ double ob[N], oe[N], be[N], Gr[N], u[N], Gm[N * M];
+    __shared__ double Tb[FL::KMAX][NN], Te[FL::KMAX][NN];
+    const int l = fw::lane();
+    double* tl = reinterpret_cast<double*>(reinterpret_cast<char*>(out) + TT::tl_off());
+    for (int q = l; q < NN; q += 32) {
+        const int a = q / N, c = q - a * N;
+        Ae[q] = Ac[q] = p.A[q];
+        Ce[q] = Cc[q] = p.C[Sym<N>::at(a, c)];
+        Je[q] = Jc[q] = p.J[Sym<N>::at(a, c)];
     }
-    __syncthreads();
-    double gb[N * M], ge[N * M];                  // Gamma_j (b rows, eta rows)
-#pragma unroll 1
-    for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = j == 0 ? Gm[q] : 0.0; }
+    for (int q = l; q < N * M; q += 32) Gm[q] = p.G[q];
+    if (l < N) {
+        be[l] = ob[l] = p.b[l];
+        Gr[l] = p.Gr[l];
+        oe[l] = -p.Gr[l];
+    }
+    __syncwarp();
 #pragma unroll 1
     for (int i = 1; i < K; ++i) {
-        if (j == 0) {
-            fd::inv_I_plus<N>(Ce, Jc, Mi, wk);    // (I + C_e J_acc)^-1
-            fd::mm<N>(Ac, Mi, T1);                // A_acc Mi
-            fd::mm<N>(T1, Ce, Tb);                // Tb = A_acc Mi C_e
-            fd::mm<N>(Mi, Ae, T2);
-            fd::tr<N>(T2, Te);                    // Te = (Mi A_e)^T
-            // offsets: b <- b + Tb eta + A_acc Mi b_e;  eta <- Te (eta - J_acc b_e) - Gr
-            fd::mv<N>(Jc, be, u);
-#pragma unroll 1
-            for (int a = 0; a < N; ++a) u[a] = oe[a] - u[a];
-            fd::mv<N>(Te, u, w);
-            fd::mv<N>(Tb, oe, u);
-#pragma unroll 1
-            for (int a = 0; a < N; ++a) { ob[a] += u[a]; oe[a] = w[a] - Gr[a]; }
-            fd::mv<N>(T1, be, u);
-#pragma unroll 1
-            for (int a = 0; a < N; ++a) ob[a] += u[a];
-            // composite: A = A_acc Mi A_e, C = Tb A_acc^T + C_acc, J = Te J_acc A_e + J_e
-            fd::mm<N>(T1, Ae, T2);
-            fd::tr<N>(Ac, T3);
-            fd::mm<N>(Tb, T3, T1);
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] += T1[q]; }
-            fd::mm<N>(Jc, Ae, T2);
-            fd::mm<N>(Te, T2, T3);
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) Jc[q] = T3[q] + Je[q];
+        fw::inv_I_plus<N>(Ce, Jc, Mi, wk);      // (I + C_e J_acc)^-1
+        fw::mm<N>(Ac, Mi, T1);                  // A_acc Mi
+        fw::mm<N>(T1, Ce, Tb[i]);               // Tb = A_acc Mi C_e
+        fw::mm_t<N>(Mi, Ae, Te[i]);             // Te = (Mi A_e)^T
+        // offsets: b <- b + Tb eta + A_acc Mi b_e;  eta <- Te (eta - J_acc b_e) - Gr
+        if (l < N) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fma(Jc[l * N + k], be[k], s);
+            u[l] = oe[l] - s;
         }
-        __syncthreads();
-        if (j < i) {                              // earlier observations: old eta parts on the right
-            double nb[N * M], nq[N * M];
-#pragma unroll 1
-            for (int a = 0; a < N; ++a)
-#pragma unroll 1
-                for (int c = 0; c < M; ++c) {
-                    double sb = gb[a * M + c], se = 0.0;
-#pragma unroll 1
-                    for (int k = 0; k < N; ++k) {
-                        sb += Tb[a * N + k] * ge[k * M + c];
-                        se += Te[a * N + k] * ge[k * M + c];
-                    }
-                    nb[a * M + c] = sb;
-                    nq[a * M + c] = se;
-                }
-#pragma unroll 1
-            for (int q = 0; q < N * M; ++q) { gb[q] = nb[q]; ge[q] = nq[q]; }
-        } else if (j == i) {
-#pragma unroll 1
-            for (int q = 0; q < N * M; ++q) { gb[q] = 0.0; ge[q] = Gm[q]; }
+        __syncwarp();
+        double nb = 0.0, nq = 0.0;
+        if (l < N) {
+            double te = 0.0, tb = 0.0, tm = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                te = fma(Te[i][l * N + k], u[k], te);
+                tb = fma(Tb[i][l * N + k], oe[k], tb);
+                tm = fma(T1[l * N + k], be[k], tm);
+            }
+            nb = ob[l] + tb + tm;
+            nq = te - Gr[l];
         }
-        __syncthreads();
+        // composite: A = A_acc Mi A_e, C = Tb A_acc^T + C_acc, J = Te J_acc A_e + J_e
+        fw::mm<N>(T1, Ae, T2);                  // new A
+        fw::mm_bt<N>(Tb[i], Ac, X);             // Tb A_acc^T
+        fw::mm<N>(Jc, Ae, Y);
+        fw::mm_add<N>(Te[i], Y, Je, Z);         // new J
+        for (int q = l; q < NN; q += 32) {
+            Ac[q] = T2[q];
+            Cc[q] += X[q];
+            Jc[q] = Z[q];
+        }
+        if (l < N) { ob[l] = nb; oe[l] = nq; }
+        __syncwarp();
     }
-    if (j < K) {
-        S* g = out + FL::oG + j * FL::GS;
-#pragma unroll 1
-        for (int q = 0; q < N * M; ++q) { g[q] = S(gb[q]); g[N * M + q] = S(ge[q]); }
-    }
-    if (j == 0) {
-#pragma unroll 1
-        for (int q = 0; q < NN; ++q) out[FL::oA + q] = S(Ac[q]);
-#pragma unroll 1
-        for (int a = 0; a < N; ++a) {
-#pragma unroll 1
-            for (int c = a; c < N; ++c) {
-                out[FL::oC + Sym<N>::at(a, c)] = S(0.5 * (Cc[a * N + c] + Cc[c * N + a]));
-                out[FL::oJ + Sym<N>::at(a, c)] = S(0.5 * (Jc[a * N + c] + Jc[c * N + a]));
-            }
-            out[FL::ob + a] = S(ob[a]);
-            out[FL::oe + a] = S(oe[a]);
-        }
-        // tree levels: level d holds the constants of its children
-#pragma unroll 1
-        for (int d = 0; d <= LB && d <= FL::LMAX; ++d) {
-            S* lv = out + FL::oL + d * FL::LS;
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) { LA[d][q] = Ac[q]; LC[d][q] = Cc[q]; LJ[d][q] = Jc[q]; }
-#pragma unroll 1
-            for (int a = 0; a < N; ++a)
-#pragma unroll 1
-                for (int c = 0; c < CL::P; ++c) {
-                    const bool in = c < N;
-                    lv[CL::oA + a * CL::P + c] = in ? S(Ac[a * N + c]) : S(0);
-                    lv[CL::oC + a * CL::P + c] = in ? S(0.5 * (Cc[a * N + c] + Cc[c * N + a])) : S(0);
-                    lv[CL::oJ + a * CL::P + c] = in ? S(0.5 * (Jc[a * N + c] + Jc[c * N + a])) : S(0);
-                }
-            if (d == LB) break;
-            fd::pair_coeffs<N>(Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);   // X, Y, Z, W
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) {
-                lv[FL::oX + q] = S(T1[q]);
-                lv[FL::oY + q] = S(Tb[q]);
-                lv[FL::oZ + q] = S(Te[q]);
-                lv[FL::oW + q] = S(T3[q]);
-            }
-            fd::pair_acj<N>(Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
-        }
-        // tile levels (item (4)): (Ac, Cc, Jc) now hold the full tile
-        double* tl = reinterpret_cast<double*>(reinterpret_cast<char*>(out) + TileTables<N, M, S>::tl_off());
-#pragma unroll 1
-        for (int e = 0; e < ne; ++e) {
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) {
-                tl[e * 3 * NN + q] = Ac[q];
-                tl[e * 3 * NN + NN + q] = Cc[q];
-                tl[e * 3 * NN + 2 * NN + q] = Jc[q];
-            }
-            if (e + 1 == ne) break;
-            fd::pair_coeffs<N>(Ac, Cc, Ac, Jc, T1, Tb, Te, T3, wk);
-            fd::pair_acj<N>(Ac, Jc, Ac, Cc, T1, Tb, T3, T2, Mi, wk, wk + NN);
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) { Ac[q] = T2[q]; Cc[q] = Mi[q]; Jc[q] = wk[q]; }
+    for (int q = l; q < NN; q += 32) {
+        const int a = q / N, c = q - a * N;
+        out[FL::oA + q] = S(Ac[q]);
+        if (c >= a) {
+            out[FL::oC + Sym<N>::at(a, c)] = S(0.5 * (Cc[a * N + c] + Cc[c * N + a]));
+            out[FL::oJ + Sym<N>::at(a, c)] = S(0.5 * (Jc[a * N + c] + Jc[c * N + a]));
         }
     }
-    __syncthreads();
-    // thread prefixes, p = j and j + KMAX: pre_p = the fold of p threads (pre_0
-    // the identity) and, for p > 0, co_p.  With 2^d the lowest set bit of p,
-    // pre_p = (level-d node) (x) pre_{p - 2^d}; unrolled over the set bits of p
-    // from the highest (earliest threads) down, pre_p is a product of at most
-    // LB level nodes.  (A sequential recurrence pre_{p+1} = fold (x) pre_p
-    // compounds its rounding errors from thread to thread and is unstable for
-    // models whose interval elements are ill-conditioned.)
-    const int B = 1 << LB;
+    if (l < N) {
+        out[FL::ob + l] = S(ob[l]);
+        out[FL::oe + l] = S(oe[l]);
+    }
+    // Gamma_j, j = K-1 down to 0: R_{K-1} = I, i.e. (Rb, Re) = (0, I), and
+    // R_{j-1} = R_j U_j: Rb <- Tb_j + Rb Te_j, Re <- Re Te_j
+    for (int q = l; q < NN; q += 32) {
+        Rb[0][q] = 0.0;
+        Re[0][q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    int cur = 0;
 #pragma unroll 1
-    for (int p = j; p < B; p += FL::KMAX) {
-        double pA[NN], pC[NN], pJ[NN], X[NN], Y[NN], Z[NN], W[NN], nA[NN], nC[NN], nJ[NN], pw[4 * NN];
-#pragma unroll 1
-        for (int q = 0; q < NN; ++q) {
-            pA[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
-            pC[q] = 0.0;
-            pJ[q] = 0.0;
+    for (int j = K - 1; j >= 0; --j) {
+        S* g = out + FL::oG + j * FL::GS;       // rows 0..N-1: Rb G, rows N..2N-1: Re G
+        for (int q = l; q < 2 * N * M; q += 32) {
+            const bool top = q < N * M;
+            const int r = (top ? q : q - N * M) / M, c = (top ? q : q - N * M) % M;
+            const double* Rm = top ? Rb[cur] : Re[cur];
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fma(Rm[r * N + k], Gm[k * M + c], s);
+            g[q] = S(s);
         }
-#pragma unroll 1
-        for (int d = LB - 1; d >= 0; --d) {
-            if (!((p >> d) & 1)) continue;
-            fd::pair_coeffs<N>(LA[d], LC[d], pA, pJ, X, Y, Z, W, pw);
-            fd::pair_acj<N>(LA[d], LJ[d], pA, pC, X, Y, W, nA, nC, nJ, pw);
-#pragma unroll 1
-            for (int q = 0; q < NN; ++q) { pA[q] = nA[q]; pC[q] = nC[q]; pJ[q] = nJ[q]; }
+        if (j == 0) break;
+        for (int q = l; q < 2 * NN; q += 32) {
+            const bool top = q < NN;
+            const int qq = top ? q : q - NN, a = qq / N, c = qq - a * N;
+            const double* Rm = top ? Rb[cur] : Re[cur];
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fma(Rm[a * N + k], Te[j][k * N + c], s);
+            (top ? Rb[cur ^ 1] : Re[cur ^ 1])[qq] = top ? Tb[j][qq] + s : s;
         }
-        // co_p: the coefficients of the last (lowest-bit) product, p = (2i+1) 2^d
-        // stored as entry i of level d (lti_co_level)
-        if (p > 0) {
-            const int d = __ffs(p) - 1, i = p >> (d + 1), cnt = B >> (d + 1);
-            S* co = out + FL::oCo + lti_co_level<N>(B, d) + i;
+        __syncwarp();
+        cur ^= 1;
+    }
+    // tree levels: level d holds the constants of its children
 #pragma unroll 1
-            for (int q = 0; q < NN; ++q) {
-                co[q * cnt] = S(X[q]);
-                co[(NN + q) * cnt] = S(Y[q]);
-                co[(2 * NN + q) * cnt] = S(Z[q]);
-                co[(3 * NN + q) * cnt] = S(W[q]);
-            }
+    for (int d = 0; d <= LB && d <= FL::LMAX; ++d) {
+        S* lv = out + FL::oL + d * FL::LS;
+        double* lf = tl + (TT::ELMAX + d) * 3 * NN;
+        for (int q = l; q < NN; q += 32) { lf[q] = Ac[q]; lf[NN + q] = Cc[q]; lf[2 * NN + q] = Jc[q]; }
+        for (int q = l; q < N * CL::P; q += 32) {
+            const int a = q / CL::P, c = q - a * CL::P;
+            const bool in = c < N;
+            lv[CL::oA + q] = in ? S(Ac[a * N + c]) : S(0);
+            lv[CL::oC + q] = in ? S(0.5 * (Cc[a * N + c] + Cc[c * N + a])) : S(0);
+            lv[CL::oJ + q] = in ? S(0.5 * (Jc[a * N + c] + Jc[c * N + a])) : S(0);
         }
-        S* pr = out + FL::oPre + p * FL::PS;
+        if (d == LB) break;
+        fw::pair_coeffs<N>(Ac, Cc, Ac, Jc, X, Y, Z, W, wk);
+        for (int q = l; q < NN; q += 32) {
+            lv[FL::oX + q] = S(X[q]);
+            lv[FL::oY + q] = S(Y[q]);
+            lv[FL::oZ + q] = S(Z[q]);
+            lv[FL::oW + q] = S(W[q]);
+        }
+        fw::pair_acj<N>(Ac, Jc, Ac, Cc, X, Y, W, T1, T2, Mi);
+        for (int q = l; q < NN; q += 32) { Ac[q] = T1[q]; Cc[q] = T2[q]; Jc[q] = Mi[q]; }
+        __syncwarp();
+    }
+    // tile levels (item (4)): (Ac, Cc, Jc) now hold the full tile
 #pragma unroll 1
-        for (int a = 0; a < N; ++a) {
+    for (int e = 0; e < ne; ++e) {
+        for (int q = l; q < NN; q += 32) {
+            tl[e * 3 * NN + q] = Ac[q];
+            tl[e * 3 * NN + NN + q] = Cc[q];
+            tl[e * 3 * NN + 2 * NN + q] = Jc[q];
+        }
+        if (e + 1 == ne) break;
+        fw::pair_coeffs<N>(Ac, Cc, Ac, Jc, X, Y, Z, W, wk);
+        fw::pair_acj<N>(Ac, Jc, Ac, Cc, X, Y, W, T1, T2, Mi);
+        for (int q = l; q < NN; q += 32) { Ac[q] = T1[q]; Cc[q] = T2[q]; Jc[q] = Mi[q]; }
+        __syncwarp();
+    }
+}
+
+// Per-warp shared scratch of k_lti_tables
+template <int N>
+union LtiTablesWk {
+    struct { double A[N * N], C[N * N], J[N * N], X[N * N], Y[N * N], Z[N * N], W[N * N], nA[N * N], nC[N * N],
+             nJ[N * N], s[2 * N * N]; } pre;
+    struct { double P[N * N], E[N * N], Mi[N * N], s[4 * N * N]; } tile;
+};
+
+// Thread-prefix tables of item (3), by one warp for p (0 <= p < B): pre_p =
+// the fold of p threads (pre_0 the identity) and, for p > 0, co_p.  With 2^d
+// the lowest set bit of p, pre_p = (level-d node) (x) pre_{p - 2^d}; unrolled
+// over the set bits of p from the highest (earliest threads) down, pre_p is a
+// product of at most LB level nodes (the FP64 levels that k_lti_fold wrote).
+// (A sequential recurrence pre_{p+1} = fold (x) pre_p compounds its rounding
+// errors from thread to thread and is unstable for models whose interval
+// elements are ill-conditioned.)
+template <int N, int M, typename S>
+__device__ void lti_prefix_warp(int pidx, int LB, S* __restrict__ out, LtiTablesWk<N>& wk)
+{
+    using FL = FoldLayout<N, M, S>;
+    using TT = TileTables<N, M, S>;
+    namespace fw = fold_warp;
+    constexpr int NN = N * N;
+    auto& w = wk.pre;
+    const int l = fw::lane(), B = 1 << LB;
+    const double* tl = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::tl_off());
+    for (int q = l; q < NN; q += 32) {
+        w.A[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+        w.C[q] = 0.0;
+        w.J[q] = 0.0;
+    }
+    __syncwarp();
 #pragma unroll 1
-            for (int c = 0; c < N; ++c) pr[a * N + c] = S(pA[a * N + c]);
-#pragma unroll 1
-            for (int c = a; c < N; ++c) {
-                pr[NN + Sym<N>::at(a, c)] = S(0.5 * (pC[a * N + c] + pC[c * N + a]));
-                pr[NN + FL::NS + Sym<N>::at(a, c)] = S(0.5 * (pJ[a * N + c] + pJ[c * N + a]));
-            }
+    for (int d = LB - 1; d >= 0; --d) {
+        if (!((pidx >> d) & 1)) continue;
+        const double* LA = tl + (TT::ELMAX + d) * 3 * NN;
+        fw::pair_coeffs<N>(LA, LA + NN, w.A, w.J, w.X, w.Y, w.Z, w.W, w.s);
+        fw::pair_acj<N>(LA, LA + 2 * NN, w.A, w.C, w.X, w.Y, w.W, w.nA, w.nC, w.nJ);
+        fw::copy<N>(w.nA, w.A);
+        fw::copy<N>(w.nC, w.C);
+        fw::copy<N>(w.nJ, w.J);
+    }
+    // co_p: the coefficients of the last (lowest-bit) product, p = (2i+1) 2^d
+    // stored as entry i of level d (lti_co_level)
+    if (pidx > 0) {
+        const int d = __ffs(pidx) - 1, i = pidx >> (d + 1), cnt = B >> (d + 1);
+        S* co = out + FL::oCo + lti_co_level<N>(B, d) + i;
+        for (int q = l; q < NN; q += 32) {
+            co[q * cnt] = S(w.X[q]);
+            co[(NN + q) * cnt] = S(w.Y[q]);
+            co[(2 * NN + q) * cnt] = S(w.Z[q]);
+            co[(3 * NN + q) * cnt] = S(w.W[q]);
+        }
+    }
+    S* pr = out + FL::oPre + pidx * FL::PS;
+    for (int q = l; q < NN; q += 32) {
+        const int a = q / N, c = q - a * N;
+        pr[q] = S(w.A[q]);
+        if (c >= a) {
+            pr[NN + Sym<N>::at(a, c)] = S(0.5 * (w.C[a * N + c] + w.C[c * N + a]));
+            pr[NN + FL::NS + Sym<N>::at(a, c)] = S(0.5 * (w.J[a * N + c] + w.J[c * N + a]));
         }
     }
 }
 
-// Tile tables of item (4): thread j computes P_j and F_j = E_j^T from the
-// tile levels (written by k_lti_fold) and the prior's P_0.  FP64 throughout.
+// Tile tables of item (4), by one warp for tile j: P_j and F_j = E_j^T from
+// the tile levels (written by k_lti_fold) and the prior's P_0.  FP64.
 template <int N, int M, typename S>
-__global__ void __launch_bounds__(64)
-k_lti_tiles(const Red<N, double> prior, int nt, int ne, S* __restrict__ out)
+__device__ void lti_tile_warp(int j, const Red<N, double>& prior, int nt, int ne, S* __restrict__ out,
+                              LtiTablesWk<N>& wk)
 {
     using TT = TileTables<N, M, S>;
-    namespace fd = fold_detail;
+    namespace fw = fold_warp;
     constexpr int NN = N * N;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nt) return;
+    auto& w = wk.tile;
+    const int l = fw::lane();
     const double* tl = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::tl_off());
-    double P[NN], E[NN], w[5 * NN];
-#pragma unroll 1
-    for (int a = 0; a < N; ++a)
-#pragma unroll 1
-        for (int c = 0; c < N; ++c) P[a * N + c] = prior.P[Sym<N>::at(a, c)];
+    for (int q = l; q < NN; q += 32) {
+        const int a = q / N, c = q - a * N;
+        w.P[q] = prior.P[Sym<N>::at(a, c)];
+    }
+    __syncwarp();
 #pragma unroll 1
     for (int e = ne - 1; e >= 0; --e)
-        if ((j >> e) & 1) fd::riccati<N>(tl + e * 3 * NN, tl + e * 3 * NN + NN, tl + e * 3 * NN + 2 * NN, P, w);
-    fd::inv_I_plus<N>(tl + NN, P, w, w + NN);            // (I + C_T P_j)^-1
-    fd::mm<N>(w, tl, E);                                   // E_j
+        if ((j >> e) & 1) fw::riccati<N>(tl + e * 3 * NN, tl + e * 3 * NN + NN, tl + e * 3 * NN + 2 * NN, w.P, w.s);
+    fw::inv_I_plus<N>(tl + NN, w.P, w.Mi, w.s);           // (I + C_T P_j)^-1
+    fw::mm<N>(w.Mi, tl, w.E);                               // E_j
     S* tp = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::p_off()) + (long)j * Sym<N>::SZ;
     S* tf = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::f_off(nt)) + (long)j * NN;
-    double* te = reinterpret_cast<double*>(reinterpret_cast<char*>(out) + TT::e_off(nt)) + (long)j * NN;
-#pragma unroll 1
-    for (int q = 0; q < NN; ++q) te[q] = E[q];
-#pragma unroll 1
-    for (int a = 0; a < N; ++a) {
-#pragma unroll 1
-        for (int c = a; c < N; ++c) tp[Sym<N>::at(a, c)] = S(P[a * N + c]);
-#pragma unroll 1
-        for (int c = 0; c < N; ++c) tf[a * N + c] = S(E[c * N + a]);
+    for (int q = l; q < NN; q += 32) {
+        const int a = q / N, c = q - a * N;
+        if (c >= a) tp[Sym<N>::at(a, c)] = S(w.P[q]);
+        tf[q] = S(w.E[c * N + a]);
     }
 }
 
-// Products of consecutive full tiles' closed-loop maps (item (5)): thread a
-// writes Pi(a, b) = E_a ... E_{b-1} for b = a..nt-1 (Pi(a, a) = I), in the
-// solve's precision.  Runs after k_lti_tiles, for nt <= PI_TILES.
+// The tables of items (3) and (4) side by side, one warp per item, four warps
+// per block of 128 threads: blocks 0 .. B/4 - 1 (rounded up) take the thread
+// prefixes p, the rest the tiles j, so that both spread over the SMs' FP64
+// pipes at once.  Runs after k_lti_fold.
 template <int N, int M, typename S>
-__global__ void __launch_bounds__(64)
-k_lti_products(int nt, S* __restrict__ out)   // any block size
+__global__ void __launch_bounds__(128)
+k_lti_tables(const Red<N, double> prior, int LB, int nt, int ne, S* __restrict__ out)
+{
+    constexpr int WPB = 4;
+    __shared__ LtiTablesWk<N> wks[WPB];
+    const int wi = threadIdx.x >> 5;
+    const int B = 1 << LB, pre_blocks = (B + WPB - 1) / WPB;
+    if (wi >= WPB) return;
+    if ((int)blockIdx.x < pre_blocks) {
+        const int pidx = blockIdx.x * WPB + wi;
+        if (pidx < B) lti_prefix_warp<N, M, S>(pidx, LB, out, wks[wi]);    // warp-uniform
+    } else {
+        const int j = ((int)blockIdx.x - pre_blocks) * WPB + wi;
+        if (j < nt) lti_tile_warp<N, M, S>(j, prior, nt, ne, out, wks[wi]);
+    }
+}
+
+// Products of consecutive full tiles' closed-loop maps (item (5)),
+// Pi(a, b) = E_a ... E_{b-1} for 0 <= a <= b < nt (Pi(a, a) = I), in the
+// solve's precision (from the tile table F_j = E_j^T: the terms that matter
+// are short products, the long ones have decayed).  A row's chain is cut into segments
+// of PI_SEG tiles so that no thread walks more than about nt / PI_SEG + PI_SEG
+// factors: k_lti_segments forms G(c) = Pi(c, c + PI_SEG), then thread (a, s)
+// of k_lti_products starts from Pi(a, a + s PI_SEG) = G(a) G(a + PI_SEG) ...
+// and walks the E_b of its segment.  Run after k_lti_tables, for nt <= PI_TILES.
+namespace products_detail {
+// E_j from F_j = E_j^T (the tile table in the solve's precision)
+template <int N, typename S>
+__device__ inline void load_E(const S* F, long j, S (&e)[N * N])
+{
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) e[q] = F[j * N * N + (q % N) * N + q / N];
+}
+template <int N, typename S>
+__device__ inline void mul(S (&P)[N * N], const S (&F)[N * N])   // P <- P F
+{
+    S Q[N * N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            S acc = S(0);
+#pragma unroll
+            for (int k = 0; k < N; ++k) acc = fma(P[i * N + k], F[k * N + j], acc);
+            Q[i * N + j] = acc;
+        }
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) P[q] = Q[q];
+}
+}  // namespace products_detail
+
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(128)
+k_lti_segments(int nt, S* __restrict__ out)   // thread c, any block size
 {
     using TT = TileTables<N, M, S>;
-    constexpr int NN = N * N;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nt) return;
-    const double* E = reinterpret_cast<const double*>(reinterpret_cast<const char*>(out) + TT::e_off(nt));
+    namespace pd = products_detail;
+    constexpr int NN = N * N, L = TT::PI_SEG;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c + L > nt - 1) return;                 // G(c) uses E_c .. E_{c+L-1}, E_{nt-2} the last
+    const S* E = reinterpret_cast<const S*>(reinterpret_cast<const char*>(out) + TT::f_off(nt));
+    S* G = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::g_off(nt)) + (long)c * NN;
+    S P[NN], En[NN];
+    pd::load_E<N>(E, c, P);
+    pd::load_E<N>(E, c + 1, En);                // one factor ahead
+#pragma unroll 1
+    for (int b = c + 1; b < c + L; ++b) {
+        S Eb[NN];
+#pragma unroll
+        for (int q = 0; q < NN; ++q) Eb[q] = En[q];
+        if (b + 1 < c + L) pd::load_E<N>(E, b + 1, En);
+        pd::mul<N>(P, Eb);
+    }
+#pragma unroll
+    for (int q = 0; q < NN; ++q) G[q] = P[q];
+}
+
+// thread (a, s): threadIdx.x / 8 + 4 blockIdx.y = a, threadIdx.x % 8 + 8 blockIdx.x = s
+// (blocks of 32 threads)
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(32)
+k_lti_products(int nt, S* __restrict__ out)
+{
+    using TT = TileTables<N, M, S>;
+    namespace pd = products_detail;
+    constexpr int NN = N * N, L = TT::PI_SEG;
+    const int a = blockIdx.y * 4 + (threadIdx.x >> 3), sg = blockIdx.x * 8 + (threadIdx.x & 7);
+    const int b0 = a + sg * L;
+    if (a >= nt || b0 > nt - 1) return;
+    const int b1 = min(b0 + L, nt);             // this thread writes Pi(a, b), b0 <= b < b1
+    const S* E = reinterpret_cast<const S*>(reinterpret_cast<const char*>(out) + TT::f_off(nt));
+    const S* G = reinterpret_cast<const S*>(reinterpret_cast<const char*>(out) + TT::g_off(nt));
     S* pi = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::pi_off(nt));
     S* qt = reinterpret_cast<S*>(reinterpret_cast<char*>(out) + TT::qt_off(nt));
-    // products in the solve's precision (the FP64 E_j rounded): the terms that
-    // matter are short products, the long ones have decayed; registers, N is a
-    // compile-time size
-    S P[NN], En[NN];
+    S P[NN], Fn[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) {
-        P[q] = q % (N + 1) == 0 ? S(1) : S(0);
-        En[q] = S(E[(long)a * NN + q]);             // E_b, loaded one step ahead
+    for (int q = 0; q < NN; ++q) P[q] = q % (N + 1) == 0 ? S(1) : S(0);
+    // Pi(a, b0) = G(a) G(a + L) ... G(a + (sg - 1) L), the next factor loaded ahead
+    if (sg > 0) {
+#pragma unroll
+        for (int q = 0; q < NN; ++q) Fn[q] = G[(long)a * NN + q];
     }
 #pragma unroll 1
-    for (int b = a; b < nt; ++b) {
+    for (int t = 0; t < sg; ++t) {
+        S Ft[NN];
+#pragma unroll
+        for (int q = 0; q < NN; ++q) Ft[q] = Fn[q];
+        if (t + 1 < sg) {
+#pragma unroll
+            for (int q = 0; q < NN; ++q) Fn[q] = G[(long)(a + (t + 1) * L) * NN + q];
+        }
+        pd::mul<N>(P, Ft);
+    }
+    if (b0 + 1 < b1) pd::load_E<N>(E, b0, Fn);
+#pragma unroll 1
+    for (int b = b0; b < b1; ++b) {
         S* o = pi + TT::pi_index(nt, a, b) * NN;
         S* ot = qt + TT::qt_index(b, a) * NN;
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
-            o[q] = S(P[q]);
-            ot[q] = S(P[(q % N) * N + q / N]);
+            o[q] = P[q];
+            ot[q] = P[(q % N) * N + q / N];
         }
-        if (b + 1 == nt) break;
-        S Eb[NN], Q[NN];                            // Pi(a, b + 1) = Pi(a, b) E_b
+        if (b + 1 == b1) break;
+        S Eb[NN];                                   // Pi(a, b + 1) = Pi(a, b) E_b
 #pragma unroll
-        for (int q = 0; q < NN; ++q) {
-            Eb[q] = En[q];
-            if (b + 2 < nt) En[q] = S(E[(long)(b + 1) * NN + q]);
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                S acc = S(0);
-#pragma unroll
-                for (int k = 0; k < N; ++k) acc = fma(P[i * N + k], Eb[k * N + j], acc);
-                Q[i * N + j] = acc;
-            }
-#pragma unroll
-        for (int q = 0; q < NN; ++q) P[q] = Q[q];
+        for (int q = 0; q < NN; ++q) Eb[q] = Fn[q];
+        if (b + 2 < b1) pd::load_E<N>(E, b + 1, Fn);
+        pd::mul<N>(P, Eb);
     }
 }
 

@@ -6,6 +6,9 @@ namespace mapk {
 
 constexpr int MAXN = 8;
 constexpr int MAXM = 8;
+// doubles of the set-up inputs F, c, L, W, H, r, R, m0, P0 at the largest
+// sizes (6 matrices and 3 vectors of order 8), rounded up
+constexpr int SETUP_IN_CAP = 512;
 
 enum SetupFlags { SETUP_SINGULAR_R = 1, SETUP_SINGULAR_P0 = 2, SETUP_SINGULAR_A = 4, SETUP_SINGULAR_Q = 8,
                   SETUP_SINGULAR_C = 16 };

@@ -436,13 +436,19 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
         LtiReduceSmem<N, M, S>::bytes(h.B, h.K, LB) > 200 * 1024)
         return MAP_OK;
     if (h.fold_K != h.K || h.fold_B != h.B) {
-        k_lti_fold<N, M, S><<<1, FL::KMAX, 0, st>>>(lti_params<N, M, double>(h), h.K, LB, ne,
-                                                    static_cast<S*>(h.d_fold));
-        k_lti_tiles<N, M, S><<<(h.nt + 63) / 64, 64, 0, st>>>(prior_of<N, double>(h), h.nt, ne,
-                                                             static_cast<S*>(h.d_fold));
-        if (h.nt <= TT::PI_TILES)
-            // serial FP64 chains, one per tile: spread over many SMs' FP64 units
-            k_lti_products<N, M, S><<<(h.nt + 3) / 4, 4, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
+        // one warp for the serial FP64 chains, then one warp per thread
+        // prefix and per tile in one launch, four to a block so that they
+        // spread over the SMs' FP64 pipes
+        k_lti_fold<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), h.K, LB, ne,
+                                             static_cast<S*>(h.d_fold));
+        k_lti_tables<N, M, S><<<((1 << LB) + 3) / 4 + (h.nt + 3) / 4, 128, 0, st>>>(
+            prior_of<N, double>(h), LB, h.nt, ne, static_cast<S*>(h.d_fold));
+        if (h.nt <= TT::PI_TILES) {
+            const int segs = (h.nt + TT::PI_SEG - 1) / TT::PI_SEG;
+            k_lti_segments<N, M, S><<<(h.nt + 127) / 128, 128, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
+            k_lti_products<N, M, S><<<dim3((segs + 7) / 8, (h.nt + 3) / 4), 32, 0, st>>>(
+                h.nt, static_cast<S*>(h.d_fold));
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
         h.fold_K = h.K;
