@@ -90,8 +90,10 @@ def work_model(n, m, K, B, nt, wbytes, r=None):
 # until the current version has been captured
 K_FILTER_DOWN_DRAM_BYTES = 10482944 + 3812864
 # the same for the single cooperative launch (k_lti_solve) that runs the whole
-# solve when every tile's CTA fits on the GPU at once (ncu capture, cold cache)
-K_SOLVE_DRAM_BYTES = 21929472 + 8958208
+# solve when every tile's CTA fits on the GPU at once; None until the current
+# version (monotone-counter grid barrier) has been captured (the previous
+# version's capture: 21929472 + 8958208 bytes)
+K_SOLVE_DRAM_BYTES = None
 
 
 def solve_bytes(n, m, wbytes):

@@ -36,6 +36,7 @@ struct map_smoother {
     int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
     int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
     int launches = 0;                  // kernels of the last solve
+    unsigned long long bar_arrivals = 0;   // grid-barrier arrivals counted at d_stats[3] so far
     double logq = 0.0, logr = 0.0;     // noise scales of the gradient parameters
     // per-phase timing (map_smoother_profile)
     bool profile = false;

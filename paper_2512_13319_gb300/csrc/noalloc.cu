@@ -204,7 +204,8 @@ extern "C" map_status map_smoother_solve_noalloc(const map_problem_desc* d, cons
     h.d_fold = arr.scratch + fold_off;     // recomputed by every call (fold_K = 0)
     h.fold_K = 0;
     h.d_stats = arr.stats;
-    if ((e = cudaMemsetAsync(arr.stats, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess)
+    // the counters and the grid-barrier arrival count (the stack handle starts at 0)
+    if ((e = cudaMemsetAsync(arr.stats, 0, 4 * sizeof(unsigned long long), st)) != cudaSuccess)
         return noalloc_fail(MAP_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const map_status s = ops->solve(h, y, x_out, nullptr, st);
     h.ws = nullptr;        // the stack handle owns nothing

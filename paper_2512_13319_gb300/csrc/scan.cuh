@@ -1424,42 +1424,42 @@ __host__ __device__ constexpr size_t rts_smem(int B, int K)
 // ---------------------------------------------------------------------------
 // Grid barrier state in global memory: arrivals and generation (both start at
 // zero; the last arrival resets the count before it advances the generation).
+// Grid barrier state: a 64-bit arrival counter that only grows, and the
+// number of arrivals before this launch (kept by the host: every launch adds
+// two barriers' worth, 2 x gridDim.x).  Barrier p of the launch (p = 1, 2)
+// completes when the counter reaches base + p * gridDim.x, so nothing is
+// reset and the last arrival releases the others by its own increment.
 struct GridSync {
-    unsigned int* count;
-    unsigned int* gen;
+    unsigned long long* count;
+    unsigned long long base;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned int* p)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
 constexpr int GRID_SPINS = 1 << 24;         // bounded wait (about a second with the back-off)
 
-// All CTAs of the (co-resident) grid reach this point; the global writes of
+// All CTAs of the (co-resident) grid reach barrier p; the global writes of
 // each CTA before it are visible to all after it.  A wait that runs out counts
 // in stats[2] and lets the CTA continue.
-__device__ __forceinline__ void grid_sync(const GridSync& gs, unsigned long long* stats)
+__device__ __forceinline__ void grid_sync(const GridSync& gs, int p, unsigned long long* stats)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire_u32(gs.gen);
+        const unsigned long long target = gs.base + (unsigned long long)p * gridDim.x;
         __threadfence();
-        if (atomicAdd(gs.count, 1u) == gridDim.x - 1) {
-            atomicExch(gs.count, 0u);
-            __threadfence();
-            atomicAdd(gs.gen, 1u);
-        } else {
-            int n = 0;
-            while (ld_acquire_u32(gs.gen) == g) {
-                if (++n > GRID_SPINS) {
-                    if (stats) atomicAdd(stats + 2, 1ull);
-                    break;
-                }
-                __nanosleep(64);
+        atomicAdd(gs.count, 1ull);
+        int n = 0;
+        while (ld_acquire_u64(gs.count) < target) {
+            if (++n > GRID_SPINS) {
+                if (stats) atomicAdd(stats + 2, 1ull);
+                break;
             }
+            __nanosleep(64);
         }
         __threadfence();
     }
@@ -1607,7 +1607,7 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
                 lt.w[j * N + a] = acc;
             }
         }
-        grid_sync(gs, ctx.stats);
+        grid_sync(gs, 1, ctx.stats);
 
         // ---- phase 2: tile prefix, thread prefixes, per-step filter, tile map
         Red<N, S> pin, X;
@@ -1641,7 +1641,7 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
             block_aff_reduce<N, S>(H, red);
             if (t == 0) aos_store(tile_aff, (long)tile, H);
         }
-        grid_sync(gs, ctx.stats);
+        grid_sync(gs, 2, ctx.stats);
 
         // ---- phase 3: tile suffix, thread end states, per-step states, bulk store
         S* st = sm + FS::stage(B);

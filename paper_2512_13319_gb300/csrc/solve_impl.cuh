@@ -222,8 +222,15 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         if (lti) sh_down = LtiDownSmem<N, Prod::W, S>::bytes(B, K, lt.co_smem);
         // single cooperative launch when every tile's CTA can be resident at once
         // (one group of tiles, 16-byte aligned observations, no per-phase events)
+        // (not under stream capture: the launch's grid-barrier base would be
+        // fixed in the graph, while the arrival counter keeps growing)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+            cudaGetLastError();
+            cap = cudaStreamCaptureStatusActive;
+        }
         if (lti && lt.pi && !dev_prior && !h.profile && nt > 1 && nt - 1 <= G &&
-            (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0) {
+            cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0) {
             const size_t sh = FusedSmem<N, Prod::W, S>::bytes(B, K);
             if (h.fused < 0) {
                 int nb = 0, sms = 0;
@@ -235,8 +242,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                 cudaGetLastError();
             }
             if (h.fused == 1) {
-                unsigned int* gw = reinterpret_cast<unsigned int*>(h.d_stats + 3);
-                const GridSync gs{gw, gw + 1};
+                const GridSync gs{h.d_stats + 3, h.bar_arrivals};
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(nt);
                 cfg.blockDim = dim3(B);
@@ -251,6 +257,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                                                    Eg, tile_aff, filt_out, ctx, fin, x_out, filtT, form, gs);
                 if (e == cudaSuccess) {
                     h.launches += 1;
+                    h.bar_arrivals += 2ull * (unsigned long long)nt;   // the launch's two grid barriers
                     return MAP_OK;
                 }
                 // the grid cannot be resident at once after all (e.g. another
