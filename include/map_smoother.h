@@ -109,7 +109,11 @@ map_status map_smoother_create(map_smoother** out, const map_problem_desc* desc)
  *             for nonlinear models those of the last iteration.
  *   cost_out  host or NULL: the discrete Onsager-Machlup cost of x_out (needs an
  *             invertible Q; synchronises the stream).
- * Asynchronous on `stream` unless cost_out is given.
+ * Asynchronous on `stream` unless cost_out is given.  Calls on one handle
+ * must be ordered (one stream, or synchronised between streams): the handle's
+ * workspace and its grid-barrier counter are shared by its solves.  Under
+ * stream capture the solve records the multi-kernel pipeline (the single
+ * cooperative launch keeps per-launch state that a graph replay would reuse).
  */
 map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void* filt_out,
                               double* cost_out, void* stream);
@@ -203,7 +207,7 @@ map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* til
 /*
  * Kernels launched by the handle's last solve (host-side read): 1 when the
  * linear time-invariant RTS solve ran as one cooperative launch (all tiles'
- * CTAs resident at once), otherwise the number of kernels of the scan
+ * CTAs resident at once, not under stream capture), otherwise the number of kernels of the scan
  * pipeline (plan-time constant kernels not counted); 0 before the first solve.
  * Returns MAP_ERR_INVALID_ARG for a NULL argument.
  */
