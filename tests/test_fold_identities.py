@@ -9,7 +9,9 @@ pin the derivations its plan-time and per-solve kernels evaluate:
   Gamma_i formed backward from those maps);
 * the composition of the per-step closed-loop maps (Section 3.5, Eq. 40-41)
   of a run of elements equals the closed-loop map of their combined element,
-  which lets the tile-end states be sums over a table of tile-map products.
+  which lets the tile-end states be sums over a table of tile-map products;
+* the coefficient form of a combine's (b, eta) part (tree levels and thread
+  prefixes) and the tile Riccati recursion evaluated by doubling.
 """
 import numpy as np
 import pytest
@@ -94,3 +96,67 @@ def test_composed_closed_loop_maps_are_the_combined_elements_map(n, m, K):
     Phi2, beta2 = closed_loop(Af, bf, Cf, S[k0], v[k0])
     assert np.abs(Phi - Phi2).max() <= 1e-10 * max(1.0, np.abs(Phi).max())
     assert np.abs(beta - beta2).max() <= 1e-10 * max(1.0, np.abs(beta).max())
+
+
+def pair(U, D, n):
+    """U (x) D (U the later operand) by the coefficient form of items (2)-(3):
+    Mi = (I + C_U J_D)^-1, X = A_D Mi, Y = X C_U, Z = (Mi A_U)^T, W = Z J_D;
+    b = X b_U + Y eta_D + b_D, eta = eta_U + Z eta_D - W b_U,
+    A = X A_U, C = Y A_D^T + C_D, J = W A_U + J_U."""
+    AU, bU, CU, eU, JU = oracle.unpack_element(U, n)
+    AD, bD, CD, eD, JD = oracle.unpack_element(D, n)
+    Mi = np.linalg.inv(np.eye(n) + CU @ JD)
+    X = AD @ Mi
+    Y = X @ CU
+    Z = (Mi @ AU).T
+    W = Z @ JD
+    return (X @ AU, X @ bU + Y @ eD + bD, Y @ AD.T + CD, eU + Z @ eD - W @ bU, W @ AU + JU)
+
+
+@pytest.mark.parametrize("n,m", [(4, 2), (2, 1), (6, 3)])
+def test_pair_coefficients_reproduce_the_combine(n, m):
+    """Items (2)-(3): the (b, eta) of a combine is a fixed linear map of the
+    operands' (b, eta), with coefficients from their (A, C, J) alone; checked
+    on folds of different lengths (different constants on each side)."""
+    elems, _ = lti_elements(n, m, 12, seed=3 * n)
+    U = elems[5]
+    for k in range(6, 9):
+        U = oracle.combine(elems[k], U, n)          # a fold of 4 steps
+    D = elems[0]
+    for k in range(1, 5):
+        D = oracle.combine(elems[k], D, n)          # a fold of 5 steps
+    ref = oracle.unpack_element(oracle.combine(U, D, n), n)
+    got = pair(U, D, n)
+    for r, g in zip(ref, got):
+        assert np.abs(g - r).max() <= 1e-11 * max(1.0, np.abs(r).max())
+
+
+@pytest.mark.parametrize("n,m", [(4, 2), (3, 1)])
+def test_tile_riccati_by_doubling(n, m):
+    """Item (4): the P part of the value function before full tile j follows
+    P_{j+1} = A_T^T P_j (I + C_T P_j)^-1 A_T + J_T from the prior's P_0; the
+    plan computes it for every j at once by applying the doubled tile
+    elements (2^e tiles) of the set bits of j, highest first."""
+    elems, model = lti_elements(n, m, 6 * 50, seed=7 * n)
+    S, _ = oracle.filter_by_combine(elems, model.m0, model.P0)
+    tile = elems[0]
+    for k in range(1, 6):
+        tile = oracle.combine(elems[k], tile, n)    # a tile of 6 steps
+
+    def ric(el, P):
+        A, _, C, _, J = oracle.unpack_element(el, n)
+        return A.T @ P @ np.linalg.solve(np.eye(n) + C @ P, A) + J
+
+    levels = [tile]
+    for _ in range(6):
+        levels.append(oracle.combine(levels[-1], levels[-1], n))
+    P0 = np.linalg.inv(model.P0)
+    P = P0.copy()
+    for j in range(1, 50):
+        P = ric(tile, P)                            # sequential, j tiles
+        assert np.abs(P - S[6 * j]).max() <= 1e-10 * max(1.0, np.abs(P).max())   # the filter's S
+        Q = P0.copy()
+        for e in range(len(levels) - 1, -1, -1):
+            if (j >> e) & 1:
+                Q = ric(levels[e], Q)
+        assert np.abs(Q - P).max() <= 1e-10 * max(1.0, np.abs(P).max()), j
