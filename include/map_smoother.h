@@ -164,8 +164,12 @@ map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, cons
 
 /*
  * Set theta = (F, log q, log r) of the handle (F NULL keeps F) and redo the
- * device set-up (discretisation); synchronises the device.  For training loops
- * that differentiate through the solve.
+ * device set-up (discretisation); synchronises the device.  The plan-time
+ * constants of linear time-invariant models (folds, tile tables, tile-map
+ * products) are recomputed by the next solve, on its stream.  For training
+ * loops that differentiate through the solve.  Returns MAP_ERR_INVALID_ARG
+ * for non-finite log_q or log_r and MAP_ERR_SINGULAR when the updated R or
+ * interval map A is singular.
  */
 map_status map_smoother_update(map_smoother* h, const double* F, double log_q, double log_r);
 
