@@ -8,6 +8,7 @@
 #include <cstdio>
 #include "../paper_2512_13319_gb300/csrc/handle.h"
 #include "../paper_2512_13319_gb300/csrc/lti_fold.cuh"
+#include "../paper_2512_13319_gb300/csrc/scan.cuh"
 
 template <int N, int M, typename S>
 static int check()
@@ -28,14 +29,41 @@ static int check()
     return bad;
 }
 
+// Shared memory of the single-launch solve: every area that a bulk copy
+// writes or reads (observations, Gamma_i, level constants, co table, staged
+// states) starts on a 16-byte boundary and the mbarriers on an 8-byte one,
+// for every tile size and steps per thread.
+template <int N, int M, typename S>
+static int check_fused()
+{
+    using FS = mapk::FusedSmem<N, M, S>;
+    int bad = 0;
+    for (int B = 32; B <= 128; B *= 2)
+        for (int K = 1; K <= 64; ++K) {
+            const size_t w = sizeof(S);
+            bool ok = FS::ys(B) * w % 16 == 0 && FS::gam(B, K) * w % 16 == 0 && FS::lv(B, K) * w % 16 == 0 &&
+                      FS::co(B, K) * w % 16 == 0 && FS::bar(B, K) * w % 8 == 0 && FS::stage(B) * w % 16 == 0 &&
+                      FS::bytes(B, K) >= (size_t)FS::end(B, K) * w;
+            if (!ok && bad++ < 3) std::printf("fused N=%d M=%d S=%zu B=%d K=%d\n", N, M, w, B, K);
+        }
+    return bad;
+}
+
 int main()
 {
+    int fb = 0;
+    fb += check_fused<2, 1, float>() + check_fused<2, 1, double>();
+    fb += check_fused<3, 1, float>() + check_fused<3, 1, double>();
+    fb += check_fused<4, 2, float>() + check_fused<4, 2, double>();
+    fb += check_fused<5, 2, float>() + check_fused<5, 2, double>();
+    fb += check_fused<6, 3, float>() + check_fused<6, 3, double>();
     int bad = 0;
     bad += check<2, 1, float>() + check<2, 1, double>();
     bad += check<3, 1, float>() + check<3, 1, double>();
     bad += check<4, 2, float>() + check<4, 2, double>();
     bad += check<5, 2, float>() + check<5, 2, double>();
     bad += check<6, 3, float>() + check<6, 3, double>();
+    bad += fb;
     std::printf(bad ? "FAIL %d\n" : "OK\n", bad);
     return bad ? 1 : 0;
 }
