@@ -6,6 +6,7 @@
 // every table read by bulk copies or 16-byte loads starts on a 16-byte
 // boundary.
 #include <cstdio>
+#include <vector>
 #include "../paper_2512_13319_gb300/csrc/handle.h"
 #include "../paper_2512_13319_gb300/csrc/lti_fold.cuh"
 #include "../paper_2512_13319_gb300/csrc/scan.cuh"
@@ -49,9 +50,38 @@ static int check_fused()
     return bad;
 }
 
+// The product table's row index pi_index(nt, a, b) (row a holding b = a..nt-1)
+// and the transposes' qt_index(b, a) (row b holding a = 0..b) each number the
+// nt (nt + 1) / 2 pairs a <= b once, rows contiguous.
+static int check_product_indices()
+{
+    using TT = mapk::TileTables<4, 2, float>;
+    int bad = 0;
+    for (long nt = 1; nt <= TT::PI_TILES; nt += (nt < 40 ? 1 : 37)) {
+        const long tri = nt * (nt + 1) / 2;
+        std::vector<int> seen_pi(tri, 0), seen_qt(tri, 0);
+        long expect_pi = 0;
+        for (long a = 0; a < nt; ++a)
+            for (long b = a; b < nt; ++b) {
+                const long i = TT::pi_index(nt, a, b);
+                if (i != expect_pi++ || i < 0 || i >= tri) { ++bad; continue; }
+                ++seen_pi[i];
+            }
+        for (long b = 0; b < nt; ++b)
+            for (long a = 0; a <= b; ++a) {
+                const long i = TT::qt_index(b, a);
+                if (i < 0 || i >= tri || (a > 0 && i != TT::qt_index(b, a - 1) + 1)) { ++bad; continue; }
+                ++seen_qt[i];
+            }
+        for (long i = 0; i < tri; ++i) bad += (seen_pi[i] != 1) + (seen_qt[i] != 1);
+    }
+    if (bad) std::printf("product indices: %d bad\n", bad);
+    return bad;
+}
+
 int main()
 {
-    int fb = 0;
+    int fb = check_product_indices();
     fb += check_fused<2, 1, float>() + check_fused<2, 1, double>();
     fb += check_fused<3, 1, float>() + check_fused<3, 1, double>();
     fb += check_fused<4, 2, float>() + check_fused<4, 2, double>();
