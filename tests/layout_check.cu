@@ -79,9 +79,36 @@ static int check_product_indices()
     return bad;
 }
 
+// The right-child coefficient table co_p by tree level (lti_co_level): entry
+// i = p >> (d + 1) of level d, p = (2i + 1) 2^d, component q at q * cnt + i
+// with cnt = B >> (d + 1); the B - 1 entries of 4 N^2 components fill the
+// 4 N^2 (B - 1) scalars once.
+template <int N>
+static int check_co_levels()
+{
+    int bad = 0;
+    for (int B = 2; B <= 128; B *= 2) {
+        const int total = 4 * N * N * (B - 1);
+        std::vector<int> seen(total, 0);
+        for (int p = 1; p < B; ++p) {
+            const int d = __builtin_ctz(p), i = p >> (d + 1), cnt = B >> (d + 1);
+            for (int q = 0; q < 4 * N * N; ++q) {
+                const int o = mapk::lti_co_level<N>(B, d) + q * cnt + i;
+                if (o < 0 || o >= total) { ++bad; continue; }
+                ++seen[o];
+            }
+        }
+        for (int o = 0; o < total; ++o) bad += seen[o] != 1;
+    }
+    if (bad) std::printf("co levels N=%d: %d bad\n", N, bad);
+    return bad;
+}
+
 int main()
 {
     int fb = check_product_indices();
+    fb += check_co_levels<2>() + check_co_levels<3>() + check_co_levels<4>() + check_co_levels<5>() +
+          check_co_levels<6>();
     fb += check_fused<2, 1, float>() + check_fused<2, 1, double>();
     fb += check_fused<3, 1, float>() + check_fused<3, 1, double>();
     fb += check_fused<4, 2, float>() + check_fused<4, 2, double>();
