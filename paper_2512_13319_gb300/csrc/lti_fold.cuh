@@ -166,11 +166,11 @@ __host__ __device__ constexpr int lti_co_level(int B, int d)
 // whole warp calls each one with the same arguments, lane l computes entries
 // l, l + 32, ... of the result, and a __syncwarp() at the end makes the result
 // visible to every lane.  Matrices are n x n row-major (n a compile-time size);
-// outputs are in shared memory and never alias an input.  The FP64 pipe of an
-// SM sub-partition takes a warp instruction at about the same cost however
-// many of its lanes are active, so a chain of small-matrix products spread over
-// the lanes issues about n times fewer FP64 instructions than the same chain in
-// one thread.
+// inputs may be in global or shared memory, outputs are in shared memory and
+// never alias an input.  The FP64 pipe of an SM sub-partition takes a warp
+// instruction at about the same cost however many of its lanes are active, so
+// a product spread over the lanes (one entry per lane) issues n FP64
+// instructions per lane-round instead of n^3 in one thread.
 namespace fold_warp {
 
 __device__ inline int lane() { return threadIdx.x & 31; }
