@@ -24,3 +24,29 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_extras_are_checked_against_the_oracle_in_the_cpu_baseline_leg():
+    """bench.py's extras hand their GPU results to oracle_checks (run only in
+    the CPU-baseline leg); here with stand-in results: the exact oracle output
+    gives 0, a perturbed one its relative error, several checks under one key
+    keep the largest, and an extra that failed keeps its error."""
+    import sys
+    import numpy as np
+    import oracle
+    from paper_2512_13319_gb300 import synth
+    sys.path.insert(0, ROOT)
+    import bench
+
+    model = synth.wiener_velocity(2)
+    _, y = synth.simulate(model, 200, 0.01, seed=3)
+    x = oracle.smooth_lti(model, y, 0.01)
+    out = {"a": {"ms": 1.0}, "b": {"ms": 1.0}, "c": {"error": "RuntimeError: x"}}
+    checks = [("a", "rel_err_vs_oracle", "smooth_lti", (model, y, 0.01), x),
+              ("b", "max_err", "smooth_lti", (model, y, 0.01), x),
+              ("b", "max_err", "smooth_lti", (model, y, 0.01), 1.01 * x),
+              ("c", "rel_err_vs_oracle", "smooth_lti", (model, y, 0.01), x)]
+    bench.oracle_checks(out, checks)
+    assert out["a"]["rel_err_vs_oracle"] == 0.0
+    assert abs(out["b"]["max_err"] - 0.01) < 1e-12
+    assert "rel_err_vs_oracle" not in out["c"]
