@@ -198,7 +198,8 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_run * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": Ts, "nx": 4, "ny": 2, "precision": "fp64"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
@@ -273,6 +274,8 @@ def ours(args):
     time.sleep(0.25)
     sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # the output of the last timed solve, kept before any other solve reuses x
+    x_timed = x.clone()
     kernels_per_solve = sm.launches()          # of the timed solves
     ms_mean = max_over_ranks(sum(step_ms) / args.steps)
     ms = max_over_ranks(statistics.median(step_ms))      # median step time, max over ranks
@@ -306,12 +309,18 @@ def ours(args):
     phase_ms = {k: statistics.median(v) for k, v in phases.items()}
     K_g, B_g, nt_g = sm.geometry()
     flops, byt = work_model(4, 2, K_g, B_g, nt_g, wbytes, r=2)
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    alu_peak = fp32_peak if prec == "fp32" else fp32_peak / 64.0
-    peak_source = ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts and max clock)"
-                   if prec == "fp32" else "FP32 figure / 64")
+    try:
+        fma = measure_fma_peaks(dev, stream)
+        alu_peak = fma["fp32"] if prec == "fp32" else fma["fp64"]
+        peak_source = (f"measured on this GPU by map_fma_peak ({'FP32' if prec == 'fp32' else 'FP64'}, "
+                       f"SM clock median {fma['clocks'].get('sm_mhz')} MHz during it)")
+    except Exception as e:           # keep the line; fall back to unit counts
+        fma = {"error": f"{type(e).__name__}: {e}"[:200]}
+        fp32_nominal = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        alu_peak = fp32_nominal if prec == "fp32" else fp32_nominal / 64.0
+        peak_source = "nominal unit counts (map_fma_peak failed)"
     if kernels_per_solve == 1:
         # one cooperative launch runs the whole solve: its duration is the
         # timed solve, its work the three phases' work
@@ -341,7 +350,6 @@ def ours(args):
     # kernels of one timed solve, as the library reports them (1 for the single
     # cooperative launch; else reduce, group totals, filter down-sweep, RTS pass)
     launches_per_solve = kernels_per_solve
-    x_last = x
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -354,6 +362,7 @@ def ours(args):
         "ms_per_step_mean": ms_mean,
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_solve * args.steps, "roofline": roofline,
         "phases": per_phase, "hbm": hbm, "fp64_recomputes": fb, "singular_pivots": sing, "copy_wait_timeouts": timeouts,
+        "fma_peaks_tflops": fma,
     }
     sm.close()
 
@@ -389,12 +398,18 @@ def ours(args):
         oracle.build()
         t_run, runs, x_ref = time_oracle(model, y_np, 10.0)
         result["cpu_baseline"] = {"value": T / t_run, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                  "sample": f"the full T=2^20 workload, {runs} runs (FP64 KF + RTS, plain C)"}
-        # relative trajectory error of the timed solve's output against the oracle
-        x_gpu = x_last.double().cpu().numpy()
+                                  "sample": f"the full T=2^20 workload, {runs} runs (FP64 KF + RTS, plain C)",
+                                  **host_cpu()}
+        # error of the last timed solve's own output against the oracle
+        x_gpu = x_timed.double().cpu().numpy()
         result["rel_err_vs_oracle"] = float(np.linalg.norm(x_gpu - x_ref) / np.linalg.norm(x_ref))
+        result["max_abs_err_rel_to_max_vs_oracle"] = float(np.abs(x_gpu - x_ref).max() / np.abs(x_ref).max())
         if checks and "extras" in result:
             oracle_checks(result["extras"], checks)
+    elif "extras" in result:
+        for name, key, *_ in checks:
+            if isinstance(result["extras"].get(name), dict) and "error" not in result["extras"][name]:
+                result["extras"][name][key] = "not checked (CPU-baseline leg skipped)"
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -416,6 +431,68 @@ def timed(fn, flush, stream, dev, reps=3):
         torch.cuda.synchronize(dev)
         times.append(a.elapsed_time(b))
     return statistics.median(times)
+
+
+def measure_fma_peaks(dev, stream):
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s), measured with the
+    library's map_fma_peak kernels (8 CTAs x 256 threads per SM, 8 independent
+    chains per thread), best of 5 launches of about 50 ms each, with the SM
+    clock sampled during them."""
+    import torch
+
+    from paper_2512_13319_gb300 import _binding as B
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    t0 = time.time()
+    out = {}
+    st = stream.cuda_stream
+    for name, kind, iters in (("fp32_ffma", B.FMA_FP32, 50_000), ("fp32_ffma2", B.FMA_FP32X2, 25_000),
+                              ("fp64_dfma", B.FMA_FP64, 750)):
+        B.map_fma_peak(kind, max(1, iters // 10), st)       # warm-up
+        best = 0.0
+        for _ in range(5):
+            flop, ms = B.map_fma_peak(kind, iters, st)
+            best = max(best, flop / (ms * 1e-3) / 1e12)
+        out[name] = best
+    t1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    out["clocks"] = sampler.summary(t0, t1)
+    out["fp32"] = max(out["fp32_ffma"], out["fp32_ffma2"])
+    out["fp64"] = out["fp64_dfma"]
+    out["how"] = ("map_fma_peak: 8 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
+                  "best of 5 launches of ~50 ms; fp32 = max(scalar FFMA, paired FFMA2)")
+    return out
+
+
+def host_cpu():
+    """CPU model and logical core count of this host (for the CPU baselines)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
 
 
 def rel_err(a, b):
@@ -550,7 +627,10 @@ def extras(dev, flush, stream):
 def oracle_checks(out, checks):
     """CPU-baseline leg: each extra's GPU result against the FP64 oracle on the
     same inputs (relative Frobenius error; several checks under one key keep the
-    largest).  A failing check records its error text instead."""
+    largest).  A check that raises records its error text under
+    ``<key>_errors``; the numeric key keeps the largest error of the others."""
+    import numpy as np
+
     import oracle
     for name, key, fn, args, got in checks:
         if not isinstance(out.get(name), dict) or "error" in out[name]:
@@ -562,8 +642,19 @@ def oracle_checks(out, checks):
             err = rel_err(got, ref)
             prev = out[name].get(key)
             out[name][key] = err if not isinstance(prev, float) else max(prev, err)
+            if fn == "grad_lti":          # per-block errors of (F, log q, log r)
+                n2 = len(ref) - 2
+                out[name]["rel_err_F_block"] = rel_err(got[:n2], ref[:n2])
+                out[name]["rel_err_log_q"] = abs(got[n2] - ref[n2]) / abs(ref[n2])
+                out[name]["rel_err_log_r"] = abs(got[n2 + 1] - ref[n2 + 1]) / abs(ref[n2 + 1])
+                out[name]["max_abs_err_F_rel_to_max_F"] = float(np.abs(got[:n2] - ref[:n2]).max()
+                                                                / np.abs(ref[:n2]).max())
+            else:
+                mx = float(np.abs(np.asarray(got) - ref).max() / np.abs(ref).max())
+                pk = "max_abs_err_rel_to_max"
+                out[name][pk] = mx if not isinstance(out[name].get(pk), float) else max(out[name][pk], mx)
         except Exception as e:          # report, do not lose the main line
-            out[name][key] = f"{type(e).__name__}: {e}"[:200]
+            out[name].setdefault(key + "_errors", []).append(f"{type(e).__name__}: {e}"[:200])
 
 
 def sequential_gpu(model, y, dtype, dev, flush, stream):

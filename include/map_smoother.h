@@ -229,14 +229,18 @@ map_status map_smoother_launches(const map_smoother* h, int* kernels);
  * has run holds until the process exits.  No cudaMalloc, cudaFree or other
  * allocating routine is called.
  *   desc   problem description as for map_smoother_create (MAP_MODEL_LINEAR,
- *          smoother MAP_RTS); T limited by the 64 MiB scratch (about 6e5
- *          intervals at nx = 4 in FP32), beyond which MAP_ERR_SHAPE is returned
- *          with a message naming the bytes needed.
+ *          smoother MAP_RTS); the launch geometry is fixed (16 steps per
+ *          thread, 128 threads per tile; desc->tile_threads is ignored), and T
+ *          is limited by the 64 MiB scratch: at most 632 832 intervals at
+ *          nx = 4, ny = 2 in FP32 (329 728 in FP64).  Beyond the limit
+ *          MAP_ERR_SHAPE is returned with a message naming the bytes needed.
  *   y, x_out  device arrays as for map_smoother_solve.
  * The model set-up synchronises `stream`; the solve kernels are then enqueued
- * on it asynchronously.  The first call on a device (with that device current)
- * looks up the device addresses of the arrays; make it before any stream
- * capture.  All calls share the arrays and they keep the last call's contents
+ * on it asynchronously.  Every call, with the target device current, looks up
+ * the device addresses of the arrays (cudaGetSymbolAddress, which allocates
+ * nothing; not cached, so a context re-created after cudaDeviceReset is
+ * handled).  The first call on a device loads the module; make it before any
+ * stream capture.  All calls share the arrays and they keep the last call's contents
  * (the precision-policy counters are cleared by each call); calls that overlap
  * on the GPU race and must be serialised by the caller.  Failures are described
  * by map_smoother_last_error(NULL).
@@ -245,8 +249,8 @@ map_status map_smoother_solve_noalloc(const map_problem_desc* desc, const void* 
                                       void* stream);
 
 /*
- * Batches of independent trajectories (row a9 of the build: thousands of
- * trajectories of uneven length and state dimension in one launch).
+ * Batches of independent trajectories (thousands of trajectories of uneven
+ * length and state dimension in one launch).
  * models[m] describes a linear model (desc.T is ignored, smoother MAP_RTS);
  * trajectory j has lengths[j] >= 1 intervals of model model_of[j].
  * All trajectories of one model are solved as ONE scan: they are concatenated
@@ -284,6 +288,18 @@ const char* map_smoother_last_error(const map_smoother* h);
 
 /* 1 when kernels for (model, nx, ny, precision) are compiled in, else 0. */
 int map_smoother_supported(int model, int nx, int ny, int precision);
+
+/*
+ * FMA throughput of the current device (no counterpart in the paper: the
+ * measured denominator of the ALU rooflines of this library's kernels).
+ * Launches 8 CTAs of 256 threads per SM, each thread running 8 independent
+ * multiply-add chains for iters x 16 rounds, timed with CUDA events on
+ * `stream` (synchronises it).  kind: 0 FP32 FFMA, 1 FP32 paired FMA (f32x2,
+ * two per instruction), 2 FP64 DFMA.  *flop_out receives the flops executed
+ * (2 per multiply-add), *ms_out the device time.  MAP_ERR_INVALID_ARG for a
+ * NULL output, iters < 1 or an unknown kind; MAP_ERR_CUDA if a CUDA call fails.
+ */
+map_status map_fma_peak(int kind, int iters, double* flop_out, float* ms_out, void* stream);
 
 /* Library version string. */
 const char* map_smoother_version(void);

@@ -26,6 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 KIND_LINEAR, KIND_CT, KIND_CUBIC = 0, 1, 2
+# model kind names carried by the model objects the tests pass in
+_KIND_BY_NAME = {"linear": KIND_LINEAR, "coord_turn": KIND_CT, "cubic": KIND_CUBIC}
 
 
 def build(force: bool = False) -> str:
@@ -202,8 +204,7 @@ def smooth_lti(model, y, dt, mode=EULER, smoother=RTS, return_filter=False):
 
 
 def _kind_of(model):
-    from paper_2512_13319_gb300 import synth
-    return {synth.LINEAR: KIND_LINEAR, synth.COORD_TURN: KIND_CT, synth.CUBIC: KIND_CUBIC}[model.kind]
+    return _KIND_BY_NAME[model.kind]
 
 
 def _model_arrays(model):

@@ -64,6 +64,7 @@ EXPORTS = {
     "map_batch_tuning": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "map_batch_last_error": (_CH, [_VP]),
     "map_batch_destroy": (None, [_VP]),
+    "map_fma_peak": (_I, [_I, _I, _D, ctypes.POINTER(ctypes.c_float), _VP]),
 }
 
 _lib = None
@@ -170,6 +171,18 @@ def map_smoother_geometry(h):
     K, Bt, nt = _I(), _I(), _I()
     _check(load().map_smoother_geometry(h, ctypes.byref(K), ctypes.byref(Bt), ctypes.byref(nt)), h)
     return K.value, Bt.value, nt.value
+
+
+FMA_FP32, FMA_FP32X2, FMA_FP64 = 0, 1, 2
+
+
+def map_fma_peak(kind, iters, stream=None):
+    """(flops executed, device ms) of the FMA-throughput kernel of `kind`."""
+    flop, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    st = load().map_fma_peak(kind, iters, ctypes.byref(flop), ctypes.byref(ms), stream)
+    if st != MAP_OK:
+        raise MapError(st, "map_fma_peak failed")
+    return flop.value, ms.value
 
 
 def map_smoother_launches(h):

@@ -11,10 +11,13 @@
 // kernels as map_smoother_solve run on that memory, so the results are the
 // same.
 //
-// Set-up: the first call on a device, with that device current, looks up the
-// device addresses of the arrays with cudaGetSymbolAddress (a host-side name
-// of a __device__ array is not a device address) and caches them for that
-// device.  Make that first call before any stream capture.
+// Set-up: every call, with the target device current, looks up the device
+// addresses of the arrays with cudaGetSymbolAddress (a host-side name of a
+// __device__ array is not a device address).  The lookup allocates nothing
+// and is not cached, so the addresses stay right when the context is torn
+// down and created again (cudaDeviceReset), which may move the module.  The
+// first call on a device loads the module into the context; make it before
+// any stream capture.
 //
 // Every call shares the arrays and they keep the contents of the last call:
 // the three device counters (precision policy, bounded waits) are cleared at the start of each
@@ -25,7 +28,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -35,7 +37,6 @@ namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;
 constexpr int SETUP_IN_DOUBLES = 8 * 8 * 4 + 8 * 5 + 8 * 8 * 2;   // F, L, W, H, R, P0 + vectors
-constexpr int MAX_DEVICES = 64;
 
 __device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
 __device__ __align__(256) unsigned long long g_stats[4];   // 3 counters + grid barrier state
@@ -43,38 +44,27 @@ __device__ __align__(256) double g_setup_in[SETUP_IN_DOUBLES];
 __device__ __align__(256) mapk::SetupOut g_setup_out;
 
 struct DeviceArrays {
-    bool ready = false;
+    int device = 0;
     char* scratch = nullptr;
     unsigned long long* stats = nullptr;
     double* setup_in = nullptr;
     mapk::SetupOut* setup_out = nullptr;
 };
 
-DeviceArrays g_dev[MAX_DEVICES];
-std::mutex g_mu;
-
-// device addresses of the arrays for the current device (looked up once)
-cudaError_t device_arrays(DeviceArrays& out)
+// device addresses of the arrays on the current device
+cudaError_t device_arrays(DeviceArrays& d)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&d.device);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    DeviceArrays& d = g_dev[dev];
-    if (!d.ready) {
-        void* p = nullptr;
-        if ((e = cudaGetSymbolAddress(&p, g_scratch)) != cudaSuccess) return e;
-        d.scratch = static_cast<char*>(p);
-        if ((e = cudaGetSymbolAddress(&p, g_stats)) != cudaSuccess) return e;
-        d.stats = static_cast<unsigned long long*>(p);
-        if ((e = cudaGetSymbolAddress(&p, g_setup_in)) != cudaSuccess) return e;
-        d.setup_in = static_cast<double*>(p);
-        if ((e = cudaGetSymbolAddress(&p, g_setup_out)) != cudaSuccess) return e;
-        d.setup_out = static_cast<mapk::SetupOut*>(p);
-        d.ready = true;
-    }
-    out = d;
+    void* p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_scratch)) != cudaSuccess) return e;
+    d.scratch = static_cast<char*>(p);
+    if ((e = cudaGetSymbolAddress(&p, g_stats)) != cudaSuccess) return e;
+    d.stats = static_cast<unsigned long long*>(p);
+    if ((e = cudaGetSymbolAddress(&p, g_setup_in)) != cudaSuccess) return e;
+    d.setup_in = static_cast<double*>(p);
+    if ((e = cudaGetSymbolAddress(&p, g_setup_out)) != cudaSuccess) return e;
+    d.setup_out = static_cast<mapk::SetupOut*>(p);
     return cudaSuccess;
 }
 
@@ -128,6 +118,7 @@ extern "C" map_status map_smoother_solve_noalloc(const map_problem_desc* d, cons
     // a handle on the stack: model and geometry as in map_smoother_create, the
     // workspace and counters in the __device__ arrays
     map_smoother h;
+    h.device = arr.device;
     h.model = MAP_MODEL_LINEAR; h.N = n; h.M = m; h.NW = nw;
     h.prec = d->precision; h.smoother = MAP_RTS; h.gn_iters = 1;
     h.T = (long)d->T; h.dt = d->dt; h.cond_max = d->cond_max > 0 ? d->cond_max : 1e6;
@@ -182,7 +173,10 @@ extern "C" map_status map_smoother_solve_noalloc(const map_problem_desc* d, cons
     if (h.consts.flags & SETUP_SINGULAR_P0) return noalloc_fail(MAP_ERR_SINGULAR, "P0 is singular");
     if (h.consts.flags & SETUP_SINGULAR_A) return noalloc_fail(MAP_ERR_SINGULAR, "the interval map A is singular");
 
-    // geometry as in map_smoother_create
+    // fixed geometry (unlike map_smoother_create, which balances K over the
+    // resident CTAs and honours desc->tile_threads): K = 16 steps per thread,
+    // B = 128 threads per tile (fewer when the trees do not fit), so that the
+    // scratch bound is a simple function of T
     const size_t es = elem_bytes(h.prec);
     const size_t V = 16 / es, P = (n + V - 1) / V * V;
     const size_t NE = 3 * n * P + 2 * P, NSCR = 3 * n * P + P, NL = n <= 2 ? 2 : n <= 4 ? 4 : 8;

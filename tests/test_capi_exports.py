@@ -17,7 +17,7 @@ def lib():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "map_smoother.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(map_(?:smoother|batch)_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(map_(?:smoother|batch|fma)_\w+)\s*\(", text)))
 
 
 def test_header_and_binding_agree():

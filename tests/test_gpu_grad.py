@@ -12,7 +12,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 DT = {"fp64": torch.float64, "fp32": torch.float32}
-GTOL = {"fp64": 1e-8, "fp32": 2e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,6 +24,33 @@ def _lib():
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+# Per-block tolerances.  The gradient's blocks differ in scale by orders of
+# magnitude (the log r entry grows with T while the F block stays O(1)), so a
+# norm over the whole vector would hide an error in the F block.  Each block
+# -- dL/dF (n*n entries), dL/dlog q, dL/dlog r -- is compared on its own, and
+# every F entry against the block's largest entry.  FP64: 1e-8.  FP32: the
+# per-step terms are formed in FP32 from FP32 trajectories (unit roundoff
+# 6e-8; the residuals x_k - A x_{k+1} - b lose about log10(|x| / |residual|)
+# ~ 2 digits to cancellation) and accumulated in FP64 over T steps, whose
+# independent rounding errors grow like sqrt(T); 1e-4 per block leaves a
+# margin of about 10 over that estimate at T = 2^18.
+BTOL = {"fp64": 1e-8, "fp32": 1e-4}
+
+
+def assert_grad(g, ref, tol):
+    g, ref = np.asarray(g, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    nn = len(ref) - 2
+    gF, rF = g[:nn], ref[:nn]
+    eF = rel(gF, rF)
+    assert eF <= tol, f"dL/dF block relative error {eF:.3e} > {tol:.0e}"
+    scale = np.abs(rF).max()
+    worst = np.abs(gF - rF).max() / scale
+    assert worst <= 10 * tol, f"largest dL/dF entry error {worst:.3e} of the block scale > {10 * tol:.0e}"
+    for i, name in ((nn, "log q"), (nn + 1, "log r")):
+        e = abs(g[i] - ref[i]) / abs(ref[i])
+        assert e <= tol, f"dL/d{name} relative error {e:.3e} > {tol:.0e} ({g[i]!r} vs {ref[i]!r})"
 
 
 def problem(T, dt=1e-3, seed=51):
@@ -60,7 +86,7 @@ def test_gradient_matches_oracle(prec, loss):
         x_ref = oracle.smooth_lti(scaled(model, logq, logr), y, dt)
         ref, _ = oracle.grad_lti(model, y, dt, logq, logr, dLdx=x_ref - x_true)
     sm.close()
-    assert rel(g, ref) <= GTOL[prec]
+    assert_grad(g, ref, BTOL[prec])
 
 
 def test_log_normaliser_flag_matches_oracle():
@@ -72,7 +98,7 @@ def test_log_normaliser_flag_matches_oracle():
     x = sm.solve(yt)
     g = sm.grad(yt, x, logdet=True)
     ref, _ = oracle.grad_lti(model, y, dt, 0.0, 0.0, logdet=True)
-    assert rel(g, ref) <= 1e-8
+    assert_grad(g, ref, 1e-8)
 
 
 def test_gradient_against_central_differences_on_the_gpu():
@@ -102,7 +128,8 @@ def test_gradient_against_central_differences_on_the_gpu():
     fd[16] = (L(F0, lq + h, lr) - L(F0, lq - h, lr)) / (2 * h)
     fd[17] = (L(F0, lq, lr + h) - L(F0, lq, lr - h)) / (2 * h)
     idx = [0, 6, 13, 11, 16, 17]
-    assert rel(g[idx], fd[idx]) <= 1e-6
+    for i in idx:   # each entry: relative 1e-6 plus the FD rounding floor
+        assert abs(g[i] - fd[i]) <= 1e-6 * abs(fd[i]) + 5e-8, (i, g[i], fd[i])
     sm.close()
 
 
@@ -118,7 +145,7 @@ def test_gradient_workload_T_2_18(prec):
     g = sm.grad(yt, x)
     ref, _ = oracle.grad_lti(model, y, dt, 0.0, 0.0)
     sm.close()
-    assert rel(g, ref) <= GTOL[prec]
+    assert_grad(g, ref, BTOL[prec])
 
 
 def test_autograd_function_matches_c_abi_gradient():
@@ -137,12 +164,13 @@ def test_autograd_function_matches_c_abi_gradient():
     loss.backward()
     ref, _ = oracle.grad_lti(model, y, dt, 0.2, -0.3, dLdx=x.detach().cpu().numpy() - x_true)
     got = np.concatenate([F.grad.numpy().ravel(), [lq.grad.item(), lr.grad.item()]])
-    assert rel(got, ref) <= 1e-8
+    assert_grad(got, ref, 1e-8)
     F.grad = None
     c = map_cost(sm, yt, F, lq, lr)
     c.backward()
     ref_c, _ = oracle.grad_lti(model, y, dt, 0.2, -0.3)
-    assert rel(F.grad.numpy().ravel(), ref_c[:16]) <= 1e-8
+    got_c = np.concatenate([F.grad.numpy().ravel(), [lq.grad.item() - got[16], lr.grad.item() - got[17]]])
+    assert_grad(got_c, ref_c, 1e-8)
     sm.close()
 
 
@@ -173,4 +201,7 @@ def test_update_equals_fresh_handle(prec):
     sm.close()
     sm2.close()
     tol = {"fp64": 1e-9, "fp32": 1e-4}[prec]
-    assert rel(x1.cpu().numpy(), oracle.smooth_lti(m2, y, dt)) <= tol
+    xr = oracle.smooth_lti(m2, y, dt)
+    xg = x1.cpu().numpy()
+    assert rel(xg, xr) <= tol
+    assert np.abs(xg - xr).max() / np.abs(xr).max() <= 10 * tol
