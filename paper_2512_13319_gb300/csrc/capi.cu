@@ -78,6 +78,7 @@ void free_handle(map_smoother* h)
     if (h->d_lam) cudaFree(h->d_lam);
     if (h->d_grad) cudaFree(h->d_grad);
     if (h->d_fold) cudaFree(h->d_fold);
+    if (h->d_tab) cudaFree(h->d_tab);
     if (h->d_setup) cudaFree(h->d_setup);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -90,6 +91,8 @@ map_status run_setup(map_smoother* h)
 {
     const int n = h->N, m = h->M, nw = h->NW;
     h->fold_K = 0;                     // linear-fold constants follow the model
+    h->tab_K = 0;                      // and so do the per-step tables
+    h->tab_ok = 0;
     std::vector<double> W = h->W, R = h->R;
     for (double& w : W) w *= std::exp(h->logq);
     for (double& r : R) r *= std::exp(h->logr);
@@ -225,6 +228,9 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
         if ((e = cudaMalloc(&h->d_grad, sizeof(double) * (n * n + 2))) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
         if ((e = cudaMalloc(&h->d_fold, fold_bytes(n, m, es, h->nt))) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+        const size_t tb = ops->tab_bytes ? ops->tab_bytes(*h) : 0;
+        if (tb && (e = cudaMalloc(reinterpret_cast<void**>(&h->d_tab), tb)) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(*h, e, "create");

@@ -34,6 +34,12 @@ struct map_smoother {
     void* d_fold = nullptr;            // linear-fold constants of K steps (linear models)
     double* d_setup = nullptr;         // set-up kernel inputs (SETUP_IN_CAP doubles), then its SetupOut
     int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
+    // per-step tables of linear time-invariant RTS solves (steptab.cuh)
+    char* d_tab = nullptr;
+    int tab_K = 0, tab_B = 0;          // geometry they were computed for (0: stale)
+    int tab_ok = 0;                    // the tables reach the stationary filter: the table solve runs
+    long tab_kt = 0, tab_kc = 0, tab_gc = 0;
+    int fused_tab = -1;                // the table solve fits co-resident (-1: not yet asked)
     int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
     int launches = 0;                  // kernels of the last solve
     unsigned long long bar_arrivals = 0;   // grid-barrier arrivals counted at d_stats[3] so far
@@ -79,6 +85,7 @@ struct Ops {
     map_status (*solve_seg)(map_smoother& h, const void* y, const unsigned char* reset, void* x_out,
                             cudaStream_t st);
     int (*resident_blocks)(int B);     // CTAs of the filter kernels per SM at B threads
+    size_t (*tab_bytes)(const map_smoother& h) = nullptr;   // per-step table buffer (0: none)
 };
 
 // geometry (steps per thread K, threads per tile B) and its workspace bytes

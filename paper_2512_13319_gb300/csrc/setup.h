@@ -39,6 +39,7 @@ cudaError_t launch_setup(const SetupIn& in, SetupOut* d_out, cudaStream_t st);
 template <int N, int M>
 struct LinCostParams {
     double A[N * N], b[N], Cinv[N * N], H[M * N], r[M], Rinv[M * M], S0[N * N], m0[N];
+    double IA[N * N];                  // I - A (dt F for the Euler element), formed in FP64
     double dt, trF;
 };
 

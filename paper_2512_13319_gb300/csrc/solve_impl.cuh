@@ -8,6 +8,7 @@
 
 #include "handle.h"
 #include "scan.cuh"
+#include "steptab.cuh"
 
 namespace mapk {
 
@@ -229,8 +230,51 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
             cudaGetLastError();
             cap = cudaStreamCaptureStatusActive;
         }
-        if (lti && lt.pi && !dev_prior && !h.profile && nt > 1 && nt - 1 <= G &&
-            cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0) {
+        const bool single = lti && lt.pi && !dev_prior && !h.profile && nt > 1 && nt - 1 <= G &&
+                            cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0;
+        // with per-step tables (steptab.cuh) the single launch runs only the
+        // data-dependent part of every step
+        if (single && h.tab_ok && h.tab_K == K && h.tab_B == B) {
+            const size_t sh = TabSmem<N, Prod::W, S>::bytes(B, K);
+            if (h.fused_tab < 0) {
+                int nb = 0, sms = 0;
+                h.fused_tab = allow_smem(k_lti_solve_tab<N, S, Prod>, sh) == cudaSuccess &&
+                              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lti_solve_tab<N, S, Prod>, B, sh) ==
+                                  cudaSuccess &&
+                              cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device) == cudaSuccess &&
+                              (long)nb * sms >= nt;
+                cudaGetLastError();
+            }
+            if (h.fused_tab == 1) {
+                using ST = StepTab<N, S>;
+                TabArgs<S> tb;
+                tb.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(nt));
+                tb.phi = reinterpret_cast<const S*>(h.d_tab + ST::phi_off(nt, h.tab_kt));
+                tb.kc = h.tab_kc;
+                tb.gc = h.tab_gc;
+                const GridSync gs{h.d_stats + 3, h.bar_arrivals};
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(nt);
+                cfg.blockDim = dim3(B);
+                cfg.dynamicSmemBytes = sh;
+                cfg.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                cudaError_t e = cudaLaunchKernelEx(&cfg, k_lti_solve_tab<N, S, Prod>, prod, K, lt, prior_of<N, S>(h),
+                                                   tile_aff, filt_out, ctx, fin, x_out, filtT, gs, tb);
+                if (e == cudaSuccess) {
+                    h.launches += 1;
+                    h.bar_arrivals += 2ull * (unsigned long long)nt;
+                    return MAP_OK;
+                }
+                cudaGetLastError();
+                h.fused_tab = 0;
+            }
+        }
+        if (single) {
             const size_t sh = FusedSmem<N, Prod::W, S>::bytes(B, K);
             if (h.fused < 0) {
                 int nb = 0, sms = 0;
@@ -442,14 +486,26 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
         LtiDownSmem<N, M, S>::bytes(h.B, h.K, false) > 200 * 1024 ||
         LtiReduceSmem<N, M, S>::bytes(h.B, h.K, LB) > 200 * 1024)
         return MAP_OK;
-    if (h.fold_K != h.K || h.fold_B != h.B) {
+    // the per-step tables need a synchronisation (their convergence point is
+    // read back), so they are (re)computed outside stream capture only
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
+    const bool want_tab = h.d_tab && cap == cudaStreamCaptureStatusNone && (h.tab_K != h.K || h.tab_B != h.B);
+    if (h.fold_K != h.K || h.fold_B != h.B || want_tab) {
+        using ST = StepTab<N, S>;
+        double* f64 = want_tab ? reinterpret_cast<double*>(h.d_tab + ST::fold_off()) : nullptr;
+        double* pre64 = want_tab ? reinterpret_cast<double*>(h.d_tab + ST::pre_off()) : nullptr;
+        double* p64 = want_tab ? reinterpret_cast<double*>(h.d_tab + ST::p64_off()) : nullptr;
         // one warp for the serial FP64 chains, then one warp per thread
         // prefix and per tile in one launch, four to a block so that they
         // spread over the SMs' FP64 pipes
         k_lti_fold<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), h.K, LB, ne,
-                                             static_cast<S*>(h.d_fold));
+                                             static_cast<S*>(h.d_fold), f64);
         k_lti_tables<N, M, S><<<((1 << LB) + 3) / 4 + (h.nt + 3) / 4, 128, 0, st>>>(
-            prior_of<N, double>(h), LB, h.nt, ne, static_cast<S*>(h.d_fold));
+            prior_of<N, double>(h), LB, h.nt, ne, static_cast<S*>(h.d_fold), pre64, p64);
         if (h.nt <= TT::PI_TILES) {
             const int segs = (h.nt + TT::PI_SEG - 1) / TT::PI_SEG;
             k_lti_segments<N, M, S><<<(h.nt + 127) / 128, 128, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
@@ -460,6 +516,34 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
         if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
         h.fold_K = h.K;
         h.fold_B = h.B;
+        h.tab_ok = 0;
+        h.tab_K = h.tab_B = 0;
+        if (want_tab) {
+            // rows of the steps k < KT; with T >= KT the convergence point kc,
+            // from which row kc stands for every later step, must leave room
+            // for the thread maps of the threads that reach it
+            const long KT = std::min<long>(h.T + 1, ST::cap());
+            const int check = h.T + 1 > KT;
+            const double tol = sizeof(S) == 4 ? 0x1p-25 : 1e-14;
+            unsigned long long meta[2] = {0, 0};
+            if ((e = cudaMemsetAsync(h.d_tab, 0, sizeof(meta), st)) != cudaSuccess)
+                return cuda_fail(h, e, "cudaMemsetAsync");
+            k_lti_steptab<N, M, S><<<(unsigned)((KT + 127) / 128), 128, 0, st>>>(
+                lti_params<N, M, double>(h), h.K, h.B, h.nt, KT, check, tol, h.d_tab);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "step table kernel launch");
+            if ((e = cudaMemcpyAsync(meta, h.d_tab, sizeof(meta), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cuda_fail(h, e, "step table read-back");
+            const long kc = check ? (long)meta[0] : h.T;
+            h.tab_K = h.K;
+            h.tab_B = h.B;
+            if (meta[1] == 0 && (!check || kc + h.K + 1 <= KT)) {
+                h.tab_ok = 1;
+                h.tab_kt = KT;
+                h.tab_kc = kc;
+                h.tab_gc = (kc + h.K - 1) / h.K;
+            }
+        }
     }
     *out = static_cast<const S*>(h.d_fold);
     return MAP_OK;
@@ -606,6 +690,7 @@ map_status cost_linear(map_smoother& h, const void* y, const void* x, double* d_
     p.dt = h.dt;
     p.trF = 0.0;
     for (int i = 0; i < N; ++i) p.trF += h.F[i * N + i];
+    for (int i = 0; i < N * N; ++i) p.IA[i] = (i % (N + 1) == 0 ? 1.0 : 0.0) - c.A[i];
     cudaError_t e = cudaMemsetAsync(d_cost, 0, sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     const int blocks = (int)std::min<long>(1024, (h.T + 255) / 256);
@@ -626,6 +711,11 @@ map_status cost_linear(map_smoother& h, const void* y, const void* x, double* d_
 //    d/dlogq = sum s^T C^-1 r, d/dlogr = sum dt (H lambda_{k+1})^T R^-1 e
 // with r_k = x_k - A x_{k+1} - b, s_k = lambda_k - A lambda_{k+1},
 // e_k = H x_{k+1} + r - y_{k+1}.  Per-step terms in S, FP64 accumulation.
+// The residuals are formed as (x_k - x_{k+1}) + (I - A) x_{k+1} - b with
+// I - A = dt F kept apart from the identity: A = I - dt F rounded to FP32
+// would carry an error of one FP32 ulp of 1 in every step's residual, the same
+// in every step, which the sum over T steps turns into a systematic error of
+// dL/dF of order ulp(1) T |x|^2 / q.
 // ---------------------------------------------------------------------------
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(256)
@@ -642,9 +732,9 @@ k_grad_contract(const S* __restrict__ y, const S* __restrict__ x, const S* __res
         for (int i = 0; i < N; ++i) { xk[i] = x[k * N + i]; x1[i] = x[(k + 1) * N + i]; }
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            S s = xk[i] - S(p.b[i]);
+            S s = (xk[i] - x1[i]) - S(p.b[i]);
 #pragma unroll
-            for (int j = 0; j < N; ++j) s = fma(-S(p.A[i * N + j]), x1[j], s);
+            for (int j = 0; j < N; ++j) s = fma(S(p.IA[i * N + j]), x1[j], s);
             r[i] = s;
         }
 #pragma unroll
@@ -674,9 +764,9 @@ k_grad_contract(const S* __restrict__ y, const S* __restrict__ x, const S* __res
             for (int i = 0; i < N; ++i) { lk[i] = lam[k * N + i]; l1[i] = lam[(k + 1) * N + i]; }
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                S s = lk[i];
+                S s = lk[i] - l1[i];
 #pragma unroll
-                for (int j = 0; j < N; ++j) s = fma(-S(p.A[i * N + j]), l1[j], s);
+                for (int j = 0; j < N; ++j) s = fma(S(p.IA[i * N + j]), l1[j], s);
                 sv[i] = s;
             }
 #pragma unroll
@@ -749,6 +839,7 @@ map_status grad_linear(map_smoother& h, const void* y, const void* x, const void
     for (int i = 0; i < M * M; ++i) p.Rinv[i] = c.Rinv[i];
     p.dt = h.dt;
     p.trF = 0.0;
+    for (int i = 0; i < N * N; ++i) p.IA[i] = h.dt * h.F[i];     // Euler element: I - A = dt F
     S* lam = nullptr;
     if (dLdx) {
         AdjProducer<N, S> prod;
@@ -787,6 +878,14 @@ map_status grad_linear(map_smoother& h, const void* y, const void* x, const void
     return MAP_OK;
 }
 
+// bytes of the per-step tables of an RTS solve (steptab.cuh)
+template <int N, typename S>
+size_t step_table_bytes(const map_smoother& h)
+{
+    if (h.smoother != MAP_RTS) return 0;
+    return StepTab<N, S>::bytes(h.nt, std::min<long>(h.T + 1, StepTab<N, S>::cap()));
+}
+
 // State dimensions up to 6 get every path; larger ones (whose 5-tuples do not
 // fit one thread's registers) the RTS solve, the cost and the sequential baseline.
 template <int N, int M, typename S>
@@ -795,7 +894,8 @@ const Ops* linear_ops()
     if constexpr (N <= 6) {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
                              &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
-                             &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>};
+                             &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>,
+                             &step_table_bytes<N, S>};
         return &ops;
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
