@@ -161,7 +161,7 @@ __device__ __forceinline__ bool apply_p(const double* __restrict__ e, double (&P
         for (int j = 0; j < N; ++j) {
             double s = 0.0;
 #pragma unroll
-            for (int k = i; k < N; ++k) s = fma(Z[i * N + k], A[k * N + j], s);   // Z upper triangular
+            for (int k = 0; k < N; ++k) s = fma(Z[i * N + k], A[k * N + j], s);
             ZA[i * N + j] = s;
         }
 #pragma unroll

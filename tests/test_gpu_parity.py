@@ -243,24 +243,37 @@ def test_host_buffer_entry_point_matches_device_entry_point():
 
 
 @pytest.mark.parametrize("kind", ["ou_full_rank_noise", "wiener_velocity_low_rank_noise"])
-def test_precision_policy_counter_and_fallback(kind):
+@pytest.mark.parametrize("pipeline", ["single_launch", "three_kernels"])
+def test_precision_policy_counter_and_fallback(kind, pipeline):
     """A huge condition threshold keeps every combine in FP32; a tiny one
     recomputes every combine in FP64, which must still agree with the oracle.
-    With full-rank process noise every per-step update inverts I + C P (one
+    Three-kernel pipeline (run when per-phase events are recorded): with
+    full-rank process noise every per-step update inverts I + C P in FP32 (one
     FP64 recompute per step at the tiny threshold); with low-rank noise the
     per-step update inverts I + Gam^T P Gam, whose condition number can be
-    exactly 1, so only the tree combines must fall back."""
+    exactly 1, so only the tree combines must fall back.  Single launch with
+    per-step tables: the per-step inverses are formed in FP64 at plan time,
+    and the FP32 combines left (one per thread, its prefix with the tile's)
+    fall back."""
+    from paper_2512_13319_gb300 import MapSmoother
     T, dt = 5000, 0.01
     model = (synth.ou_model(4, 2, seed=11) if kind.startswith("ou")
              else synth.wiener_velocity(2, q=1.0, r=0.1))
     _, y = synth.simulate(model, T, dt, seed=10, substeps=1)
     ref = oracle.smooth_lti(model, y, dt)
-    x1, st1 = gpu_solve(model, y, dt, "fp32", cond_max=1e30)
-    x2, st2 = gpu_solve(model, y, dt, "fp32", cond_max=1.0 + 1e-12)
+    out = []
+    for cm in (1e30, 1.0 + 1e-12):
+        sm = MapSmoother(model, T, dt, precision="fp32", cond_max=cm)
+        sm.profile(pipeline == "three_kernels")
+        x = sm.solve(torch.tensor(y, dtype=torch.float32, device="cuda")).cpu().numpy()
+        out.append((x, sm.stats(), sm.launches()))
+        sm.close()
+    (x1, st1, n1), (x2, st2, n2) = out
+    assert (n1 == 1) == (pipeline == "single_launch") and n1 == n2
     assert_traj(x1, ref, 1e-4)
     assert_traj(x2, ref, 1e-4)
     assert st2[0] > st1[0]
-    if kind.startswith("ou"):
+    if kind.startswith("ou") and pipeline == "three_kernels":
         assert st2[0] >= T
     assert st1[1] == 0 and st2[1] == 0
 
