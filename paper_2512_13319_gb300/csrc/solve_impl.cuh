@@ -250,6 +250,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                 TabArgs<S> tb;
                 tb.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(nt));
                 tb.phi = reinterpret_cast<const S*>(h.d_tab + ST::phi_off(nt, h.tab_kt));
+                tb.wi = reinterpret_cast<const S*>(h.d_tab + ST::wi_off(nt, h.tab_kt));
                 tb.kc = h.tab_kc;
                 tb.gc = h.tab_gc;
                 const GridSync gs{h.d_stats + 3, h.bar_arrivals};
@@ -883,7 +884,7 @@ template <int N, typename S>
 size_t step_table_bytes(const map_smoother& h)
 {
     if (h.smoother != MAP_RTS) return 0;
-    return StepTab<N, S>::bytes(h.nt, std::min<long>(h.T + 1, StepTab<N, S>::cap()));
+    return StepTab<N, S>::bytes(h.nt, std::min<long>(h.T + 1, StepTab<N, S>::cap()), h.K);
 }
 
 // State dimensions up to 6 get every path; larger ones (whose 5-tuples do not

@@ -61,7 +61,23 @@ struct StepTab {
     __host__ __device__ static constexpr size_t rows_off(long nt) { return al(p64_off() + sizeof(double) * nt * NN); }
     __host__ __device__ static constexpr long phi_count(long kt) { return kt / 8 + 2; }
     __host__ __device__ static constexpr size_t phi_off(long nt, long kt) { return al(rows_off(nt) + sizeof(S) * kt * RS); }
-    __host__ __device__ static constexpr size_t bytes(long nt, long kt) { return phi_off(nt, kt) + sizeof(S) * phi_count(kt) * NN; }
+    // then the same constants (E, MC, o, mb: WC components) warp-interleaved by
+    // thread: component c of step i of thread g at ((g/32 K + i) WC + c) 32 + g%32,
+    // so that a warp's load of one component of one step is one 128-byte line
+    static constexpr int WC = NN + NS + 2 * N;
+    __host__ __device__ static constexpr long wi_threads(long kt, int K) { return ((kt + K - 1) / K + 31) / 32 * 32; }
+    __host__ __device__ static constexpr size_t wi_off(long nt, long kt)
+    {
+        return al(phi_off(nt, kt) + sizeof(S) * phi_count(kt) * NN);
+    }
+    __host__ __device__ static constexpr long wi_index(long g, int i, int c, int K)
+    {
+        return (((g >> 5) * K + i) * WC + c) * 32 + (g & 31);
+    }
+    __host__ __device__ static constexpr size_t bytes(long nt, long kt, int K)
+    {
+        return wi_off(nt, kt) + sizeof(S) * (size_t)wi_threads(kt, K) * K * WC;
+    }
     // table length cap: the FP32 table converges within 2^-25 earlier
     static constexpr long cap() { return sizeof(S) == 4 ? 16384 : 32768; }
 };
@@ -243,6 +259,13 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
         Zb[a] = zb;
         Pb[a] = pb;
     }
+    // the row, and the same constants in the warp-interleaved copy
+    S* wi = reinterpret_cast<S*>(tab + ST::wi_off(nt, KT));
+    const long g = k / K;
+    auto put = [&](int off, double val) {
+        row[off] = S(val);
+        wi[ST::wi_index(g, i, off, K)] = S(val);
+    };
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll
@@ -251,7 +274,7 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
 #pragma unroll
             for (int q = 0; q < N; ++q) e = fma(-CZt[a * N + q], ZA[q * N + c], e);
             E[a * N + c] = e;
-            row[ST::oE + a * N + c] = S(e);
+            put(ST::oE + a * N + c, e);
         }
 #pragma unroll
     for (int a = 0; a < N; ++a)
@@ -260,7 +283,7 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
             double mc = 0.5 * (C[a * N + c] + C[c * N + a]);
 #pragma unroll
             for (int q = 0; q < N; ++q) mc = fma(-CZt[a * N + q], CZt[c * N + q], mc);
-            row[ST::oMC + Sym<N>::at(a, c)] = S(mc);
+            put(ST::oMC + Sym<N>::at(a, c), mc);
             row[ST::oP + Sym<N>::at(a, c)] = S(P[a * N + c]);
         }
 #pragma unroll
@@ -271,8 +294,8 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
             mb = fma(-CZt[a * N + q], Zb[q], mb);
             o = fma(-E[q * N + a], Pb[q], o);
         }
-        row[ST::oMB + a] = S(mb);
-        row[ST::oO + a] = S(o);
+        put(ST::oMB + a, mb);
+        put(ST::oO + a, o);
     }
     if (i == 0) {
         // Phi_g = (I + C_K P)^-1 A_K = A_K - C_K Z_K^T (Z_K A_K)
@@ -328,6 +351,7 @@ template <typename S>
 struct TabArgs {
     const S* rows;      // step rows (StepTab)
     const S* phi;       // thread maps
+    const S* wi;        // the rows warp-interleaved by thread (threads that start before kc)
     long kc;            // steps k >= kc read row kc
     long gc;            // threads g >= gc read map gc
 };
@@ -354,6 +378,32 @@ __device__ __forceinline__ void load_stepc(const S* __restrict__ row, StepC<N, S
         c.o[q] = __ldg(row + ST::oO + q);
         c.mb[q] = __ldg(row + ST::oMB + q);
     }
+}
+
+// step i of thread g from the warp-interleaved copy (coalesced over the warp)
+template <int N, typename S>
+__device__ __forceinline__ void load_stepc_wi(const S* __restrict__ wi, long g, int i, int K, StepC<N, S>& c)
+{
+    using ST = StepTab<N, S>;
+    const S* p = wi + ST::wi_index(g, i, 0, K);
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) c.E[q] = __ldg(p + (ST::oE + q) * 32);
+#pragma unroll
+    for (int q = 0; q < Sym<N>::SZ; ++q) c.MC[q] = __ldg(p + (ST::oMC + q) * 32);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        c.o[q] = __ldg(p + (ST::oO + q) * 32);
+        c.mb[q] = __ldg(p + (ST::oMB + q) * 32);
+    }
+}
+
+template <int N, typename S>
+__device__ __forceinline__ void load_stepE_wi(const S* __restrict__ wi, long g, int i, int K, S (&E)[N * N])
+{
+    using ST = StepTab<N, S>;
+    const S* p = wi + ST::wi_index(g, i, 0, K);
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) E[q] = __ldg(p + (ST::oE + q) * 32);
 }
 
 template <int N, typename S>
@@ -514,11 +564,11 @@ k_lti_solve_tab(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, 
 #pragma unroll
         for (int a = 0; a < N; ++a) v[a] = X.v[a];
         // forward: g_k = MC v_k + mb; v_{k+1} = E^T v_k + o + G y_{k+1} - Gr
-#pragma unroll 1
-        for (int i = 0; i < nv; ++i) {
+        // (threads that start before kc read the interleaved rows, two steps
+        // per iteration so that the next step's loads are in flight)
+        auto fwd = [&](int i, const StepC<N, S>& c) {
             const long k = k0 + i;
             const S* row = tb.rows + min(k, tb.kc) * ST::RS;
-            if (!steady) load_stepc<N, S>(row, c);
             if (filt_out) {
 #pragma unroll
                 for (int a = 0; a < N; ++a) filt_out[k * Red<N, S>::NCOMP + a] = v[a];
@@ -545,6 +595,24 @@ k_lti_solve_tab(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, 
             stage_state<N, S>(mine + i * N, g);
 #pragma unroll
             for (int a = 0; a < N; ++a) v[a] = nvv[a];
+        };
+        if (steady) {
+#pragma unroll 1
+            for (int i = 0; i < nv; ++i) fwd(i, c);
+        } else {
+            int i = 0;
+#pragma unroll 1
+            for (; i + 1 < nv; i += 2) {
+                StepC<N, S> c0, c1;
+                load_stepc_wi<N, S>(tb.wi, gthr, i, K, c0);
+                load_stepc_wi<N, S>(tb.wi, gthr, i + 1, K, c1);
+                fwd(i, c0);
+                fwd(i + 1, c1);
+            }
+            if (i < nv) {
+                load_stepc_wi<N, S>(tb.wi, gthr, i, K, c);
+                fwd(i, c);
+            }
         }
         S* xT = x_out + T * N;
         if (last && k0 < T && k0 + K >= T) {        // the value function at x_T and its minimiser
@@ -567,28 +635,45 @@ k_lti_solve_tab(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, 
         // the thread's composite map x_{k0} = Phi x_{k0+nv} + beta: beta by
         // Horner over the staged g_k, Phi from the table (full threads) or the
         // product of the per-step E_k (the thread that reaches T)
+        // backward over the thread's steps: z <- E_k z + g_k from the staged g_k,
+        // the result optionally staged in place of g_k
+        auto back = [&](S (&z)[N], bool stage) {
+            auto one = [&](int i, const S (&E)[NN]) {
+                S nz[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    S acc = mine[i * N + a];
+#pragma unroll
+                    for (int q = 0; q < N; ++q) acc = fma(E[a * N + q], z[q], acc);
+                    nz[a] = acc;
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) z[a] = nz[a];
+                if (stage) stage_state<N, S>(mine + i * N, z);
+            };
+            if (steady) {
+#pragma unroll 1
+                for (int i = nv - 1; i >= 0; --i) one(i, c.E);
+            } else {
+                int i = nv - 1;
+#pragma unroll 1
+                for (; i >= 1; i -= 2) {
+                    S E0[NN], E1[NN];
+                    load_stepE_wi<N, S>(tb.wi, gthr, i, K, E0);
+                    load_stepE_wi<N, S>(tb.wi, gthr, i - 1, K, E1);
+                    one(i, E0);
+                    one(i - 1, E1);
+                }
+                if (i == 0) {
+                    S E0[NN];
+                    load_stepE_wi<N, S>(tb.wi, gthr, 0, K, E0);
+                    one(0, E0);
+                }
+            }
+        };
         Aff<N, S> comp_t;
         set_identity(comp_t);
-#pragma unroll 1
-        for (int i = nv - 1; i >= 0; --i) {
-            S E[NN];
-            if (steady) {
-#pragma unroll
-                for (int q = 0; q < NN; ++q) E[q] = c.E[q];
-            } else {
-                load_stepE<N, S>(tb.rows + min(k0 + i, tb.kc) * ST::RS, E);
-            }
-            S nb[N];
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                S acc = mine[i * N + a];
-#pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(E[a * N + q], comp_t.c[q], acc);
-                nb[a] = acc;
-            }
-#pragma unroll
-            for (int a = 0; a < N; ++a) comp_t.c[a] = nb[a];
-        }
+        back(comp_t.c, false);
         if (nv == K) {
             const S* ph = tb.phi + min(gthr, tb.gc) * NN;
 #pragma unroll
@@ -615,27 +700,7 @@ k_lti_solve_tab(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, 
         lti_tile_suffix_sum<N, S>(lt, tile_aff, tile, gridDim.x, xT, red, xe_sh);
         S x[N];
         block_aff_end_states<N, S>(comp_t, xe_sh, red, x);
-#pragma unroll 1
-        for (int i = nv - 1; i >= 0; --i) {          // x_k = E_k x_{k+1} + g_k, in place of g_k
-            S E[NN];
-            if (steady) {
-#pragma unroll
-                for (int q = 0; q < NN; ++q) E[q] = c.E[q];
-            } else {
-                load_stepE<N, S>(tb.rows + min(k0 + i, tb.kc) * ST::RS, E);
-            }
-            S y[N];
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                S acc = mine[i * N + a];
-#pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(E[a * N + q], x[q], acc);
-                y[a] = acc;
-            }
-#pragma unroll
-            for (int a = 0; a < N; ++a) x[a] = y[a];
-            stage_state<N, S>(mine + i * N, x);
-        }
+        back(x, true);                               // x_k = E_k x_{k+1} + g_k, in place of g_k
         __syncthreads();
         const int KN = K * N;
         const long base = (long)tile * B * KN;
