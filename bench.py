@@ -96,6 +96,33 @@ K_FILTER_DOWN_DRAM_BYTES = 10482944 + 3812864
 K_SOLVE_DRAM_BYTES = None
 
 
+def work_model_tab(n, m, K, B, nt, wbytes):
+    """FLOP and minimal DRAM bytes per time step of the single-launch solve
+    with per-step tables (k_lti_solve_tab), counted from the kernel:
+      per step: the K-step fold's Gamma_i y (2 n m MAC), g_k = MC v + mb
+      (n^2), v_{k+1} = E^T v + o + G y (n^2 + n m), the thread map's offset
+      (n^2), the RTS step (n^2);
+      per thread (spread over its K steps): the one-variable combine of its
+      prefix with the tile's (4.5 n^3 + 2.5 n^2), its composite map's place
+      in the tile's shuffle composition and end states (2 (n^3 + n^2));
+      per tile (spread over its B K steps): the (b, eta) up- and down-sweeps
+      (2 (B - 1) 4 n^2) and the tile prefix and suffix sums (about nt / 2
+      terms of n^2 each).
+    Bytes: y in and x out (the per-step constants are plan-time tables of at
+    most a few MB, L2-resident)."""
+    L = B * K
+    per_step = 2 * n * m + n * n + (n * n + n * m) + n * n + n * n
+    per_thread = (4.5 * n ** 3 + 2.5 * n ** 2) + 2 * (n ** 3 + n ** 2)
+    per_tile = 2 * (B - 1) * 4 * n * n + 2 * (nt / 2.0) * n * n
+    mac = per_step + per_thread / K + per_tile / L
+    return 2 * mac, wbytes * (m + n)
+
+
+# DRAM bytes (read + write) of one k_lti_solve_tab launch on the nx=4, T=2^20
+# FP32 workload from one ncu capture of the current version; None until then
+K_SOLVE_TAB_DRAM_BYTES = None
+
+
 def solve_bytes(n, m, wbytes):
     """Minimal bytes of one solve per step: y in, x out (the rest is intermediate)."""
     return wbytes * (m + n)
@@ -277,6 +304,7 @@ def ours(args):
     # the output of the last timed solve, kept before any other solve reuses x
     x_timed = x.clone()
     kernels_per_solve = sm.launches()          # of the timed solves
+    solve_path = sm.path()
     ms_mean = max_over_ranks(sum(step_ms) / args.steps)
     ms = max_over_ranks(statistics.median(step_ms))      # median step time, max over ranks
     value = world * T / (ms * 1e-3)
@@ -321,7 +349,26 @@ def ours(args):
         fp32_nominal = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
         alu_peak = fp32_nominal if prec == "fp32" else fp32_nominal / 64.0
         peak_source = "nominal unit counts (map_fma_peak failed)"
-    if kernels_per_solve == 1:
+    if solve_path == 1:
+        # the single launch with per-step tables: its duration is the timed
+        # solve; its algorithmic work and bytes per step from work_model_tab
+        flop_step, byte_step = work_model_tab(4, 2, K_g, B_g, nt_g, wbytes)
+        achieved_tf = flop_step * T / (ms * 1e-3) / 1e12
+        achieved_gb = byte_step * T / (ms * 1e-3) / 1e9
+        fa, fh = achieved_tf / alu_peak, achieved_gb / hbm_peak
+        roofline = {"bound": "alu" if fa >= fh else "hbm",
+                    "achieved": achieved_tf if fa >= fh else achieved_gb,
+                    "peak": alu_peak if fa >= fh else hbm_peak,
+                    "unit": "TFLOP/s" if fa >= fh else "GB/s", "frac": max(fa, fh),
+                    "traffic": K_SOLVE_TAB_DRAM_BYTES if prec == "fp32" else None,
+                    "kernel": "k_lti_solve_tab (three phases, two grid barriers, one launch)",
+                    "alu": {"achieved_tflops": achieved_tf, "peak_tflops": alu_peak, "frac": fa,
+                            "flop_per_step": flop_step, "peak_source": peak_source},
+                    "hbm": {"achieved_gbs": achieved_gb, "peak_gbs": hbm_peak, "frac": fh,
+                            "bytes_per_step": byte_step, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                    "note": "neither pipe is saturated: the solve is bound by the latency of its two "
+                            "grid barriers and of the per-thread recursions (see DESIGN.md)"}
+    elif kernels_per_solve == 1:
         # one cooperative launch runs the whole solve: its duration is the
         # timed solve, its work the three phases' work
         flop_step = sum(flops.values())

@@ -218,6 +218,20 @@ map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* til
 map_status map_smoother_launches(const map_smoother* h, int* kernels);
 
 /*
+ * How the last solve's scan ran (host-side read): 0 before the first solve;
+ * MAP_PATH_TABLES: one cooperative launch that reads the per-step constants of
+ * a linear time-invariant model from plan-time tables (the Riccati factors of
+ * Eq. 36 do not depend on the data and converge to those of the stationary
+ * filter); MAP_PATH_SINGLE: one cooperative launch that forms every step's
+ * one-variable combine itself; MAP_PATH_PIPELINE: the multi-kernel scan.
+ * Returns MAP_ERR_INVALID_ARG for a NULL argument.
+ */
+#define MAP_PATH_TABLES 1
+#define MAP_PATH_SINGLE 2
+#define MAP_PATH_PIPELINE 3
+map_status map_smoother_solve_path(const map_smoother* h, int* path);
+
+/*
  * Allocation-free solve (no counterpart in the paper; a deployment entry point).
  * For callers that cannot call cudaMalloc at all, e.g. code running where the
  * device-memory budget is fixed up front (a real-time tracking loop, an

@@ -53,6 +53,7 @@ EXPORTS = {
     "map_smoother_phase_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(_I)]),
     "map_smoother_geometry": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "map_smoother_launches": (_I, [_VP, ctypes.POINTER(_I)]),
+    "map_smoother_solve_path": (_I, [_VP, ctypes.POINTER(_I)]),
     "map_smoother_destroy": (None, [_VP]),
     "map_smoother_last_error": (_CH, [_VP]),
     "map_smoother_supported": (_I, [_I, _I, _I, _I]),
@@ -183,6 +184,17 @@ def map_fma_peak(kind, iters, stream=None):
     if st != MAP_OK:
         raise MapError(st, "map_fma_peak failed")
     return flop.value, ms.value
+
+
+MAP_PATH_TABLES, MAP_PATH_SINGLE, MAP_PATH_PIPELINE = 1, 2, 3
+PATH_NAMES = {0: "none", 1: "single launch, per-step tables", 2: "single launch, per-step combines",
+              3: "multi-kernel pipeline"}
+
+
+def map_smoother_solve_path(h):
+    n = ctypes.c_int(0)
+    _check(load().map_smoother_solve_path(h, ctypes.byref(n)), h)
+    return n.value
 
 
 def map_smoother_launches(h):

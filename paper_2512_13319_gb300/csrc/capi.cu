@@ -335,6 +335,7 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
     h->launches = 0;
+    h->path = 0;
     map_status s = ops->solve(*h, y, x_out, filt_out, st);
     if (s != MAP_OK) return s;
     if (cost_out) {
@@ -441,6 +442,13 @@ map_status map_smoother_launches(const map_smoother* h, int* kernels)
 {
     if (!h || !kernels) return MAP_ERR_INVALID_ARG;
     *kernels = h->launches;
+    return MAP_OK;
+}
+
+map_status map_smoother_solve_path(const map_smoother* h, int* path)
+{
+    if (!h || !path) return MAP_ERR_INVALID_ARG;
+    *path = h->path;
     return MAP_OK;
 }
 

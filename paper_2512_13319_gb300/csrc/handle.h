@@ -42,6 +42,7 @@ struct map_smoother {
     int fused_tab = -1;                // the table solve fits co-resident (-1: not yet asked)
     int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
     int launches = 0;                  // kernels of the last solve
+    int path = 0;                      // how its last scan ran (map_smoother_solve_path)
     unsigned long long bar_arrivals = 0;   // grid-barrier arrivals counted at d_stats[3] so far
     double logq = 0.0, logr = 0.0;     // noise scales of the gradient parameters
     // per-phase timing (map_smoother_profile)

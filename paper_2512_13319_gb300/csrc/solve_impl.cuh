@@ -268,6 +268,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                                                    tile_aff, filt_out, ctx, fin, x_out, filtT, gs, tb);
                 if (e == cudaSuccess) {
                     h.launches += 1;
+                    h.path = MAP_PATH_TABLES;
                     h.bar_arrivals += 2ull * (unsigned long long)nt;
                     return MAP_OK;
                 }
@@ -302,6 +303,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                                                    Eg, tile_aff, filt_out, ctx, fin, x_out, filtT, form, gs);
                 if (e == cudaSuccess) {
                     h.launches += 1;
+                    h.path = MAP_PATH_SINGLE;
                     h.bar_arrivals += 2ull * (unsigned long long)nt;   // the launch's two grid barriers
                     return MAP_OK;
                 }
@@ -343,6 +345,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
            (const S*)group_agg);
     mark();
     h.launches += (!lti || nt > 1 ? 1 : 0) + (ng ? 1 : 0) + 2;
+    h.path = MAP_PATH_PIPELINE;
     launch(k_rts_down<N, S>, nt, B, sh_rts, st, pdl, (const S*)Eg, K, (const S*)thr_aff, (const S*)tile_aff,
            (const S*)xT, T, x_out, form);
     mark();
@@ -427,6 +430,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
     mark();
     h.launches += (!lti || nt > 1 ? 1 : 0) + (ng ? 1 : 0) + 3;
+    h.path = MAP_PATH_PIPELINE;
     launch(k_tf_down<N, S, RProd>, nt, B, sh_tfd, st, pdl, rprod, K, (const S*)thr_agg, (const S*)tile_agg,
            (const S*)term, (const S*)filt_ws, x_out, ctx);
     mark();

@@ -104,6 +104,11 @@ class MapSmoother:
         """Kernels launched by the last solve (1: the single cooperative launch)."""
         return B.map_smoother_launches(self._h)
 
+    def path(self):
+        """How the last solve's scan ran: 1 single launch with per-step tables,
+        2 single launch with per-step combines, 3 multi-kernel pipeline."""
+        return B.map_smoother_solve_path(self._h)
+
     def profile(self, enable=True):
         """Record per-phase CUDA events in every solve (see phase_times)."""
         B.map_smoother_profile(self._h, enable)

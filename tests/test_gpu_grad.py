@@ -31,12 +31,15 @@ def rel(a, b):
 # norm over the whole vector would hide an error in the F block.  Each block
 # -- dL/dF (n*n entries), dL/dlog q, dL/dlog r -- is compared on its own, and
 # every F entry against the block's largest entry.  FP64: 1e-8.  FP32: the
-# per-step terms are formed in FP32 from FP32 trajectories (unit roundoff
-# 6e-8; the residuals x_k - A x_{k+1} - b lose about log10(|x| / |residual|)
-# ~ 2 digits to cancellation) and accumulated in FP64 over T steps, whose
-# independent rounding errors grow like sqrt(T); 1e-4 per block leaves a
-# margin of about 10 over that estimate at T = 2^18.
-BTOL = {"fp64": 1e-8, "fp32": 1e-4}
+# per-step terms are exact functions of the FP32 trajectories x (and lambda),
+# so their error is that of the trajectories, about 5e-6 of |x|, and it is
+# not smooth: the scan composes its maps in a different order at every
+# thread and tile boundary.  The residuals x_k - A x_{k+1} - b that the F
+# block is built from are of order dt |w| ~ 1e-3 |x| at the MAP trajectory,
+# so at a boundary step a residual is off by ~5e-3 of itself; one step in K
+# (K ~ 18) carries such an error, which gives ~1e-4 on the F block (measured:
+# 5e-5 .. 2e-4 at T = 2e4 .. 2^18).  1e-3 per block leaves a margin of 5-10.
+BTOL = {"fp64": 1e-8, "fp32": 1e-3}
 
 
 def assert_grad(g, ref, tol):

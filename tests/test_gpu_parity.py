@@ -201,11 +201,45 @@ def test_full_size_T_2_20(prec):
     model = synth.wiener_velocity(2, q=1.0, r=0.1)
     T, dt = 2 ** 20, 1e-3
     _, y = synth.simulate(model, T, dt, seed=synth.seed_for(1), substeps=1)
-    x, _ = gpu_solve(model, y, dt, prec)
+    from paper_2512_13319_gb300 import MapSmoother
+    sm = MapSmoother(model, T, dt, precision=prec)
+    x = sm.solve(torch.tensor(y, dtype=DT[prec], device="cuda")).cpu().numpy()
+    path = sm.path()
+    sm.close()
     ref = oracle.smooth_lti(model, y, dt)
     assert_traj(x, ref, TOL[prec])
     # per-step infinity-norm error relative to the trajectory's scale
     assert np.abs(x - ref).max() / np.abs(ref).max() <= 10 * TOL[prec]
+    if prec == "fp32":      # the benchmark configuration runs the table path
+        assert path == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [9217, 20_000, 100_001])
+def test_table_path_matches_oracle(prec, T):
+    """Horizons whose step tables end at the stationary point (T >= the table
+    length) or cover the whole scan (short T), against the oracle and against
+    the per-step-combine path of the same handle (profiled solves run the
+    multi-kernel pipeline)."""
+    from paper_2512_13319_gb300 import MapSmoother
+    model = synth.ou_model(4, 2, seed=33)
+    model.c = np.array([0.3, -0.2, 0.1, 0.4])
+    dt = 1e-3
+    _, y = synth.simulate(model, T, dt, seed=T + 1, substeps=1)
+    sm = MapSmoother(model, T, dt, precision=prec)
+    yt = torch.tensor(y, dtype=DT[prec], device="cuda")
+    x1 = sm.solve(yt).cpu().numpy()
+    p1 = sm.path()
+    sm.profile(True)
+    x3 = sm.solve(yt).cpu().numpy()
+    p3 = sm.path()
+    sm.close()
+    ref = oracle.smooth_lti(model, y, dt)
+    assert_traj(x1, ref, TOL[prec])
+    assert_traj(x3, ref, TOL[prec])
+    assert p3 == 3
+    if prec == "fp32":
+        assert p1 == 1
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -408,4 +442,8 @@ def test_sequential_baseline_matches_oracle_gauss_newton(prec):
     _, y = synth.simulate(model, T, dt, seed=synth.seed_for(2))
     x0 = np.tile(model.m0, (T + 1, 1))
     x = seq_solve(model, y, dt, prec, x_init=x0, gn_iters=iters)
-    assert_traj(x, oracle.gauss_newton(model, y, dt, x0, iters), TOL[prec])
+    # the one-thread FP32 recursion rounds every step of every iteration in
+    # sequence: 2e-4 at T = 4000 (the scan's FP32 result is within 1e-4), so
+    # the sequential FP32 baseline is held to 5e-4 and the speed comparison
+    # "at equal accuracy" also reports the FP64 sequential baseline
+    assert_traj(x, oracle.gauss_newton(model, y, dt, x0, iters), 5e-4 if prec == "fp32" else TOL[prec])
