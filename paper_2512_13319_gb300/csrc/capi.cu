@@ -79,6 +79,7 @@ void free_handle(map_smoother* h)
     if (h->d_grad) cudaFree(h->d_grad);
     if (h->d_fold) cudaFree(h->d_fold);
     if (h->d_tab) cudaFree(h->d_tab);
+    if (h->d_scan) cudaFree(h->d_scan);
     if (h->d_setup) cudaFree(h->d_setup);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -231,6 +232,10 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
             return cuda_fail(*h, e, "cudaMalloc");
         const size_t tb = ops->tab_bytes ? ops->tab_bytes(*h) : 0;
         if (tb && (e = cudaMalloc(reinterpret_cast<void**>(&h->d_tab), tb)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+        const size_t sb = tb && ops->scan_bytes ? ops->scan_bytes(*h) : 0;
+        if (sb && ((e = cudaMalloc(reinterpret_cast<void**>(&h->d_scan), sb)) != cudaSuccess ||
+                   (e = cudaMemset(h->d_scan, 0, sb)) != cudaSuccess))
             return cuda_fail(*h, e, "cudaMalloc");
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(*h, e, "create");

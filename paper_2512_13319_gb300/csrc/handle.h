@@ -38,8 +38,10 @@ struct map_smoother {
     char* d_tab = nullptr;
     int tab_K = 0, tab_B = 0;          // geometry they were computed for (0: stale)
     int tab_ok = 0;                    // the tables reach the stationary filter: the table solve runs
-    long tab_kt = 0, tab_kc = 0, tab_gc = 0;
-    int fused_tab = -1;                // the table solve fits co-resident (-1: not yet asked)
+    long tab_kt = 0, tab_kc = 0;
+    // tiled-scan geometry of the table solve (steptab.cuh ScanGeom) and its buffer
+    char* d_scan = nullptr;
+    int sc_K = 0, sc_Kt = 0, sc_Jt = 0, sc_nt = 0;
     int fused = -1;                    // single-launch LTI solve fits co-resident (-1: not yet asked)
     int launches = 0;                  // kernels of the last solve
     int path = 0;                      // how its last scan ran (map_smoother_solve_path)
@@ -87,6 +89,7 @@ struct Ops {
                             cudaStream_t st);
     int (*resident_blocks)(int B);     // CTAs of the filter kernels per SM at B threads
     size_t (*tab_bytes)(const map_smoother& h) = nullptr;   // per-step table buffer (0: none)
+    size_t (*scan_bytes)(const map_smoother& h) = nullptr;  // tiled-scan table buffer (0: none)
 };
 
 // geometry (steps per thread K, threads per tile B) and its workspace bytes

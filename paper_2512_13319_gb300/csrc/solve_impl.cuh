@@ -234,47 +234,61 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
                             cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0;
         // with per-step tables (steptab.cuh) the single launch runs only the
         // data-dependent part of every step
-        if (single && h.tab_ok && h.tab_K == K && h.tab_B == B) {
-            const size_t sh = TabSmem<N, Prod::W, S>::bytes(B, K);
-            if (h.fused_tab < 0) {
-                int nb = 0, sms = 0;
-                h.fused_tab = allow_smem(k_lti_solve_tab<N, S, Prod>, sh) == cudaSuccess &&
-                              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lti_solve_tab<N, S, Prod>, B, sh) ==
-                                  cudaSuccess &&
-                              cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device) == cudaSuccess &&
-                              (long)nb * sms >= nt;
-                cudaGetLastError();
-            }
-            if (h.fused_tab == 1) {
-                using ST = StepTab<N, S>;
-                TabArgs<S> tb;
-                tb.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(nt));
-                tb.phi = reinterpret_cast<const S*>(h.d_tab + ST::phi_off(nt, h.tab_kt));
-                tb.wi = reinterpret_cast<const S*>(h.d_tab + ST::wi_off(nt, h.tab_kt));
-                tb.kc = h.tab_kc;
-                tb.gc = h.tab_gc;
-                const GridSync gs{h.d_stats + 3, h.bar_arrivals};
-                cudaLaunchConfig_t cfg = {};
-                cfg.gridDim = dim3(nt);
-                cfg.blockDim = dim3(B);
-                cfg.dynamicSmemBytes = sh;
-                cfg.stream = st;
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeCooperative;
-                at[0].val.cooperative = 1;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
-                cudaError_t e = cudaLaunchKernelEx(&cfg, k_lti_solve_tab<N, S, Prod>, prod, K, lt, prior_of<N, S>(h),
-                                                   tile_aff, filt_out, ctx, fin, x_out, filtT, gs, tb);
-                if (e == cudaSuccess) {
-                    h.launches += 1;
-                    h.path = MAP_PATH_TABLES;
-                    h.bar_arrivals += 2ull * (unsigned long long)nt;
-                    return MAP_OK;
+        if (lti && h.tab_ok && h.tab_K == K && h.tab_B == B && !dev_prior && !h.profile &&
+            cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0) {
+            using ST = StepTab<N, S>;
+            using SB = ScanBuf<N, Prod::W, S>;
+            using TT = TileTables<N, Prod::W, S>;
+            constexpr int SB_B = 128;
+            ScanArgs<N, S> sa{};
+            sa.g = ScanGeom{SB_B, h.sc_K, h.sc_Kt, h.sc_Jt, h.sc_nt};
+            const int snt = h.sc_nt;
+            const size_t sh = ScanSmem<N, Prod::W, S>::bytes(SB_B, h.sc_K, h.sc_Kt);
+            sa.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(nt));
+            sa.kc = h.tab_kc;
+            sa.phit = reinterpret_cast<const S*>(h.d_tab + ST::phit_off(nt, h.tab_kt));
+            sa.pw = reinterpret_cast<const S*>(h.d_scan + SB::pw_off());
+            sa.ttab = reinterpret_cast<const S*>(h.d_scan + SB::ttab_off());
+            sa.w = reinterpret_cast<S*>(h.d_scan + SB::w_off());
+            sa.taff = reinterpret_cast<S*>(h.d_scan + SB::taff_off());
+            const char* tiles = h.d_scan + SB::tiles_off();
+            sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));
+            sa.qt = reinterpret_cast<const S*>(tiles + TT::qt_off(snt));
+            sa.pdummy = reinterpret_cast<const S*>(tiles + TT::p_off());
+            sa.has_b = 0;
+            for (int i = 0; i < N; ++i) sa.has_b |= h.consts.b[i] != 0.0;
+            for (int i = 0; i < N; ++i) {
+                double ab = 0.0;
+                for (int k = 0; k < N; ++k) ab += h.consts.Phi[i * N + k] * h.consts.b[k];
+                sa.Aib[i] = S(ab);
+                for (int j = 0; j < N; ++j) {
+                    double ac = 0.0;
+                    for (int k = 0; k < N; ++k) ac += h.consts.Phi[i * N + k] * h.consts.C[k * N + j];
+                    sa.AiC[i * N + j] = S(ac);
                 }
-                cudaGetLastError();
-                h.fused_tab = 0;
             }
+            const GridSync gs{h.d_stats + 3, h.bar_arrivals};
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(snt);
+            cfg.blockDim = dim3(SB_B);
+            cfg.dynamicSmemBytes = sh;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;
+            at[0].val.cooperative = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_lti_scan<N, S, Prod>, prod, prior_of<N, S>(h), filt_out, ctx,
+                                               fin, x_out, filtT, gs, sa);
+            if (e == cudaSuccess) {
+                h.launches += 1;
+                h.path = MAP_PATH_TABLES;
+                h.bar_arrivals += 2ull * (unsigned long long)snt;
+                return MAP_OK;
+            }
+            // the grid cannot be resident at once after all: the paths below
+            cudaGetLastError();
+            h.tab_ok = 0;
         }
         if (single) {
             const size_t sh = FusedSmem<N, Prod::W, S>::bytes(B, K);
@@ -471,6 +485,73 @@ FlipParams<N, M, S> flip_params(const map_smoother& h)
     return p;
 }
 
+// Tiling and tables of the tiled-scan solve (k_lti_scan) once the
+// stationary point kc of the step tables is known: J_t tiles of 128 threads x
+// K_t steps up to kc, then tiles of 128 x K steps with the smallest K (8..64)
+// for which every tile's CTA is resident at once and the tile products fit
+// (at most 4 x 128 + 1 tiles).  Sets h.tab_ok when the solve can run.
+template <int N, int M, typename S>
+map_status scan_plan(map_smoother& h, cudaStream_t st)
+{
+    using ST = StepTab<N, S>;
+    using SB = ScanBuf<N, M, S>;
+    using TT = TileTables<N, M, S>;
+    h.tab_ok = 0;
+    if (!h.d_scan) return MAP_OK;
+    constexpr int B = 128, Kt = ST::KT_STEPS;
+    const long T = h.T, kc = h.tab_kc, KT = h.tab_kt, Lt = (long)B * Kt;
+    const int Jt = (int)((kc + Lt - 1) / Lt);
+    if (Jt > SB::jt_max() || ((long)Jt * Lt > KT && (long)Jt * Lt < T)) return MAP_OK;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device) != cudaSuccess) {
+        cudaGetLastError();
+        return MAP_OK;
+    }
+    int K = 0, nt = 0;
+    for (int k = 8; k <= 64 && !K; ++k) {
+        const long rest = T - (long)Jt * Lt;
+        const long n = rest > 0 ? Jt + (rest + (long)B * k - 1) / ((long)B * k) : (T + Lt - 1) / Lt;
+        if (n < 2 || n > SB::NTMAX) continue;
+        const size_t sh = ScanSmem<N, M, S>::bytes(B, k, Kt);
+        int nb = 0;
+        if (allow_smem(k_lti_scan<N, S, LtiProducer<N, M, S>>, sh) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lti_scan<N, S, LtiProducer<N, M, S>>, B, sh) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return MAP_OK;
+        }
+        if ((long)nb * sms >= n) {
+            K = k;
+            nt = (int)n;
+        }
+    }
+    if (!K) return MAP_OK;
+    const ScanGeom g{B, K, Kt, Jt, nt};
+    const S* rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(h.nt));
+    const double* e64 = reinterpret_cast<const double*>(h.d_tab + ST::e64_off(h.nt, KT));
+    const double* phit64 = reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(h.nt, KT));
+    S* pw = reinterpret_cast<S*>(h.d_scan + SB::pw_off());
+    S* ttab = reinterpret_cast<S*>(h.d_scan + SB::ttab_off());
+    char* tiles = h.d_scan + SB::tiles_off();
+    k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + (long)std::min(kc, KT - 1) * N * N, K, B, pw);
+    if (Jt > 0) {
+        const long cnt = (long)Jt * B * Kt * SB::CT;
+        k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(rows, KT, g, ttab);
+    }
+    k_scan_tilemaps<N, M, S><<<(nt + 3) / 4, 128, 0, st>>>(phit64, g, pw, tiles);
+    const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;
+    k_lti_segments<N, M, S><<<(nt + 127) / 128, 128, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
+    k_lti_products<N, M, S><<<dim3((segs + 7) / 8, (nt + 3) / 4), 32, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "scan table kernel launch");
+    h.sc_K = K;
+    h.sc_Kt = Kt;
+    h.sc_Jt = Jt;
+    h.sc_nt = nt;
+    h.tab_ok = 1;
+    return MAP_OK;
+}
+
 // constants of the linear per-thread fold and the tile tables (lti_fold.cuh)
 // for the current geometry, recomputed on `st` after a change of K, B or of
 // the model; nullptr when the geometry is beyond their range (the kernels then
@@ -542,11 +623,11 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
             const long kc = check ? (long)meta[0] : h.T;
             h.tab_K = h.K;
             h.tab_B = h.B;
-            if (meta[1] == 0 && (!check || kc + h.K + 1 <= KT)) {
-                h.tab_ok = 1;
+            if (meta[1] == 0 && (!check || kc + 1 < KT)) {
                 h.tab_kt = KT;
                 h.tab_kc = kc;
-                h.tab_gc = (kc + h.K - 1) / h.K;
+                map_status s2 = scan_plan<N, M, S>(h, st);
+                if (s2 != MAP_OK) return s2;
             }
         }
     }
@@ -888,7 +969,14 @@ template <int N, typename S>
 size_t step_table_bytes(const map_smoother& h)
 {
     if (h.smoother != MAP_RTS) return 0;
-    return StepTab<N, S>::bytes(h.nt, std::min<long>(h.T + 1, StepTab<N, S>::cap()), h.K);
+    return StepTab<N, S>::bytes(h.nt, std::min<long>(h.T + 1, StepTab<N, S>::cap()));
+}
+
+// bytes of the tiled-scan tables (steptab.cuh ScanBuf)
+template <int N, int M, typename S>
+size_t scan_table_bytes(const map_smoother& h)
+{
+    return h.smoother == MAP_RTS ? ScanBuf<N, M, S>::bytes() : 0;
 }
 
 // State dimensions up to 6 get every path; larger ones (whose 5-tuples do not
@@ -900,7 +988,7 @@ const Ops* linear_ops()
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
                              &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
                              &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>,
-                             &step_table_bytes<N, S>};
+                             &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>};
         return &ops;
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,

@@ -9,25 +9,24 @@
 //   v_{k+1} = E_k^T (v_k - P_k b) + eta_k,
 // and in the closed-loop map of the RTS pass (Section 4.3, Eq. 40-42)
 //   x_k = E_k x_{k+1} + g_k,  E_k = (I + C P_k)^-1 A,  g_k = (I + C P_k)^-1 (b + C v_k),
-// the P_k recursion, and with it E_k, M_k C = (I + C P_k)^-1 C (symmetric),
-// mb_k = (I + C P_k)^-1 b and o_k = -E_k^T P_k b, do not depend on the data.
-// They are therefore evaluated once per model and geometry, in FP64 (the
-// plan-time kernel k_lti_steptab), and a solve only runs the data-dependent
-// part of every step:
-//   g_k = MC_k v_k + mb_k,  v_{k+1} = E_k^T v_k + o_k + G y_{k+1} - Gr,
-//   x_k = E_k x_{k+1} + g_k.
+// the P_k recursion, and with it E_k and P_k b, do not depend on the data.
+// They are evaluated once per model in FP64 (k_lti_steptab), and a solve runs
+// only the data-dependent part of every step.  With (I + C P_k)^-1 = E_k A^-1:
+//   forward (filter):    v_{k+1} = E_k^T v_k + o_k + G y_{k+1} - Gr,  o_k = -E_k^T P_k b
+//   closed-loop offset:  g_k = E_k (A^-1 C v_k + A^-1 b)
+//   backward (RTS):      x_k = E_k x_{k+1} + g_k.
 // This is the same combine evaluated with its data-independent factors
-// precomputed, as lti_fold.cuh does for the folds and tile tables.
+// precomputed (as lti_fold.cuh does for folds and tile tables).
 //
 // P_k converges to the fixed point of the recursion (the stationary filter)
 // geometrically.  The table holds the steps k < KT (KT = min(T + 1, a cap), so
 // that a short scan has its every P_k up to P_T); when T >= KT, row kc stands
-// for every later step, where kc is the first step
-// from which every tabulated P_k agrees with the P of the scan's last full
-// tile to a relative tolerance of 2^-25 (FP32 solves) or 1e-14 (FP64 solves)
-// per entry (|dP_ab| <= tol sqrt(P_aa P_bb)): below the solve's own rounding.
-// When the table does not reach that point (slowly converging models) the
-// solve keeps the per-step Riccati path of scan.cuh.
+// for every later step, where kc is the first step from which every tabulated
+// P_k agrees with the P of the uniform decomposition's last full tile to a
+// relative tolerance of 2^-25 (FP32 solves) or 1e-14 (FP64 solves) per entry
+// (|dP_ab| <= tol sqrt(P_aa P_bb)): below the solve's own rounding.  When the
+// table does not reach that point (slowly converging models) the solve keeps
+// the per-step combine paths of scan.cuh.
 //
 // Every tabulated P_k is formed independently of the others from the FP64
 // plan-time tables of lti_fold.cuh: the value function before tile j (P_j),
@@ -38,6 +37,19 @@
 // matrices, the second with eigenvalues >= 1):
 //   P (I + C P)^-1 = (P^-1 + C)^-1 = Z^T Z,   (I + C P)^-1 = I - C Z^T Z,
 // so no pivoting is needed and every lane of a warp runs the same instructions.
+//
+// The solve (k_lti_scan) is a scan of affine maps.  A thread owns consecutive
+// steps; its filter map v -> Psi v + W (Psi = Phi^T, Phi = E_{k0} ... E_{k0+K-1}
+// the composition of its closed-loop maps, data-independent) and its RTS map
+// x -> Phi x + beta compose over the threads of a tile and over the tiles.
+// Only the offsets W and beta depend on the data.  Tiles whose threads all
+// start after kc share Phi = Phi_inf, so the linear parts of every partial
+// composition inside such a tile are powers Phi_inf^d (a plan-time table of
+// B + 1 matrices) and the in-tile scans run on offsets alone (one N x N
+// matrix-vector product per shuffle level).  The first tiles (before kc) take
+// K_t = 16 / sizeof(S) steps per thread, read their per-step E_k (and P_k b)
+// from shared memory (one bulk copy per tile) and compose full maps, as does
+// the last tile.
 #pragma once
 #include "scan.cuh"
 
@@ -45,41 +57,35 @@ namespace mapk {
 
 // Layout of the step-table buffer (offsets in bytes): a few counters, the
 // FP64 pre_s (A, C, J; s < BMAX), the FP64 i-step folds (A, C, J; i <= KMAX)
-// and the FP64 P_j of the tiles (all full N x N matrices), then the rows of
-// the steps k < KT in the solve's precision S (E, MC packed, o, mb, P packed)
-// and the composite maps Phi of the threads that start at k = g K < KT.
+// and the FP64 P_j of the tiles of the uniform (B, K) decomposition (all full
+// N x N matrices), then per step k < KT: the row in the solve's precision S
+// (E, o, mb, P b, P packed) and E in FP64, and for the thread starts
+// k = g K_t < KT the K_t-step maps Phi_g in S and in FP64.
 template <int N, typename S>
 struct StepTab {
     static constexpr int NN = N * N, NS = Sym<N>::SZ;
-    static constexpr int oE = 0, oMC = NN, oO = NN + NS, oMB = NN + NS + N, oP = NN + NS + 2 * N;
-    static constexpr int RS = ((NN + 2 * NS + 2 * N) * (int)sizeof(S) + 15) / 16 * 16 / (int)sizeof(S);
+    static constexpr int oE = 0, oO = NN, oMB = NN + N, oPB = NN + 2 * N, oP = NN + 3 * N;
+    static constexpr int RS = ((NN + 3 * N + NS) * (int)sizeof(S) + 15) / 16 * 16 / (int)sizeof(S);
     static constexpr int BMAX = 128, KMAX = 64;
+    static constexpr int KT_STEPS = 16 / (int)sizeof(S);      // steps per thread before kc
     __host__ __device__ static constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
     __host__ __device__ static constexpr size_t pre_off() { return 256; }
     __host__ __device__ static constexpr size_t fold_off() { return al(pre_off() + sizeof(double) * BMAX * 3 * NN); }
     __host__ __device__ static constexpr size_t p64_off() { return al(fold_off() + sizeof(double) * (KMAX + 1) * 3 * NN); }
     __host__ __device__ static constexpr size_t rows_off(long nt) { return al(p64_off() + sizeof(double) * nt * NN); }
-    __host__ __device__ static constexpr long phi_count(long kt) { return kt / 8 + 2; }
-    __host__ __device__ static constexpr size_t phi_off(long nt, long kt) { return al(rows_off(nt) + sizeof(S) * kt * RS); }
-    // then the same constants (E, MC, o, mb: WC components) warp-interleaved by
-    // thread: component c of step i of thread g at ((g/32 K + i) WC + c) 32 + g%32,
-    // so that a warp's load of one component of one step is one 128-byte line
-    static constexpr int WC = NN + NS + 2 * N;
-    __host__ __device__ static constexpr long wi_threads(long kt, int K) { return ((kt + K - 1) / K + 31) / 32 * 32; }
-    __host__ __device__ static constexpr size_t wi_off(long nt, long kt)
+    __host__ __device__ static constexpr size_t e64_off(long nt, long kt) { return al(rows_off(nt) + sizeof(S) * kt * RS); }
+    __host__ __device__ static constexpr long phit_count(long kt) { return kt / KT_STEPS + 1; }
+    __host__ __device__ static constexpr size_t phit_off(long nt, long kt) { return al(e64_off(nt, kt) + sizeof(double) * kt * NN); }
+    __host__ __device__ static constexpr size_t phit64_off(long nt, long kt)
     {
-        return al(phi_off(nt, kt) + sizeof(S) * phi_count(kt) * NN);
+        return al(phit_off(nt, kt) + sizeof(S) * phit_count(kt) * NN);
     }
-    __host__ __device__ static constexpr long wi_index(long g, int i, int c, int K)
+    __host__ __device__ static constexpr size_t bytes(long nt, long kt)
     {
-        return (((g >> 5) * K + i) * WC + c) * 32 + (g & 31);
-    }
-    __host__ __device__ static constexpr size_t bytes(long nt, long kt, int K)
-    {
-        return wi_off(nt, kt) + sizeof(S) * (size_t)wi_threads(kt, K) * K * WC;
+        return phit64_off(nt, kt) + sizeof(double) * phit_count(kt) * NN;
     }
     // table length cap: the FP32 table converges within 2^-25 earlier
-    static constexpr long cap() { return sizeof(S) == 4 ? 16384 : 32768; }
+    __host__ __device__ static constexpr long cap() { return sizeof(S) == 4 ? 16384 : 32768; }
 };
 
 namespace steptab_detail {
@@ -193,15 +199,53 @@ __device__ __forceinline__ bool apply_p(const double* __restrict__ e, double (&P
     return ok;
 }
 
+// closed-loop map (I + Cf P)^-1 Af = Af - Cf Z^T (Z Af) of the fold (Af, Cf)
+// stored at f (full matrices) for the value function P
+template <int N>
+__device__ __forceinline__ bool fold_map(const double* __restrict__ f, const double (&P)[N * N], double (&Phi)[N * N])
+{
+    constexpr int NN = N * N;
+    double Af[NN], Cf[NN], Z[NN], ZA[NN], CZt[NN];
+    load_full<N>(f, Af);
+    load_full<N>(f + NN, Cf);
+#pragma unroll
+    for (int q = 0; q < NN; ++q) Cf[q] = 0.5 * (Cf[q] + Cf[(q % N) * N + q / N]);
+    const bool ok = zfactor<N>(P, Cf, Z);
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double za = 0.0, cz = 0.0;
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                za = fma(Z[a * N + q], Af[q * N + c], za);
+                cz = fma(Cf[a * N + q], Z[c * N + q], cz);
+            }
+            ZA[a * N + c] = za;
+            CZt[a * N + c] = cz;
+        }
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double e = Af[a * N + c];
+#pragma unroll
+            for (int q = 0; q < N; ++q) e = fma(-CZt[a * N + q], ZA[q * N + c], e);
+            Phi[a * N + c] = e;
+        }
+    return ok;
+}
+
 }  // namespace steptab_detail
 
 // One thread per tabulated step k < KT (FP64): P_k from the tile, thread-prefix
 // and i-step tables (see the top of this file), then the row of constants and,
-// for the first step of a thread (k = g K), the thread's composite closed-loop
-// map Phi_g = (I + C_K P_k)^-1 A_K of its K-step fold (the composition of its
-// K per-step maps: the closed-loop map of the combined element).  With check,
-// every step whose P_k differs from P_ref beyond tol raises meta[0] to k + 1;
-// meta[1] counts non-positive Cholesky pivots.
+// for the first step of a thread of K_t steps (k = g K_t), the thread's
+// composite closed-loop map Phi_g = (I + C_Kt P_k)^-1 A_Kt of its K_t-step
+// fold (the composition of its K_t per-step maps: the closed-loop map of the
+// combined element).  With check, every step whose P_k differs from P_ref
+// beyond tol raises meta[0] to k + 1; meta[1] counts non-positive Cholesky
+// pivots.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, int check, double tol,
@@ -209,7 +253,7 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
 {
     namespace sd = steptab_detail;
     using ST = StepTab<N, S>;
-    constexpr int NN = N * N;
+    constexpr int NN = N * N, Kt = ST::KT_STEPS;
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= KT) return;
     const double* pre = reinterpret_cast<const double*>(tab + ST::pre_off());
@@ -217,6 +261,7 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
     const double* p64 = reinterpret_cast<const double*>(tab + ST::p64_off());
     unsigned long long* meta = reinterpret_cast<unsigned long long*>(tab);
     S* row = reinterpret_cast<S*>(tab + ST::rows_off(nt)) + k * ST::RS;
+    double* e64 = reinterpret_cast<double*>(tab + ST::e64_off(nt, KT)) + k * NN;
     const long L = (long)B * K;
     const int j = (int)(k / L), s = (int)((k % L) / K), i = (int)(k % K);
     double P[NN];
@@ -224,7 +269,7 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
     bool ok = true;
     if (s > 0) ok = sd::apply_p<N>(pre + (long)s * 3 * NN, P) && ok;
     if (i > 0) ok = sd::apply_p<N>(fold + (long)i * 3 * NN, P) && ok;
-    // per-step constants from Z of (P, C)
+    // per-step constants from Z of (P, C): E = A - C Z^T (Z A), mb = b - C Z^T (Z b)
     double A[NN], C[NN], b[N], Z[NN], ZA[NN], CZt[NN];
 #pragma unroll
     for (int q = 0; q < NN; ++q) {
@@ -259,13 +304,6 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
         Zb[a] = zb;
         Pb[a] = pb;
     }
-    // the row, and the same constants in the warp-interleaved copy
-    S* wi = reinterpret_cast<S*>(tab + ST::wi_off(nt, KT));
-    const long g = k / K;
-    auto put = [&](int off, double val) {
-        row[off] = S(val);
-        wi[ST::wi_index(g, i, off, K)] = S(val);
-    };
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll
@@ -274,17 +312,8 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
 #pragma unroll
             for (int q = 0; q < N; ++q) e = fma(-CZt[a * N + q], ZA[q * N + c], e);
             E[a * N + c] = e;
-            put(ST::oE + a * N + c, e);
-        }
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int c = a; c < N; ++c) {
-            double mc = 0.5 * (C[a * N + c] + C[c * N + a]);
-#pragma unroll
-            for (int q = 0; q < N; ++q) mc = fma(-CZt[a * N + q], CZt[c * N + q], mc);
-            put(ST::oMC + Sym<N>::at(a, c), mc);
-            row[ST::oP + Sym<N>::at(a, c)] = S(P[a * N + c]);
+            row[ST::oE + a * N + c] = S(e);
+            e64[a * N + c] = e;
         }
 #pragma unroll
     for (int a = 0; a < N; ++a) {
@@ -294,41 +323,22 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
             mb = fma(-CZt[a * N + q], Zb[q], mb);
             o = fma(-E[q * N + a], Pb[q], o);
         }
-        put(ST::oMB + a, mb);
-        put(ST::oO + a, o);
+        row[ST::oMB + a] = S(mb);
+        row[ST::oO + a] = S(o);
+        row[ST::oPB + a] = S(Pb[a]);
+#pragma unroll
+        for (int c = a; c < N; ++c) row[ST::oP + Sym<N>::at(a, c)] = S(P[a * N + c]);
     }
-    if (i == 0) {
-        // Phi_g = (I + C_K P)^-1 A_K = A_K - C_K Z_K^T (Z_K A_K)
-        const double* fK = fold + (long)K * 3 * NN;
-        double AK[NN], CK[NN], ZK[NN];
-        sd::load_full<N>(fK, AK);
-        sd::load_full<N>(fK + NN, CK);
+    if (k % Kt == 0) {
+        double Ph[NN];
+        ok = sd::fold_map<N>(fold + (long)Kt * 3 * NN, P, Ph) && ok;
+        S* ph = reinterpret_cast<S*>(tab + ST::phit_off(nt, KT)) + (k / Kt) * NN;
+        double* ph64 = reinterpret_cast<double*>(tab + ST::phit64_off(nt, KT)) + (k / Kt) * NN;
 #pragma unroll
-        for (int q = 0; q < NN; ++q) CK[q] = 0.5 * (CK[q] + CK[(q % N) * N + q / N]);
-        ok = sd::zfactor<N>(P, CK, ZK) && ok;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                double za = 0.0, cz = 0.0;
-#pragma unroll
-                for (int q = 0; q < N; ++q) {
-                    za = fma(ZK[a * N + q], AK[q * N + c], za);
-                    cz = fma(CK[a * N + q], ZK[c * N + q], cz);
-                }
-                ZA[a * N + c] = za;
-                CZt[a * N + c] = cz;
-            }
-        S* ph = reinterpret_cast<S*>(tab + ST::phi_off(nt, KT)) + (k / K) * NN;
-#pragma unroll
-        for (int a = 0; a < N; ++a)
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                double e = AK[a * N + c];
-#pragma unroll
-                for (int q = 0; q < N; ++q) e = fma(-CZt[a * N + q], ZA[q * N + c], e);
-                ph[a * N + c] = S(e);
-            }
+        for (int q = 0; q < NN; ++q) {
+            ph[q] = S(Ph[q]);
+            ph64[q] = Ph[q];
+        }
     }
     if (check) {
         double Pr[NN];
@@ -345,366 +355,649 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
 }
 
 // ---------------------------------------------------------------------------
-// single-launch RTS solve with the per-step tables
+// tables of the tiled scan (k_lti_scan), computed once kc is known
 // ---------------------------------------------------------------------------
-template <typename S>
-struct TabArgs {
-    const S* rows;      // step rows (StepTab)
-    const S* phi;       // thread maps
-    const S* wi;        // the rows warp-interleaved by thread (threads that start before kc)
-    long kc;            // steps k >= kc read row kc
-    long gc;            // threads g >= gc read map gc
-};
-
-// per-step constants of one table row
-template <int N, typename S>
-struct StepC {
-    S E[N * N];
-    S MC[Sym<N>::SZ];
-    S o[N];
-    S mb[N];
-};
-
-template <int N, typename S>
-__device__ __forceinline__ void load_stepc(const S* __restrict__ row, StepC<N, S>& c)
-{
-    using ST = StepTab<N, S>;
-#pragma unroll
-    for (int q = 0; q < N * N; ++q) c.E[q] = __ldg(row + ST::oE + q);
-#pragma unroll
-    for (int q = 0; q < Sym<N>::SZ; ++q) c.MC[q] = __ldg(row + ST::oMC + q);
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        c.o[q] = __ldg(row + ST::oO + q);
-        c.mb[q] = __ldg(row + ST::oMB + q);
-    }
-}
-
-// step i of thread g from the warp-interleaved copy (coalesced over the warp)
-template <int N, typename S>
-__device__ __forceinline__ void load_stepc_wi(const S* __restrict__ wi, long g, int i, int K, StepC<N, S>& c)
-{
-    using ST = StepTab<N, S>;
-    const S* p = wi + ST::wi_index(g, i, 0, K);
-#pragma unroll
-    for (int q = 0; q < N * N; ++q) c.E[q] = __ldg(p + (ST::oE + q) * 32);
-#pragma unroll
-    for (int q = 0; q < Sym<N>::SZ; ++q) c.MC[q] = __ldg(p + (ST::oMC + q) * 32);
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        c.o[q] = __ldg(p + (ST::oO + q) * 32);
-        c.mb[q] = __ldg(p + (ST::oMB + q) * 32);
-    }
-}
-
-template <int N, typename S>
-__device__ __forceinline__ void load_stepE_wi(const S* __restrict__ wi, long g, int i, int K, S (&E)[N * N])
-{
-    using ST = StepTab<N, S>;
-    const S* p = wi + ST::wi_index(g, i, 0, K);
-#pragma unroll
-    for (int q = 0; q < N * N; ++q) E[q] = __ldg(p + (ST::oE + q) * 32);
-}
-
-template <int N, typename S>
-__device__ __forceinline__ void load_stepE(const S* __restrict__ row, S (&E)[N * N])
-{
-#pragma unroll
-    for (int q = 0; q < N * N; ++q) E[q] = __ldg(row + StepTab<N, S>::oE + q);
-}
-
-// shared memory of k_lti_solve_tab (offsets in scalars): the (b, eta) nodes
-// and the tile's prefix, the composition area, the tile's observations (bulk
-// copy), the Gamma_i, two mbarriers, the level constants and the co table;
-// after the thread prefixes the per-step g_k of every thread (K N scalars per
-// thread, in the tile's output order) overwrite the level constants and the
-// co table, and the RTS phase turns them into the states in place.
-template <int N, int M, typename S>
-struct TabSmem {
-    using FL = FoldLayout<N, M, S>;
-    using FS = FusedSmem<N, M, S>;
-    __host__ __device__ static constexpr int gst(int B, int K) { return FS::lv(B, K); }
-    __host__ __device__ static constexpr size_t bytes(int B, int K)
+// Tiling: J_t tiles of B threads x K_t steps cover [0, J_t B K_t) (J_t B K_t
+// >= kc), then tiles of B threads x K steps; tile j starts at
+// s_j = j B K_t (j < J_t) or J_t B K_t + (j - J_t) B K.
+struct ScanGeom {
+    int B, K, Kt, Jt, nt;
+    __host__ __device__ long start(int j) const
     {
-        const int e = FS::co(B, K) + B * FL::CS, g = gst(B, K) + B * K * N;
-        return sizeof(S) * (size_t)(e > g ? e : g);
+        return j < Jt ? (long)j * B * Kt : (long)Jt * B * Kt + (long)(j - Jt) * B * K;
     }
+    __host__ __device__ int steps(int j) const { return j < Jt ? Kt : K; }
 };
+
+// Layout of the scan buffer (offsets in bytes): the powers Phi_inf^d
+// (d = 0..BMAX), the per-step E_k (and P_k b) of the tiles before kc in the
+// order of their shared-memory copy (component c of step i of thread t at
+// (i CT + c) B + t), the tiles' offsets w_j and RTS maps, then the tile
+// tables of lti_fold.cuh (TileTables: F_j = E_j^T and the products Pi).
+template <int N, int M, typename S>
+struct ScanBuf {
+    static constexpr int NN = N * N, BMAX = 128, NTMAX = 4 * BMAX + 1;
+    static constexpr int CT = NN + N;                         // E, P b
+    using ST = StepTab<N, S>;
+    __host__ __device__ static constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
+    __host__ __device__ static constexpr long jt_max() { return ST::cap() / (BMAX * ST::KT_STEPS) + 2; }
+    __host__ __device__ static constexpr size_t pw_off() { return 0; }
+    __host__ __device__ static constexpr size_t ttab_off() { return al(sizeof(S) * (BMAX + 1) * NN); }
+    __host__ __device__ static constexpr size_t ttab_tile() { return (size_t)BMAX * ST::KT_STEPS * CT; }
+    __host__ __device__ static constexpr size_t w_off() { return al(ttab_off() + sizeof(S) * jt_max() * ttab_tile()); }
+    __host__ __device__ static constexpr size_t taff_off() { return al(w_off() + sizeof(S) * NTMAX * N); }
+    __host__ __device__ static constexpr size_t tiles_off() { return al(taff_off() + sizeof(S) * NTMAX * (NN + N)); }
+    __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::bytes(NTMAX); }
+};
+
+namespace scan_plan_detail {
+// c = a b (FP64 N x N in shared memory), lanes of one warp: entry q by lane q % 32
+template <int N>
+__device__ inline void wmul(const double* a, const double* b, double* c)
+{
+    for (int q = threadIdx.x & 31; q < N * N; q += 32) {
+        const int i = q / N, j = q - i * N;
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(a[i * N + k], b[k * N + j], s);
+        c[q] = s;
+    }
+    __syncwarp();
+}
+}  // namespace scan_plan_detail
+
+// Phi_inf = E_kc^K (FP64, warp 0, binary powers), then Phi_inf^d for
+// d = 0..B by doubling levels (Phi^d = Phi^(d - 2^l) Phi^(2^l), all d of a
+// level at once), written in S.  One CTA of 256 threads.
+template <int N, typename S>
+__global__ void __launch_bounds__(256) k_scan_powers(const double* __restrict__ e_kc, int K, int B, S* __restrict__ pw)
+{
+    namespace pd = scan_plan_detail;
+    constexpr int NN = N * N;
+    __shared__ double W[StepTab<N, S>::BMAX + 1][NN];
+    __shared__ double X[NN], Y[NN], Z[NN];
+    const int t = threadIdx.x;
+    if (t < 32) {
+        for (int q = t; q < NN; q += 32) {
+            X[q] = __ldg(e_kc + q);                       // E^(2^bit)
+            Y[q] = q % (N + 1) == 0 ? 1.0 : 0.0;          // accumulated power
+        }
+        __syncwarp();
+        for (int e = K; e > 0; e >>= 1) {
+            if (e & 1) {
+                pd::wmul<N>(Y, X, Z);
+                for (int q = t; q < NN; q += 32) Y[q] = Z[q];
+                __syncwarp();
+            }
+            if (e > 1) {
+                pd::wmul<N>(X, X, Z);
+                for (int q = t; q < NN; q += 32) X[q] = Z[q];
+                __syncwarp();
+            }
+        }
+        for (int q = t; q < NN; q += 32) {
+            W[0][q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+            W[1][q] = Y[q];
+        }
+    }
+    __syncthreads();
+    for (int l = 1; l < B; l <<= 1) {
+        // d in (l, min(2l, B)] from W[d - l] W[l] (both known after the level before)
+        const int cnt = (min(2 * l, B) - l) * NN;
+        for (int e = t; e < cnt; e += blockDim.x) {
+            const int d = l + 1 + e / NN, q = e % NN, i = q / N, jj = q - i * N;
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fma(W[d - l][i * N + k], W[l][k * N + jj], s);
+            W[d][q] = s;
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < (B + 1) * NN; e += blockDim.x) pw[e] = S(W[e / NN][e % NN]);
+}
+
+// Tile maps E_j (the composition of a tile's per-step closed-loop maps) as
+// F_j = E_j^T in the tile tables: a tile before kc multiplies the FP64 maps of
+// its B threads (one warp per tile, lanes over the entries), a later tile
+// takes Phi_inf^B.  The last tile's map is not used by the tile products.
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(128)
+k_scan_tilemaps(const double* __restrict__ phit64, ScanGeom g, const S* __restrict__ pw, char* __restrict__ tiles)
+{
+    namespace pd = scan_plan_detail;
+    using TT = TileTables<N, M, S>;
+    constexpr int NN = N * N;
+    __shared__ double Wk[4][3][NN];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int j = blockIdx.x * 4 + w;
+    if (j >= g.nt) return;
+    S* F = reinterpret_cast<S*>(tiles + TT::f_off(g.nt)) + (long)j * NN;
+    if (j >= g.Jt || j == g.nt - 1) {
+        const S* P = pw + (long)g.B * NN;
+        for (int q = l; q < NN; q += 32) F[q] = P[(q % N) * N + q / N];
+        return;
+    }
+    double* acc = Wk[w][0];
+    double* nxt = Wk[w][1];
+    double* tmp = Wk[w][2];
+    for (int q = l; q < NN; q += 32) acc[q] = __ldg(phit64 + ((long)j * g.B) * NN + q);
+    __syncwarp();
+    for (int t = 1; t < g.B; ++t) {
+        for (int q = l; q < NN; q += 32) nxt[q] = __ldg(phit64 + ((long)j * g.B + t) * NN + q);
+        __syncwarp();
+        pd::wmul<N>(acc, nxt, tmp);
+        for (int q = l; q < NN; q += 32) acc[q] = tmp[q];
+        __syncwarp();
+    }
+    for (int q = l; q < NN; q += 32) F[q] = S(acc[(q % N) * N + q / N]);
+}
+
+// Per-step E_k and P_k b of the tiles before kc, in the order of their
+// shared-memory copy; zeros past the table
+template <int N, typename S>
+__global__ void k_scan_ttab(const S* __restrict__ rows, long KT, ScanGeom g, S* __restrict__ ttab)
+{
+    using ST = StepTab<N, S>;
+    constexpr int NN = N * N, CT = NN + N;
+    const long per = (long)g.B * g.Kt * CT;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= per * g.Jt) return;
+    const int j = (int)(e / per);
+    const long r = e % per;
+    const int t = (int)(r % g.B), ic = (int)(r / g.B), i = ic / CT, c = ic % CT;
+    const long k = (long)j * g.B * g.Kt + (long)t * g.Kt + i;
+    S v = S(0);
+    if (k < KT) v = c < NN ? rows[k * ST::RS + ST::oE + c] : rows[k * ST::RS + ST::oPB + (c - NN)];
+    ttab[e] = v;
+}
+
+// ---------------------------------------------------------------------------
+// the tiled-scan solve
+// ---------------------------------------------------------------------------
+template <int N, typename S>
+struct ScanArgs {
+    const S* rows;          // step rows (StepTab)
+    long kc;                // steps k >= kc read row kc
+    const S* pw;            // Phi_inf^d, d = 0..B
+    const S* ttab;          // per-step E_k, P_k b of the tiles before kc
+    const S* phit;          // K_t-step thread maps before kc
+    S* w;                   // tile offsets of the filter maps
+    S* taff;                // tile RTS maps
+    const S* pi;            // tile-map products (TileTables)
+    const S* qt;
+    const S* pdummy;        // a readable P_j table for the tile-prefix helper (its P is not used)
+    ScanGeom g;
+    int has_b;              // b != 0: the o_k and P_k b terms
+    S AiC[N * N];           // A^-1 C
+    S Aib[N];               // A^-1 b
+};
+
+// shared memory of k_lti_scan (offsets in scalars): the composition area, the
+// warp totals, the tile's observations, the per-step offsets g_k (staged
+// states in the RTS phase; exchange area of the full-map compositions before
+// that), then the powers Phi_inf^d (tiles after kc) or the per-step E_k, P_k b
+// (tiles before kc), then the mbarrier
+template <int N, int M, typename S>
+struct ScanSmem {
+    static constexpr int NN = N * N, NA = NN + N, CT = NN + N;
+    __host__ __device__ static constexpr int al(int x) { return (x + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int red_size(int B) { return (B / 32) * (NA + N) + N; }
+    __host__ __device__ static constexpr int wt(int B) { return al(red_size(B)); }
+    __host__ __device__ static constexpr int ys(int B) { return al(wt(B) + 2 * (B / 32) * N + 2 * N); }
+    __host__ __device__ static constexpr int gst(int B, int Kmax) { return al(ys(B) + B * Kmax * M); }
+    __host__ __device__ static constexpr int tabs(int B, int Kmax)
+    {
+        return al(gst(B, Kmax) + (B * Kmax * N > B * NA ? B * Kmax * N : B * NA));
+    }
+    __host__ __device__ static constexpr int bar(int B, int K, int Kt)
+    {
+        // the tile kind with the larger footprint decides
+        const int a = tabs(B, K) + (B + 1) * NN, c = tabs(B, Kt) + B * Kt * CT;
+        return al(a > c ? a : c);
+    }
+    __host__ __device__ static constexpr size_t bytes(int B, int K, int Kt) { return sizeof(S) * (size_t)bar(B, K, Kt) + 16; }
+};
+
+template <int N, typename S>
+__device__ __forceinline__ void mat_vec(const S* __restrict__ Mx, const S* x, S* y)     // y = M x
+{
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        S acc = S(0);
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc = fma(Mx[a * N + q], x[q], acc);
+        y[a] = acc;
+    }
+}
+template <int N, typename S>
+__device__ __forceinline__ void mat_tvec(const S* __restrict__ Mx, const S* x, S* y)    // y = M^T x
+{
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        S acc = S(0);
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc = fma(Mx[q * N + a], x[q], acc);
+        y[a] = acc;
+    }
+}
+
+// The maps of the B threads exchanged so that thread t holds thread B-1-t's
+// map (scratch: B Aff records); ends with a barrier.  With the order of the
+// threads reversed, block_aff_reduce and block_aff_end_states compose the
+// filter maps in time order (the earlier map innermost).
+template <int N, typename S>
+__device__ __forceinline__ void reverse_maps(Aff<N, S>& H, S* scratch)
+{
+    constexpr int NA = Aff<N, S>::NCOMP;
+    const int B = blockDim.x, t = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < NA; ++c) scratch[c * B + (B - 1 - t)] = comp(H, c);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NA; ++c) comp(H, c) = scratch[c * B + t];
+    __syncthreads();
+}
+
+// N scalars of thread t moved to thread B-1-t; ends with a barrier
+template <int N, typename S>
+__device__ __forceinline__ void reverse_vec(S (&v)[N], S* scratch)
+{
+    const int B = blockDim.x, t = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < N; ++c) scratch[c * B + (B - 1 - t)] = v[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = scratch[c * B + t];
+    __syncthreads();
+}
 
 template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
-k_lti_solve_tab(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, const Red<N, S> prior,
-                S* __restrict__ tile_aff, S* __restrict__ filt_out, CombineCtx ctx, S* __restrict__ final_out,
-                S* __restrict__ x_out, S* __restrict__ filtT_out, const GridSync gs, const TabArgs<S> tb)
+k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restrict__ filt_out, CombineCtx ctx,
+           S* __restrict__ final_out, S* __restrict__ x_out, S* __restrict__ filtT_out, const GridSync gs,
+           const __grid_constant__ ScanArgs<N, S> sa)
 {
-    if constexpr (Prod::LINEAR_FOLD && N <= 6) {
-        constexpr int M = Prod::W, NN = N * N, NS = Sym<N>::SZ;
-        using FL = FoldLayout<N, M, S>;
-        using FS = FusedSmem<N, M, S>;
+    if constexpr (Prod::LINEAR_FOLD) {
+        constexpr int M = Prod::W, NN = N * N, NA = NN + N, CT = NN + N;
         using ST = StepTab<N, S>;
+        using SM = ScanSmem<N, M, S>;
         extern __shared__ __align__(16) unsigned char smem_raw[];
         S* sm = reinterpret_cast<S*>(smem_raw);
-        const int B = blockDim.x, t = threadIdx.x;
+        const ScanGeom& g = sa.g;
+        const int B = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = B >> 5;
         const int tile = blockIdx.x;
-        const long gthr = (long)tile * B + t;
-        const long k0 = gthr * K;
+        const bool trans = tile < g.Jt;                    // before kc: K_t steps, tabulated E_k in smem
+        const bool last = tile + 1 == g.nt;
+        const bool powers = !trans && !last;               // in-tile scans on offsets with Phi_inf^d
+        const int Kj = g.steps(tile);
+        const long s0 = g.start(tile);
+        const long k0 = s0 + (long)t * Kj;
         const long T = prod.T;
-        const bool last = tile + 1 == (int)gridDim.x;
-        const S* fold = lt.fold;
-        S* bq = sm + FS::bq(B);
-        S* ps = sm + FS::pin(B);
-        S* red = sm + FS::red(B);
-        S* ys = sm + FS::ys(B);
-        S* gam = sm + FS::gam(B, K);
-        S* lv = sm + FS::lv(B, K);
-        S* co = sm + FS::co(B, K);
-        S* gst = sm + TabSmem<N, M, S>::gst(B, K);
-        unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + FS::bar(B, K));
+        const int nv = (int)max(0L, min((long)Kj, T - k0));
+        S* red = sm;
+        S* wt = sm + SM::wt(B);
+        S* ys = sm + SM::ys(B);
+        S* gst = sm + SM::gst(B, Kj);
+        S* tb = sm + SM::tabs(B, Kj);                      // powers or per-step E_k, P_k b
+        unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + SM::bar(B, g.K, g.Kt));
+        S* mine = gst + t * Kj * N;
 
-        // ---- phase 1: the tile's observations, per-thread folds, up-sweep, w_j
-        const int LB = ilog2(B);
-        const unsigned ybytes = last ? 0u : (unsigned)(sizeof(S) * (size_t)B * K * M);
-        const unsigned lbytes = (unsigned)(sizeof(S) * (size_t)LB * FL::LS);
-        const unsigned cbytes = (unsigned)(sizeof(S) * (size_t)(B - 1) * FL::CS);
-        const unsigned gbytes = (unsigned)(sizeof(S) * (size_t)((K * FL::GS + 3) / 4 * 4));
-        unsigned long long* bar_co = bar + 1;
-        if (t == 0) {
-            mbar_init(bar, 1);
-            mbar_init(bar_co, 1);
-        }
+        // ---- phase 1: observations and tables into shared memory, the
+        // thread's filter offset W (map v -> Psi v + W from v = 0), the
+        // tile's filter offset w_j
+        // (rounded up to whole 16-byte words: both source tables and the shared
+        // area are padded to them)
+        const unsigned tbytes =
+            (unsigned)((sizeof(S) * (trans ? (size_t)B * g.Kt * CT : (size_t)(B + 1) * NN) + 15) / 16 * 16);
+        const long yoff = s0 * M;
+        const long ycnt = (long)B * Kj * M;
+        const bool ybulk = !last;                         // full tiles: one bulk copy of their rows
+        if (t == 0) mbar_init(bar, 1);
         __syncthreads();
         if (t == 0) {
-            mbar_arrive_expect_tx(bar, ybytes + lbytes + gbytes);
-            if (!last) bulk_copy_g2s(ys, prod.y + (long)tile * B * K * M, ybytes, bar);
-            bulk_copy_g2s(lv, fold + FL::oL, lbytes, bar);
-            bulk_copy_g2s(gam, fold + FL::oG, gbytes, bar);
-            mbar_arrive_expect_tx(bar_co, cbytes);
-            bulk_copy_g2s(co, fold + FL::oCo, cbytes, bar_co);
+            mbar_arrive_expect_tx(bar, tbytes + (ybulk ? (unsigned)(sizeof(S) * ycnt) : 0u));
+            if (ybulk) bulk_copy_g2s(ys, prod.y + yoff, (unsigned)(sizeof(S) * ycnt), bar);
+            bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * g.Kt * CT : sa.pw, tbytes, bar);
         }
-        if (!last) {
-            for (int q = t; q < NS; q += B) red[q] = lt.P[(long)tile * NS + q];
-            for (int q = t; q < NN; q += B) red[NS + q] = lt.F[(long)tile * NN + q];
+        if (!ybulk) {
+            const long have = T * M - yoff;
+            for (long q = t; q < ycnt; q += B) ys[q] = q < have ? prod.y[yoff + q] : S(0);
         }
-        if (last) {
-            const long base = (long)tile * B * K * M, have = T * M - base;
-            for (long q = t; q < (long)B * K * M; q += B) ys[q] = q < have ? prod.y[base + q] : S(0);
+        // constants of the steps after kc (row kc; only read by threads with steps)
+        S Einf[NN], oinf[N];
+        if (!trans && nv > 0) {
+            const S* r = sa.rows + sa.kc * ST::RS;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) Einf[q] = __ldg(r + ST::oE + q);
+#pragma unroll
+            for (int q = 0; q < N; ++q) oinf[q] = __ldg(r + ST::oO + q);
         }
         const bool ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
         if (!__syncthreads_and(ok)) {
             if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
-            mbar_wait_bounded(bar, 0, MBAR_POLLS);
+            mbar_wait_bounded(bar, 0, MBAR_POLLS);      // the copy may still be in flight
         }
-        const S* yt = ys + t * K * M;
-        S leaf[2 * N];
-        if (!last || k0 + K <= T) {
+        const S* yt = ys + t * Kj * M;
+        // step constants: E_k (and o_k) of step i of this thread
+        auto step_E = [&](int i, S (&E)[NN]) {
+            if (trans) {
 #pragma unroll
-            for (int q = 0; q < N; ++q) { leaf[q] = __ldg(fold + FL::ob + q); leaf[N + q] = __ldg(fold + FL::oe + q); }
-#pragma unroll 2
-            for (int i = 0; i < K; ++i) {
-                const S* gi = gam + i * FL::GS;
+                for (int q = 0; q < NN; ++q) E[q] = tb[(i * CT + q) * B + t];
+            } else {
 #pragma unroll
-                for (int a = 0; a < N; ++a)
-#pragma unroll
-                    for (int c = 0; c < M; ++c) {
-                        leaf[a] = fma(gi[a * M + c], yt[i * M + c], leaf[a]);
-                        leaf[N + a] = fma(gi[(N + a) * M + c], yt[i * M + c], leaf[N + a]);
-                    }
+                for (int q = 0; q < NN; ++q) E[q] = Einf[q];
             }
+        };
+        auto step_o = [&](int i, const S (&E)[NN], S (&o)[N]) {
+            if (!trans) {
+#pragma unroll
+                for (int q = 0; q < N; ++q) o[q] = oinf[q];
+            } else if (sa.has_b) {
+                S pb[N];
+#pragma unroll
+                for (int q = 0; q < N; ++q) pb[q] = tb[(i * CT + NN + q) * B + t];
+                S eo[N];
+                mat_tvec<N, S>(E, pb, eo);
+#pragma unroll
+                for (int q = 0; q < N; ++q) o[q] = -eo[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < N; ++q) o[q] = S(0);
+            }
+        };
+        // v <- E^T v + o + G y_{k+1} - Gr
+        auto fstep = [&](int i, const S (&E)[NN], S (&v)[N]) {
+            S o[N], nv2[N];
+            step_o(i, E, o);
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                S acc = o[a] - prod.p.Gr[a];
+#pragma unroll
+                for (int m = 0; m < M; ++m) acc = fma(prod.p.G[a * M + m], yt[i * M + m], acc);
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(E[q * N + a], v[q], acc);
+                nv2[a] = acc;
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) v[a] = nv2[a];
+        };
+        S W[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) W[a] = S(0);
+#pragma unroll 1
+        for (int i = 0; i < nv; ++i) {
+            S E[NN];
+            step_E(i, E);
+            fstep(i, E, W);
+        }
+        // the thread's map matrix Phi (RTS direction; the filter map's is Phi^T)
+        Aff<N, S> Fm;                                  // filter map (Psi, W) on the full-map path
+        S We[N];                                       // exclusive in-tile filter offset (powers path)
+        if (powers) {
+            // warp-inclusive prefix of the offsets: W_l <- Psi^d W_{l-d} + W_l
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                S o[N], p[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) o[a] = __shfl_up_sync(0xffffffffu, W[a], d);
+                if (lane >= d) {
+                    mat_tvec<N, S>(tb + d * NN, o, p);
+#pragma unroll
+                    for (int a = 0; a < N; ++a) W[a] += p[a];
+                }
+            }
+            if (lane == 31)
+#pragma unroll
+                for (int a = 0; a < N; ++a) wt[wid * N + a] = W[a];
+            __syncthreads();
+            S WP[N];                                   // composition of the warps before this one
+#pragma unroll
+            for (int a = 0; a < N; ++a) WP[a] = S(0);
+            for (int w2 = 0; w2 < wid; ++w2) {
+                S p[N];
+                mat_tvec<N, S>(tb + 32 * NN, WP, p);
+#pragma unroll
+                for (int a = 0; a < N; ++a) WP[a] = p[a] + wt[w2 * N + a];
+            }
+            {
+                S p[N];
+                mat_tvec<N, S>(tb + (lane + 1) * NN, WP, p);
+#pragma unroll
+                for (int a = 0; a < N; ++a) W[a] += p[a];          // inclusive tile prefix
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const S up = __shfl_up_sync(0xffffffffu, W[a], 1);
+                We[a] = lane == 0 ? WP[a] : up;
+            }
+            if (t == B - 1)
+#pragma unroll
+                for (int a = 0; a < N; ++a) sa.w[(long)tile * N + a] = W[a];
         } else {
+            // full maps: Phi of this thread (table, or the product of its steps)
+            if (nv == Kj && trans) {
 #pragma unroll
-            for (int c = 0; c < 2 * N; ++c) leaf[c] = S(0);
-        }
+                for (int q = 0; q < NN; ++q) Fm.F[q] = __ldg(sa.phit + ((long)tile * B + t) * NN + q);
+            } else if (nv == Kj) {
 #pragma unroll
-        for (int c = 0; c < 2 * N; ++c) bq[c * B + t] = leaf[c];
-        lti_tree_up<N, M, S>(bq, lv);
-        if (!last && t == 0) {                     // w_j = eta_j - F_j P_j b_j
-            const S* rq = bq + lti_node_level(2 * N, B, ilog2(B));
-            S Pb[N];
+                for (int q = 0; q < NN; ++q) Fm.F[q] = tb[NN + q];            // Phi_inf
+            } else {
 #pragma unroll
-            for (int a = 0; a < N; ++a) {
-                S acc = S(0);
+                for (int q = 0; q < NN; ++q) Fm.F[q] = q % (N + 1) == 0 ? S(1) : S(0);
+#pragma unroll 1
+                for (int i = 0; i < nv; ++i) {
+                    S E[NN], F2[NN];
+                    step_E(i, E);
+                    ms::mm<N, S>(Fm.F, E, F2);
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc = fma(red[Sym<N>::at(a, c)], rq[c], acc);
-                Pb[a] = acc;
+                    for (int q = 0; q < NN; ++q) Fm.F[q] = F2[q];
+                }
+            }
+            // filter map: matrix Phi^T, offset W
+            {
+                S Ft[NN];
+#pragma unroll
+                for (int q = 0; q < NN; ++q) Ft[q] = Fm.F[(q % N) * N + q / N];
+#pragma unroll
+                for (int q = 0; q < NN; ++q) Fm.F[q] = Ft[q];
             }
 #pragma unroll
-            for (int a = 0; a < N; ++a) {
-                S acc = rq[N + a];
+            for (int a = 0; a < N; ++a) Fm.c[a] = W[a];
+            if (!last) {
+                Aff<N, S> H = Fm;
+                reverse_maps<N, S>(H, gst);
+                block_aff_reduce<N, S>(H, red);        // F_{B-1} o ... o F_0 in thread 0
+                if (t == 0)
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc = fma(-red[NS + a * N + c], Pb[c], acc);
-                lt.w[(long)tile * N + a] = acc;
+                    for (int a = 0; a < N; ++a) sa.w[(long)tile * N + a] = H.c[a];
             }
         }
         grid_sync(gs, 1, ctx.stats);
 
-        // ---- phase 2: tile prefix, thread prefixes, per-step filter, tile map
-        Red<N, S> pin, X;
-        lti_tile_prefix_sum<N, S>(lt, tile, gridDim.x, prior, red, pin);
-        if (t == 0) node_store(pin, ps);
-        if (!mbar_wait_bounded(bar_co, 0, MBAR_POLLS) && ctx.stats && t == 0) atomicAdd(ctx.stats + 2, 1ull);
-        lti_tree_down_linear<N, M, S>(bq, co);     // starts and ends with a barrier
-        {
-            Red<N, S> P;
-            node_load(ps, P);
-            S dl[2 * N];
-#pragma unroll
-            for (int c = 0; c < 2 * N; ++c) dl[c] = bq[c * B + t];
-            if (k0 < T)
-                lti_thread_value<N, M, S>(fold, dl, P, ctx, X);
-            else
-                X = P;
-        }
-        __syncthreads();                           // level constants and co table are dead: gst takes them
-        const int nv = (int)max(0L, min((long)K, T - k0));   // this thread's steps before T
-        const bool steady = k0 >= tb.kc;
-        StepC<N, S> c;
-        if (steady && nv > 0) load_stepc<N, S>(tb.rows + tb.kc * ST::RS, c);   // row kc exists when kc < T
-        S* mine = gst + t * K * N;
+        // ---- phase 2: tile prefix, thread start values, per-step filter,
+        // thread RTS maps and the tile's RTS map
         S v[N];
+        {
+            LtiTiles<S> lt{};
+            lt.qt = sa.qt;
+            lt.pi = sa.pi;
+            lt.w = sa.w;
+            lt.P = sa.pdummy;
+            Red<N, S> pin;
+            lti_tile_prefix_sum<N, S>(lt, tile, g.nt, prior, red, pin);
+            S* vt = wt + 2 * (B / 32) * N;
+            if (t == 0)
 #pragma unroll
-        for (int a = 0; a < N; ++a) v[a] = X.v[a];
-        // forward: g_k = MC v_k + mb; v_{k+1} = E^T v_k + o + G y_{k+1} - Gr
-        // (threads that start before kc read the interleaved rows, two steps
-        // per iteration so that the next step's loads are in flight)
-        auto fwd = [&](int i, const StepC<N, S>& c) {
+                for (int a = 0; a < N; ++a) vt[a] = pin.v[a];
+            __syncthreads();
+            S vtile[N];
+#pragma unroll
+            for (int a = 0; a < N; ++a) vtile[a] = vt[a];
+            if (powers) {
+                S p[N];
+                mat_tvec<N, S>(tb + t * NN, vtile, p);
+#pragma unroll
+                for (int a = 0; a < N; ++a) v[a] = p[a] + We[a];
+            } else {
+                // v at thread t's start = (F_{t-1} o ... o F_0)(v_tile): the end
+                // states of the reversed sequence
+                Aff<N, S> H = Fm;
+                reverse_maps<N, S>(H, gst);
+                S* xe = vt;                            // block_aff_end_states reads thread 0's copy
+                S r[N];
+                block_aff_end_states<N, S>(H, xe, red, r);
+                reverse_vec<N, S>(r, gst);
+#pragma unroll
+                for (int a = 0; a < N; ++a) v[a] = r[a];
+            }
+        }
+        // forward: g_k = E_k (A^-1 C v_k + A^-1 b) staged; v_{k+1} = E_k^T v_k + o_k + G y - Gr
+#pragma unroll 1
+        for (int i = 0; i < nv; ++i) {
             const long k = k0 + i;
-            const S* row = tb.rows + min(k, tb.kc) * ST::RS;
+            S E[NN];
+            step_E(i, E);
             if (filt_out) {
+                const S* r = sa.rows + min(k, sa.kc) * ST::RS;
 #pragma unroll
                 for (int a = 0; a < N; ++a) filt_out[k * Red<N, S>::NCOMP + a] = v[a];
 #pragma unroll
-                for (int q = 0; q < NS; ++q) filt_out[k * Red<N, S>::NCOMP + N + q] = __ldg(row + ST::oP + q);
+                for (int q = 0; q < Sym<N>::SZ; ++q) filt_out[k * Red<N, S>::NCOMP + N + q] = __ldg(r + ST::oP + q);
             }
-            S g[N], nvv[N];
+            S u[N], gk[N];
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-                S acc = c.mb[a];
+                S acc = sa.Aib[a];
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(c.MC[Sym<N>::at(a, q)], v[q], acc);
-                g[a] = acc;
+                for (int q = 0; q < N; ++q) acc = fma(sa.AiC[a * N + q], v[q], acc);
+                u[a] = acc;
             }
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                S acc = c.o[a] - prod.p.Gr[a];
-#pragma unroll
-                for (int m = 0; m < M; ++m) acc = fma(prod.p.G[a * M + m], yt[i * M + m], acc);
-#pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(c.E[q * N + a], v[q], acc);
-                nvv[a] = acc;
-            }
-            stage_state<N, S>(mine + i * N, g);
-#pragma unroll
-            for (int a = 0; a < N; ++a) v[a] = nvv[a];
-        };
-        if (steady) {
-#pragma unroll 1
-            for (int i = 0; i < nv; ++i) fwd(i, c);
-        } else {
-            int i = 0;
-#pragma unroll 1
-            for (; i + 1 < nv; i += 2) {
-                StepC<N, S> c0, c1;
-                load_stepc_wi<N, S>(tb.wi, gthr, i, K, c0);
-                load_stepc_wi<N, S>(tb.wi, gthr, i + 1, K, c1);
-                fwd(i, c0);
-                fwd(i + 1, c1);
-            }
-            if (i < nv) {
-                load_stepc_wi<N, S>(tb.wi, gthr, i, K, c);
-                fwd(i, c);
-            }
+            mat_vec<N, S>(E, u, gk);
+            stage_state<N, S>(mine + i * N, gk);
+            fstep(i, E, v);
         }
         S* xT = x_out + T * N;
-        if (last && k0 < T && k0 + K >= T) {        // the value function at x_T and its minimiser
+        if (last && k0 < T && k0 + Kj >= T) {          // the value function at x_T and its minimiser
             Red<N, S> XT;
-            const S* rT = tb.rows + min(T, tb.kc) * ST::RS;
+            const S* rT = sa.rows + min(T, sa.kc) * ST::RS;
 #pragma unroll
             for (int a = 0; a < N; ++a) XT.v[a] = v[a];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) XT.P[q] = __ldg(rT + ST::oP + q);
+            for (int q = 0; q < Sym<N>::SZ; ++q) XT.P[q] = __ldg(rT + ST::oP + q);
             if (final_out) aos_store(final_out, 0, XT);
             S xt[N];
             if (!red_argmin<N, S>(XT, xt) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
 #pragma unroll
             for (int a = 0; a < N; ++a) xT[a] = xt[a];
-            if (filtT_out) {
+            if (filtT_out)
 #pragma unroll
                 for (int q = 0; q < Red<N, S>::NCOMP; ++q) filtT_out[q] = comp(XT, q);
-            }
         }
-        // the thread's composite map x_{k0} = Phi x_{k0+nv} + beta: beta by
-        // Horner over the staged g_k, Phi from the table (full threads) or the
-        // product of the per-step E_k (the thread that reaches T)
-        // backward over the thread's steps: z <- E_k z + g_k from the staged g_k,
-        // the result optionally staged in place of g_k
+        // backward over the thread's steps: z <- E_k z + g_k (staged in place when asked)
         auto back = [&](S (&z)[N], bool stage) {
-            auto one = [&](int i, const S (&E)[NN]) {
-                S nz[N];
+#pragma unroll 1
+            for (int i = nv - 1; i >= 0; --i) {
+                S E[NN], nz[N];
+                step_E(i, E);
+                mat_vec<N, S>(E, z, nz);
 #pragma unroll
-                for (int a = 0; a < N; ++a) {
-                    S acc = mine[i * N + a];
-#pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(E[a * N + q], z[q], acc);
-                    nz[a] = acc;
-                }
-#pragma unroll
-                for (int a = 0; a < N; ++a) z[a] = nz[a];
+                for (int a = 0; a < N; ++a) z[a] = nz[a] + mine[i * N + a];
                 if (stage) stage_state<N, S>(mine + i * N, z);
-            };
-            if (steady) {
-#pragma unroll 1
-                for (int i = nv - 1; i >= 0; --i) one(i, c.E);
-            } else {
-                int i = nv - 1;
-#pragma unroll 1
-                for (; i >= 1; i -= 2) {
-                    S E0[NN], E1[NN];
-                    load_stepE_wi<N, S>(tb.wi, gthr, i, K, E0);
-                    load_stepE_wi<N, S>(tb.wi, gthr, i - 1, K, E1);
-                    one(i, E0);
-                    one(i - 1, E1);
-                }
-                if (i == 0) {
-                    S E0[NN];
-                    load_stepE_wi<N, S>(tb.wi, gthr, 0, K, E0);
-                    one(0, E0);
-                }
             }
         };
-        Aff<N, S> comp_t;
-        set_identity(comp_t);
-        back(comp_t.c, false);
-        if (nv == K) {
-            const S* ph = tb.phi + min(gthr, tb.gc) * NN;
+        S beta[N];
 #pragma unroll
-            for (int q = 0; q < NN; ++q) comp_t.F[q] = __ldg(ph + q);
-        } else {
-#pragma unroll 1
-            for (int i = 0; i < nv; ++i) {           // Phi <- Phi E_k
-                S E[NN], F2[NN];
-                load_stepE<N, S>(tb.rows + min(k0 + i, tb.kc) * ST::RS, E);
-                ms::mm<N, S>(comp_t.F, E, F2);
+        for (int a = 0; a < N; ++a) beta[a] = S(0);
+        back(beta, false);
+        S Be[N];                                       // exclusive in-tile RTS suffix offset (powers path)
+        Aff<N, S> Rm;                                  // RTS map (full-map path)
+        if (powers) {
+            // warp-inclusive suffix: B_l <- B_l + Phi^d B_{l+d}
+            S Bs[N];
 #pragma unroll
-                for (int q = 0; q < NN; ++q) comp_t.F[q] = F2[q];
+            for (int a = 0; a < N; ++a) Bs[a] = beta[a];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                S o[N], p[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) o[a] = __shfl_down_sync(0xffffffffu, Bs[a], d);
+                if (lane + d < 32) {
+                    mat_vec<N, S>(tb + d * NN, o, p);
+#pragma unroll
+                    for (int a = 0; a < N; ++a) Bs[a] += p[a];
+                }
             }
-        }
-        {
-            Aff<N, S> H = comp_t;
-            block_aff_reduce<N, S>(H, red);       // starts with shuffles, ends with a barrier
-            if (t == 0) aos_store(tile_aff, (long)tile, H);
+            S* bt = wt + (B / 32) * N;
+            if (lane == 0)
+#pragma unroll
+                for (int a = 0; a < N; ++a) bt[wid * N + a] = Bs[a];
+            __syncthreads();
+            S BN[N];                                   // composition of the warps after this one
+#pragma unroll
+            for (int a = 0; a < N; ++a) BN[a] = S(0);
+            for (int w2 = nw - 1; w2 > wid; --w2) {
+                S p[N];
+                mat_vec<N, S>(tb + 32 * NN, BN, p);
+#pragma unroll
+                for (int a = 0; a < N; ++a) BN[a] = bt[w2 * N + a] + p[a];
+            }
+            {
+                S p[N];
+                mat_vec<N, S>(tb + (32 - lane) * NN, BN, p);
+#pragma unroll
+                for (int a = 0; a < N; ++a) Bs[a] += p[a];         // inclusive tile suffix
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const S dn = __shfl_down_sync(0xffffffffu, Bs[a], 1);
+                Be[a] = lane == 31 ? BN[a] : dn;
+            }
+            if (t == 0) {
+#pragma unroll
+                for (int a = 0; a < N; ++a) sa.taff[(long)tile * NA + NN + a] = Bs[a];
+            }
+        } else {
+            {
+                S Ft[NN];                              // back to the RTS direction
+#pragma unroll
+                for (int q = 0; q < NN; ++q) Ft[q] = Fm.F[(q % N) * N + q / N];
+#pragma unroll
+                for (int q = 0; q < NN; ++q) Rm.F[q] = Ft[q];
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) Rm.c[a] = beta[a];
+            Aff<N, S> H = Rm;
+            __syncthreads();                           // the composition area is free
+            block_aff_reduce<N, S>(H, red);
+            if (t == 0) aos_store(sa.taff, (long)tile, H);
         }
         grid_sync(gs, 2, ctx.stats);
 
         // ---- phase 3: tile suffix, thread end states, per-step states, bulk store
-        S* xe_sh = red + (B / 32) * (Aff<N, S>::NCOMP + N);
-        lti_tile_suffix_sum<N, S>(lt, tile_aff, tile, gridDim.x, xT, red, xe_sh);
         S x[N];
-        block_aff_end_states<N, S>(comp_t, xe_sh, red, x);
-        back(x, true);                               // x_k = E_k x_{k+1} + g_k, in place of g_k
+        {
+            LtiTiles<S> lt{};
+            lt.pi = sa.pi;
+            lt.qt = sa.qt;
+            lt.w = sa.w;
+            lt.P = sa.pdummy;
+            S* xe_sh = red + (B / 32) * (NA + N);
+            lti_tile_suffix_sum<N, S>(lt, sa.taff, tile, g.nt, xT, red, xe_sh);
+            if (powers) {
+                S xe[N], p[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) xe[a] = xe_sh[a];
+                mat_vec<N, S>(tb + (B - 1 - t) * NN, xe, p);
+#pragma unroll
+                for (int a = 0; a < N; ++a) x[a] = p[a] + Be[a];
+            } else {
+                block_aff_end_states<N, S>(Rm, xe_sh, red, x);
+            }
+        }
+        back(x, true);                                 // x_k = E_k x_{k+1} + g_k, in place of g_k
         __syncthreads();
-        const int KN = K * N;
-        const long base = (long)tile * B * KN;
-        const long cnt = min((long)B * KN, T * N - base);
+        const long base = s0 * N;
+        const long cnt = min((long)B * Kj * N, T * N - base);
         long done = 0;
         if ((reinterpret_cast<uintptr_t>(x_out + base) & 15) == 0) {
             done = cnt * (long)sizeof(S) / 16 * 16 / (long)sizeof(S);
