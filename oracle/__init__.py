@@ -60,6 +60,10 @@ def _load():
             _lib.orc_cost.argtypes = [i, i, i, i, d, D, D, d, D, D, D, D, D, D, D, D, D]
             _lib.orc_gauss_newton.argtypes = [i, i, i, i, d, D, D, d, D, D, D, D, D, D, D, D, i, D]
             _lib.orc_grad_lti.argtypes = [i, i, i, d, D, D, D, d, D, D, D, d, D, D, D, D, i, D, D]
+            _lib.orc_block_elements.argtypes = [i, i, i, i, d, D, D, D, D, D, D, D, D]
+            _lib.orc_exact_elements.argtypes = [i, i, i, d, D, D, D, D, D, D, D, D]
+            _lib.orc_smooth_elements.argtypes = [i, i, D, D, D, D, D, D]
+            _lib.orc_dense_block.argtypes = [i, i, i, i, d, D, D, D, D, D, D, D, D, D, D, D]
         return _lib
 
 
@@ -254,3 +258,58 @@ def grad_lti(model, y, dt, logq=0.0, logr=0.0, dLdx=None, logdet=False):
                                 _p(_f(model.P0)), _p(y), _p(None if dLdx is None else _f(dLdx)),
                                 int(bool(logdet)), _p(g), _p(x)))
     return g, x
+
+
+# ---------------------------------------------------------------- block and exact elements
+
+def block_elements(model, y, dt, nsub):
+    """Block elements (T, 3n^2+2n): nsub explicit Euler substeps of Eq. 37 per
+    interval (Section 5.1) with the interval's sample held, combined by Eq. 36."""
+    y = _f(y); T = y.shape[0]; n, m = model.nx, model.ny
+    out = np.empty((T, elem_size(n)))
+    _check(_load().orc_block_elements(n, m, T, int(nsub), dt, _p(_f(model.F)), _p(_f(model.c, (n,))),
+                                      _p(_f(model.Q)), _p(_f(model.H)), _p(_f(model.r, (m,))),
+                                      _p(_f(model.R)), _p(y), _p(out)))
+    return out
+
+
+def exact_elements(model, y, dt):
+    """Exact elements (T, 3n^2+2n): Eq. 37 solved over each interval with constant
+    coefficients and the interval's sample held (Hamiltonian matrix exponential)."""
+    y = _f(y); T = y.shape[0]; n, m = model.nx, model.ny
+    out = np.empty((T, elem_size(n)))
+    _check(_load().orc_exact_elements(n, m, T, dt, _p(_f(model.F)), _p(_f(model.c, (n,))), _p(_f(model.Q)),
+                                      _p(_f(model.H)), _p(_f(model.r, (m,))), _p(_f(model.R)), _p(y), _p(out)))
+    return out
+
+
+def smooth_elements(elems, m0, P0, return_filter=False):
+    """MAP trajectory (T+1, n) for per-step elements by the sequential KF + RTS."""
+    elems = _f(elems); T = elems.shape[0]; m0 = _f(m0); n = m0.shape[0]
+    x = np.empty((T + 1, n))
+    mf = np.empty((T + 1, n)) if return_filter else None
+    Pf = np.empty((T + 1, n, n)) if return_filter else None
+    _check(_load().orc_smooth_elements(n, T, _p(elems), _p(m0), _p(_f(P0)), _p(x), _p(mf), _p(Pf)))
+    return (x, mf, Pf) if return_filter else x
+
+
+def smooth_block(model, y, dt, nsub, return_filter=False):
+    """MAP trajectory of the block-element discretisation (Section 5.1)."""
+    return smooth_elements(block_elements(model, y, dt, nsub), model.m0, model.P0, return_filter)
+
+
+def smooth_exact(model, y, dt, return_filter=False):
+    """MAP trajectory of the exact-element discretisation (Eq. 37 solved exactly)."""
+    return smooth_elements(exact_elements(model, y, dt), model.m0, model.P0, return_filter)
+
+
+def dense_block(model, y, dt, nsub):
+    """States at every substep (nsub T + 1, n) of a block solve (Section 4.3
+    recovery between grid points) from its grid states and filter moments."""
+    y = _f(y); T = y.shape[0]; n, m = model.nx, model.ny
+    x, mf, Pf = smooth_block(model, y, dt, nsub, return_filter=True)
+    xd = np.empty((nsub * T + 1, n))
+    _check(_load().orc_dense_block(n, m, T, int(nsub), dt, _p(_f(model.F)), _p(_f(model.c, (n,))),
+                                   _p(_f(model.Q)), _p(_f(model.H)), _p(_f(model.r, (m,))), _p(_f(model.R)),
+                                   _p(y), _p(x), _p(mf), _p(_f(Pf)), _p(xd)))
+    return xd

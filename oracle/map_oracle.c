@@ -929,3 +929,207 @@ done:
     free(rk); free(sk); free(Cr); free(Cs); free(e); free(w); free(hl);
     return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* block elements, exact elements, dense output (Section 5.1, Eq. 37)  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Block elements (Section 5.1: T blocks of nsub substeps each, the backward
+ * conditional ODEs of Eq. 37 integrated by explicit Euler inside a block).
+ * Substep j of block k spans [t_k + j h, t_k + (j+1) h], h = dt / nsub; its
+ * element is one Euler step of Eq. 37 from the boundary values:
+ *   A = I - h F, b = -h c, C = h Q, J = h H^T R^-1 H, eta = h H^T R^-1 (y - r),
+ * with the block's sample y = y_{k+1} held over the block (Eq. 37 has a
+ * continuous measurement; the data are one sample per block).  The block
+ * element is the combination (Eq. 36) of its substeps, the later substep on
+ * the left.  elems: (T, 3n^2 + 2n).
+ */
+int orc_block_elements(int n, int m, int T, int nsub, double dt, const double *F, const double *c,
+                       const double *Q, const double *H, const double *r, const double *R,
+                       const double *y, double *elems)
+{
+    if (nsub < 1) return ORC_ERR_ARG;
+    size_t nn = (size_t)n * n, es = 3 * nn + 2 * (size_t)n;
+    const double h = dt / nsub;
+    double *A = (double *)malloc(sizeof(double) * nn), *b = (double *)malloc(sizeof(double) * n);
+    double *C = (double *)malloc(sizeof(double) * nn);
+    double *e = (double *)malloc(sizeof(double) * es), *acc = (double *)malloc(sizeof(double) * es);
+    double *tmp = (double *)malloc(sizeof(double) * es);
+    int rc = orc_discretise(n, h, F, c, Q, 0, A, b, C);
+    for (int k = 0; k < T && !rc; ++k) {
+        rc = orc_elements_lti(n, m, 1, h, A, b, C, H, r, R, y + (size_t)k * m, e);
+        memcpy(acc, e, sizeof(double) * es);
+        for (int j = 1; j < nsub && !rc; ++j) {
+            rc = orc_combine(n, e, acc, tmp);
+            memcpy(acc, tmp, sizeof(double) * es);
+        }
+        memcpy(elems + (size_t)k * es, acc, sizeof(double) * es);
+    }
+    free(A); free(b); free(C); free(e); free(acc); free(tmp);
+    return rc;
+}
+
+/*
+ * Exact elements: all five rows of Eq. 37 solved over [t_k, t_{k+1}] with
+ * constant coefficients and y = y_{k+1} held.  The element is the conditional
+ * minimum of the interval's cost; with the costate p of that minimisation the
+ * reversed-time state and costate obey the linear Hamiltonian system
+ *   d/ds [x; p; 1] = Z [x; p; 1],
+ *   Z = [[Ft, -Q, ct], [-H^T R^-1 H, -Ft^T, H^T R^-1 (y - r)], [0, 0, 0]],
+ * Ft = -F, ct = -c (time reversal, Section 2.2), and the element's gradients
+ * are dV/dz = -p(dt) = C^-1 (z - A phi - b) and dV/dphi = p(0) = J phi - eta
+ * - A^T C^-1 (z - A phi - b).  With Psi = e^{Z dt} in blocks (x, p, 1) this
+ * gives
+ *   C = -Psi12 Psi22^-1,  A = Psi11 + C Psi21,  J = -Psi22^-1 Psi21,
+ *   b = psi1 + C psi2,    eta = Psi22^-1 psi2.
+ * elems: (T, 3n^2 + 2n).
+ */
+int orc_exact_elements(int n, int m, int T, double dt, const double *F, const double *c,
+                       const double *Q, const double *H, const double *r, const double *R,
+                       const double *y, double *elems)
+{
+    size_t nn = (size_t)n * n, es = 3 * nn + 2 * (size_t)n;
+    const int d = 2 * n + 1;
+    double *Z = (double *)calloc((size_t)d * d, sizeof(double)), *E = (double *)malloc(sizeof(double) * d * d);
+    double *Ri = (double *)malloc(sizeof(double) * m * m), *HtRi = (double *)malloc(sizeof(double) * n * m);
+    double *W = (double *)malloc(sizeof(double) * nn), *u = (double *)malloc(sizeof(double) * m);
+    double *q = (double *)malloc(sizeof(double) * n);
+    double *P11 = (double *)malloc(sizeof(double) * nn), *P12 = (double *)malloc(sizeof(double) * nn);
+    double *P21 = (double *)malloc(sizeof(double) * nn), *P22 = (double *)malloc(sizeof(double) * nn);
+    double *P22i = (double *)malloc(sizeof(double) * nn), *t1 = (double *)malloc(sizeof(double) * nn);
+    double *p1 = (double *)malloc(sizeof(double) * n), *p2 = (double *)malloc(sizeof(double) * n);
+    int rc = ORC_OK;
+    if (inv(m, R, Ri)) { rc = ORC_ERR_SINGULAR; goto done; }
+    mTm(n, m, m, H, Ri, HtRi);
+    mm(n, m, n, HtRi, H, W);
+    for (int k = 0; k < T; ++k) {
+        for (int i = 0; i < m; ++i) u[i] = y[(size_t)k * m + i] - r[i];
+        mv(n, m, HtRi, u, q);
+        for (int i = 0; i < d * d; ++i) Z[i] = 0.0;
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                Z[i * d + j] = -F[i * n + j] * dt;                 /* Ft */
+                Z[i * d + n + j] = -Q[i * n + j] * dt;             /* -Q */
+                Z[(n + i) * d + j] = -W[i * n + j] * dt;           /* -H^T R^-1 H */
+                Z[(n + i) * d + n + j] = F[j * n + i] * dt;        /* -Ft^T */
+            }
+            Z[i * d + 2 * n] = -c[i] * dt;                         /* ct */
+            Z[(n + i) * d + 2 * n] = q[i] * dt;                    /* H^T R^-1 (y - r) */
+        }
+        expm(d, Z, E);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                P11[i * n + j] = E[i * d + j];
+                P12[i * n + j] = E[i * d + n + j];
+                P21[i * n + j] = E[(n + i) * d + j];
+                P22[i * n + j] = E[(n + i) * d + n + j];
+            }
+            p1[i] = E[i * d + 2 * n];
+            p2[i] = E[(n + i) * d + 2 * n];
+        }
+        if (inv(n, P22, P22i)) { rc = ORC_ERR_SINGULAR; goto done; }
+        double *e = elems + (size_t)k * es;
+        mm(n, n, n, P12, P22i, t1);
+        for (size_t i = 0; i < nn; ++i) E_C(e, n)[i] = -t1[i];             /* C */
+        symmetrise(n, E_C(e, n));
+        mm(n, n, n, E_C(e, n), P21, t1);
+        for (size_t i = 0; i < nn; ++i) E_A(e, n)[i] = P11[i] + t1[i];      /* A */
+        mm(n, n, n, P22i, P21, t1);
+        for (size_t i = 0; i < nn; ++i) E_J(e, n)[i] = -t1[i];              /* J */
+        symmetrise(n, E_J(e, n));
+        mv(n, n, E_C(e, n), p2, E_B(e, n));
+        for (int i = 0; i < n; ++i) E_B(e, n)[i] += p1[i];                   /* b */
+        mv(n, n, P22i, p2, E_ETA(e, n));                                     /* eta */
+    }
+done:
+    free(Z); free(E); free(Ri); free(HtRi); free(W); free(u); free(q);
+    free(P11); free(P12); free(P21); free(P22); free(P22i); free(t1); free(p1); free(p2);
+    return rc;
+}
+
+/*
+ * MAP trajectory for arbitrary per-step elements (original-time order,
+ * element k on [t_k, t_{k+1}]): the forward model of every element
+ * (orc_forward_model) and the Kalman filter + RTS smoother (orc_kf_rts) with
+ * the element's (J_k, eta_k) as the information term on x_{k+1}.
+ */
+int orc_smooth_elements(int n, int T, const double *elems, const double *m0, const double *P0,
+                        double *x, double *mf, double *Pf)
+{
+    size_t nn = (size_t)n * n, es = 3 * nn + 2 * (size_t)n;
+    double *Phi = (double *)malloc(sizeof(double) * (size_t)T * nn);
+    double *beta = (double *)malloc(sizeof(double) * (size_t)T * n);
+    double *Sig = (double *)malloc(sizeof(double) * (size_t)T * nn);
+    double *J = (double *)malloc(sizeof(double) * (size_t)T * nn);
+    double *eta = (double *)malloc(sizeof(double) * (size_t)T * n);
+    int rc = ORC_OK;
+    for (int k = 0; k < T && !rc; ++k) {
+        const double *e = elems + (size_t)k * es;
+        rc = orc_forward_model(n, E_A(e, n), E_B(e, n), E_C(e, n), Phi + (size_t)k * nn, beta + (size_t)k * n,
+                               Sig + (size_t)k * nn);
+        memcpy(J + (size_t)k * nn, E_J(e, n), sizeof(double) * nn);
+        memcpy(eta + (size_t)k * n, E_ETA(e, n), sizeof(double) * n);
+    }
+    if (!rc) rc = orc_kf_rts(n, T, Phi, nn, beta, n, Sig, nn, J, nn, eta, n, m0, P0, x, mf, Pf);
+    free(Phi); free(beta); free(Sig); free(J); free(eta);
+    return rc;
+}
+
+/*
+ * Dense output of a block solve (Section 4.3, recovery of x*(tau) between
+ * grid points): inside block k the filter value function at x_k (S = Pf_k^-1,
+ * v = S mf_k) is carried across the substeps by the one-variable combine
+ * (Eq. 36) with the substep elements, each substep's closed-loop map
+ * E = (I + C S)^-1 A, g = (I + C S)^-1 (b + C v) (Eq. 40-41) is kept, and the
+ * block's smoothed end state x_{k+1} is taken back through the maps.
+ * xd: (nsub T + 1, n), row k nsub + j the state at t_k + j h.
+ */
+int orc_dense_block(int n, int m, int T, int nsub, double dt, const double *F, const double *c,
+                    const double *Q, const double *H, const double *r, const double *R,
+                    const double *y, const double *x, const double *mf, const double *Pf, double *xd)
+{
+    size_t nn = (size_t)n * n, es = 3 * nn + 2 * (size_t)n;
+    const double h = dt / nsub;
+    double *A = (double *)malloc(sizeof(double) * nn), *b = (double *)malloc(sizeof(double) * n);
+    double *C = (double *)malloc(sizeof(double) * nn), *e = (double *)malloc(sizeof(double) * es);
+    double *S = (double *)malloc(sizeof(double) * nn), *v = (double *)malloc(sizeof(double) * n);
+    double *M = (double *)malloc(sizeof(double) * nn), *Mi = (double *)malloc(sizeof(double) * nn);
+    double *Em = (double *)malloc(sizeof(double) * (size_t)nsub * nn), *gm = (double *)malloc(sizeof(double) * (size_t)nsub * n);
+    double *t1 = (double *)malloc(sizeof(double) * nn), *t2 = (double *)malloc(sizeof(double) * nn);
+    double *u = (double *)malloc(sizeof(double) * n), *w = (double *)malloc(sizeof(double) * n);
+    int rc = orc_discretise(n, h, F, c, Q, 0, A, b, C);
+    for (int k = 0; k < T && !rc; ++k) {
+        rc = orc_elements_lti(n, m, 1, h, A, b, C, H, r, R, y + (size_t)k * m, e);
+        if (rc || inv(n, Pf + (size_t)k * nn, S)) { rc = rc ? rc : ORC_ERR_SINGULAR; break; }
+        mv(n, n, S, mf + (size_t)k * n, v);
+        for (int j = 0; j < nsub && !rc; ++j) {
+            mm(n, n, n, C, S, M);                                /* I + C S */
+            for (int i = 0; i < n; ++i) M[i * n + i] += 1.0;
+            if (inv(n, M, Mi)) { rc = ORC_ERR_SINGULAR; break; }
+            mm(n, n, n, Mi, A, Em + (size_t)j * nn);             /* E */
+            mv(n, n, C, v, u);
+            for (int i = 0; i < n; ++i) u[i] += b[i];
+            mv(n, n, Mi, u, gm + (size_t)j * n);                 /* g */
+            /* S <- A^T S E + J,  v <- E^T (v - S b) + eta */
+            mv(n, n, S, b, u);
+            for (int i = 0; i < n; ++i) u[i] = v[i] - u[i];
+            mTv(n, n, Em + (size_t)j * nn, u, w);
+            for (int i = 0; i < n; ++i) v[i] = w[i] + E_ETA(e, n)[i];
+            mm(n, n, n, S, Em + (size_t)j * nn, t1);
+            mTm(n, n, n, A, t1, t2);
+            for (size_t i = 0; i < nn; ++i) S[i] = t2[i] + E_J(e, n)[i];
+            symmetrise(n, S);
+        }
+        memcpy(u, x + (size_t)(k + 1) * n, sizeof(double) * n);
+        for (int j = nsub - 1; j >= 0; --j) {
+            mv(n, n, Em + (size_t)j * nn, u, w);
+            for (int i = 0; i < n; ++i) u[i] = w[i] + gm[(size_t)j * n + i];
+            memcpy(xd + ((size_t)k * nsub + j) * n, u, sizeof(double) * n);
+        }
+    }
+    if (!rc) memcpy(xd + (size_t)T * nsub * n, x + (size_t)T * n, sizeof(double) * n);
+    free(A); free(b); free(C); free(e); free(S); free(v); free(M); free(Mi); free(Em); free(gm);
+    free(t1); free(t2); free(u); free(w);
+    return rc;
+}
