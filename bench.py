@@ -97,30 +97,31 @@ K_SOLVE_DRAM_BYTES = None
 
 
 def work_model_tab(n, m, K, B, nt, wbytes):
-    """FLOP and minimal DRAM bytes per time step of the single-launch solve
-    with per-step tables (k_lti_solve_tab), counted from the kernel:
-      per step: the K-step fold's Gamma_i y (2 n m MAC), g_k = MC v + mb
-      (n^2), v_{k+1} = E^T v + o + G y (n^2 + n m), the thread map's offset
-      (n^2), the RTS step (n^2);
-      per thread (spread over its K steps): the one-variable combine of its
-      prefix with the tile's (4.5 n^3 + 2.5 n^2), its composite map's place
-      in the tile's shuffle composition and end states (2 (n^3 + n^2));
-      per tile (spread over its B K steps): the (b, eta) up- and down-sweeps
-      (2 (B - 1) 4 n^2) and the tile prefix and suffix sums (about nt / 2
-      terms of n^2 each).
+    """FLOP and minimal DRAM bytes per time step of the tiled-scan solve with
+    per-step tables (k_lti_scan), counted from the kernel for the tiles after
+    the stationary point (all but a few of the tiles):
+      per step: the filter offset E^T v + G y_{k+1} in phase 1 and again in
+      phase 2 (2 (n^2 + n m) MAC), g_k = E (A^-1 C v + A^-1 b) (2 n^2), the
+      RTS map's offset and the RTS step itself (2 n^2);
+      per thread (spread over its K steps): the warp shuffle scans of the
+      filter and RTS offsets with the power table (2 x 5 levels of n^2), the
+      warp carries (B / 32 - 1 of n^2 per direction) and the thread's start
+      values (4 n^2);
+      per tile (spread over its B K steps): the tile prefix and suffix sums
+      (about nt / 2 terms of n^2 each).
     Bytes: y in and x out (the per-step constants are plan-time tables of at
     most a few MB, L2-resident)."""
     L = B * K
-    per_step = 2 * n * m + n * n + (n * n + n * m) + n * n + n * n
-    per_thread = (4.5 * n ** 3 + 2.5 * n ** 2) + 2 * (n ** 3 + n ** 2)
-    per_tile = 2 * (B - 1) * 4 * n * n + 2 * (nt / 2.0) * n * n
+    per_step = 2 * (n * n + n * m) + 2 * n * n + 2 * n * n
+    per_thread = 2 * 5 * n * n + 2 * (B // 32 - 1) * n * n + 4 * n * n
+    per_tile = 2 * (nt / 2.0) * n * n
     mac = per_step + per_thread / K + per_tile / L
     return 2 * mac, wbytes * (m + n)
 
 
-# DRAM bytes (read + write) of one k_lti_solve_tab launch on the nx=4, T=2^20
+# DRAM bytes (read + write) of one k_lti_scan launch on the nx=4, T=2^20
 # FP32 workload from one ncu capture of the current version; None until then
-K_SOLVE_TAB_DRAM_BYTES = None
+K_SCAN_DRAM_BYTES = None
 
 
 def solve_bytes(n, m, wbytes):
@@ -360,8 +361,8 @@ def ours(args):
                     "achieved": achieved_tf if fa >= fh else achieved_gb,
                     "peak": alu_peak if fa >= fh else hbm_peak,
                     "unit": "TFLOP/s" if fa >= fh else "GB/s", "frac": max(fa, fh),
-                    "traffic": K_SOLVE_TAB_DRAM_BYTES if prec == "fp32" else None,
-                    "kernel": "k_lti_solve_tab (three phases, two grid barriers, one launch)",
+                    "traffic": K_SCAN_DRAM_BYTES if prec == "fp32" else None,
+                    "kernel": "k_lti_scan (tiled affine scan with per-step tables: three phases, two grid barriers, one launch)",
                     "alu": {"achieved_tflops": achieved_tf, "peak_tflops": alu_peak, "frac": fa,
                             "flop_per_step": flop_step, "peak_source": peak_source},
                     "hbm": {"achieved_gbs": achieved_gb, "peak_gbs": hbm_peak, "frac": fh,
@@ -665,8 +666,43 @@ def extras(dev, flush, stream):
         return {"workload": "parameter update + solve, OU nx=4, T=2^18, FP32", "ms": ms,
                 "solve_only_ms": solve_ms}
 
+    def block_dense():
+        # Section 5.1 block elements (10 Euler substeps per interval) and the
+        # dense output at every substep
+        model = synth.ou_model(4, 2, seed=1001)
+        nsub = 10
+        _, y = synth.simulate(model, T_FULL, DT, seed=1012, substeps=1)
+        sm = MapSmoother(model, T_FULL, DT, precision="fp32", discretisation="block", substeps=nsub)
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        x = torch.empty((T_FULL + 1, 4), dtype=torch.float32, device=dev)
+        ms = timed(lambda: sm.solve(yt, x_out=x), flush, stream, dev)
+        x, f, _ = sm.solve(yt, filt=True)
+        xd = torch.empty((T_FULL * nsub + 1, 4), dtype=torch.float32, device=dev)
+        ms_dense = timed(lambda: sm.dense(yt, x, f, out=xd), flush, stream, dev)
+        checks.append(("block_elements", "rel_err_vs_oracle", "smooth_block", (model, y, DT, nsub),
+                       x.cpu().numpy()))
+        checks.append(("block_elements", "dense_rel_err_vs_oracle", "dense_block", (model, y, DT, nsub),
+                       xd.cpu().numpy()))
+        sm.close()
+        return {"workload": "OU nx=4 ny=2, T=2^20, dt=1e-3, block elements of 10 Euler substeps, FP32, RTS; "
+                            "dense output at all 10 T + 1 substep times", "ms": ms,
+                "value": T_FULL / (ms * 1e-3), "unit": UNIT, "dense_ms": ms_dense}
+
+    def exact():
+        model = synth.ou_model(4, 2, seed=1001)
+        _, y = synth.simulate(model, T_FULL, DT, seed=1013, substeps=1)
+        sm = MapSmoother(model, T_FULL, DT, precision="fp32", discretisation="exact")
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        x = torch.empty((T_FULL + 1, 4), dtype=torch.float32, device=dev)
+        ms = timed(lambda: sm.solve(yt, x_out=x), flush, stream, dev)
+        checks.append(("exact_elements", "rel_err_vs_oracle", "smooth_exact", (model, y, DT), x.cpu().numpy()))
+        sm.close()
+        return {"workload": "OU nx=4 ny=2, T=2^20, dt=1e-3, exact elements (Eq. 37 solved over each "
+                            "interval), FP32, RTS", "ms": ms, "value": T_FULL / (ms * 1e-3), "unit": UNIT}
+
     for name, fn in (("ou_nx8", ou8), ("two_filter", two_filter), ("coordinated_turn", coord_turn),
-                     ("batched", batched), ("gradient", gradient), ("parameter_update", parameter_update)):
+                     ("batched", batched), ("gradient", gradient), ("parameter_update", parameter_update),
+                     ("block_elements", block_dense), ("exact_elements", exact)):
         guard(name, fn)
     return out, checks
 

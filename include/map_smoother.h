@@ -64,7 +64,13 @@ typedef enum { MAP_FP64 = 0, MAP_FP32 = 1 } map_precision;
 typedef enum {
     MAP_EULER = 0,              /* one explicit Euler step of Eq. 37 per interval */
     MAP_EXPM = 1,               /* exact A, b, C of Eq. 37 (linear models only) */
-    MAP_AUTO = 2                /* MAP_EXPM when |F|_inf dt > 0.05, else MAP_EULER */
+    MAP_AUTO = 2,               /* MAP_EXPM when |F|_inf dt > 0.05, else MAP_EULER */
+    MAP_BLOCK_EULER = 3,        /* Section 5.1 blocks: desc.substeps explicit Euler steps of all
+                                   five rows of Eq. 37 per interval, the interval's sample held
+                                   over its substeps (linear models, RTS smoother) */
+    MAP_RICCATI_EXACT = 4       /* all five rows of Eq. 37 solved exactly with constant
+                                   coefficients, the interval's sample held (the limit of
+                                   MAP_BLOCK_EULER with many substeps; linear models, RTS) */
 } map_discretisation;
 
 typedef enum { MAP_RTS = 0, MAP_TWO_FILTER = 1 } map_smoother_kind;
@@ -88,6 +94,7 @@ typedef struct {
     double cond_max;            /* FP32: recompute a combine in FP64 when the infinity-norm
                                    condition estimate of (I + C J) exceeds this (0 = 1e6) */
     int tile_threads;           /* threads per tile CTA: 32, 64 or 128 (0 = 128, reduced to fit) */
+    int substeps;               /* MAP_BLOCK_EULER: Euler substeps per interval, 1..64 (0 = 10) */
 } map_problem_desc;
 
 /*
@@ -117,6 +124,24 @@ map_status map_smoother_create(map_smoother** out, const map_problem_desc* desc)
  */
 map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void* filt_out,
                               double* cost_out, void* stream);
+
+/*
+ * Dense output between the grid points of a MAP_BLOCK_EULER handle
+ * (Section 4.3, recovery of x*(tau) inside the intervals): for every interval
+ * k the filter value function at x_k is carried across the interval's
+ * substeps by the one-variable combine of Eq. 36 with the substep elements,
+ * and the smoothed x_{k+1} is taken back through the substeps' closed-loop
+ * maps (Eq. 40-41).
+ *   y          device, T x ny: the observations of the solve;
+ *   x          device, (T+1) x nx: the solve's trajectory;
+ *   filt       device, (T+1) x (nx + nx(nx+1)/2): the solve's filter output
+ *              (map_smoother_solve filt_out);
+ *   dense_out  device, (T substeps + 1) x nx: row k substeps + j holds the
+ *              state at t_k + j dt / substeps.
+ * Asynchronous on `stream`.  MAP_ERR_UNSUPPORTED for other discretisations.
+ */
+map_status map_smoother_dense(map_smoother* h, const void* y, const void* x, const void* filt,
+                              void* dense_out, void* stream);
 
 /*
  * Sequential baseline on the GPU: the same elements, information-filter
@@ -204,6 +229,9 @@ map_status map_smoother_phase_times(map_smoother* h, float* ms_out, int cap, int
  * per thread K, threads per tile CTA B and the number of tiles ceil(T / (B K)).
  * K is chosen at create time so that the tiles fill whole waves of the CTAs
  * that the GPU keeps resident (at least 8, at most 64 steps per thread).
+ * After a solve that ran the tiled scan with per-step tables
+ * (MAP_PATH_TABLES), K and tiles are that scan's: K steps per thread of the
+ * tiles after the stationary point and its number of tiles.
  * Returns MAP_ERR_INVALID_ARG for a NULL argument.
  */
 map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* tiles);

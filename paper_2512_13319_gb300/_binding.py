@@ -18,7 +18,7 @@ MAP_OK, MAP_ERR_INVALID_ARG, MAP_ERR_SHAPE, MAP_ERR_CUDA = 0, -1, -2, -3
 MAP_ERR_SINGULAR, MAP_ERR_TIMEOUT, MAP_ERR_UNSUPPORTED = -4, -5, -6
 MAP_MODEL_LINEAR, MAP_MODEL_COORD_TURN, MAP_MODEL_CUBIC = 0, 1, 2
 MAP_FP64, MAP_FP32 = 0, 1
-MAP_EULER, MAP_EXPM, MAP_AUTO = 0, 1, 2
+MAP_EULER, MAP_EXPM, MAP_AUTO, MAP_BLOCK_EULER, MAP_RICCATI_EXACT = 0, 1, 2, 3, 4
 MAP_RTS, MAP_TWO_FILTER = 0, 1
 
 _STATUS = {0: "MAP_OK", -1: "MAP_ERR_INVALID_ARG", -2: "MAP_ERR_SHAPE", -3: "MAP_ERR_CUDA",
@@ -35,6 +35,7 @@ class map_problem_desc(ctypes.Structure):
         ("m0", _D), ("P0", _D), ("gamma", ctypes.c_double),
         ("precision", ctypes.c_int), ("discretisation", ctypes.c_int), ("smoother", ctypes.c_int),
         ("gn_iters", ctypes.c_int), ("cond_max", ctypes.c_double), ("tile_threads", ctypes.c_int),
+        ("substeps", ctypes.c_int),
     ]
 
 
@@ -45,6 +46,7 @@ EXPORTS = {
     "map_smoother_solve": (_I, [_VP, _VP, _VP, _VP, _D, _VP]),
     "map_smoother_solve_sequential": (_I, [_VP, _VP, _VP, _VP]),
     "map_smoother_solve_host": (_I, [_VP, _VP, _VP, _VP]),
+    "map_smoother_dense": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "map_smoother_solve_noalloc": (_I, [ctypes.POINTER(map_problem_desc), _VP, _VP, _VP]),
     "map_smoother_grad": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP]),
     "map_smoother_update": (_I, [_VP, _D, ctypes.c_double, ctypes.c_double]),
@@ -133,6 +135,10 @@ def map_smoother_solve(h, y_ptr, x_ptr, filt_ptr=None, want_cost=False, stream=N
 
 def map_smoother_solve_sequential(h, y_ptr, x_ptr, stream=None):
     _check(load().map_smoother_solve_sequential(h, y_ptr, x_ptr, stream), h)
+
+
+def map_smoother_dense(h, y_ptr, x_ptr, filt_ptr, dense_ptr, stream=None):
+    _check(load().map_smoother_dense(h, y_ptr, x_ptr, filt_ptr, dense_ptr, stream), h)
 
 
 def map_smoother_solve_host(h, y_host_ptr, x_host_ptr, stream=None):
@@ -228,7 +234,7 @@ _MODEL_KIND = {"linear": MAP_MODEL_LINEAR, "coord_turn": MAP_MODEL_COORD_TURN, "
 
 
 def make_desc(model, T, dt, precision=MAP_FP32, discretisation=MAP_EULER, smoother=MAP_RTS,
-              gn_iters=1, cond_max=0.0, tile_threads=0, t0=0.0):
+              gn_iters=1, cond_max=0.0, tile_threads=0, t0=0.0, substeps=0):
     """Build a map_problem_desc from a ``synth.Model``; returns (desc, keepalive)."""
     n, m = model.nx, model.ny
     nw = model.L.shape[1]
@@ -248,4 +254,5 @@ def make_desc(model, T, dt, precision=MAP_FP32, discretisation=MAP_EULER, smooth
     d.gamma = float(model.params.get("gamma", 0.0))
     d.precision, d.discretisation, d.smoother = precision, discretisation, smoother
     d.gn_iters, d.cond_max, d.tile_threads = int(gn_iters), float(cond_max), int(tile_threads)
+    d.substeps = int(substeps)
     return d, arrs

@@ -88,4 +88,15 @@ __device__ __forceinline__ void bulk_commit_and_wait()
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
+// start bringing the bytes at src into L2 (the range widened to whole 16-byte
+// words: the caller's allocation must hold them); nothing waits for it, later
+// loads of the range hit L2
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes)
+{
+    const unsigned long long a = reinterpret_cast<unsigned long long>(src);
+    const unsigned long long lo = a & ~15ull, hi = (a + bytes + 15ull) & ~15ull;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 }  // namespace mapk

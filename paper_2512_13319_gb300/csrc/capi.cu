@@ -114,7 +114,7 @@ map_status run_setup(map_smoother* h)
         return cuda_fail(*h, e, "cudaMemcpy");
     const double* b = h->d_setup;
     SetupIn si{};
-    si.nx = n; si.ny = m; si.nw = nw; si.mode = h->disc; si.dt = h->dt;
+    si.nx = n; si.ny = m; si.nw = nw; si.mode = h->disc; si.dt = h->dt; si.substeps = h->substeps;
     size_t o = 0;
     si.F = b + o; o += (size_t)n * n;
     si.c = b + o; o += n;
@@ -142,8 +142,16 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(*h, MAP_ERR_INVALID_ARG, "dt must be positive");
     if (d->precision != MAP_FP32 && d->precision != MAP_FP64)
         return fail(*h, MAP_ERR_INVALID_ARG, "unknown precision");
-    if (d->discretisation < MAP_EULER || d->discretisation > MAP_AUTO)
+    if (d->discretisation < MAP_EULER || d->discretisation > MAP_RICCATI_EXACT)
         return fail(*h, MAP_ERR_INVALID_ARG, "unknown discretisation");
+    if (d->discretisation >= MAP_BLOCK_EULER) {
+        if (d->model != MAP_MODEL_LINEAR || d->smoother != MAP_RTS || n > 6)
+            return fail(*h, MAP_ERR_UNSUPPORTED,
+                        "block and exact elements are built for linear models with nx <= 6 and the RTS smoother");
+        if (d->substeps < 0 || d->substeps > 64)
+            return fail(*h, MAP_ERR_INVALID_ARG, "substeps must be in 1..64 (0 = 10)");
+    }
+    h->substeps = d->discretisation == MAP_BLOCK_EULER ? (d->substeps > 0 ? d->substeps : 10) : 1;
     if (d->smoother != MAP_RTS && d->smoother != MAP_TWO_FILTER)
         return fail(*h, MAP_ERR_INVALID_ARG, "unknown smoother");
     if (!d->L || !d->W || !d->R || !d->m0 || !d->P0)
@@ -344,6 +352,8 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
     map_status s = ops->solve(*h, y, x_out, filt_out, st);
     if (s != MAP_OK) return s;
     if (cost_out) {
+        if (h->disc >= MAP_BLOCK_EULER)
+            return fail(*h, MAP_ERR_UNSUPPORTED, "the MAP cost output is defined for per-step elements");
         if (h->consts.flags & SETUP_SINGULAR_C)
             return fail(*h, MAP_ERR_UNSUPPORTED, "the MAP cost needs an invertible process noise");
         if (!ops->cost) return fail(*h, MAP_ERR_UNSUPPORTED, "no cost kernel for this model");
@@ -364,6 +374,17 @@ map_status map_smoother_solve_sequential(map_smoother* h, const void* y, void* x
         return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
     return ops->solve_sequential(*h, y, x_out, static_cast<cudaStream_t>(stream));
+}
+
+map_status map_smoother_dense(map_smoother* h, const void* y, const void* x, const void* filt, void* dense_out,
+                              void* stream)
+{
+    if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }
+    if (!y || !x || !filt || !dense_out) return fail(*h, MAP_ERR_INVALID_ARG, "y, x, filt and dense_out are required");
+    const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
+    if (!ops->dense || h->disc != MAP_BLOCK_EULER)
+        return fail(*h, MAP_ERR_UNSUPPORTED, "dense output needs a linear model with MAP_BLOCK_EULER elements");
+    return ops->dense(*h, y, x, filt, dense_out, static_cast<cudaStream_t>(stream));
 }
 
 map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_host, void* stream)
@@ -437,9 +458,10 @@ map_status map_smoother_stats(map_smoother* h, unsigned long long out[3], int re
 map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* tiles)
 {
     if (!h || !K || !B || !tiles) return MAP_ERR_INVALID_ARG;
-    *K = h->K;
+    const bool scan = h->path == MAP_PATH_TABLES && h->sc_nt > 0;
+    *K = scan ? h->sc_K : h->K;
     *B = h->B;
-    *tiles = h->nt;
+    *tiles = scan ? h->sc_nt : h->nt;
     return MAP_OK;
 }
 

@@ -21,11 +21,25 @@
 
 namespace mapk {
 
-#define MAXD 17   // 2 * 8 + 1
+#define MAXD 32   // 4 * 8 (exact elements); 2 * 8 + 1 for the exponential of mode 1
+
+// working matrices of the block-element composition (mode 3)
+struct BlockWork {
+    double A[MAXN * MAXN], b0[MAXN], C[MAXN * MAXN], J[MAXN * MAXN];    // accumulated block
+    double Bb[MAXN * MAXM], Gy[MAXN * MAXM], g0[MAXN];
+    double An[MAXN * MAXN], b0n[MAXN], Cn[MAXN * MAXN], Jn[MAXN * MAXN];  // the next one
+    double Bbn[MAXN * MAXM], Gyn[MAXN * MAXM], g0n[MAXN];
+    double M[MAXN * MAXN], Mi[MAXN * MAXN], T1[MAXN * MAXN], T2[MAXN * MAXN], T3[MAXN * MAXN];
+    double U[MAXN * MAXM], u[MAXN];
+};
 
 struct SetupShared {
-    double Z[MAXD * MAXD], E[MAXD * MAXD], T1[MAXD * MAXD], T2[MAXD * MAXD];
+    union {
+        struct { double Z[MAXD * MAXD], E[MAXD * MAXD], T1[MAXD * MAXD], T2[MAXD * MAXD]; };
+        BlockWork bw;
+    };
     double X[8 * 8], Y[8 * 8];
+    double HR[MAXN * MAXM], Wm[MAXN * MAXN];   // H^T R^-1 and H^T R^-1 H (modes 3, 4)
     double inw[6][2 * MAXN * MAXN];        // per-warp scratch of the stage-3 warps
     double Gam[MAXN * MAXN];
     int flag;
@@ -223,6 +237,224 @@ __device__ void bexpm(SetupShared& s, int d)
     }
 }
 
+// y = a x (n x k matrix, k-vector), all threads; ends with a barrier
+__device__ void bmv(const double* a, const double* x, double* y, int n, int k)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s = fma(a[i * k + l], x[l], s);
+        y[i] = s;
+    }
+    __syncthreads();
+}
+
+// Block element (mode 3; Section 5.1): `substeps` explicit Euler steps of all
+// five rows of Eq. 37, each over h = dt / substeps from the boundary values,
+//   A_s = I - h F, b_s = -h c, C_s = h Q, J_s = h H^T R^-1 H,
+//   eta_s = h H^T R^-1 (y - r)   (the interval's sample y held),
+// combined in time order by Eq. 36 (the later substep i on the left of the
+// accumulated block j):
+//   Mi = (I + C_i J_j)^-1,  T1 = A_j Mi,  T2 = (Mi A_i)^T = A_i^T (I + J_j C_i)^-1,
+//   A = T1 A_i,  b = T1 (b_i + C_i eta_j) + b_j,  C = T1 C_i A_j^T + C_j,
+//   eta = T2 (eta_j - J_j b_i) + eta_i,  J = T2 J_j A_i + J_i.
+// b and eta stay affine in y: b = Bb y + b0, eta = Gy y - g0 (the substep
+// has Bb = 0, Gy = h H^T R^-1, g0 = Gy r).  Outputs A, b (= b0), C, J,
+// G (= Gy), Gr (= g0), Bb, and the substep element (sA, sb, sC, sJ, sG, sGr).
+__device__ void setup_block(const SetupIn& in, SetupShared& s, SetupOut* out)
+{
+    const int n = in.nx, m = in.ny, ns = in.substeps < 1 ? 1 : in.substeps;
+    const int nn = n * n, nm = n * m, tid = threadIdx.x, nth = blockDim.x;
+    const double h = in.dt / ns;
+    BlockWork& w = s.bw;
+    for (int e = tid; e < nn; e += nth) {
+        const int i = e / n, j = e % n;
+        out->sA[e] = w.A[e] = (i == j ? 1.0 : 0.0) - h * in.F[e];
+        out->sC[e] = w.C[e] = h * out->Q[e];
+        out->sJ[e] = w.J[e] = h * s.Wm[e];
+    }
+    for (int e = tid; e < nm; e += nth) {
+        out->sG[e] = w.Gy[e] = h * s.HR[e];
+        w.Bb[e] = 0.0;
+    }
+    for (int i = tid; i < n; i += nth) {
+        out->sb[i] = w.b0[i] = -h * in.c[i];
+        double acc = 0.0;
+        for (int l = 0; l < m; ++l) acc = fma(h * s.HR[i * m + l], in.r[l], acc);
+        out->sGr[i] = w.g0[i] = acc;
+    }
+    __syncthreads();
+    const double *Ai = out->sA, *Ci = out->sC, *Ji = out->sJ, *bi = out->sb, *Gi = out->sG, *gi = out->sGr;
+#pragma unroll 1
+    for (int step = 1; step < ns; ++step) {
+        bmm(Ci, w.J, w.M, n, n, n);                            // I + C_i J_j
+        for (int i = tid; i < n; i += nth) w.M[i * n + i] += 1.0;
+        __syncthreads();
+        if ((tid >> 5) == 0 && !winv(w.M, w.Mi, n, s.inw[0]) && (tid & 31) == 0) atomicOr(&s.flag, SETUP_SINGULAR_A);
+        __syncthreads();
+        bmm(w.A, w.Mi, w.T1, n, n, n);                         // T1 = A_j Mi
+        bmm(w.T1, Ai, w.An, n, n, n);                          // A = T1 A_i
+        bmm(w.T1, Ci, w.T2, n, n, n);                          // T1 C_i
+        for (int e = tid; e < nn; e += nth) {                  // C = T1 C_i A_j^T + C_j
+            const int i = e / n, j = e % n;
+            double acc = w.C[e];
+            for (int l = 0; l < n; ++l) acc = fma(w.T2[i * n + l], w.A[j * n + l], acc);
+            w.Cn[e] = acc;
+        }
+        bmm(Ci, w.Gy, w.U, n, n, m);                           // C_i Gy_j
+        bmm(w.T1, w.U, w.Bbn, n, n, m);
+        for (int e = tid; e < nm; e += nth) w.Bbn[e] += w.Bb[e];       // Bb = T1 C_i Gy_j + Bb_j
+        bmv(Ci, w.g0, w.u, n, n);                              // C_i g0_j
+        for (int i = tid; i < n; i += nth) w.u[i] = bi[i] - w.u[i];
+        __syncthreads();
+        bmv(w.T1, w.u, w.b0n, n, n);
+        for (int i = tid; i < n; i += nth) w.b0n[i] += w.b0[i];        // b0 = T1 (b_i - C_i g0_j) + b0_j
+        bmm(w.Mi, Ai, w.T3, n, n, n);                          // Mi A_i
+        for (int e = tid; e < nn; e += nth) w.T2[e] = w.T3[(e % n) * n + e / n];   // T2 = (Mi A_i)^T
+        __syncthreads();
+        bmm(w.T2, w.Gy, w.Gyn, n, n, m);
+        for (int e = tid; e < nm; e += nth) w.Gyn[e] += Gi[e];         // Gy = T2 Gy_j + Gy_i
+        bmv(w.J, bi, w.u, n, n);                               // J_j b_i
+        for (int i = tid; i < n; i += nth) w.u[i] += w.g0[i];
+        __syncthreads();
+        bmv(w.T2, w.u, w.g0n, n, n);
+        for (int i = tid; i < n; i += nth) w.g0n[i] += gi[i];          // g0 = T2 (g0_j + J_j b_i) + g0_i
+        bmm(w.T2, w.J, w.T3, n, n, n);
+        bmm(w.T3, Ai, w.Jn, n, n, n);
+        for (int e = tid; e < nn; e += nth) w.Jn[e] += Ji[e];          // J = T2 J_j A_i + J_i
+        __syncthreads();
+        for (int e = tid; e < nn; e += nth) {
+            w.A[e] = w.An[e];
+            w.C[e] = w.Cn[e];
+            w.J[e] = w.Jn[e];
+        }
+        for (int e = tid; e < nm; e += nth) {
+            w.Bb[e] = w.Bbn[e];
+            w.Gy[e] = w.Gyn[e];
+        }
+        for (int i = tid; i < n; i += nth) {
+            w.b0[i] = w.b0n[i];
+            w.g0[i] = w.g0n[i];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nn; e += nth) {
+        const int i = e / n, j = e % n;
+        out->A[e] = w.A[e];
+        out->C[e] = 0.5 * (w.C[i * n + j] + w.C[j * n + i]);
+        out->J[e] = 0.5 * (w.J[i * n + j] + w.J[j * n + i]);
+    }
+    for (int e = tid; e < nm; e += nth) {
+        out->Bb[e] = w.Bb[e];
+        out->G[e] = w.Gy[e];
+    }
+    for (int i = tid; i < n; i += nth) {
+        out->b[i] = w.b0[i];
+        out->Gr[i] = w.g0[i];
+    }
+    __syncthreads();
+}
+
+// Exact element (mode 4): all five rows of Eq. 37 with constant coefficients
+// over dt, the interval's sample y held.  The element is the conditional
+// minimum of the interval's cost; the reversed-time state x and costate p of
+// that minimisation obey d/ds [x; p] = K0 [x; p] + k with
+//   K0 = [[Ft, -Q], [-H^T R^-1 H, -Ft^T]],  k = [ct; H^T R^-1 (y - r)],
+// Ft = -F, ct = -c, and the element's gradients are dV/dz = -p(dt),
+// dV/dphi = p(0).  One exponential of [[K0 dt, I dt], [0, 0]] (order 4n)
+// gives Psi = e^{K0 dt} and L = int_0^dt e^{K0 u} du, the affine part being
+// psi = L k.  In blocks (x, p):
+//   C = -Psi12 Psi22^-1,  A = Psi11 + C Psi21,  J = -Psi22^-1 Psi21,
+//   b = psi1 + C psi2,    eta = Psi22^-1 psi2,
+// so, with HR = H^T R^-1,
+//   Bb = (L12 + C L22) HR,  b0 = -(L11 + C L21) c - Bb r,
+//   Gy = Psi22^-1 L22 HR,   g0 = Psi22^-1 L21 c + Gy r.
+// Scratch in the output arrays that the set-up overwrites afterwards (Phi,
+// Cinv, Qinv) and in X, Y.
+__device__ void setup_exact(const SetupIn& in, SetupShared& s, SetupOut* out)
+{
+    const int n = in.nx, m = in.ny, n2 = 2 * n, d = 4 * n, nn = n * n, tid = threadIdx.x, nth = blockDim.x;
+    const double h = in.dt;
+    for (int e = tid; e < d * d; e += nth) {
+        const int i = e / d, j = e % d;
+        double z = 0.0;
+        if (i < n && j < n) z = -in.F[i * n + j] * h;
+        else if (i < n && j < n2) z = -out->Q[i * n + (j - n)] * h;
+        else if (i >= n && i < n2 && j < n) z = -s.Wm[(i - n) * n + j] * h;
+        else if (i >= n && i < n2 && j >= n && j < n2) z = in.F[(j - n) * n + (i - n)] * h;
+        else if (i < n2 && j >= n2 && j - n2 == i) z = h;
+        s.Z[e] = z;
+    }
+    __syncthreads();
+    bexpm(s, d);
+    auto E = [&](int i, int j) { return s.E[i * d + j]; };
+    for (int e = tid; e < nn; e += nth) s.X[e] = E(n + e / n, n + e % n);      // Psi22
+    __syncthreads();
+    if ((tid >> 5) == 0 && !winv(s.X, s.Y, n, s.inw[0]) && (tid & 31) == 0) atomicOr(&s.flag, SETUP_SINGULAR_A);
+    __syncthreads();
+    double* Pi = s.Y;                                                          // Psi22^-1
+    for (int e = tid; e < nn; e += nth) {
+        const int i = e / n, j = e % n;
+        double c = 0.0, jj = 0.0;
+        for (int l = 0; l < n; ++l) {
+            c = fma(E(i, n + l), Pi[l * n + j], c);          // Psi12 Psi22^-1
+            jj = fma(Pi[i * n + l], E(n + l, j), jj);        // Psi22^-1 Psi21
+        }
+        out->C[e] = -c;
+        out->J[e] = -jj;
+    }
+    __syncthreads();
+    double* LC1 = out->Cinv;
+    double* LC2 = out->Qinv;
+    double* PL = out->Phi;
+    for (int e = tid; e < nn; e += nth) {
+        const int i = e / n, j = e % n;
+        double a = E(i, j), l1 = E(i, n2 + j), l2 = E(i, n2 + n + j), pl = 0.0;
+        for (int l = 0; l < n; ++l) {
+            a = fma(out->C[i * n + l], E(n + l, j), a);              // Psi11 + C Psi21
+            l1 = fma(out->C[i * n + l], E(n + l, n2 + j), l1);       // L11 + C L21
+            l2 = fma(out->C[i * n + l], E(n + l, n2 + n + j), l2);   // L12 + C L22
+            pl = fma(Pi[i * n + l], E(n + l, n2 + n + j), pl);       // Psi22^-1 L22
+        }
+        out->A[e] = a;
+        LC1[e] = l1;
+        LC2[e] = l2;
+        PL[e] = pl;
+    }
+    __syncthreads();
+    bmm(LC2, s.HR, out->Bb, n, n, m);
+    bmm(PL, s.HR, out->G, n, n, m);
+    for (int i = tid; i < n; i += nth) {
+        double lc = 0.0, l21c = 0.0;
+        for (int l = 0; l < n; ++l) {
+            lc = fma(LC1[i * n + l], in.c[l], lc);
+            l21c = fma(E(n + i, n2 + l), in.c[l], l21c);     // L21 c
+        }
+        s.X[i] = l21c;
+        double br = 0.0;
+        for (int l = 0; l < m; ++l) br = fma(out->Bb[i * m + l], in.r[l], br);
+        out->b[i] = -lc - br;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nth) {
+        double g = 0.0;
+        for (int l = 0; l < n; ++l) g = fma(Pi[i * n + l], s.X[l], g);
+        for (int l = 0; l < m; ++l) g = fma(out->G[i * m + l], in.r[l], g);
+        out->Gr[i] = g;
+    }
+    __syncthreads();
+    for (int e = tid; e < nn; e += nth) {
+        const int i = e / n, j = e % n;
+        s.X[e] = 0.5 * (out->C[i * n + j] + out->C[j * n + i]);
+        s.T1[e] = 0.5 * (out->J[i * n + j] + out->J[j * n + i]);
+    }
+    __syncthreads();
+    for (int e = tid; e < nn; e += nth) {
+        out->C[e] = s.X[e];
+        out->J[e] = s.T1[e];
+    }
+    __syncthreads();
+}
+
 __global__ void k_setup(SetupIn in, SetupOut* out)
 {
     __shared__ SetupShared s;
@@ -239,6 +471,7 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
         out->Q[e] = acc;
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) out->Bb[e] = 0.0;
     if (in.mode == 0) {
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const int i = e / n, j = e % n;
@@ -247,6 +480,24 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
         }
         for (int i = threadIdx.x; i < n; i += blockDim.x) out->b[i] = -dt * in.c[i];
         __syncthreads();
+    } else if (in.mode >= 3) {
+        // R^-1, H^T R^-1 and H^T R^-1 H first: the measurement rows of Eq. 37
+        // enter the element itself
+        if ((threadIdx.x >> 5) == 0 && !winv(in.R, out->Rinv, m, s.inw[0]) && (threadIdx.x & 31) == 0)
+            atomicOr(&s.flag, SETUP_SINGULAR_R);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+            const int i = e / m, j = e % m;
+            double acc = 0.0;
+            for (int l = 0; l < m; ++l) acc = fma(in.H[l * n + i], out->Rinv[l * m + j], acc);
+            s.HR[e] = acc;
+        }
+        __syncthreads();
+        bmm(s.HR, in.H, s.Wm, n, m, n);
+        if (in.mode == 3)
+            setup_block(in, s, out);
+        else
+            setup_exact(in, s, out);
     } else {
         const int d = 2 * n + 1;
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
@@ -293,13 +544,16 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
         if (bad && (threadIdx.x & 31) == 0) atomicOr(&s.flag, bad);
     }
     __syncthreads();
-    // measurement: G = dt H^T R^-1, J = G H (symmetrised), Gr = G r
-    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
-        double acc = 0.0;
-        for (int l = 0; l < m; ++l) acc = fma(in.H[l * n + i], out->Rinv[l * m + j], acc);
-        out->G[e] = dt * acc;
-    }
+    // measurement: G = dt H^T R^-1, J = G H (symmetrised), Gr = G r (modes 3
+    // and 4 have set them with the element)
+    if (in.mode < 3)
+        for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+            const int i = e / m, j = e % m;
+            double acc = 0.0;
+            for (int l = 0; l < m; ++l) acc = fma(in.H[l * n + i], out->Rinv[l * m + j], acc);
+            out->G[e] = dt * acc;
+        }
+    __syncthreads();
     // prior: v0 = S0 m0
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double acc = 0.0;
@@ -322,16 +576,18 @@ __global__ void k_setup(SetupIn in, SetupOut* out)
         for (int l = 0; l < n; ++l) acc = fma(s.T1[i * n + l], out->Phi[j * n + l], acc);
         out->Sigma[e] = acc;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double acc = 0.0;
-        for (int l = 0; l < m; ++l) acc = fma(out->G[i * m + l], in.r[l], acc);
-        out->Gr[i] = acc;
-    }
+    if (in.mode < 3)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double acc = 0.0;
+            for (int l = 0; l < m; ++l) acc = fma(out->G[i * m + l], in.r[l], acc);
+            out->Gr[i] = acc;
+        }
     __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        out->J[e] = 0.5 * (s.Y[i * n + j] + s.Y[j * n + i]);
-    }
+    if (in.mode < 3)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            out->J[e] = 0.5 * (s.Y[i * n + j] + s.Y[j * n + i]);
+        }
     if (threadIdx.x == 0) out->flags = s.flag;
 }
 

@@ -11,6 +11,7 @@
 struct map_smoother {
     // problem
     int model = 0, N = 0, M = 0, NW = 0, prec = 0, disc = 0, smoother = 0, gn_iters = 1;
+    int substeps = 1;                  // Euler substeps per interval (MAP_BLOCK_EULER)
     long T = 0;
     double dt = 0, gamma = 0, cond_max = 1e6;
     int device = 0;
@@ -90,6 +91,8 @@ struct Ops {
     int (*resident_blocks)(int B);     // CTAs of the filter kernels per SM at B threads
     size_t (*tab_bytes)(const map_smoother& h) = nullptr;   // per-step table buffer (0: none)
     size_t (*scan_bytes)(const map_smoother& h) = nullptr;  // tiled-scan table buffer (0: none)
+    map_status (*dense)(map_smoother& h, const void* y, const void* x, const void* filt, void* out,
+                        cudaStream_t st) = nullptr;         // states between the grid points
 };
 
 // geometry (steps per thread K, threads per tile B) and its workspace bytes

@@ -3,8 +3,9 @@
 // parallel in halves of similar size:
 //   INST_PART 0: the operation table, the RTS solve, the cost, the sequential
 //                baseline and the occupancy query;
-//   INST_PART 1: the two-filter solve, the gradient and the batched solve
-//                (state dimensions up to 6), which part 0 declares extern.
+//   INST_PART 1: the two-filter solve, the gradient, the batched solve and
+//                the block/exact-element solve with its dense output (state
+//                dimensions up to 6), which part 0 declares extern.
 #include "solve_impl.cuh"
 namespace mapk {
 #if INST_PART == 0
@@ -15,6 +16,10 @@ extern template map_status grad_linear<INST_N, INST_M, INST_S>(map_smoother&, co
                                                                const void*, int, double*, cudaStream_t);
 extern template map_status solve_linear_seg<INST_N, INST_M, INST_S>(map_smoother&, const void*,
                                                                     const unsigned char*, void*, cudaStream_t);
+extern template map_status solve_linear_block<INST_N, INST_M, INST_S>(map_smoother&, const void*, void*, void*,
+                                                                      cudaStream_t, bool);
+extern template map_status dense_linear<INST_N, INST_M, INST_S>(map_smoother&, const void*, const void*,
+                                                                const void*, void*, cudaStream_t);
 #endif
 template const Ops* linear_ops<INST_N, INST_M, INST_S>();
 #else
@@ -24,5 +29,9 @@ template map_status grad_linear<INST_N, INST_M, INST_S>(map_smoother&, const voi
                                                         double*, cudaStream_t);
 template map_status solve_linear_seg<INST_N, INST_M, INST_S>(map_smoother&, const void*, const unsigned char*,
                                                              void*, cudaStream_t);
+template map_status solve_linear_block<INST_N, INST_M, INST_S>(map_smoother&, const void*, void*, void*, cudaStream_t,
+                                                               bool);
+template map_status dense_linear<INST_N, INST_M, INST_S>(map_smoother&, const void*, const void*, const void*, void*,
+                                                         cudaStream_t);
 #endif
 }  // namespace mapk

@@ -109,6 +109,70 @@ struct LtiProducer {
 };
 
 // ---------------------------------------------------------------------------
+// Block and exact elements of a linear time-invariant model (Section 5.1
+// blocks of Euler substeps, or Eq. 37 solved exactly): the interval's sample
+// is held across the interval, so both offsets depend on it,
+//   b_k = Bb y_{k+1} + b0,   eta_k = G y_{k+1} - Gr,
+// while A, C, J are the same for every interval.  Elements are combined on
+// the general path (no linear fold).
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+struct BlockParams {
+    static constexpr int NS = Sym<N>::SZ;
+    S A[N * N];
+    S C[NS];
+    S J[NS];
+    S Bb[N * M];
+    S b0[N];
+    S G[N * M];
+    S Gr[N];
+};
+
+template <int N, int M, typename S>
+struct BlockProducer {
+    static constexpr int W = M;
+    static constexpr bool RESETS = false;
+    static constexpr bool LINEAR_FOLD = false;
+    static constexpr bool LOWRANK = false;
+    __device__ __forceinline__ bool is_reset(long) const { return false; }
+    const S* y;                      // (T, M), row k holds y_{k+1}
+    long T;
+    BlockParams<N, M, S> p;
+
+    __device__ __forceinline__ void load1(long k, S* row) const
+    {
+#pragma unroll
+        for (int j = 0; j < W; ++j) row[j] = k < T ? __ldg(y + k * W + j) : S(0);
+    }
+
+    __device__ __forceinline__ void terminal(Red<N, S>& r) const
+    {
+#pragma unroll
+        for (int i = 0; i < Red<N, S>::NCOMP; ++i) comp(r, i) = S(0);
+    }
+
+    __device__ __forceinline__ void make(long k, const S* row, Elem<N, S>& e) const
+    {
+        if (k >= T) { set_identity(e); return; }
+#pragma unroll
+        for (int i = 0; i < N * N; ++i) e.A[i] = p.A[i];
+#pragma unroll
+        for (int i = 0; i < Sym<N>::SZ; ++i) { e.C[i] = p.C[i]; e.J[i] = p.J[i]; }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            S sb = p.b0[i], se = -p.Gr[i];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                sb = fma(p.Bb[i * M + j], row[j], sb);
+                se = fma(p.G[i * M + j], row[j], se);
+            }
+            e.b[i] = sb;
+            e.eta[i] = se;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Many independent trajectories of one linear model in one scan.  Trajectory
 // j > 0 is preceded by the model's prior element a_T = (0, 0, 0, P0^-1 m0,
 // P0^-1) (Eq. 31): on the left of the combine (Eq. 36) an element with

@@ -16,6 +16,7 @@ enum SetupFlags { SETUP_SINGULAR_R = 1, SETUP_SINGULAR_P0 = 2, SETUP_SINGULAR_A 
 // device pointers to FP64 row-major inputs
 struct SetupIn {
     int nx, ny, nw, mode;
+    int substeps;                      // block elements (mode 3)
     double dt;
     const double *F, *c, *L, *W, *H, *r, *R, *m0, *P0;
 };
@@ -31,6 +32,11 @@ struct SetupOut {
     double Gpinv[MAXN * MAXN];         // (Gam^T Gam)^-1 Gam^T, rank x n (leading dimension n)
     int rank;                          // numerical rank of C (pivoted Cholesky, relative 1e-13)
     int flags;
+    // block and exact elements (modes 3, 4): b = Bb y + b and eta = G y - Gr are
+    // affine in the interval's sample y; Bb = 0 for the other modes
+    double Bb[MAXN * MAXM];
+    // one substep element of mode 3 (dense output): A, b, C, J, and eta = sG (y - r)
+    double sA[MAXN * MAXN], sb[MAXN], sC[MAXN * MAXN], sJ[MAXN * MAXN], sG[MAXN * MAXM], sGr[MAXN];
 };
 
 cudaError_t launch_setup(const SetupIn& in, SetupOut* d_out, cudaStream_t st);

@@ -653,9 +653,149 @@ map_status solve_linear_tf(map_smoother& h, const void* y, void* x_out, void* fi
     return run_tf<N, S>(h, prod, rprod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, fold);
 }
 
+// ---------------------------------------------------------------------------
+// block and exact elements (MAP_BLOCK_EULER, MAP_RICCATI_EXACT): both offsets
+// of the element depend on the interval's sample (BlockProducer), so they take
+// the general combine path; dense output between the grid points
+// ---------------------------------------------------------------------------
+template <int N, int M, typename S>
+BlockParams<N, M, S> block_params(const map_smoother& h)
+{
+    const SetupOut& c = h.consts;
+    BlockParams<N, M, S> p;
+    for (int i = 0; i < N * N; ++i) p.A[i] = S(c.A[i]);
+    for (int i = 0; i < N; ++i) { p.b0[i] = S(c.b[i]); p.Gr[i] = S(c.Gr[i]); }
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) {
+            p.C[Sym<N>::at(i, j)] = S(c.C[i * N + j]);
+            p.J[Sym<N>::at(i, j)] = S(c.J[i * N + j]);
+        }
+    for (int i = 0; i < N * M; ++i) { p.Bb[i] = S(c.Bb[i]); p.G[i] = S(c.G[i]); }
+    return p;
+}
+
+template <int N, int M, typename S>
+map_status solve_linear_block(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st,
+                              bool sequential)
+{
+    BlockProducer<N, M, S> prod;
+    prod.y = static_cast<const S*>(y);
+    prod.T = h.T;
+    prod.p = block_params<N, M, S>(h);
+    if (sequential) return run_sequential<N, S>(h, prod, static_cast<S*>(x_out), st);
+    return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
+}
+
+// one substep element of a block (dense output)
+template <int N, int M, typename S>
+struct SubParams {
+    S A[N * N];
+    S b[N];
+    S C[Sym<N>::SZ];
+    S J[Sym<N>::SZ];
+    S G[N * M];
+    S Gr[N];
+};
+
+// Dense output (Section 4.3 recovery between grid points), one thread per
+// interval k: the filter value function at x_k (filt row k) is carried across
+// the interval's substeps by the one-variable combine (Eq. 36, `apply`), whose
+// closed-loop maps (Eq. 40-41) are kept in shared memory (ns of them per
+// thread); then x_{k+1} is taken back through them.  Row k ns + j of out is
+// the state at t_k + j dt / ns; row T ns is x_T.
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(64)
+k_dense_block(const S* __restrict__ y, const S* __restrict__ x, const S* __restrict__ filt, long T, int ns,
+              const SubParams<N, M, S> p, S* __restrict__ out, CombineCtx ctx)
+{
+    constexpr int NN = N * N, NA = NN + N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* my = reinterpret_cast<S*>(smem_raw) + (long)threadIdx.x * ns * NA;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= T) return;
+    Red<N, S> X;
+#pragma unroll
+    for (int q = 0; q < Red<N, S>::NCOMP; ++q) comp(X, q) = filt[k * Red<N, S>::NCOMP + q];
+    Elem<N, S> e;
+#pragma unroll
+    for (int q = 0; q < NN; ++q) e.A[q] = p.A[q];
+#pragma unroll
+    for (int q = 0; q < Sym<N>::SZ; ++q) { e.C[q] = p.C[q]; e.J[q] = p.J[q]; }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        S se = -p.Gr[i];
+#pragma unroll
+        for (int j = 0; j < M; ++j) se = fma(p.G[i * M + j], y[k * M + j], se);
+        e.b[i] = p.b[i];
+        e.eta[i] = se;
+    }
+#pragma unroll 1
+    for (int j = 0; j < ns; ++j) {
+        S E[NN], g[N];
+        apply<N, S, true>(e, X, E, g, ctx);
+#pragma unroll
+        for (int q = 0; q < NN; ++q) my[j * NA + q] = E[q];
+#pragma unroll
+        for (int q = 0; q < N; ++q) my[j * NA + NN + q] = g[q];
+    }
+    S z[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) z[a] = x[(k + 1) * N + a];
+#pragma unroll 1
+    for (int j = ns - 1; j >= 0; --j) {
+        S nz[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            S acc = my[j * NA + NN + a];
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(my[j * NA + a * N + q], z[q], acc);
+            nz[a] = acc;
+        }
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            z[a] = nz[a];
+            out[(k * ns + j) * N + a] = nz[a];
+        }
+    }
+    if (k == T - 1)
+#pragma unroll
+        for (int a = 0; a < N; ++a) out[T * ns * N + a] = x[T * N + a];
+}
+
+template <int N, int M, typename S>
+map_status dense_linear(map_smoother& h, const void* y, const void* x, const void* filt, void* out, cudaStream_t st)
+{
+    if (h.disc != MAP_BLOCK_EULER) return fail(h, MAP_ERR_UNSUPPORTED, "dense output needs MAP_BLOCK_EULER elements");
+    const SetupOut& c = h.consts;
+    SubParams<N, M, S> p;
+    for (int i = 0; i < N * N; ++i) p.A[i] = S(c.sA[i]);
+    for (int i = 0; i < N; ++i) { p.b[i] = S(c.sb[i]); p.Gr[i] = S(c.sGr[i]); }
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) {
+            p.C[Sym<N>::at(i, j)] = S(c.sC[i * N + j]);
+            p.J[Sym<N>::at(i, j)] = S(c.sJ[i * N + j]);
+        }
+    for (int i = 0; i < N * M; ++i) p.G[i] = S(c.sG[i]);
+    const int ns = h.substeps;
+    const size_t per = sizeof(S) * (size_t)ns * (N * N + N);
+    int threads = (int)std::min<size_t>(64, (200 * 1024) / per);
+    if (threads < 1) return fail(h, MAP_ERR_SHAPE, "too many substeps for the dense output");
+    const size_t sh = per * threads;
+    cudaError_t e = allow_smem(k_dense_block<N, M, S>, sh);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+    const CombineCtx ctx{(float)h.cond_max, h.d_stats};
+    k_dense_block<N, M, S><<<(unsigned)((h.T + threads - 1) / threads), threads, sh, st>>>(
+        static_cast<const S*>(y), static_cast<const S*>(x), static_cast<const S*>(filt), h.T, ns, p,
+        static_cast<S*>(out), ctx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "dense output kernel launch");
+    return MAP_OK;
+}
+
 template <int N, int M, typename S>
 map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_out, cudaStream_t st)
 {
+    if constexpr (N <= 6)
+        if (h.disc >= MAP_BLOCK_EULER) return solve_linear_block<N, M, S>(h, y, x_out, filt_out, st, false);
     const S* fold = nullptr;
     if (map_status s = lti_fold_consts<N, M, S>(h, st, &fold); s != MAP_OK) return s;
     if constexpr (N <= 6) if (h.smoother == MAP_TWO_FILTER) return solve_linear_tf<N, M, S>(h, y, x_out, filt_out, st, fold);
@@ -669,6 +809,8 @@ map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_
 template <int N, int M, typename S>
 map_status solve_linear_sequential(map_smoother& h, const void* y, void* x_out, cudaStream_t st)
 {
+    if constexpr (N <= 6)
+        if (h.disc >= MAP_BLOCK_EULER) return solve_linear_block<N, M, S>(h, y, x_out, nullptr, st, true);
     LtiProducer<N, M, S> prod;
     prod.y = static_cast<const S*>(y);
     prod.T = h.T;
@@ -988,7 +1130,7 @@ const Ops* linear_ops()
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
                              &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
                              &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>,
-                             &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>};
+                             &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>, &dense_linear<N, M, S>};
         return &ops;
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,

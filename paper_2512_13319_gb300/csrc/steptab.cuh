@@ -651,18 +651,26 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             (unsigned)((sizeof(S) * (trans ? (size_t)B * g.Kt * CT : (size_t)(B + 1) * NN) + 15) / 16 * 16);
         const long yoff = s0 * M;
         const long ycnt = (long)B * Kj * M;
-        const bool ybulk = !last;                         // full tiles: one bulk copy of their rows
+        // the tile's rows by one bulk copy: all of them for full tiles, the
+        // whole 16-byte words before T for the last tile (the rest below)
+        const long yhave = min(ycnt, T * M - yoff);
+        const long ybulk = yhave * (long)sizeof(S) / 16 * 16 / (long)sizeof(S);
         if (t == 0) mbar_init(bar, 1);
         __syncthreads();
         if (t == 0) {
-            mbar_arrive_expect_tx(bar, tbytes + (ybulk ? (unsigned)(sizeof(S) * ycnt) : 0u));
-            if (ybulk) bulk_copy_g2s(ys, prod.y + yoff, (unsigned)(sizeof(S) * ycnt), bar);
+            mbar_arrive_expect_tx(bar, tbytes + (unsigned)(sizeof(S) * ybulk));
+            if (ybulk > 0) bulk_copy_g2s(ys, prod.y + yoff, (unsigned)(sizeof(S) * ybulk), bar);
             bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * g.Kt * CT : sa.pw, tbytes, bar);
+            // the tile-product rows that the tile prefix and suffix sums read
+            // after the grid barriers (data-independent): into L2 now
+            using TT1 = TileTables<N, 1, S>;
+            if (tile > 0)
+                bulk_prefetch_l2(sa.qt + TT1::qt_index(tile, 0) * NN, (unsigned)(sizeof(S) * (size_t)(tile + 1) * NN));
+            if (tile + 1 < g.nt)
+                bulk_prefetch_l2(sa.pi + TT1::pi_index(g.nt, tile + 1, tile + 1) * NN,
+                                 (unsigned)(sizeof(S) * (size_t)(g.nt - tile - 1) * NN));
         }
-        if (!ybulk) {
-            const long have = T * M - yoff;
-            for (long q = t; q < ycnt; q += B) ys[q] = q < have ? prod.y[yoff + q] : S(0);
-        }
+        for (long q = ybulk + t; q < ycnt; q += B) ys[q] = q < yhave ? prod.y[yoff + q] : S(0);
         // constants of the steps after kc (row kc; only read by threads with steps)
         S Einf[NN], oinf[N];
         if (!trans && nv > 0) {

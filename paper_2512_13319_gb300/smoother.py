@@ -9,7 +9,8 @@ import torch
 from . import _binding as B
 
 _PREC = {"fp32": B.MAP_FP32, "fp64": B.MAP_FP64}
-_DISC = {"euler": B.MAP_EULER, "expm": B.MAP_EXPM, "auto": B.MAP_AUTO}
+_DISC = {"euler": B.MAP_EULER, "expm": B.MAP_EXPM, "auto": B.MAP_AUTO, "block": B.MAP_BLOCK_EULER,
+         "exact": B.MAP_RICCATI_EXACT}
 _SMOOTHER = {"rts": B.MAP_RTS, "two_filter": B.MAP_TWO_FILTER}
 
 
@@ -21,12 +22,13 @@ class MapSmoother:
     """
 
     def __init__(self, model, T, dt, precision="fp32", discretisation="euler", smoother="rts",
-                 gn_iters=1, cond_max=0.0, tile_threads=0):
+                 gn_iters=1, cond_max=0.0, tile_threads=0, substeps=0):
         self.model, self.T, self.dt, self.smoother = model, int(T), float(dt), smoother
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.nx, self.ny = model.nx, model.ny
         desc, keep = B.make_desc(model, T, dt, _PREC[precision], _DISC[discretisation],
-                                 _SMOOTHER[smoother], gn_iters, cond_max, tile_threads)
+                                 _SMOOTHER[smoother], gn_iters, cond_max, tile_threads, substeps=substeps)
+        self.substeps = (substeps or 10) if discretisation == "block" else 1
         self._h = B.map_smoother_create(desc)
         del keep
 
@@ -59,6 +61,19 @@ class MapSmoother:
         if filt or cost:
             return x_out, f, c
         return x_out
+
+    def dense(self, y, x, filt, out=None, stream=None):
+        """States at every substep ((T substeps + 1, nx)) of a block-element solve
+        from its observations, trajectory and filter output."""
+        self._check_dev(y, (self.T, self.ny), "y")
+        self._check_dev(x, (self.T + 1, self.nx), "x")
+        self._check_dev(filt, (self.T + 1, self.nx + self.nx * (self.nx + 1) // 2), "filt")
+        if out is None:
+            out = torch.empty((self.T * self.substeps + 1, self.nx), dtype=self.dtype, device=y.device)
+        self._check_dev(out, (self.T * self.substeps + 1, self.nx), "out")
+        B.map_smoother_dense(self._h, y.data_ptr(), x.data_ptr(), filt.data_ptr(), out.data_ptr(),
+                             self._stream(stream))
+        return out
 
     def solve_sequential(self, y, x_out=None, x_init=None, stream=None):
         """Single-thread sequential baseline on the GPU (same elements, no scan)."""
