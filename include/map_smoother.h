@@ -43,13 +43,27 @@ extern "C" {
 
 typedef struct map_smoother map_smoother;   /* opaque handle */
 
+/*
+ * Device errors.  The kernels never wait without a limit: a bulk copy into
+ * shared memory or a grid barrier that does not complete within its poll limit
+ * (about a second) is abandoned, and a pivot that is not positive even in FP64
+ * is detected.  Either marks the launch's result invalid and raises a flag of
+ * the handle in host-mapped memory.  Because solves are asynchronous, the flag
+ * is reported by the handle's NEXT call that checks it: map_smoother_solve,
+ * _solve_sequential, _dense and _grad check it before they launch; the calls
+ * that synchronise (_solve_host, _grad, _stats, and _solve with cost_out) also
+ * check it after their synchronisation.  That call returns MAP_ERR_TIMEOUT (a
+ * wait ran out) or MAP_ERR_SINGULAR (a singular pivot), sets last_error and
+ * clears the flag; the CUDA context stays usable and later calls run normally.
+ */
+
 typedef enum {
     MAP_OK = 0,
     MAP_ERR_INVALID_ARG = -1,   /* null pointer, bad enum, misaligned pointer */
     MAP_ERR_SHAPE = -2,         /* unsupported nx/ny combination, T < 1 */
     MAP_ERR_CUDA = -3,          /* a CUDA runtime call failed */
     MAP_ERR_SINGULAR = -4,      /* a matrix that must be invertible was not */
-    MAP_ERR_TIMEOUT = -5,       /* reserved: no call of this library waits on the device */
+    MAP_ERR_TIMEOUT = -5,       /* a bounded device wait ran out (see "Device errors" below) */
     MAP_ERR_UNSUPPORTED = -6    /* valid request this build does not implement */
 } map_status;
 
@@ -200,11 +214,24 @@ map_status map_smoother_update(map_smoother* h, const double* F, double log_q, d
 
 /*
  * Device-side counters since create or the last reset: [0] combines
- * recomputed in FP64 (precision policy), [1] singular pivots met, [2] bulk
- * input copies whose bounded wait gave up (their tile was not computed and
- * the solve's result is invalid; expected to stay 0).  Synchronises the stream.
+ * recomputed in FP64 (precision policy), [1] singular pivots met, [2] bounded
+ * device waits (bulk copies, grid barriers) that ran out (the result of their
+ * launch is invalid; expected to stay 0).  Synchronises the stream; out is
+ * written, and the return value is then MAP_ERR_TIMEOUT / MAP_ERR_SINGULAR
+ * when the handle's error flag was raised (see "Device errors").
  */
 map_status map_smoother_stats(map_smoother* h, unsigned long long out[3], int reset, void* stream);
+
+/*
+ * Test of the device-error path without a fault or a hang: one CTA of 32
+ * threads waits on a shared-memory mbarrier that nothing arrives on, with the
+ * poll-limited wait of the solve kernels, then on a grid-barrier counter that
+ * nothing advances (spin limit `polls`); each wait runs out and is reported
+ * exactly as in a solve (counter [2] and the handle's error flag), so the next
+ * checking call returns MAP_ERR_TIMEOUT.  polls must be 1..1048576
+ * (MAP_ERR_INVALID_ARG otherwise).  Asynchronous on `stream`.
+ */
+map_status map_smoother_wait_selftest(map_smoother* h, int polls, void* stream);
 
 /*
  * Per-phase device timing.  With profiling on, every solve records CUDA events

@@ -68,6 +68,7 @@ EXPORTS = {
     "map_batch_last_error": (_CH, [_VP]),
     "map_batch_destroy": (None, [_VP]),
     "map_fma_peak": (_I, [_I, _I, _D, ctypes.POINTER(ctypes.c_float), _VP]),
+    "map_smoother_wait_selftest": (_I, [_VP, _I, _VP]),
 }
 
 _lib = None
@@ -178,6 +179,10 @@ def map_smoother_geometry(h):
     K, Bt, nt = _I(), _I(), _I()
     _check(load().map_smoother_geometry(h, ctypes.byref(K), ctypes.byref(Bt), ctypes.byref(nt)), h)
     return K.value, Bt.value, nt.value
+
+
+def map_smoother_wait_selftest(h, polls, stream=None):
+    _check(load().map_smoother_wait_selftest(h, int(polls), stream), h)
 
 
 FMA_FP32, FMA_FP32X2, FMA_FP64 = 0, 1, 2

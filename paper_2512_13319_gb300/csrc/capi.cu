@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "elements.cuh"
 #include "handle.h"
 
 namespace mapk {
@@ -49,6 +50,26 @@ map_status cuda_fail(map_smoother& h, cudaError_t e, const char* where)
     return MAP_ERR_CUDA;
 }
 
+map_status device_errors(map_smoother& h)
+{
+    if (!h.h_flags) return MAP_OK;
+    volatile unsigned* f = h.h_flags;
+    if (f[EV_TIMEOUT]) {
+        f[EV_TIMEOUT] = 0;
+        f[EV_SINGULAR] = 0;
+        return fail(h, MAP_ERR_TIMEOUT,
+                    "a bounded device wait (bulk copy or grid barrier) ran out in an earlier launch on this "
+                    "handle: the results of that launch are not valid");
+    }
+    if (f[EV_SINGULAR]) {
+        f[EV_SINGULAR] = 0;
+        return fail(h, MAP_ERR_SINGULAR,
+                    "a singular pivot in an earlier launch on this handle (a combine's FP64 inverse or the "
+                    "terminal solve): the results of that launch are not valid");
+    }
+    return MAP_OK;
+}
+
 }  // namespace mapk
 
 using namespace mapk;
@@ -71,6 +92,7 @@ void free_handle(map_smoother* h)
     if (!h) return;
     if (h->ws) cudaFree(h->ws);
     if (h->d_stats) cudaFree(h->d_stats);
+    if (h->h_flags) cudaFreeHost(h->h_flags);
     if (h->d_y) cudaFree(h->d_y);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_xtmp) cudaFree(h->d_xtmp);
@@ -222,11 +244,24 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
 
     h->ws_bytes = ops->workspace_bytes(*h);
     if ((e = cudaMalloc(&h->ws, h->ws_bytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc workspace");
-    // three event counters, then the grid barrier state of the single-launch solve
-    if ((e = cudaMalloc(&h->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess)
+    // event words (counters, the grid barrier state of the single-launch
+    // solves) and the host-mapped error flags whose device address word 4 holds
+    if ((e = cudaMalloc(&h->d_stats, STATS_WORDS * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMalloc");
-    if ((e = cudaMemset(h->d_stats, 0, 4 * sizeof(unsigned long long))) != cudaSuccess)
+    if ((e = cudaMemset(h->d_stats, 0, STATS_WORDS * sizeof(unsigned long long))) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMemset");
+    if ((e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_flags), 4 * sizeof(unsigned), cudaHostAllocMapped)) !=
+        cudaSuccess)
+        return cuda_fail(*h, e, "cudaHostAlloc");
+    std::memset(h->h_flags, 0, 4 * sizeof(unsigned));
+    {
+        void* dflags = nullptr;
+        if ((e = cudaHostGetDevicePointer(&dflags, h->h_flags, 0)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaHostGetDevicePointer");
+        const unsigned long long a = reinterpret_cast<uintptr_t>(dflags);
+        if ((e = cudaMemcpy(h->d_stats + EV_FLAGS, &a, sizeof(a), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMemcpy");
+    }
     if ((e = cudaMalloc(&h->d_cost, sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
     if (h->model != MAP_MODEL_LINEAR) {
         if ((e = cudaMalloc(&h->d_xtmp, (size_t)(h->T + 1) * n * es)) != cudaSuccess)
@@ -345,6 +380,7 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
     if (!y || !x_out) return fail(*h, MAP_ERR_INVALID_ARG, "y and x_out are required");
     if (!aligned16(y) || !aligned16(x_out) || (filt_out && !aligned16(filt_out)))
         return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+    if (map_status s = device_errors(*h); s != MAP_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
     h->launches = 0;
@@ -362,6 +398,7 @@ map_status map_smoother_solve(map_smoother* h, const void* y, void* x_out, void*
         cudaError_t e = cudaMemcpyAsync(cost_out, h->d_cost, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(*h, e, "cost read-back");
+        return device_errors(*h);
     }
     return MAP_OK;
 }
@@ -372,6 +409,7 @@ map_status map_smoother_solve_sequential(map_smoother* h, const void* y, void* x
     if (!y || !x_out) return fail(*h, MAP_ERR_INVALID_ARG, "y and x_out are required");
     if (!aligned16(y) || !aligned16(x_out))
         return fail(*h, MAP_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+    if (map_status s = device_errors(*h); s != MAP_OK) return s;
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
     return ops->solve_sequential(*h, y, x_out, static_cast<cudaStream_t>(stream));
 }
@@ -384,6 +422,7 @@ map_status map_smoother_dense(map_smoother* h, const void* y, const void* x, con
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
     if (!ops->dense || h->disc != MAP_BLOCK_EULER)
         return fail(*h, MAP_ERR_UNSUPPORTED, "dense output needs a linear model with MAP_BLOCK_EULER elements");
+    if (map_status s = device_errors(*h); s != MAP_OK) return s;
     return ops->dense(*h, y, x, filt, dense_out, static_cast<cudaStream_t>(stream));
 }
 
@@ -409,7 +448,7 @@ map_status map_smoother_solve_host(map_smoother* h, const void* y_host, void* x_
     if ((e = cudaMemcpyAsync(x_host, h->d_x, xbytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(*h, e, "cudaMemcpyAsync D2H");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(*h, e, "cudaStreamSynchronize");
-    return MAP_OK;
+    return device_errors(*h);
 }
 
 map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, const void* dL_dx, int flags,
@@ -425,7 +464,10 @@ map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, cons
         return fail(*h, MAP_ERR_UNSUPPORTED, "gradients need an invertible process noise Q");
     const Ops* ops = find_ops(h->model, h->N, h->M, h->prec);
     if (!ops->grad) return fail(*h, MAP_ERR_UNSUPPORTED, "no gradient kernels for this state dimension");
-    return ops->grad(*h, y, x, dL_dx, flags, dL_dtheta, static_cast<cudaStream_t>(stream));
+    if (map_status s = device_errors(*h); s != MAP_OK) return s;
+    if (map_status s = ops->grad(*h, y, x, dL_dx, flags, dL_dtheta, static_cast<cudaStream_t>(stream)); s != MAP_OK)
+        return s;
+    return device_errors(*h);               // the gradient read-back synchronised the stream
 }
 
 map_status map_smoother_update(map_smoother* h, const double* F, double log_q, double log_r)
@@ -452,7 +494,7 @@ map_status map_smoother_stats(map_smoother* h, unsigned long long out[3], int re
     if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->d_stats, 0, 3 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(*h, e, "stats");
-    return MAP_OK;
+    return device_errors(*h);
 }
 
 map_status map_smoother_geometry(const map_smoother* h, int* K, int* B, int* tiles)

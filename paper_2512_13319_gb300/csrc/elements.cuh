@@ -57,9 +57,32 @@ struct Aff {
     S c[N];
 };
 
+// A handle's device event words (unsigned long long): [0] combines whose
+// inverse was recomputed in FP64, [1] singular pivots, [2] bounded waits that
+// ran out, [3] grid-barrier arrivals of the single-launch solves, [4] device
+// address of the handle's host-mapped error flags (0: none), [5] the counter
+// of the wait self-test.
+constexpr int STATS_WORDS = 8;
+enum : int { EV_FP64 = 0, EV_SINGULAR = 1, EV_TIMEOUT = 2, EV_BARRIER = 3, EV_FLAGS = 4, EV_SELFTEST = 5 };
+
+// Count event ev (EV_SINGULAR, EV_TIMEOUT) and raise the matching host-visible
+// flag: the result of the launch is not valid, and the handle's next call
+// returns the error (the flags live in mapped host memory, so the host reads
+// them without a device synchronisation).
+__device__ __forceinline__ void report_event(unsigned long long* stats, int ev)
+{
+    if (!stats) return;
+    atomicAdd(stats + ev, 1ull);
+    const unsigned long long a = *reinterpret_cast<volatile unsigned long long*>(stats + EV_FLAGS);
+    if (a) {
+        *(reinterpret_cast<volatile unsigned*>(a) + ev) = 1u;
+        __threadfence_system();
+    }
+}
+
 struct CombineCtx {
     float cond_max;                  // FP64 inverse when |M| |M^-1| exceeds this
-    unsigned long long* stats;       // [0] FP64 inverses, [1] singular pivots
+    unsigned long long* stats;       // the event words above
 };
 
 template <int N, typename S>
@@ -146,7 +169,7 @@ __device__ __noinline__ void inverse_I_plus_fp64(const S* buf, S* out, unsigned 
     for (int i = 0; i < N * N; ++i) out[i] = S(Mi[i]);
     if (stats) {
         atomicAdd(stats, 1ull);
-        if (!ok) atomicAdd(stats + 1, 1ull);
+        if (!ok) report_event(stats, EV_SINGULAR);
     }
 }
 

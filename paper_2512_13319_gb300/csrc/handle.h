@@ -25,7 +25,8 @@ struct map_smoother {
     // device memory owned by the handle
     char* ws = nullptr;
     size_t ws_bytes = 0;
-    unsigned long long* d_stats = nullptr;
+    unsigned long long* d_stats = nullptr;  // event words (STATS_WORDS of them, elements.cuh)
+    unsigned* h_flags = nullptr;       // host-mapped error flags raised by report_event (elements.cuh)
     void* d_y = nullptr;               // staging for the host-buffer entry point
     void* d_x = nullptr;
     void* d_xtmp = nullptr;            // Gauss-Newton ping-pong trajectory
@@ -106,6 +107,9 @@ map_status create_handle(map_smoother** out, const map_problem_desc* desc);
 const Ops* find_ops(int model, int N, int M, int prec);
 
 map_status fail(map_smoother& h, map_status s, const std::string& msg);
+// MAP_ERR_TIMEOUT / MAP_ERR_SINGULAR (and clears the flag) when an earlier
+// launch on the handle raised its host-mapped error flag; MAP_OK otherwise
+map_status device_errors(map_smoother& h);
 // message returned by map_smoother_last_error(NULL) on this thread
 void set_handle_free_error(const std::string& msg);
 map_status cuda_fail(map_smoother& h, cudaError_t e, const char* where);

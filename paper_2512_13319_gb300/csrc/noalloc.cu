@@ -31,6 +31,7 @@
 #include <string>
 #include <vector>
 
+#include "elements.cuh"
 #include "handle.h"
 
 namespace {
@@ -39,7 +40,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;
 constexpr int SETUP_IN_DOUBLES = 8 * 8 * 4 + 8 * 5 + 8 * 8 * 2;   // F, L, W, H, R, P0 + vectors
 
 __device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
-__device__ __align__(256) unsigned long long g_stats[4];   // 3 counters + grid barrier state
+__device__ __align__(256) unsigned long long g_stats[mapk::STATS_WORDS];   // event words (no error flags)
 __device__ __align__(256) double g_setup_in[SETUP_IN_DOUBLES];
 __device__ __align__(256) mapk::SetupOut g_setup_out;
 
@@ -199,7 +200,7 @@ extern "C" map_status map_smoother_solve_noalloc(const map_problem_desc* d, cons
     h.fold_K = 0;
     h.d_stats = arr.stats;
     // the counters and the grid-barrier arrival count (the stack handle starts at 0)
-    if ((e = cudaMemsetAsync(arr.stats, 0, 4 * sizeof(unsigned long long), st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(arr.stats, 0, mapk::STATS_WORDS * sizeof(unsigned long long), st)) != cudaSuccess)
         return noalloc_fail(MAP_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const map_status s = ops->solve(h, y, x_out, nullptr, st);
     h.ws = nullptr;        // the stack handle owns nothing

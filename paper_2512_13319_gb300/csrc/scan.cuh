@@ -21,6 +21,8 @@
 // x_k = E_k x_{k+1} + g_k from the last step backwards (an original-time
 // suffix), starting from x_T = S_T^-1 v_T (Eq. 18 initial condition).
 #pragma once
+#include <cstdint>
+
 #include "producers.cuh"
 #include "coop.cuh"
 #include "lti_fold.cuh"
@@ -744,7 +746,7 @@ __device__ __forceinline__ void write_final_if_last(long T, int tile, int K, con
     Red<N, S> P = X;
     aos_store(final_out, 0, P);
     S x[N];
-    if (!red_argmin<N, S>(P, x) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+    if (!red_argmin<N, S>(P, x)) report_event(ctx.stats, EV_SINGULAR);
 #pragma unroll
     for (int i = 0; i < N; ++i) xT_out[i] = x[i];
     if (filtT_out) {
@@ -814,7 +816,7 @@ k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ th
     for (int q = t; q < (LB + 1) * FL::LS; q += B) lv[q] = fold[FL::oL + q];
     bool ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
     if (!__syncthreads_and(ok)) {
-        if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
+        if (t == 0) report_event(ctx.stats, EV_TIMEOUT);
         mbar_wait_bounded(bar, 0, MBAR_POLLS);      // the copy may still be in flight
         return;
     }
@@ -953,7 +955,7 @@ __device__ __forceinline__ void filter_steps(const Prod& prod, int K, long k0, l
                 // trajectory start: the previous trajectory ends at the argmin of X
 #pragma unroll
                 for (int j = 0; j < N * N; ++j) a.F[j] = S(0);
-                if (!red_argmin<N, S>(X, a.c) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+                if (!red_argmin<N, S>(X, a.c)) report_event(ctx.stats, EV_SINGULAR);
                 apply<N, S, false>(e, X, nullptr, nullptr, ctx);
             } else {
                 bool done = false;
@@ -1446,7 +1448,8 @@ constexpr int GRID_SPINS = 1 << 24;         // bounded wait (about a second with
 // All CTAs of the (co-resident) grid reach barrier p; the global writes of
 // each CTA before it are visible to all after it.  A wait that runs out counts
 // in stats[2] and lets the CTA continue.
-__device__ __forceinline__ void grid_sync(const GridSync& gs, int p, unsigned long long* stats)
+__device__ __forceinline__ void grid_sync(const GridSync& gs, int p, unsigned long long* stats,
+                                          int spins = GRID_SPINS)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1455,8 +1458,8 @@ __device__ __forceinline__ void grid_sync(const GridSync& gs, int p, unsigned lo
         atomicAdd(gs.count, 1ull);
         int n = 0;
         while (ld_acquire_u64(gs.count) < target) {
-            if (++n > GRID_SPINS) {
-                if (stats) atomicAdd(stats + 2, 1ull);
+            if (++n > spins) {
+                report_event(stats, EV_TIMEOUT);
                 break;
             }
             __nanosleep(64);
@@ -1562,7 +1565,7 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
         }
         const bool ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
         if (!__syncthreads_and(ok)) {
-            if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
+            if (t == 0) report_event(ctx.stats, EV_TIMEOUT);
             mbar_wait_bounded(bar, 0, MBAR_POLLS);  // the copy may still be in flight
         }
         S leaf[2 * N];
@@ -1613,8 +1616,8 @@ k_lti_solve(const __grid_constant__ Prod prod, int K, const LtiTiles<S> lt, cons
         Red<N, S> pin, X;
         lti_tile_prefix_sum<N, S>(lt, tile, gridDim.x, prior, red, pin);
         if (t == 0) node_store(pin, ps);
-        if (!mbar_wait_bounded(bar_co, 0, MBAR_POLLS) && ctx.stats && t == 0)
-            atomicAdd(ctx.stats + 2, 1ull);        // the co table
+        if (!mbar_wait_bounded(bar_co, 0, MBAR_POLLS) && t == 0)
+            report_event(ctx.stats, EV_TIMEOUT);   // the co table
         lti_tree_down_linear<N, M, S>(bq, co);     // starts and ends with a barrier
         {
             Red<N, S> P;
@@ -1692,7 +1695,7 @@ k_sequential(const __grid_constant__ Prod prod, Red<N, S> prior, S* __restrict__
         aos_store(Eg, k, a);
     }
     S x[N];
-    if (!red_argmin<N, S>(X, x) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+    if (!red_argmin<N, S>(X, x)) report_event(ctx.stats, EV_SINGULAR);
 #pragma unroll
     for (int j = 0; j < N; ++j) x_out[T * N + j] = x[j];
     for (long k = T - 1; k >= 0; --k) {

@@ -741,8 +741,11 @@ k_dense_block(const S* __restrict__ y, const S* __restrict__ x, const S* __restr
     S z[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) z[a] = x[(k + 1) * N + a];
+    // substep 0 is the grid point itself: its row is x_k as the solve gave it
+#pragma unroll
+    for (int a = 0; a < N; ++a) out[k * ns * N + a] = x[k * N + a];
 #pragma unroll 1
-    for (int j = ns - 1; j >= 0; --j) {
+    for (int j = ns - 1; j >= 1; --j) {
         S nz[N];
 #pragma unroll
         for (int a = 0; a < N; ++a) {

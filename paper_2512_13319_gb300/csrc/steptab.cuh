@@ -682,7 +682,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         }
         const bool ok = mbar_wait_bounded(bar, 0, MBAR_POLLS);
         if (!__syncthreads_and(ok)) {
-            if (t == 0 && ctx.stats) atomicAdd(ctx.stats + 2, 1ull);
+            if (t == 0) report_event(ctx.stats, EV_TIMEOUT);
             mbar_wait_bounded(bar, 0, MBAR_POLLS);      // the copy may still be in flight
         }
         const S* yt = ys + t * Kj * M;
@@ -894,7 +894,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             for (int q = 0; q < Sym<N>::SZ; ++q) XT.P[q] = __ldg(rT + ST::oP + q);
             if (final_out) aos_store(final_out, 0, XT);
             S xt[N];
-            if (!red_argmin<N, S>(XT, xt) && ctx.stats) atomicAdd(ctx.stats + 1, 1ull);
+            if (!red_argmin<N, S>(XT, xt)) report_event(ctx.stats, EV_SINGULAR);
 #pragma unroll
             for (int a = 0; a < N; ++a) xT[a] = xt[a];
             if (filtT_out)

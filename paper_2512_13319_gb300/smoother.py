@@ -138,6 +138,11 @@ class MapSmoother:
         wait gave up) since create or the last reset."""
         return B.map_smoother_stats(self._h, reset, self._stream(stream))
 
+    def wait_selftest(self, polls=1000, stream=None):
+        """Run the bounded-wait self-test kernel: the handle's next checking
+        call raises MapError(MAP_ERR_TIMEOUT)."""
+        B.map_smoother_wait_selftest(self._h, polls, self._stream(stream))
+
     def close(self):
         if getattr(self, "_h", None):
             B.map_smoother_destroy(self._h)
