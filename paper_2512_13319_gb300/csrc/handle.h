@@ -38,7 +38,7 @@ struct map_smoother {
     int fold_K = 0, fold_B = 0;        // K and B they were computed for (0: stale)
     // per-step tables of linear time-invariant RTS solves (steptab.cuh)
     char* d_tab = nullptr;
-    int tab_K = 0, tab_B = 0;          // geometry they were computed for (0: stale)
+    int tab_state = 0;                 // 0: stale (model set-up changed), 1: computed
     int tab_ok = 0;                    // the tables reach the stationary filter: the table solve runs
     long tab_kt = 0, tab_kc = 0;
     // tiled-scan geometry of the table solve (steptab.cuh ScanGeom) and its buffer

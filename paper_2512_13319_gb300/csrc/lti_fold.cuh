@@ -370,13 +370,10 @@ __device__ inline void riccati(const double* A, const double* C, const double* J
 // (b, eta) -> (b + Tb_i eta, Te_i eta) of step i.  Then the tree levels of
 // item (2) (also kept in FP64 for k_lti_tables) and the tile levels of item
 // (4).  LB: log2 of the threads per tile (B = 2^LB <= BMAX); ne: the tile
-// levels to write (2^ne above every tile index).  With f64 != nullptr the
-// FP64 (A, C, J) of the i-step folds, i = 1..K, go to f64 + i * 3 N^2 (full
-// matrices), for the per-step tables of steptab.cuh.
+// levels to write (2^ne above every tile index).
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(32)
-k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict__ out,
-           double* __restrict__ f64 = nullptr)
+k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict__ out)
 {
     using FL = FoldLayout<N, M, S>;
     using CL = CoopLayout<N, S>;
@@ -402,15 +399,6 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
         oe[l] = -p.Gr[l];
     }
     __syncwarp();
-    auto keep_fold = [&](int i) {               // the i-step fold in FP64
-        if (!f64) return;
-        for (int q = l; q < NN; q += 32) {
-            f64[(i * 3) * NN + q] = Ac[q];
-            f64[(i * 3 + 1) * NN + q] = Cc[q];
-            f64[(i * 3 + 2) * NN + q] = Jc[q];
-        }
-    };
-    keep_fold(1);
 #pragma unroll 1
     for (int i = 1; i < K; ++i) {
         fw::inv_I_plus<N>(Ce, Jc, Mi, wk);      // (I + C_e J_acc)^-1
@@ -449,7 +437,6 @@ k_lti_fold(const LtiParams<N, M, double> p, int K, int LB, int ne, S* __restrict
         }
         if (l < N) { ob[l] = nb; oe[l] = nq; }
         __syncwarp();
-        keep_fold(i + 1);
     }
     for (int q = l; q < NN; q += 32) {
         const int a = q / N, c = q - a * N;
@@ -554,7 +541,7 @@ union LtiTablesWk {
 // errors from thread to thread and is unstable for models whose interval
 // elements are ill-conditioned.)
 template <int N, int M, typename S>
-__device__ void lti_prefix_warp(int pidx, int LB, S* __restrict__ out, LtiTablesWk<N>& wk, double* pre64)
+__device__ void lti_prefix_warp(int pidx, int LB, S* __restrict__ out, LtiTablesWk<N>& wk)
 {
     using FL = FoldLayout<N, M, S>;
     using TT = TileTables<N, M, S>;
@@ -591,12 +578,6 @@ __device__ void lti_prefix_warp(int pidx, int LB, S* __restrict__ out, LtiTables
             co[(3 * NN + q) * cnt] = S(w.W[q]);
         }
     }
-    if (pre64)
-        for (int q = l; q < NN; q += 32) {
-            pre64[(pidx * 3) * NN + q] = w.A[q];
-            pre64[(pidx * 3 + 1) * NN + q] = w.C[q];
-            pre64[(pidx * 3 + 2) * NN + q] = w.J[q];
-        }
     S* pr = out + FL::oPre + pidx * FL::PS;
     for (int q = l; q < NN; q += 32) {
         const int a = q / N, c = q - a * N;
@@ -612,7 +593,7 @@ __device__ void lti_prefix_warp(int pidx, int LB, S* __restrict__ out, LtiTables
 // the tile levels (written by k_lti_fold) and the prior's P_0.  FP64.
 template <int N, int M, typename S>
 __device__ void lti_tile_warp(int j, const Red<N, double>& prior, int nt, int ne, S* __restrict__ out,
-                              LtiTablesWk<N>& wk, double* p64)
+                              LtiTablesWk<N>& wk)
 {
     using TT = TileTables<N, M, S>;
     namespace fw = fold_warp;
@@ -636,20 +617,16 @@ __device__ void lti_tile_warp(int j, const Red<N, double>& prior, int nt, int ne
         const int a = q / N, c = q - a * N;
         if (c >= a) tp[Sym<N>::at(a, c)] = S(w.P[q]);
         tf[q] = S(w.E[c * N + a]);
-        if (p64) p64[(long)j * NN + q] = w.P[q];
     }
 }
 
 // The tables of items (3) and (4) side by side, one warp per item, four warps
 // per block of 128 threads: blocks 0 .. B/4 - 1 (rounded up) take the thread
 // prefixes p, the rest the tiles j, so that both spread over the SMs' FP64
-// pipes at once.  Runs after k_lti_fold.  With pre64 / p64 != nullptr the
-// FP64 pre_p (A, C, J; full matrices, 3 N^2 each) and P_j (N^2 each) are kept
-// there too, for the per-step tables of steptab.cuh.
+// pipes at once.  Runs after k_lti_fold.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(128)
-k_lti_tables(const Red<N, double> prior, int LB, int nt, int ne, S* __restrict__ out,
-             double* __restrict__ pre64 = nullptr, double* __restrict__ p64 = nullptr)
+k_lti_tables(const Red<N, double> prior, int LB, int nt, int ne, S* __restrict__ out)
 {
     constexpr int WPB = 4;
     __shared__ LtiTablesWk<N> wks[WPB];
@@ -658,10 +635,10 @@ k_lti_tables(const Red<N, double> prior, int LB, int nt, int ne, S* __restrict__
     if (wi >= WPB) return;
     if ((int)blockIdx.x < pre_blocks) {
         const int pidx = blockIdx.x * WPB + wi;
-        if (pidx < B) lti_prefix_warp<N, M, S>(pidx, LB, out, wks[wi], pre64);    // warp-uniform
+        if (pidx < B) lti_prefix_warp<N, M, S>(pidx, LB, out, wks[wi]);    // warp-uniform
     } else {
         const int j = ((int)blockIdx.x - pre_blocks) * WPB + wi;
-        if (j < nt) lti_tile_warp<N, M, S>(j, prior, nt, ne, out, wks[wi], p64);
+        if (j < nt) lti_tile_warp<N, M, S>(j, prior, nt, ne, out, wks[wi]);
     }
 }
 

@@ -232,64 +232,6 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         }
         const bool single = lti && lt.pi && !dev_prior && !h.profile && nt > 1 && nt - 1 <= G &&
                             cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0;
-        // with per-step tables (steptab.cuh) the single launch runs only the
-        // data-dependent part of every step
-        if (lti && h.tab_ok && h.tab_K == K && h.tab_B == B && !dev_prior && !h.profile &&
-            cap == cudaStreamCaptureStatusNone && (reinterpret_cast<uintptr_t>(prod.y) & 15) == 0) {
-            using ST = StepTab<N, S>;
-            using SB = ScanBuf<N, Prod::W, S>;
-            using TT = TileTables<N, Prod::W, S>;
-            constexpr int SB_B = 128;
-            ScanArgs<N, S> sa{};
-            sa.g = ScanGeom{SB_B, h.sc_K, h.sc_Kt, h.sc_Jt, h.sc_nt};
-            const int snt = h.sc_nt;
-            const size_t sh = ScanSmem<N, Prod::W, S>::bytes(SB_B, h.sc_K, h.sc_Kt);
-            sa.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(nt));
-            sa.kc = h.tab_kc;
-            sa.phit = reinterpret_cast<const S*>(h.d_tab + ST::phit_off(nt, h.tab_kt));
-            sa.pw = reinterpret_cast<const S*>(h.d_scan + SB::pw_off());
-            sa.ttab = reinterpret_cast<const S*>(h.d_scan + SB::ttab_off());
-            sa.w = reinterpret_cast<S*>(h.d_scan + SB::w_off());
-            sa.taff = reinterpret_cast<S*>(h.d_scan + SB::taff_off());
-            const char* tiles = h.d_scan + SB::tiles_off();
-            sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));
-            sa.qt = reinterpret_cast<const S*>(tiles + TT::qt_off(snt));
-            sa.pdummy = reinterpret_cast<const S*>(tiles + TT::p_off());
-            sa.has_b = 0;
-            for (int i = 0; i < N; ++i) sa.has_b |= h.consts.b[i] != 0.0;
-            for (int i = 0; i < N; ++i) {
-                double ab = 0.0;
-                for (int k = 0; k < N; ++k) ab += h.consts.Phi[i * N + k] * h.consts.b[k];
-                sa.Aib[i] = S(ab);
-                for (int j = 0; j < N; ++j) {
-                    double ac = 0.0;
-                    for (int k = 0; k < N; ++k) ac += h.consts.Phi[i * N + k] * h.consts.C[k * N + j];
-                    sa.AiC[i * N + j] = S(ac);
-                }
-            }
-            const GridSync gs{h.d_stats + 3, h.bar_arrivals};
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(snt);
-            cfg.blockDim = dim3(SB_B);
-            cfg.dynamicSmemBytes = sh;
-            cfg.stream = st;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeCooperative;
-            at[0].val.cooperative = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            cudaError_t e = cudaLaunchKernelEx(&cfg, k_lti_scan<N, S, Prod>, prod, prior_of<N, S>(h), filt_out, ctx,
-                                               fin, x_out, filtT, gs, sa);
-            if (e == cudaSuccess) {
-                h.launches += 1;
-                h.path = MAP_PATH_TABLES;
-                h.bar_arrivals += 2ull * (unsigned long long)snt;
-                return MAP_OK;
-            }
-            // the grid cannot be resident at once after all: the paths below
-            cudaGetLastError();
-            h.tab_ok = 0;
-        }
         if (single) {
             const size_t sh = FusedSmem<N, Prod::W, S>::bytes(B, K);
             if (h.fused < 0) {
@@ -490,12 +432,13 @@ FlipParams<N, M, S> flip_params(const map_smoother& h)
 // K_t steps up to kc, then tiles of 128 x K steps with the smallest K (8..64)
 // for which every tile's CTA is resident at once and the tile products fit
 // (at most 4 x 128 + 1 tiles).  Sets h.tab_ok when the solve can run.
-template <int N, int M, typename S>
+template <int N, int M, typename S, bool HB>
 map_status scan_plan(map_smoother& h, cudaStream_t st)
 {
     using ST = StepTab<N, S>;
     using SB = ScanBuf<N, M, S>;
     using TT = TileTables<N, M, S>;
+    auto kern = k_lti_scan<N, S, LtiProducer<N, M, S>, HB>;
     h.tab_ok = 0;
     if (!h.d_scan) return MAP_OK;
     constexpr int B = 128, Kt = ST::KT_STEPS;
@@ -514,9 +457,8 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
         if (n < 2 || n > SB::NTMAX) continue;
         const size_t sh = ScanSmem<N, M, S>::bytes(B, k, Kt);
         int nb = 0;
-        if (allow_smem(k_lti_scan<N, S, LtiProducer<N, M, S>>, sh) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lti_scan<N, S, LtiProducer<N, M, S>>, B, sh) !=
-                cudaSuccess) {
+        if (allow_smem(kern, sh) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, B, sh) != cudaSuccess) {
             cudaGetLastError();
             return MAP_OK;
         }
@@ -527,17 +469,21 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     }
     if (!K) return MAP_OK;
     const ScanGeom g{B, K, Kt, Jt, nt};
-    const S* rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off(h.nt));
-    const double* e64 = reinterpret_cast<const double*>(h.d_tab + ST::e64_off(h.nt, KT));
-    const double* phit64 = reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(h.nt, KT));
+    const S* rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off());
+    const double* e64 = reinterpret_cast<const double*>(h.d_tab + ST::e64_off(KT));
+    const double* phit64 = reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(KT));
+    const S* mk = reinterpret_cast<const S*>(h.d_tab + ST::mk_off(KT));
     S* pw = reinterpret_cast<S*>(h.d_scan + SB::pw_off());
     S* ttab = reinterpret_cast<S*>(h.d_scan + SB::ttab_off());
+    S* gsv = reinterpret_cast<S*>(h.d_scan + SB::gs_off());
     char* tiles = h.d_scan + SB::tiles_off();
-    k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + (long)std::min(kc, KT - 1) * N * N, K, B, pw);
-    if (Jt > 0) {
+    const long kr = std::min(kc, KT - 1);
+    k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + kr * N * N, K, B, pw);
+    if (Jt > 0 && ScanSmem<N, M, S>::STAGE) {
         const long cnt = (long)Jt * B * Kt * SB::CT;
         k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(rows, KT, g, ttab);
     }
+    k_scan_gs<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, S>(h), mk + kr * N * N, HB ? 1 : 0, gsv);
     k_scan_tilemaps<N, M, S><<<(nt + 3) / 4, 128, 0, st>>>(phit64, g, pw, tiles);
     const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;
     k_lti_segments<N, M, S><<<(nt + 127) / 128, 128, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
@@ -549,6 +495,145 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     h.sc_Jt = Jt;
     h.sc_nt = nt;
     h.tab_ok = 1;
+    return MAP_OK;
+}
+
+// whether the stream is being captured into a graph (errors count as capturing)
+inline bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cap != cudaStreamCaptureStatusNone;
+}
+
+// the sample's share of the element offset (b_k = Bb y_k + b0) of block and
+// exact elements; off for per-step elements
+template <int N, int M>
+SampleOffset<N, M> sample_offset(const map_smoother& h)
+{
+    SampleOffset<N, M> so{};
+    so.on = h.disc >= MAP_BLOCK_EULER;
+    for (int i = 0; i < N * M; ++i) so.Bb[i] = so.on ? h.consts.Bb[i] : 0.0;
+    return so;
+}
+
+// Per-step tables (steptab.cuh) of an RTS solve of a linear time-invariant
+// model and the tiled-scan plan, computed once per model (they depend on the
+// model constants and T only): the element powers, every step's row, the
+// stationary point kc (read back: a synchronisation, so never under stream
+// capture), then the scan tables.  h.tab_ok tells whether the tiled scan can
+// run; otherwise the solve keeps the other paths.
+template <int N, int M, typename S, bool HB>
+map_status table_plan(map_smoother& h, cudaStream_t st)
+{
+    using ST = StepTab<N, S>;
+    if (!h.d_tab || h.tab_state || h.smoother != MAP_RTS || capturing(st)) return MAP_OK;
+    h.tab_ok = 0;
+    h.tab_state = 1;
+    // rows of the steps k < KT; with T >= KT the convergence point kc, from
+    // which row kc stands for every later step, must leave room for the
+    // thread maps of the threads that reach it
+    const long KT = std::min<long>(h.T + 1, ST::cap());
+    const int check = h.T + 1 > KT;
+    const double tol = sizeof(S) == 4 ? 0x1p-25 : 1e-14;
+    unsigned long long meta[2] = {0, 0};
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h.d_tab, 0, sizeof(meta), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    k_step_powers<N, M><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), prior_of<N, double>(h), h.T, KT, h.d_tab);
+    k_lti_steptab<N, M, S><<<(unsigned)((KT + 127) / 128), 128, 0, st>>>(
+        lti_params<N, M, double>(h), prior_of<N, double>(h), KT, check, tol, sample_offset<N, M>(h), h.d_tab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "step table kernel launch");
+    if ((e = cudaMemcpyAsync(meta, h.d_tab, sizeof(meta), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(h, e, "step table read-back");
+    const long kc = check ? (long)meta[0] : h.T;
+    if (meta[1] != 0 || (check && kc + 1 >= KT)) return MAP_OK;
+    h.tab_kt = KT;
+    h.tab_kc = kc;
+    return scan_plan<N, M, S, HB>(h, st);
+}
+
+// The tiled-scan solve (one cooperative launch) when its tables are ready;
+// *ran is false when the other paths must run.
+template <int N, int M, typename S, bool HB>
+map_status run_scan(map_smoother& h, const LtiProducer<N, M, S>& prod, S* x_out, S* filt_out, cudaStream_t st,
+                    bool* ran)
+{
+    using ST = StepTab<N, S>;
+    using SB = ScanBuf<N, M, S>;
+    using TT = TileTables<N, M, S>;
+    using R = Red<N, S>;
+    *ran = false;
+    if (map_status s = table_plan<N, M, S, HB>(h, st); s != MAP_OK) return s;
+    if (!h.tab_ok || h.profile || capturing(st)) return MAP_OK;
+    if (ScanSmem<N, M, S>::STAGE && (reinterpret_cast<uintptr_t>(prod.y) & 15) != 0) return MAP_OK;
+    constexpr int B = 128;
+    const int snt = h.sc_nt;
+    const long KT = h.tab_kt;
+    ScanArgs<N, M, S> sa{};
+    sa.g = ScanGeom{B, h.sc_K, h.sc_Kt, h.sc_Jt, snt};
+    sa.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off());
+    sa.kc = h.tab_kc;
+    sa.phit = reinterpret_cast<const S*>(h.d_tab + ST::phit_off(KT));
+    sa.mk = reinterpret_cast<const S*>(h.d_tab + ST::mk_off(KT));
+    sa.pw = reinterpret_cast<const S*>(h.d_scan + SB::pw_off());
+    sa.ttab = reinterpret_cast<const S*>(h.d_scan + SB::ttab_off());
+    sa.w = reinterpret_cast<S*>(h.d_scan + SB::w_off());
+    sa.taff = reinterpret_cast<S*>(h.d_scan + SB::taff_off());
+    sa.gs = reinterpret_cast<const S*>(h.d_scan + SB::gs_off());
+    const char* tiles = h.d_scan + SB::tiles_off();
+    sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));
+    sa.qt = reinterpret_cast<const S*>(tiles + TT::qt_off(snt));
+    sa.pdummy = reinterpret_cast<const S*>(tiles + TT::p_off());
+    const SetupOut& c = h.consts;
+    sa.has_b = 0;
+    for (int i = 0; i < N; ++i) sa.has_b |= c.b[i] != 0.0;
+    for (int i = 0; i < N; ++i) {
+        double ab = 0.0;
+        for (int k = 0; k < N; ++k) ab += c.Phi[i * N + k] * c.b[k];
+        sa.Aib[i] = S(ab);
+        for (int j = 0; j < N; ++j) {
+            double ac = 0.0;
+            for (int k = 0; k < N; ++k) ac += c.Phi[i * N + k] * c.C[k * N + j];
+            sa.AiC[i * N + j] = S(ac);
+        }
+        for (int j = 0; j < M; ++j) {
+            double ab2 = 0.0;
+            if (HB)
+                for (int k = 0; k < N; ++k) ab2 += c.Phi[i * N + k] * c.Bb[k * M + j];
+            sa.AiBb[i * M + j] = S(ab2);
+        }
+    }
+    const CombineCtx ctx{(float)h.cond_max, h.d_stats};
+    const Layout<N, S> L = Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad, false);
+    S* fin = reinterpret_cast<S*>(h.ws + L.fin);
+    S* filtT = filt_out ? filt_out + h.T * R::NCOMP : (S*)nullptr;
+    const GridSync gs{h.d_stats + EV_BARRIER, h.bar_arrivals};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(snt);
+    cfg.blockDim = dim3(B);
+    cfg.dynamicSmemBytes = ScanSmem<N, M, S>::bytes(B, h.sc_K, h.sc_Kt);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_lti_scan<N, S, LtiProducer<N, M, S>, HB>, prod, prior_of<N, S>(h),
+                                       filt_out, ctx, fin, x_out, filtT, gs, sa);
+    if (e != cudaSuccess) {
+        // the grid cannot be resident at once after all: the other paths
+        cudaGetLastError();
+        h.tab_ok = 0;
+        return MAP_OK;
+    }
+    h.launches += 1;
+    h.path = MAP_PATH_TABLES;
+    h.bar_arrivals += 2ull * (unsigned long long)snt;
+    *ran = true;
     return MAP_OK;
 }
 
@@ -572,26 +657,13 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
         LtiDownSmem<N, M, S>::bytes(h.B, h.K, false) > 200 * 1024 ||
         LtiReduceSmem<N, M, S>::bytes(h.B, h.K, LB) > 200 * 1024)
         return MAP_OK;
-    // the per-step tables need a synchronisation (their convergence point is
-    // read back), so they are (re)computed outside stream capture only
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
-        cudaGetLastError();
-        cap = cudaStreamCaptureStatusActive;
-    }
-    const bool want_tab = h.d_tab && cap == cudaStreamCaptureStatusNone && (h.tab_K != h.K || h.tab_B != h.B);
-    if (h.fold_K != h.K || h.fold_B != h.B || want_tab) {
-        using ST = StepTab<N, S>;
-        double* f64 = want_tab ? reinterpret_cast<double*>(h.d_tab + ST::fold_off()) : nullptr;
-        double* pre64 = want_tab ? reinterpret_cast<double*>(h.d_tab + ST::pre_off()) : nullptr;
-        double* p64 = want_tab ? reinterpret_cast<double*>(h.d_tab + ST::p64_off()) : nullptr;
+    if (h.fold_K != h.K || h.fold_B != h.B) {
         // one warp for the serial FP64 chains, then one warp per thread
         // prefix and per tile in one launch, four to a block so that they
         // spread over the SMs' FP64 pipes
-        k_lti_fold<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), h.K, LB, ne,
-                                             static_cast<S*>(h.d_fold), f64);
+        k_lti_fold<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), h.K, LB, ne, static_cast<S*>(h.d_fold));
         k_lti_tables<N, M, S><<<((1 << LB) + 3) / 4 + (h.nt + 3) / 4, 128, 0, st>>>(
-            prior_of<N, double>(h), LB, h.nt, ne, static_cast<S*>(h.d_fold), pre64, p64);
+            prior_of<N, double>(h), LB, h.nt, ne, static_cast<S*>(h.d_fold));
         if (h.nt <= TT::PI_TILES) {
             const int segs = (h.nt + TT::PI_SEG - 1) / TT::PI_SEG;
             k_lti_segments<N, M, S><<<(h.nt + 127) / 128, 128, 0, st>>>(h.nt, static_cast<S*>(h.d_fold));
@@ -602,34 +674,6 @@ map_status lti_fold_consts(map_smoother& h, cudaStream_t st, const S** out)
         if (e != cudaSuccess) return cuda_fail(h, e, "fold constants kernel launch");
         h.fold_K = h.K;
         h.fold_B = h.B;
-        h.tab_ok = 0;
-        h.tab_K = h.tab_B = 0;
-        if (want_tab) {
-            // rows of the steps k < KT; with T >= KT the convergence point kc,
-            // from which row kc stands for every later step, must leave room
-            // for the thread maps of the threads that reach it
-            const long KT = std::min<long>(h.T + 1, ST::cap());
-            const int check = h.T + 1 > KT;
-            const double tol = sizeof(S) == 4 ? 0x1p-25 : 1e-14;
-            unsigned long long meta[2] = {0, 0};
-            if ((e = cudaMemsetAsync(h.d_tab, 0, sizeof(meta), st)) != cudaSuccess)
-                return cuda_fail(h, e, "cudaMemsetAsync");
-            k_lti_steptab<N, M, S><<<(unsigned)((KT + 127) / 128), 128, 0, st>>>(
-                lti_params<N, M, double>(h), h.K, h.B, h.nt, KT, check, tol, h.d_tab);
-            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "step table kernel launch");
-            if ((e = cudaMemcpyAsync(meta, h.d_tab, sizeof(meta), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(st)) != cudaSuccess)
-                return cuda_fail(h, e, "step table read-back");
-            const long kc = check ? (long)meta[0] : h.T;
-            h.tab_K = h.K;
-            h.tab_B = h.B;
-            if (meta[1] == 0 && (!check || kc + 1 < KT)) {
-                h.tab_kt = KT;
-                h.tab_kc = kc;
-                map_status s2 = scan_plan<N, M, S>(h, st);
-                if (s2 != MAP_OK) return s2;
-            }
-        }
     }
     *out = static_cast<const S*>(h.d_fold);
     return MAP_OK;
@@ -683,6 +727,16 @@ map_status solve_linear_block(map_smoother& h, const void* y, void* x_out, void*
     prod.T = h.T;
     prod.p = block_params<N, M, S>(h);
     if (sequential) return run_sequential<N, S>(h, prod, static_cast<S*>(x_out), st);
+    // A, C and J are the same for every interval: the tiled scan with the
+    // per-step tables, with the sample's share of the offset
+    LtiProducer<N, M, S> lp;
+    lp.y = prod.y;
+    lp.T = h.T;
+    lp.p = lti_params<N, M, S>(h);
+    bool ran = false;
+    if (map_status s = run_scan<N, M, S, true>(h, lp, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, &ran);
+        s != MAP_OK || ran)
+        return s;
     return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st);
 }
 
@@ -799,13 +853,20 @@ map_status solve_linear(map_smoother& h, const void* y, void* x_out, void* filt_
 {
     if constexpr (N <= 6)
         if (h.disc >= MAP_BLOCK_EULER) return solve_linear_block<N, M, S>(h, y, x_out, filt_out, st, false);
-    const S* fold = nullptr;
-    if (map_status s = lti_fold_consts<N, M, S>(h, st, &fold); s != MAP_OK) return s;
-    if constexpr (N <= 6) if (h.smoother == MAP_TWO_FILTER) return solve_linear_tf<N, M, S>(h, y, x_out, filt_out, st, fold);
     LtiProducer<N, M, S> prod;
     prod.y = static_cast<const S*>(y);
     prod.T = h.T;
     prod.p = lti_params<N, M, S>(h);
+    if (h.smoother == MAP_RTS) {
+        bool ran = false;
+        if (map_status s = run_scan<N, M, S, false>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st,
+                                                   &ran);
+            s != MAP_OK || ran)
+            return s;
+    }
+    const S* fold = nullptr;
+    if (map_status s = lti_fold_consts<N, M, S>(h, st, &fold); s != MAP_OK) return s;
+    if constexpr (N <= 6) if (h.smoother == MAP_TWO_FILTER) return solve_linear_tf<N, M, S>(h, y, x_out, filt_out, st, fold);
     return run_rts<N, S>(h, prod, static_cast<S*>(x_out), static_cast<S*>(filt_out), st, false, fold);
 }
 
@@ -1114,7 +1175,7 @@ template <int N, typename S>
 size_t step_table_bytes(const map_smoother& h)
 {
     if (h.smoother != MAP_RTS) return 0;
-    return StepTab<N, S>::bytes(h.nt, std::min<long>(h.T + 1, StepTab<N, S>::cap()));
+    return StepTab<N, S>::bytes(std::min<long>(h.T + 1, StepTab<N, S>::cap()));
 }
 
 // bytes of the tiled-scan tables (steptab.cuh ScanBuf)
@@ -1138,7 +1199,8 @@ const Ops* linear_ops()
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
                              &solve_linear_sequential<N, M, S>, nullptr, nullptr,
-                             &rts_resident_blocks<N, S, LtiProducer<N, M, S>>};
+                             &rts_resident_blocks<N, S, LtiProducer<N, M, S>>,
+                             &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>};
         return &ops;
     }
 }

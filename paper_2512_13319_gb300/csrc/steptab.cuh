@@ -56,36 +56,41 @@
 namespace mapk {
 
 // Layout of the step-table buffer (offsets in bytes): a few counters, the
-// FP64 pre_s (A, C, J; s < BMAX), the FP64 i-step folds (A, C, J; i <= KMAX)
-// and the FP64 P_j of the tiles of the uniform (B, K) decomposition (all full
-// N x N matrices), then per step k < KT: the row in the solve's precision S
-// (E, o, mb, P b, P packed) and E in FP64, and for the thread starts
-// k = g K_t < KT the K_t-step maps Phi_g in S and in FP64.
+// FP64 element powers e^(2^l) (A, C, J as full N x N matrices; l < LPOW),
+// the FP64 P_T of the last step, then per step k < KT: the row in the solve's
+// precision S (E, o, mb, P b, P packed), E in FP64 and, for elements whose
+// offset b depends on the held sample (b_k = Bb y_k + b0), -E_k^T P_k Bb
+// (N x M in an N x N slot); and for the thread starts k = g K_t < KT the
+// K_t-step maps Phi_g in S and in FP64.
 template <int N, typename S>
 struct StepTab {
     static constexpr int NN = N * N, NS = Sym<N>::SZ;
     static constexpr int oE = 0, oO = NN, oMB = NN + N, oPB = NN + 2 * N, oP = NN + 3 * N;
     static constexpr int RS = ((NN + 3 * N + NS) * (int)sizeof(S) + 15) / 16 * 16 / (int)sizeof(S);
-    static constexpr int BMAX = 128, KMAX = 64;
-    static constexpr int KT_STEPS = 16 / (int)sizeof(S);      // steps per thread before kc
+    static constexpr int BMAX = 128, LPOW = 48;
+    // steps per thread before kc: 16 bytes of a step's scalar per thread row
+    // for N <= 6; for larger N the tiles before kc read their rows from
+    // global memory and keep to 8 bytes
+    static constexpr int KT_STEPS = (N <= 6 ? 16 : 8) / (int)sizeof(S);
     __host__ __device__ static constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
-    __host__ __device__ static constexpr size_t pre_off() { return 256; }
-    __host__ __device__ static constexpr size_t fold_off() { return al(pre_off() + sizeof(double) * BMAX * 3 * NN); }
-    __host__ __device__ static constexpr size_t p64_off() { return al(fold_off() + sizeof(double) * (KMAX + 1) * 3 * NN); }
-    __host__ __device__ static constexpr size_t rows_off(long nt) { return al(p64_off() + sizeof(double) * nt * NN); }
-    __host__ __device__ static constexpr size_t e64_off(long nt, long kt) { return al(rows_off(nt) + sizeof(S) * kt * RS); }
+    __host__ __device__ static constexpr size_t pow_off() { return 256; }
+    __host__ __device__ static constexpr size_t pref_off() { return al(pow_off() + sizeof(double) * LPOW * 3 * NN); }
+    __host__ __device__ static constexpr size_t rows_off() { return al(pref_off() + sizeof(double) * NN); }
+    __host__ __device__ static constexpr size_t e64_off(long kt) { return al(rows_off() + sizeof(S) * kt * RS); }
+    __host__ __device__ static constexpr size_t mk_off(long kt) { return al(e64_off(kt) + sizeof(double) * kt * NN); }
     __host__ __device__ static constexpr long phit_count(long kt) { return kt / KT_STEPS + 1; }
-    __host__ __device__ static constexpr size_t phit_off(long nt, long kt) { return al(e64_off(nt, kt) + sizeof(double) * kt * NN); }
-    __host__ __device__ static constexpr size_t phit64_off(long nt, long kt)
+    __host__ __device__ static constexpr size_t phit_off(long kt) { return al(mk_off(kt) + sizeof(S) * kt * NN); }
+    __host__ __device__ static constexpr size_t phit64_off(long kt)
     {
-        return al(phit_off(nt, kt) + sizeof(S) * phit_count(kt) * NN);
+        return al(phit_off(kt) + sizeof(S) * phit_count(kt) * NN);
     }
-    __host__ __device__ static constexpr size_t bytes(long nt, long kt)
+    __host__ __device__ static constexpr size_t bytes(long kt)
     {
-        return phit64_off(nt, kt) + sizeof(double) * phit_count(kt) * NN;
+        return phit64_off(kt) + sizeof(double) * phit_count(kt) * NN;
     }
     // table length cap: the FP32 table converges within 2^-25 earlier
     __host__ __device__ static constexpr long cap() { return sizeof(S) == 4 ? 16384 : 32768; }
+    __host__ __device__ static constexpr int log2_kt() { return KT_STEPS >= 4 ? 2 : KT_STEPS == 2 ? 1 : 0; }
 };
 
 namespace steptab_detail {
@@ -238,37 +243,90 @@ __device__ __forceinline__ bool fold_map(const double* __restrict__ f, const dou
 
 }  // namespace steptab_detail
 
-// One thread per tabulated step k < KT (FP64): P_k from the tile, thread-prefix
-// and i-step tables (see the top of this file), then the row of constants and,
-// for the first step of a thread of K_t steps (k = g K_t), the thread's
-// composite closed-loop map Phi_g = (I + C_Kt P_k)^-1 A_Kt of its K_t-step
-// fold (the composition of its K_t per-step maps: the closed-loop map of the
-// combined element).  With check, every step whose P_k differs from P_ref
-// beyond tol raises meta[0] to k + 1; meta[1] counts non-positive Cholesky
-// pivots.
+// Element powers e^(2^l) of the data-free interval element e = (A, C, J)
+// (Eq. 36 combine of an element with itself, FP64 with row-pivoted inverses),
+// for every l with 2^l <= max(T, KT), and P_T, the value function after all T
+// steps (the powers of the set bits of T applied to P_0; powers of one element
+// commute).  One thread.
+template <int N, int M>
+__global__ void __launch_bounds__(32)
+k_step_powers(const LtiParams<N, M, double> p, const Red<N, double> prior, long T, long KT, char* __restrict__ tab)
+{
+    using ST = StepTab<N, float>;
+    constexpr int NN = N * N;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double* pw = reinterpret_cast<double*>(tab + ST::pow_off());
+    const CombineCtx ctx{0.0f, nullptr};          // every inverse by the FP64 row-pivoted path
+    Elem<N, double> e;
+#pragma unroll
+    for (int q = 0; q < NN; ++q) e.A[q] = p.A[q];
+#pragma unroll
+    for (int q = 0; q < Sym<N>::SZ; ++q) { e.C[q] = p.C[q]; e.J[q] = p.J[q]; }
+#pragma unroll
+    for (int q = 0; q < N; ++q) { e.b[q] = 0.0; e.eta[q] = 0.0; }
+    Red<N, double> X = prior;
+    const long top = T > KT ? T : KT;
+#pragma unroll 1
+    for (int l = 0; l < ST::LPOW && (1L << l) <= top; ++l) {
+        double* w = pw + (long)l * 3 * NN;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const int a = q / N, c = q % N;
+            w[q] = e.A[q];
+            w[NN + q] = e.C[Sym<N>::at(a, c)];
+            w[2 * NN + q] = e.J[Sym<N>::at(a, c)];
+        }
+        if ((T >> l) & 1) apply<N, double, false>(e, X, nullptr, nullptr, ctx);
+        combine<N, double>(e, e, e, ctx);
+    }
+    double* pr = reinterpret_cast<double*>(tab + ST::pref_off());
+#pragma unroll
+    for (int q = 0; q < NN; ++q) {
+        const int a = q / N, c = q % N;
+        pr[q] = X.P[Sym<N>::at(a, c)];
+    }
+}
+
+// Optional held-sample dependence of the element offset: b_k = Bb y_k + b0
+// (block and exact elements); Bb is N x M row-major.
+template <int N, int M>
+struct SampleOffset {
+    int on;
+    double Bb[N * M];
+};
+
+// One thread per tabulated step k < KT (FP64): P_k from the element powers
+// (the set bits of k applied to P_0), then the row of constants, -E_k^T P_k Bb
+// when the offset depends on the sample, and for the first step of a thread of
+// K_t steps (k = g K_t) the thread's composite closed-loop map
+// Phi_g = (I + C_Kt P_k)^-1 A_Kt of the K_t-step element e^(K_t) (the
+// composition of its K_t per-step maps: the closed-loop map of the combined
+// element).  With check, every step whose P_k differs from P_T beyond tol
+// raises meta[0] to k + 1; meta[1] counts non-positive Cholesky pivots.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(128)
-k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, int check, double tol,
-              char* __restrict__ tab)
+k_lti_steptab(const LtiParams<N, M, double> p, const Red<N, double> prior, long KT, int check, double tol,
+              const SampleOffset<N, M> so, char* __restrict__ tab)
 {
     namespace sd = steptab_detail;
     using ST = StepTab<N, S>;
     constexpr int NN = N * N, Kt = ST::KT_STEPS;
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= KT) return;
-    const double* pre = reinterpret_cast<const double*>(tab + ST::pre_off());
-    const double* fold = reinterpret_cast<const double*>(tab + ST::fold_off());
-    const double* p64 = reinterpret_cast<const double*>(tab + ST::p64_off());
+    const double* pw = reinterpret_cast<const double*>(tab + ST::pow_off());
     unsigned long long* meta = reinterpret_cast<unsigned long long*>(tab);
-    S* row = reinterpret_cast<S*>(tab + ST::rows_off(nt)) + k * ST::RS;
-    double* e64 = reinterpret_cast<double*>(tab + ST::e64_off(nt, KT)) + k * NN;
-    const long L = (long)B * K;
-    const int j = (int)(k / L), s = (int)((k % L) / K), i = (int)(k % K);
+    S* row = reinterpret_cast<S*>(tab + ST::rows_off()) + k * ST::RS;
+    double* e64 = reinterpret_cast<double*>(tab + ST::e64_off(KT)) + k * NN;
     double P[NN];
-    sd::load_full<N>(p64 + (long)j * NN, P);
+#pragma unroll
+    for (int q = 0; q < NN; ++q) {
+        const int a = q / N, c = q % N;
+        P[q] = prior.P[Sym<N>::at(a, c)];
+    }
     bool ok = true;
-    if (s > 0) ok = sd::apply_p<N>(pre + (long)s * 3 * NN, P) && ok;
-    if (i > 0) ok = sd::apply_p<N>(fold + (long)i * 3 * NN, P) && ok;
+#pragma unroll 1
+    for (int l = 0; (k >> l) != 0; ++l)
+        if ((k >> l) & 1) ok = sd::apply_p<N>(pw + (long)l * 3 * NN, P) && ok;
     // per-step constants from Z of (P, C): E = A - C Z^T (Z A), mb = b - C Z^T (Z b)
     double A[NN], C[NN], b[N], Z[NN], ZA[NN], CZt[NN];
 #pragma unroll
@@ -329,11 +387,34 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
 #pragma unroll
         for (int c = a; c < N; ++c) row[ST::oP + Sym<N>::at(a, c)] = S(P[a * N + c]);
     }
+    if (so.on) {
+        // -E^T P Bb: the sample's share of o_k
+        S* mk = reinterpret_cast<S*>(tab + ST::mk_off(KT)) + k * NN;
+        double PB[N * M];
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(P[a * N + q], so.Bb[q * M + c], acc);
+                PB[a * M + c] = acc;
+            }
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(-E[q * N + a], PB[q * M + c], acc);
+                mk[a * M + c] = S(acc);
+            }
+    }
     if (k % Kt == 0) {
         double Ph[NN];
-        ok = sd::fold_map<N>(fold + (long)Kt * 3 * NN, P, Ph) && ok;
-        S* ph = reinterpret_cast<S*>(tab + ST::phit_off(nt, KT)) + (k / Kt) * NN;
-        double* ph64 = reinterpret_cast<double*>(tab + ST::phit64_off(nt, KT)) + (k / Kt) * NN;
+        ok = sd::fold_map<N>(pw + (long)ST::log2_kt() * 3 * NN, P, Ph) && ok;
+        S* ph = reinterpret_cast<S*>(tab + ST::phit_off(KT)) + (k / Kt) * NN;
+        double* ph64 = reinterpret_cast<double*>(tab + ST::phit64_off(KT)) + (k / Kt) * NN;
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
             ph[q] = S(Ph[q]);
@@ -342,7 +423,7 @@ k_lti_steptab(const LtiParams<N, M, double> p, int K, int B, int nt, long KT, in
     }
     if (check) {
         double Pr[NN];
-        sd::load_full<N>(p64 + (long)(nt >= 2 ? nt - 2 : 0) * NN, Pr);
+        sd::load_full<N>(reinterpret_cast<const double*>(tab + ST::pref_off()), Pr);
         bool conv = true;
 #pragma unroll
         for (int a = 0; a < N; ++a)
@@ -370,14 +451,16 @@ struct ScanGeom {
 };
 
 // Layout of the scan buffer (offsets in bytes): the powers Phi_inf^d
-// (d = 0..BMAX), the per-step E_k (and P_k b) of the tiles before kc in the
-// order of their shared-memory copy (component c of step i of thread t at
-// (i CT + c) B + t), the tiles' offsets w_j and RTS maps, then the tile
-// tables of lti_fold.cuh (TileTables: F_j = E_j^T and the products Pi).
+// (d = 0..BMAX), the per-step E_k and o_k of the tiles before kc in the order
+// of their shared-memory copy (component c of step i of thread t at
+// (i CT + c) B + t), the tiles' offsets w_j and RTS maps, the measurement
+// gain of the steps after kc (G, plus -E^T P Bb when the offset depends on the
+// sample), then the tile tables of lti_fold.cuh (TileTables: F_j = E_j^T and
+// the products Pi).
 template <int N, int M, typename S>
 struct ScanBuf {
     static constexpr int NN = N * N, BMAX = 128, NTMAX = 4 * BMAX + 1;
-    static constexpr int CT = NN + N;                         // E, P b
+    static constexpr int CT = NN + N;                         // E, o
     using ST = StepTab<N, S>;
     __host__ __device__ static constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
     __host__ __device__ static constexpr long jt_max() { return ST::cap() / (BMAX * ST::KT_STEPS) + 2; }
@@ -386,7 +469,8 @@ struct ScanBuf {
     __host__ __device__ static constexpr size_t ttab_tile() { return (size_t)BMAX * ST::KT_STEPS * CT; }
     __host__ __device__ static constexpr size_t w_off() { return al(ttab_off() + sizeof(S) * jt_max() * ttab_tile()); }
     __host__ __device__ static constexpr size_t taff_off() { return al(w_off() + sizeof(S) * NTMAX * N); }
-    __host__ __device__ static constexpr size_t tiles_off() { return al(taff_off() + sizeof(S) * NTMAX * (NN + N)); }
+    __host__ __device__ static constexpr size_t gs_off() { return al(taff_off() + sizeof(S) * NTMAX * (NN + N)); }
+    __host__ __device__ static constexpr size_t tiles_off() { return al(gs_off() + sizeof(S) * N * M); }
     __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::bytes(NTMAX); }
 };
 
@@ -492,7 +576,7 @@ k_scan_tilemaps(const double* __restrict__ phit64, ScanGeom g, const S* __restri
     for (int q = l; q < NN; q += 32) F[q] = S(acc[(q % N) * N + q / N]);
 }
 
-// Per-step E_k and P_k b of the tiles before kc, in the order of their
+// Per-step E_k and o_k of the tiles before kc, in the order of their
 // shared-memory copy; zeros past the table
 template <int N, typename S>
 __global__ void k_scan_ttab(const S* __restrict__ rows, long KT, ScanGeom g, S* __restrict__ ttab)
@@ -507,52 +591,67 @@ __global__ void k_scan_ttab(const S* __restrict__ rows, long KT, ScanGeom g, S* 
     const int t = (int)(r % g.B), ic = (int)(r / g.B), i = ic / CT, c = ic % CT;
     const long k = (long)j * g.B * g.Kt + (long)t * g.Kt + i;
     S v = S(0);
-    if (k < KT) v = c < NN ? rows[k * ST::RS + ST::oE + c] : rows[k * ST::RS + ST::oPB + (c - NN)];
+    if (k < KT) v = c < NN ? rows[k * ST::RS + ST::oE + c] : rows[k * ST::RS + ST::oO + (c - NN)];
     ttab[e] = v;
+}
+
+// measurement gain of the steps after kc: G + (-E^T P Bb of row kc)
+template <int N, int M, typename S>
+__global__ void k_scan_gs(const LtiParams<N, M, S> p, const S* __restrict__ mk_kc, int on, S* __restrict__ gs)
+{
+    for (int q = threadIdx.x; q < N * M; q += blockDim.x) gs[q] = p.G[q] + (on ? mk_kc[q] : S(0));
 }
 
 // ---------------------------------------------------------------------------
 // the tiled-scan solve
 // ---------------------------------------------------------------------------
-template <int N, typename S>
+template <int N, int M, typename S>
 struct ScanArgs {
     const S* rows;          // step rows (StepTab)
     long kc;                // steps k >= kc read row kc
     const S* pw;            // Phi_inf^d, d = 0..B
-    const S* ttab;          // per-step E_k, P_k b of the tiles before kc
+    const S* ttab;          // per-step E_k, o_k of the tiles before kc
     const S* phit;          // K_t-step thread maps before kc
     S* w;                   // tile offsets of the filter maps
     S* taff;                // tile RTS maps
     const S* pi;            // tile-map products (TileTables)
     const S* qt;
     const S* pdummy;        // a readable P_j table for the tile-prefix helper (its P is not used)
+    const S* gs;            // measurement gain of the steps after kc (with the sample's share of o)
+    const S* mk;            // per-step -E_k^T P_k Bb (steps before kc; offsets depending on the sample)
     ScanGeom g;
-    int has_b;              // b != 0: the o_k and P_k b terms
+    int has_b;              // b != 0: the A^-1 b term of g_k
     S AiC[N * N];           // A^-1 C
-    S Aib[N];               // A^-1 b
+    S Aib[N];               // A^-1 b (b0 when the offset depends on the sample)
+    S AiBb[N * M];          // A^-1 Bb
 };
 
 // shared memory of k_lti_scan (offsets in scalars): the composition area, the
 // warp totals, the tile's observations, the per-step offsets g_k (staged
 // states in the RTS phase; exchange area of the full-map compositions before
-// that), then the powers Phi_inf^d (tiles after kc) or the per-step E_k, P_k b
-// (tiles before kc), then the mbarrier
+// that), then the powers Phi_inf^d (tiles after kc) or the per-step E_k, o_k
+// (tiles before kc), then the mbarrier.  With STAGE false (state dimensions
+// above 6, whose per-step data would not fit for a grid of co-resident tiles)
+// the observations are read from global memory, the g_k and states go
+// through x_out, and the tiles before kc read their rows from global memory:
+// only the composition areas and the powers stay.
 template <int N, int M, typename S>
 struct ScanSmem {
     static constexpr int NN = N * N, NA = NN + N, CT = NN + N;
+    static constexpr bool STAGE = N <= 6;
     __host__ __device__ static constexpr int al(int x) { return (x + 3) / 4 * 4; }
     __host__ __device__ static constexpr int red_size(int B) { return (B / 32) * (NA + N) + N; }
     __host__ __device__ static constexpr int wt(int B) { return al(red_size(B)); }
     __host__ __device__ static constexpr int ys(int B) { return al(wt(B) + 2 * (B / 32) * N + 2 * N); }
-    __host__ __device__ static constexpr int gst(int B, int Kmax) { return al(ys(B) + B * Kmax * M); }
+    __host__ __device__ static constexpr int gst(int B, int Kmax) { return al(ys(B) + (STAGE ? B * Kmax * M : 0)); }
     __host__ __device__ static constexpr int tabs(int B, int Kmax)
     {
-        return al(gst(B, Kmax) + (B * Kmax * N > B * NA ? B * Kmax * N : B * NA));
+        return al(gst(B, Kmax) + (STAGE && B * Kmax * N > B * NA ? B * Kmax * N : B * NA));
     }
     __host__ __device__ static constexpr int bar(int B, int K, int Kt)
     {
         // the tile kind with the larger footprint decides
-        const int a = tabs(B, K) + (B + 1) * NN, c = tabs(B, Kt) + B * Kt * CT;
+        const int a = tabs(B, K) + (B + 1) * NN, c = tabs(B, Kt) + (STAGE ? B * Kt * CT : 0);
         return al(a > c ? a : c);
     }
     __host__ __device__ static constexpr size_t bytes(int B, int K, int Kt) { return sizeof(S) * (size_t)bar(B, K, Kt) + 16; }
@@ -611,22 +710,35 @@ __device__ __forceinline__ void reverse_vec(S (&v)[N], S* scratch)
     __syncthreads();
 }
 
-template <int N, typename S, class Prod>
+// The tiled-scan solve, one CTA of 128 threads per tile, all tiles
+// co-resident (cooperative launch), three phases separated by two grid
+// barriers:
+//   1. the thread's filter offset W (its map v -> Psi v + W from v = 0) and
+//      the tile's offset w_j;
+//   2. the tile prefix (tile tables), the thread start values, the per-step
+//      filter with the closed-loop offsets g_k staged, the thread's RTS offset
+//      and the tile's RTS map;
+//   3. the tile suffix, the thread end states and the per-step RTS pass.
+// HB: the element offset depends on the held sample, b_k = Bb y_k + b0
+// (block and exact elements): o_k gains -E_k^T P_k Bb y_k (folded into the
+// gain of the steps after kc) and g_k gains E_k A^-1 Bb y_k.
+template <int N, typename S, class Prod, bool HB>
 __global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
 k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restrict__ filt_out, CombineCtx ctx,
            S* __restrict__ final_out, S* __restrict__ x_out, S* __restrict__ filtT_out, const GridSync gs,
-           const __grid_constant__ ScanArgs<N, S> sa)
+           const __grid_constant__ ScanArgs<N, Prod::W, S> sa)
 {
     if constexpr (Prod::LINEAR_FOLD) {
         constexpr int M = Prod::W, NN = N * N, NA = NN + N, CT = NN + N;
         using ST = StepTab<N, S>;
         using SM = ScanSmem<N, M, S>;
+        constexpr bool STAGE = SM::STAGE;
         extern __shared__ __align__(16) unsigned char smem_raw[];
         S* sm = reinterpret_cast<S*>(smem_raw);
         const ScanGeom& g = sa.g;
         const int B = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = B >> 5;
         const int tile = blockIdx.x;
-        const bool trans = tile < g.Jt;                    // before kc: K_t steps, tabulated E_k in smem
+        const bool trans = tile < g.Jt;                    // before kc: K_t steps, tabulated E_k
         const bool last = tile + 1 == g.nt;
         const bool powers = !trans && !last;               // in-tile scans on offsets with Phi_inf^d
         const int Kj = g.steps(tile);
@@ -637,20 +749,22 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         S* red = sm;
         S* wt = sm + SM::wt(B);
         S* ys = sm + SM::ys(B);
-        S* gst = sm + SM::gst(B, Kj);
-        S* tb = sm + SM::tabs(B, Kj);                      // powers or per-step E_k, P_k b
+        S* gst = sm + SM::gst(B, Kj);                      // staged g_k / states, exchange area
+        S* tb = sm + SM::tabs(B, Kj);                      // powers or per-step E_k, o_k
         unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + SM::bar(B, g.K, g.Kt));
-        S* mine = gst + t * Kj * N;
+        S* mine = STAGE ? gst + t * Kj * N : x_out + k0 * N;   // this thread's g_k, then states
 
         // ---- phase 1: observations and tables into shared memory, the
         // thread's filter offset W (map v -> Psi v + W from v = 0), the
         // tile's filter offset w_j
         // (rounded up to whole 16-byte words: both source tables and the shared
         // area are padded to them)
+        const bool tcopy = STAGE || !trans;
         const unsigned tbytes =
-            (unsigned)((sizeof(S) * (trans ? (size_t)B * g.Kt * CT : (size_t)(B + 1) * NN) + 15) / 16 * 16);
+            tcopy ? (unsigned)((sizeof(S) * (trans ? (size_t)B * g.Kt * CT : (size_t)(B + 1) * NN) + 15) / 16 * 16)
+                  : 0u;
         const long yoff = s0 * M;
-        const long ycnt = (long)B * Kj * M;
+        const long ycnt = STAGE ? (long)B * Kj * M : 0;
         // the tile's rows by one bulk copy: all of them for full tiles, the
         // whole 16-byte words before T for the last tile (the rest below)
         const long yhave = min(ycnt, T * M - yoff);
@@ -660,7 +774,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         if (t == 0) {
             mbar_arrive_expect_tx(bar, tbytes + (unsigned)(sizeof(S) * ybulk));
             if (ybulk > 0) bulk_copy_g2s(ys, prod.y + yoff, (unsigned)(sizeof(S) * ybulk), bar);
-            bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * g.Kt * CT : sa.pw, tbytes, bar);
+            if (tbytes) bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * g.Kt * CT : sa.pw, tbytes, bar);
             // the tile-product rows that the tile prefix and suffix sums read
             // after the grid barriers (data-independent): into L2 now
             using TT1 = TileTables<N, 1, S>;
@@ -685,43 +799,53 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             if (t == 0) report_event(ctx.stats, EV_TIMEOUT);
             mbar_wait_bounded(bar, 0, MBAR_POLLS);      // the copy may still be in flight
         }
-        const S* yt = ys + t * Kj * M;
-        // step constants: E_k (and o_k) of step i of this thread
+        const S* yt = STAGE ? ys + t * Kj * M : prod.y + k0 * M;
+        // step constants: E_k and o_k of step i of this thread
         auto step_E = [&](int i, S (&E)[NN]) {
             if (trans) {
+                if constexpr (STAGE) {
 #pragma unroll
-                for (int q = 0; q < NN; ++q) E[q] = tb[(i * CT + q) * B + t];
+                    for (int q = 0; q < NN; ++q) E[q] = tb[(i * CT + q) * B + t];
+                } else {
+                    const S* r = sa.rows + (k0 + i) * ST::RS + ST::oE;
+#pragma unroll
+                    for (int q = 0; q < NN; ++q) E[q] = __ldg(r + q);
+                }
             } else {
 #pragma unroll
                 for (int q = 0; q < NN; ++q) E[q] = Einf[q];
             }
         };
-        auto step_o = [&](int i, const S (&E)[NN], S (&o)[N]) {
+        auto step_o = [&](int i, S (&o)[N]) {
             if (!trans) {
 #pragma unroll
                 for (int q = 0; q < N; ++q) o[q] = oinf[q];
-            } else if (sa.has_b) {
-                S pb[N];
+            } else if constexpr (STAGE) {
 #pragma unroll
-                for (int q = 0; q < N; ++q) pb[q] = tb[(i * CT + NN + q) * B + t];
-                S eo[N];
-                mat_tvec<N, S>(E, pb, eo);
-#pragma unroll
-                for (int q = 0; q < N; ++q) o[q] = -eo[q];
+                for (int q = 0; q < N; ++q) o[q] = tb[(i * CT + NN + q) * B + t];
             } else {
+                const S* r = sa.rows + (k0 + i) * ST::RS + ST::oO;
 #pragma unroll
-                for (int q = 0; q < N; ++q) o[q] = S(0);
+                for (int q = 0; q < N; ++q) o[q] = __ldg(r + q);
             }
         };
         // v <- E^T v + o + G y_{k+1} - Gr
         auto fstep = [&](int i, const S (&E)[NN], S (&v)[N]) {
             S o[N], nv2[N];
-            step_o(i, E, o);
+            step_o(i, o);
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 S acc = o[a] - prod.p.Gr[a];
 #pragma unroll
-                for (int m = 0; m < M; ++m) acc = fma(prod.p.G[a * M + m], yt[i * M + m], acc);
+                for (int m = 0; m < M; ++m) {
+                    S gc;
+                    if constexpr (HB)
+                        gc = trans ? prod.p.G[a * M + m] + __ldg(sa.mk + (k0 + i) * NN + a * M + m)
+                                   : __ldg(sa.gs + a * M + m);
+                    else
+                        gc = prod.p.G[a * M + m];
+                    acc = fma(gc, yt[i * M + m], acc);
+                }
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc = fma(E[q * N + a], v[q], acc);
                 nv2[a] = acc;
@@ -859,7 +983,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
                 for (int a = 0; a < N; ++a) v[a] = r[a];
             }
         }
-        // forward: g_k = E_k (A^-1 C v_k + A^-1 b) staged; v_{k+1} = E_k^T v_k + o_k + G y - Gr
+        // forward: g_k = E_k (A^-1 C v_k + A^-1 b_k) staged; v_{k+1} = E_k^T v_k + o_k + G y - Gr
 #pragma unroll 1
         for (int i = 0; i < nv; ++i) {
             const long k = k0 + i;
@@ -878,6 +1002,9 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
                 S acc = sa.Aib[a];
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc = fma(sa.AiC[a * N + q], v[q], acc);
+                if constexpr (HB)
+#pragma unroll
+                    for (int m = 0; m < M; ++m) acc = fma(sa.AiBb[a * M + m], yt[i * M + m], acc);
                 u[a] = acc;
             }
             mat_vec<N, S>(E, u, gk);
@@ -1003,20 +1130,22 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             }
         }
         back(x, true);                                 // x_k = E_k x_{k+1} + g_k, in place of g_k
-        __syncthreads();
-        const long base = s0 * N;
-        const long cnt = min((long)B * Kj * N, T * N - base);
-        long done = 0;
-        if ((reinterpret_cast<uintptr_t>(x_out + base) & 15) == 0) {
-            done = cnt * (long)sizeof(S) / 16 * 16 / (long)sizeof(S);
-            if (t == 0 && done > 0) {
-                fence_proxy_async_smem();
-                bulk_copy_s2g(x_out + base, gst, (unsigned)(done * sizeof(S)));
-                bulk_commit_and_wait();
+        if constexpr (STAGE) {
+            __syncthreads();
+            const long base = s0 * N;
+            const long cnt = min((long)B * Kj * N, T * N - base);
+            long done = 0;
+            if ((reinterpret_cast<uintptr_t>(x_out + base) & 15) == 0) {
+                done = cnt * (long)sizeof(S) / 16 * 16 / (long)sizeof(S);
+                if (t == 0 && done > 0) {
+                    fence_proxy_async_smem();
+                    bulk_copy_s2g(x_out + base, gst, (unsigned)(done * sizeof(S)));
+                    bulk_commit_and_wait();
+                }
             }
+            for (long idx = done + t; idx < cnt; idx += B) x_out[base + idx] = gst[idx];
+            __syncthreads();
         }
-        for (long idx = done + t; idx < cnt; idx += B) x_out[base + idx] = gst[idx];
-        __syncthreads();
     }
 }
 

@@ -143,6 +143,42 @@ def test_dense_output(prec, T, nsub):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("disc", ["block", "exact"])
+def test_tiled_scan_and_general_path(prec, disc):
+    """A, C and J of block and exact elements are the same for every interval:
+    the solve takes the tiled scan with per-step tables and the sample's share
+    of the offset (path 1); with per-phase events it takes the general
+    combine path.  Both against the oracle, and the filter output of the
+    tiled scan against the oracle's filter means."""
+    m = model_with_offsets(seed=91)
+    T, dt = 30_000, 0.01
+    _, y = synth.simulate(m, T, dt, seed=92)
+    ref, mf, _ = (oracle.smooth_block(m, y, dt, 10, return_filter=True) if disc == "block"
+                  else oracle.smooth_exact(m, y, dt, return_filter=True))
+    sm = smoother(m, T, dt, prec, disc, substeps=10)
+    yt = torch.tensor(y, dtype=DT[prec], device="cuda")
+    x, f, _ = sm.solve(yt, filt=True)
+    assert sm.path() == 1
+    sm.profile(True)
+    xg = sm.solve(yt).cpu().numpy()
+    assert sm.path() == 3
+    st = sm.stats()
+    assert st[1] == 0 and st[2] == 0
+    sm.close()
+    assert_traj(x.cpu().numpy(), ref, TOL[prec])
+    assert_traj(xg, ref, TOL[prec] if prec == "fp64" else 5e-4)
+    f = f.cpu().numpy().astype(np.float64)
+    n = 4
+    iu = np.triu_indices(n)
+    for k in (0, 1, T // 3, T):
+        S = np.zeros((n, n))
+        S[iu] = f[k, n:]
+        S = S + S.T - np.diag(np.diag(S))
+        mk = np.linalg.solve(S, f[k, :n])
+        assert np.abs(mk - mf[k]).max() <= 100 * TOL[prec] * max(1.0, np.abs(mf[k]).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sequential_block_baseline(prec):
     m = model_with_offsets(seed=61)
     T, dt = 3000, 0.02
@@ -161,6 +197,7 @@ def test_block_full_size_T_2_20_fp32():
     _, y = synth.simulate(m, T, dt, seed=72)
     sm, yt, x, f = solve(m, y, dt, "fp32", "block", filt=True, substeps=nsub)
     xd = sm.dense(yt, x, f).cpu().numpy()
+    assert sm.path() == 1
     sm.close()
     assert_traj(x.cpu().numpy(), oracle.smooth_block(m, y, dt, nsub), TOL["fp32"])
     assert_traj(xd, oracle.dense_block(m, y, dt, nsub), TOL["fp32"])

@@ -381,20 +381,46 @@ def test_two_filter_full_size_matches_rts(prec):
 # ---------------------------------------------------------------- nx = 8 OU
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("T", [1, 17, 3000])
+@pytest.mark.parametrize("T", [1, 17, 3000, 20_000, 70_001])
 def test_ou_nx8(prec, T):
+    """nx = 8 through the tiled scan (tiles before the stationary point read
+    their rows from global memory, g_k and states go through x_out) and, for
+    the shortest horizons, the general path."""
+    from paper_2512_13319_gb300 import MapSmoother
     model = synth.ou_model(8, 4, seed=1001)
     _, y = synth.simulate(model, T, 1e-3, seed=T + 5, substeps=1)
-    x, _ = gpu_solve(model, y, 1e-3, prec)
-    assert_traj(x, oracle.smooth_lti(model, y, 1e-3), TOL[prec])
+    sm = MapSmoother(model, T, 1e-3, precision=prec)
+    x, f, _ = sm.solve(torch.tensor(y, dtype=DT[prec], device="cuda"), filt=True)
+    path, st = sm.path(), sm.stats()
+    sm.close()
+    assert st[1] == 0 and st[2] == 0
+    if T >= 3000 and prec == "fp32":
+        assert path == 1
+    x = x.cpu().numpy()
+    xr, mf, Pf = oracle.smooth_lti(model, y, 1e-3, return_filter=True)
+    assert_traj(x, xr, TOL[prec])
+    # the filter output: S^-1 v and S^-1 are the oracle's filter mean and covariance
+    f = f.cpu().numpy().astype(np.float64)
+    n = 8
+    iu = np.triu_indices(n)
+    for k in (0, T // 2, T):
+        S = np.zeros((n, n))
+        S[iu] = f[k, n:]
+        S = S + S.T - np.diag(np.diag(S))
+        m = np.linalg.solve(S, f[k, :n])
+        assert np.abs(m - mf[k]).max() <= 100 * TOL[prec] * max(1.0, np.abs(mf[k]).max())
 
 
 def test_ou_nx8_full_size_fp32():
     """The second model of the benchmark configuration: OU nx=8, ny=4, T=2^20."""
+    from paper_2512_13319_gb300 import MapSmoother
     model = synth.ou_model(8, 4, seed=1001)
     T, dt = 2 ** 20, 1e-3
     _, y = synth.simulate(model, T, dt, seed=synth.seed_for(1) + 10, substeps=1)
-    x, _ = gpu_solve(model, y, dt, "fp32")
+    sm = MapSmoother(model, T, dt, precision="fp32")
+    x = sm.solve(torch.tensor(y, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert sm.path() == 1
+    sm.close()
     assert_traj(x, oracle.smooth_lti(model, y, dt), TOL["fp32"])
 
 
