@@ -202,6 +202,18 @@ map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, cons
                              int flags, double* dL_dtheta, void* stream);
 
 /*
+ * The Gaussian log-normalisers that the MAP cost of map_smoother_solve
+ * (cost_out) omits, at the handle's current parameters:
+ *   *out = T/2 log det(2 pi C) + T/2 log det(2 pi R / dt),  C = dt q L W L^T,
+ * the per-interval transition covariance of the Euler element (Section 4.2)
+ * and the measurement covariance of a sample over dt.  Their derivative is the
+ * MAP_GRAD_LOGDET share of map_smoother_grad.  Host arithmetic, no device
+ * work.  MAP_ERR_UNSUPPORTED for nonlinear models or other than Euler
+ * elements; MAP_ERR_SINGULAR when C or R is not positive definite.
+ */
+map_status map_smoother_log_normaliser(const map_smoother* h, double* out);
+
+/*
  * Set theta = (F, log q, log r) of the handle (F NULL keeps F) and redo the
  * device set-up (discretisation); synchronises the device.  The plan-time
  * constants of linear time-invariant models (folds, tile tables, tile-map

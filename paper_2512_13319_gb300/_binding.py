@@ -69,6 +69,7 @@ EXPORTS = {
     "map_batch_destroy": (None, [_VP]),
     "map_fma_peak": (_I, [_I, _I, _D, ctypes.POINTER(ctypes.c_float), _VP]),
     "map_smoother_wait_selftest": (_I, [_VP, _I, _VP]),
+    "map_smoother_log_normaliser": (_I, [_VP, _D]),
 }
 
 _lib = None
@@ -179,6 +180,12 @@ def map_smoother_geometry(h):
     K, Bt, nt = _I(), _I(), _I()
     _check(load().map_smoother_geometry(h, ctypes.byref(K), ctypes.byref(Bt), ctypes.byref(nt)), h)
     return K.value, Bt.value, nt.value
+
+
+def map_smoother_log_normaliser(h):
+    out = ctypes.c_double(0.0)
+    _check(load().map_smoother_log_normaliser(h, ctypes.byref(out)), h)
+    return out.value
 
 
 def map_smoother_wait_selftest(h, polls, stream=None):

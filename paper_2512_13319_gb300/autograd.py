@@ -7,9 +7,6 @@ R = e^log_r R of the model the smoother was created with.
 """
 from __future__ import annotations
 
-import math
-
-import numpy as np
 import torch
 
 
@@ -50,11 +47,7 @@ class MapCost(torch.autograd.Function):
         _set_params(smoother, F, log_q, log_r)
         x, _, cost = smoother.solve(y, cost=True)
         if logdet:
-            m = smoother.model
-            dt, T = smoother.dt, smoother.T
-            C = dt * math.exp(float(log_q)) * (m.L @ m.W @ m.L.T)
-            R = math.exp(float(log_r)) * m.R / dt
-            cost += 0.5 * T * (np.linalg.slogdet(2 * math.pi * C)[1] + np.linalg.slogdet(2 * math.pi * R)[1])
+            cost += smoother.log_normaliser()
         ctx.smoother = smoother
         ctx.logdet = logdet
         ctx.save_for_backward(y, x)

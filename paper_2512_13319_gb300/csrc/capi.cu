@@ -470,6 +470,56 @@ map_status map_smoother_grad(map_smoother* h, const void* y, const void* x, cons
     return device_errors(*h);               // the gradient read-back synchronised the stream
 }
 
+namespace {
+// log det of the symmetric positive definite n x n matrix A (row-major) by
+// Cholesky; false when a pivot is not positive
+bool logdet_spd(int n, std::vector<double> A, double* out)
+{
+    double ld = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = A[j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+        if (!(d > 0.0)) return false;
+        const double l = std::sqrt(d);
+        A[j * n + j] = l;
+        ld += 2.0 * std::log(l);
+        for (int i = j + 1; i < n; ++i) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = s / l;
+        }
+    }
+    *out = ld;
+    return true;
+}
+}  // namespace
+
+map_status map_smoother_log_normaliser(const map_smoother* h, double* out)
+{
+    if (!h || !out) return MAP_ERR_INVALID_ARG;
+    map_smoother& hm = const_cast<map_smoother&>(*h);
+    if (h->model != MAP_MODEL_LINEAR || h->disc != MAP_EULER)
+        return fail(hm, MAP_ERR_UNSUPPORTED, "the log-normalisers are those of linear models with Euler elements");
+    const int n = h->N, m = h->M, nw = h->NW;
+    const double twopi = 2.0 * 3.14159265358979323846;
+    std::vector<double> C((size_t)n * n, 0.0), R((size_t)m * m);
+    const double cq = twopi * h->dt * std::exp(h->logq);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < nw; ++a)
+                for (int b = 0; b < nw; ++b) s += h->L[i * nw + a] * h->W[a * nw + b] * h->L[j * nw + b];
+            C[i * n + j] = cq * s;
+        }
+    const double cr = twopi * std::exp(h->logr) / h->dt;
+    for (int i = 0; i < m * m; ++i) R[i] = cr * h->R[i];
+    double lc = 0.0, lr = 0.0;
+    if (!logdet_spd(n, C, &lc)) return fail(hm, MAP_ERR_SINGULAR, "the process noise C = dt Q is not positive definite");
+    if (!logdet_spd(m, R, &lr)) return fail(hm, MAP_ERR_SINGULAR, "R is not positive definite");
+    *out = 0.5 * double(h->T) * (lc + lr);
+    return MAP_OK;
+}
+
 map_status map_smoother_update(map_smoother* h, const double* F, double log_q, double log_r)
 {
     if (!h) { g_create_error = "handle is NULL"; return MAP_ERR_INVALID_ARG; }

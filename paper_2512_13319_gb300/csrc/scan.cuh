@@ -507,22 +507,39 @@ __device__ __forceinline__ void lti_tile_prefix_sum(const LtiTiles<S>& lt, int t
     // most 5 per thread (tile <= 4B + 1): all their operands are loaded first
     // (16-byte loads of the table rows), then multiplied
     constexpr int UMAX = 5;
-    S Qm[UMAX][NN], wv[UMAX][N];
+    if constexpr (N <= 6) {
+        S Qm[UMAX][NN], wv[UMAX][N];
 #pragma unroll
-    for (int u = 0; u < UMAX; ++u) {
-        const int i = t - 1 + u * (int)blockDim.x;
-        const bool on = i < tile;
-        const S* Q = lt.qt + TT::qt_index(tile, on ? i + 1 : 0) * NN;   // Pi(i+1, tile)^T
-        load_run_aligned<NN, S>(Q, Qm[u]);
+        for (int u = 0; u < UMAX; ++u) {
+            const int i = t - 1 + u * (int)blockDim.x;
+            const bool on = i < tile;
+            const S* Q = lt.qt + TT::qt_index(tile, on ? i + 1 : 0) * NN;   // Pi(i+1, tile)^T
+            load_run_aligned<NN, S>(Q, Qm[u]);
 #pragma unroll
-        for (int c = 0; c < N; ++c) wv[u][c] = !on ? S(0) : i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
+            for (int c = 0; c < N; ++c) wv[u][c] = !on ? S(0) : i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
+        }
+#pragma unroll
+        for (int u = 0; u < UMAX; ++u)
+#pragma unroll
+            for (int r = 0; r < N; ++r)
+#pragma unroll
+                for (int c = 0; c < N; ++c) v[r] = fma(Qm[u][r * N + c], wv[u][c], v[r]);
+    } else {
+        // larger matrices: one term at a time (registers)
+#pragma unroll 1
+        for (int u = 0; u < UMAX; ++u) {
+            const int i = t - 1 + u * (int)blockDim.x;
+            if (i >= tile) break;
+            S Qm[NN], wv[N];
+            load_run_aligned<NN, S>(lt.qt + TT::qt_index(tile, i + 1) * NN, Qm);
+#pragma unroll
+            for (int c = 0; c < N; ++c) wv[c] = i < 0 ? prior.v[c] : lt.w[(long)i * N + c];
+#pragma unroll
+            for (int r = 0; r < N; ++r)
+#pragma unroll
+                for (int c = 0; c < N; ++c) v[r] = fma(Qm[r * N + c], wv[c], v[r]);
+        }
     }
-#pragma unroll
-    for (int u = 0; u < UMAX; ++u)
-#pragma unroll
-        for (int r = 0; r < N; ++r)
-#pragma unroll
-            for (int c = 0; c < N; ++c) v[r] = fma(Qm[u][r * N + c], wv[u][c], v[r]);
     block_vec_sum<N, S>(v, red);
     if (t == 0) {
 #pragma unroll
@@ -557,31 +574,55 @@ __device__ __forceinline__ void lti_tile_suffix_sum(const LtiTiles<S>& lt, const
     // terms i = tile + 1 + t + u B (at most 5 per thread: nt <= 4B + 1): all
     // operands loaded first, then multiplied; i = nt - 1 is x_L
     constexpr int UMAX = 5;
-    S Pm[UMAX][NN], uv[UMAX][N];
-#pragma unroll
-    for (int uu = 0; uu < UMAX; ++uu) {
-        const int i = tile + 1 + t + uu * (int)blockDim.x;
-        const bool on = i < nt;
-        load_run_aligned<NN, S>(lt.pi + TT::pi_index(nt, tile + 1, on ? i : tile + 1) * NN, Pm[uu]);
-        if (on && i + 1 == nt) {
+    auto term = [&](int i, S (&u)[N]) {
+        if (i + 1 == nt) {
             Aff<N, S> a;
 #pragma unroll
             for (int c = 0; c < NA; ++c) comp(a, c) = tile_aff[(long)i * NA + c];
             S x[N];
 #pragma unroll
             for (int c = 0; c < N; ++c) x[c] = xT[c];
-            affine_apply<N, S>(a, x, uv[uu]);
+            affine_apply<N, S>(a, x, u);
         } else {
 #pragma unroll
-            for (int c = 0; c < N; ++c) uv[uu][c] = on ? tile_aff[(long)i * NA + NN + c] : S(0);
+            for (int c = 0; c < N; ++c) u[c] = tile_aff[(long)i * NA + NN + c];
+        }
+    };
+    if constexpr (N <= 6) {
+        S Pm[UMAX][NN], uv[UMAX][N];
+#pragma unroll
+        for (int uu = 0; uu < UMAX; ++uu) {
+            const int i = tile + 1 + t + uu * (int)blockDim.x;
+            const bool on = i < nt;
+            load_run_aligned<NN, S>(lt.pi + TT::pi_index(nt, tile + 1, on ? i : tile + 1) * NN, Pm[uu]);
+            if (on) {
+                term(i, uv[uu]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < N; ++c) uv[uu][c] = S(0);
+            }
+        }
+#pragma unroll
+        for (int uu = 0; uu < UMAX; ++uu)
+#pragma unroll
+            for (int r = 0; r < N; ++r)
+#pragma unroll
+                for (int c = 0; c < N; ++c) v[r] = fma(Pm[uu][r * N + c], uv[uu][c], v[r]);
+    } else {
+        // larger matrices: one term at a time (registers)
+#pragma unroll 1
+        for (int uu = 0; uu < UMAX; ++uu) {
+            const int i = tile + 1 + t + uu * (int)blockDim.x;
+            if (i >= nt) break;
+            S Pm[NN], u[N];
+            load_run_aligned<NN, S>(lt.pi + TT::pi_index(nt, tile + 1, i) * NN, Pm);
+            term(i, u);
+#pragma unroll
+            for (int r = 0; r < N; ++r)
+#pragma unroll
+                for (int c = 0; c < N; ++c) v[r] = fma(Pm[r * N + c], u[c], v[r]);
         }
     }
-#pragma unroll
-    for (int uu = 0; uu < UMAX; ++uu)
-#pragma unroll
-        for (int r = 0; r < N; ++r)
-#pragma unroll
-            for (int c = 0; c < N; ++c) v[r] = fma(Pm[uu][r * N + c], uv[uu][c], v[r]);
     block_vec_sum<N, S>(v, red);
     if (t == 0)
 #pragma unroll

@@ -478,7 +478,14 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     S* gsv = reinterpret_cast<S*>(h.d_scan + SB::gs_off());
     char* tiles = h.d_scan + SB::tiles_off();
     const long kr = std::min(kc, KT - 1);
-    k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + kr * N * N, K, B, pw);
+    // the last tile, when after kc: its partial thread tp and that thread's steps
+    const bool last_steady = nt - 1 >= Jt;
+    const long rem = T - g.start(nt - 1);
+    const int tp = (int)std::min<long>(B, rem / K), nvp = tp < B ? (int)(rem - (long)tp * K) : 0;
+    S* taff = reinterpret_cast<S*>(h.d_scan + SB::taff_off());
+    k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + kr * N * N, K, B, pw, tp, nvp,
+                                          reinterpret_cast<S*>(h.d_scan + SB::ep_off()),
+                                          last_steady ? taff + (long)(nt - 1) * (N * N + N) : nullptr);
     if (Jt > 0 && ScanSmem<N, M, S>::STAGE) {
         const long cnt = (long)Jt * B * Kt * SB::CT;
         k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(rows, KT, g, ttab);
@@ -584,6 +591,7 @@ map_status run_scan(map_smoother& h, const LtiProducer<N, M, S>& prod, S* x_out,
     sa.w = reinterpret_cast<S*>(h.d_scan + SB::w_off());
     sa.taff = reinterpret_cast<S*>(h.d_scan + SB::taff_off());
     sa.gs = reinterpret_cast<const S*>(h.d_scan + SB::gs_off());
+    sa.ep = reinterpret_cast<const S*>(h.d_scan + SB::ep_off());
     const char* tiles = h.d_scan + SB::tiles_off();
     sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));
     sa.qt = reinterpret_cast<const S*>(tiles + TT::qt_off(snt));

@@ -455,8 +455,8 @@ struct ScanGeom {
 // of their shared-memory copy (component c of step i of thread t at
 // (i CT + c) B + t), the tiles' offsets w_j and RTS maps, the measurement
 // gain of the steps after kc (G, plus -E^T P Bb when the offset depends on the
-// sample), then the tile tables of lti_fold.cuh (TileTables: F_j = E_j^T and
-// the products Pi).
+// sample), the partial thread's map E_inf^nv of the last tile, then the tile
+// tables of lti_fold.cuh (TileTables: F_j = E_j^T and the products Pi).
 template <int N, int M, typename S>
 struct ScanBuf {
     static constexpr int NN = N * N, BMAX = 128, NTMAX = 4 * BMAX + 1;
@@ -470,7 +470,8 @@ struct ScanBuf {
     __host__ __device__ static constexpr size_t w_off() { return al(ttab_off() + sizeof(S) * jt_max() * ttab_tile()); }
     __host__ __device__ static constexpr size_t taff_off() { return al(w_off() + sizeof(S) * NTMAX * N); }
     __host__ __device__ static constexpr size_t gs_off() { return al(taff_off() + sizeof(S) * NTMAX * (NN + N)); }
-    __host__ __device__ static constexpr size_t tiles_off() { return al(gs_off() + sizeof(S) * N * M); }
+    __host__ __device__ static constexpr size_t ep_off() { return al(gs_off() + sizeof(S) * N * M); }
+    __host__ __device__ static constexpr size_t tiles_off() { return al(ep_off() + sizeof(S) * NN); }
     __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::bytes(NTMAX); }
 };
 
@@ -492,9 +493,14 @@ __device__ inline void wmul(const double* a, const double* b, double* c)
 
 // Phi_inf = E_kc^K (FP64, warp 0, binary powers), then Phi_inf^d for
 // d = 0..B by doubling levels (Phi^d = Phi^(d - 2^l) Phi^(2^l), all d of a
-// level at once), written in S.  One CTA of 256 threads.
+// level at once), written in S.  Then the last tile's maps when it lies after
+// kc: its thread tp holds the last nvp < K steps (threads after it none), so
+// the state at thread tp's start is Ep x_T + beta_tp with Ep = E_kc^nvp, and
+// the tile's RTS map matrix is Phi_inf^tp Ep (the matrix part of its entry in
+// the tile RTS maps; the kernel adds the offset).  One CTA of 256 threads.
 template <int N, typename S>
-__global__ void __launch_bounds__(256) k_scan_powers(const double* __restrict__ e_kc, int K, int B, S* __restrict__ pw)
+__global__ void __launch_bounds__(256) k_scan_powers(const double* __restrict__ e_kc, int K, int B, S* __restrict__ pw,
+                                                     int tp, int nvp, S* __restrict__ ep, S* __restrict__ taff_last)
 {
     namespace pd = scan_plan_detail;
     constexpr int NN = N * N;
@@ -538,6 +544,30 @@ __global__ void __launch_bounds__(256) k_scan_powers(const double* __restrict__ 
         __syncthreads();
     }
     for (int e = t; e < (B + 1) * NN; e += blockDim.x) pw[e] = S(W[e / NN][e % NN]);
+    if (t < 32 && taff_last) {
+        for (int q = t; q < NN; q += 32) {
+            X[q] = __ldg(e_kc + q);
+            Y[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+        }
+        __syncwarp();
+        for (int e = nvp; e > 0; e >>= 1) {
+            if (e & 1) {
+                pd::wmul<N>(Y, X, Z);
+                for (int q = t; q < NN; q += 32) Y[q] = Z[q];
+                __syncwarp();
+            }
+            if (e > 1) {
+                pd::wmul<N>(X, X, Z);
+                for (int q = t; q < NN; q += 32) X[q] = Z[q];
+                __syncwarp();
+            }
+        }
+        pd::wmul<N>(W[tp], Y, Z);
+        for (int q = t; q < NN; q += 32) {
+            ep[q] = S(Y[q]);
+            taff_last[q] = S(Z[q]);
+        }
+    }
 }
 
 // Tile maps E_j (the composition of a tile's per-step closed-loop maps) as
@@ -619,6 +649,7 @@ struct ScanArgs {
     const S* pdummy;        // a readable P_j table for the tile-prefix helper (its P is not used)
     const S* gs;            // measurement gain of the steps after kc (with the sample's share of o)
     const S* mk;            // per-step -E_k^T P_k Bb (steps before kc; offsets depending on the sample)
+    const S* ep;            // E_inf^nv of the last tile's partial thread
     ScanGeom g;
     int has_b;              // b != 0: the A^-1 b term of g_k
     S AiC[N * N];           // A^-1 C
@@ -740,12 +771,15 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         const int tile = blockIdx.x;
         const bool trans = tile < g.Jt;                    // before kc: K_t steps, tabulated E_k
         const bool last = tile + 1 == g.nt;
-        const bool powers = !trans && !last;               // in-tile scans on offsets with Phi_inf^d
+        const bool powers = !trans;                        // in-tile scans on offsets with Phi_inf^d
         const int Kj = g.steps(tile);
         const long s0 = g.start(tile);
         const long k0 = s0 + (long)t * Kj;
         const long T = prod.T;
         const int nv = (int)max(0L, min((long)Kj, T - k0));
+        // the first thread with fewer than Kj steps (B: none); in the last tile
+        // the threads after it have none
+        const int tp = last ? (int)min((long)B, (T - s0) / Kj) : B;
         S* red = sm;
         S* wt = sm + SM::wt(B);
         S* ys = sm + SM::ys(B);
@@ -1047,10 +1081,16 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         S Be[N];                                       // exclusive in-tile RTS suffix offset (powers path)
         Aff<N, S> Rm;                                  // RTS map (full-map path)
         if (powers) {
-            // warp-inclusive suffix: B_l <- B_l + Phi^d B_{l+d}
+            // warp-inclusive suffix: B_l <- B_l + Phi^d B_{l+d} over the
+            // threads before tp (the partial thread of the last tile enters
+            // through its start state, below)
             S Bs[N];
 #pragma unroll
-            for (int a = 0; a < N; ++a) Bs[a] = beta[a];
+            for (int a = 0; a < N; ++a) Bs[a] = t < tp ? beta[a] : S(0);
+            S* bp = wt + 2 * (B / 32) * N + N;         // beta of thread tp
+            if (t == tp)
+#pragma unroll
+                for (int a = 0; a < N; ++a) bp[a] = beta[a];
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 S o[N], p[N];
@@ -1088,6 +1128,12 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
                 Be[a] = lane == 31 ? BN[a] : dn;
             }
             if (t == 0) {
+                if (tp < B) {                          // + Phi_inf^tp beta_tp
+                    S p[N];
+                    mat_vec<N, S>(tb + tp * NN, bp, p);
+#pragma unroll
+                    for (int a = 0; a < N; ++a) Bs[a] += p[a];
+                }
 #pragma unroll
                 for (int a = 0; a < N; ++a) sa.taff[(long)tile * NA + NN + a] = Bs[a];
             }
@@ -1119,12 +1165,30 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             S* xe_sh = red + (B / 32) * (NA + N);
             lti_tile_suffix_sum<N, S>(lt, sa.taff, tile, g.nt, xT, red, xe_sh);
             if (powers) {
+                // state at thread tp's start (tp = B: the tile's end state)
+                S* xs = wt + 2 * (B / 32) * N;
+                if (tp < B) {
+                    if (t == 0) {
+                        const S* bp = wt + 2 * (B / 32) * N + N;
+                        S Ep[NN], xv[N], p[N];
+#pragma unroll
+                        for (int q = 0; q < NN; ++q) Ep[q] = __ldg(sa.ep + q);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) xv[a] = xe_sh[a];
+                        mat_vec<N, S>(Ep, xv, p);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) xs[a] = p[a] + bp[a];
+                    }
+                    __syncthreads();
+                } else {
+                    xs = xe_sh;
+                }
                 S xe[N], p[N];
 #pragma unroll
-                for (int a = 0; a < N; ++a) xe[a] = xe_sh[a];
-                mat_vec<N, S>(tb + (B - 1 - t) * NN, xe, p);
+                for (int a = 0; a < N; ++a) xe[a] = xs[a];
+                mat_vec<N, S>(tb + (tp - 1 - min(t, tp - 1)) * NN, xe, p);
 #pragma unroll
-                for (int a = 0; a < N; ++a) x[a] = p[a] + Be[a];
+                for (int a = 0; a < N; ++a) x[a] = t < tp ? p[a] + Be[a] : xe_sh[a];
             } else {
                 block_aff_end_states<N, S>(Rm, xe_sh, red, x);
             }

@@ -107,6 +107,11 @@ class MapSmoother:
                                    self.nx * self.nx + 2, B.MAP_GRAD_LOGDET if logdet else 0,
                                    self._stream(stream))
 
+    def log_normaliser(self):
+        """T/2 log det(2 pi C) + T/2 log det(2 pi R/dt) at the current parameters
+        (the constants the MAP cost of ``solve(cost=True)`` omits)."""
+        return B.map_smoother_log_normaliser(self._h)
+
     def update(self, F=None, log_q=0.0, log_r=0.0):
         """Set theta = (F, log q, log r) (Q = e^log_q L W L^T, R = e^log_r R)."""
         B.map_smoother_update(self._h, F, log_q, log_r)

@@ -104,6 +104,27 @@ def test_log_normaliser_flag_matches_oracle():
     assert_grad(g, ref, 1e-8)
 
 
+def test_log_normaliser_value():
+    """The C ABI's log-normaliser is -T (log N(0; 0, dt Q) + log N(0; 0, R/dt))
+    (scipy's Gaussian log density at its mean), and an update of (log q, log r)
+    moves it by T/2 (nx d log q + ny d log r)."""
+    from scipy.stats import multivariate_normal
+    from paper_2512_13319_gb300 import MapSmoother
+    T, dt = 1000, 1e-2
+    model, _, _ = problem(T, dt, seed=63)
+    sm = MapSmoother(model, T, dt, precision="fp64")
+    C = dt * model.L @ model.W @ model.L.T
+    Rd = model.R / dt
+    ref = -T * (multivariate_normal(np.zeros(model.nx), C).logpdf(np.zeros(model.nx))
+                + multivariate_normal(np.zeros(model.ny), Rd).logpdf(np.zeros(model.ny)))
+    v0 = sm.log_normaliser()
+    assert abs(v0 - ref) <= 1e-10 * abs(ref)
+    sm.update(model.F, 0.3, -0.2)
+    v1 = sm.log_normaliser()
+    assert abs((v1 - v0) - 0.5 * T * (model.nx * 0.3 - model.ny * 0.2)) <= 1e-9 * abs(ref)
+    sm.close()
+
+
 def test_gradient_against_central_differences_on_the_gpu():
     """FP64 GPU solves at theta +- h (h = 1e-6) against the adjoint gradient."""
     from paper_2512_13319_gb300 import MapSmoother
