@@ -471,7 +471,6 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     const ScanGeom g{B, K, Kt, Jt, nt};
     const S* rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off());
     const double* e64 = reinterpret_cast<const double*>(h.d_tab + ST::e64_off(KT));
-    const double* phit64 = reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(KT));
     const S* mk = reinterpret_cast<const S*>(h.d_tab + ST::mk_off(KT));
     S* pw = reinterpret_cast<S*>(h.d_scan + SB::pw_off());
     S* ttab = reinterpret_cast<S*>(h.d_scan + SB::ttab_off());
@@ -491,7 +490,8 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
         k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(rows, KT, g, ttab);
     }
     k_scan_gs<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, S>(h), mk + kr * N * N, HB ? 1 : 0, gsv);
-    k_scan_tilemaps<N, M, S><<<(nt + 3) / 4, 128, 0, st>>>(phit64, g, pw, tiles);
+    k_scan_tilemaps<N, M, S><<<(unsigned)(((long)nt * N * N + 127) / 128), 128, 0, st>>>(
+        reinterpret_cast<const double*>(h.d_tab + ST::tmap_off()), g, pw, tiles);
     const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;
     k_lti_segments<N, M, S><<<(nt + 127) / 128, 128, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
     k_lti_products<N, M, S><<<dim3((segs + 7) / 8, (nt + 3) / 4), 32, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
@@ -549,9 +549,12 @@ map_status table_plan(map_smoother& h, cudaStream_t st)
     unsigned long long meta[2] = {0, 0};
     cudaError_t e;
     if ((e = cudaMemsetAsync(h.d_tab, 0, sizeof(meta), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-    k_step_powers<N, M><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), prior_of<N, double>(h), h.T, KT, h.d_tab);
+    k_step_powers<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, double>(h), prior_of<N, double>(h), h.T, KT, h.d_tab);
+    k_step_small<N, S><<<ST::SMALL / 4, 128, 0, st>>>(h.d_tab);
+    const long nb = ST::base_count(KT);
+    k_step_base<N, S><<<(unsigned)((nb + 3) / 4), 128, 0, st>>>(prior_of<N, double>(h), KT, h.d_tab);
     k_lti_steptab<N, M, S><<<(unsigned)((KT + 127) / 128), 128, 0, st>>>(
-        lti_params<N, M, double>(h), prior_of<N, double>(h), KT, check, tol, sample_offset<N, M>(h), h.d_tab);
+        lti_params<N, M, double>(h), KT, check, tol, sample_offset<N, M>(h), h.d_tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "step table kernel launch");
     if ((e = cudaMemcpyAsync(meta, h.d_tab, sizeof(meta), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)

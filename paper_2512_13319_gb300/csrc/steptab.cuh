@@ -57,11 +57,12 @@ namespace mapk {
 
 // Layout of the step-table buffer (offsets in bytes): a few counters, the
 // FP64 element powers e^(2^l) (A, C, J as full N x N matrices; l < LPOW),
-// the FP64 P_T of the last step, then per step k < KT: the row in the solve's
+// the FP64 P_T of the last step, the FP64 e^i (i < SMALL) and
+// P_{SMALL j}, the FP64 maps of the tiles before kc, then per step k < KT: the row in the solve's
 // precision S (E, o, mb, P b, P packed), E in FP64 and, for elements whose
 // offset b depends on the held sample (b_k = Bb y_k + b0), -E_k^T P_k Bb
 // (N x M in an N x N slot); and for the thread starts k = g K_t < KT the
-// K_t-step maps Phi_g in S and in FP64.
+// K_t-step maps Phi_g in S.
 template <int N, typename S>
 struct StepTab {
     static constexpr int NN = N * N, NS = Sym<N>::SZ;
@@ -75,22 +76,25 @@ struct StepTab {
     __host__ __device__ static constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
     __host__ __device__ static constexpr size_t pow_off() { return 256; }
     __host__ __device__ static constexpr size_t pref_off() { return al(pow_off() + sizeof(double) * LPOW * 3 * NN); }
-    __host__ __device__ static constexpr size_t rows_off() { return al(pref_off() + sizeof(double) * NN); }
+    // e^i (i < SMALL) as full (A, C, J), and P_{SMALL j} (j <= cap / SMALL)
+    static constexpr int SMALL = 64;
+    __host__ __device__ static constexpr size_t small_off() { return al(pref_off() + sizeof(double) * NN); }
+    __host__ __device__ static constexpr size_t base_off() { return al(small_off() + sizeof(double) * SMALL * 3 * NN); }
+    __host__ __device__ static constexpr long base_count(long kt) { return kt / SMALL + 1; }
+    // FP64 maps of the tiles before kc (tiles of 128 threads x K_t steps)
+    static constexpr int TILE_STEPS = 128 * KT_STEPS;
+    __host__ __device__ static constexpr size_t tmap_off() { return al(base_off() + sizeof(double) * base_count(cap()) * NN); }
+    __host__ __device__ static constexpr long tmap_count(long kt) { return kt / TILE_STEPS + 1; }
+    __host__ __device__ static constexpr size_t rows_off() { return al(tmap_off() + sizeof(double) * tmap_count(cap()) * NN); }
     __host__ __device__ static constexpr size_t e64_off(long kt) { return al(rows_off() + sizeof(S) * kt * RS); }
     __host__ __device__ static constexpr size_t mk_off(long kt) { return al(e64_off(kt) + sizeof(double) * kt * NN); }
     __host__ __device__ static constexpr long phit_count(long kt) { return kt / KT_STEPS + 1; }
     __host__ __device__ static constexpr size_t phit_off(long kt) { return al(mk_off(kt) + sizeof(S) * kt * NN); }
-    __host__ __device__ static constexpr size_t phit64_off(long kt)
-    {
-        return al(phit_off(kt) + sizeof(S) * phit_count(kt) * NN);
-    }
-    __host__ __device__ static constexpr size_t bytes(long kt)
-    {
-        return phit64_off(kt) + sizeof(double) * phit_count(kt) * NN;
-    }
+    __host__ __device__ static constexpr size_t bytes(long kt) { return phit_off(kt) + sizeof(S) * phit_count(kt) * NN; }
     // table length cap: the FP32 table converges within 2^-25 earlier
     __host__ __device__ static constexpr long cap() { return sizeof(S) == 4 ? 16384 : 32768; }
     __host__ __device__ static constexpr int log2_kt() { return KT_STEPS >= 4 ? 2 : KT_STEPS == 2 ? 1 : 0; }
+    __host__ __device__ static constexpr int log2_tile() { return 7 + log2_kt(); }
 };
 
 namespace steptab_detail {
@@ -151,6 +155,9 @@ __device__ __forceinline__ bool zfactor(const double (&P)[N * N], const double (
         }
     ok = chol<N>(G, R) && ok;
     // forward substitution R Z = L^T, column by column
+    double ir[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) ir[i] = 1.0 / R[i * N + i];
 #pragma unroll
     for (int c = 0; c < N; ++c)
 #pragma unroll
@@ -158,7 +165,7 @@ __device__ __forceinline__ bool zfactor(const double (&P)[N * N], const double (
             double s = L[c * N + i];              // (L^T)[i][c]
 #pragma unroll
             for (int k = 0; k < i; ++k) s = fma(-R[i * N + k], Z[k * N + c], s);
-            Z[i * N + c] = s / R[i * N + i];
+            Z[i * N + c] = s * ir[i];
         }
     return ok;
 }
@@ -243,48 +250,122 @@ __device__ __forceinline__ bool fold_map(const double* __restrict__ f, const dou
 
 }  // namespace steptab_detail
 
+// Per-warp shared scratch of the plan-time element kernels (fold_warp helpers:
+// lane l holds entries l, l + 32, ... of each small FP64 matrix)
+template <int N>
+struct PowWk {
+    double A[N * N], C[N * N], J[N * N], X[N * N], Y[N * N], Z[N * N], W[N * N], T1[N * N], T2[N * N],
+        T3[N * N], P[N * N], wk[4 * N * N];
+};
+
+// e (x) e of a data-free element (A, C, J), in place (one warp)
+template <int N>
+__device__ inline void warp_double(PowWk<N>& w)
+{
+    namespace fw = fold_warp;
+    constexpr int NN = N * N;
+    fw::pair_coeffs<N>(w.A, w.C, w.A, w.J, w.X, w.Y, w.Z, w.W, w.wk);
+    fw::pair_acj<N>(w.A, w.J, w.A, w.C, w.X, w.Y, w.W, w.T1, w.T2, w.T3);
+    for (int q = fw::lane(); q < NN; q += 32) { w.A[q] = w.T1[q]; w.C[q] = w.T2[q]; w.J[q] = w.T3[q]; }
+    __syncwarp();
+}
+
 // Element powers e^(2^l) of the data-free interval element e = (A, C, J)
-// (Eq. 36 combine of an element with itself, FP64 with row-pivoted inverses),
-// for every l with 2^l <= max(T, KT), and P_T, the value function after all T
-// steps (the powers of the set bits of T applied to P_0; powers of one element
-// commute).  One thread.
-template <int N, int M>
+// (Eq. 36 combine of an element with itself), for every l with
+// 2^l <= max(T, KT), and P_T, the value function after all T steps (the
+// powers of the set bits of T applied to P_0; powers of one element commute).
+// One warp, lane-parallel FP64 (the doublings are a chain in series).
+template <int N, int M, typename S>
 __global__ void __launch_bounds__(32)
 k_step_powers(const LtiParams<N, M, double> p, const Red<N, double> prior, long T, long KT, char* __restrict__ tab)
 {
-    using ST = StepTab<N, float>;
+    namespace fw = fold_warp;
+    using ST = StepTab<N, S>;
     constexpr int NN = N * N;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ PowWk<N> w;
+    const int l0 = threadIdx.x;
     double* pw = reinterpret_cast<double*>(tab + ST::pow_off());
-    const CombineCtx ctx{0.0f, nullptr};          // every inverse by the FP64 row-pivoted path
-    Elem<N, double> e;
-#pragma unroll
-    for (int q = 0; q < NN; ++q) e.A[q] = p.A[q];
-#pragma unroll
-    for (int q = 0; q < Sym<N>::SZ; ++q) { e.C[q] = p.C[q]; e.J[q] = p.J[q]; }
-#pragma unroll
-    for (int q = 0; q < N; ++q) { e.b[q] = 0.0; e.eta[q] = 0.0; }
-    Red<N, double> X = prior;
+    for (int q = l0; q < NN; q += 32) {
+        const int a = q / N, c = q % N;
+        w.A[q] = p.A[q];
+        w.C[q] = p.C[Sym<N>::at(a, c)];
+        w.J[q] = p.J[Sym<N>::at(a, c)];
+        w.P[q] = prior.P[Sym<N>::at(a, c)];
+    }
+    __syncwarp();
     const long top = T > KT ? T : KT;
 #pragma unroll 1
     for (int l = 0; l < ST::LPOW && (1L << l) <= top; ++l) {
-        double* w = pw + (long)l * 3 * NN;
-#pragma unroll
-        for (int q = 0; q < NN; ++q) {
-            const int a = q / N, c = q % N;
-            w[q] = e.A[q];
-            w[NN + q] = e.C[Sym<N>::at(a, c)];
-            w[2 * NN + q] = e.J[Sym<N>::at(a, c)];
-        }
-        if ((T >> l) & 1) apply<N, double, false>(e, X, nullptr, nullptr, ctx);
-        combine<N, double>(e, e, e, ctx);
+        double* o = pw + (long)l * 3 * NN;
+        for (int q = l0; q < NN; q += 32) { o[q] = w.A[q]; o[NN + q] = w.C[q]; o[2 * NN + q] = w.J[q]; }
+        if ((T >> l) & 1) fw::riccati<N>(w.A, w.C, w.J, w.P, w.wk);
+        warp_double<N>(w);
     }
     double* pr = reinterpret_cast<double*>(tab + ST::pref_off());
-#pragma unroll
-    for (int q = 0; q < NN; ++q) {
-        const int a = q / N, c = q % N;
-        pr[q] = X.P[Sym<N>::at(a, c)];
+    for (int q = l0; q < NN; q += 32) pr[q] = w.P[q];
+}
+
+// e^i for i < SMALL (the combination of the powers of the set bits of i;
+// e^0 is the neutral element A = I, C = J = 0), one warp each
+template <int N, typename S>
+__global__ void __launch_bounds__(128) k_step_small(char* __restrict__ tab)
+{
+    namespace fw = fold_warp;
+    using ST = StepTab<N, S>;
+    constexpr int NN = N * N;
+    __shared__ PowWk<N> wks[4];
+    PowWk<N>& w = wks[threadIdx.x >> 5];
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), l0 = fw::lane();
+    if (i >= ST::SMALL) return;
+    const double* pw = reinterpret_cast<const double*>(tab + ST::pow_off());
+    for (int q = l0; q < NN; q += 32) {
+        w.A[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+        w.C[q] = 0.0;
+        w.J[q] = 0.0;
     }
+    __syncwarp();
+#pragma unroll 1
+    for (int l = 0; (i >> l) != 0; ++l) {
+        if (!((i >> l) & 1)) continue;
+        const double* u = pw + (long)l * 3 * NN;           // e^(2^l), the later operand
+        for (int q = l0; q < NN; q += 32) { w.T1[q] = u[q]; w.T2[q] = u[NN + q]; w.T3[q] = u[2 * NN + q]; }
+        __syncwarp();
+        fw::pair_coeffs<N>(w.T1, w.T2, w.A, w.J, w.X, w.Y, w.Z, w.W, w.wk);
+        fw::pair_acj<N>(w.T1, w.T3, w.A, w.C, w.X, w.Y, w.W, w.P, w.Z, w.wk);
+        for (int q = l0; q < NN; q += 32) { w.A[q] = w.P[q]; w.C[q] = w.Z[q]; w.J[q] = w.wk[q]; }
+        __syncwarp();
+    }
+    double* o = reinterpret_cast<double*>(tab + ST::small_off()) + (long)i * 3 * NN;
+    for (int q = l0; q < NN; q += 32) { o[q] = w.A[q]; o[NN + q] = w.C[q]; o[2 * NN + q] = w.J[q]; }
+}
+
+// P_{SMALL j} for j <= (KT - 1) / SMALL: the powers of the set bits of SMALL j
+// applied to P_0, one warp each
+template <int N, typename S>
+__global__ void __launch_bounds__(128) k_step_base(const Red<N, double> prior, long KT, char* __restrict__ tab)
+{
+    namespace fw = fold_warp;
+    using ST = StepTab<N, S>;
+    constexpr int NN = N * N;
+    __shared__ PowWk<N> wks[4];
+    PowWk<N>& w = wks[threadIdx.x >> 5];
+    const long j = (long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int l0 = fw::lane();
+    if (j * ST::SMALL >= KT) return;
+    const double* pw = reinterpret_cast<const double*>(tab + ST::pow_off());
+    for (int q = l0; q < NN; q += 32) w.P[q] = prior.P[Sym<N>::at(q / N, q % N)];
+    __syncwarp();
+    const long k = j * ST::SMALL;
+#pragma unroll 1
+    for (int l = 0; (k >> l) != 0; ++l)
+        if ((k >> l) & 1) {
+            const double* u = pw + (long)l * 3 * NN;
+            for (int q = l0; q < NN; q += 32) { w.A[q] = u[q]; w.C[q] = u[NN + q]; w.J[q] = u[2 * NN + q]; }
+            __syncwarp();
+            fw::riccati<N>(w.A, w.C, w.J, w.P, w.wk);
+        }
+    double* o = reinterpret_cast<double*>(tab + ST::base_off()) + j * NN;
+    for (int q = l0; q < NN; q += 32) o[q] = w.P[q];
 }
 
 // Optional held-sample dependence of the element offset: b_k = Bb y_k + b0
@@ -295,17 +376,18 @@ struct SampleOffset {
     double Bb[N * M];
 };
 
-// One thread per tabulated step k < KT (FP64): P_k from the element powers
-// (the set bits of k applied to P_0), then the row of constants, -E_k^T P_k Bb
+// One thread per tabulated step k < KT (FP64): P_k = e^(k mod SMALL) applied
+// to P_{SMALL floor(k / SMALL)}, then the row of constants, -E_k^T P_k Bb
 // when the offset depends on the sample, and for the first step of a thread of
 // K_t steps (k = g K_t) the thread's composite closed-loop map
 // Phi_g = (I + C_Kt P_k)^-1 A_Kt of the K_t-step element e^(K_t) (the
 // composition of its K_t per-step maps: the closed-loop map of the combined
-// element).  With check, every step whose P_k differs from P_T beyond tol
+// element), and likewise for the first step of a tile of 128 x K_t steps the
+// tile's map.  With check, every step whose P_k differs from P_T beyond tol
 // raises meta[0] to k + 1; meta[1] counts non-positive Cholesky pivots.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(128)
-k_lti_steptab(const LtiParams<N, M, double> p, const Red<N, double> prior, long KT, int check, double tol,
+k_lti_steptab(const LtiParams<N, M, double> p, long KT, int check, double tol,
               const SampleOffset<N, M> so, char* __restrict__ tab)
 {
     namespace sd = steptab_detail;
@@ -318,15 +400,10 @@ k_lti_steptab(const LtiParams<N, M, double> p, const Red<N, double> prior, long 
     S* row = reinterpret_cast<S*>(tab + ST::rows_off()) + k * ST::RS;
     double* e64 = reinterpret_cast<double*>(tab + ST::e64_off(KT)) + k * NN;
     double P[NN];
-#pragma unroll
-    for (int q = 0; q < NN; ++q) {
-        const int a = q / N, c = q % N;
-        P[q] = prior.P[Sym<N>::at(a, c)];
-    }
+    sd::load_full<N>(reinterpret_cast<const double*>(tab + ST::base_off()) + (k / ST::SMALL) * NN, P);
     bool ok = true;
-#pragma unroll 1
-    for (int l = 0; (k >> l) != 0; ++l)
-        if ((k >> l) & 1) ok = sd::apply_p<N>(pw + (long)l * 3 * NN, P) && ok;
+    if (k % ST::SMALL)
+        ok = sd::apply_p<N>(reinterpret_cast<const double*>(tab + ST::small_off()) + (k % ST::SMALL) * 3 * NN, P);
     // per-step constants from Z of (P, C): E = A - C Z^T (Z A), mb = b - C Z^T (Z b)
     double A[NN], C[NN], b[N], Z[NN], ZA[NN], CZt[NN];
 #pragma unroll
@@ -410,16 +487,19 @@ k_lti_steptab(const LtiParams<N, M, double> p, const Red<N, double> prior, long 
                 mk[a * M + c] = S(acc);
             }
     }
+    if (k % ST::TILE_STEPS == 0) {
+        double Tm[NN];
+        ok = sd::fold_map<N>(pw + (long)ST::log2_tile() * 3 * NN, P, Tm) && ok;
+        double* tm = reinterpret_cast<double*>(tab + ST::tmap_off()) + (k / ST::TILE_STEPS) * NN;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) tm[q] = Tm[q];
+    }
     if (k % Kt == 0) {
         double Ph[NN];
         ok = sd::fold_map<N>(pw + (long)ST::log2_kt() * 3 * NN, P, Ph) && ok;
         S* ph = reinterpret_cast<S*>(tab + ST::phit_off(KT)) + (k / Kt) * NN;
-        double* ph64 = reinterpret_cast<double*>(tab + ST::phit64_off(KT)) + (k / Kt) * NN;
 #pragma unroll
-        for (int q = 0; q < NN; ++q) {
-            ph[q] = S(Ph[q]);
-            ph64[q] = Ph[q];
-        }
+        for (int q = 0; q < NN; ++q) ph[q] = S(Ph[q]);
     }
     if (check) {
         double Pr[NN];
@@ -571,39 +651,21 @@ __global__ void __launch_bounds__(256) k_scan_powers(const double* __restrict__ 
 }
 
 // Tile maps E_j (the composition of a tile's per-step closed-loop maps) as
-// F_j = E_j^T in the tile tables: a tile before kc multiplies the FP64 maps of
-// its B threads (one warp per tile, lanes over the entries), a later tile
-// takes Phi_inf^B.  The last tile's map is not used by the tile products.
+// F_j = E_j^T in the tile tables: a tile before kc takes the closed-loop map
+// of the element of its 128 K_t steps at its first step (the step tables'
+// tile maps), a later tile Phi_inf^B.  The last tile's map is not used by the
+// tile products.  One thread per entry.
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(128)
-k_scan_tilemaps(const double* __restrict__ phit64, ScanGeom g, const S* __restrict__ pw, char* __restrict__ tiles)
+k_scan_tilemaps(const double* __restrict__ tmap64, ScanGeom g, const S* __restrict__ pw, char* __restrict__ tiles)
 {
-    namespace pd = scan_plan_detail;
     using TT = TileTables<N, M, S>;
     constexpr int NN = N * N;
-    __shared__ double Wk[4][3][NN];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int j = blockIdx.x * 4 + w;
-    if (j >= g.nt) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)g.nt * NN) return;
+    const int j = (int)(e / NN), q = (int)(e % NN), qt = (q % N) * N + q / N;
     S* F = reinterpret_cast<S*>(tiles + TT::f_off(g.nt)) + (long)j * NN;
-    if (j >= g.Jt || j == g.nt - 1) {
-        const S* P = pw + (long)g.B * NN;
-        for (int q = l; q < NN; q += 32) F[q] = P[(q % N) * N + q / N];
-        return;
-    }
-    double* acc = Wk[w][0];
-    double* nxt = Wk[w][1];
-    double* tmp = Wk[w][2];
-    for (int q = l; q < NN; q += 32) acc[q] = __ldg(phit64 + ((long)j * g.B) * NN + q);
-    __syncwarp();
-    for (int t = 1; t < g.B; ++t) {
-        for (int q = l; q < NN; q += 32) nxt[q] = __ldg(phit64 + ((long)j * g.B + t) * NN + q);
-        __syncwarp();
-        pd::wmul<N>(acc, nxt, tmp);
-        for (int q = l; q < NN; q += 32) acc[q] = tmp[q];
-        __syncwarp();
-    }
-    for (int q = l; q < NN; q += 32) F[q] = S(acc[(q % N) * N + q / N]);
+    F[q] = j >= g.Jt || j == g.nt - 1 ? pw[(long)g.B * NN + qt] : S(__ldg(tmap64 + (long)j * NN + qt));
 }
 
 // Per-step E_k and o_k of the tiles before kc, in the order of their
