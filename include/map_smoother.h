@@ -109,6 +109,7 @@ typedef struct {
                                    condition estimate of (I + C J) exceeds this (0 = 1e6) */
     int tile_threads;           /* threads per tile CTA: 32, 64 or 128 (0 = 128, reduced to fit) */
     int substeps;               /* MAP_BLOCK_EULER: Euler substeps per interval, 1..64 (0 = 10) */
+    int steps_per_thread;       /* K of the scans, 1..64 (0 = chosen for whole waves of CTAs) */
 } map_problem_desc;
 
 /*

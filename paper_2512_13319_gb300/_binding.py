@@ -35,7 +35,7 @@ class map_problem_desc(ctypes.Structure):
         ("m0", _D), ("P0", _D), ("gamma", ctypes.c_double),
         ("precision", ctypes.c_int), ("discretisation", ctypes.c_int), ("smoother", ctypes.c_int),
         ("gn_iters", ctypes.c_int), ("cond_max", ctypes.c_double), ("tile_threads", ctypes.c_int),
-        ("substeps", ctypes.c_int),
+        ("substeps", ctypes.c_int), ("steps_per_thread", ctypes.c_int),
     ]
 
 
@@ -246,7 +246,7 @@ _MODEL_KIND = {"linear": MAP_MODEL_LINEAR, "coord_turn": MAP_MODEL_COORD_TURN, "
 
 
 def make_desc(model, T, dt, precision=MAP_FP32, discretisation=MAP_EULER, smoother=MAP_RTS,
-              gn_iters=1, cond_max=0.0, tile_threads=0, t0=0.0, substeps=0):
+              gn_iters=1, cond_max=0.0, tile_threads=0, t0=0.0, substeps=0, steps_per_thread=0):
     """Build a map_problem_desc from a ``synth.Model``; returns (desc, keepalive)."""
     n, m = model.nx, model.ny
     nw = model.L.shape[1]
@@ -267,4 +267,5 @@ def make_desc(model, T, dt, precision=MAP_FP32, discretisation=MAP_EULER, smooth
     d.precision, d.discretisation, d.smoother = precision, discretisation, smoother
     d.gn_iters, d.cond_max, d.tile_threads = int(gn_iters), float(cond_max), int(tile_threads)
     d.substeps = int(substeps)
+    d.steps_per_thread = int(steps_per_thread)
     return d, arrs

@@ -2,6 +2,7 @@
 // ownership and dispatch to the compiled (model, N, M, precision) instances.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -240,7 +241,10 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     if (B < 32 || B > 128 || (B & (B - 1)))
         return fail(*h, MAP_ERR_INVALID_ARG, "tile_threads must be 32, 64 or 128");
     while (B > 32 && tree_bytes(B) > (d->tile_threads > 0 ? 200 : 100) * 1024) B /= 2;
-    set_geometry(*h, balanced_steps_per_thread(*h, B), B);
+    if (d->steps_per_thread < 0 || d->steps_per_thread > max_steps_per_thread(*h, B))
+        return fail(*h, MAP_ERR_INVALID_ARG,
+                    "steps_per_thread must be 0 (automatic) or 1.." + std::to_string(max_steps_per_thread(*h, B)));
+    set_geometry(*h, d->steps_per_thread > 0 ? d->steps_per_thread : balanced_steps_per_thread(*h, B), B);
 
     h->ws_bytes = ops->workspace_bytes(*h);
     if ((e = cudaMalloc(&h->ws, h->ws_bytes)) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc workspace");
@@ -297,6 +301,16 @@ bool mapk::geometry_fits(const map_smoother& h, int B)
     return es * (2 * (size_t)B * NE + (size_t)B / NL * NSCR) <= 200 * 1024;
 }
 
+int mapk::max_steps_per_thread(const map_smoother& h, int B)
+{
+    // the RTS pass stages B*K states next to its affine tree in shared memory
+    const size_t es = elem_bytes(h.prec);
+    const size_t n = h.N, V = 16 / es, P = (n + V - 1) / V * V, NA = n * P + P;
+    int kmax = 64;
+    while (kmax > 1 && es * (2 * (size_t)B * NA + (size_t)B * ((kmax * n) | 1)) > 200 * 1024) --kmax;
+    return kmax;
+}
+
 int mapk::balanced_steps_per_thread(const map_smoother& h, int B)
 {
     // A tile of B*K steps is one CTA and all tiles of a launch run at once
@@ -312,11 +326,7 @@ int mapk::balanced_steps_per_thread(const map_smoother& h, int B)
     }
     const int per_sm = ops && ops->resident_blocks ? ops->resident_blocks(B) : 1;
     const long wave = (long)sms * per_sm * B;
-    // the RTS pass stages B*K states next to its affine tree in shared memory
-    const size_t es = elem_bytes(h.prec);
-    const size_t n = h.N, V = 16 / es, P = (n + V - 1) / V * V, NA = n * P + P;
-    int kmax = KMAX;
-    while (kmax > KMIN && es * (2 * (size_t)B * NA + (size_t)B * ((kmax * n) | 1)) > 200 * 1024) --kmax;
+    const int kmax = std::max(KMIN, max_steps_per_thread(h, B));
     const long waves = std::max(1L, (h.T + wave * kmax - 1) / (wave * kmax));
     const long K = (h.T + waves * wave - 1) / (waves * wave);
     return (int)std::min<long>(kmax, std::max<long>(KMIN, K));

@@ -100,6 +100,8 @@ struct Ops {
 void set_geometry(map_smoother& h, int K, int B);
 // K for B threads per tile such that the tiles fill whole waves of resident CTAs
 int balanced_steps_per_thread(const map_smoother& h, int B);
+// largest K whose RTS staging fits shared memory at B threads per tile
+int max_steps_per_thread(const map_smoother& h, int B);
 bool geometry_fits(const map_smoother& h, int B);
 map_status ensure_workspace(map_smoother& h, size_t bytes);
 map_status create_handle(map_smoother** out, const map_problem_desc* desc);

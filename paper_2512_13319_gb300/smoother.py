@@ -22,12 +22,13 @@ class MapSmoother:
     """
 
     def __init__(self, model, T, dt, precision="fp32", discretisation="euler", smoother="rts",
-                 gn_iters=1, cond_max=0.0, tile_threads=0, substeps=0):
+                 gn_iters=1, cond_max=0.0, tile_threads=0, substeps=0, steps_per_thread=0):
         self.model, self.T, self.dt, self.smoother = model, int(T), float(dt), smoother
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.nx, self.ny = model.nx, model.ny
         desc, keep = B.make_desc(model, T, dt, _PREC[precision], _DISC[discretisation],
-                                 _SMOOTHER[smoother], gn_iters, cond_max, tile_threads, substeps=substeps)
+                                 _SMOOTHER[smoother], gn_iters, cond_max, tile_threads, substeps=substeps,
+                                 steps_per_thread=steps_per_thread)
         self.substeps = (substeps or 10) if discretisation == "block" else 1
         self._h = B.map_smoother_create(desc)
         del keep
