@@ -199,6 +199,23 @@ def time_oracle(model, y, budget_s, min_runs=1):
     return t_tot / runs, runs, x
 
 
+def time_oracle_batch():
+    """The oracle on the 4096-trajectory batch over all host cores, one
+    trajectory per thread (the C oracle releases the GIL in its ctypes calls)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_2512_13319_gb300 import synth
+    models, lengths, model_of, ys = synth.batched_workload()
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda j: oracle.smooth_lti(models[model_of[j]], ys[j], 0.01), range(len(lengths))))
+    dt = time.perf_counter() - t
+    return {"value": float(lengths.sum()) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "all 4096 trajectories, one trajectory per thread (FP64 KF + RTS, plain C)", **host_cpu()}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -454,6 +471,9 @@ def ours(args):
         result["max_abs_err_rel_to_max_vs_oracle"] = float(np.abs(x_gpu - x_ref).max() / np.abs(x_ref).max())
         if checks and "extras" in result:
             oracle_checks(result["extras"], checks)
+            b = result["extras"].get("batched")
+            if isinstance(b, dict) and "error" not in b:
+                b["cpu_all_cores"] = time_oracle_batch()
     elif "extras" in result:
         for name, key, *_ in checks:
             if isinstance(result["extras"].get(name), dict) and "error" not in result["extras"][name]:

@@ -490,6 +490,9 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
         k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(rows, KT, g, ttab);
     }
     k_scan_gs<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, S>(h), mk + kr * N * N, HB ? 1 : 0, gsv);
+    if (Jt > 0)
+        k_scan_qsuf<N, S><<<(Jt + 3) / 4, 128, 0, st>>>(reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(KT)),
+                                                         g, reinterpret_cast<S*>(h.d_scan + SB::qsuf_off()));
     k_scan_tilemaps<N, M, S><<<(unsigned)(((long)nt * N * N + 127) / 128), 128, 0, st>>>(
         reinterpret_cast<const double*>(h.d_tab + ST::tmap_off()), g, pw, tiles);
     const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;
@@ -595,6 +598,8 @@ map_status run_scan(map_smoother& h, const LtiProducer<N, M, S>& prod, S* x_out,
     sa.taff = reinterpret_cast<S*>(h.d_scan + SB::taff_off());
     sa.gs = reinterpret_cast<const S*>(h.d_scan + SB::gs_off());
     sa.ep = reinterpret_cast<const S*>(h.d_scan + SB::ep_off());
+    sa.qsuf = reinterpret_cast<const S*>(h.d_scan + SB::qsuf_off());
+    sa.pinv = reinterpret_cast<const double*>(h.d_tab + ST::pinv_off());
     const char* tiles = h.d_scan + SB::tiles_off();
     sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));
     sa.qt = reinterpret_cast<const S*>(tiles + TT::qt_off(snt));

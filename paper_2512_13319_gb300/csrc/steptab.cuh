@@ -57,12 +57,12 @@ namespace mapk {
 
 // Layout of the step-table buffer (offsets in bytes): a few counters, the
 // FP64 element powers e^(2^l) (A, C, J as full N x N matrices; l < LPOW),
-// the FP64 P_T of the last step, the FP64 e^i (i < SMALL) and
+// the FP64 P_T of the last step and its inverse, the FP64 e^i (i < SMALL) and
 // P_{SMALL j}, the FP64 maps of the tiles before kc, then per step k < KT: the row in the solve's
 // precision S (E, o, mb, P b, P packed), E in FP64 and, for elements whose
 // offset b depends on the held sample (b_k = Bb y_k + b0), -E_k^T P_k Bb
 // (N x M in an N x N slot); and for the thread starts k = g K_t < KT the
-// K_t-step maps Phi_g in S.
+// K_t-step maps Phi_g in S and in FP64.
 template <int N, typename S>
 struct StepTab {
     static constexpr int NN = N * N, NS = Sym<N>::SZ;
@@ -78,7 +78,8 @@ struct StepTab {
     __host__ __device__ static constexpr size_t pref_off() { return al(pow_off() + sizeof(double) * LPOW * 3 * NN); }
     // e^i (i < SMALL) as full (A, C, J), and P_{SMALL j} (j <= cap / SMALL)
     static constexpr int SMALL = 64;
-    __host__ __device__ static constexpr size_t small_off() { return al(pref_off() + sizeof(double) * NN); }
+    __host__ __device__ static constexpr size_t pinv_off() { return al(pref_off() + sizeof(double) * NN); }
+    __host__ __device__ static constexpr size_t small_off() { return al(pinv_off() + sizeof(double) * NN); }
     __host__ __device__ static constexpr size_t base_off() { return al(small_off() + sizeof(double) * SMALL * 3 * NN); }
     __host__ __device__ static constexpr long base_count(long kt) { return kt / SMALL + 1; }
     // FP64 maps of the tiles before kc (tiles of 128 threads x K_t steps)
@@ -90,7 +91,8 @@ struct StepTab {
     __host__ __device__ static constexpr size_t mk_off(long kt) { return al(e64_off(kt) + sizeof(double) * kt * NN); }
     __host__ __device__ static constexpr long phit_count(long kt) { return kt / KT_STEPS + 1; }
     __host__ __device__ static constexpr size_t phit_off(long kt) { return al(mk_off(kt) + sizeof(S) * kt * NN); }
-    __host__ __device__ static constexpr size_t bytes(long kt) { return phit_off(kt) + sizeof(S) * phit_count(kt) * NN; }
+    __host__ __device__ static constexpr size_t phit64_off(long kt) { return al(phit_off(kt) + sizeof(S) * phit_count(kt) * NN); }
+    __host__ __device__ static constexpr size_t bytes(long kt) { return phit64_off(kt) + sizeof(double) * phit_count(kt) * NN; }
     // table length cap: the FP32 table converges within 2^-25 earlier
     __host__ __device__ static constexpr long cap() { return sizeof(S) == 4 ? 16384 : 32768; }
     __host__ __device__ static constexpr int log2_kt() { return KT_STEPS >= 4 ? 2 : KT_STEPS == 2 ? 1 : 0; }
@@ -273,7 +275,8 @@ __device__ inline void warp_double(PowWk<N>& w)
 // Element powers e^(2^l) of the data-free interval element e = (A, C, J)
 // (Eq. 36 combine of an element with itself), for every l with
 // 2^l <= max(T, KT), and P_T, the value function after all T steps (the
-// powers of the set bits of T applied to P_0; powers of one element commute).
+// powers of the set bits of T applied to P_0; powers of one element commute),
+// and P_T^-1, with which the solve forms x_T = P_T^-1 v_T (Eq. 18).
 // One warp, lane-parallel FP64 (the doublings are a chain in series).
 template <int N, int M, typename S>
 __global__ void __launch_bounds__(32)
@@ -302,7 +305,15 @@ k_step_powers(const LtiParams<N, M, double> p, const Red<N, double> prior, long 
         warp_double<N>(w);
     }
     double* pr = reinterpret_cast<double*>(tab + ST::pref_off());
-    for (int q = l0; q < NN; q += 32) pr[q] = w.P[q];
+    for (int q = l0; q < NN; q += 32) {
+        pr[q] = w.P[q];
+        w.T1[q] = w.P[q] - (q % (N + 1) == 0 ? 1.0 : 0.0);      // P_T - I
+        w.T2[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    fw::inv_I_plus<N>(w.T1, w.T2, w.T3, w.wk);                  // (I + (P_T - I))^-1 = P_T^-1
+    double* pi = reinterpret_cast<double*>(tab + ST::pinv_off());
+    for (int q = l0; q < NN; q += 32) pi[q] = w.T3[q];
 }
 
 // e^i for i < SMALL (the combination of the powers of the set bits of i;
@@ -498,8 +509,12 @@ k_lti_steptab(const LtiParams<N, M, double> p, long KT, int check, double tol,
         double Ph[NN];
         ok = sd::fold_map<N>(pw + (long)ST::log2_kt() * 3 * NN, P, Ph) && ok;
         S* ph = reinterpret_cast<S*>(tab + ST::phit_off(KT)) + (k / Kt) * NN;
+        double* ph64 = reinterpret_cast<double*>(tab + ST::phit64_off(KT)) + (k / Kt) * NN;
 #pragma unroll
-        for (int q = 0; q < NN; ++q) ph[q] = S(Ph[q]);
+        for (int q = 0; q < NN; ++q) {
+            ph[q] = S(Ph[q]);
+            ph64[q] = Ph[q];
+        }
     }
     if (check) {
         double Pr[NN];
@@ -535,7 +550,8 @@ struct ScanGeom {
 // of their shared-memory copy (component c of step i of thread t at
 // (i CT + c) B + t), the tiles' offsets w_j and RTS maps, the measurement
 // gain of the steps after kc (G, plus -E^T P Bb when the offset depends on the
-// sample), the partial thread's map E_inf^nv of the last tile, then the tile
+// sample), the partial thread's map E_inf^nv of the last tile, the suffix
+// products Q_t of the thread maps of the tiles before kc, then the tile
 // tables of lti_fold.cuh (TileTables: F_j = E_j^T and the products Pi).
 template <int N, int M, typename S>
 struct ScanBuf {
@@ -551,7 +567,9 @@ struct ScanBuf {
     __host__ __device__ static constexpr size_t taff_off() { return al(w_off() + sizeof(S) * NTMAX * N); }
     __host__ __device__ static constexpr size_t gs_off() { return al(taff_off() + sizeof(S) * NTMAX * (NN + N)); }
     __host__ __device__ static constexpr size_t ep_off() { return al(gs_off() + sizeof(S) * N * M); }
-    __host__ __device__ static constexpr size_t tiles_off() { return al(ep_off() + sizeof(S) * NN); }
+    // per thread of a tile before kc: Q_t = (Phi_{t+1} ... Phi_{B-1})^T
+    __host__ __device__ static constexpr size_t qsuf_off() { return al(ep_off() + sizeof(S) * NN); }
+    __host__ __device__ static constexpr size_t tiles_off() { return al(qsuf_off() + sizeof(S) * jt_max() * BMAX * NN); }
     __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::bytes(NTMAX); }
 };
 
@@ -668,6 +686,33 @@ k_scan_tilemaps(const double* __restrict__ tmap64, ScanGeom g, const S* __restri
     F[q] = j >= g.Jt || j == g.nt - 1 ? pw[(long)g.B * NN + qt] : S(__ldg(tmap64 + (long)j * NN + qt));
 }
 
+// Suffix products of the thread maps of each tile before kc (one warp per
+// tile, FP64): Q_t = (Phi_{t+1} ... Phi_{B-1})^T, Q_{B-1} = I.  The filter
+// offset of such a tile is then w_j = sum_t Q_t W_t.
+template <int N, typename S>
+__global__ void __launch_bounds__(128)
+k_scan_qsuf(const double* __restrict__ phit64, ScanGeom g, S* __restrict__ qsuf)
+{
+    namespace fw = fold_warp;
+    constexpr int NN = N * N;
+    __shared__ double Wk[4][2][NN];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int j = blockIdx.x * 4 + w;
+    if (j >= g.Jt || j == g.nt - 1) return;           // the last tile has no w_j (its maps may pass KT)
+    double* acc = Wk[w][0];
+    double* tmp = Wk[w][1];
+    for (int q = l; q < NN; q += 32) acc[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    __syncwarp();
+    for (int t = g.B - 1; t >= 0; --t) {
+        S* o = qsuf + ((long)j * g.B + t) * NN;
+        for (int q = l; q < NN; q += 32) o[q] = S(acc[(q % N) * N + q / N]);
+        if (t == 0) break;
+        fw::mm<N>(phit64 + ((long)j * g.B + t) * NN, acc, tmp);
+        for (int q = l; q < NN; q += 32) acc[q] = tmp[q];
+        __syncwarp();
+    }
+}
+
 // Per-step E_k and o_k of the tiles before kc, in the order of their
 // shared-memory copy; zeros past the table
 template <int N, typename S>
@@ -712,6 +757,8 @@ struct ScanArgs {
     const S* gs;            // measurement gain of the steps after kc (with the sample's share of o)
     const S* mk;            // per-step -E_k^T P_k Bb (steps before kc; offsets depending on the sample)
     const S* ep;            // E_inf^nv of the last tile's partial thread
+    const S* qsuf;          // suffix products of the thread maps of the tiles before kc
+    const double* pinv;     // P_T^-1 (FP64)
     ScanGeom g;
     int has_b;              // b != 0: the A^-1 b term of g_k
     S AiC[N * N];           // A^-1 C
@@ -1032,12 +1079,15 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
 #pragma unroll
             for (int a = 0; a < N; ++a) Fm.c[a] = W[a];
             if (!last) {
-                Aff<N, S> H = Fm;
-                reverse_maps<N, S>(H, gst);
-                block_aff_reduce<N, S>(H, red);        // F_{B-1} o ... o F_0 in thread 0
+                // w_j = sum_t Q_t W_t (Q_t the plan-time suffix products)
+                S Q[NN], p[N];
+#pragma unroll
+                for (int q = 0; q < NN; ++q) Q[q] = __ldg(sa.qsuf + ((long)tile * B + t) * NN + q);
+                mat_vec<N, S>(Q, W, p);
+                block_vec_sum<N, S>(p, red);
                 if (t == 0)
 #pragma unroll
-                    for (int a = 0; a < N; ++a) sa.w[(long)tile * N + a] = H.c[a];
+                    for (int a = 0; a < N; ++a) sa.w[(long)tile * N + a] = p[a];
             }
         }
         grid_sync(gs, 1, ctx.stats);
@@ -1116,10 +1166,14 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
 #pragma unroll
             for (int q = 0; q < Sym<N>::SZ; ++q) XT.P[q] = __ldg(rT + ST::oP + q);
             if (final_out) aos_store(final_out, 0, XT);
-            S xt[N];
-            if (!red_argmin<N, S>(XT, xt)) report_event(ctx.stats, EV_SINGULAR);
+            // x_T = P_T^-1 v_T with the plan-time FP64 inverse, accumulated in FP64
 #pragma unroll
-            for (int a = 0; a < N; ++a) xT[a] = xt[a];
+            for (int a = 0; a < N; ++a) {
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(__ldg(sa.pinv + a * N + q), double(v[q]), acc);
+                xT[a] = S(acc);
+            }
             if (filtT_out)
 #pragma unroll
                 for (int q = 0; q < Red<N, S>::NCOMP; ++q) filtT_out[q] = comp(XT, q);
