@@ -58,7 +58,7 @@ def _load():
             _lib.orc_two_filter_paper.argtypes = [i, i, D, D, D, D]
             _lib.orc_smooth_lti.argtypes = [i, i, i, d, i, i, D, D, D, D, D, D, D, D, D, D, D, D]
             _lib.orc_cost.argtypes = [i, i, i, i, d, D, D, d, D, D, D, D, D, D, D, D, D]
-            _lib.orc_gauss_newton.argtypes = [i, i, i, i, d, D, D, d, D, D, D, D, D, D, D, D, i, D]
+            _lib.orc_gauss_newton.argtypes = [i, i, i, i, d, D, D, d, D, D, D, D, D, D, D, D, i, i, D]
             _lib.orc_grad_lti.argtypes = [i, i, i, d, D, D, D, d, D, D, D, d, D, D, D, D, i, D, D]
             _lib.orc_block_elements.argtypes = [i, i, i, i, d, D, D, D, D, D, D, D, D]
             _lib.orc_exact_elements.argtypes = [i, i, i, d, D, D, D, D, D, D, D, D]
@@ -232,15 +232,16 @@ def cost(model, y, x, dt):
     return out.value
 
 
-def gauss_newton(model, y, dt, x_init, iters):
-    """Iterated linearisation (Gauss-Newton) MAP trajectory of a nonlinear model."""
+def gauss_newton(model, y, dt, x_init, iters, mode=EULER):
+    """Iterated linearisation (Gauss-Newton) MAP trajectory of a nonlinear model
+    (Section 4.4); mode EXPM discretises each step's local linear drift exactly."""
     y = _f(y); T = y.shape[0]; n, m = model.nx, model.ny
     F, c, H, r = _model_arrays(model)
     x = np.empty((T + 1, n))
     _check(_load().orc_gauss_newton(_kind_of(model), n, m, T, dt, _p(F), _p(c),
                                     float(model.params.get("gamma", 0.0)), _p(_f(model.Q)),
                                     _p(H), _p(r), _p(_f(model.R)), _p(_f(model.m0)),
-                                    _p(_f(model.P0)), _p(y), _p(_f(x_init)), iters, _p(x)))
+                                    _p(_f(model.P0)), _p(y), _p(_f(x_init)), iters, int(mode), _p(x)))
     return x
 
 

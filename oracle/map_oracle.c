@@ -742,17 +742,21 @@ done:
 /*
  * Iterated linearisation (Section 4.4; continuous-time IEKS = Gauss-Newton):
  * starting from xbar (T+1, n), repeat `iters` times: linearise the drift at
- * x_{k+1} (Euler interval: A_k = I - dt F(xbar_{k+1}),
- * b_k = -dt (f(xbar_{k+1}) - F xbar_{k+1}), C_k = dt Q) and the measurement at
- * x_{k+1} (J_k = dt Hb^T R^-1 Hb, eta_k = dt Hb^T R^-1 (y - h(xbar) + Hb xbar)
- * - 1/2 dt grad div f(xbar)), solve the linear problem by filter + smoother,
- * and set xbar to the result.  Output x (T+1, n).
+ * x_{k+1}, f(x) ~ F_k x + c_k with F_k = F(xbar_{k+1}) and
+ * c_k = f(xbar_{k+1}) - F_k xbar_{k+1}, and discretise that local linear
+ * model over the interval (orc_discretise: mode 0 the Euler interval
+ * A_k = I - dt F_k, b_k = -dt c_k, C_k = dt Q; mode 1 the exact solution of
+ * the A, b, C rows of Eq. 37 with the local coefficients, A_k = e^{-F_k dt}
+ * and so on); linearise the measurement at x_{k+1} (J_k = dt Hb^T R^-1 Hb,
+ * eta_k = dt Hb^T R^-1 (y - h(xbar) + Hb xbar) - 1/2 dt grad div f(xbar));
+ * solve the linear problem by filter + smoother, and set xbar to the result.
+ * Output x (T+1, n).
  */
 int orc_gauss_newton(int kind, int n, int m, int T, double dt, const double *F,
                      const double *c, double gamma, const double *Q, const double *H,
                      const double *r, const double *R, const double *m0,
                      const double *P0, const double *y, const double *xinit,
-                     int iters, double *x)
+                     int iters, int mode, double *x)
 {
     size_t nn = (size_t)n * n;
     double *Phi = (double *)malloc(sizeof(double) * (size_t)T * nn);
@@ -778,13 +782,10 @@ int orc_gauss_newton(int kind, int n, int m, int T, double dt, const double *F,
             drift_jac(kind, n, x1, F, c, gamma, f, Fj);
             for (int i = 0; i < n; ++i) {
                 double s = f[i];
-                for (int j = 0; j < n; ++j) {
-                    A[i * n + j] = (i == j ? 1.0 : 0.0) - dt * Fj[i * n + j];
-                    C[i * n + j] = dt * Q[i * n + j];
-                    s -= Fj[i * n + j] * x1[j];
-                }
-                b[i] = -dt * s;
+                for (int j = 0; j < n; ++j) s -= Fj[i * n + j] * x1[j];
+                g[i] = s;                                   /* c_k of the local linear drift */
             }
+            if (orc_discretise(n, dt, Fj, g, Q, mode, A, b, C)) { rc = ORC_ERR_ARG; goto done; }
             if (orc_forward_model(n, A, b, C, Phi + (size_t)k * nn, beta + (size_t)k * n,
                                   Sig + (size_t)k * nn)) { rc = ORC_ERR_SINGULAR; goto done; }
             meas_res_jac(kind, n, m, x1, y + (size_t)k * m, H, r, res, Hj);
