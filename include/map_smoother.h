@@ -77,8 +77,11 @@ typedef enum { MAP_FP64 = 0, MAP_FP32 = 1 } map_precision;
 
 typedef enum {
     MAP_EULER = 0,              /* one explicit Euler step of Eq. 37 per interval */
-    MAP_EXPM = 1,               /* exact A, b, C of Eq. 37 (linear models only) */
-    MAP_AUTO = 2,               /* MAP_EXPM when |F|_inf dt > 0.05, else MAP_EULER */
+    MAP_EXPM = 1,               /* exact A, b, C of Eq. 37 with constant coefficients; for
+                                   nonlinear models per step, with the coefficients of the
+                                   drift linearised at each Gauss-Newton iterate (Section 4.4) */
+    MAP_AUTO = 2,               /* linear models: MAP_EXPM when |F|_inf dt > 0.05, else
+                                   MAP_EULER; nonlinear models: MAP_EULER */
     MAP_BLOCK_EULER = 3,        /* Section 5.1 blocks: desc.substeps explicit Euler steps of all
                                    five rows of Eq. 37 per interval, the interval's sample held
                                    over its substeps (linear models, RTS smoother) */

@@ -137,7 +137,7 @@ map_status run_setup(map_smoother* h)
         return cuda_fail(*h, e, "cudaMemcpy");
     const double* b = h->d_setup;
     SetupIn si{};
-    si.nx = n; si.ny = m; si.nw = nw; si.mode = h->disc; si.dt = h->dt; si.substeps = h->substeps;
+    si.nx = n; si.ny = m; si.nw = nw; si.mode = h->model != MAP_MODEL_LINEAR && h->disc == MAP_EXPM ? MAP_EULER : h->disc;   // nonlinear: per step si.dt = h->dt; si.substeps = h->substeps;
     size_t o = 0;
     si.F = b + o; o += (size_t)n * n;
     si.c = b + o; o += n;
@@ -219,8 +219,6 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
         }
         disc = (h->model == MAP_MODEL_LINEAR && nF * h->dt > 0.05) ? MAP_EXPM : MAP_EULER;
     }
-    if (disc == MAP_EXPM && h->model != MAP_MODEL_LINEAR)
-        return fail(*h, MAP_ERR_UNSUPPORTED, "exact discretisation needs a linear drift");
     h->disc = disc;
 
     cudaError_t e = cudaGetDevice(&h->device);

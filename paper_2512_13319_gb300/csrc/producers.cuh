@@ -380,6 +380,8 @@ template <int N, int M, typename S>
 struct NlParams {
     static constexpr int NS = Sym<N>::SZ;
     S dt;
+    int expm;         // per-step exact discretisation of the local linear drift
+    S Q[NS];          // L W L^T
     S C[NS];          // dt Q
     S Rinv[M];        // diagonal of R^-1
     S F[N * N];       // linear part of the cubic drift
@@ -456,6 +458,100 @@ struct CubicModel {
     }
 };
 
+// Exact interval element (A, b, C) of the local linear drift f ~ F x + c over
+// dt (the A, b, C rows of Eq. 37 with constant coefficients, reversed drift
+// -F): A = e^{-F dt}, b = -int_0^dt e^{-F u} du c,
+// C = int_0^dt e^{-F u} Q e^{-F^T u} du.  Scaling and squaring: with
+// h = dt / 2^s and |F| h <= 1/4, truncated series
+//   A_h = sum_j X^j / j!,  b_h = -h sum_j X^j / (j+1)! c   (X = -F h),
+//   C_h = sum_k h^(k+1) / (k+1)! L_k,  L_0 = Q,  L_{k+1} = -F L_k - L_k F^T
+// (the Taylor coefficients of the integrand), then s doublings of the
+// data-free element, (A, b, C) -> (A A, A b + b, A C A^T + C) (Eq. 36 with
+// J = 0).  Terms up to order 6 in FP32, 12 in FP64.
+template <int N, typename S>
+__device__ __forceinline__ void local_exact_element(const S* F, const S* c, const S* Qp, S dt, S* A, S* b, S* Cp)
+{
+    constexpr int NN = N * N, P = sizeof(S) == 4 ? 6 : 12;
+    S nrm = S(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        S r = S(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) r += fabs(F[i * N + j]);
+        nrm = fmax(nrm, r);
+    }
+    int sq = 0;
+    S h = dt;
+    while (nrm * h > S(0.25) && sq < 30) { h *= S(0.5); ++sq; }
+    S X[NN], Pw[NN], Ph[N], L[NN], Cf[NN];
+#pragma unroll
+    for (int q = 0; q < NN; ++q) {
+        X[q] = -F[q] * h;
+        Pw[q] = q % (N + 1) == 0 ? S(1) : S(0);          // X^0
+        A[q] = Pw[q];
+        L[q] = Qp[Sym<N>::at(q / N, q % N)];
+        Cf[q] = h * L[q];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) Ph[i] = c[i];            // sum_j X^j / (j+1)! c, term j = 0
+    S fj = S(1);                                         // j!
+    S hk = h;                                            // h^(k+1) / (k+1)!
+#pragma unroll 1
+    for (int j = 1; j <= P; ++j) {
+        S T1[NN];
+        ms::mm<N, S>(Pw, X, T1);                         // X^j (j! folded in below)
+        fj *= S(j);
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            Pw[q] = T1[q];
+            A[q] += T1[q] / fj;
+        }
+        S v[N];
+        ms::mv<N, S>(T1, c, v);
+#pragma unroll
+        for (int i = 0; i < N; ++i) Ph[i] += v[i] / (fj * S(j + 1));
+        // L_j = -F L_{j-1} - L_{j-1} F^T
+        S FL[NN];
+        ms::mm<N, S>(F, L, FL);
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int d = 0; d < N; ++d) T1[a * N + d] = -(FL[a * N + d] + FL[d * N + a]);
+        hk *= h / S(j + 1);
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            L[q] = T1[q];
+            Cf[q] += hk * L[q];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) b[i] = -h * Ph[i];
+#pragma unroll 1
+    for (int s2 = 0; s2 < sq; ++s2) {
+        S A2[NN], AC[NN], C2[NN], Ab[N];
+        ms::mm<N, S>(A, A, A2);
+        ms::mv<N, S>(A, b, Ab);
+        ms::mm<N, S>(A, Cf, AC);
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int d = 0; d < N; ++d) {
+                S acc = Cf[a * N + d];
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(AC[a * N + q], A[d * N + q], acc);
+                C2[a * N + d] = acc;
+            }
+#pragma unroll
+        for (int q = 0; q < NN; ++q) { A[q] = A2[q]; Cf[q] = C2[q]; }
+#pragma unroll
+        for (int i = 0; i < N; ++i) b[i] += Ab[i];
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int d = a; d < N; ++d) Cp[Sym<N>::at(a, d)] = S(0.5) * (Cf[a * N + d] + Cf[d * N + a]);
+}
+
 template <class Model, typename S>
 struct NlProducer {
     static constexpr int N = Model::N, M = Model::M;
@@ -507,18 +603,31 @@ struct NlProducer {
         Model::drift(p, x1, f, Fj, gd);
         Model::measure(p, x1, yk, res, Hj);
         const S dt = p.dt;
+        if (p.expm) {
+            // local linear drift F x + c, c = f(xbar) - F xbar, discretised exactly
+            S cl[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            S s = f[i];
+            for (int i = 0; i < N; ++i) {
+                S s = f[i];
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                e.A[i * N + j] = (i == j ? S(1) : S(0)) - dt * Fj[i * N + j];
-                s = fma(-Fj[i * N + j], x1[j], s);
+                for (int j = 0; j < N; ++j) s = fma(-Fj[i * N + j], x1[j], s);
+                cl[i] = s;
             }
-            e.b[i] = -dt * s;
-        }
+            local_exact_element<N, S>(Fj, cl, p.Q, dt, e.A, e.b, e.C);
+        } else {
 #pragma unroll
-        for (int i = 0; i < Sym<N>::SZ; ++i) e.C[i] = p.C[i];
+            for (int i = 0; i < N; ++i) {
+                S s = f[i];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    e.A[i * N + j] = (i == j ? S(1) : S(0)) - dt * Fj[i * N + j];
+                    s = fma(-Fj[i * N + j], x1[j], s);
+                }
+                e.b[i] = -dt * s;
+            }
+#pragma unroll
+            for (int i = 0; i < Sym<N>::SZ; ++i) e.C[i] = p.C[i];
+        }
         // measurement information and the linearised divergence term
         S u[M];
 #pragma unroll

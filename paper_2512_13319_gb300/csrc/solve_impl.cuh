@@ -1230,8 +1230,12 @@ NlParams<N, M, S> nl_params(const map_smoother& h)
 {
     NlParams<N, M, S> p;
     p.dt = S(h.dt);
+    p.expm = h.disc == MAP_EXPM;
     for (int i = 0; i < N; ++i)
-        for (int j = i; j < N; ++j) p.C[Sym<N>::at(i, j)] = S(h.dt * h.consts.Q[i * N + j]);
+        for (int j = i; j < N; ++j) {
+            p.C[Sym<N>::at(i, j)] = S(h.dt * h.consts.Q[i * N + j]);
+            p.Q[Sym<N>::at(i, j)] = S(h.consts.Q[i * N + j]);
+        }
     for (int i = 0; i < M; ++i) p.Rinv[i] = S(1.0 / h.R[i * M + i]);
     for (int i = 0; i < N * N; ++i) p.F[i] = S(h.F[i]);
     for (int i = 0; i < N; ++i) p.c[i] = S(h.c[i]);

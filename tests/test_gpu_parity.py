@@ -440,6 +440,39 @@ def test_coordinated_turn_gauss_newton_T_2_16(prec):
     assert stats[1] == 0 and stats[2] == 0
 
 
+# ---------------------------------------------------------------- per-step exact discretisation (GN)
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [4000, 2 ** 16])
+def test_coordinated_turn_gauss_newton_exact_discretisation(prec, T):
+    """Gauss-Newton with each step's local linear drift discretised exactly
+    (MAP_EXPM on a nonlinear model) against the oracle's same iteration."""
+    model = synth.coordinated_turn()
+    dt, iters = 1e-3, 10
+    _, y = synth.simulate(model, T, dt, seed=1002)
+    x0 = np.tile(model.m0, (T + 1, 1))
+    x, stats = gpu_solve(model, y, dt, prec, x_init=x0, gn_iters=iters, discretisation="expm")
+    ref = oracle.gauss_newton(model, y, dt, x0, iters, mode=oracle.EXPM)
+    assert_traj(x, ref, TOL[prec])
+    assert stats[1] == 0 and stats[2] == 0
+    if prec == "fp64":
+        # a different problem from the Euler iteration (first order in dt)
+        assert rel(ref, oracle.gauss_newton(model, y, dt, x0, iters)) > 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cubic_drift_gauss_newton_exact_discretisation(prec):
+    """Large steps (dt |F| up to about 0.6: the element's scaling and squaring
+    halves the step) and the divergence term."""
+    model = synth.cubic_model(2, gamma=1.5, q=0.5, r=0.05)
+    model.m0 = np.array([1.0, -0.5])
+    T, dt, iters = 3000, 0.1, 8
+    _, y = synth.simulate(model, T, dt, seed=5)
+    x0 = np.tile(model.m0, (T + 1, 1))
+    x, _ = gpu_solve(model, y, dt, prec, x_init=x0, gn_iters=iters, discretisation="expm")
+    assert_traj(x, oracle.gauss_newton(model, y, dt, x0, iters, mode=oracle.EXPM), TOL[prec])
+
+
 # ---------------------------------------------------------------- sequential GPU baseline
 
 def seq_solve(model, y, dt, prec, x_init=None, **kw):
@@ -475,3 +508,14 @@ def test_sequential_baseline_matches_oracle_gauss_newton(prec):
     # the sequential FP32 baseline is held to 5e-4 and the speed comparison
     # "at equal accuracy" also reports the FP64 sequential baseline
     assert_traj(x, oracle.gauss_newton(model, y, dt, x0, iters), 5e-4 if prec == "fp32" else TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sequential_baseline_gauss_newton_exact_discretisation(prec):
+    model = synth.coordinated_turn()
+    T, dt, iters = 4000, 1e-3, 10
+    _, y = synth.simulate(model, T, dt, seed=synth.seed_for(2))
+    x0 = np.tile(model.m0, (T + 1, 1))
+    x = seq_solve(model, y, dt, prec, x_init=x0, gn_iters=iters, discretisation="expm")
+    assert_traj(x, oracle.gauss_newton(model, y, dt, x0, iters, mode=oracle.EXPM),
+                5e-4 if prec == "fp32" else TOL[prec])
