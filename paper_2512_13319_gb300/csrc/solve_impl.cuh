@@ -485,14 +485,16 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + kr * N * N, K, B, pw, tp, nvp,
                                           reinterpret_cast<S*>(h.d_scan + SB::ep_off()),
                                           last_steady ? taff + (long)(nt - 1) * (N * N + N) : nullptr);
-    if (Jt > 0 && ScanSmem<N, M, S>::STAGE) {
-        const long cnt = (long)Jt * B * Kt * SB::CT;
-        k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(rows, KT, g, ttab);
-    }
-    k_scan_gs<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, S>(h), mk + kr * N * N, HB ? 1 : 0, gsv);
     if (Jt > 0)
         k_scan_qsuf<N, S><<<(Jt + 3) / 4, 128, 0, st>>>(reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(KT)),
                                                          g, reinterpret_cast<S*>(h.d_scan + SB::qsuf_off()));
+    if (Jt > 0 && ScanSmem<N, M, S>::STAGE) {
+        const long cnt = (long)Jt * SB::ttab_rec(B, Kt);
+        k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
+            rows, reinterpret_cast<const S*>(h.d_tab + ST::phit_off(KT)),
+            reinterpret_cast<const S*>(h.d_scan + SB::qsuf_off()), KT, g, ttab);
+    }
+    k_scan_gs<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, S>(h), mk + kr * N * N, HB ? 1 : 0, gsv);
     k_scan_tilemaps<N, M, S><<<(unsigned)(((long)nt * N * N + 127) / 128), 128, 0, st>>>(
         reinterpret_cast<const double*>(h.d_tab + ST::tmap_off()), g, pw, tiles);
     const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;

@@ -562,7 +562,10 @@ struct ScanBuf {
     __host__ __device__ static constexpr long jt_max() { return ST::cap() / (BMAX * ST::KT_STEPS) + 2; }
     __host__ __device__ static constexpr size_t pw_off() { return 0; }
     __host__ __device__ static constexpr size_t ttab_off() { return al(sizeof(S) * (BMAX + 1) * NN); }
-    __host__ __device__ static constexpr size_t ttab_tile() { return (size_t)BMAX * ST::KT_STEPS * CT; }
+    // record of a tile before kc: its per-step (E_k, o_k), then its threads'
+    // maps Phi_t and suffix products Q_t (component q of thread t at q B + t)
+    __host__ __device__ static constexpr size_t ttab_rec(int B, int Kt) { return (size_t)B * (Kt * CT + 2 * NN); }
+    __host__ __device__ static constexpr size_t ttab_tile() { return ttab_rec(BMAX, ST::KT_STEPS); }
     __host__ __device__ static constexpr size_t w_off() { return al(ttab_off() + sizeof(S) * jt_max() * ttab_tile()); }
     __host__ __device__ static constexpr size_t taff_off() { return al(w_off() + sizeof(S) * NTMAX * N); }
     __host__ __device__ static constexpr size_t gs_off() { return al(taff_off() + sizeof(S) * NTMAX * (NN + N)); }
@@ -713,22 +716,35 @@ k_scan_qsuf(const double* __restrict__ phit64, ScanGeom g, S* __restrict__ qsuf)
     }
 }
 
-// Per-step E_k and o_k of the tiles before kc, in the order of their
-// shared-memory copy; zeros past the table
+// Records of the tiles before kc in the order of their shared-memory copy
+// (ScanBuf::ttab_rec): per-step E_k and o_k, the thread maps Phi_t and the
+// suffix products Q_t; zeros past the tables
 template <int N, typename S>
-__global__ void k_scan_ttab(const S* __restrict__ rows, long KT, ScanGeom g, S* __restrict__ ttab)
+__global__ void k_scan_ttab(const S* __restrict__ rows, const S* __restrict__ phit, const S* __restrict__ qsuf, long KT,
+                            ScanGeom g, S* __restrict__ ttab)
 {
     using ST = StepTab<N, S>;
     constexpr int NN = N * N, CT = NN + N;
-    const long per = (long)g.B * g.Kt * CT;
+    const long steps = (long)g.B * g.Kt * CT, per = steps + 2L * g.B * NN;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= per * g.Jt) return;
     const int j = (int)(e / per);
     const long r = e % per;
-    const int t = (int)(r % g.B), ic = (int)(r / g.B), i = ic / CT, c = ic % CT;
-    const long k = (long)j * g.B * g.Kt + (long)t * g.Kt + i;
     S v = S(0);
-    if (k < KT) v = c < NN ? rows[k * ST::RS + ST::oE + c] : rows[k * ST::RS + ST::oO + (c - NN)];
+    if (r < steps) {
+        const int t = (int)(r % g.B), ic = (int)(r / g.B), i = ic / CT, c = ic % CT;
+        const long k = (long)j * g.B * g.Kt + (long)t * g.Kt + i;
+        if (k < KT) v = c < NN ? rows[k * ST::RS + ST::oE + c] : rows[k * ST::RS + ST::oO + (c - NN)];
+    } else {
+        const long r2 = r - steps;
+        const int which = (int)(r2 / ((long)g.B * NN)), q = (int)((r2 % ((long)g.B * NN)) / g.B), t = (int)(r2 % g.B);
+        const long th = (long)j * g.B + t;
+        if (which == 0) {
+            if (th * g.Kt < KT) v = phit[th * NN + q];
+        } else {
+            v = qsuf[th * NN + q];
+        }
+    }
     ttab[e] = v;
 }
 
@@ -791,7 +807,7 @@ struct ScanSmem {
     __host__ __device__ static constexpr int bar(int B, int K, int Kt)
     {
         // the tile kind with the larger footprint decides
-        const int a = tabs(B, K) + (B + 1) * NN, c = tabs(B, Kt) + (STAGE ? B * Kt * CT : 0);
+        const int a = tabs(B, K) + (B + 1) * NN, c = tabs(B, Kt) + (STAGE ? B * (Kt * CT + 2 * NN) : 0);
         return al(a > c ? a : c);
     }
     __host__ __device__ static constexpr size_t bytes(int B, int K, int Kt) { return sizeof(S) * (size_t)bar(B, K, Kt) + 16; }
@@ -904,7 +920,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         // area are padded to them)
         const bool tcopy = STAGE || !trans;
         const unsigned tbytes =
-            tcopy ? (unsigned)((sizeof(S) * (trans ? (size_t)B * g.Kt * CT : (size_t)(B + 1) * NN) + 15) / 16 * 16)
+            tcopy ? (unsigned)((sizeof(S) * (trans ? (size_t)B * (g.Kt * CT + 2 * NN) : (size_t)(B + 1) * NN) + 15) / 16 * 16)
                   : 0u;
         const long yoff = s0 * M;
         const long ycnt = STAGE ? (long)B * Kj * M : 0;
@@ -917,7 +933,8 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         if (t == 0) {
             mbar_arrive_expect_tx(bar, tbytes + (unsigned)(sizeof(S) * ybulk));
             if (ybulk > 0) bulk_copy_g2s(ys, prod.y + yoff, (unsigned)(sizeof(S) * ybulk), bar);
-            if (tbytes) bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * g.Kt * CT : sa.pw, tbytes, bar);
+            if (tbytes)
+                bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * (g.Kt * CT + 2 * NN) : sa.pw, tbytes, bar);
             // the tile-product rows that the tile prefix and suffix sums read
             // after the grid barriers (data-independent): into L2 now
             using TT1 = TileTables<N, 1, S>;
@@ -1051,8 +1068,13 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         } else {
             // full maps: Phi of this thread (table, or the product of its steps)
             if (nv == Kj && trans) {
+                if constexpr (STAGE) {
 #pragma unroll
-                for (int q = 0; q < NN; ++q) Fm.F[q] = __ldg(sa.phit + ((long)tile * B + t) * NN + q);
+                    for (int q = 0; q < NN; ++q) Fm.F[q] = tb[B * g.Kt * CT + q * B + t];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NN; ++q) Fm.F[q] = __ldg(sa.phit + ((long)tile * B + t) * NN + q);
+                }
             } else if (nv == Kj) {
 #pragma unroll
                 for (int q = 0; q < NN; ++q) Fm.F[q] = tb[NN + q];            // Phi_inf
@@ -1081,8 +1103,13 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             if (!last) {
                 // w_j = sum_t Q_t W_t (Q_t the plan-time suffix products)
                 S Q[NN], p[N];
+                if constexpr (STAGE) {
 #pragma unroll
-                for (int q = 0; q < NN; ++q) Q[q] = __ldg(sa.qsuf + ((long)tile * B + t) * NN + q);
+                    for (int q = 0; q < NN; ++q) Q[q] = tb[B * (g.Kt * CT + NN) + q * B + t];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NN; ++q) Q[q] = __ldg(sa.qsuf + ((long)tile * B + t) * NN + q);
+                }
                 mat_vec<N, S>(Q, W, p);
                 block_vec_sum<N, S>(p, red);
                 if (t == 0)
