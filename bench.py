@@ -629,6 +629,24 @@ def extras(dev, flush, stream):
                 "sequential_gpu_ms": ms_seq,
                 "speedup_vs_sequential_gpu": ms_seq / ms}
 
+    def coord_turn_expm():
+        # Gauss-Newton with each step's linearised drift discretised exactly
+        model = synth.coordinated_turn()
+        T, iters = 2 ** 16, 10
+        _, y = synth.simulate(model, T, DT, seed=1002)
+        x0 = np.tile(model.m0, (T + 1, 1))
+        sm = MapSmoother(model, T, DT, precision="fp32", gn_iters=iters, discretisation="expm")
+        yt = torch.tensor(y, dtype=torch.float32, device=dev)
+        xi = torch.tensor(x0, dtype=torch.float32, device=dev)
+        x = torch.empty_like(xi)
+        ms = timed(lambda: sm.solve(yt, x_out=x, x_init=xi), flush, stream, dev)
+        checks.append(("coordinated_turn_expm", "rel_err_vs_oracle", "gauss_newton",
+                       (model, y, DT, x0, iters, 1), x.cpu().numpy()))     # mode 1: exact discretisation
+        sm.close()
+        return {"workload": "coordinated turn nx=5 ny=2, T=2^16, dt=1e-3, 10 Gauss-Newton iterations, each step's "
+                            "linearised drift discretised exactly, FP32", "ms": ms,
+                "value": T * iters / (ms * 1e-3), "unit": "time-steps x iterations/s"}
+
     def batched():
         from paper_2512_13319_gb300.batch import MapBatch
         models, lengths, model_of, ys = synth.batched_workload()
@@ -721,6 +739,7 @@ def extras(dev, flush, stream):
                             "interval), FP32, RTS", "ms": ms, "value": T_FULL / (ms * 1e-3), "unit": UNIT}
 
     for name, fn in (("ou_nx8", ou8), ("two_filter", two_filter), ("coordinated_turn", coord_turn),
+                     ("coordinated_turn_expm", coord_turn_expm),
                      ("batched", batched), ("gradient", gradient), ("parameter_update", parameter_update),
                      ("block_elements", block_dense), ("exact_elements", exact)):
         guard(name, fn)

@@ -137,7 +137,10 @@ map_status run_setup(map_smoother* h)
         return cuda_fail(*h, e, "cudaMemcpy");
     const double* b = h->d_setup;
     SetupIn si{};
-    si.nx = n; si.ny = m; si.nw = nw; si.mode = h->model != MAP_MODEL_LINEAR && h->disc == MAP_EXPM ? MAP_EULER : h->disc;   // nonlinear: per step si.dt = h->dt; si.substeps = h->substeps;
+    // nonlinear models discretise per step in their producers: their set-up takes the Euler constants
+    si.nx = n; si.ny = m; si.nw = nw;
+    si.mode = h->model != MAP_MODEL_LINEAR && h->disc == MAP_EXPM ? MAP_EULER : h->disc;
+    si.dt = h->dt; si.substeps = h->substeps;
     size_t o = 0;
     si.F = b + o; o += (size_t)n * n;
     si.c = b + o; o += n;

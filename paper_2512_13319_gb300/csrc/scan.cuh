@@ -912,7 +912,7 @@ k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ th
 // phase 1: per-thread fold and per-tile total of the filter elements
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod>
-__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
+__global__ void __launch_bounds__(128, (Prod::LINEAR_FOLD ? (N <= 6 ? 3 : 1) : (N <= 4 ? 3 : 1)))
 k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
                 S* __restrict__ tile_agg, S* __restrict__ terminal_out, CombineCtx ctx)
 {
@@ -1053,7 +1053,7 @@ __device__ __forceinline__ void filter_steps(const Prod& prod, int K, long k0, l
 // per-tile compositions; the last CTA writes the value function at x_T
 // ---------------------------------------------------------------------------
 template <int N, typename S, class Prod>
-__global__ void __launch_bounds__(128, (N <= 6 ? 3 : 1))
+__global__ void __launch_bounds__(128, (Prod::LINEAR_FOLD ? (N <= 6 ? 3 : 1) : (N <= 4 ? 3 : 1)))
 k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
               const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
               S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
