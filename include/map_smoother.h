@@ -348,18 +348,25 @@ map_status map_smoother_solve_noalloc(const map_problem_desc* desc, const void* 
  *         order, with one unused row between consecutive trajectories;
  *   x[m]  device, x_rows x nx: trajectory j's lengths[j] + 1 states in order.
  * map_batch_rows gives y_rows and x_rows (0 for models without trajectories).
- * map_batch_solve: on the first call, (steps per thread, threads per tile) of
- * every model are autotuned by timing the candidates on these arrays (eager
- * launches, synchronising `stream`); the per-model pipelines are then captured
- * into one CUDA graph with concurrent branches, and every call with the same
- * arrays is one graph launch on `stream` (asynchronous).  New arrays re-capture.
+ * map_batch_solve: on the first call (eager launches, synchronising
+ * `stream`) every model plans its chunked solve: its per-step tables (every
+ * trajectory starts from the model's prior, so its filter factors at local
+ * step k are the model's tabulated ones) and the maps of its chunks of 256
+ * steps; the solve is then five data-parallel kernels over the chunks of all
+ * its trajectories.  A model whose tables do not reach the stationary filter
+ * takes the segmented scan, whose (steps per thread, threads per tile) are
+ * autotuned by timing the candidates on these arrays.  The per-model launches
+ * are then captured into one CUDA graph with concurrent branches, and every
+ * call with the same arrays is one graph launch on `stream` (asynchronous).
+ * New arrays re-capture.
  */
 typedef struct map_batch map_batch;
 map_status map_batch_create(map_batch** out, const map_problem_desc* models, int nmodels,
                             const int64_t* lengths, const int* model_of, int ntraj);
 map_status map_batch_rows(const map_batch* b, int model, int64_t* y_rows, int64_t* x_rows);
 map_status map_batch_solve(map_batch* b, const void* const* y, void* const* x, void* stream);
-/* the autotuned (steps per thread, threads per tile) of model m (0, 0 before the first solve) */
+/* the (steps per thread, threads per tile) of model m (0, 0 before the first solve): for the
+ * chunked solve (256, 128), one thread per chunk of 256 steps in CTAs of 128 */
 map_status map_batch_tuning(const map_batch* b, int model, int* K, int* B);
 const char* map_batch_last_error(const map_batch* b);
 void map_batch_destroy(map_batch* b);

@@ -1,13 +1,18 @@
 // Batched solve: many independent trajectories of a few linear models.
 //
-// Trajectories of the same model are one scan: they are concatenated with the
-// model's prior element at every trajectory start (see SegLtiProducer), so a
-// batch of any size and length mix is one filter scan + RTS pass per model.
-// The per-model pipelines are captured once into a CUDA graph whose branches
-// run concurrently; each later call with the same arrays is one graph launch.
-// The steps per thread K and threads per tile B of every model are chosen by
+// Trajectories of the same model are stored concatenated, one spare row
+// between them.  Every trajectory starts from the model's prior, so the
+// data-independent part of its solve (the filter's P_k and closed-loop maps)
+// is that of the model's per-step tables at its local step: the chunked solve
+// of batch_scan.cuh runs all trajectories of a model as five data-parallel
+// kernels over chunks of its trajectories.  A model whose tables do not reach
+// the stationary filter takes the segmented scan instead: the trajectories
+// form one scan with the prior element at every trajectory start (see
+// SegLtiProducer), its steps per thread K and threads per tile B chosen by
 // timing the candidates (K = 8, 16 and the wave-filling K of each B) on the
-// caller's first arrays (autotuning).
+// caller's first arrays (autotuning).  The per-model launches are captured once
+// into a CUDA graph whose branches run concurrently; each later call with the
+// same arrays is one graph launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +33,8 @@ struct map_batch {
         cudaStream_t stream = nullptr;
         cudaEvent_t done = nullptr;
         bool tuned = false;
+        bool chunked = false;          // the chunked solve runs (tables converged)
+        BatchPlan bp;
     };
     int nmodels = 0;
     std::vector<Group> groups;
@@ -58,6 +65,12 @@ void destroy_batch(map_batch* b)
     for (auto& g : b->groups) {
         if (g.h) map_smoother_destroy(g.h);
         if (g.d_reset) cudaFree(g.d_reset);
+        if (g.bp.traj) cudaFree(g.bp.traj);
+        if (g.bp.chunk_traj) cudaFree(g.bp.chunk_traj);
+        if (g.bp.W) cudaFree(g.bp.W);
+        if (g.bp.V) cudaFree(g.bp.V);
+        if (g.bp.Bt) cudaFree(g.bp.Bt);
+        if (g.bp.tm) cudaFree(g.bp.tm);
         if (g.stream) cudaStreamDestroy(g.stream);
         if (g.done) cudaEventDestroy(g.done);
     }
@@ -76,7 +89,37 @@ __global__ void k_mark_resets(const long long* __restrict__ pos, int n, unsigned
 map_status solve_group(map_batch::Group& g, const void* y, void* x, cudaStream_t st)
 {
     const Ops* ops = find_ops(g.h->model, g.h->N, g.h->M, g.h->prec);
+    if (g.chunked) return ops->batch(*g.h, g.bp, y, x, st);
     return ops->solve_seg(*g.h, y, g.d_reset, x, st);
+}
+
+// device arrays of the chunked solve of one model: trajectories (first row,
+// length, chunks), the trajectory of each chunk, per-chunk scratch and the
+// chunk maps
+map_status plan_chunks(map_batch::Group& g, const std::vector<long>& rows, const std::vector<long>& lens)
+{
+    std::vector<BatchTraj> tr(rows.size());
+    std::vector<int> ct;
+    for (size_t j = 0; j < rows.size(); ++j) {
+        const int nc = (int)((lens[j] + BATCH_CH - 1) / BATCH_CH);
+        tr[j] = BatchTraj{rows[j], lens[j], (int)ct.size(), nc};
+        for (int i = 0; i < nc; ++i) ct.push_back((int)j);
+    }
+    BatchPlan& bp = g.bp;
+    bp.ntraj = (int)tr.size();
+    bp.nchunks = (int)ct.size();
+    const size_t es = elem_bytes(g.h->prec), per = es * (size_t)g.h->N * bp.nchunks;
+    bp.tm_cap = (int)(16384 * (es == 4 ? 1 : 2) / BATCH_CH + 2);
+    cudaError_t e;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&bp.traj), sizeof(BatchTraj) * tr.size())) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&bp.chunk_traj), sizeof(int) * ct.size())) != cudaSuccess ||
+        (e = cudaMalloc(&bp.W, per)) != cudaSuccess || (e = cudaMalloc(&bp.V, per)) != cudaSuccess ||
+        (e = cudaMalloc(&bp.Bt, per)) != cudaSuccess ||
+        (e = cudaMalloc(&bp.tm, es * (size_t)g.h->N * g.h->N * bp.tm_cap)) != cudaSuccess ||
+        (e = cudaMemcpy(bp.traj, tr.data(), sizeof(BatchTraj) * tr.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bp.chunk_traj, ct.data(), sizeof(int) * ct.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return MAP_ERR_CUDA;
+    return MAP_OK;
 }
 
 // time the (K, B) candidates on the caller's arrays; keep the fastest
@@ -150,11 +193,14 @@ map_status map_batch_create(map_batch** out, const map_problem_desc* models, int
     cudaError_t e;
     for (int m = 0; m < nmodels; ++m) {
         std::vector<long long> starts;
+        std::vector<long> rows, lens;
         long pos = 0;
         int cnt = 0;
         for (int j = 0; j < ntraj; ++j) {
             if (model_of[j] != m) continue;
             if (cnt > 0) { starts.push_back(pos); pos += 1; }   // the inserted prior element
+            rows.push_back(pos);
+            lens.push_back((long)lengths[j]);
             pos += lengths[j];
             ++cnt;
         }
@@ -198,6 +244,12 @@ map_status map_batch_create(map_batch** out, const map_problem_desc* models, int
                 return bfail(nullptr, MAP_ERR_CUDA, std::string("reset flags: ") + cudaGetErrorString(e));
             }
         }
+        const Ops* gops = find_ops(g.h->model, g.h->N, g.h->M, g.h->prec);
+        if (gops && gops->batch && plan_chunks(g, rows, lens) != MAP_OK) {
+            b->groups.push_back(g);
+            destroy_batch(b);
+            return bfail(nullptr, MAP_ERR_CUDA, "chunk tables of the batch");
+        }
         cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
         b->groups.push_back(g);
@@ -227,11 +279,24 @@ map_status map_batch_solve(map_batch* b, const void* const* y, void* const* x, v
             return bfail(b, MAP_ERR_INVALID_ARG, "every model with trajectories needs 16-byte aligned y and x");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    // first call: autotune every group (eager launches on its own stream)
+    // first call: plan the chunked solve of every group, else autotune its
+    // segmented scan (eager launches on its own stream)
     for (auto& g : b->groups)
         if (!g.tuned) {
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
                 return bfail(b, MAP_ERR_CUDA, cudaGetErrorString(e));
+            const Ops* ops = find_ops(g.h->model, g.h->N, g.h->M, g.h->prec);
+            if (ops->batch && g.bp.traj) {
+                const map_status s = ops->batch(*g.h, g.bp, y[g.model], x[g.model], g.stream);
+                if (s == MAP_OK) {
+                    g.chunked = true;
+                    g.tuned = true;
+                    if ((e = cudaStreamSynchronize(g.stream)) != cudaSuccess)
+                        return bfail(b, MAP_ERR_CUDA, cudaGetErrorString(e));
+                    continue;
+                }
+                if (s != MAP_ERR_UNSUPPORTED) return bfail(b, s, g.h->err);
+            }
             if (map_status s = autotune(b, g, y[g.model], x[g.model]); s != MAP_OK) return s;
         }
     std::vector<const void*> key;
@@ -267,7 +332,10 @@ map_status map_batch_tuning(const map_batch* b, int model, int* K, int* B)
     *K = 0;
     *B = 0;
     for (const auto& g : b->groups)
-        if (g.model == model) { *K = g.h->K; *B = g.h->B; }
+        if (g.model == model) {
+            *K = g.chunked ? BATCH_CH : g.h->K;        // chunked: steps per chunk, one thread each
+            *B = g.chunked ? 128 : g.h->B;
+        }
     return MAP_OK;
 }
 

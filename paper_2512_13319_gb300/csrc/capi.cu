@@ -116,6 +116,7 @@ map_status run_setup(map_smoother* h)
     const int n = h->N, m = h->M, nw = h->NW;
     h->fold_K = 0;                     // linear-fold constants follow the model
     h->tab_state = 0;                  // and so do the per-step tables
+    h->tab_conv = 0;
     h->tab_ok = 0;
     std::vector<double> W = h->W, R = h->R;
     for (double& w : W) w *= std::exp(h->logq);

@@ -1,9 +1,9 @@
 // One explicit instance of the linear-model solver.  The build compiles this
 // file twice per (INST_N, INST_M, INST_S), so that the instances build in
 // parallel in halves of similar size:
-//   INST_PART 0: the operation table, the RTS solve, the cost, the sequential
-//                baseline and the occupancy query;
-//   INST_PART 1: the two-filter solve, the gradient, the batched solve and
+//   INST_PART 0: the operation table, the RTS solve, the chunked batch solve,
+//                the cost, the sequential baseline and the occupancy query;
+//   INST_PART 1: the two-filter solve, the gradient, the segmented batch solve and
 //                the block/exact-element solve with its dense output (state
 //                dimensions up to 6), which part 0 declares extern.
 #include "solve_impl.cuh"

@@ -9,6 +9,7 @@
 #include "handle.h"
 #include "scan.cuh"
 #include "steptab.cuh"
+#include "batch_scan.cuh"
 
 namespace mapk {
 
@@ -565,9 +566,11 @@ map_status table_plan(map_smoother& h, cudaStream_t st)
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(h, e, "step table read-back");
     const long kc = check ? (long)meta[0] : h.T;
+    h.tab_conv = 0;
     if (meta[1] != 0 || (check && kc + 1 >= KT)) return MAP_OK;
     h.tab_kt = KT;
     h.tab_kc = kc;
+    h.tab_conv = 1;
     return scan_plan<N, M, S, HB>(h, st);
 }
 
@@ -1203,6 +1206,69 @@ size_t scan_table_bytes(const map_smoother& h)
     return h.smoother == MAP_RTS ? ScanBuf<N, M, S>::bytes() : 0;
 }
 
+// Chunked solve of many trajectories of this model (batch_scan.cuh): the step
+// tables and chunk maps on the first call (not under stream capture), then
+// the five data-parallel kernels.  MAP_ERR_UNSUPPORTED when the tables do not
+// reach the stationary filter (the caller then keeps the segmented scan).
+template <int N, int M, typename S>
+map_status batch_linear(map_smoother& h, BatchPlan& bp, const void* y, void* x, cudaStream_t st)
+{
+    using ST = StepTab<N, S>;
+    constexpr int NN = N * N;
+    if (!bp.ready) {
+        if (capturing(st)) return fail(h, MAP_ERR_UNSUPPORTED, "the first batch solve plans its tables: not under capture");
+        if (map_status s = table_plan<N, M, S, false>(h, st); s != MAP_OK) return s;
+        if (!h.tab_conv) return fail(h, MAP_ERR_UNSUPPORTED, "the step tables do not reach the stationary filter");
+        const int ntm = (int)((h.tab_kc + BATCH_CH - 1) / BATCH_CH) + 1;
+        if (ntm > bp.tm_cap) return fail(h, MAP_ERR_UNSUPPORTED, "too many chunk maps before the stationary point");
+        k_batch_chunk_maps<N, S><<<(ntm + 63) / 64, 64, 0, st>>>(h.d_tab, h.tab_kt, ntm, static_cast<S*>(bp.tm));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(h, e, "chunk map kernel launch");
+        bp.ntm = ntm;
+        bp.ready = true;
+    }
+    BatchArgs<N, M, S> a{};
+    a.y = static_cast<const S*>(y);
+    a.x = static_cast<S*>(x);
+    a.traj = bp.traj;
+    a.chunk_traj = bp.chunk_traj;
+    a.ntraj = bp.ntraj;
+    a.nchunks = bp.nchunks;
+    a.W = static_cast<S*>(bp.W);
+    a.V = static_cast<S*>(bp.V);
+    a.Bt = static_cast<S*>(bp.Bt);
+    a.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off());
+    a.kc = h.tab_kc;
+    a.tm = static_cast<const S*>(bp.tm);
+    a.ntm = bp.ntm;
+    a.prior = prior_of<N, S>(h);
+    const SetupOut& c = h.consts;
+    for (int i = 0; i < N; ++i) {
+        double ab = 0.0;
+        for (int k = 0; k < N; ++k) ab += c.Phi[i * N + k] * c.b[k];
+        a.Aib[i] = S(ab);
+        a.Gr[i] = S(c.Gr[i]);
+        for (int j = 0; j < N; ++j) {
+            double ac = 0.0;
+            for (int k = 0; k < N; ++k) ac += c.Phi[i * N + k] * c.C[k * N + j];
+            a.AiC[i * N + j] = S(ac);
+        }
+    }
+    for (int i = 0; i < N * M; ++i) a.G[i] = S(c.G[i]);
+    a.ctx = CombineCtx{(float)h.cond_max, h.d_stats};
+    const unsigned gc = (unsigned)((bp.nchunks + 127) / 128), gt = (unsigned)((bp.ntraj + 127) / 128);
+    k_batch_a<N, M, S><<<gc, 128, 0, st>>>(a);
+    k_batch_b<N, M, S><<<gt, 128, 0, st>>>(a);
+    k_batch_c<N, M, S><<<gc, 128, 0, st>>>(a);
+    k_batch_d<N, M, S><<<gt, 128, 0, st>>>(a);
+    k_batch_e<N, M, S><<<gc, 128, 0, st>>>(a);
+    (void)NN;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch kernel launch");
+    h.launches = 5;
+    return MAP_OK;
+}
+
 // State dimensions up to 6 get every path; larger ones (whose 5-tuples do not
 // fit one thread's registers) the RTS solve, the cost and the sequential baseline.
 template <int N, int M, typename S>
@@ -1212,7 +1278,8 @@ const Ops* linear_ops()
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
                              &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
                              &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>,
-                             &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>, &dense_linear<N, M, S>};
+                             &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>, &dense_linear<N, M, S>,
+                             &batch_linear<N, M, S>};
         return &ops;
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,
