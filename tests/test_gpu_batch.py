@@ -51,8 +51,9 @@ def test_mixed_batch_matches_oracle_per_trajectory(prec):
         ref = oracle.smooth_lti(models[model_of[j]], ys[j], dt)
         assert_traj(xs[j], ref, TOL[prec], (j, lengths[j], dims[j]))
     for m in range(3):
-        # the chunked solve over the model's step tables (chunks of 256 steps),
-        # or the autotuned segmented scan when the tables do not converge
+        # the chunked solve over the model's step tables (one thread per
+        # chunk of 256 steps, CTAs of 128), or the autotuned segmented scan
+        # when the tables do not converge
         K, B = mb.tuning(m)
         assert (K, B) == (256, 128) or (8 <= K <= 64 and B in (32, 64, 128))
         if prec == "fp32":
