@@ -40,6 +40,7 @@ struct map_smoother {
     char* d_tab = nullptr;
     int tab_state = 0;                 // 0: stale (model set-up changed), 1: computed
     int tab_conv = 0;                  // the tables reached the stationary filter (kc valid)
+    double tab_einf[64] = {};          // E of row kc in FP64 (N x N, N <= 8)
     int tab_ok = 0;                    // the tables reach the stationary filter: the table solve runs
     long tab_kt = 0, tab_kc = 0;
     // tiled-scan geometry of the table solve (steptab.cuh ScanGeom) and its buffer

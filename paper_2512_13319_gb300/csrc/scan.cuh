@@ -1484,7 +1484,7 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-constexpr int GRID_SPINS = 1 << 24;         // bounded wait (about a second with the back-off)
+constexpr int GRID_SPINS = 1 << 25;         // bounded wait (about a second with the back-off)
 
 // All CTAs of the (co-resident) grid reach barrier p; the global writes of
 // each CTA before it are visible to all after it.  A wait that runs out counts
@@ -1503,7 +1503,7 @@ __device__ __forceinline__ void grid_sync(const GridSync& gs, int p, unsigned lo
                 report_event(stats, EV_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
         __threadfence();
     }

@@ -486,9 +486,12 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     k_scan_powers<N, S><<<1, 256, 0, st>>>(e64 + kr * N * N, K, B, pw, tp, nvp,
                                           reinterpret_cast<S*>(h.d_scan + SB::ep_off()),
                                           last_steady ? taff + (long)(nt - 1) * (N * N + N) : nullptr);
-    if (Jt > 0)
-        k_scan_qsuf<N, S><<<(Jt + 3) / 4, 128, 0, st>>>(reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(KT)),
-                                                         g, reinterpret_cast<S*>(h.d_scan + SB::qsuf_off()));
+    if (Jt > 0) {
+        const size_t qsh = sizeof(double) * 2 * 128 * N * N;
+        if (cudaError_t e = allow_smem(k_scan_qsuf<N, S>, qsh); e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+        k_scan_qsuf<N, S><<<Jt, 128, qsh, st>>>(reinterpret_cast<const double*>(h.d_tab + ST::phit64_off(KT)), g,
+                                               reinterpret_cast<S*>(h.d_scan + SB::qsuf_off()));
+    }
     if (Jt > 0 && ScanSmem<N, M, S>::STAGE) {
         const long cnt = (long)Jt * SB::ttab_rec(B, Kt);
         k_scan_ttab<N, S><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
@@ -570,6 +573,10 @@ map_status table_plan(map_smoother& h, cudaStream_t st)
     if (meta[1] != 0 || (check && kc + 1 >= KT)) return MAP_OK;
     h.tab_kt = KT;
     h.tab_kc = kc;
+    // E_inf (FP64, row kc) for the plan-time products of the solve's steady steps
+    if ((e = cudaMemcpy(h.tab_einf, reinterpret_cast<const double*>(h.d_tab + ST::e64_off(KT)) + std::min(kc, KT - 1) * N * N,
+                        sizeof(double) * N * N, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "step table read-back");
     h.tab_conv = 1;
     return scan_plan<N, M, S, HB>(h, st);
 }
@@ -626,6 +633,42 @@ map_status run_scan(map_smoother& h, const LtiProducer<N, M, S>& prod, S* x_out,
             if (HB)
                 for (int k = 0; k < N; ++k) ab2 += c.Phi[i * N + k] * c.Bb[k * M + j];
             sa.AiBb[i * M + j] = S(ab2);
+        }
+    }
+    {
+        // E_inf times those, with E_inf the FP64 closed-loop map of row kc
+        const double* Einf = h.tab_einf;
+        double AiC[N * N], Aib[N], AiBb[N * M];
+        for (int i = 0; i < N; ++i) {
+            double ab = 0.0;
+            for (int k = 0; k < N; ++k) ab += c.Phi[i * N + k] * c.b[k];
+            Aib[i] = ab;
+            for (int j = 0; j < N; ++j) {
+                double ac = 0.0;
+                for (int k = 0; k < N; ++k) ac += c.Phi[i * N + k] * c.C[k * N + j];
+                AiC[i * N + j] = ac;
+            }
+            for (int j = 0; j < M; ++j) {
+                double ab2 = 0.0;
+                if (HB)
+                    for (int k = 0; k < N; ++k) ab2 += c.Phi[i * N + k] * c.Bb[k * M + j];
+                AiBb[i * M + j] = ab2;
+            }
+        }
+        for (int i = 0; i < N; ++i) {
+            double eb = 0.0;
+            for (int k = 0; k < N; ++k) eb += Einf[i * N + k] * Aib[k];
+            sa.EAib[i] = S(eb);
+            for (int j = 0; j < N; ++j) {
+                double ec = 0.0;
+                for (int k = 0; k < N; ++k) ec += Einf[i * N + k] * AiC[k * N + j];
+                sa.EAiC[i * N + j] = S(ec);
+            }
+            for (int j = 0; j < M; ++j) {
+                double eb2 = 0.0;
+                for (int k = 0; k < N; ++k) eb2 += Einf[i * N + k] * AiBb[k * M + j];
+                sa.EAiBb[i * M + j] = S(eb2);
+            }
         }
     }
     const CombineCtx ctx{(float)h.cond_max, h.d_stats};

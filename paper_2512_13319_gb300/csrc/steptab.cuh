@@ -689,30 +689,46 @@ k_scan_tilemaps(const double* __restrict__ tmap64, ScanGeom g, const S* __restri
     F[q] = j >= g.Jt || j == g.nt - 1 ? pw[(long)g.B * NN + qt] : S(__ldg(tmap64 + (long)j * NN + qt));
 }
 
-// Suffix products of the thread maps of each tile before kc (one warp per
-// tile, FP64): Q_t = (Phi_{t+1} ... Phi_{B-1})^T, Q_{B-1} = I.  The filter
-// offset of such a tile is then w_j = sum_t Q_t W_t.
+// Suffix products of the thread maps of each tile before kc (one CTA of B
+// threads per tile, FP64): Q_t = (Phi_{t+1} ... Phi_{B-1})^T, Q_{B-1} = I.  The
+// filter offset of such a tile is then w_j = sum_t Q_t W_t.  Inclusive suffix
+// products S_t = Phi_t ... Phi_{B-1} by a Kogge-Stone scan in shared memory
+// (S_t <- S_t S_{t+d}), then Q_t = S_{t+1}^T.
 template <int N, typename S>
 __global__ void __launch_bounds__(128)
 k_scan_qsuf(const double* __restrict__ phit64, ScanGeom g, S* __restrict__ qsuf)
 {
-    namespace fw = fold_warp;
     constexpr int NN = N * N;
-    __shared__ double Wk[4][2][NN];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int j = blockIdx.x * 4 + w;
-    if (j >= g.Jt || j == g.nt - 1) return;           // the last tile has no w_j (its maps may pass KT)
-    double* acc = Wk[w][0];
-    double* tmp = Wk[w][1];
-    for (int q = l; q < NN; q += 32) acc[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
-    __syncwarp();
-    for (int t = g.B - 1; t >= 0; --t) {
-        S* o = qsuf + ((long)j * g.B + t) * NN;
-        for (int q = l; q < NN; q += 32) o[q] = S(acc[(q % N) * N + q / N]);
-        if (t == 0) break;
-        fw::mm<N>(phit64 + ((long)j * g.B + t) * NN, acc, tmp);
-        for (int q = l; q < NN; q += 32) acc[q] = tmp[q];
-        __syncwarp();
+    extern __shared__ double qsm[];                      // 2 x 128 x NN
+    auto buf = [&](int b2, int i) { return qsm + ((long)b2 * 128 + i) * NN; };
+    const int j = blockIdx.x, t = threadIdx.x, B = g.B;
+    if (j >= g.Jt || j == g.nt - 1 || B > 128) return;   // the last tile has no w_j (its maps may pass KT)
+    int cur = 0;
+    if (t < B)
+        for (int q = 0; q < NN; ++q) buf(0, t)[q] = __ldg(phit64 + ((long)j * B + t) * NN + q);
+    __syncthreads();
+    for (int d = 1; d < B; d <<= 1) {
+        if (t < B) {
+            if (t + d < B) {
+                for (int q = 0; q < NN; ++q) {
+                    const int r = q / N, c = q % N;
+                    double acc = 0.0;
+                    for (int k = 0; k < N; ++k) acc = fma(buf(cur, t)[r * N + k], buf(cur, t + d)[k * N + c], acc);
+                    buf(cur ^ 1, t)[q] = acc;
+                }
+            } else {
+                for (int q = 0; q < NN; ++q) buf(cur ^ 1, t)[q] = buf(cur, t)[q];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (t < B) {
+        S* o = qsuf + ((long)j * B + t) * NN;
+        for (int q = 0; q < NN; ++q) {
+            const int r = q / N, c = q % N;
+            o[q] = t + 1 < B ? S(buf(cur, t + 1)[c * N + r]) : (r == c ? S(1) : S(0));
+        }
     }
 }
 
@@ -780,6 +796,9 @@ struct ScanArgs {
     S AiC[N * N];           // A^-1 C
     S Aib[N];               // A^-1 b (b0 when the offset depends on the sample)
     S AiBb[N * M];          // A^-1 Bb
+    S EAiC[N * N];          // E_inf A^-1 C, E_inf A^-1 b, E_inf A^-1 Bb (the steps after kc)
+    S EAib[N];
+    S EAiBb[N * M];
 };
 
 // shared memory of k_lti_scan (offsets in scalars): the composition area, the
@@ -1169,18 +1188,34 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
 #pragma unroll
                 for (int q = 0; q < Sym<N>::SZ; ++q) filt_out[k * Red<N, S>::NCOMP + N + q] = __ldg(r + ST::oP + q);
             }
-            S u[N], gk[N];
+            S gk[N];
+            if (!trans) {
+                // steps after kc: g_k = (E_inf A^-1 C) v_k + E_inf A^-1 b_k with the
+                // products formed once at plan time
 #pragma unroll
-            for (int a = 0; a < N; ++a) {
-                S acc = sa.Aib[a];
+                for (int a = 0; a < N; ++a) {
+                    S acc = sa.EAib[a];
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(sa.AiC[a * N + q], v[q], acc);
-                if constexpr (HB)
+                    for (int q = 0; q < N; ++q) acc = fma(sa.EAiC[a * N + q], v[q], acc);
+                    if constexpr (HB)
 #pragma unroll
-                    for (int m = 0; m < M; ++m) acc = fma(sa.AiBb[a * M + m], yt[i * M + m], acc);
-                u[a] = acc;
+                        for (int m = 0; m < M; ++m) acc = fma(sa.EAiBb[a * M + m], yt[i * M + m], acc);
+                    gk[a] = acc;
+                }
+            } else {
+                S u[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    S acc = sa.Aib[a];
+#pragma unroll
+                    for (int q = 0; q < N; ++q) acc = fma(sa.AiC[a * N + q], v[q], acc);
+                    if constexpr (HB)
+#pragma unroll
+                        for (int m = 0; m < M; ++m) acc = fma(sa.AiBb[a * M + m], yt[i * M + m], acc);
+                    u[a] = acc;
+                }
+                mat_vec<N, S>(E, u, gk);
             }
-            mat_vec<N, S>(E, u, gk);
             stage_state<N, S>(mine + i * N, gk);
             fstep(i, E, v);
         }
