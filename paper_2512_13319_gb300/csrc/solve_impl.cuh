@@ -554,7 +554,7 @@ map_status table_plan(map_smoother& h, cudaStream_t st)
     // thread maps of the threads that reach it
     const long KT = std::min<long>(h.T + 1, ST::cap());
     const int check = h.T + 1 > KT;
-    const double tol = sizeof(S) == 4 ? 0x1p-25 : 1e-14;
+    const double tol = sizeof(S) == 4 ? 0x1p-25 : 1e-12;
     unsigned long long meta[2] = {0, 0};
     cudaError_t e;
     if ((e = cudaMemsetAsync(h.d_tab, 0, sizeof(meta), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");

@@ -23,8 +23,10 @@
 // that a short scan has its every P_k up to P_T); when T >= KT, row kc stands
 // for every later step, where kc is the first step from which every tabulated
 // P_k agrees with the P of the uniform decomposition's last full tile to a
-// relative tolerance of 2^-25 (FP32 solves) or 1e-14 (FP64 solves) per entry
-// (|dP_ab| <= tol sqrt(P_aa P_bb)): below the solve's own rounding.  When the
+// relative tolerance of 2^-25 (FP32 solves: below the solve's own rounding)
+// or 1e-12 (FP64 solves: three orders below their 1e-9 accuracy target, and
+// above the rounding noise of the FP64 tables themselves) per entry
+// (|dP_ab| <= tol sqrt(P_aa P_bb)).  When the
 // table does not reach that point (slowly converging models) the solve keeps
 // the per-step combine paths of scan.cuh.
 //
@@ -1009,8 +1011,10 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             }
         };
         // v <- E^T v + o + G y_{k+1} - Gr
+        // (the data term is formed apart from the recursion, so that its
+        // shared-memory loads overlap the E^T v chain)
         auto fstep = [&](int i, const S (&E)[NN], S (&v)[N]) {
-            S o[N], nv2[N];
+            S o[N], gy[N], nv2[N];
             step_o(i, o);
 #pragma unroll
             for (int a = 0; a < N; ++a) {
@@ -1025,9 +1029,14 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
                         gc = prod.p.G[a * M + m];
                     acc = fma(gc, yt[i * M + m], acc);
                 }
+                gy[a] = acc;
+            }
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(E[q * N + a], v[q], acc);
-                nv2[a] = acc;
+            for (int a = 0; a < N; ++a) {
+                S acc = E[a] * v[0];
+#pragma unroll
+                for (int q = 1; q < N; ++q) acc = fma(E[q * N + a], v[q], acc);
+                nv2[a] = acc + gy[a];
             }
 #pragma unroll
             for (int a = 0; a < N; ++a) v[a] = nv2[a];
