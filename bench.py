@@ -120,7 +120,8 @@ def work_model_tab(n, m, K, B, nt, wbytes):
 
 
 # DRAM bytes (read + write) of one k_lti_scan launch on the nx=4, T=2^20
-# FP32 workload from one ncu capture of the current version; None until then
+# FP32 workload from one ncu capture of the current version (profiles/); None
+# until the current version has been captured
 K_SCAN_DRAM_BYTES = None
 
 
