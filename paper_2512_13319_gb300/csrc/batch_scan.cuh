@@ -124,13 +124,22 @@ __global__ void __launch_bounds__(128) k_batch_a(const __grid_constant__ BatchAr
     for (int i = 0; i < N; ++i) W[i] = S(0);
     auto run = [&](auto steady) {
         constexpr bool ST_ = decltype(steady)::value;
+        const S* yc = a.y + (tr.row + k0) * M;
+        S y0[M], y1[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            y0[m] = __ldg(yc + m);
+            y1[m] = nv > 1 ? __ldg(yc + M + m) : S(0);
+        }
 #pragma unroll 1
         for (int s = 0; s < nv; ++s) {
-            S E[N * N], yk[M];
-            bs.template E_of<ST_>(a, k0 + s, E);
+            S E[N * N], y2[M];
 #pragma unroll
-            for (int m = 0; m < M; ++m) yk[m] = __ldg(a.y + (tr.row + k0 + s) * M + m);
-            bs.template fstep<ST_>(a, k0 + s, E, yk, W);
+            for (int m = 0; m < M; ++m) y2[m] = s + 2 < nv ? __ldg(yc + (s + 2) * M + m) : S(0);
+            bs.template E_of<ST_>(a, k0 + s, E);
+            bs.template fstep<ST_>(a, k0 + s, E, y0, W);
+#pragma unroll
+            for (int m = 0; m < M; ++m) { y0[m] = y1[m]; y1[m] = y2[m]; }
         }
     };
     if (k0 >= a.kc) run(std::true_type{}); else run(std::false_type{});
@@ -189,9 +198,18 @@ __global__ void __launch_bounds__(128) k_batch_c(const __grid_constant__ BatchAr
     S* xr = a.x + (tr.row + k0) * N;
     auto fwd = [&](auto st_) {
         constexpr bool ST_ = decltype(st_)::value;
+        const S* yc = a.y + (tr.row + k0) * M;
+        S y0[M], y1[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            y0[m] = __ldg(yc + m);
+            y1[m] = nv > 1 ? __ldg(yc + M + m) : S(0);
+        }
 #pragma unroll 1
         for (int s = 0; s < nv; ++s) {
-            S E[N * N], yk[M], u[N], g[N];
+            S E[N * N], y2[M], u[N], g[N];
+#pragma unroll
+            for (int m = 0; m < M; ++m) y2[m] = s + 2 < nv ? __ldg(yc + (s + 2) * M + m) : S(0);
             bs.template E_of<ST_>(a, k0 + s, E);
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -202,9 +220,9 @@ __global__ void __launch_bounds__(128) k_batch_c(const __grid_constant__ BatchAr
             }
             mat_vec<N, S>(E, u, g);
             store_vec<N, S>(xr + (long)s * N, g);
+            bs.template fstep<ST_>(a, k0 + s, E, y0, v);
 #pragma unroll
-            for (int m = 0; m < M; ++m) yk[m] = __ldg(a.y + (tr.row + k0 + s) * M + m);
-            bs.template fstep<ST_>(a, k0 + s, E, yk, v);
+            for (int m = 0; m < M; ++m) { y0[m] = y1[m]; y1[m] = y2[m]; }
         }
     };
     if (steady) fwd(std::true_type{}); else fwd(std::false_type{});
@@ -225,15 +243,21 @@ __global__ void __launch_bounds__(128) k_batch_c(const __grid_constant__ BatchAr
     }
     auto back = [&](auto st_) {
         constexpr bool ST_ = decltype(st_)::value;
+        // the staged g of the next two steps are loaded ahead of the recursion
+        S g0[N], g1[N];
+        load_vec<N, S>(xr + (long)(nv - 1) * N, g0);
+        if (nv > 1) load_vec<N, S>(xr + (long)(nv - 2) * N, g1);
 #pragma unroll 1
         for (int s = nv - 1; s >= 0; --s) {
-            S E[N * N], g[N], nz[N];
+            S E[N * N], g2[N], nz[N];
+            if (s >= 2) load_vec<N, S>(xr + (long)(s - 2) * N, g2);
             bs.template E_of<ST_>(a, k0 + s, E);
-            load_vec<N, S>(xr + (long)s * N, g);
             mat_vec<N, S>(E, z, nz);
 #pragma unroll
-            for (int i = 0; i < N; ++i) z[i] = nz[i] + g[i];
+            for (int i = 0; i < N; ++i) z[i] = nz[i] + g0[i];
             if (lastc) store_vec<N, S>(xr + (long)s * N, z);
+#pragma unroll
+            for (int i = 0; i < N; ++i) { g0[i] = g1[i]; g1[i] = g2[i]; }
         }
     };
     if (steady) back(std::true_type{}); else back(std::false_type{});
@@ -280,15 +304,21 @@ __global__ void __launch_bounds__(128) k_batch_e(const __grid_constant__ BatchAr
     S* xr = a.x + (tr.row + k0) * N;
     auto back = [&](auto st_) {
         constexpr bool ST_ = decltype(st_)::value;
+        // the staged g of the next two steps are loaded ahead of the recursion
+        S g0[N], g1[N];
+        load_vec<N, S>(xr + (long)(BATCH_CH - 1) * N, g0);
+        load_vec<N, S>(xr + (long)(BATCH_CH - 2) * N, g1);
 #pragma unroll 1
         for (int s = BATCH_CH - 1; s >= 0; --s) {
-            S E[N * N], g[N], nz[N];
+            S E[N * N], g2[N], nz[N];
+            if (s >= 2) load_vec<N, S>(xr + (long)(s - 2) * N, g2);
             bs.template E_of<ST_>(a, k0 + s, E);
-            load_vec<N, S>(xr + (long)s * N, g);
             mat_vec<N, S>(E, z, nz);
 #pragma unroll
-            for (int i = 0; i < N; ++i) z[i] = nz[i] + g[i];
+            for (int i = 0; i < N; ++i) z[i] = nz[i] + g0[i];
             store_vec<N, S>(xr + (long)s * N, z);
+#pragma unroll
+            for (int i = 0; i < N; ++i) { g0[i] = g1[i]; g1[i] = g2[i]; }
         }
     };
     if (k0 >= a.kc) back(std::true_type{}); else back(std::false_type{});

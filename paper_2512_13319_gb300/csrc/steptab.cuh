@@ -807,15 +807,16 @@ struct ScanArgs {
 // warp totals, the tile's observations, the per-step offsets g_k (staged
 // states in the RTS phase; exchange area of the full-map compositions before
 // that), then the powers Phi_inf^d (tiles after kc) or the per-step E_k, o_k
-// (tiles before kc), then the mbarrier.  With STAGE false (state dimensions
-// above 6, whose per-step data would not fit for a grid of co-resident tiles)
+// (tiles before kc), then the mbarrier.  With STAGE false (FP64, and FP32
+// state dimensions above 6, whose per-step data would not fit for a grid of
+// co-resident tiles)
 // the observations are read from global memory, the g_k and states go
 // through x_out, and the tiles before kc read their rows from global memory:
 // only the composition areas and the powers stay.
 template <int N, int M, typename S>
 struct ScanSmem {
     static constexpr int NN = N * N, NA = NN + N, CT = NN + N;
-    static constexpr bool STAGE = N <= 6;
+    static constexpr bool STAGE = N <= 6 && sizeof(S) == 4;
     __host__ __device__ static constexpr int al(int x) { return (x + 3) / 4 * 4; }
     __host__ __device__ static constexpr int red_size(int B) { return (B / 32) * (NA + N) + N; }
     __host__ __device__ static constexpr int wt(int B) { return al(red_size(B)); }
