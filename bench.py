@@ -569,6 +569,11 @@ def rel_err(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def hbm_peak_gbs():
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    return peaks.get("hbm_gbs", 6800.0)
+
+
 def extras(dev, flush, stream):
     """The other workloads of the path, timed on the GPU.  Returns the results
     and the checks that the CPU-baseline leg resolves with the oracle (extra,
@@ -661,11 +666,22 @@ def extras(dev, flush, stream):
         for j in rng.choice(len(lengths), size=20, replace=False):
             checks.append(("batched", "max_rel_err_vs_oracle_20_sampled", "smooth_lti",
                            (models[model_of[j]], ys[j], 0.01), xs[j]))
-        tuning = {f"nx={mdl.nx}": mb.tuning(i) for i, mdl in enumerate(models)}
+        KB, B = mb.tuning(0)
+        persistent = mb.persistent()
         mb.close()
+        steps = int(lengths.sum())
+        # bytes the persistent kernel must move: y read twice (forward and
+        # backward sweeps) and x written once, per step of each model
+        nx_of = np.array([models[m].nx for m in model_of])
+        ny_of = np.array([models[m].ny for m in model_of])
+        min_bytes = float(np.sum(lengths * (2 * ny_of + nx_of) * 4 + nx_of * 4))
         return {"workload": "4096 Wiener-velocity trajectories, nx in {2,4,6}, lengths log-uniform 256..65536, "
-                            "dt=0.01, FP32, one CUDA graph", "steps": int(lengths.sum()), "ms": ms,
-                "value": float(lengths.sum()) / (ms * 1e-3), "unit": UNIT, "tuning_K_B": tuning}
+                            "dt=0.01, FP32, one persistent launch in a CUDA graph", "steps": steps, "ms": ms,
+                "value": steps / (ms * 1e-3), "unit": UNIT, "persistent_kernel": persistent,
+                "steps_per_thread": KB, "threads_per_cta": B,
+                "hbm": {"bytes": min_bytes, "gbs": min_bytes / (ms * 1e-3) / 1e9,
+                        "frac": min_bytes / (ms * 1e-3) / 1e9 / hbm_peak_gbs(),
+                        "note": "y read in both sweeps + x written, per step (model-dependent sizes)"}}
 
     def gradient():
         T = 2 ** 18

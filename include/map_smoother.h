@@ -336,38 +336,41 @@ map_status map_smoother_solve_noalloc(const map_problem_desc* desc, const void* 
 /*
  * Batches of independent trajectories (thousands of trajectories of uneven
  * length and state dimension in one launch).
- * models[m] describes a linear model (desc.T is ignored, smoother MAP_RTS);
- * trajectory j has lengths[j] >= 1 intervals of model model_of[j].
- * All trajectories of one model are solved as ONE scan: they are concatenated
- * in input order with the model's prior element (Eq. 31 a_T) inserted before
- * every trajectory but the first; on the left of the combine (Eq. 36) that
- * element keeps only its own value function, so it restarts the filter, and
- * its closed-loop map is the constant map to the argmin of the previous
- * trajectory's final value function (Eq. 18).  Per model m:
+ * models[m] describes a linear model (desc.T is ignored, smoother MAP_RTS,
+ * nx <= 6, every model in the same precision); trajectory j has
+ * lengths[j] >= 1 intervals of model model_of[j].  Per model m:
  *   y[m]  device, y_rows x ny: trajectory j's lengths[j] observation rows in
  *         order, with one unused row between consecutive trajectories;
  *   x[m]  device, x_rows x nx: trajectory j's lengths[j] + 1 states in order.
  * map_batch_rows gives y_rows and x_rows (0 for models without trajectories).
- * map_batch_solve: on the first call (eager launches, synchronising
- * `stream`) every model plans its chunked solve: its per-step tables (every
- * trajectory starts from the model's prior, so its filter factors at local
- * step k are the model's tabulated ones) and the maps of its chunks of 256
- * steps; the solve is then five data-parallel kernels over the chunks of all
- * its trajectories.  A model whose tables do not reach the stationary filter
- * takes the segmented scan, whose (steps per thread, threads per tile) are
- * autotuned by timing the candidates on these arrays.  The per-model launches
- * are then captured into one CUDA graph with concurrent branches, and every
- * call with the same arrays is one graph launch on `stream` (asynchronous).
- * New arrays re-capture.
+ * Every trajectory starts from its model's prior (Eq. 31 a_T), so its filter
+ * factor at local step k is the model's tabulated one (the per-step tables of
+ * the Eq. 36 one-variable combine, Section 4.2 elements), and its solve is the
+ * affine filter and RTS recursions (Section 4.3, Eq. 40-42) on those tables.
+ * map_batch_solve: on the first call (eager launches, synchronising `stream`)
+ * every model plans its step tables; when all of them reach the stationary
+ * filter the batch runs as ONE launch of a persistent kernel over all models
+ * and trajectories (CTAs take whole trajectories, longest first, from a work
+ * counter), whose threads per CTA and steps per thread are chosen by timing
+ * the candidates on these arrays (autotuning); the launch is captured into a
+ * CUDA graph and every later call is one graph launch on `stream`
+ * (asynchronous; new arrays update the kernel's model records on `stream`).
+ * Otherwise every model takes the segmented scan (its trajectories as one scan
+ * with the prior element inserted before every trajectory but the first,
+ * which restarts the filter), with its own autotuned (steps per thread,
+ * threads per tile), and the per-model launches form one graph with
+ * concurrent branches.
  */
 typedef struct map_batch map_batch;
 map_status map_batch_create(map_batch** out, const map_problem_desc* models, int nmodels,
                             const int64_t* lengths, const int* model_of, int ntraj);
 map_status map_batch_rows(const map_batch* b, int model, int64_t* y_rows, int64_t* x_rows);
 map_status map_batch_solve(map_batch* b, const void* const* y, void* const* x, void* stream);
-/* the (steps per thread, threads per tile) of model m (0, 0 before the first solve): for the
- * chunked solve (256, 128), one thread per chunk of 256 steps in CTAs of 128 */
+/* the (steps per thread, threads per CTA) of model m (0, 0 before the first solve): the
+ * persistent kernel's (the same for every model), or the model's segmented scan's */
 map_status map_batch_tuning(const map_batch* b, int model, int* K, int* B);
+/* 1 when the batch runs as one launch of the persistent kernel, else 0 */
+int map_batch_persistent(const map_batch* b);
 const char* map_batch_last_error(const map_batch* b);
 void map_batch_destroy(map_batch* b);
 

@@ -67,6 +67,7 @@ EXPORTS = {
     "map_batch_tuning": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "map_batch_last_error": (_CH, [_VP]),
     "map_batch_destroy": (None, [_VP]),
+    "map_batch_persistent": (_I, [_VP]),
     "map_fma_peak": (_I, [_I, _I, _D, ctypes.POINTER(ctypes.c_float), _VP]),
     "map_smoother_wait_selftest": (_I, [_VP, _I, _VP]),
     "map_smoother_log_normaliser": (_I, [_VP, _D]),

@@ -10,8 +10,9 @@ from . import _binding as B
 
 
 class MapBatch:
-    """Independent trajectories of a few linear models, solved per model as one
-    scan with reset elements (see include/map_smoother.h, map_batch_create)."""
+    """Independent trajectories of a few linear models: one launch of the
+    persistent batch kernel for all of them, or per model one scan with reset
+    elements (see include/map_smoother.h, map_batch_create)."""
 
     def __init__(self, models, lengths, model_of, dts, precision="fp32"):
         self.models = list(models)
@@ -93,6 +94,10 @@ class MapBatch:
         K, Bt = ctypes.c_int(), ctypes.c_int()
         B.load().map_batch_tuning(self._h, model, ctypes.byref(K), ctypes.byref(Bt))
         return K.value, Bt.value
+
+    def persistent(self):
+        """True when the batch runs as one launch of the persistent kernel."""
+        return bool(B.load().map_batch_persistent(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

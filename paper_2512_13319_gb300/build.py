@@ -36,7 +36,8 @@ def nvcc() -> str:
 def units():
     """(object name, source, extra defines) of every translation unit."""
     out = [("capi", "capi.cu", []), ("discretise", "discretise.cu", []), ("noalloc", "noalloc.cu", []),
-           ("batch", "batch.cu", []), ("peaks", "peaks.cu", []), ("selftest", "selftest.cu", [])]
+           ("batch", "batch.cu", []), ("batch_persist", "batch_persist.cu", []),
+           ("peaks", "peaks.cu", []), ("selftest", "selftest.cu", [])]
     for prec, typ in (("f32", "float"), ("f64", "double")):
         for n, m in LINEAR_SHAPES:
             for part in ((0, 1) if n <= 6 else (0,)):

@@ -81,29 +81,6 @@ inline size_t fold_bytes(int n, int m, size_t es, long nt)
     return pi + (nt <= 4 * 128 + 1 ? al(2 * es * (size_t)(nt * (nt + 1) / 2) * n * n) + es * (size_t)nt * n * n : 0);
 }
 
-// steps per chunk of the chunked batch solve (a multiple of StepTab::SMALL)
-constexpr int BATCH_CH = 256;
-
-// One trajectory of a batch (batch_scan.cuh): its first y (and x) row in the
-// model's concatenated arrays, its intervals and its chunks
-struct BatchTraj {
-    long row;
-    long L;
-    int c0, nc;
-};
-
-// Device arrays of the chunked batch solve of one model (batch.cu, batch_scan.cuh)
-struct BatchPlan {
-    BatchTraj* traj = nullptr;        // ntraj
-    int* chunk_traj = nullptr;        // nchunks: trajectory of each chunk
-    void* W = nullptr;                // nchunks x N scalars each
-    void* V = nullptr;
-    void* Bt = nullptr;
-    void* tm = nullptr;               // chunk maps, up to tm_cap matrices
-    int ntraj = 0, nchunks = 0, tm_cap = 0, ntm = 0;
-    bool ready = false;               // tables and chunk maps formed
-};
-
 // Per-(model, N, M, precision) entry points, explicitly instantiated in the inst_*.cu files.
 struct Ops {
     size_t (*workspace_bytes)(const map_smoother& h);
@@ -119,8 +96,8 @@ struct Ops {
     size_t (*scan_bytes)(const map_smoother& h) = nullptr;  // tiled-scan table buffer (0: none)
     map_status (*dense)(map_smoother& h, const void* y, const void* x, const void* filt, void* out,
                         cudaStream_t st) = nullptr;         // states between the grid points
-    map_status (*batch)(map_smoother& h, BatchPlan& bp, const void* y, void* x,
-                        cudaStream_t st) = nullptr;         // chunked solve of many trajectories
+    map_status (*batch_model)(map_smoother& h, void* out, int KB,
+                              cudaStream_t st) = nullptr;   // BpModel<S> record for the persistent batch solve
 };
 
 // geometry (steps per thread K, threads per tile B) and its workspace bytes

@@ -9,7 +9,7 @@
 #include "handle.h"
 #include "scan.cuh"
 #include "steptab.cuh"
-#include "batch_scan.cuh"
+#include "batch_persist.h"
 
 namespace mapk {
 
@@ -1249,66 +1249,78 @@ size_t scan_table_bytes(const map_smoother& h)
     return h.smoother == MAP_RTS ? ScanBuf<N, M, S>::bytes() : 0;
 }
 
-// Chunked solve of many trajectories of this model (batch_scan.cuh): the step
-// tables and chunk maps on the first call (not under stream capture), then
-// the five data-parallel kernels.  MAP_ERR_UNSUPPORTED when the tables do not
-// reach the stationary filter (the caller then keeps the segmented scan).
+// Record of this model for the persistent batch solve (batch_persist.cu):
+// the step tables on the first call (not under stream capture), then the
+// constants of the affine recursions of its trajectories with KB steps per
+// thread, written to out (a host BpModel<S>).  MAP_ERR_UNSUPPORTED when the
+// tables do not reach the stationary filter (the batch then keeps the
+// segmented scan).
 template <int N, int M, typename S>
-map_status batch_linear(map_smoother& h, BatchPlan& bp, const void* y, void* x, cudaStream_t st)
+map_status batch_model(map_smoother& h, void* out, int KB, cudaStream_t st)
 {
     using ST = StepTab<N, S>;
     constexpr int NN = N * N;
-    if (!bp.ready) {
-        if (capturing(st)) return fail(h, MAP_ERR_UNSUPPORTED, "the first batch solve plans its tables: not under capture");
-        if (map_status s = table_plan<N, M, S, false>(h, st); s != MAP_OK) return s;
-        if (!h.tab_conv) return fail(h, MAP_ERR_UNSUPPORTED, "the step tables do not reach the stationary filter");
-        const int ntm = (int)((h.tab_kc + BATCH_CH - 1) / BATCH_CH) + 1;
-        if (ntm > bp.tm_cap) return fail(h, MAP_ERR_UNSUPPORTED, "too many chunk maps before the stationary point");
-        k_batch_chunk_maps<N, S><<<(ntm + 63) / 64, 64, 0, st>>>(h.d_tab, h.tab_kt, ntm, static_cast<S*>(bp.tm));
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(h, e, "chunk map kernel launch");
-        bp.ntm = ntm;
-        bp.ready = true;
-    }
-    BatchArgs<N, M, S> a{};
-    a.y = static_cast<const S*>(y);
-    a.x = static_cast<S*>(x);
-    a.traj = bp.traj;
-    a.chunk_traj = bp.chunk_traj;
-    a.ntraj = bp.ntraj;
-    a.nchunks = bp.nchunks;
-    a.W = static_cast<S*>(bp.W);
-    a.V = static_cast<S*>(bp.V);
-    a.Bt = static_cast<S*>(bp.Bt);
-    a.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off());
-    a.kc = h.tab_kc;
-    a.tm = static_cast<const S*>(bp.tm);
-    a.ntm = bp.ntm;
-    a.prior = prior_of<N, S>(h);
+    if (capturing(st)) return fail(h, MAP_ERR_UNSUPPORTED, "the first batch solve plans its tables: not under capture");
+    if (map_status s = table_plan<N, M, S, false>(h, st); s != MAP_OK) return s;
+    if (!h.tab_conv) return fail(h, MAP_ERR_UNSUPPORTED, "the step tables do not reach the stationary filter");
+    BpModel<S> d{};
+    d.N = N;
+    d.M = M;
+    d.RS = ST::RS;
+    d.oE = ST::oE;
+    d.oO = ST::oO;
+    d.oP = ST::oP;
+    d.kc = h.tab_kc;
+    d.rows = reinterpret_cast<const S*>(h.d_tab + ST::rows_off());
+    d.stats = h.d_stats;
+    S row[ST::RS];
+    cudaError_t e = cudaMemcpy(row, d.rows + d.kc * ST::RS, sizeof(row), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step table read-back");
+    for (int q = 0; q < NN; ++q) d.Einf[q] = row[ST::oE + q];
+    for (int q = 0; q < N; ++q) d.oinf[q] = row[ST::oO + q];
+    // FP64 products: E_inf^KB, A^-1 C, A^-1 b and their products with E_inf
+    const double* E = h.tab_einf;
     const SetupOut& c = h.consts;
+    double P[NN], T2[NN], AiC[NN], Aib[N];
+    for (int q = 0; q < NN; ++q) P[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    for (int s = 0; s < KB; ++s) {
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < N; ++k) acc += P[i * N + k] * E[k * N + j];
+                T2[i * N + j] = acc;
+            }
+        for (int q = 0; q < NN; ++q) P[q] = T2[q];
+    }
     for (int i = 0; i < N; ++i) {
         double ab = 0.0;
         for (int k = 0; k < N; ++k) ab += c.Phi[i * N + k] * c.b[k];
-        a.Aib[i] = S(ab);
-        a.Gr[i] = S(c.Gr[i]);
+        Aib[i] = ab;
         for (int j = 0; j < N; ++j) {
             double ac = 0.0;
             for (int k = 0; k < N; ++k) ac += c.Phi[i * N + k] * c.C[k * N + j];
-            a.AiC[i * N + j] = S(ac);
+            AiC[i * N + j] = ac;
         }
     }
-    for (int i = 0; i < N * M; ++i) a.G[i] = S(c.G[i]);
-    a.ctx = CombineCtx{(float)h.cond_max, h.d_stats};
-    const unsigned gc = (unsigned)((bp.nchunks + 127) / 128), gt = (unsigned)((bp.ntraj + 127) / 128);
-    k_batch_a<N, M, S><<<gc, 128, 0, st>>>(a);
-    k_batch_b<N, M, S><<<gt, 128, 0, st>>>(a);
-    k_batch_c<N, M, S><<<gc, 128, 0, st>>>(a);
-    k_batch_d<N, M, S><<<gt, 128, 0, st>>>(a);
-    k_batch_e<N, M, S><<<gc, 128, 0, st>>>(a);
-    (void)NN;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(h, e, "batch kernel launch");
-    h.launches = 5;
+    for (int i = 0; i < N; ++i) {
+        double eb = 0.0;
+        for (int k = 0; k < N; ++k) eb += E[i * N + k] * Aib[k];
+        d.EAib[i] = S(eb);
+        d.Aib[i] = S(Aib[i]);
+        for (int j = 0; j < N; ++j) {
+            double ec = 0.0;
+            for (int k = 0; k < N; ++k) ec += E[i * N + k] * AiC[k * N + j];
+            d.EAiC[i * N + j] = S(ec);
+            d.AiC[i * N + j] = S(AiC[i * N + j]);
+        }
+    }
+    for (int q = 0; q < NN; ++q) d.PhiK[q] = S(P[q]);
+    for (int q = 0; q < N * M; ++q) d.G[q] = S(c.G[q]);
+    for (int q = 0; q < N; ++q) {
+        d.Gr[q] = S(c.Gr[q]);
+        d.v0[q] = S(c.v0[q]);
+    }
+    *static_cast<BpModel<S>*>(out) = d;
     return MAP_OK;
 }
 
@@ -1322,7 +1334,7 @@ const Ops* linear_ops()
                              &solve_linear_sequential<N, M, S>, &grad_linear<N, M, S>,
                              &solve_linear_seg<N, M, S>, &rts_resident_blocks<N, S, LtiProducer<N, M, S>>,
                              &step_table_bytes<N, S>, &scan_table_bytes<N, M, S>, &dense_linear<N, M, S>,
-                             &batch_linear<N, M, S>};
+                             &batch_model<N, M, S>};
         return &ops;
     } else {
         static const Ops ops{&rts_workspace<N, S>, &solve_linear<N, M, S>, &cost_linear<N, M, S>,

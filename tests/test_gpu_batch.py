@@ -1,5 +1,6 @@
-"""Batched solve (one scan per model with reset elements, one CUDA graph)
-against the FP64 oracle, trajectory by trajectory."""
+"""Batched solve (one launch of the persistent kernel for every model and
+trajectory, in a CUDA graph) against the FP64 oracle, trajectory by
+trajectory."""
 import numpy as np
 import pytest
 
@@ -50,14 +51,13 @@ def test_mixed_batch_matches_oracle_per_trajectory(prec):
     for j in range(len(lengths)):
         ref = oracle.smooth_lti(models[model_of[j]], ys[j], dt)
         assert_traj(xs[j], ref, TOL[prec], (j, lengths[j], dims[j]))
-    for m in range(3):
-        # the chunked solve over the model's step tables (one thread per
-        # chunk of 256 steps, CTAs of 128), or the autotuned segmented scan
-        # when the tables do not converge
-        K, B = mb.tuning(m)
-        assert (K, B) == (256, 128) or (8 <= K <= 64 and B in (32, 64, 128))
-        if prec == "fp32":
-            assert (K, B) == (256, 128)
+    # the persistent kernel over every model's step tables, with an autotuned
+    # (steps per thread, threads per CTA) shared by all models
+    assert mb.persistent()
+    tun = {mb.tuning(m) for m in range(3)}
+    assert len(tun) == 1
+    K, B = tun.pop()
+    assert K in (8, 12, 16) and B in (64, 128)
     # graph replay and re-capture on new arrays give the same states
     first = [x.clone() for x in xdev]
     mb.solve(ydev, xdev)
