@@ -499,6 +499,15 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
             reinterpret_cast<const S*>(h.d_scan + SB::qsuf_off()), KT, g, ttab);
     }
     k_scan_gs<N, M, S><<<1, 32, 0, st>>>(lti_params<N, M, S>(h), mk + kr * N * N, HB ? 1 : 0, gsv);
+    {
+        // powers M^d (d < nt) of the full-tile map after kc for the tile sums
+        double* msq = reinterpret_cast<double*>(h.d_scan + SB::msq_off());
+        int nsq = 1;
+        while ((1 << nsq) < nt) ++nsq;
+        k_scan_msq<N><<<1, 32, 0, st>>>(e64 + kr * N * N, K, B, nsq, msq);
+        k_scan_mpow<N, S><<<(unsigned)((nt + 3) / 4), 128, 0, st>>>(msq, nsq, nt,
+                                                                  reinterpret_cast<S*>(h.d_scan + SB::mp_off()));
+    }
     k_scan_tilemaps<N, M, S><<<(unsigned)(((long)nt * N * N + 127) / 128), 128, 0, st>>>(
         reinterpret_cast<const double*>(h.d_tab + ST::tmap_off()), g, pw, tiles);
     const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;
@@ -611,6 +620,7 @@ map_status run_scan(map_smoother& h, const LtiProducer<N, M, S>& prod, S* x_out,
     sa.gs = reinterpret_cast<const S*>(h.d_scan + SB::gs_off());
     sa.ep = reinterpret_cast<const S*>(h.d_scan + SB::ep_off());
     sa.qsuf = reinterpret_cast<const S*>(h.d_scan + SB::qsuf_off());
+    sa.mp = reinterpret_cast<const S*>(h.d_scan + SB::mp_off());
     sa.pinv = reinterpret_cast<const double*>(h.d_tab + ST::pinv_off());
     const char* tiles = h.d_scan + SB::tiles_off();
     sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));

@@ -574,7 +574,12 @@ struct ScanBuf {
     __host__ __device__ static constexpr size_t ep_off() { return al(gs_off() + sizeof(S) * N * M); }
     // per thread of a tile before kc: Q_t = (Phi_{t+1} ... Phi_{B-1})^T
     __host__ __device__ static constexpr size_t qsuf_off() { return al(ep_off() + sizeof(S) * NN); }
-    __host__ __device__ static constexpr size_t tiles_off() { return al(qsuf_off() + sizeof(S) * jt_max() * BMAX * NN); }
+    // powers M^d (d < NTMAX) of the map M = Phi_inf^B of a full tile after kc,
+    // and its FP64 squares M^(2^l) (l < MSQ) they are formed from
+    static constexpr int MSQ = 10;
+    __host__ __device__ static constexpr size_t mp_off() { return al(qsuf_off() + sizeof(S) * jt_max() * BMAX * NN); }
+    __host__ __device__ static constexpr size_t msq_off() { return al(mp_off() + sizeof(S) * NTMAX * NN); }
+    __host__ __device__ static constexpr size_t tiles_off() { return al(msq_off() + sizeof(double) * MSQ * NN); }
     __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::bytes(NTMAX); }
 };
 
@@ -671,6 +676,63 @@ __global__ void __launch_bounds__(256) k_scan_powers(const double* __restrict__ 
             taff_last[q] = S(Z[q]);
         }
     }
+}
+
+// The squares M^(2^l), l < MSQ, of the map M = E_kc^(K B) of a full tile after
+// kc (FP64, one warp, lane-parallel products)
+template <int N>
+__global__ void __launch_bounds__(32) k_scan_msq(const double* __restrict__ e_kc, int K, int B, int nsq,
+                                                 double* __restrict__ sq)
+{
+    namespace pd = scan_plan_detail;
+    constexpr int NN = N * N;
+    __shared__ double X[NN], Y[NN], Z[NN];
+    const int l = threadIdx.x;
+    for (int q = l; q < NN; q += 32) {
+        X[q] = __ldg(e_kc + q);
+        Y[q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (long e = (long)K * B; e; e >>= 1) {        // Y = E^(K B) by binary powering
+        if (e & 1) {
+            pd::wmul<N>(Y, X, Z);
+            for (int q = l; q < NN; q += 32) Y[q] = Z[q];
+            __syncwarp();
+        }
+        if (e > 1) {
+            pd::wmul<N>(X, X, Z);
+            for (int q = l; q < NN; q += 32) X[q] = Z[q];
+            __syncwarp();
+        }
+    }
+    for (int q = l; q < NN; q += 32) sq[q] = Y[q];
+    __syncwarp();
+    for (int i = 1; i < nsq; ++i) {
+        pd::wmul<N>(sq + (i - 1) * NN, sq + (i - 1) * NN, Z);
+        for (int q = l; q < NN; q += 32) sq[i * NN + q] = Z[q];
+        __syncwarp();
+    }
+}
+
+// M^d for d < nt from the squares, one warp per d (FP64, lane-parallel), in S
+template <int N, typename S>
+__global__ void __launch_bounds__(128) k_scan_mpow(const double* __restrict__ sq, int nsq, int nt, S* __restrict__ mp)
+{
+    namespace pd = scan_plan_detail;
+    constexpr int NN = N * N;
+    __shared__ double P[4][NN], Z[4][NN];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int d = blockIdx.x * 4 + w;
+    if (d >= nt) return;                                    // warp-uniform
+    for (int q = l; q < NN; q += 32) P[w][q] = q % (N + 1) == 0 ? 1.0 : 0.0;
+    __syncwarp();
+    for (int i = 0; i < nsq; ++i)
+        if ((d >> i) & 1) {
+            pd::wmul<N>(P[w], sq + i * NN, Z[w]);
+            for (int q = l; q < NN; q += 32) P[w][q] = Z[w][q];
+            __syncwarp();
+        }
+    for (int q = l; q < NN; q += 32) mp[(long)d * NN + q] = S(P[w][q]);
 }
 
 // Tile maps E_j (the composition of a tile's per-step closed-loop maps) as
@@ -792,6 +854,7 @@ struct ScanArgs {
     const S* mk;            // per-step -E_k^T P_k Bb (steps before kc; offsets depending on the sample)
     const S* ep;            // E_inf^nv of the last tile's partial thread
     const S* qsuf;          // suffix products of the thread maps of the tiles before kc
+    const S* mp;            // M^d, M = Phi_inf^B the map of a full tile after kc
     const double* pinv;     // P_T^-1 (FP64)
     ScanGeom g;
     int has_b;              // b != 0: the A^-1 b term of g_k
@@ -888,6 +951,133 @@ __device__ __forceinline__ void reverse_vec(S (&v)[N], S* scratch)
     __syncthreads();
 }
 
+// Tile sums of the tiled scan (item (5) of lti_fold.cuh) with the powers of
+// the full-tile map after kc: every full tile j >= Jt has the map
+// M = Phi_inf^B, so Pi(a, b) = M^(b - a) for Jt <= a <= b <= nt - 1, and a
+// product reaching back before Jt splits as Pi(a, b) = Pi(a, Jt) M^(b - Jt).
+// Only the products among the first Jt + 1 tiles come from the product tables;
+// the rest read the power table M^d (one small table shared by every tile).
+//
+// The value function's v before tile `tile` (in vout, thread 0):
+//   v_j = Pi(0, j)^T v_0 + sum_{i<j} Pi(i+1, j)^T w_i.
+// Terms i = t - 1 + u B (i = -1: v_0); at most 5 per thread (nt <= 4 B + 1),
+// their operands loaded first.
+template <int N, typename S>
+__device__ __forceinline__ void scan_tile_prefix(const S* __restrict__ qt, const S* __restrict__ mp,
+                                                 const S* __restrict__ w, int tile, int Jt, const S (&v0)[N],
+                                                 S* red, S (&vout)[N])
+{
+    using TT = TileTables<N, 1, S>;                     // qt_index does not depend on M
+    constexpr int NN = N * N, UMAX = 5;
+    const int t = threadIdx.x;
+    if (tile == 0) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) vout[a] = v0[a];
+        return;
+    }
+    S v[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) v[a] = S(0);
+    // a term before min(tile, Jt) goes through Pi(i+1, jb)^T with jb = min(tile, Jt),
+    // then (M^(tile - jb))^T; a later one through (M^(tile-1-i))^T alone
+    const int jb = min(tile, Jt);
+    S Pl[NN];
+    if (tile > jb) load_run_aligned<NN, S>(mp + (long)(tile - jb) * NN, Pl);
+#pragma unroll 1
+    for (int u = 0; u < UMAX; ++u) {
+        const int i = t - 1 + u * (int)blockDim.x;
+        if (i >= tile) break;
+        S wv[N], p[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) wv[c] = i < 0 ? v0[c] : w[(long)i * N + c];
+        S Q[NN];
+        if (i < jb) {
+            load_run_aligned<NN, S>(qt + TT::qt_index(jb, i + 1) * NN, Q);     // Pi(i+1, jb)^T
+            mat_vec<N, S>(Q, wv, p);
+            if (tile > jb) {
+                mat_tvec<N, S>(Pl, p, wv);
+#pragma unroll
+                for (int c = 0; c < N; ++c) p[c] = wv[c];
+            }
+        } else {
+            load_run_aligned<NN, S>(mp + (long)(tile - 1 - i) * NN, Q);        // M^(tile-1-i)
+            mat_tvec<N, S>(Q, wv, p);
+        }
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] += p[c];
+    }
+    block_vec_sum<N, S>(v, red);
+#pragma unroll
+    for (int a = 0; a < N; ++a) vout[a] = v[a];
+}
+
+// The state at the end of tile `tile` (thread 0 writes it to xe; ends with a
+// barrier): x_T for the last tile, else
+//   x_end(j) = Pi(j+1, nt-1) x_L + sum_{i=j+1}^{nt-2} Pi(j+1, i) beta_i,
+// x_L the last tile's map applied to x_T and beta_i the offset of tile i's map.
+template <int N, typename S>
+__device__ __forceinline__ void scan_tile_suffix(const S* __restrict__ pi, const S* __restrict__ mp,
+                                                 const S* __restrict__ tile_aff, int tile, int nt, int Jt,
+                                                 const S* xT, S* red, S* xe)
+{
+    using TT = TileTables<N, 1, S>;
+    constexpr int NN = N * N, NA = Aff<N, S>::NCOMP, UMAX = 5;
+    const int t = threadIdx.x;
+    if (tile + 1 == nt) {
+        if (t == 0)
+#pragma unroll
+            for (int i = 0; i < N; ++i) xe[i] = xT[i];
+        __syncthreads();
+        return;
+    }
+    S v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = S(0);
+    // a term past ib = max(tile + 1, Jt) goes through M^(i - ib), then, when
+    // tile + 1 < ib, through Pi(tile+1, ib); an earlier one through Pi(tile+1, i)
+    const int a0 = tile + 1, ib = min(max(a0, Jt), nt - 1);
+    S Pf[NN];
+    if (a0 < ib) load_run_aligned<NN, S>(pi + TT::pi_index(nt, a0, ib) * NN, Pf);
+#pragma unroll 1
+    for (int uu = 0; uu < UMAX; ++uu) {
+        const int i = a0 + t + uu * (int)blockDim.x;
+        if (i >= nt) break;
+        S u[N], p[N];
+        if (i + 1 == nt) {
+            Aff<N, S> a;
+#pragma unroll
+            for (int c = 0; c < NA; ++c) comp(a, c) = tile_aff[(long)i * NA + c];
+            S x[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) x[c] = xT[c];
+            affine_apply<N, S>(a, x, u);
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) u[c] = tile_aff[(long)i * NA + NN + c];
+        }
+        S Q[NN];
+        if (i < ib) {
+            load_run_aligned<NN, S>(pi + TT::pi_index(nt, a0, i) * NN, Q);      // Pi(tile+1, i)
+            mat_vec<N, S>(Q, u, p);
+        } else {
+            load_run_aligned<NN, S>(mp + (long)(i - ib) * NN, Q);               // M^(i - ib)
+            mat_vec<N, S>(Q, u, p);
+            if (a0 < ib) {
+                mat_vec<N, S>(Pf, p, u);
+#pragma unroll
+                for (int c = 0; c < N; ++c) p[c] = u[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] += p[c];
+    }
+    block_vec_sum<N, S>(v, red);
+    if (t == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) xe[i] = v[i];
+    __syncthreads();
+}
+
 // The tiled-scan solve, one CTA of 128 threads per tile, all tiles
 // co-resident (cooperative launch), three phases separated by two grid
 // barriers:
@@ -957,14 +1147,9 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
             if (ybulk > 0) bulk_copy_g2s(ys, prod.y + yoff, (unsigned)(sizeof(S) * ybulk), bar);
             if (tbytes)
                 bulk_copy_g2s(tb, trans ? sa.ttab + (long)tile * B * (g.Kt * CT + 2 * NN) : sa.pw, tbytes, bar);
-            // the tile-product rows that the tile prefix and suffix sums read
-            // after the grid barriers (data-independent): into L2 now
-            using TT1 = TileTables<N, 1, S>;
-            if (tile > 0)
-                bulk_prefetch_l2(sa.qt + TT1::qt_index(tile, 0) * NN, (unsigned)(sizeof(S) * (size_t)(tile + 1) * NN));
-            if (tile + 1 < g.nt)
-                bulk_prefetch_l2(sa.pi + TT1::pi_index(g.nt, tile + 1, tile + 1) * NN,
-                                 (unsigned)(sizeof(S) * (size_t)(g.nt - tile - 1) * NN));
+            // the power table that the tile prefix and suffix sums read after
+            // the grid barriers (data-independent, the same for every tile): into L2 now
+            if (tile == 0) bulk_prefetch_l2(sa.mp, (unsigned)(sizeof(S) * (size_t)g.nt * NN));
         }
         for (long q = ybulk + t; q < ycnt; q += B) ys[q] = q < yhave ? prod.y[yoff + q] : S(0);
         // constants of the steps after kc (row kc; only read by threads with steps)
@@ -1152,17 +1337,12 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         // thread RTS maps and the tile's RTS map
         S v[N];
         {
-            LtiTiles<S> lt{};
-            lt.qt = sa.qt;
-            lt.pi = sa.pi;
-            lt.w = sa.w;
-            lt.P = sa.pdummy;
-            Red<N, S> pin;
-            lti_tile_prefix_sum<N, S>(lt, tile, g.nt, prior, red, pin);
+            S pv[N];
+            scan_tile_prefix<N, S>(sa.qt, sa.mp, sa.w, tile, g.Jt, prior.v, red, pv);
             S* vt = wt + 2 * (B / 32) * N;
             if (t == 0)
 #pragma unroll
-                for (int a = 0; a < N; ++a) vt[a] = pin.v[a];
+                for (int a = 0; a < N; ++a) vt[a] = pv[a];
             __syncthreads();
             S vtile[N];
 #pragma unroll
@@ -1345,13 +1525,8 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         // ---- phase 3: tile suffix, thread end states, per-step states, bulk store
         S x[N];
         {
-            LtiTiles<S> lt{};
-            lt.pi = sa.pi;
-            lt.qt = sa.qt;
-            lt.w = sa.w;
-            lt.P = sa.pdummy;
             S* xe_sh = red + (B / 32) * (NA + N);
-            lti_tile_suffix_sum<N, S>(lt, sa.taff, tile, g.nt, xT, red, xe_sh);
+            scan_tile_suffix<N, S>(sa.pi, sa.mp, sa.taff, tile, g.nt, g.Jt, xT, red, xe_sh);
             if (powers) {
                 // state at thread tp's start (tp = B: the tile's end state)
                 S* xs = wt + 2 * (B / 32) * N;
