@@ -510,9 +510,11 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     }
     k_scan_tilemaps<N, M, S><<<(unsigned)(((long)nt * N * N + 127) / 128), 128, 0, st>>>(
         reinterpret_cast<const double*>(h.d_tab + ST::tmap_off()), g, pw, tiles);
-    const int segs = (nt + TT::PI_SEG - 1) / TT::PI_SEG;
-    k_lti_segments<N, M, S><<<(nt + 127) / 128, 128, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
-    k_lti_products<N, M, S><<<dim3((segs + 7) / 8, (nt + 3) / 4), 32, 0, st>>>(nt, reinterpret_cast<S*>(tiles));
+    {
+        // the tile-map products among the tiles up to Jt (the later ones take powers)
+        const int J1 = std::min(Jt, nt - 1), np = (J1 + 1) * (J1 + 2) / 2;
+        k_scan_tprod<N, M, S><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(nt, J1, tiles);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "scan table kernel launch");
     h.sc_K = K;

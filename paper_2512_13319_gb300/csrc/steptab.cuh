@@ -714,6 +714,44 @@ __global__ void __launch_bounds__(32) k_scan_msq(const double* __restrict__ e_kc
     }
 }
 
+// Products Pi(a, b) = E_a ... E_{b-1} of the tile maps among the tiles up to
+// J1 = min(Jt, nt - 1) (0 <= a <= b <= J1), the only ones the tile sums of the
+// tiled scan read (the later tiles share one map and take its powers), with
+// their transposes: one thread per pair, from the tile table F_j = E_j^T.
+template <int N, int M, typename S>
+__global__ void __launch_bounds__(128) k_scan_tprod(int nt, int J1, char* __restrict__ tiles)
+{
+    using TT = TileTables<N, M, S>;
+    namespace pd = products_detail;
+    constexpr int NN = N * N;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    // pair p -> (a, b) with b = a .. J1, rows a = 0 .. J1
+    int a = 0, q = p;
+    while (a <= J1 && q > J1 - a) {
+        q -= J1 - a + 1;
+        ++a;
+    }
+    if (a > J1) return;
+    const int b = a + q;
+    const S* F = reinterpret_cast<const S*>(tiles + TT::f_off(nt));
+    S P[NN];
+#pragma unroll
+    for (int r = 0; r < NN; ++r) P[r] = r % (N + 1) == 0 ? S(1) : S(0);
+#pragma unroll 1
+    for (int j = a; j < b; ++j) {
+        S E[NN];
+        pd::load_E<N>(F, j, E);
+        pd::mul<N>(P, E);
+    }
+    S* pi = reinterpret_cast<S*>(tiles + TT::pi_off(nt)) + TT::pi_index(nt, a, b) * NN;
+    S* qt = reinterpret_cast<S*>(tiles + TT::qt_off(nt)) + TT::qt_index(b, a) * NN;
+#pragma unroll
+    for (int r = 0; r < NN; ++r) {
+        pi[r] = P[r];
+        qt[r] = P[(r % N) * N + r / N];
+    }
+}
+
 // M^d for d < nt from the squares, one warp per d (FP64, lane-parallel), in S
 template <int N, typename S>
 __global__ void __launch_bounds__(128) k_scan_mpow(const double* __restrict__ sq, int nsq, int nt, S* __restrict__ mp)
