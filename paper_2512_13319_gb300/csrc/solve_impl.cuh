@@ -513,7 +513,9 @@ map_status scan_plan(map_smoother& h, cudaStream_t st)
     {
         // the tile-map products among the tiles up to Jt (the later ones take powers)
         const int J1 = std::min(Jt, nt - 1), np = (J1 + 1) * (J1 + 2) / 2;
-        k_scan_tprod<N, M, S><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(nt, J1, tiles);
+        k_scan_tprod<N, M, S><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(
+            nt, J1, tiles, (int)(SB::jt_max() + 1), reinterpret_cast<S*>(h.d_scan + SB::tpi_off()),
+            reinterpret_cast<S*>(h.d_scan + SB::tqt_off()));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "scan table kernel launch");
@@ -625,9 +627,9 @@ map_status run_scan(map_smoother& h, const LtiProducer<N, M, S>& prod, S* x_out,
     sa.mp = reinterpret_cast<const S*>(h.d_scan + SB::mp_off());
     sa.pinv = reinterpret_cast<const double*>(h.d_tab + ST::pinv_off());
     const char* tiles = h.d_scan + SB::tiles_off();
-    sa.pi = reinterpret_cast<const S*>(tiles + TT::pi_off(snt));
-    sa.qt = reinterpret_cast<const S*>(tiles + TT::qt_off(snt));
-    sa.pdummy = reinterpret_cast<const S*>(tiles + TT::p_off());
+    sa.pi = reinterpret_cast<const S*>(h.d_scan + SB::tpi_off());
+    sa.qt = reinterpret_cast<const S*>(h.d_scan + SB::tqt_off());
+    sa.tld = (int)(SB::jt_max() + 1);
     const SetupOut& c = h.consts;
     sa.has_b = 0;
     for (int i = 0; i < N; ++i) sa.has_b |= c.b[i] != 0.0;

@@ -557,7 +557,7 @@ struct ScanGeom {
 // tables of lti_fold.cuh (TileTables: F_j = E_j^T and the products Pi).
 template <int N, int M, typename S>
 struct ScanBuf {
-    static constexpr int NN = N * N, BMAX = 128, NTMAX = 4 * BMAX + 1;
+    static constexpr int NN = N * N, BMAX = 128, NTMAX = 5 * BMAX;
     static constexpr int CT = NN + N;                         // E, o
     using ST = StepTab<N, S>;
     __host__ __device__ static constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -579,8 +579,14 @@ struct ScanBuf {
     static constexpr int MSQ = 10;
     __host__ __device__ static constexpr size_t mp_off() { return al(qsuf_off() + sizeof(S) * jt_max() * BMAX * NN); }
     __host__ __device__ static constexpr size_t msq_off() { return al(mp_off() + sizeof(S) * NTMAX * NN); }
-    __host__ __device__ static constexpr size_t tiles_off() { return al(msq_off() + sizeof(double) * MSQ * NN); }
-    __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::bytes(NTMAX); }
+    // products Pi(a, b) of the tile maps among the tiles up to jt_max(), and
+    // their transposes, entry (a, b) at a (jt_max() + 1) + b
+    __host__ __device__ static constexpr long tp_count() { return (jt_max() + 1) * (jt_max() + 1); }
+    __host__ __device__ static constexpr size_t tpi_off() { return al(msq_off() + sizeof(double) * MSQ * NN); }
+    __host__ __device__ static constexpr size_t tqt_off() { return al(tpi_off() + sizeof(S) * tp_count() * NN); }
+    __host__ __device__ static constexpr size_t tiles_off() { return al(tqt_off() + sizeof(S) * tp_count() * NN); }
+    // the tile tables (TileTables: the tile maps F_j), without the products
+    __host__ __device__ static constexpr size_t bytes() { return tiles_off() + TileTables<N, M, S>::pi_off(NTMAX); }
 };
 
 namespace scan_plan_detail {
@@ -717,9 +723,11 @@ __global__ void __launch_bounds__(32) k_scan_msq(const double* __restrict__ e_kc
 // Products Pi(a, b) = E_a ... E_{b-1} of the tile maps among the tiles up to
 // J1 = min(Jt, nt - 1) (0 <= a <= b <= J1), the only ones the tile sums of the
 // tiled scan read (the later tiles share one map and take its powers), with
-// their transposes: one thread per pair, from the tile table F_j = E_j^T.
+// their transposes (entry (a, b) at a ld + b): one thread per pair, from the
+// tile table F_j = E_j^T.
 template <int N, int M, typename S>
-__global__ void __launch_bounds__(128) k_scan_tprod(int nt, int J1, char* __restrict__ tiles)
+__global__ void __launch_bounds__(128) k_scan_tprod(int nt, int J1, const char* __restrict__ tiles, int ld,
+                                                   S* __restrict__ tpi, S* __restrict__ tqt)
 {
     using TT = TileTables<N, M, S>;
     namespace pd = products_detail;
@@ -743,8 +751,8 @@ __global__ void __launch_bounds__(128) k_scan_tprod(int nt, int J1, char* __rest
         pd::load_E<N>(F, j, E);
         pd::mul<N>(P, E);
     }
-    S* pi = reinterpret_cast<S*>(tiles + TT::pi_off(nt)) + TT::pi_index(nt, a, b) * NN;
-    S* qt = reinterpret_cast<S*>(tiles + TT::qt_off(nt)) + TT::qt_index(b, a) * NN;
+    S* pi = tpi + ((long)a * ld + b) * NN;
+    S* qt = tqt + ((long)a * ld + b) * NN;
 #pragma unroll
     for (int r = 0; r < NN; ++r) {
         pi[r] = P[r];
@@ -885,9 +893,9 @@ struct ScanArgs {
     const S* phit;          // K_t-step thread maps before kc
     S* w;                   // tile offsets of the filter maps
     S* taff;                // tile RTS maps
-    const S* pi;            // tile-map products (TileTables)
-    const S* qt;
-    const S* pdummy;        // a readable P_j table for the tile-prefix helper (its P is not used)
+    const S* pi;            // tile-map products Pi(a, b) among the tiles up to Jt, entry a tld + b
+    const S* qt;            // their transposes, entry a tld + b holding Pi(a, b)^T
+    int tld;
     const S* gs;            // measurement gain of the steps after kc (with the sample's share of o)
     const S* mk;            // per-step -E_k^T P_k Bb (steps before kc; offsets depending on the sample)
     const S* ep;            // E_inf^nv of the last tile's partial thread
@@ -1001,11 +1009,10 @@ __device__ __forceinline__ void reverse_vec(S (&v)[N], S* scratch)
 // Terms i = t - 1 + u B (i = -1: v_0); at most 5 per thread (nt <= 4 B + 1),
 // their operands loaded first.
 template <int N, typename S>
-__device__ __forceinline__ void scan_tile_prefix(const S* __restrict__ qt, const S* __restrict__ mp,
+__device__ __forceinline__ void scan_tile_prefix(const S* __restrict__ qt, int ld, const S* __restrict__ mp,
                                                  const S* __restrict__ w, int tile, int Jt, const S (&v0)[N],
                                                  S* red, S (&vout)[N])
 {
-    using TT = TileTables<N, 1, S>;                     // qt_index does not depend on M
     constexpr int NN = N * N, UMAX = 5;
     const int t = threadIdx.x;
     if (tile == 0) {
@@ -1030,7 +1037,7 @@ __device__ __forceinline__ void scan_tile_prefix(const S* __restrict__ qt, const
         for (int c = 0; c < N; ++c) wv[c] = i < 0 ? v0[c] : w[(long)i * N + c];
         S Q[NN];
         if (i < jb) {
-            load_run_aligned<NN, S>(qt + TT::qt_index(jb, i + 1) * NN, Q);     // Pi(i+1, jb)^T
+            load_run_aligned<NN, S>(qt + ((long)(i + 1) * ld + jb) * NN, Q);    // Pi(i+1, jb)^T
             mat_vec<N, S>(Q, wv, p);
             if (tile > jb) {
                 mat_tvec<N, S>(Pl, p, wv);
@@ -1054,11 +1061,10 @@ __device__ __forceinline__ void scan_tile_prefix(const S* __restrict__ qt, const
 //   x_end(j) = Pi(j+1, nt-1) x_L + sum_{i=j+1}^{nt-2} Pi(j+1, i) beta_i,
 // x_L the last tile's map applied to x_T and beta_i the offset of tile i's map.
 template <int N, typename S>
-__device__ __forceinline__ void scan_tile_suffix(const S* __restrict__ pi, const S* __restrict__ mp,
+__device__ __forceinline__ void scan_tile_suffix(const S* __restrict__ pi, int ld, const S* __restrict__ mp,
                                                  const S* __restrict__ tile_aff, int tile, int nt, int Jt,
                                                  const S* xT, S* red, S* xe)
 {
-    using TT = TileTables<N, 1, S>;
     constexpr int NN = N * N, NA = Aff<N, S>::NCOMP, UMAX = 5;
     const int t = threadIdx.x;
     if (tile + 1 == nt) {
@@ -1075,7 +1081,7 @@ __device__ __forceinline__ void scan_tile_suffix(const S* __restrict__ pi, const
     // tile + 1 < ib, through Pi(tile+1, ib); an earlier one through Pi(tile+1, i)
     const int a0 = tile + 1, ib = min(max(a0, Jt), nt - 1);
     S Pf[NN];
-    if (a0 < ib) load_run_aligned<NN, S>(pi + TT::pi_index(nt, a0, ib) * NN, Pf);
+    if (a0 < ib) load_run_aligned<NN, S>(pi + ((long)a0 * ld + ib) * NN, Pf);
 #pragma unroll 1
     for (int uu = 0; uu < UMAX; ++uu) {
         const int i = a0 + t + uu * (int)blockDim.x;
@@ -1095,7 +1101,7 @@ __device__ __forceinline__ void scan_tile_suffix(const S* __restrict__ pi, const
         }
         S Q[NN];
         if (i < ib) {
-            load_run_aligned<NN, S>(pi + TT::pi_index(nt, a0, i) * NN, Q);      // Pi(tile+1, i)
+            load_run_aligned<NN, S>(pi + ((long)a0 * ld + i) * NN, Q);          // Pi(tile+1, i)
             mat_vec<N, S>(Q, u, p);
         } else {
             load_run_aligned<NN, S>(mp + (long)(i - ib) * NN, Q);               // M^(i - ib)
@@ -1376,7 +1382,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         S v[N];
         {
             S pv[N];
-            scan_tile_prefix<N, S>(sa.qt, sa.mp, sa.w, tile, g.Jt, prior.v, red, pv);
+            scan_tile_prefix<N, S>(sa.qt, sa.tld, sa.mp, sa.w, tile, g.Jt, prior.v, red, pv);
             S* vt = wt + 2 * (B / 32) * N;
             if (t == 0)
 #pragma unroll
@@ -1564,7 +1570,7 @@ k_lti_scan(const __grid_constant__ Prod prod, const Red<N, S> prior, S* __restri
         S x[N];
         {
             S* xe_sh = red + (B / 32) * (NA + N);
-            scan_tile_suffix<N, S>(sa.pi, sa.mp, sa.taff, tile, g.nt, g.Jt, xT, red, xe_sh);
+            scan_tile_suffix<N, S>(sa.pi, sa.tld, sa.mp, sa.taff, tile, g.nt, g.Jt, xT, red, xe_sh);
             if (powers) {
                 // state at thread tp's start (tp = B: the tile's end state)
                 S* xs = wt + 2 * (B / 32) * N;
