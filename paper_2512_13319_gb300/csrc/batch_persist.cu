@@ -134,6 +134,16 @@ __device__ __forceinline__ int padded(int e, float inv)
     return e + (int)(((float)e + 0.5f) * inv);
 }
 
+// start bringing the whole 16-byte words of [p, p + bytes) into L2 (a later
+// block's observations; nothing waits for it)
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes)
+{
+    const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+    const unsigned long long lo = (a + 15ull) & ~15ull, hi = (a + bytes) & ~15ull;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 template <typename S, int B>
 __device__ __forceinline__ void stage_in(const S* __restrict__ g, int cnt, S* sm, float inv)
 {
@@ -355,6 +365,8 @@ __device__ void traj(const BpArgs<S>& a, const BpModel<S>* __restrict__ md, cons
         const long b0 = (long)b * BS;
         const int cnt = (int)min(BS, L - b0);
         __syncthreads();                               // the block before is done with ys
+        if (t == 0 && b + 1 < nb)                      // the next block's observations into L2
+            prefetch_l2(y + (b0 + BS) * M, sizeof(S) * (size_t)min(BS, L - b0 - BS) * M);
         stage_in<S, B>(y + b0 * M, cnt * M, ys, yinv);
         __syncthreads();
         const long k0 = b0 + (long)t * KB;
@@ -424,6 +436,8 @@ __device__ void traj(const BpArgs<S>& a, const BpModel<S>* __restrict__ md, cons
         const long b0 = (long)b * BS;
         const int cnt = (int)min(BS, L - b0);
         __syncthreads();                               // the block after is stored, bc read
+        if (t == 0 && b > 0)                           // the previous block's observations into L2
+            prefetch_l2(y + (b0 - BS) * M, sizeof(S) * (size_t)BS * M);
         stage_in<S, B>(y + b0 * M, cnt * M, ys, yinv);
         __syncthreads();
         const long k0 = b0 + (long)t * KB;
