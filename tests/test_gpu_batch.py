@@ -106,3 +106,33 @@ def test_full_batch_4096_trajectories_sampled():
         ref = oracle.smooth_lti(models[model_of[j]], ys[j], dt)
         assert_traj(xs[j], ref, TOL["fp32"], (j, lengths[j]))
     mb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_every_state_shape_matches_oracle(prec):
+    """One batch over every (nx, ny) the batch kernel is built for: OU models
+    with (3, 1) and (5, 2) beside Wiener velocity (2, 1), (4, 2) and (6, 3),
+    ragged lengths across several blocks of the kernel and a block boundary
+    +- 1, each trajectory against the oracle."""
+    from paper_2512_13319_gb300.batch import MapBatch
+    dt = 0.01
+    models = [synth.wiener_velocity(1), synth.ou_model(3, 1, seed=11), synth.wiener_velocity(2),
+              synth.ou_model(5, 2, seed=12), synth.wiener_velocity(3)]
+    rng = np.random.default_rng(21)
+    lengths = np.concatenate([[1, 5, 1535, 1536, 1537, 3072, 4097, 9000],
+                              rng.integers(1, 6000, size=12)]).astype(np.int64)
+    model_of = np.arange(len(lengths)) % len(models)
+    ys = []
+    for j, L in enumerate(lengths):
+        _, y = synth.simulate(models[model_of[j]], int(L), dt, seed=300 + j, substeps=1)
+        ys.append(y)
+    mb = MapBatch(models, lengths, model_of, [dt] * len(models), precision=prec)
+    ydev = mb.pack_observations(ys)
+    xdev = mb.empty_outputs()
+    mb.solve(ydev, xdev)
+    torch.cuda.synchronize()
+    xs = mb.unpack_states(xdev)
+    for j in range(len(lengths)):
+        ref = oracle.smooth_lti(models[model_of[j]], ys[j], dt)
+        assert_traj(xs[j], ref, TOL[prec], (j, int(lengths[j]), models[model_of[j]].nx))
+    mb.close()
