@@ -46,6 +46,17 @@ __device__ __forceinline__ int lvl_off(int B, int d) { return 2 * B - ((2 * B) >
 
 __device__ __forceinline__ int ilog2(int B) { return 31 - __clz(B); }
 
+// copy of cnt scalars (a multiple of 16 bytes, both ends 16-byte aligned) by
+// all threads of the block, 16 bytes at a time
+template <typename S>
+__device__ __forceinline__ void block_copy16(S* __restrict__ dst, const S* __restrict__ src, long cnt)
+{
+    const long n16 = cnt * (long)sizeof(S) / 16;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (long i = threadIdx.x; i < n16; i += blockDim.x) d4[i] = s4[i];
+}
+
 // vectorised copy of a contiguous run of CNT scalars (16-byte aligned endpoints)
 template <int CNT, typename S>
 __device__ __forceinline__ void store_run(S* __restrict__ dst, const S* src)
@@ -713,7 +724,8 @@ template <int N, typename S, class Prod>
 __device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, int K, const S* __restrict__ thr_agg,
                                                    const Red<N, S>& pin, const LtiTiles<S>& lt,
                                                    bool use_leaf, const S (&leaf)[2 * N], S* nodes,
-                                                   const CombineCtx& ctx, Red<N, S>& X)
+                                                   const CombineCtx& ctx, Red<N, S>& X,
+                                                   const S* __restrict__ tree = nullptr)
 {
     const int B = blockDim.x, t = threadIdx.x;
     const long gthr = (long)tile * B + t;
@@ -741,12 +753,17 @@ __device__ __forceinline__ void tile_thread_prefix(const Prod& prod, int tile, i
             return;
         }
     }
-    {
+    if (tree) {
+        // the up-sweep tree that the reduce kernel built from the same leaves
+        __syncthreads();                   // the tile prefix is done with the nodes
+        block_copy16<S>(nodes, tree, (long)2 * B * CoopLayout<N, S>::NE);
+        __syncthreads();
+    } else {
         Elem<N, S> G;
         wi_load(thr_agg, gthr, G);
         node_store(G, slot<N, S>(nodes, B, 0, t));
+        coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
     }
-    coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
     coop_elem_down<N, S>(nodes, scratch_of<N, S>(nodes), pin, ctx, X);
 }
 
@@ -914,7 +931,7 @@ k_filter_reduce_lti(const __grid_constant__ Prod prod, int K, S* __restrict__ th
 template <int N, typename S, class Prod>
 __global__ void __launch_bounds__(128, (Prod::LINEAR_FOLD ? (N <= 6 ? 3 : 1) : (N <= 4 ? 3 : 1)))
 k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
-                S* __restrict__ tile_agg, S* __restrict__ terminal_out, CombineCtx ctx)
+                S* __restrict__ tile_agg, S* __restrict__ terminal_out, CombineCtx ctx, S* __restrict__ trees)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* nodes = reinterpret_cast<S*>(smem_raw);
@@ -946,6 +963,9 @@ k_filter_reduce(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_ag
     wi_store(thr_agg, gthr, G);
     node_store(G, slot<N, S>(nodes, B, 0, t));
     coop_elem_up<N, S>(nodes, scratch_of<N, S>(nodes), ctx);
+    if (trees)                             // the tile's tree, for the down-sweep to reuse
+        block_copy16<S>(trees + (long)blockIdx.x * 2 * B * CoopLayout<N, S>::NE, nodes,
+                        (long)2 * B * CoopLayout<N, S>::NE);
     if (t == 0) {
         Elem<N, S> root;
         node_load(slot<N, S>(nodes, B, ilog2(B), 0), root);
@@ -1058,7 +1078,7 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
               const S* __restrict__ tile_agg, const Red<N, S> prior, const S* __restrict__ prior_dev,
               S* __restrict__ Eg, S* __restrict__ thr_aff, S* __restrict__ tile_aff, S* __restrict__ filt_out,
               CombineCtx ctx, const LtiTiles<S> lt, S* __restrict__ final_out, S* __restrict__ xT_out,
-              S* __restrict__ filtT_out, const S* __restrict__ group_agg)
+              S* __restrict__ filtT_out, const S* __restrict__ group_agg, const S* __restrict__ trees)
 {
     const S* __restrict__ fold = lt.fold;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1081,7 +1101,8 @@ k_filter_down(const __grid_constant__ Prod prod, int K, S* __restrict__ thr_agg,
         lti_tile_prefix<N, S>(lt, tile, prior, nodes, pin);
     else
         tile_prefix_of<N, S>(tile_agg, tile, scan_prior(prior, prior_dev), nodes, ctx, pin, group_agg);
-    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, lt, last_lti, leaf, nodes, ctx, X);
+    tile_thread_prefix<N, S>(prod, tile, K, thr_agg, pin, lt, last_lti, leaf, nodes, ctx, X,
+                             trees && !fold ? trees + (long)tile * 2 * B * CoopLayout<N, S>::NE : nullptr);
 
     Aff<N, S> comp_t;
     filter_steps<N, S>(prod, K, k0, gthr, X, Eg, filt_out, ctx, comp_t,

@@ -24,10 +24,12 @@ inline int ilog2_host(int x)
 
 template <int N, typename S>
 struct Layout {
-    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, group_agg, total;
+    size_t thr_agg, tile_agg, fin, Eg, thr_aff, tile_aff, filt_ws, term, group_agg, trees, total;
     // filt_ws (the forward filter values of the two-filter smoother) only when
-    // two_filter; Eg (the closed-loop maps) always (RTS pass, sequential baseline)
-    static Layout make(long nthr, long nt, long Tpad, bool two_filter)
+    // two_filter; Eg (the closed-loop maps) always (RTS pass, sequential baseline);
+    // trees (each tile's up-sweep tree, kept by the reduce kernel for the
+    // down-sweep) only when asked (nonlinear models)
+    static Layout make(long nthr, long nt, long Tpad, bool two_filter, bool trees = false)
     {
         const long B = nt > 0 ? nthr / nt : 0;
         using E = Elem<N, S>;
@@ -45,6 +47,7 @@ struct Layout {
         l.term = o;      o = align_up(o + sizeof(S) * R::NCOMP);
         const long ng = B > 0 ? (nt + prefix_group_tiles((int)B) - 1) / prefix_group_tiles((int)B) : 0;
         l.group_agg = o; o = align_up(o + sizeof(S) * E::NCOMP * ng);
+        l.trees = o;     o = align_up(o + (trees ? sizeof(S) * 2 * CoopLayout<N, S>::NE * nthr : 0));
         l.total = o;
         return l;
     }
@@ -112,7 +115,8 @@ LtiParams<N, M, S> lti_params(const map_smoother& h)
 template <int N, typename S>
 size_t rts_workspace(const map_smoother& h)
 {
-    return Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad, h.smoother == MAP_TWO_FILTER).total;
+    return Layout<N, S>::make((long)h.nt * h.B, h.nt, h.Tpad, h.smoother == MAP_TWO_FILTER,
+                              h.model != MAP_MODEL_LINEAR).total;
 }
 
 // CTAs of B threads of the filter kernels of `Prod` resident on one SM
@@ -172,13 +176,16 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     using R = Red<N, S>;
     const int B = h.B, nt = h.nt, K = h.K;
     const long nthr = (long)nt * B;
-    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad, h.smoother == MAP_TWO_FILTER);
+    const bool keep_trees = h.model != MAP_MODEL_LINEAR;
+    const Layout<N, S> L = Layout<N, S>::make(nthr, nt, h.Tpad, h.smoother == MAP_TWO_FILTER, keep_trees);
     S* thr_agg = reinterpret_cast<S*>(h.ws + L.thr_agg);
     S* tile_agg = reinterpret_cast<S*>(h.ws + L.tile_agg);
     S* fin = reinterpret_cast<S*>(h.ws + L.fin);
     S* Eg = reinterpret_cast<S*>(h.ws + L.Eg);
     S* thr_aff = reinterpret_cast<S*>(h.ws + L.thr_aff);
     S* tile_aff = reinterpret_cast<S*>(h.ws + L.tile_aff);
+    // the reduce kernel keeps each tile's up-sweep tree for the down-sweep
+    S* trees = keep_trees ? reinterpret_cast<S*>(h.ws + L.trees) : nullptr;
     const CombineCtx ctx{(float)h.cond_max, h.d_stats};
     const long T = h.T;
     S* xT = x_out + T * N;
@@ -272,7 +279,8 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
         }
     }
     if (!lti) {
-        launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx);
+        launch(k_filter_reduce<N, S, Prod>, nt, B, sh_reduce, st, false, prod, K, thr_agg, tile_agg, term, ctx,
+               trees);
         first = false;
     } else if (nt > 1) {
         if constexpr (Prod::LINEAR_FOLD && N <= 6) {
@@ -299,7 +307,7 @@ map_status run_rts(map_smoother& h, const Prod& prod, S* x_out, S* filt_out, cud
     mark();
     launch(k_filter_down<N, S, Prod>, nt, B, sh_down, st, pdl && !first, prod, K, thr_agg, (const S*)tile_agg,
            prior_of<N, S>(h), (const S*)term, Eg, thr_aff, tile_aff, filt_out, ctx, lt, fin, xT, filtT,
-           (const S*)group_agg);
+           (const S*)group_agg, (const S*)trees);
     mark();
     h.launches += (!lti || nt > 1 ? 1 : 0) + (ng ? 1 : 0) + 2;
     h.path = MAP_PATH_PIPELINE;
@@ -363,7 +371,7 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
         if (lti) sh_states = LtiDownSmem<N, Prod::W, S>::bytes(B, K, lt.co_smem);
     if (!lti) {
         launch(k_filter_reduce<N, S, Prod>, nt, B, sh_tree, st, false, fprod, K, thr_agg, tile_agg, (S*)nullptr,
-               ctx);
+               ctx, (S*)nullptr);
         first = false;
     } else if (nt > 1) {
         if constexpr (Prod::LINEAR_FOLD && N <= 6) {
@@ -384,7 +392,8 @@ map_status run_tf(map_smoother& h, const Prod& fprod, const RProd& rprod, S* x_o
     launch(k_filter_states<N, S, Prod>, nt, B, sh_states, st, pdl && !first, fprod, K, thr_agg,
            (const S*)tile_agg, prior_of<N, S>(h), filt_ws, filt_out, ctx, lt, fin, xT, filtT);
     mark();
-    launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx);
+    launch(k_filter_reduce<N, S, RProd>, nt, B, sh_tree, st, pdl, rprod, K, thr_agg, tile_agg, term, ctx,
+           (S*)nullptr);
     mark();
     h.launches += (!lti || nt > 1 ? 1 : 0) + (ng ? 1 : 0) + 3;
     h.path = MAP_PATH_PIPELINE;
