@@ -108,8 +108,10 @@ typedef struct {
     int discretisation;         /* map_discretisation */
     int smoother;               /* map_smoother_kind */
     int gn_iters;               /* nonlinear models: number of linearisation iterations, >= 1 */
-    double cond_max;            /* FP32: recompute a combine in FP64 when the infinity-norm
-                                   condition estimate of (I + C J) exceeds this (0 = 1e6) */
+    double cond_max;            /* FP32: recompute a combine's (I + C J) inverse in FP64 when
+                                   its infinity-norm condition estimate exceeds this (0 = 1e6);
+                                   a diagonal pivot that fails the pivot test is first redone
+                                   in FP32 with row pivoting, kept within this bound */
     int tile_threads;           /* threads per tile CTA: 32, 64 or 128 (0 = 128, reduced to fit) */
     int substeps;               /* MAP_BLOCK_EULER: Euler substeps per interval, 1..64 (0 = 10) */
     int steps_per_thread;       /* K of the scans, 1..64 (0 = chosen for whole waves of CTAs) */

@@ -253,7 +253,7 @@ __device__ __forceinline__ void coop_inverse(const S* __restrict__ Cm, const S* 
                     buf[Sym<N>::at(i, j)] = Cm[i * L::P + j];
                     buf[NS + Sym<N>::at(i, j)] = Xm[i * L::P + j];
                 }
-            inverse_I_plus_fp64<N, S>(buf, out, ctx.stats);
+            inverse_I_plus_fp64<N, S>(buf, out, ctx.stats, ctx.cond_max);
 #pragma unroll
             for (int i = 0; i < N; ++i)
 #pragma unroll

@@ -149,15 +149,35 @@ __device__ __forceinline__ void convert(const Elem<N, Ss>& s, Elem<N, Sd>& d)
 // ---------------------------------------------------------------------------
 // (I + C P) and its inverse.  Fast path: diagonal pivots in precision S, with
 // the pivot test and the infinity-norm condition estimate.  Slow path (rare):
-// (I + C P) formed and inverted in FP64 with row pivoting; only the inverse is
-// returned, the rest of the operation stays in S.  The slow path copies its
+// in FP32 solves, first the same matrix with row pivoting in FP32, kept when
+// its condition estimate is within cond_max; otherwise (and in FP64 solves)
+// (I + C P) formed and inverted in FP64 with row pivoting.  Only the inverse
+// is returned, the rest of the operation stays in S.  The slow path copies its
 // inputs into a local buffer inside the branch, so the operands of the fast
 // path stay in registers.
 // ---------------------------------------------------------------------------
 template <int N, typename S>
-__device__ __noinline__ void inverse_I_plus_fp64(const S* buf, S* out, unsigned long long* stats)
+__device__ __noinline__ void inverse_I_plus_fp64(const S* buf, S* out, unsigned long long* stats,
+                                                 float cond_max = 0.f)
 {
     constexpr int NS = Sym<N>::SZ;
+    if constexpr (std::is_same<S, float>::value) {
+        if (cond_max > 0.f) {
+            float M[N * N], Mi[N * N];
+            ms::sym_sym<N, float>(buf, buf + NS, M);
+#pragma unroll
+            for (int i = 0; i < N; ++i) M[i * N + i] += 1.f;
+            const float nM = ms::norm_inf<N, float>(M);
+            if (ms::inv_row_pivot<N, float>(M, Mi)) {
+                const float nMi = ms::norm_inf<N, float>(Mi);
+                if (nM * nMi <= cond_max) {           // false for inf and NaN
+#pragma unroll
+                    for (int i = 0; i < N * N; ++i) out[i] = Mi[i];
+                    return;
+                }
+            }
+        }
+    }
     double Cd[NS], Pd[NS], M[N * N], Mi[N * N];
 #pragma unroll
     for (int i = 0; i < NS; ++i) { Cd[i] = double(buf[i]); Pd[i] = double(buf[NS + i]); }
@@ -189,7 +209,7 @@ __device__ __forceinline__ void inverse_I_plus(const S* Cp, const S* Pp, S* Mi, 
         S buf[2 * NS], out[N * N];
 #pragma unroll
         for (int i = 0; i < NS; ++i) { buf[i] = Cp[i]; buf[NS + i] = Pp[i]; }
-        inverse_I_plus_fp64<N, S>(buf, out, stats);
+        inverse_I_plus_fp64<N, S>(buf, out, stats, cond_max);
 #pragma unroll
         for (int i = 0; i < N * N; ++i) Mi[i] = out[i];
     }
