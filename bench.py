@@ -344,6 +344,9 @@ def ours(args):
     e2e = {"value": world * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y_host.numel() * wbytes),
            "d2h_bytes_per_step": int(x_host.numel() * wbytes), "ms_per_step": e2e_s * 1e3}
 
+    # geometry of the timed path (read before the profiled solves below, which
+    # run the three-kernel pipeline with its own geometry)
+    K_g, B_g, nt_g = sm.geometry()
     # per-phase device times (profiled solves, L2 flushed before each; these run
     # the three-kernel pipeline, whose kernel boundaries the events mark)
     sm.profile(True)
@@ -355,8 +358,8 @@ def ours(args):
             phases.setdefault(k, []).append(v)
     sm.profile(False)
     phase_ms = {k: statistics.median(v) for k, v in phases.items()}
-    K_g, B_g, nt_g = sm.geometry()
-    flops, byt = work_model(4, 2, K_g, B_g, nt_g, wbytes, r=2)
+    K_p, B_p, nt_p = sm.geometry()             # the profiled pipeline's
+    flops, byt = work_model(4, 2, K_p, B_p, nt_p, wbytes, r=2)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     try:
