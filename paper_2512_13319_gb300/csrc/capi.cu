@@ -97,6 +97,7 @@ void free_handle(map_smoother* h)
     if (h->d_y) cudaFree(h->d_y);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_xtmp) cudaFree(h->d_xtmp);
+    if (h->d_etab) cudaFree(h->d_etab);
     if (h->d_cost) cudaFree(h->d_cost);
     if (h->d_lam) cudaFree(h->d_lam);
     if (h->d_grad) cudaFree(h->d_grad);
@@ -271,6 +272,11 @@ map_status create_impl(map_smoother* h, const map_problem_desc* d)
     if ((e = cudaMalloc(&h->d_cost, sizeof(double))) != cudaSuccess) return cuda_fail(*h, e, "cudaMalloc");
     if (h->model != MAP_MODEL_LINEAR) {
         if ((e = cudaMalloc(&h->d_xtmp, (size_t)(h->T + 1) * n * es)) != cudaSuccess)
+            return cuda_fail(*h, e, "cudaMalloc");
+        // exact per-step elements: one row of (A, b, C) per step, formed once per
+        // iteration (rows of whole 16-byte words)
+        const size_t rs = ((size_t)(n * n + n + n * (n + 1) / 2) * es + 15) / 16 * 16;
+        if (h->disc == MAP_EXPM && (e = cudaMalloc(&h->d_etab, (size_t)h->T * rs)) != cudaSuccess)
             return cuda_fail(*h, e, "cudaMalloc");
     } else {
         if ((e = cudaMalloc(&h->d_lam, (size_t)(h->T + 1) * n * es)) != cudaSuccess)

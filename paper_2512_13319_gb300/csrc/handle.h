@@ -30,6 +30,7 @@ struct map_smoother {
     void* d_y = nullptr;               // staging for the host-buffer entry point
     void* d_x = nullptr;
     void* d_xtmp = nullptr;            // Gauss-Newton ping-pong trajectory
+    void* d_etab = nullptr;            // Gauss-Newton with exact per-step elements: (A, b, C) of every step
     double* d_cost = nullptr;
     void* d_lam = nullptr;             // adjoint trajectory (linear models)
     double* d_grad = nullptr;          // gradient accumulators

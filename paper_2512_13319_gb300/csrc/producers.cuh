@@ -552,6 +552,14 @@ __device__ __forceinline__ void local_exact_element(const S* F, const S* c, cons
         for (int d = a; d < N; ++d) Cp[Sym<N>::at(a, d)] = S(0.5) * (Cf[a * N + d] + Cf[d * N + a]);
 }
 
+// Row layout of the per-step exact elements (A, b, C packed) of an iteration,
+// rows of whole 16-byte words
+template <int N, typename S>
+struct ExactRow {
+    static constexpr int oA = 0, ob = N * N, oC = N * N + N;
+    static constexpr int RS = ((N * N + N + Sym<N>::SZ) * (int)sizeof(S) + 15) / 16 * 16 / (int)sizeof(S);
+};
+
 template <class Model, typename S>
 struct NlProducer {
     static constexpr int N = Model::N, M = Model::M;
@@ -564,6 +572,7 @@ struct NlProducer {
     const S* xbar;                    // (T+1, N)
     long T;
     NlParams<N, M, S> p;
+    const S* etab = nullptr;          // exact elements of this iteration (ExactRow), or formed per use
 
     template <int K>
     __device__ __forceinline__ void load(long k0, S (&buf)[K * W]) const
@@ -613,7 +622,18 @@ struct NlProducer {
                 for (int j = 0; j < N; ++j) s = fma(-Fj[i * N + j], x1[j], s);
                 cl[i] = s;
             }
-            local_exact_element<N, S>(Fj, cl, p.Q, dt, e.A, e.b, e.C);
+            if (etab) {
+                using ER = ExactRow<N, S>;
+                const S* r = etab + k * ER::RS;
+#pragma unroll
+                for (int q = 0; q < N * N; ++q) e.A[q] = __ldg(r + ER::oA + q);
+#pragma unroll
+                for (int q = 0; q < N; ++q) e.b[q] = __ldg(r + ER::ob + q);
+#pragma unroll
+                for (int q = 0; q < Sym<N>::SZ; ++q) e.C[q] = __ldg(r + ER::oC + q);
+            } else {
+                local_exact_element<N, S>(Fj, cl, p.Q, dt, e.A, e.b, e.C);
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -655,5 +675,36 @@ struct NlProducer {
             }
     }
 };
+
+// The exact elements (A, b, C) of every step of one Gauss-Newton iteration,
+// linearised at xbar_{k+1}: one thread per step, so that the scan kernels read
+// them instead of forming them in each of their passes.
+template <class Model, typename S>
+__global__ void __launch_bounds__(128) k_exact_rows(const NlProducer<Model, S> prod, S* __restrict__ tab)
+{
+    constexpr int N = Model::N;
+    using ER = ExactRow<N, S>;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= prod.T) return;
+    S x1[N], f[N], Fj[N * N], gd[N], cl[N], A[N * N], b[N], Cp[Sym<N>::SZ];
+#pragma unroll
+    for (int j = 0; j < N; ++j) x1[j] = __ldg(prod.xbar + (k + 1) * N + j);
+    Model::drift(prod.p, x1, f, Fj, gd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        S s = f[i];
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(-Fj[i * N + j], x1[j], s);
+        cl[i] = s;
+    }
+    local_exact_element<N, S>(Fj, cl, prod.p.Q, prod.p.dt, A, b, Cp);
+    S* r = tab + k * ER::RS;
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) r[ER::oA + q] = A[q];
+#pragma unroll
+    for (int q = 0; q < N; ++q) r[ER::ob + q] = b[q];
+#pragma unroll
+    for (int q = 0; q < Sym<N>::SZ; ++q) r[ER::oC + q] = Cp[q];
+}
 
 }  // namespace mapk

@@ -1405,6 +1405,15 @@ map_status solve_nonlinear(map_smoother& h, const void* y, void* x_out, void* fi
     for (int it = 0; it < h.gn_iters; ++it) {
         prod.xbar = cur;
         const bool last = it + 1 == h.gn_iters;
+        if (prod.p.expm && h.d_etab) {
+            // the exact elements of this iteration, once, for both scan passes
+            prod.etab = nullptr;
+            k_exact_rows<Model, S><<<(unsigned)((h.T + 127) / 128), 128, 0, st>>>(prod, static_cast<S*>(h.d_etab));
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+            prod.etab = static_cast<const S*>(h.d_etab);
+            h.launches += 1;
+        }
         map_status s = run_rts<N, S>(h, prod, nxt, last ? static_cast<S*>(filt_out) : nullptr, st);
         if (s != MAP_OK) return s;
         std::swap(cur, nxt);
