@@ -39,10 +39,10 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;
 constexpr int SETUP_IN_DOUBLES = 8 * 8 * 4 + 8 * 5 + 8 * 8 * 2;   // F, L, W, H, R, P0 + vectors
 
-__device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
-__device__ __align__(256) unsigned long long g_stats[mapk::STATS_WORDS];   // event words (no error flags)
-__device__ __align__(256) double g_setup_in[SETUP_IN_DOUBLES];
-__device__ __align__(256) mapk::SetupOut g_setup_out;
+static __device__ __align__(256) unsigned char g_scratch[NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned long long g_stats[mapk::STATS_WORDS];   // event words (no error flags)
+static __device__ __align__(256) double g_setup_in[SETUP_IN_DOUBLES];
+static __device__ __align__(256) mapk::SetupOut g_setup_out;
 
 struct DeviceArrays {
     int device = 0;
