@@ -390,7 +390,7 @@ def ours(args):
                     "hbm": {"achieved_gbs": achieved_gb, "peak_gbs": hbm_peak, "frac": fh,
                             "bytes_per_step": byte_step, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
                     "note": "neither pipe is saturated: the solve is bound by the latency of its two "
-                            "grid barriers and of the per-thread recursions (see DESIGN.md)"}
+                            "grid barriers, about 2 us each, and of the per-thread recursions"}
     elif kernels_per_solve == 1:
         # one cooperative launch runs the whole solve: its duration is the
         # timed solve, its work the three phases' work
