@@ -64,7 +64,7 @@ typedef enum {
     MAP_ERR_CUDA = -3,          /* a CUDA runtime call failed */
     MAP_ERR_SINGULAR = -4,      /* a matrix that must be invertible was not */
     MAP_ERR_TIMEOUT = -5,       /* a bounded device wait ran out (see "Device errors" below) */
-    MAP_ERR_UNSUPPORTED = -6    /* valid request this build does not implement */
+    MAP_ERR_UNSUPPORTED = -6    /* valid request that this library does not implement */
 } map_status;
 
 typedef enum {
